@@ -1,0 +1,841 @@
+// ORACLE -- test infrastructure only.
+//
+// A plain, slow, FP64 CPU restatement of the calibration objective and of the parallel
+// simulated-annealing search of Ferreiro, Garcia, Lopez-Salas and Vazquez, "SABR/LIBOR market
+// models: pricing and calibration for some interest rate derivatives" (arXiv 2408.01470).
+// Only the test-suite, the smoke check and the CPU-baseline leg of the benchmark load it.  It
+// shares no code, header, table or helper with the CUDA library; the two meet only through the
+// seeded synthetic inputs.
+//
+// Every numeric routine is templated on its scalar so that the same definitions, instantiated
+// with forward-mode dual numbers, give the gradient and the Jacobian (an independent route from
+// the library's hand-written adjoint).
+//
+// What each part follows, and what pins it (tests/test_oracle_*.py):
+//   normal_cdf / black / vega ...... Black's formula for caplets and swaptions (Section 1, the
+//                                    cost functions of Section 3).  Pins: closed-form points,
+//                                    put-call parity, the zero-vol and zero-strike limits.
+//   sabr_hagan2002 ................. Hagan et al.'s lognormal expansion with the z/x(z) factor,
+//                                    named as "the Hagan second order approximation" in
+//                                    Section 2.1.  Pins: beta=1,nu=0 gives alpha; ATM limit;
+//                                    mirror symmetry; a 50-digit evaluation of the textbook form.
+//   sabr_paper ..................... Eq. (sigmaHagan) as printed.  Pin: the paper's calibrated
+//                                    parameters (Table tab:paramsHaganVolas) reproduce its model
+//                                    vols (Table tab:haganVolas).
+//   rebonato_caplet ................ Eq. (haganForRebonato), the integrals by composite
+//                                    Gauss-Legendre.  Pins: closed form of int g^2, 50-digit
+//                                    adaptive quadrature of both integrals.
+//   swap_params .................... the approximate swaption volatility (a quadratic form of
+//                                    time-integrated forward-rate vols over the correlation
+//                                    matrices of Eqs. rhoij, thetaij, phiij).  The paper names it
+//                                    but does not print it; this is the reading fixed for this
+//                                    project.  Pins: one-period swap == caplet; rho=1 with equal
+//                                    vols gives the caplet vol; V1 >= 0.
+//   objective ...................... f_c and f_s of Section 3 in price space with vega weights.
+//                                    Pin: zero at the generating point on noise-free quotes.
+//   philox4x64_10 .................. Salmon, Moraes, Dror, Shaw (SC'11).  Pins: numpy's Philox
+//                                    bit generator and the all-zero known-answer vector.
+//   anneal ......................... the SA loop of Section 3 and its one-GPU parallel form
+//                                    (chains per level, min-reduction, broadcast).  Pins: the
+//                                    evaluation-count identity C(LN+1); recovery on tiny sets.
+//   lm ............................. Levenberg-Marquardt polish (replaces the Nelder-Mead of the
+//                                    hybrid scheme in Section 3).  Pin: recovery of the
+//                                    generating point on noise-free quotes.
+//
+// Readings of places where the paper is silent are listed at each function.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <map>
+#include <utility>
+#include <algorithm>
+#include <limits>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace orc {
+
+// ------------------------------------------------------------------ dual numbers (forward mode)
+constexpr int ND = 12;
+
+struct Dual {
+  double v;
+  double d[ND];
+  Dual() : v(0.0) { for (int i = 0; i < ND; ++i) d[i] = 0.0; }
+  Dual(double x) : v(x) { for (int i = 0; i < ND; ++i) d[i] = 0.0; }
+};
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+
+inline Dual operator+(const Dual& a, const Dual& b) { Dual r(a.v + b.v); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+inline Dual operator-(const Dual& a, const Dual& b) { Dual r(a.v - b.v); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+inline Dual operator*(const Dual& a, const Dual& b) { Dual r(a.v * b.v); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+inline Dual operator/(const Dual& a, const Dual& b) { Dual r(a.v / b.v); for (int i = 0; i < ND; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v); return r; }
+inline Dual operator-(const Dual& a) { Dual r(-a.v); for (int i = 0; i < ND; ++i) r.d[i] = -a.d[i]; return r; }
+inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
+inline Dual operator+(double a, const Dual& b) { return b + a; }
+inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
+inline Dual operator-(double a, const Dual& b) { return -b + a; }
+inline Dual operator*(const Dual& a, double b) { Dual r(a.v * b); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b; return r; }
+inline Dual operator*(double a, const Dual& b) { return b * a; }
+inline Dual operator/(const Dual& a, double b) { Dual r(a.v / b); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] / b; return r; }
+inline Dual operator/(double a, const Dual& b) { Dual r(a / b.v); for (int i = 0; i < ND; ++i) r.d[i] = -a * b.d[i] / (b.v * b.v); return r; }
+inline Dual& operator+=(Dual& a, const Dual& b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, const Dual& b) { a = a - b; return a; }
+inline Dual& operator*=(Dual& a, const Dual& b) { a = a * b; return a; }
+
+// chain rule: f(a) with f'(a) = dv
+inline Dual chain(const Dual& a, double fv, double dv) { Dual r(fv); for (int i = 0; i < ND; ++i) r.d[i] = dv * a.d[i]; return r; }
+inline Dual exp(const Dual& a) { double e = std::exp(a.v); return chain(a, e, e); }
+inline Dual log(const Dual& a) { return chain(a, std::log(a.v), 1.0 / a.v); }
+inline Dual log1p(const Dual& a) { return chain(a, std::log1p(a.v), 1.0 / (1.0 + a.v)); }
+inline Dual sqrt(const Dual& a) { double s = std::sqrt(a.v); return chain(a, s, 0.5 / s); }
+inline Dual erfc(const Dual& a) { return chain(a, std::erfc(a.v), -2.0 / std::sqrt(M_PI) * std::exp(-a.v * a.v)); }
+
+using std::exp; using std::log; using std::log1p; using std::sqrt; using std::erfc;
+
+// ------------------------------------------------------------------ Gauss-Legendre nodes
+// Roots of the Legendre polynomial P_n by Newton's method on the three-term recurrence,
+// in long double; weights 2 / ((1 - x^2) P_n'(x)^2).  Nodes ascending.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0); w.assign(n, 0.0);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n; ++i) {
+    long double z = std::cos(pi * (i + 0.75L) / (n + 0.5L));
+    long double dp = 0.0L;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1.0L, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        long double p2 = ((2.0L * k - 1.0L) * z * p1 - (k - 1.0L) * p0) / k;
+        p0 = p1; p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0L);
+      long double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs((double)dz) < 1e-19) break;
+    }
+    // recompute the derivative at the converged root
+    long double p0 = 1.0L, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      long double p2 = ((2.0L * k - 1.0L) * z * p1 - (k - 1.0L) * p0) / k;
+      p0 = p1; p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0L);
+    x[n - 1 - i] = (double)z;
+    w[n - 1 - i] = (double)(2.0L / ((1.0L - z * z) * dp * dp));
+  }
+  // i-th root from the top is descending in z; reversed above -> ascending
+}
+
+// ------------------------------------------------------------------ Black's formula
+// Phi(x) = erfc(-x / sqrt 2) / 2.
+template <class S> S normal_cdf(const S& x) { return 0.5 * erfc(-x / std::sqrt(2.0)); }
+
+// Black's formula for an option on a forward F struck at K, expiry T, Black vol sigma, discount
+// D (tau P(0,T_{k+1}) for a caplet, the annuity for a swaption).
+template <class S> S black_call(double F, double K, double T, const S& sigma, double D) {
+  S v = sigma * std::sqrt(T);
+  S d1 = std::log(F / K) / v + 0.5 * v;
+  S d2 = d1 - v;
+  return D * (F * normal_cdf(d1) - K * normal_cdf(d2));
+}
+template <class S> S black_put(double F, double K, double T, const S& sigma, double D) {
+  S v = sigma * std::sqrt(T);
+  S d1 = std::log(F / K) / v + 0.5 * v;
+  S d2 = d1 - v;
+  return D * (K * normal_cdf(-d2) - F * normal_cdf(-d1));
+}
+// Reading: every quote is priced as its out-of-the-money option (a put below the forward, a call
+// at or above it); put-call parity makes the two sides equivalent.
+template <class S> S black_otm(double F, double K, double T, const S& sigma, double D) {
+  return (K < F) ? black_put(F, K, T, sigma, D) : black_call(F, K, T, sigma, D);
+}
+// dPrice/dsigma, identical for calls and puts.
+static double black_vega(double F, double K, double T, double sigma, double D) {
+  double v = sigma * std::sqrt(T);
+  double d1 = std::log(F / K) / v + 0.5 * v;
+  return D * F * std::exp(-0.5 * d1 * d1) / std::sqrt(2.0 * M_PI) * std::sqrt(T);
+}
+
+// ------------------------------------------------------------------ SABR implied vol
+// x(z) = log((sqrt(1 - 2 rho z + z^2) + z - rho) / (1 - rho)), written as log1p of
+// ((s - 1) + z) / (1 - rho) with s - 1 = (z^2 - 2 rho z) / (s + 1) for z >= 0, and through the
+// exact mirror x(z; rho) = -x(-z; -rho) for z < 0 (both rewrites are algebraic identities).
+template <class S> S x_of_z(const S& z, const S& rho) {
+  if (val(z) < 0.0) return -x_of_z(-z, -rho);
+  S s = sqrt(1.0 - 2.0 * rho * z + z * z);
+  return log1p(((z * z - 2.0 * rho * z) / (s + 1.0) + z) / (1.0 - rho));
+}
+// z / x(z), with its Taylor series 1 - rho z / 2 + (2 - 3 rho^2) z^2 / 12 for |z| < 1e-6.
+template <class S> S z_over_x(const S& z, const S& rho) {
+  if (std::fabs(val(z)) < 1e-6) return 1.0 - 0.5 * rho * z + (2.0 - 3.0 * rho * rho) * z * z / 12.0;
+  return z / x_of_z(z, rho);
+}
+
+// Hagan, Kumar, Lesniewski, Woodward (2002), lognormal expansion:
+//   sigma = alpha / ((FK)^{(1-b)/2} [1 + (1-b)^2 l^2/24 + (1-b)^4 l^4/1920]) * z/x(z)
+//           * {1 + [(1-b)^2 alpha^2 / (24 (FK)^{1-b}) + rho b nu alpha / (4 (FK)^{(1-b)/2})
+//                  + (2 - 3 rho^2) nu^2 / 24] T},
+//   l = log(F/K), z = (nu/alpha) (FK)^{(1-b)/2} l.
+template <class S>
+S sabr_hagan2002(double F, double K, double T, const S& alpha, double beta, const S& rho, const S& nu) {
+  double omb = 1.0 - beta;
+  double fk = std::pow(F * K, 0.5 * omb);
+  double l = std::log(F / K);
+  S z = nu / alpha * fk * l;
+  S zx = z_over_x(z, rho);
+  double den = fk * (1.0 + omb * omb * l * l / 24.0 + omb * omb * omb * omb * l * l * l * l / 1920.0);
+  S corr = 1.0 + (omb * omb * alpha * alpha / (24.0 * fk * fk) + rho * beta * nu * alpha / (4.0 * fk)
+                  + (2.0 - 3.0 * rho * rho) * nu * nu / 24.0) * T;
+  return alpha / den * zx * corr;
+}
+
+// Eq. (sigmaHagan) verbatim, with phi_ii -> rho, sigma_i -> nu, omega = F^{1-b} / alpha,
+// m = log(K/F).  No expiry dependence.
+template <class S>
+S sabr_paper(double F, double K, const S& alpha, double beta, const S& rho, const S& nu) {
+  double omb = 1.0 - beta;
+  double fo = std::pow(F, omb);
+  S omega = fo / alpha;
+  double m = std::log(K / F);
+  S rno = rho * nu * omega;
+  return alpha / fo * (1.0 - 0.5 * (omb - rno) * m
+                       + (omb * omb + (2.0 - 3.0 * rho * rho) * nu * nu * omega * omega + 3.0 * (omb - rno)) * (m * m) / 12.0);
+}
+
+// ------------------------------------------------------------------ market
+struct Desc {  // mirrors the ctypes structure in oracle/__init__.py
+  int32_t model, formula;
+  double beta;
+  int32_t n_fwd;
+  const double* T;
+  const double* P;
+  int32_t n_cap;
+  const int32_t* cap_fwd;
+  const double* cap_K;
+  const double* cap_vol;
+  const double* cap_w;  // may be null -> 1/vega^2
+  int32_t n_swp;
+  const int32_t* swp_start;
+  const int32_t* swp_end;
+  const double* swp_K;
+  const double* swp_vol;
+  const double* swp_w;
+  int32_t n_param;
+  const double* lo;
+  const double* hi;
+  const uint8_t* free_mask;
+  double panel;
+  int32_t quad_nodes;
+};
+
+struct Market {
+  int model, formula, n_param, Q;
+  double beta, panel;
+  std::vector<double> T, P, F, tau;
+  // caplets
+  std::vector<int> cfwd;
+  std::vector<double> cK, cvol, cw, cpm;
+  // swaptions, with the distinct underlying swaps
+  std::vector<int> sstart, send, sswap;
+  std::vector<double> sK, svol, sw, spm;
+  std::vector<std::pair<int, int>> swaps;
+  std::vector<double> swapA, swapS;           // annuity, swap rate
+  std::vector<std::vector<double>> swapW;     // W_i = w_i F_i^b / S^b over the window
+  std::vector<double> lo, hi;
+  std::vector<uint8_t> freem;
+  std::vector<double> xi, wi;                 // Gauss-Legendre on [-1, 1]
+  int n_instr() const { return (int)cK.size() + (int)sK.size(); }
+};
+
+static int n_panels(double t, double panel) { return (int)std::lround(t / panel); }
+
+static Market* build_market(const Desc* d) {
+  Market* m = new Market();
+  m->model = d->model; m->formula = d->formula; m->beta = d->beta; m->n_param = d->n_param;
+  m->panel = d->panel; m->Q = d->quad_nodes;
+  int n = d->n_fwd;
+  m->T.assign(d->T, d->T + n + 1);
+  m->P.assign(d->P, d->P + n + 1);
+  m->F.resize(n); m->tau.resize(n);
+  for (int k = 0; k < n; ++k) {
+    m->tau[k] = m->T[k + 1] - m->T[k];
+    m->F[k] = (m->P[k] / m->P[k + 1] - 1.0) / m->tau[k];   // simply-compounded forward
+  }
+  gauss_legendre(m->Q, m->xi, m->wi);
+  m->lo.assign(d->lo, d->lo + d->n_param);
+  m->hi.assign(d->hi, d->hi + d->n_param);
+  m->freem.assign(d->free_mask, d->free_mask + d->n_param);
+  for (int k = 0; k < d->n_cap; ++k) {
+    int i = d->cap_fwd[k];
+    double F = m->F[i], K = d->cap_K[k], T = m->T[i], D = m->tau[i] * m->P[i + 1];
+    double vol = d->cap_vol ? d->cap_vol[k] : 0.2;
+    m->cfwd.push_back(i); m->cK.push_back(K); m->cvol.push_back(vol);
+    m->cpm.push_back(black_otm(F, K, T, vol, D));
+    double vg = black_vega(F, K, T, vol, D);
+    m->cw.push_back(d->cap_w ? d->cap_w[k] : 1.0 / (vg * vg));
+  }
+  std::map<std::pair<int, int>, int> index;
+  for (int s = 0; s < d->n_swp; ++s) {
+    int a = d->swp_start[s], b = d->swp_end[s];
+    auto key = std::make_pair(a, b);
+    if (!index.count(key)) {
+      int id = (int)m->swaps.size();
+      index[key] = id;
+      m->swaps.push_back(key);
+      double A = 0.0;
+      for (int k = a; k < b; ++k) A += m->tau[k] * m->P[k + 1];
+      double S = 0.0;
+      for (int k = a; k < b; ++k) S += m->tau[k] * m->P[k + 1] / A * m->F[k];
+      std::vector<double> W;
+      for (int k = a; k < b; ++k)
+        W.push_back(m->tau[k] * m->P[k + 1] / A * std::pow(m->F[k], m->beta) / std::pow(S, m->beta));
+      m->swapA.push_back(A); m->swapS.push_back(S); m->swapW.push_back(W);
+    }
+    int id = index[key];
+    double K = d->swp_K[s], T = m->T[a], A = m->swapA[id], S = m->swapS[id];
+    double vol = d->swp_vol ? d->swp_vol[s] : 0.2;
+    m->sstart.push_back(a); m->send.push_back(b); m->sswap.push_back(id);
+    m->sK.push_back(K); m->svol.push_back(vol);
+    m->spm.push_back(black_otm(S, K, T, vol, A));
+    double vg = black_vega(S, K, T, vol, A);
+    m->sw.push_back(d->swp_w ? d->swp_w[s] : 1.0 / (vg * vg));
+  }
+  return m;
+}
+
+// ------------------------------------------------------------------ Rebonato model
+// g(u) and h(u) at time-to-fixing u = T_i - t (Section 2.3).
+template <class S> S g_of(const S* th, double u) { return (th[0] + th[1] * u) * exp(-th[2] * u) + th[3]; }
+template <class S> S h_of(const S* th, double u) { return (th[4] + th[5] * u) * exp(-th[6] * u) + th[7]; }
+
+// Eq. (haganForRebonato) with kappa = 1, the caplet's SABR alpha and nu:
+//   G = int_0^Ti g(Ti - t)^2 dt,   X = int_0^Ti g(Ti - t)^2 H(t) dt,   H(t) = int_0^t h(Ti - s)^2 ds
+//   (t hhat(t)^2 = H(t) removes the 1/t of the printed form),
+//   alpha = sqrt(G / Ti),   nu = sqrt(2 X) / (alpha Ti).
+// Reading (the quadrature is the definition): composite Gauss-Legendre with Q nodes on every
+// panel [p D, (p+1) D] of [0, Ti]; H at a node t of panel p is the sum of the full panels below
+// plus a Q-node Gauss-Legendre rule on [p D, t].
+template <class S>
+void rebonato_caplet(const Market& m, const S* th, double Ti, S& alpha, S& nu, S* Gout = nullptr, S* Xout = nullptr) {
+  const int n = n_panels(Ti, m.panel), Q = m.Q;
+  const double D = m.panel;
+  S G = 0.0, X = 0.0, Hcum = 0.0;
+  for (int p = 0; p < n; ++p) {
+    double t0 = p * D;
+    for (int q = 0; q < Q; ++q) {
+      double t = t0 + 0.5 * D * (1.0 + m.xi[q]);
+      double wq = 0.5 * D * m.wi[q];
+      S gv = g_of(th, Ti - t);
+      double half = 0.5 * (t - t0);
+      S part = 0.0;
+      for (int r = 0; r < Q; ++r) {
+        double s = t0 + half * (1.0 + m.xi[r]);
+        S hv = h_of(th, Ti - s);
+        part += half * m.wi[r] * hv * hv;
+      }
+      G += wq * gv * gv;
+      X += wq * gv * gv * (Hcum + part);
+    }
+    for (int q = 0; q < Q; ++q) {
+      double t = t0 + 0.5 * D * (1.0 + m.xi[q]);
+      S hv = h_of(th, Ti - t);
+      Hcum += 0.5 * D * m.wi[q] * hv * hv;
+    }
+  }
+  alpha = sqrt(G / Ti);
+  nu = sqrt(2.0 * X) / (alpha * Ti);
+  if (Gout) *Gout = G;
+  if (Xout) *Xout = X;
+}
+
+// The approximate swaption volatility (reading; the paper names Rebonato's approximation but
+// prints no formula).  For the swap over forwards [a, b) with expiry T = T_a, frozen weights
+// W_i = w_i F_i^b / S^b and
+//   G_ij = int_0^T g_i g_j dt,   X_ij = theta_ij int_0^T g_i g_j (int_0^t h_i h_j ds) dt,
+//   V1 = sum W_i W_j rho_ij G_ij,  V2 = sum W_i W_j rho_ij X_ij,  V3 = sum W_i W_j phi_ij G_ij,
+//   alpha_S = sqrt(V1 / T),  nu_S = sqrt(2 V2) / (alpha_S T),  rho_S = clamp(V3 / V1, +-0.999),
+// with rho_ij, theta_ij, phi_ij from Eqs. (rhoij), (thetaij), (phiij) at eta1 = eta2 = 0 and
+// phi_ii = phi for every forward, and the quadrature of rebonato_caplet.  For a one-period swap
+// this is exactly the caplet mapping.
+template <class S>
+void swap_params(const Market& m, const S* th, int id, S& alpha, S& nu, S& rho, S* V = nullptr) {
+  const int a = m.swaps[id].first, b = m.swaps[id].second, Q = m.Q;
+  const double TE = m.T[a], D = m.panel;
+  const int n = n_panels(TE, D);
+  const std::vector<double>& W = m.swapW[id];
+  S V1 = 0.0, V2 = 0.0, V3 = 0.0;
+  for (int i = a; i < b; ++i) {
+    for (int j = a; j < b; ++j) {
+      double Ti = m.T[i], Tj = m.T[j], dT = std::fabs(Ti - Tj);
+      S rho_ij = exp(-th[9] * dT);
+      S theta_ij = exp(-th[10] * dT);
+      S phi_ij = th[8] * exp(-th[11] * dT);
+      S Gij = 0.0, Xij = 0.0, Hcum = 0.0;
+      for (int p = 0; p < n; ++p) {
+        double t0 = p * D;
+        for (int q = 0; q < Q; ++q) {
+          double t = t0 + 0.5 * D * (1.0 + m.xi[q]);
+          double wq = 0.5 * D * m.wi[q];
+          S gg = g_of(th, Ti - t) * g_of(th, Tj - t);
+          double half = 0.5 * (t - t0);
+          S part = 0.0;
+          for (int r = 0; r < Q; ++r) {
+            double s = t0 + half * (1.0 + m.xi[r]);
+            part += half * m.wi[r] * h_of(th, Ti - s) * h_of(th, Tj - s);
+          }
+          Gij += wq * gg;
+          Xij += wq * gg * (Hcum + part);
+        }
+        for (int q = 0; q < Q; ++q) {
+          double t = t0 + 0.5 * D * (1.0 + m.xi[q]);
+          Hcum += 0.5 * D * m.wi[q] * h_of(th, Ti - t) * h_of(th, Tj - t);
+        }
+      }
+      Xij = theta_ij * Xij;
+      double WW = W[i - a] * W[j - a];
+      V1 += WW * rho_ij * Gij;
+      V2 += WW * rho_ij * Xij;
+      V3 += WW * phi_ij * Gij;
+    }
+  }
+  alpha = sqrt(V1 / TE);
+  nu = sqrt(2.0 * V2) / (alpha * TE);
+  S r = V3 / V1;
+  if (val(r) > 0.999) r = S(0.999);
+  if (val(r) < -0.999) r = S(-0.999);
+  rho = r;
+  if (V) { V[0] = V1; V[1] = V2; V[2] = V3; }
+}
+
+// ------------------------------------------------------------------ model vols, objective
+template <class S>
+S model_vol(const Market& m, double F, double K, double T, const S& alpha, const S& rho, const S& nu) {
+  if (m.formula == 1) return sabr_paper(F, K, alpha, m.beta, rho, nu);
+  return sabr_hagan2002(F, K, T, alpha, m.beta, rho, nu);
+}
+
+// Model vols of every instrument (caplets first, then swaptions), per-forward and per-swap SABR
+// parameters computed once each.
+template <class S>
+void all_vols(const Market& m, const S* th, std::vector<S>& vols) {
+  const int nc = (int)m.cK.size(), ns = (int)m.sK.size();
+  vols.assign(nc + ns, S(0.0));
+  std::map<int, std::pair<S, S>> fwd_par;
+  for (int k = 0; k < nc; ++k) {
+    int i = m.cfwd[k];
+    double F = m.F[i], K = m.cK[k], T = m.T[i];
+    if (m.model == 0) {
+      vols[k] = model_vol(m, F, K, T, th[0], th[1], th[2]);
+    } else {
+      auto it = fwd_par.find(i);
+      if (it == fwd_par.end()) {
+        S al, nu;
+        rebonato_caplet(m, th, T, al, nu);
+        it = fwd_par.emplace(i, std::make_pair(al, nu)).first;
+      }
+      vols[k] = model_vol(m, F, K, T, it->second.first, th[8], it->second.second);
+    }
+  }
+  std::vector<int> done(m.swaps.size(), 0);
+  std::vector<S> sa(m.swaps.size()), sn(m.swaps.size()), sr(m.swaps.size());
+  for (int s = 0; s < ns; ++s) {
+    int id = m.sswap[s];
+    if (!done[id]) { swap_params(m, th, id, sa[id], sn[id], sr[id]); done[id] = 1; }
+    vols[nc + s] = model_vol(m, m.swapS[id], m.sK[s], m.T[m.sstart[s]], sa[id], sr[id], sn[id]);
+  }
+}
+
+// Residuals r_k = sqrt(w_k) (P_k(theta) - P_k^mkt); returns false if any model vol is not a
+// finite positive number (the point is infeasible: f = +inf).
+template <class S>
+bool residuals(const Market& m, const S* th, std::vector<S>& r) {
+  std::vector<S> vols;
+  all_vols(m, th, vols);
+  const int nc = (int)m.cK.size(), ns = (int)m.sK.size();
+  r.assign(nc + ns, S(0.0));
+  for (int k = 0; k < nc + ns; ++k) {
+    double v = val(vols[k]);
+    if (!(v > 0.0) || !std::isfinite(v)) return false;
+  }
+  for (int k = 0; k < nc; ++k) {
+    int i = m.cfwd[k];
+    S p = black_otm(m.F[i], m.cK[k], m.T[i], vols[k], m.tau[i] * m.P[i + 1]);
+    r[k] = std::sqrt(m.cw[k]) * (p - m.cpm[k]);
+  }
+  for (int s = 0; s < ns; ++s) {
+    int id = m.sswap[s];
+    S p = black_otm(m.swapS[id], m.sK[s], m.T[m.sstart[s]], vols[nc + s], m.swapA[id]);
+    r[nc + s] = std::sqrt(m.sw[s]) * (p - m.spm[s]);
+  }
+  return true;
+}
+
+// f(theta) = sum_k w_k (P_k(theta) - P_k^mkt)^2, summed in instrument order; +inf if infeasible.
+// Reading: f_c of Section 3 is a sum of squared vol errors; pricing in price space with
+// w_k = 1 / vega_k(sigma_k^mkt)^2 keeps it equal to f_c to first order.
+template <class S>
+S objective_t(const Market& m, const S* th) {
+  std::vector<S> vols;
+  all_vols(m, th, vols);
+  const int nc = (int)m.cK.size(), ns = (int)m.sK.size();
+  S f = 0.0;
+  for (int k = 0; k < nc + ns; ++k) {
+    double v = val(vols[k]);
+    if (!(v > 0.0) || !std::isfinite(v)) return S(std::numeric_limits<double>::infinity());
+  }
+  for (int k = 0; k < nc; ++k) {
+    int i = m.cfwd[k];
+    S p = black_otm(m.F[i], m.cK[k], m.T[i], vols[k], m.tau[i] * m.P[i + 1]);
+    S e = p - m.cpm[k];
+    f += m.cw[k] * e * e;
+  }
+  for (int s = 0; s < ns; ++s) {
+    int id = m.sswap[s];
+    S p = black_otm(m.swapS[id], m.sK[s], m.T[m.sstart[s]], vols[nc + s], m.swapA[id]);
+    S e = p - m.spm[s];
+    f += m.sw[s] * e * e;
+  }
+  if (!std::isfinite(val(f))) return S(std::numeric_limits<double>::infinity());
+  return f;
+}
+
+static double objective(const Market& m, const double* th) { return objective_t<double>(m, th); }
+
+// RMSE of model vols against market vols, in vol points.
+static double rmse_volpt(const Market& m, const double* th) {
+  std::vector<double> vols;
+  all_vols(m, th, vols);
+  const int nc = (int)m.cK.size();
+  double s = 0.0;
+  for (size_t k = 0; k < vols.size(); ++k) {
+    double mk = k < (size_t)nc ? m.cvol[k] : m.svol[k - nc];
+    double e = vols[k] - mk;
+    s += e * e;
+  }
+  return 100.0 * std::sqrt(s / (double)vols.size());
+}
+
+static void seed_duals(const Market& m, const double* th, std::vector<Dual>& x) {
+  x.assign(m.n_param, Dual(0.0));
+  for (int k = 0; k < m.n_param; ++k) { x[k] = Dual(th[k]); x[k].d[k] = 1.0; }
+}
+
+// ------------------------------------------------------------------ Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): ten rounds
+// of two 64x64->128 multiplications with the Weyl key schedule.
+static void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+  uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    unsigned __int128 p0 = (unsigned __int128)M0 * c0;
+    unsigned __int128 p1 = (unsigned __int128)M1 * c2;
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// The uniforms of one annealing step: block b of step s, level l, chain c (market index in the
+// upper half of the chain word) under key (seed, 0); word j of the step is uniform j,
+// u = (x >> 11) 2^-53 in [0, 1).
+static void step_uniforms(uint64_t seed, uint64_t chain_word, int level, int step, int count, double* u) {
+  uint64_t key[2] = {seed, 0};
+  for (int b = 0; b * 4 < count; ++b) {
+    uint64_t ctr[4] = {(uint64_t)b, (uint64_t)step, (uint64_t)level, chain_word};
+    uint64_t o[4];
+    philox4x64_10(ctr, key, o);
+    for (int w = 0; w < 4 && 4 * b + w < count; ++w) u[4 * b + w] = (double)(o[w] >> 11) * 0x1.0p-53;
+  }
+}
+
+// ------------------------------------------------------------------ simulated annealing
+struct SAOpts {  // mirrors oracle/__init__.py
+  int32_t n_chains, n_levels, steps;
+  double T0, cooling, step_frac, step_floor;
+  uint64_t seed;
+  uint64_t market_index;
+  const double* x0;
+  int32_t n_threads;
+};
+
+// Neighbour (reading; the paper leaves ComputeNeighbour open): every free slot moves by
+// sf (hi - lo) (2u - 1), is reflected once at the bound it crossed and then clamped.
+static void neighbour(const Market& m, const double* x, const double* u, double sf, double* y) {
+  for (int k = 0; k < m.n_param; ++k) {
+    if (!m.freem[k]) { y[k] = x[k]; continue; }
+    double v = x[k] + sf * (m.hi[k] - m.lo[k]) * (2.0 * u[k] - 1.0);
+    if (v < m.lo[k]) v = 2.0 * m.lo[k] - v;
+    if (v > m.hi[k]) v = 2.0 * m.hi[k] - v;
+    if (v < m.lo[k]) v = m.lo[k];
+    if (v > m.hi[k]) v = m.hi[k];
+    y[k] = v;
+  }
+}
+
+// The annealing loop of Section 3 in its one-GPU parallel form: at each temperature every chain
+// runs `steps` Metropolis steps from the shared start point; the start point of the next level
+// is the chain end point with the lowest f (ties to the lowest chain index).  T_{l+1} = cooling T_l.
+// Readings: T0 <= 0 means T0 = f(x0); the step fraction of level l is
+// max(step_frac sqrt(T_l / T0), step_floor); every chain evaluates f(x0) once, so the count of
+// objective evaluations is C (L N + 1); the best point ever accepted is kept apart and returned.
+static int anneal(const Market& m, const SAOpts& o, double* x_best, double* f_best,
+                  double* chain_xb, double* chain_fb, double* trace_f, double* trace_x,
+                  uint8_t* bits, int64_t* n_evals, double* T0_used) {
+  const int P = m.n_param, C = o.n_chains, L = o.n_levels, N = o.steps;
+  std::vector<double> x0(P);
+  for (int k = 0; k < P; ++k) x0[k] = o.x0 ? o.x0[k] : 0.5 * (m.lo[k] + m.hi[k]);
+  double f0 = objective(m, x0.data());
+  double T0 = o.T0 > 0.0 ? o.T0 : ((std::isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
+  std::vector<double> xs = x0, xb((size_t)C * P), fb(C, f0), xe((size_t)C * P), fe(C);
+  for (int c = 0; c < C; ++c) std::copy(x0.begin(), x0.end(), xb.begin() + (size_t)c * P);
+  double fs = f0;
+  double T = T0;
+  for (int l = 0; l < L; ++l) {
+    double sf = std::max(o.step_frac * std::sqrt(T / T0), o.step_floor);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(o.n_threads > 0 ? o.n_threads : 1)
+    for (int c = 0; c < C; ++c) {
+      std::vector<double> x(xs), y(P), u(P + 1);
+      double f = fs;
+      uint64_t cw = (uint64_t)c | (o.market_index << 32);
+      for (int s = 0; s < N; ++s) {
+        step_uniforms(o.seed, cw, l, s, P + 1, u.data());
+        neighbour(m, x.data(), u.data(), sf, y.data());
+        double fy = objective(m, y.data());
+        if (!(fy == fy)) fy = std::numeric_limits<double>::infinity();
+        bool acc = (fy < f) || (u[P] < std::exp(-(fy - f) / T));
+        if (bits) bits[((size_t)c * L + l) * N + s] = acc ? 1 : 0;
+        if (acc) {
+          x = y; f = fy;
+          if (f < fb[c]) { fb[c] = f; std::copy(x.begin(), x.end(), xb.begin() + (size_t)c * P); }
+        }
+      }
+      std::copy(x.begin(), x.end(), xe.begin() + (size_t)c * P);
+      fe[c] = f;
+    }
+    int best = 0;
+    for (int c = 1; c < C; ++c) if (fe[c] < fe[best]) best = c;
+    std::copy(xe.begin() + (size_t)best * P, xe.begin() + (size_t)(best + 1) * P, xs.begin());
+    fs = fe[best];
+    if (trace_f) trace_f[l] = fs;
+    if (trace_x) std::copy(xs.begin(), xs.end(), trace_x + (size_t)l * P);
+    T = T * o.cooling;
+  }
+  int best = 0;
+  for (int c = 1; c < C; ++c) if (fb[c] < fb[best]) best = c;
+  std::copy(xb.begin() + (size_t)best * P, xb.begin() + (size_t)(best + 1) * P, x_best);
+  *f_best = fb[best];
+  if (chain_xb) std::copy(xb.begin(), xb.end(), chain_xb);
+  if (chain_fb) std::copy(fb.begin(), fb.end(), chain_fb);
+  if (n_evals) *n_evals = (int64_t)C * ((int64_t)L * N + 1);
+  if (T0_used) *T0_used = T0;
+  return 0;
+}
+
+// ------------------------------------------------------------------ Levenberg-Marquardt
+// Classic LM with Marquardt's diagonal scaling: solve (J^T J + mu diag(J^T J)) d = -J^T r over
+// the free slots by Cholesky, project theta + d on the box, accept if f drops (mu /= 10), else
+// mu *= 10.  Stops at the target RMSE (vol points), after max_iter accepted or rejected trials,
+// or when mu exceeds 1e16.  Reading: a zero diagonal entry is floored at 1e-12 of the largest.
+static bool cholesky_solve(std::vector<double> A, std::vector<double> b, int n, std::vector<double>& x) {
+  for (int j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+    if (!(s > 0.0)) return false;
+    double d = std::sqrt(s);
+    A[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = t / d;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    double t = b[i];
+    for (int k = 0; k < i; ++k) t -= A[i * n + k] * b[k];
+    b[i] = t / A[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double t = b[i];
+    for (int k = i + 1; k < n; ++k) t -= A[k * n + i] * b[k];
+    b[i] = t / A[i * n + i];
+  }
+  x = b;
+  return true;
+}
+
+static int lm(const Market& m, const double* theta0, int max_iter, double target_rmse, double mu0,
+              double* theta_out, double* f_out, double* rmse_out, int* iters_out) {
+  const int P = m.n_param;
+  std::vector<int> fi;
+  for (int k = 0; k < P; ++k) if (m.freem[k]) fi.push_back(k);
+  const int nf = (int)fi.size();
+  std::vector<double> th(theta0, theta0 + P);
+  double f = objective(m, th.data());
+  double mu = mu0;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    if (rmse_volpt(m, th.data()) <= target_rmse) break;
+    std::vector<Dual> xd;
+    seed_duals(m, th.data(), xd);
+    std::vector<Dual> r;
+    if (!residuals(m, xd.data(), r)) break;
+    std::vector<double> A((size_t)nf * nf, 0.0), g(nf, 0.0);
+    for (const Dual& rk : r) {
+      for (int a = 0; a < nf; ++a) {
+        g[a] += rk.d[fi[a]] * rk.v;
+        for (int b = 0; b < nf; ++b) A[a * nf + b] += rk.d[fi[a]] * rk.d[fi[b]];
+      }
+    }
+    double dmax = 0.0;
+    for (int a = 0; a < nf; ++a) dmax = std::max(dmax, A[a * nf + a]);
+    bool improved = false;
+    while (mu < 1e16) {
+      std::vector<double> M = A, rhs(nf), d;
+      for (int a = 0; a < nf; ++a) {
+        M[a * nf + a] += mu * std::max(A[a * nf + a], 1e-12 * dmax);
+        rhs[a] = -g[a];
+      }
+      if (cholesky_solve(M, rhs, nf, d)) {
+        std::vector<double> tn = th;
+        for (int a = 0; a < nf; ++a) {
+          int k = fi[a];
+          tn[k] = std::min(std::max(th[k] + d[a], m.lo[k]), m.hi[k]);
+        }
+        double fn = objective(m, tn.data());
+        if (fn < f) { th = tn; f = fn; mu = std::max(mu / 10.0, 1e-12); improved = true; break; }
+      }
+      mu *= 10.0;
+    }
+    if (!improved) break;
+  }
+  std::copy(th.begin(), th.end(), theta_out);
+  *f_out = f;
+  *rmse_out = rmse_volpt(m, th.data());
+  *iters_out = it;
+  return 0;
+}
+
+}  // namespace orc
+
+// ====================================================================== C interface (ctypes)
+extern "C" {
+
+void* orc_market_new(const orc::Desc* d) { return orc::build_market(d); }
+void orc_market_free(void* m) { delete (orc::Market*)m; }
+
+void orc_gl_nodes(int n, double* x, double* w) {
+  std::vector<double> xs, ws;
+  orc::gauss_legendre(n, xs, ws);
+  std::copy(xs.begin(), xs.end(), x);
+  std::copy(ws.begin(), ws.end(), w);
+}
+
+double orc_normal_cdf(double x) { return orc::normal_cdf(x); }
+double orc_black_call(double F, double K, double T, double s, double D) { return orc::black_call(F, K, T, s, D); }
+double orc_black_put(double F, double K, double T, double s, double D) { return orc::black_put(F, K, T, s, D); }
+double orc_black_otm(double F, double K, double T, double s, double D) { return orc::black_otm(F, K, T, s, D); }
+double orc_black_vega(double F, double K, double T, double s, double D) { return orc::black_vega(F, K, T, s, D); }
+double orc_z_over_x(double z, double rho) { return orc::z_over_x(z, rho); }
+double orc_sabr_hagan2002(double F, double K, double T, double a, double b, double r, double n) {
+  return orc::sabr_hagan2002(F, K, T, a, b, r, n);
+}
+double orc_sabr_paper(double F, double K, double a, double b, double r, double n) {
+  return orc::sabr_paper(F, K, a, b, r, n);
+}
+
+// Forward levels and market prices/weights as the oracle sees them.
+void orc_market_info(const void* mp, double* F, double* cap_pm, double* cap_w, double* swp_pm,
+                     double* swp_w, double* swp_S, double* swp_A) {
+  const orc::Market& m = *(const orc::Market*)mp;
+  if (F) std::copy(m.F.begin(), m.F.end(), F);
+  if (cap_pm) std::copy(m.cpm.begin(), m.cpm.end(), cap_pm);
+  if (cap_w) std::copy(m.cw.begin(), m.cw.end(), cap_w);
+  if (swp_pm) std::copy(m.spm.begin(), m.spm.end(), swp_pm);
+  if (swp_w) std::copy(m.sw.begin(), m.sw.end(), swp_w);
+  for (size_t s = 0; s < m.sK.size(); ++s) {
+    if (swp_S) swp_S[s] = m.swapS[m.sswap[s]];
+    if (swp_A) swp_A[s] = m.swapA[m.sswap[s]];
+  }
+}
+
+void orc_rebonato_caplet(const void* mp, const double* th, double Ti, double* out4) {
+  double a, n, G, X;
+  orc::rebonato_caplet(*(const orc::Market*)mp, th, Ti, a, n, &G, &X);
+  out4[0] = G; out4[1] = X; out4[2] = a; out4[3] = n;
+}
+
+// SABR parameters of the swap underlying swaption s: out6 = (V1, V2, V3, alpha, nu, rho).
+void orc_swap_params(const void* mp, const double* th, int s, double* out6) {
+  const orc::Market& m = *(const orc::Market*)mp;
+  double a, n, r, V[3];
+  orc::swap_params(m, th, m.sswap[s], a, n, r, V);
+  out6[0] = V[0]; out6[1] = V[1]; out6[2] = V[2]; out6[3] = a; out6[4] = n; out6[5] = r;
+}
+
+void orc_model_vols(const void* mp, const double* th, double* vols) {
+  std::vector<double> v;
+  orc::all_vols(*(const orc::Market*)mp, th, v);
+  std::copy(v.begin(), v.end(), vols);
+}
+
+double orc_objective(const void* mp, const double* th) { return orc::objective(*(const orc::Market*)mp, th); }
+
+void orc_objective_batch(const void* mp, const double* X, int64_t n, double* f, int n_threads) {
+  const orc::Market& m = *(const orc::Market*)mp;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
+  for (int64_t i = 0; i < n; ++i) f[i] = orc::objective(m, X + i * m.n_param);
+}
+
+double orc_rmse_volpt(const void* mp, const double* th) { return orc::rmse_volpt(*(const orc::Market*)mp, th); }
+
+// f and df/dtheta (all slots, free or not) by forward-mode dual numbers.
+double orc_objective_grad(const void* mp, const double* th, double* grad) {
+  const orc::Market& m = *(const orc::Market*)mp;
+  std::vector<orc::Dual> x;
+  orc::seed_duals(m, th, x);
+  orc::Dual f = orc::objective_t<orc::Dual>(m, x.data());
+  for (int k = 0; k < m.n_param; ++k) grad[k] = f.d[k];
+  return f.v;
+}
+
+// Residuals r_k and their Jacobian J[k, p] (row-major, n_instr x n_param); returns 0 if feasible.
+int orc_residuals_jac(const void* mp, const double* th, double* r, double* J) {
+  const orc::Market& m = *(const orc::Market*)mp;
+  std::vector<orc::Dual> x, rr;
+  orc::seed_duals(m, th, x);
+  if (!orc::residuals(m, x.data(), rr)) return 1;
+  for (size_t k = 0; k < rr.size(); ++k) {
+    r[k] = rr[k].v;
+    if (J) for (int p = 0; p < m.n_param; ++p) J[k * m.n_param + p] = rr[k].d[p];
+  }
+  return 0;
+}
+
+void orc_philox4x64_10(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { orc::philox4x64_10(ctr, key, out); }
+
+void orc_step_uniforms(uint64_t seed, uint64_t chain_word, int level, int step, int count, double* u) {
+  orc::step_uniforms(seed, chain_word, level, step, count, u);
+}
+
+int orc_anneal(const void* mp, const orc::SAOpts* o, double* x_best, double* f_best, double* chain_xb,
+               double* chain_fb, double* trace_f, double* trace_x, uint8_t* bits, int64_t* n_evals,
+               double* T0_used) {
+  return orc::anneal(*(const orc::Market*)mp, *o, x_best, f_best, chain_xb, chain_fb, trace_f, trace_x,
+                     bits, n_evals, T0_used);
+}
+
+int orc_lm(const void* mp, const double* theta0, int max_iter, double target_rmse, double mu0,
+           double* theta_out, double* f_out, double* rmse_out, int* iters_out) {
+  return orc::lm(*(const orc::Market*)mp, theta0, max_iter, target_rmse, mu0, theta_out, f_out, rmse_out, iters_out);
+}
+
+}  // extern "C"

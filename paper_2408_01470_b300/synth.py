@@ -1,0 +1,287 @@
+"""Seeded synthetic market inputs, shared by the oracle tests, the library tests and the bench.
+
+This module holds none of the calibration method's arithmetic.  It lays out
+
+* a tenor grid and discount factors built from a prescribed simply-compounded forward curve
+  (the recipe's forward levels, P(0,T_{k+1}) = P(0,T_k) / (1 + tau_k F_k)),
+* strike grids around the recipe's forward levels (never around a model quantity),
+* parameter boxes, generating ("true") parameters drawn uniformly inside them,
+* Gaussian noise draws, in vol units, one per instrument.
+
+Model vols at the generating parameters, and the quotes built from them, are computed by whoever
+consumes a skeleton: the oracle in the tests, the library itself in the bench.
+
+The shapes follow the paper's EURIBOR workload (Section 4, Tables tab:curvaFD, tab:smilesFws and
+tab:smilesTS): semi-annual forwards, caplet smiles on a log-moneyness grid, and an expiry x tenor x
+moneyness swaption grid.  The values are synthetic.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+MODEL_SABR_SMILE = 0
+MODEL_REBONATO_LMM = 1
+
+FORMULA_HAGAN2002 = 0
+FORMULA_PAPER = 1
+
+# Parameter slots of the Rebonato SABR/LIBOR model (Section 2.3 and the parameter classes of
+# Section 3): g(u) = (a + b u) e^{-c u} + d, h(u) = (alpha_h + beta_h u) e^{-gamma_h u} + delta_h,
+# phi = phi_ii, and the correlation decays lambda1 (rho_ij), lambda2 (theta_ij), lambda3 (phi_ij).
+REBONATO_SLOTS = ("a", "b", "c", "d", "alpha_h", "beta_h", "gamma_h", "delta_h",
+                  "phi", "lambda1", "lambda2", "lambda3")
+SMILE_SLOTS = ("alpha", "rho", "nu")
+
+BASE_SEED = 240801470
+
+
+@dataclasses.dataclass
+class Skeleton:
+    """Everything a market needs except its quotes."""
+    name: str
+    model: int
+    formula: int
+    beta: float
+    T: np.ndarray          # float64 [n_fwd+1]: fixing times T_0..T_{n-1}, then the last payment time
+    P: np.ndarray          # float64 [n_fwd+1]: discount factors P(0, T_k)
+    cap_fwd: np.ndarray    # int32 [n_cap]: forward index of each caplet
+    cap_K: np.ndarray      # float64 [n_cap]
+    swp_start: np.ndarray  # int32 [n_swp]: first forward of the underlying swap
+    swp_end: np.ndarray    # int32 [n_swp]: one past the last forward
+    swp_K: np.ndarray      # float64 [n_swp]
+    lo: np.ndarray         # float64 [n_param]: search box
+    hi: np.ndarray
+    free: np.ndarray       # uint8 [n_param]: 1 = the annealer moves this slot
+    theta_true: np.ndarray  # float64 [n_param]: generating parameters
+    noise: np.ndarray      # float64 [n_cap + n_swp]: N(0, sigma_n) draws in vol units
+    panel: float = 0.5     # quadrature panel width (years)
+    quad_nodes: int = 8    # Gauss-Legendre nodes per panel
+    # annealing schedule of the workload
+    n_chains: int = 64
+    n_levels: int = 100
+    steps: int = 50
+    cooling: float = 0.9
+
+    @property
+    def n_fwd(self) -> int:
+        return len(self.T) - 1
+
+    @property
+    def n_cap(self) -> int:
+        return len(self.cap_K)
+
+    @property
+    def n_swp(self) -> int:
+        return len(self.swp_K)
+
+    @property
+    def n_instr(self) -> int:
+        return self.n_cap + self.n_swp
+
+    @property
+    def n_param(self) -> int:
+        return len(self.lo)
+
+    def box_centre(self) -> np.ndarray:
+        return 0.5 * (self.lo + self.hi)
+
+    def replace(self, **kw) -> "Skeleton":
+        return dataclasses.replace(self, **kw)
+
+
+def _curve_from_forwards(fix_times: np.ndarray, fwd: np.ndarray, p_first: float):
+    """Tenor grid and discount factors for a prescribed forward curve (the input recipe)."""
+    n = len(fwd)
+    T = np.empty(n + 1)
+    T[:n] = fix_times
+    T[n] = fix_times[-1] + (fix_times[-1] - fix_times[-2] if n > 1 else 0.5)
+    P = np.empty(n + 1)
+    P[0] = p_first
+    for k in range(n):
+        P[k + 1] = P[k] / (1.0 + (T[k + 1] - T[k]) * fwd[k])
+    return T, P
+
+
+def smile_2y(seed: int = BASE_SEED, noise_volpt: float = 0.2, formula: int = FORMULA_HAGAN2002,
+             noise_free: bool = False) -> Skeleton:
+    """Single SABR smile: F = 3%, expiry 2y, 11 strikes F-200bp..F+200bp in 40bp steps.
+
+    Generating point (alpha, beta, rho, nu) = (0.03, 0.5, -0.3, 0.4); beta is fixed.
+    Annealing schedule: 64 chains x 100 temperatures x 50 steps, cooling 0.9.
+    """
+    rng = np.random.default_rng(seed)
+    f = 0.03
+    # flat simply-compounded 3% curve, semi-annual: P(0,2) = 1.015^-4, P(0,2.5) = P(0,2)/1.015
+    T, P = _curve_from_forwards(np.array([2.0]), np.array([f]), 1.015 ** -4)
+    T[1] = 2.5
+    strikes = f + 1e-4 * np.arange(-200, 201, 40)
+    n = len(strikes)
+    noise = np.zeros(n) if noise_free else rng.normal(0.0, noise_volpt / 100.0, size=n)
+    return Skeleton(
+        name="smile_2y", model=MODEL_SABR_SMILE, formula=formula, beta=0.5, T=T, P=P,
+        cap_fwd=np.zeros(n, np.int32), cap_K=strikes.astype(np.float64),
+        swp_start=np.zeros(0, np.int32), swp_end=np.zeros(0, np.int32), swp_K=np.zeros(0),
+        lo=np.array([0.005, -0.99, 0.01]), hi=np.array([0.1, 0.99, 1.5]),
+        free=np.ones(3, np.uint8), theta_true=np.array([0.03, -0.3, 0.4]), noise=noise,
+        n_chains=64, n_levels=100, steps=50, cooling=0.9)
+
+
+# Boxes the generating Rebonato parameters are drawn from (uniform), slot by slot.
+_REB_TRUE_BOX = np.array([
+    [0.0, 0.02],   # a
+    [0.0, 0.05],   # b
+    [0.3, 2.0],    # c
+    [0.02, 0.05],  # d
+    [0.0, 0.3],    # alpha_h
+    [0.0, 0.5],    # beta_h
+    [0.3, 2.0],    # gamma_h
+    [0.1, 0.4],    # delta_h
+    [-0.6, 0.2],   # phi
+    [0.05, 0.3],   # lambda1
+    [0.05, 0.5],   # lambda2
+    [0.0, 0.3],    # lambda3
+])
+
+
+def _rebonato_search_box():
+    lo = _REB_TRUE_BOX[:, 0].copy()
+    hi = _REB_TRUE_BOX[:, 1].copy()
+    w = hi - lo
+    lo, hi = lo - 0.5 * w, hi + 0.5 * w
+    lo[2] = max(lo[2], 0.05)   # c
+    lo[6] = max(lo[6], 0.05)   # gamma_h
+    lo[8] = max(lo[8], -0.99)  # phi
+    hi[8] = min(hi[8], 0.99)
+    lo[9:12] = np.maximum(lo[9:12], 0.0)  # correlation decays stay non-negative
+    return lo, hi
+
+
+def _semiannual_curve(n_fwd: int):
+    fix = 0.5 * (np.arange(n_fwd) + 1.0)
+    fwd = 0.01 + 0.03 * np.arange(n_fwd) / max(n_fwd - 1, 1)
+    T, P = _curve_from_forwards(fix, fwd, 1.0 / (1.0 + 0.5 * 0.01))
+    return T, P, fwd
+
+
+def caplet_term_structure(seed: int = BASE_SEED + 1, noise_volpt: float = 0.02,
+                          n_fwd: int = 20, n_strikes: int = 15, noise_free: bool = False,
+                          formula: int = FORMULA_HAGAN2002) -> Skeleton:
+    """Rebonato SABR/LIBOR caplet term structure.
+
+    n_fwd semi-annual forwards (fixings 0.5, 1.0, ...), forward levels rising linearly from 1% to
+    4%, and n_strikes caplets per forward at K = F e^m, m in linspace(-0.7, 0.7).  Nine free
+    parameters (the abcd forms of g and h, and phi); the correlation decays do not reach caplets
+    and stay fixed.  Schedule: 4096 chains x 200 temperatures x 100 steps, cooling 0.95.
+    """
+    rng = np.random.default_rng(seed)
+    T, P, fwd = _semiannual_curve(n_fwd)
+    m = np.linspace(-0.7, 0.7, n_strikes)
+    cap_fwd = np.repeat(np.arange(n_fwd, dtype=np.int32), n_strikes)
+    cap_K = (fwd[:, None] * np.exp(m)[None, :]).reshape(-1)
+    lo, hi = _rebonato_search_box()
+    theta = rng.uniform(_REB_TRUE_BOX[:, 0], _REB_TRUE_BOX[:, 1])
+    free = np.array([1] * 9 + [0] * 3, np.uint8)
+    n = len(cap_K)
+    noise = np.zeros(n) if noise_free else rng.normal(0.0, noise_volpt / 100.0, size=n)
+    return Skeleton(
+        name=f"caplets_{n_fwd}x{n_strikes}", model=MODEL_REBONATO_LMM, formula=formula, beta=0.5,
+        T=T, P=P, cap_fwd=cap_fwd, cap_K=cap_K, swp_start=np.zeros(0, np.int32),
+        swp_end=np.zeros(0, np.int32), swp_K=np.zeros(0), lo=lo, hi=hi, free=free,
+        theta_true=theta, noise=noise, n_chains=4096, n_levels=200, steps=100, cooling=0.95)
+
+
+def joint_caplet_swaption(seed: int = BASE_SEED + 2, noise_volpt: float = 0.02, n_fwd: int = 40,
+                          cap_fwds: int = 20, n_strikes: int = 15, expiries=range(1, 11),
+                          tenors=range(1, 11), swp_m=(-0.6, -0.4, -0.2, 0.0, 0.2, 0.4, 0.6),
+                          noise_free: bool = False) -> Skeleton:
+    """Joint caplet + swaption market on n_fwd semi-annual forwards (1% -> 4%).
+
+    Caplets: forwards 0..cap_fwds-1 x n_strikes log-moneyness points in [-0.7, 0.7].
+    Swaptions: expiry E years x tenor L years x moneyness m; the underlying swap runs over the
+    forwards fixing at E, E+0.5, ..., E+L-0.5, and the strike is the plain average of those
+    forward levels times e^m.  All twelve parameters free.  Schedule: 16384 chains x 200 x 100.
+    """
+    rng = np.random.default_rng(seed)
+    T, P, fwd = _semiannual_curve(n_fwd)
+    m = np.linspace(-0.7, 0.7, n_strikes)
+    cap_fwd = np.repeat(np.arange(cap_fwds, dtype=np.int32), n_strikes)
+    cap_K = (fwd[:cap_fwds, None] * np.exp(m)[None, :]).reshape(-1)
+    s0, s1, sk = [], [], []
+    for e in expiries:
+        for ln in tenors:
+            a = int(round(2 * e)) - 1
+            b = a + int(round(2 * ln))
+            if b > n_fwd:
+                continue
+            level = fwd[a:b].mean()
+            for mm in swp_m:
+                s0.append(a)
+                s1.append(b)
+                sk.append(level * np.exp(mm))
+    lo, hi = _rebonato_search_box()
+    theta = rng.uniform(_REB_TRUE_BOX[:, 0], _REB_TRUE_BOX[:, 1])
+    n = len(cap_K) + len(sk)
+    noise = np.zeros(n) if noise_free else rng.normal(0.0, noise_volpt / 100.0, size=n)
+    return Skeleton(
+        name=f"joint_{n_fwd}f_{len(cap_K)}c_{len(sk)}s", model=MODEL_REBONATO_LMM,
+        formula=FORMULA_HAGAN2002, beta=0.5, T=T, P=P, cap_fwd=cap_fwd, cap_K=cap_K,
+        swp_start=np.array(s0, np.int32), swp_end=np.array(s1, np.int32),
+        swp_K=np.array(sk, np.float64), lo=lo, hi=hi, free=np.ones(12, np.uint8),
+        theta_true=theta, noise=noise, n_chains=16384, n_levels=200, steps=100, cooling=0.95)
+
+
+def batch_market(j: int, noise_volpt: float = 0.02) -> Skeleton:
+    """Member j of the uneven batch: M ~ U{10..60} forwards, U{50..1000} instruments.
+
+    The swaption fraction is U(0,1); caplets sample (forward, m) pairs and swaptions sample
+    (expiry, tenor, m) triples inside the M/2-year horizon.  Each member has its own seed.
+    """
+    rng = np.random.default_rng(BASE_SEED + 1000 + j)
+    n_fwd = int(rng.integers(10, 61))
+    n_instr = int(rng.integers(50, 1001))
+    frac_swp = float(rng.uniform(0.0, 1.0))
+    n_swp = int(round(frac_swp * n_instr))
+    n_cap = n_instr - n_swp
+    T, P, fwd = _semiannual_curve(n_fwd)
+    cf = rng.integers(0, n_fwd, size=n_cap).astype(np.int32)
+    cm = rng.uniform(-0.7, 0.7, size=n_cap)
+    order = np.lexsort((cm, cf))
+    cf, cm = cf[order], cm[order]
+    cap_K = fwd[cf] * np.exp(cm)
+    s0 = np.empty(n_swp, np.int32)
+    s1 = np.empty(n_swp, np.int32)
+    sk = np.empty(n_swp)
+    for s in range(n_swp):
+        a = int(rng.integers(1, n_fwd))       # first forward index >= 1: expiry >= 1y... 0.5y grid
+        b = int(rng.integers(a + 1, min(a + 20, n_fwd) + 1))
+        s0[s], s1[s] = a, b
+        sk[s] = fwd[a:b].mean() * np.exp(rng.uniform(-0.6, 0.6))
+    order = np.lexsort((sk, s1, s0))
+    s0, s1, sk = s0[order], s1[order], sk[order]
+    lo, hi = _rebonato_search_box()
+    theta = rng.uniform(_REB_TRUE_BOX[:, 0], _REB_TRUE_BOX[:, 1])
+    noise = rng.normal(0.0, noise_volpt / 100.0, size=n_instr)
+    return Skeleton(
+        name=f"batch_{j}", model=MODEL_REBONATO_LMM, formula=FORMULA_HAGAN2002, beta=0.5,
+        T=T, P=P, cap_fwd=cf, cap_K=cap_K, swp_start=s0, swp_end=s1, swp_K=sk, lo=lo, hi=hi,
+        free=np.ones(12, np.uint8), theta_true=theta, noise=noise,
+        n_chains=4096, n_levels=100, steps=50, cooling=0.9)
+
+
+def uniform_in_box(skel: Skeleton, n: int, seed: int) -> np.ndarray:
+    """n parameter sets drawn uniformly in the search box (fixed slots keep theta_true)."""
+    rng = np.random.default_rng(seed)
+    X = np.repeat(skel.theta_true[None, :], n, axis=0)
+    free = skel.free.astype(bool)
+    X[:, free] = rng.uniform(skel.lo[free], skel.hi[free], size=(n, int(free.sum())))
+    return X
+
+
+def market_vols(skel: Skeleton, model_vols_at_truth: np.ndarray,
+                noise: Optional[np.ndarray] = None) -> np.ndarray:
+    """Quotes in vol units: the model vols at the generating point plus the noise draws."""
+    nz = skel.noise if noise is None else noise
+    return np.asarray(model_vols_at_truth, np.float64) + nz

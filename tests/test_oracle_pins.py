@@ -1,0 +1,461 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: values printed in the paper,
+50-digit mpmath evaluations of the textbook definitions, closed forms, limits, symmetries,
+numpy's independent Philox and Gauss-Legendre routines, and brute force.
+"""
+import math
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_01470_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+mp.mp.dps = 50
+
+
+# ------------------------------------------------------------------ quadrature nodes
+def test_gauss_legendre_matches_numpy_and_is_exact_to_degree_15():
+    x, w = oracle.gl_nodes(8)
+    xr, wr = np.polynomial.legendre.leggauss(8)
+    assert np.max(np.abs(x - xr)) < 1e-15
+    assert np.max(np.abs(w - wr)) < 1e-15
+    for deg in range(16):
+        exact = 0.0 if deg % 2 else 2.0 / (deg + 1)
+        assert abs(np.sum(w * x ** deg) - exact) < 1e-14
+
+
+# ------------------------------------------------------------------ Black
+def _mp_ncdf(x):
+    return mp.ncdf(x)
+
+
+def _mp_black(F, K, T, s, D, call):
+    F, K, T, s, D = map(mp.mpf, (F, K, T, s, D))
+    v = s * mp.sqrt(T)
+    d1 = mp.log(F / K) / v + v / 2
+    d2 = d1 - v
+    if call:
+        return D * (F * mp.ncdf(d1) - K * mp.ncdf(d2))
+    return D * (K * mp.ncdf(-d2) - F * mp.ncdf(-d1))
+
+
+@pytest.mark.parametrize("x", [-12.0, -5.0, -1.3, 0.0, 0.4, 2.5, 7.0])
+def test_normal_cdf_against_mpmath(x):
+    ref = float(_mp_ncdf(x))
+    # the rounding of -x/sqrt(2) is amplified by d log Phi / dx ~ |x| in the lower tail
+    assert abs(oracle.normal_cdf(x) - ref) <= 4e-16 * (1.0 + x * x) * ref
+
+
+@pytest.mark.parametrize("F,K,T,s,D", [
+    (0.03, 0.02, 2.0, 0.25, 0.95), (0.03, 0.05, 2.0, 0.18, 0.95), (0.012, 0.0054, 0.5, 1.2, 0.99),
+    (0.04, 0.08, 10.0, 0.3, 0.6), (0.025, 0.025, 5.0, 0.4, 0.8)])
+def test_black_against_mpmath_and_parity(F, K, T, s, D):
+    c = oracle.black_call(F, K, T, s, D)
+    p = oracle.black_put(F, K, T, s, D)
+    assert abs(c - float(_mp_black(F, K, T, s, D, True))) <= 1e-14 * D * F
+    assert abs(p - float(_mp_black(F, K, T, s, D, False))) <= 1e-14 * D * F
+    # put-call parity: C - P = D (F - K)
+    assert abs((c - p) - D * (F - K)) <= 1e-15 * D * max(F, K) * 4
+    otm = oracle.black_otm(F, K, T, s, D)
+    assert otm == (p if K < F else c)
+
+
+def test_black_limits():
+    F, T, D = 0.03, 2.0, 0.9
+    # vanishing vol: out-of-the-money value -> 0, in-the-money call -> discounted intrinsic
+    assert oracle.black_otm(F, 0.02, T, 1e-6, D) < 1e-300
+    assert abs(oracle.black_call(F, 0.02, T, 1e-6, D) - D * (F - 0.02)) < 1e-16
+    # strike -> 0: both normal probabilities -> 1 and the call tends to D (F - K)
+    assert abs(oracle.black_call(F, 1e-12, T, 0.3, D) - D * (F - 1e-12)) < 1e-17
+
+
+def test_vega_is_the_derivative_of_black():
+    F, K, T, s, D = 0.03, 0.036, 3.0, 0.22, 0.9
+    h = 1e-6
+    fd = (oracle.black_otm(F, K, T, s + h, D) - oracle.black_otm(F, K, T, s - h, D)) / (2 * h)
+    assert abs(oracle.black_vega(F, K, T, s, D) - fd) < 1e-8 * abs(fd)
+
+
+# ------------------------------------------------------------------ SABR (Hagan et al. 2002)
+def _mp_hagan(F, K, T, a, b, r, n):
+    """The textbook form with the plain x(z) = log((sqrt(1-2rz+z^2)+z-r)/(1-r)), 50 digits."""
+    F, K, T, a, b, r, n = map(mp.mpf, (F, K, T, a, b, r, n))
+    omb = 1 - b
+    fk = (F * K) ** (omb / 2)
+    l = mp.log(F / K)
+    z = n / a * fk * l
+    if z == 0:
+        zx = mp.mpf(1)
+    else:
+        x = mp.log((mp.sqrt(1 - 2 * r * z + z * z) + z - r) / (1 - r))
+        zx = z / x
+    den = fk * (1 + omb ** 2 * l ** 2 / 24 + omb ** 4 * l ** 4 / 1920)
+    corr = 1 + (omb ** 2 * a * a / (24 * fk * fk) + r * b * n * a / (4 * fk) + (2 - 3 * r * r) * n * n / 24) * T
+    return a / den * zx * corr
+
+
+@pytest.mark.parametrize("K", [0.01, 0.018, 0.0299, 0.03, 0.0301, 0.034, 0.05, 0.08])
+@pytest.mark.parametrize("r", [-0.9, -0.3, 0.0, 0.5, 0.95])
+def test_hagan2002_against_50_digit_textbook_form(K, r):
+    F, T, a, b, n = 0.03, 2.0, 0.03, 0.5, 0.4
+    ref = float(_mp_hagan(F, K, T, a, b, r, n))
+    got = oracle.sabr_hagan2002(F, K, T, a, b, r, n)
+    assert abs(got - ref) <= 4e-15 * ref
+
+
+def test_hagan2002_reduces_to_alpha_at_beta1_nu0():
+    for K in (0.01, 0.03, 0.07):
+        for r in (-0.5, 0.0, 0.7):
+            assert oracle.sabr_hagan2002(0.03, K, 5.0, 0.21, 1.0, r, 0.0) == pytest.approx(0.21, abs=1e-16)
+
+
+def test_hagan2002_atm_continuity_and_series():
+    # z/x(z) is continuous through z = 0 where the oracle switches to the series
+    for r in (-0.7, 0.0, 0.6):
+        for z in (1e-6 * (1 - 1e-9), 1e-6 * (1 + 1e-9), -1e-6 * (1 + 1e-9)):
+            ref = float(mp.mpf(z) / mp.log((mp.sqrt(1 - 2 * r * mp.mpf(z) + mp.mpf(z) ** 2) + z - r) / (1 - r)))
+            assert abs(oracle.z_over_x(z, r) - ref) < 1e-15
+        assert oracle.z_over_x(0.0, r) == 1.0
+
+
+def test_hagan2002_mirror_symmetry():
+    # at T = 0, swapping F and K with rho -> -rho leaves the vol unchanged (x(-z;-rho) = -x(z;rho))
+    for (F, K) in ((0.03, 0.045), (0.02, 0.011)):
+        for r in (-0.6, 0.3):
+            a = oracle.sabr_hagan2002(F, K, 0.0, 0.04, 0.5, r, 0.5)
+            b = oracle.sabr_hagan2002(K, F, 0.0, 0.04, 0.5, -r, 0.5)
+            assert abs(a - b) <= 2e-15 * a
+
+
+# ------------------------------------------------------------------ SABR, Eq. (sigmaHagan)
+def _golden_rows():
+    with open(os.path.join(GOLDEN, "hagan_paper_volas.txt")) as fh:
+        return [l.split() for l in fh if l.strip() and not l.startswith("#")]
+
+
+@pytest.mark.parametrize("row", _golden_rows(), ids=lambda r: r[0])
+def test_paper_formula_reproduces_the_papers_calibrated_table(row):
+    phi, nu = float(row[1]), float(row[2])
+    vols = [float(v) / 100.0 for v in row[3:]]
+    atm = vols[2]
+    for m, printed in zip((-0.4, -0.2, 0.0, 0.2, 0.4), vols):
+        # with F = 1, alpha / F^{1-beta} equals the printed at-the-money model vol
+        got = oracle.sabr_paper(1.0, math.exp(m), atm, 0.5, phi, nu)
+        # printed to 0.01 vol-pt, inputs to 4 digits: 0.015 vol-pt covers both roundings
+        assert abs(got - printed) * 100.0 < 0.015, (row[0], m, got * 100, printed * 100)
+
+
+def test_paper_formula_atm_and_hagan_agree_at_first_order():
+    # at ATM both forms give alpha / F^{1-beta} (Hagan at T = 0); their first-order terms in
+    # log-moneyness agree, the second-order terms differ by the paper's extra 3(...)/12 term
+    F, a, b, r, n = 0.03, 0.03, 0.5, -0.3, 0.4
+    assert oracle.sabr_paper(F, F, a, b, r, n) == pytest.approx(a / F ** (1 - b), rel=1e-15)
+    assert oracle.sabr_hagan2002(F, F, 0.0, a, b, r, n) == pytest.approx(a / F ** (1 - b), rel=1e-15)
+    eps = 1e-4
+    sp = [oracle.sabr_paper(F, F * math.exp(s * eps), a, b, r, n) for s in (-1, 1)]
+    sh = [oracle.sabr_hagan2002(F, F * math.exp(s * eps), 0.0, a, b, r, n) for s in (-1, 1)]
+    slope_p = (sp[1] - sp[0]) / (2 * eps)
+    slope_h = (sh[1] - sh[0]) / (2 * eps)
+    assert slope_p == pytest.approx(slope_h, rel=2e-3)
+
+
+# ------------------------------------------------------------------ market curve and swaps
+def test_forwards_recover_the_recipe_curve_and_swap_rate_identity():
+    sk = synth.joint_caplet_swaption()
+    m = oracle.Market(sk)
+    info = m.info()
+    fwd = 0.01 + 0.03 * np.arange(sk.n_fwd) / (sk.n_fwd - 1)
+    assert np.max(np.abs(info["F"] - fwd)) < 1e-15
+    # swap rate S = sum w_k F_k is the par rate (P(T_a) - P(T_b)) / annuity
+    for s in range(0, sk.n_swp, 37):
+        a, b = sk.swp_start[s], sk.swp_end[s]
+        par = (sk.P[a] - sk.P[b]) / info["swp_A"][s]
+        assert abs(info["swp_S"][s] - par) < 1e-15
+
+
+# ------------------------------------------------------------------ Rebonato integrals
+def _theta(a=0.012, b=0.03, c=1.1, d=0.03, ah=0.15, bh=0.3, gh=0.9, dh=0.25, phi=-0.3,
+           l1=0.1, l2=0.2, l3=0.05):
+    return np.array([a, b, c, d, ah, bh, gh, dh, phi, l1, l2, l3])
+
+
+def _mp_g(th, u):
+    return (th[0] + th[1] * u) * mp.exp(-th[2] * u) + th[3]
+
+
+def _mp_h(th, u):
+    return (th[4] + th[5] * u) * mp.exp(-th[6] * u) + th[7]
+
+
+def _mp_caplet_integrals(th, Ti):
+    th = [mp.mpf(float(v)) for v in th]
+    Ti = mp.mpf(Ti)
+    G = mp.quad(lambda t: _mp_g(th, Ti - t) ** 2, mp.linspace(0, Ti, 5))
+
+    def H(t):
+        return mp.quad(lambda s: _mp_h(th, Ti - s) ** 2, [0, t])
+    X = mp.quad(lambda t: _mp_g(th, Ti - t) ** 2 * H(t), mp.linspace(0, Ti, 3))
+    return G, X
+
+
+@pytest.mark.parametrize("Ti", [0.5, 2.0, 6.5])
+def test_rebonato_integrals_against_high_precision_quadrature(Ti):
+    mp.mp.dps = 20
+    sk = synth.caplet_term_structure()
+    m = oracle.Market(sk)
+    th = _theta(c=2.7, gh=0.2)
+    got = m.rebonato_caplet(th, Ti)
+    G, X = _mp_caplet_integrals(th, Ti)
+    assert abs(got["G"] - float(G)) <= 1e-13 * float(G)
+    assert abs(got["X"] - float(X)) <= 1e-12 * float(X)
+    a = math.sqrt(float(G) / Ti)
+    assert got["alpha"] == pytest.approx(a, rel=1e-13)
+    assert got["nu"] == pytest.approx(math.sqrt(2 * float(X)) / (a * Ti), rel=1e-12)
+    mp.mp.dps = 50
+
+
+def test_rebonato_with_constant_vol_functions_is_plain_sabr():
+    # g = g0, h = h0 constant: G = g0^2 T, H(t) = h0^2 t, X = g0^2 h0^2 T^2 / 2,
+    # so alpha = g0 and nu = h0 exactly (up to rounding) at every maturity
+    sk = synth.caplet_term_structure()
+    m = oracle.Market(sk)
+    th = _theta(a=0.0, b=0.0, d=0.037, ah=0.0, bh=0.0, dh=0.42)
+    for Ti in (0.5, 3.0, 10.0):
+        r = m.rebonato_caplet(th, Ti)
+        assert r["alpha"] == pytest.approx(0.037, rel=1e-14)
+        assert r["nu"] == pytest.approx(0.42, rel=1e-14)
+
+
+# ------------------------------------------------------------------ swaption forms
+def _one_period_market():
+    sk = synth.joint_caplet_swaption(expiries=(1, 3, 7), tenors=(1, 2), swp_m=(0.0,))
+    # add one-period swaps on forwards 1, 5, 13 (expiries 1, 3, 7 years)
+    starts = np.array([1, 5, 13], np.int32)
+    sk = sk.replace(swp_start=np.concatenate([sk.swp_start, starts]),
+                    swp_end=np.concatenate([sk.swp_end, starts + 1]),
+                    swp_K=np.concatenate([sk.swp_K, np.full(3, 0.02)]),
+                    noise=np.zeros(sk.n_cap + sk.n_swp + 3))
+    return sk
+
+
+def test_one_period_swap_equals_the_caplet_mapping():
+    sk = _one_period_market()
+    m = oracle.Market(sk)
+    th = _theta()
+    n0 = sk.n_swp - 3
+    for k, fwd in enumerate((1, 5, 13)):
+        sp = m.swap_params(th, n0 + k)
+        cp = m.rebonato_caplet(th, sk.T[fwd])
+        assert sp["alpha"] == pytest.approx(cp["alpha"], rel=1e-14)
+        assert sp["nu"] == pytest.approx(cp["nu"], rel=1e-14)
+        assert sp["rho"] == pytest.approx(th[8], rel=1e-15)
+
+
+def test_full_correlation_and_constant_vols_give_the_common_vol():
+    # rho_ij = theta_ij = 1, phi_ij = phi, g = g0, h = h0, beta = 1: the swap rate is a plain
+    # weighted sum of forwards moving together, so alpha_S = g0, nu_S = h0, rho_S = phi
+    sk = synth.joint_caplet_swaption(expiries=(2, 5), tenors=(3, 6), swp_m=(0.0,))
+    sk = sk.replace(beta=1.0)
+    m = oracle.Market(sk)
+    th = _theta(a=0.0, b=0.0, d=0.25, ah=0.0, bh=0.0, dh=0.3, phi=-0.4, l1=0.0, l2=0.0, l3=0.0)
+    for s in range(sk.n_swp):
+        sp = m.swap_params(th, s)
+        assert sp["alpha"] == pytest.approx(0.25, rel=1e-13)
+        assert sp["nu"] == pytest.approx(0.3, rel=1e-13)
+        assert sp["rho"] == pytest.approx(-0.4, rel=1e-13)
+
+
+def test_swap_forms_against_high_precision_quadrature_two_forwards():
+    mp.mp.dps = 20
+    sk = synth.joint_caplet_swaption(expiries=(1,), tenors=(1,), swp_m=(0.0,))  # forwards 1, 2
+    m = oracle.Market(sk)
+    th = _theta()
+    got = m.swap_params(th, 0)
+    a, b = int(sk.swp_start[0]), int(sk.swp_end[0])
+    thm = [mp.mpf(float(v)) for v in th]
+    TE = mp.mpf(float(sk.T[a]))
+    info = m.info()
+    S = info["swp_S"][0]
+    A = info["swp_A"][0]
+    V = [mp.mpf(0)] * 3
+    for i in range(a, b):
+        for j in range(a, b):
+            Ti, Tj = mp.mpf(float(sk.T[i])), mp.mpf(float(sk.T[j]))
+            Gij = mp.quad(lambda t: _mp_g(thm, Ti - t) * _mp_g(thm, Tj - t), [0, TE])
+
+            def inner(t, Ti=Ti, Tj=Tj):
+                return mp.quad(lambda s: _mp_h(thm, Ti - s) * _mp_h(thm, Tj - s), [0, t])
+            Xij = mp.quad(lambda t: _mp_g(thm, Ti - t) * _mp_g(thm, Tj - t) * inner(t), [0, TE])
+            dT = abs(Ti - Tj)
+            rho_ij, theta_ij, phi_ij = mp.exp(-thm[9] * dT), mp.exp(-thm[10] * dT), thm[8] * mp.exp(-thm[11] * dT)
+            wi = (sk.T[i + 1] - sk.T[i]) * sk.P[i + 1] / A * info["F"][i] ** sk.beta / S ** sk.beta
+            wj = (sk.T[j + 1] - sk.T[j]) * sk.P[j + 1] / A * info["F"][j] ** sk.beta / S ** sk.beta
+            V[0] += wi * wj * rho_ij * Gij
+            V[1] += wi * wj * rho_ij * theta_ij * Xij
+            V[2] += wi * wj * phi_ij * Gij
+    assert got["V1"] == pytest.approx(float(V[0]), rel=1e-12)
+    assert got["V2"] == pytest.approx(float(V[1]), rel=1e-11)
+    assert got["V3"] == pytest.approx(float(V[2]), rel=1e-12)
+    mp.mp.dps = 50
+
+
+def test_swap_form_V1_non_negative():
+    sk = synth.joint_caplet_swaption(expiries=(1, 4, 9), tenors=(1, 5, 10), swp_m=(0.0,))
+    m = oracle.Market(sk)
+    X = synth.uniform_in_box(sk, 20, seed=5)
+    for th in X:
+        for s in range(sk.n_swp):
+            sp = m.swap_params(th, s)
+            assert sp["V1"] >= 0.0 and sp["V2"] >= 0.0
+
+
+# ------------------------------------------------------------------ objective
+def test_objective_zero_at_generating_point_and_vega_weighting():
+    sk = synth.caplet_term_structure(noise_free=True)
+    m, vols = oracle.quoted_market(sk)
+    assert m.objective(sk.theta_true) == 0.0
+    # for a small move the vega-weighted price objective matches the sum of squared vol errors
+    th = sk.theta_true.copy()
+    th[3] *= 1.0005
+    th[8] += 0.0005
+    dv = m.model_vols(th) - vols
+    assert m.objective(th) == pytest.approx(np.sum(dv ** 2), rel=2e-3)
+    assert m.rmse_volpt(th) == pytest.approx(100 * np.sqrt(np.mean(dv ** 2)), rel=1e-12)
+
+
+def test_objective_infeasible_point_is_inf():
+    sk = synth.smile_2y()
+    m, _ = oracle.quoted_market(sk)
+    # alpha = 0 gives z = inf and a NaN vol: the point is infeasible and f = +inf
+    assert math.isinf(m.objective(np.array([0.0, 0.0, 0.4])))
+    assert np.isfinite(m.objective(sk.theta_true))
+
+
+def test_anneal_replayed_step_by_step():
+    # a pure-Python replay of the annealing loop on a tiny case, from the oracle's objective and
+    # its Philox uniforms alone: neighbour, Metropolis, min over chain end points, cooling
+    sk = synth.smile_2y()
+    m, _ = oracle.quoted_market(sk)
+    C, L, N, cool, seed = 3, 3, 4, 0.8, 21
+    r = m.anneal(C, L, N, cool, seed=seed, want_bits=True)
+    P = sk.n_param
+    xs = sk.box_centre()
+    fs = m.objective(xs)
+    T0 = fs
+    T = T0
+    bits = np.zeros((C, L, N), np.uint8)
+    for l in range(L):
+        sf = max(0.1 * math.sqrt(T / T0), 1e-3)
+        ends = []
+        for c in range(C):
+            x, f = xs.copy(), fs
+            for s in range(N):
+                u = oracle.step_uniforms(seed, c, l, s, P + 1)
+                y = x + sf * (sk.hi - sk.lo) * (2.0 * u[:P] - 1.0)
+                y = np.where(y < sk.lo, 2 * sk.lo - y, y)
+                y = np.where(y > sk.hi, 2 * sk.hi - y, y)
+                y = np.clip(y, sk.lo, sk.hi)
+                fy = m.objective(y)
+                acc = fy < f or u[P] < math.exp(-(fy - f) / T)
+                bits[c, l, s] = acc
+                if acc:
+                    x, f = y, fy
+            ends.append((f, c, x))
+        fs, _, xs = min(ends, key=lambda e: (e[0], e[1]))
+        assert r["trace_f"][l] == fs
+        T *= cool
+    assert np.array_equal(bits, r["bits"])
+    assert r["T0"] == T0
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_against_numpy_and_known_answer():
+    key = [0x0123456789ABCDEF, 17]
+    for ctr in ([5, 7, 11, 13], [0, 0, 0, 0], [2**64 - 1, 3, 2**63, 9]):
+        bg = np.random.Philox(counter=np.array([(ctr[0] - 1) % 2**64] + ctr[1:], dtype=np.uint64),
+                              key=np.array(key, dtype=np.uint64))
+        if ctr[0] == 0:
+            # numpy pre-increments with carry; skip the borrow case
+            continue
+        ref = bg.random_raw(4)
+        assert np.array_equal(oracle.philox4x64_10(ctr, key), ref)
+    # Random123 known-answer vector: counter 0, key 0
+    kat = [0x16554d9eca36314c, 0xdb20fe9d672d0fdc, 0xd7e772cee186176b, 0x7e68b68aec7ba23b]
+    assert [int(v) for v in oracle.philox4x64_10([0, 0, 0, 0], [0, 0])] == kat
+
+
+def test_step_uniforms_layout():
+    u = oracle.step_uniforms(99, 5, 3, 7, 13)
+    raw = np.concatenate([oracle.philox4x64_10([b, 7, 3, 5], [99, 0]) for b in range(4)])
+    ref = (raw[:13] >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    assert np.array_equal(u, ref)
+    assert np.all((u >= 0) & (u < 1))
+
+
+# ------------------------------------------------------------------ annealing
+def test_anneal_evaluation_count_identity_and_determinism():
+    # the paper's identity: 16384 chains x (688 levels x 10 steps + 1) = 112,738,304
+    assert 16384 * (688 * 10 + 1) == 112738304
+    assert math.ceil(math.log(0.01 / 10) / math.log(0.99)) == 688
+    sk = synth.smile_2y()
+    m, _ = oracle.quoted_market(sk)
+    r1 = m.anneal(8, 6, 5, 0.9, seed=11, want_bits=True)
+    r2 = m.anneal(8, 6, 5, 0.9, seed=11, want_bits=True, n_threads=4)
+    assert r1["n_evals"] == 8 * (6 * 5 + 1)
+    assert np.array_equal(r1["bits"], r2["bits"])
+    assert np.array_equal(r1["x_best"], r2["x_best"])
+    assert r1["f_best"] <= r1["trace_f"].min() + 0.0
+
+
+def test_anneal_plus_lm_recover_generating_point_noise_free():
+    sk = synth.smile_2y(noise_free=True)
+    m, _ = oracle.quoted_market(sk)
+    r = m.anneal(16, 60, 30, 0.85, seed=3)
+    assert r["f_best"] < 1e-3 * m.objective(sk.box_centre())
+    p = m.lm(r["x_best"], max_iter=100)
+    assert np.max(np.abs(p["theta"] - sk.theta_true)) < 1e-8
+    assert p["rmse"] < 1e-7
+
+
+# ------------------------------------------------------------------ gradient and Jacobian
+@pytest.mark.parametrize("maker", [synth.smile_2y, synth.caplet_term_structure])
+def test_gradient_against_central_differences(maker):
+    sk = maker()
+    m, _ = oracle.quoted_market(sk)
+    th = synth.uniform_in_box(sk, 1, seed=9)[0]
+    if sk.model == synth.MODEL_REBONATO_LMM:
+        th = 0.5 * (th + sk.theta_true)
+    f, g = m.objective_grad(th)
+    assert f == m.objective(th)
+    for k in range(sk.n_param):
+        h = 1e-6 * max(abs(th[k]), 1.0)
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (m.objective(tp) - m.objective(tm)) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(g))), (k, g[k], fd)
+
+
+def test_gradient_equals_two_JT_r():
+    sk = synth.joint_caplet_swaption(expiries=(1, 3), tenors=(1, 2), swp_m=(-0.2, 0.2))
+    m, _ = oracle.quoted_market(sk)
+    th = 0.5 * (sk.theta_true + sk.box_centre())
+    f, g = m.objective_grad(th)
+    r, J = m.residuals_jac(th)
+    assert f == pytest.approx(float(r @ r), rel=1e-13)
+    assert np.allclose(g, 2 * J.T @ r, rtol=1e-11, atol=1e-14 * np.abs(g).max())
+
+
+def test_lm_recovers_rebonato_caplet_parameters_from_nearby_start():
+    sk = synth.caplet_term_structure(noise_free=True, n_fwd=8, n_strikes=5)
+    m, _ = oracle.quoted_market(sk)
+    th0 = sk.theta_true.copy()
+    th0[:9] *= 1.03
+    p = m.lm(th0, max_iter=200)
+    assert p["rmse"] < 1e-6
+    assert p["f"] < 1e-14
