@@ -1,0 +1,225 @@
+/* sabr_lmm.h -- C-ABI of the B300 (sm_103a) SABR/LIBOR calibration library.
+ *
+ * The library evaluates, on one GPU, the calibration objective of the SABR/LIBOR market models
+ * of Ferreiro, Garcia, Lopez-Salas and Vazquez (arXiv 2408.01470, Sections 2-3), and runs the
+ * parallel simulated-annealing search of Section 3 (thousands of Metropolis chains per
+ * temperature, a minimum over the chains' end points, the start point broadcast to the next
+ * level), followed by an optional Levenberg-Marquardt polish.
+ *
+ * Conventions for every call:
+ *   - Plain pointers only.  "host" pointers are read during the call and may be freed after it;
+ *     "device" pointers must be CUDA global memory of the current device, owned by the caller.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls
+ *     that take a stream only enqueue work; the caller synchronises before reading outputs.
+ *     sabr_lmm_anneal synchronises its own stream before returning.
+ *   - Every call returns a sabr_lmm_status.  On any status other than SABR_LMM_OK a message is
+ *     available from sabr_lmm_last_error() (thread-local, valid until the next call on the same
+ *     thread) and no output has been written, except for SABR_LMM_ECUDA and SABR_LMM_ETIMEOUT
+ *     raised after launch, where device outputs are unspecified.
+ *   - A parameter point whose model vol for some instrument is not a finite positive number is
+ *     infeasible: its objective is +inf.  That is a value, not an error.
+ */
+#ifndef SABR_LMM_H
+#define SABR_LMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SABR_LMM_OK = 0,
+  SABR_LMM_EINVAL = 1,    /* invalid argument or market description */
+  SABR_LMM_ENOMEM = 2,    /* device or host allocation failed */
+  SABR_LMM_ECUDA = 3,     /* a CUDA call or kernel failed */
+  SABR_LMM_ETIMEOUT = 4,  /* a bounded device-side wait gave up (the context stays usable) */
+  SABR_LMM_ENOTSUP = 5    /* valid but not supported by this build (e.g. quad_nodes != 8) */
+} sabr_lmm_status;
+
+/* Arithmetic of the hot path.
+ *   FP64      : every price, integral and sum in FP64 (the plain form).
+ *   FP32      : integrals, SABR vols and Black prices in FP32; objective sums, the Metropolis
+ *               comparison and the chain state in FP64.
+ *   FP32_TF32X3 / FP32_BF16X3 : FP32, with the swaption quadratic forms contracted on the
+ *               tensor cores with split (3-term) products accumulated in FP32.              */
+typedef enum {
+  SABR_LMM_FP64 = 0,
+  SABR_LMM_FP32 = 1,
+  SABR_LMM_FP32_TF32X3 = 2,
+  SABR_LMM_FP32_BF16X3 = 3
+} sabr_lmm_prec;
+
+/* Models (Section 2).
+ *   SMILE    : one SABR smile; parameters [alpha, rho, nu] shared by every caplet; beta fixed.
+ *   REBONATO : the Rebonato SABR/LIBOR model (Section 2.3), 12 parameter slots
+ *              [a, b, c, d, alpha_h, beta_h, gamma_h, delta_h, phi, lambda1, lambda2, lambda3]:
+ *              g(u) = (a + b u) e^{-c u} + d and h(u) = (alpha_h + beta_h u) e^{-gamma_h u} + delta_h
+ *              at time-to-fixing u, kappa = 1, phi_ii = phi, and the correlations of
+ *              Eqs. (rhoij), (thetaij), (phiij) with eta1 = eta2 = 0.                       */
+typedef enum { SABR_LMM_MODEL_SMILE = 0, SABR_LMM_MODEL_REBONATO = 1 } sabr_lmm_model;
+
+/* SABR implied-vol formula.
+ *   HAGAN2002 : Hagan, Kumar, Lesniewski, Woodward (2002) lognormal expansion with z/x(z) and
+ *               the first-order expiry correction ("the Hagan second order approximation
+ *               formula", Section 2.1).
+ *   PAPER     : Eq. (sigmaHagan) exactly as printed (no expiry dependence).                */
+typedef enum { SABR_LMM_HAGAN2002 = 0, SABR_LMM_PAPER = 1 } sabr_lmm_formula;
+
+/* A market: a tenor structure, caplet and swaption quotes, and the parameter box.
+ * All arrays are host memory, read during sabr_lmm_load_market only.
+ *   T[n_fwd+1]   : T[k] is the fixing time of forward k (years, strictly increasing, > 0);
+ *                  T[n_fwd] is the payment time of the last forward.  Accrual tau_k = T[k+1]-T[k].
+ *   P[n_fwd+1]   : discount factors P(0, T[k]) > 0.  Forward k is (P[k]/P[k+1] - 1) / tau_k.
+ *   cap_fwd[n_cap], cap_K[n_cap], cap_vol[n_cap] : caplet on forward cap_fwd[k] (expiry T[k],
+ *                  paid at T[k+1]) struck at cap_K[k] > 0, quoted at Black vol cap_vol[k] > 0.
+ *   cap_w        : NULL -> weight 1/vega^2 at the quoted vol; else caller weights >= 0.
+ *   swp_start/swp_end/swp_K/swp_vol[n_swp] : swaption expiring at T[swp_start] on the swap
+ *                  over forwards [swp_start, swp_end) (annuity sum tau_k P[k+1], frozen weights).
+ *   swp_w        : as cap_w.
+ *   lo/hi[n_param], free_mask[n_param] : search box and the slots the annealer moves (1) or
+ *                  keeps (0).  n_param must be 3 (SMILE) or 12 (REBONATO).
+ *   panel        : quadrature panel width (years); for REBONATO every T[k] must be a whole
+ *                  multiple of it.  quad_nodes: Gauss-Legendre nodes per panel (8 only).
+ * Quotes are vols: the library prices them with Black's formula (the out-of-the-money option:
+ * a put below the forward, a call at or above it) to get the market prices.                  */
+typedef struct {
+  int32_t model;
+  int32_t formula;
+  double beta;
+  int32_t n_fwd;
+  const double* T;
+  const double* P;
+  int32_t n_cap;
+  const int32_t* cap_fwd;
+  const double* cap_K;
+  const double* cap_vol;
+  const double* cap_w;
+  int32_t n_swp;
+  const int32_t* swp_start;
+  const int32_t* swp_end;
+  const double* swp_K;
+  const double* swp_vol;
+  const double* swp_w;
+  int32_t n_param;
+  const double* lo;
+  const double* hi;
+  const uint8_t* free_mask;
+  double panel;
+  int32_t quad_nodes;
+} sabr_lmm_market_desc;
+
+typedef struct sabr_lmm_market sabr_lmm_market; /* opaque, library-owned device arena */
+
+/* Validate n_markets descriptions (d[0..n_markets-1]), copy them to the device once and
+ * precompute every market-only constant there (forwards, discounts, annuities, swap rates,
+ * frozen weights, market prices, vega weights, log-moneyness).  Paper: the problem statement
+ * of Section 3 (cost functions f_c and f_s).  Allocates device memory (freed by
+ * sabr_lmm_free_market).  Errors: EINVAL (message names the field), ENOMEM, ENOTSUP, ECUDA.  */
+sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* d, int32_t n_markets,
+                                     void* stream, sabr_lmm_market** out);
+void sabr_lmm_free_market(sabr_lmm_market* m);
+
+/* f[i] = sum_k w_k (P_k(X[i]) - P_k^mkt)^2 over every caplet and swaption of market
+ * `market_idx`, for n parameter sets X (device, row-major n x n_param, FP64).  f: device [n],
+ * FP64.  Paper: f_c and f_s of Section 3, the SABR vols of Eq. (sigmaHagan) or Hagan (2002)
+ * with the model mappings of Eq. (haganForRebonato).  Errors: EINVAL (n < 0, bad index or
+ * precision, NULL pointers with n > 0), ECUDA.                                                */
+sabr_lmm_status sabr_lmm_objective(const sabr_lmm_market* m, int32_t market_idx, const double* X,
+                                   int64_t n, int32_t prec, double* f, void* stream);
+
+/* Model Black vols of every instrument (caplets first, then swaptions) for n parameter sets:
+ * vols device [n x (n_cap + n_swp)], FP64.  Infeasible entries are NaN.  Same errors.        */
+sabr_lmm_status sabr_lmm_model_vols(const sabr_lmm_market* m, int32_t market_idx, const double* X,
+                                    int64_t n, int32_t prec, double* vols, void* stream);
+
+/* f[i] and its gradient G[i, :] = df/dtheta (device [n x n_param], FP64, every slot, free or
+ * not) by a hand-written reverse-mode (adjoint) sweep through pricing, SABR, the model mapping
+ * and the quadrature.  Arithmetic per `prec` (FP64, or FP32 accumulating the parameter
+ * adjoints in FP64).  Paper: derivative of the cost functions of Section 3.  Same errors.    */
+sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int32_t market_idx,
+                                        const double* X, int64_t n, int32_t prec, double* f,
+                                        double* G, void* stream);
+
+/* Simulated annealing (Section 3, one-GPU parallel form).
+ * Level l runs at T_l = T0 cooling^l (T_{l+1} = cooling T_l).  Every chain starts the level at
+ * the shared start point and runs steps_per_level Metropolis steps: each free slot moves by
+ * s_l (hi - lo)(2u - 1), reflected once at the bound it crosses and clamped, with
+ * s_l = max(step_frac sqrt(T_l / T0), step_floor); the move is accepted if the objective drops
+ * or u < exp(-dE / T_l).  The next start point is the end point with the lowest objective
+ * (ties to the lowest chain index).  Uniforms: Philox4x64-10 keyed (seed, 0), counter
+ * (block, step, level, chain | market << 32), u = (word >> 11) 2^-53, words 0..n_param-1 move
+ * slots 0..n_param-1 and word n_param decides acceptance.  Every chain evaluates f(x0) once,
+ * so C (L N + 1) objective evaluations are made.
+ *   T0 <= 0  -> T0 = f(x0) (1 if that is not a finite positive number).
+ *   x0 NULL  -> box centre.  x0 is host memory [n_markets x n_param].
+ *   lm_top_k > 0 -> Levenberg-Marquardt polish of the lm_top_k lowest best-ever chain points
+ *   (lm_max_iter trials each, stop at target_rmse_volpt), the best polished point returned. */
+typedef struct {
+  int32_t n_chains;
+  int32_t n_levels;
+  int32_t steps_per_level;
+  double T0;
+  double cooling;
+  double step_frac;
+  double step_floor;
+  uint64_t seed;
+  const double* x0;
+  int32_t prec;
+  int32_t lm_top_k;
+  int32_t lm_max_iter;
+  double target_rmse_volpt;
+  int32_t warps_per_block; /* 0 -> autotuned */
+  int32_t use_graph;       /* 1 -> the level loop is captured once and replayed as a CUDA graph */
+  int32_t record_accepts;  /* 1 -> fill sabr_lmm_result.accept_bits (market 0; small runs)     */
+} sabr_lmm_anneal_opts;
+
+/* Results, per market, in caller-allocated host arrays (any may be NULL).
+ *   x_best [n_markets x n_param], f_best, rmse_volpt [n_markets]: best point found (after the
+ *   polish when enabled), its objective and its vol RMSE in vol points.
+ *   trace_f [n_markets x n_levels]: the start objective of each next level (the per-level min).
+ *   accept_bits [n_chains x n_levels x steps] (market 0 only; for tests, small runs).
+ *   n_evals: objective evaluations made by the annealer (C (L N + 1) per market).
+ *   seconds: device time of the annealing loop; lm_seconds: device time of the polish.      */
+typedef struct {
+  double* x_best;
+  double* f_best;
+  double* rmse_volpt;
+  double* trace_f;
+  uint8_t* accept_bits;
+  int64_t n_evals;
+  double seconds;
+  double lm_seconds;
+  double T0_used;
+} sabr_lmm_result;
+
+sabr_lmm_status sabr_lmm_anneal(const sabr_lmm_market* m, const sabr_lmm_anneal_opts* opts,
+                                sabr_lmm_result* out);
+
+/* The same search split for callers that time or overlap it: prepare allocates the chain state
+ * and plans the launches; launch enqueues the whole search on `stream` (no host sync); fetch
+ * synchronises that stream and copies results; free releases the plan.                      */
+typedef struct sabr_lmm_anneal_plan sabr_lmm_anneal_plan;
+sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* m, const sabr_lmm_anneal_opts* opts,
+                                        void* stream, sabr_lmm_anneal_plan** plan);
+sabr_lmm_status sabr_lmm_anneal_launch(sabr_lmm_anneal_plan* plan, void* stream);
+sabr_lmm_status sabr_lmm_anneal_fetch(sabr_lmm_anneal_plan* plan, sabr_lmm_result* out);
+void sabr_lmm_anneal_plan_free(sabr_lmm_anneal_plan* plan);
+
+/* Levenberg-Marquardt polish of n points X (device [n x n_param], FP64, updated in place):
+ * J from a tangent sweep, (J^T J + mu diag J^T J) d = -J^T r by Cholesky over the free slots,
+ * projection on the box, mu /10 on success, x10 on failure.  f, rmse: device [n] or NULL.    */
+sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t market_idx, double* X,
+                                   int64_t n, int32_t max_iter, double target_rmse_volpt,
+                                   double* f, double* rmse, void* stream);
+
+/* Introspection: the Gauss-Legendre rule the kernels use (nodes on [-1,1], weights), q = 8. */
+sabr_lmm_status sabr_lmm_quadrature_rule(int32_t q, double* x, double* w);
+
+const char* sabr_lmm_last_error(void);
+const char* sabr_lmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SABR_LMM_H */

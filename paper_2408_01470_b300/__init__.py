@@ -1,0 +1,321 @@
+"""B300-native SABR/LIBOR market-model calibration (arXiv 2408.01470), ctypes binding.
+
+This module only marshals arguments into the C-ABI of ``libsabr_lmm.so`` (declared in
+``include/sabr_lmm.h``); every number of the hot path is computed by the library's CUDA kernels.
+PyTorch provides device memory and streams.  There is no CPU fallback: ``load()`` raises if the
+library is missing or no CUDA device is visible.
+
+Entry points (same names as the C-ABI, without the ``sabr_lmm_`` prefix):
+    Market(...)                 sabr_lmm_load_market / sabr_lmm_free_market
+    Market.objective(X, prec)   sabr_lmm_objective
+    Market.model_vols(X, prec)  sabr_lmm_model_vols
+    Market.objective_grad(...)  sabr_lmm_objective_grad
+    Market.anneal(...)          sabr_lmm_anneal
+    Market.anneal_prepare(...)  sabr_lmm_anneal_prepare / _launch / _fetch / _plan_free
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsabr_lmm.so")
+
+FP64, FP32, FP32_TF32X3, FP32_BF16X3 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": FP32_TF32X3, "bf16x3": FP32_BF16X3}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP"}
+
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_U8 = C.POINTER(C.c_uint8)
+
+
+class SabrLmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"sabr_lmm {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MarketDesc(C.Structure):
+    _fields_ = [
+        ("model", C.c_int32), ("formula", C.c_int32), ("beta", C.c_double),
+        ("n_fwd", C.c_int32), ("T", _D), ("P", _D),
+        ("n_cap", C.c_int32), ("cap_fwd", _I32), ("cap_K", _D), ("cap_vol", _D), ("cap_w", _D),
+        ("n_swp", C.c_int32), ("swp_start", _I32), ("swp_end", _I32), ("swp_K", _D),
+        ("swp_vol", _D), ("swp_w", _D),
+        ("n_param", C.c_int32), ("lo", _D), ("hi", _D), ("free_mask", _U8),
+        ("panel", C.c_double), ("quad_nodes", C.c_int32),
+    ]
+
+
+class AnnealOpts(C.Structure):
+    _fields_ = [
+        ("n_chains", C.c_int32), ("n_levels", C.c_int32), ("steps_per_level", C.c_int32),
+        ("T0", C.c_double), ("cooling", C.c_double), ("step_frac", C.c_double),
+        ("step_floor", C.c_double), ("seed", C.c_uint64), ("x0", _D), ("prec", C.c_int32),
+        ("lm_top_k", C.c_int32), ("lm_max_iter", C.c_int32), ("target_rmse_volpt", C.c_double),
+        ("warps_per_block", C.c_int32), ("use_graph", C.c_int32), ("record_accepts", C.c_int32),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("x_best", _D), ("f_best", _D), ("rmse_volpt", _D), ("trace_f", _D),
+        ("accept_bits", _U8), ("n_evals", C.c_int64), ("seconds", C.c_double),
+        ("lm_seconds", C.c_double), ("T0_used", C.c_double),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective", "sabr_lmm_model_vols",
+           "sabr_lmm_objective_grad", "sabr_lmm_anneal", "sabr_lmm_anneal_prepare", "sabr_lmm_anneal_launch",
+           "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_lm_polish",
+           "sabr_lmm_quadrature_rule", "sabr_lmm_last_error", "sabr_lmm_version")
+
+
+def open_library(path: str = LIB_PATH):
+    """dlopen the library and declare its signatures (no CUDA call is made)."""
+    if not os.path.exists(path):
+        raise ImportError(f"the CUDA library {path} is missing; build it with "
+                          "`python -m paper_2408_01470_b300.build`")
+    lib = C.CDLL(path)
+    lib.sabr_lmm_load_market.argtypes = [C.POINTER(MarketDesc), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.sabr_lmm_free_market.argtypes = [C.c_void_p]
+    lib.sabr_lmm_free_market.restype = None
+    for name in ("sabr_lmm_objective", "sabr_lmm_model_vols"):
+        getattr(lib, name).argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_objective_grad.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_anneal.argtypes = [C.c_void_p, C.POINTER(AnnealOpts), C.POINTER(Result)]
+    lib.sabr_lmm_anneal_prepare.argtypes = [C.c_void_p, C.POINTER(AnnealOpts), C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.sabr_lmm_anneal_launch.argtypes = [C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_anneal_fetch.argtypes = [C.c_void_p, C.POINTER(Result)]
+    lib.sabr_lmm_anneal_plan_free.argtypes = [C.c_void_p]
+    lib.sabr_lmm_anneal_plan_free.restype = None
+    lib.sabr_lmm_lm_polish.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_double,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_quadrature_rule.argtypes = [C.c_int32, _D, _D]
+    lib.sabr_lmm_last_error.restype = C.c_char_p
+    lib.sabr_lmm_version.restype = C.c_char_p
+    return lib
+
+
+def load():
+    """The library, loaded once; raises if it is missing or no CUDA device is visible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("paper_2408_01470_b300 needs a CUDA device (B300, sm_103a); none is visible")
+            torch.cuda.init()
+            _lib = open_library()
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise SabrLmmError(status, _lib.sabr_lmm_last_error().decode())
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def describe(skel, vols, weights=None):
+    """A MarketDesc for a synth.Skeleton and quotes; returns (desc, keep-alive arrays)."""
+    n_cap = skel.n_cap
+    vols = _f64(vols)
+    keep = dict(T=_f64(skel.T), P=_f64(skel.P), cap_fwd=np.ascontiguousarray(skel.cap_fwd, np.int32),
+                cap_K=_f64(skel.cap_K), cap_vol=_f64(vols[:n_cap]),
+                swp_start=np.ascontiguousarray(skel.swp_start, np.int32),
+                swp_end=np.ascontiguousarray(skel.swp_end, np.int32), swp_K=_f64(skel.swp_K),
+                swp_vol=_f64(vols[n_cap:]), lo=_f64(skel.lo), hi=_f64(skel.hi),
+                free=np.ascontiguousarray(skel.free, np.uint8))
+    d = MarketDesc()
+    d.model, d.formula, d.beta = skel.model, skel.formula, skel.beta
+    d.n_fwd = skel.n_fwd
+    d.T, d.P = keep["T"].ctypes.data_as(_D), keep["P"].ctypes.data_as(_D)
+    d.n_cap = n_cap
+    d.cap_fwd = keep["cap_fwd"].ctypes.data_as(_I32)
+    d.cap_K, d.cap_vol = keep["cap_K"].ctypes.data_as(_D), keep["cap_vol"].ctypes.data_as(_D)
+    d.n_swp = skel.n_swp
+    d.swp_start = keep["swp_start"].ctypes.data_as(_I32)
+    d.swp_end = keep["swp_end"].ctypes.data_as(_I32)
+    d.swp_K, d.swp_vol = keep["swp_K"].ctypes.data_as(_D), keep["swp_vol"].ctypes.data_as(_D)
+    if weights is not None:
+        w = _f64(weights)
+        keep["cap_w"], keep["swp_w"] = _f64(w[:n_cap]), _f64(w[n_cap:])
+        d.cap_w = keep["cap_w"].ctypes.data_as(_D)
+        d.swp_w = keep["swp_w"].ctypes.data_as(_D)
+    d.n_param = skel.n_param
+    d.lo, d.hi = keep["lo"].ctypes.data_as(_D), keep["hi"].ctypes.data_as(_D)
+    d.free_mask = keep["free"].ctypes.data_as(_U8)
+    d.panel, d.quad_nodes = skel.panel, skel.quad_nodes
+    return d, keep
+
+
+class Market:
+    """One or more markets loaded on the device (sabr_lmm_load_market)."""
+
+    def __init__(self, skels, vols, weights=None, stream=None):
+        import torch
+        lib = load()
+        if not isinstance(skels, (list, tuple)):
+            skels, vols = [skels], [vols]
+            weights = [weights]
+        elif weights is None:
+            weights = [None] * len(skels)
+        self.skels = list(skels)
+        descs = (MarketDesc * len(skels))()
+        self._keep = []
+        for j, (s, v, w) in enumerate(zip(skels, vols, weights)):
+            d, keep = describe(s, v, w)
+            descs[j] = d
+            self._keep.append(keep)
+        h = C.c_void_p()
+        _check(lib.sabr_lmm_load_market(descs, len(skels), _stream_ptr(stream), C.byref(h)))
+        self.h = h
+        self._lib = lib
+        self._torch = torch
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            self._lib.sabr_lmm_free_market(self.h)
+            self.h = C.c_void_p()
+
+    def _X(self, X, j):
+        t = self._torch
+        if not isinstance(X, t.Tensor):
+            X = t.as_tensor(np.atleast_2d(X), dtype=t.float64)
+        X = X.to(device="cuda", dtype=t.float64).contiguous()
+        if X.dim() == 1:
+            X = X[None, :]
+        assert X.shape[1] == self.skels[j].n_param
+        return X
+
+    def objective(self, X, prec="fp64", market=0, stream=None):
+        X = self._X(X, market)
+        f = self._torch.empty(X.shape[0], dtype=self._torch.float64, device="cuda")
+        _check(self._lib.sabr_lmm_objective(self.h, market, C.c_void_p(X.data_ptr()), X.shape[0], _prec(prec),
+                                            C.c_void_p(f.data_ptr()), _stream_ptr(stream)))
+        return f
+
+    def model_vols(self, X, prec="fp64", market=0, stream=None):
+        X = self._X(X, market)
+        n_instr = self.skels[market].n_instr
+        v = self._torch.empty((X.shape[0], n_instr), dtype=self._torch.float64, device="cuda")
+        _check(self._lib.sabr_lmm_model_vols(self.h, market, C.c_void_p(X.data_ptr()), X.shape[0], _prec(prec),
+                                             C.c_void_p(v.data_ptr()), _stream_ptr(stream)))
+        return v
+
+    def objective_grad(self, X, prec="fp64", market=0, stream=None):
+        X = self._X(X, market)
+        n = X.shape[0]
+        f = self._torch.empty(n, dtype=self._torch.float64, device="cuda")
+        G = self._torch.empty_like(X)
+        _check(self._lib.sabr_lmm_objective_grad(self.h, market, C.c_void_p(X.data_ptr()), n, _prec(prec),
+                                                 C.c_void_p(f.data_ptr()), C.c_void_p(G.data_ptr()),
+                                                 _stream_ptr(stream)))
+        return f, G
+
+    def _opts(self, n_chains, n_levels, steps, cooling, seed, prec, T0, step_frac, step_floor, x0,
+              lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, record_accepts):
+        o = AnnealOpts()
+        o.n_chains, o.n_levels, o.steps_per_level = n_chains, n_levels, steps
+        o.T0, o.cooling, o.step_frac, o.step_floor = T0, cooling, step_frac, step_floor
+        o.seed = seed
+        keep = None
+        if x0 is not None:
+            keep = _f64(x0).reshape(-1)
+            o.x0 = keep.ctypes.data_as(_D)
+        o.prec = _prec(prec)
+        o.lm_top_k, o.lm_max_iter, o.target_rmse_volpt = lm_top_k, lm_max_iter, target_rmse
+        o.warps_per_block, o.use_graph, o.record_accepts = warps_per_block, int(use_graph), int(record_accepts)
+        return o, keep
+
+    def _result(self, n_chains, n_levels, steps, record_accepts):
+        nm = len(self.skels)
+        P = self.skels[0].n_param
+        arrs = dict(x_best=np.zeros((nm, P)), f_best=np.zeros(nm), rmse=np.zeros(nm),
+                    trace_f=np.zeros((nm, n_levels)))
+        bits = np.zeros((n_chains, n_levels, steps), np.uint8) if record_accepts else None
+        r = Result()
+        r.x_best = arrs["x_best"].ctypes.data_as(_D)
+        r.f_best = arrs["f_best"].ctypes.data_as(_D)
+        r.rmse_volpt = arrs["rmse"].ctypes.data_as(_D)
+        r.trace_f = arrs["trace_f"].ctypes.data_as(_D)
+        if bits is not None:
+            r.accept_bits = bits.ctypes.data_as(_U8)
+        return r, arrs, bits
+
+    @staticmethod
+    def _pack(r, arrs, bits):
+        return dict(x_best=arrs["x_best"], f_best=arrs["f_best"], rmse_volpt=arrs["rmse"],
+                    trace_f=arrs["trace_f"], bits=bits, n_evals=r.n_evals, seconds=r.seconds,
+                    lm_seconds=r.lm_seconds, T0=r.T0_used)
+
+    def anneal(self, n_chains, n_levels, steps, cooling, seed, prec="fp64", T0=0.0, step_frac=0.1,
+               step_floor=1e-3, x0=None, lm_top_k=0, lm_max_iter=50, target_rmse=0.0,
+               warps_per_block=0, use_graph=False, record_accepts=False):
+        o, keep = self._opts(n_chains, n_levels, steps, cooling, seed, prec, T0, step_frac, step_floor, x0,
+                             lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, record_accepts)
+        r, arrs, bits = self._result(n_chains, n_levels, steps, record_accepts)
+        _check(self._lib.sabr_lmm_anneal(self.h, C.byref(o), C.byref(r)))
+        del keep
+        return self._pack(r, arrs, bits)
+
+    def anneal_prepare(self, n_chains, n_levels, steps, cooling, seed, prec="fp64", T0=0.0, step_frac=0.1,
+                       step_floor=1e-3, x0=None, lm_top_k=0, lm_max_iter=50, target_rmse=0.0,
+                       warps_per_block=0, use_graph=True, stream=None):
+        o, keep = self._opts(n_chains, n_levels, steps, cooling, seed, prec, T0, step_frac, step_floor, x0,
+                             lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, False)
+        h = C.c_void_p()
+        _check(self._lib.sabr_lmm_anneal_prepare(self.h, C.byref(o), _stream_ptr(stream), C.byref(h)))
+        return AnnealPlan(self, h, (n_chains, n_levels, steps))
+
+
+class AnnealPlan:
+    """sabr_lmm_anneal_prepare / launch / fetch / plan_free."""
+
+    def __init__(self, market, h, dims):
+        self.market, self.h, self.dims = market, h, dims
+        self._lib = market._lib
+
+    def launch(self, stream=None):
+        _check(self._lib.sabr_lmm_anneal_launch(self.h, _stream_ptr(stream)))
+
+    def fetch(self):
+        C_, L, N = self.dims
+        r, arrs, bits = self.market._result(C_, L, N, False)
+        _check(self._lib.sabr_lmm_anneal_fetch(self.h, C.byref(r)))
+        return Market._pack(r, arrs, bits)
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            self._lib.sabr_lmm_anneal_plan_free(self.h)
+            self.h = C.c_void_p()
+
+
+def quadrature_rule(q: int = 8):
+    lib = _lib or open_library()
+    x, w = np.zeros(q), np.zeros(q)
+    st = lib.sabr_lmm_quadrature_rule(q, x.ctypes.data_as(_D), w.ctypes.data_as(_D))
+    if st != 0:
+        raise SabrLmmError(st, lib.sabr_lmm_last_error().decode())
+    return x, w

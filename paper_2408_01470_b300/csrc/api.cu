@@ -1,0 +1,612 @@
+// C-ABI of the library (include/sabr_lmm.h): validation, the device arena of a market, kernel
+// dispatch by (precision, model, formula), and the annealing plan (optionally replayed as a CUDA
+// graph).  Host code only schedules: every number of the hot path is computed in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sabr_lmm.h"
+#include "kernels.cuh"
+
+using namespace sabr;
+
+namespace {
+
+thread_local std::string g_err;
+
+sabr_lmm_status fail(sabr_lmm_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Gauss-Legendre, 8 nodes on [-1, 1] (tabulated values of the Legendre roots and weights).
+const double kGLx[8] = {-0.96028985649753623168, -0.79666647741362673959, -0.52553240991632898582,
+                        -0.18343464249564980494, 0.18343464249564980494, 0.52553240991632898582,
+                        0.79666647741362673959, 0.96028985649753623168};
+const double kGLw[8] = {0.10122853629037625915, 0.22238103445337447054, 0.31370664587788728734,
+                        0.36268378337836198297, 0.36268378337836198297, 0.31370664587788728734,
+                        0.22238103445337447054, 0.10122853629037625915};
+
+// Layout builder for one device arena: 256-byte aligned regions.
+struct Arena {
+  size_t size = 0;
+  size_t take(size_t bytes) {
+    size_t off = (size + 255) & ~size_t(255);
+    size = off + std::max<size_t>(bytes, 16);
+    return off;
+  }
+};
+
+struct HostMarket {
+  int model, formula, n_param, n_fwd, n_cap, n_swp;
+  double beta;
+  std::vector<double> lo, hi, cap_vol, swp_vol;
+  std::vector<uint8_t> freem;
+};
+
+}  // namespace
+
+struct sabr_lmm_market {
+  void* arena = nullptr;
+  std::vector<DevMarket> dm;
+  std::vector<HostMarket> hm;
+  int device = 0;
+};
+
+struct sabr_lmm_anneal_plan {
+  const sabr_lmm_market* mk = nullptr;
+  sabr_lmm_anneal_opts opts{};
+  int W = 4;
+  int grid = 0;
+  void* state = nullptr;          // device chain state for every market
+  std::vector<SAState> st;        // per market
+  std::vector<SAParams> sp;
+  std::vector<double> x0;         // host copy
+  double* x0_dev = nullptr;
+  double* vols_dev = nullptr;     // scratch for the RMSE of the best point
+  double* rmse_dev = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+std::string validate(const sabr_lmm_market_desc& d, int idx) {
+  char buf[256];
+  auto bad = [&](const char* what) {
+    snprintf(buf, sizeof buf, "market %d: %s", idx, what);
+    return std::string(buf);
+  };
+  if (d.model != SABR_LMM_MODEL_SMILE && d.model != SABR_LMM_MODEL_REBONATO) return bad("model must be 0 or 1");
+  if (d.formula != SABR_LMM_HAGAN2002 && d.formula != SABR_LMM_PAPER) return bad("formula must be 0 or 1");
+  if (!(d.beta >= 0.0 && d.beta <= 1.0)) return bad("beta must be in [0, 1]");
+  if (d.n_fwd < 1 || d.n_fwd > 120) return bad("n_fwd must be in [1, 120]");
+  if (!d.T || !d.P) return bad("T and P are required");
+  for (int k = 0; k <= d.n_fwd; ++k) {
+    if (!(d.T[k] > 0.0) || !std::isfinite(d.T[k])) return bad("T must be finite and > 0");
+    if (k > 0 && !(d.T[k] > d.T[k - 1])) return bad("T must be strictly increasing");
+    if (!(d.P[k] > 0.0) || !std::isfinite(d.P[k])) return bad("P must be finite and > 0");
+  }
+  if (d.n_cap < 0 || d.n_swp < 0 || d.n_cap + d.n_swp < 1) return bad("need at least one instrument");
+  if (d.n_cap > 0 && (!d.cap_fwd || !d.cap_K || !d.cap_vol)) return bad("caplet arrays are required");
+  if (d.n_swp > 0 && (!d.swp_start || !d.swp_end || !d.swp_K || !d.swp_vol)) return bad("swaption arrays are required");
+  for (int k = 0; k < d.n_cap; ++k) {
+    if (d.cap_fwd[k] < 0 || d.cap_fwd[k] >= d.n_fwd) return bad("cap_fwd out of range");
+    if (!(d.cap_K[k] > 0.0) || !std::isfinite(d.cap_K[k])) return bad("cap_K must be finite and > 0");
+    if (!(d.cap_vol[k] > 0.0) || !std::isfinite(d.cap_vol[k])) return bad("cap_vol must be finite and > 0");
+    if (d.cap_w && !(d.cap_w[k] >= 0.0 && std::isfinite(d.cap_w[k]))) return bad("cap_w must be finite and >= 0");
+  }
+  for (int k = 0; k < d.n_swp; ++k) {
+    if (d.swp_start[k] < 0 || d.swp_end[k] <= d.swp_start[k] || d.swp_end[k] > d.n_fwd)
+      return bad("swaption window out of range");
+    if (d.swp_end[k] - d.swp_start[k] > 64) return bad("swap windows longer than 64 forwards are not supported");
+    if (!(d.swp_K[k] > 0.0) || !std::isfinite(d.swp_K[k])) return bad("swp_K must be finite and > 0");
+    if (!(d.swp_vol[k] > 0.0) || !std::isfinite(d.swp_vol[k])) return bad("swp_vol must be finite and > 0");
+    if (d.swp_w && !(d.swp_w[k] >= 0.0 && std::isfinite(d.swp_w[k]))) return bad("swp_w must be finite and >= 0");
+  }
+  if (d.model == SABR_LMM_MODEL_SMILE) {
+    if (d.n_param != 3) return bad("the smile model has 3 parameters [alpha, rho, nu]");
+    if (d.n_swp != 0) return bad("the smile model prices caplets only");
+  } else {
+    if (d.n_param != 12) return bad("the Rebonato model has 12 parameter slots");
+    if (!(d.panel > 0.0)) return bad("panel must be > 0");
+    for (int k = 0; k <= d.n_fwd; ++k) {
+      double r = d.T[k] / d.panel;
+      if (std::fabs(r - std::round(r)) > 1e-9 * std::max(1.0, r)) return bad("every T[k] must be a multiple of panel");
+    }
+    if (std::round(d.T[d.n_fwd] / d.panel) > 240) return bad("more than 240 panels");
+  }
+  if (!d.lo || !d.hi || !d.free_mask) return bad("lo, hi and free_mask are required");
+  for (int k = 0; k < d.n_param; ++k)
+    if (!(d.lo[k] <= d.hi[k]) || !std::isfinite(d.lo[k]) || !std::isfinite(d.hi[k])) return bad("box must satisfy lo <= hi");
+  return std::string();
+}
+
+int n_panels(double t, double panel) { return (int)std::lround(t / panel); }
+
+}  // namespace
+
+// ====================================================================== load / free
+extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* descs, int32_t n_markets, void* stream,
+                                                sabr_lmm_market** out) {
+  if (!descs || !out || n_markets < 1) return fail(SABR_LMM_EINVAL, "descs, out and n_markets >= 1 are required");
+  *out = nullptr;
+  for (int j = 0; j < n_markets; ++j) {
+    if (descs[j].quad_nodes != 8 && descs[j].model == SABR_LMM_MODEL_REBONATO)
+      return fail(SABR_LMM_ENOTSUP, "quad_nodes must be 8");
+    std::string e = validate(descs[j], j);
+    if (!e.empty()) return fail(SABR_LMM_EINVAL, e);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena A;
+  struct Off {
+    size_t T, P, cap_K, cap_vol, cap_wu, swp_K, swp_vol, swp_wu, cap_fwd, swp_start, swp_end, swp_swap, swap_a, swap_b,
+        capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
+        swp_w, cblk64, cblk32, sblk64, sblk32, q64, q32, err;
+  };
+  std::vector<Off> off(n_markets);
+  std::vector<DevMarket> dm(n_markets);
+  std::vector<HostMarket> hm(n_markets);
+  // host-side integer bookkeeping
+  std::vector<std::vector<int>> capfwd(n_markets), fwdnp(n_markets), swp_swap(n_markets), swap_a(n_markets),
+      swap_b(n_markets), swap_np(n_markets);
+  for (int j = 0; j < n_markets; ++j) {
+    const sabr_lmm_market_desc& d = descs[j];
+    DevMarket& m = dm[j];
+    std::memset(&m, 0, sizeof m);
+    m.model = d.model; m.formula = d.formula; m.n_param = d.n_param; m.n_fwd = d.n_fwd;
+    m.n_cap = d.n_cap; m.n_swp = d.n_swp; m.beta = d.beta;
+    m.panel = d.model == SABR_LMM_MODEL_REBONATO ? d.panel : 0.5;
+    m.n_cap_pad = (d.n_cap + 3) / 4 * 4;
+    m.n_swp_pad = (d.n_swp + 3) / 4 * 4;
+    std::vector<int> seen(d.n_fwd, 0);
+    for (int k = 0; k < d.n_cap; ++k)
+      if (!seen[d.cap_fwd[k]]) { seen[d.cap_fwd[k]] = 1; capfwd[j].push_back(d.cap_fwd[k]); }
+    m.n_capfwd = (int)capfwd[j].size();
+    fwdnp[j].assign(d.n_fwd, 0);
+    int NP = 0;
+    for (int i = 0; i < d.n_fwd; ++i) {
+      fwdnp[j][i] = d.model == SABR_LMM_MODEL_REBONATO ? n_panels(d.T[i], m.panel) : 0;
+      if (seen[i]) NP = std::max(NP, fwdnp[j][i]);
+    }
+    std::map<std::pair<int, int>, int> idx;
+    int max_win = 1;
+    for (int k = 0; k < d.n_swp; ++k) {
+      auto key = std::make_pair(d.swp_start[k], d.swp_end[k]);
+      auto it = idx.find(key);
+      if (it == idx.end()) {
+        int id = (int)swap_a[j].size();
+        idx[key] = id;
+        swap_a[j].push_back(key.first);
+        swap_b[j].push_back(key.second);
+        swap_np[j].push_back(n_panels(d.T[key.first], m.panel));
+        max_win = std::max(max_win, key.second - key.first);
+        swp_swap[j].push_back(id);
+      } else {
+        swp_swap[j].push_back(it->second);
+      }
+    }
+    m.n_swap = (int)swap_a[j].size();
+    m.max_win = max_win;
+    m.NP = std::max(NP, 1);
+    HostMarket& h = hm[j];
+    h.model = d.model; h.formula = d.formula; h.n_param = d.n_param; h.n_fwd = d.n_fwd;
+    h.n_cap = d.n_cap; h.n_swp = d.n_swp; h.beta = d.beta;
+    h.lo.assign(d.lo, d.lo + d.n_param);
+    h.hi.assign(d.hi, d.hi + d.n_param);
+    h.freem.assign(d.free_mask, d.free_mask + d.n_param);
+    h.cap_vol.assign(d.cap_vol ? d.cap_vol : d.cap_K, (d.cap_vol ? d.cap_vol : d.cap_K) + d.n_cap);
+    h.swp_vol.assign(d.swp_vol ? d.swp_vol : d.swp_K, (d.swp_vol ? d.swp_vol : d.swp_K) + d.n_swp);
+    Off& o = off[j];
+    const int nf1 = d.n_fwd + 1;
+    o.T = A.take(nf1 * 8); o.P = A.take(nf1 * 8);
+    o.cap_K = A.take(d.n_cap * 8); o.cap_vol = A.take(d.n_cap * 8); o.cap_wu = A.take(d.n_cap * 8);
+    o.swp_K = A.take(d.n_swp * 8); o.swp_vol = A.take(d.n_swp * 8); o.swp_wu = A.take(d.n_swp * 8);
+    o.cap_fwd = A.take(d.n_cap * 4); o.swp_start = A.take(d.n_swp * 4); o.swp_end = A.take(d.n_swp * 4);
+    o.swp_swap = A.take(d.n_swp * 4); o.swap_a = A.take(m.n_swap * 4); o.swap_b = A.take(m.n_swap * 4);
+    o.capfwd_list = A.take(m.n_capfwd * 4); o.fwd_np = A.take(d.n_fwd * 4);
+    o.lo = A.take(d.n_param * 8); o.hi = A.take(d.n_param * 8); o.freem = A.take(d.n_param);
+    o.F = A.take(d.n_fwd * 8); o.tau = A.take(d.n_fwd * 8);
+    o.swap_A = A.take(m.n_swap * 8); o.swap_S = A.take(m.n_swap * 8); o.swap_TE = A.take(m.n_swap * 8);
+    o.swap_W = A.take((size_t)m.n_swap * max_win * 8); o.swap_np = A.take(m.n_swap * 4);
+    o.cap_pm = A.take(d.n_cap * 8); o.cap_w = A.take(d.n_cap * 8);
+    o.swp_pm = A.take(d.n_swp * 8); o.swp_w = A.take(d.n_swp * 8);
+    o.cblk64 = A.take(instr_block_bytes<double>(m.n_cap_pad)); o.cblk32 = A.take(instr_block_bytes<float>(m.n_cap_pad));
+    o.sblk64 = A.take(instr_block_bytes<double>(m.n_swp_pad)); o.sblk32 = A.take(instr_block_bytes<float>(m.n_swp_pad));
+    o.q64 = A.take(sizeof(QuadTab<double>)); o.q32 = A.take(sizeof(QuadTab<float>));
+    o.err = A.take(16);
+  }
+  std::vector<unsigned char> host(A.size, 0);
+  auto put = [&](size_t o, const void* src, size_t bytes) { if (src && bytes) std::memcpy(host.data() + o, src, bytes); };
+  // quadrature table (same for every market of a given panel width)
+  for (int j = 0; j < n_markets; ++j) {
+    const sabr_lmm_market_desc& d = descs[j];
+    const Off& o = off[j];
+    const DevMarket& m = dm[j];
+    put(o.T, d.T, (d.n_fwd + 1) * 8); put(o.P, d.P, (d.n_fwd + 1) * 8);
+    put(o.cap_K, d.cap_K, d.n_cap * 8); put(o.cap_vol, d.cap_vol, d.n_cap * 8); put(o.cap_wu, d.cap_w, d.cap_w ? d.n_cap * 8 : 0);
+    put(o.swp_K, d.swp_K, d.n_swp * 8); put(o.swp_vol, d.swp_vol, d.n_swp * 8); put(o.swp_wu, d.swp_w, d.swp_w ? d.n_swp * 8 : 0);
+    put(o.cap_fwd, d.cap_fwd, d.n_cap * 4); put(o.swp_start, d.swp_start, d.n_swp * 4); put(o.swp_end, d.swp_end, d.n_swp * 4);
+    put(o.swp_swap, swp_swap[j].data(), d.n_swp * 4);
+    put(o.swap_a, swap_a[j].data(), m.n_swap * 4); put(o.swap_b, swap_b[j].data(), m.n_swap * 4);
+    put(o.swap_np, swap_np[j].data(), m.n_swap * 4);
+    put(o.capfwd_list, capfwd[j].data(), m.n_capfwd * 4); put(o.fwd_np, fwdnp[j].data(), d.n_fwd * 4);
+    put(o.lo, d.lo, d.n_param * 8); put(o.hi, d.hi, d.n_param * 8); put(o.freem, d.free_mask, d.n_param);
+    QuadTab<double> q64;
+    QuadTab<float> q32;
+    const double D = m.panel;
+    for (int q = 0; q < kQ; ++q) {
+      const double oq = 0.5 * D * (1.0 + kGLx[q]);
+      const double hq = 0.5 * (D - oq);
+      q64.o[q] = oq; q64.w[q] = 0.5 * D * kGLw[q];
+      for (int r = 0; r < kQ; ++r) {
+        q64.o2[q * kQ + r] = oq + hq * (1.0 + kGLx[r]);
+        q64.w2[q * kQ + r] = hq * kGLw[r];
+      }
+    }
+    for (int i = 0; i < kQ; ++i) { q32.o[i] = (float)q64.o[i]; q32.w[i] = (float)q64.w[i]; }
+    for (int i = 0; i < kQ * kQ; ++i) { q32.o2[i] = (float)q64.o2[i]; q32.w2[i] = (float)q64.w2[i]; }
+    put(o.q64, &q64, sizeof q64);
+    put(o.q32, &q32, sizeof q32);
+  }
+  sabr_lmm_market* mk = new sabr_lmm_market();
+  cudaGetDevice(&mk->device);
+  cudaError_t e = cudaMalloc(&mk->arena, A.size);
+  if (e != cudaSuccess) { delete mk; return fail(SABR_LMM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+  e = cudaMemcpyAsync(mk->arena, host.data(), A.size, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { cudaFree(mk->arena); delete mk; return fail(SABR_LMM_ECUDA, cudaGetErrorString(e)); }
+  char* base = (char*)mk->arena;
+  for (int j = 0; j < n_markets; ++j) {
+    DevMarket& m = dm[j];
+    const Off& o = off[j];
+    m.T = (const double*)(base + o.T); m.P = (const double*)(base + o.P);
+    m.cap_K = (const double*)(base + o.cap_K); m.cap_vol = (const double*)(base + o.cap_vol);
+    m.cap_wu = descs[j].cap_w ? (const double*)(base + o.cap_wu) : nullptr;
+    m.swp_K = (const double*)(base + o.swp_K); m.swp_vol = (const double*)(base + o.swp_vol);
+    m.swp_wu = descs[j].swp_w ? (const double*)(base + o.swp_wu) : nullptr;
+    m.cap_fwd = (const int*)(base + o.cap_fwd); m.swp_start = (const int*)(base + o.swp_start);
+    m.swp_end = (const int*)(base + o.swp_end); m.swp_swap = (const int*)(base + o.swp_swap);
+    m.swap_a = (const int*)(base + o.swap_a); m.swap_b = (const int*)(base + o.swap_b);
+    m.capfwd_list = (const int*)(base + o.capfwd_list); m.fwd_np = (const int*)(base + o.fwd_np);
+    m.lo = (const double*)(base + o.lo); m.hi = (const double*)(base + o.hi);
+    m.freem = (const unsigned char*)(base + o.freem);
+    m.F = (double*)(base + o.F); m.tau = (double*)(base + o.tau);
+    m.swap_A = (double*)(base + o.swap_A); m.swap_S = (double*)(base + o.swap_S); m.swap_TE = (double*)(base + o.swap_TE);
+    m.swap_W = (double*)(base + o.swap_W); m.swap_np = (int*)(base + o.swap_np);
+    m.cap_pm = (double*)(base + o.cap_pm); m.cap_w = (double*)(base + o.cap_w);
+    m.swp_pm = (double*)(base + o.swp_pm); m.swp_w = (double*)(base + o.swp_w);
+    m.cblk64 = base + o.cblk64; m.cblk32 = base + o.cblk32; m.sblk64 = base + o.sblk64; m.sblk32 = base + o.sblk32;
+    m.q64 = (const QuadTab<double>*)(base + o.q64); m.q32 = (const QuadTab<float>*)(base + o.q32);
+    m.err = (int*)(base + o.err);
+    setup_forwards_kernel<<<(m.n_fwd + 127) / 128, 128, 0, s>>>(m);
+    if (m.n_swap > 0) setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
+    const int ni = m.n_cap + m.n_swp;
+    setup_instruments_kernel<<<(ni + 127) / 128, 128, 0, s>>>(m);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { cudaFree(mk->arena); delete mk; return fail(SABR_LMM_ECUDA, cudaGetErrorString(e)); }
+  mk->dm = dm;
+  mk->hm = hm;
+  *out = mk;
+  return SABR_LMM_OK;
+}
+
+extern "C" void sabr_lmm_free_market(sabr_lmm_market* m) {
+  if (!m) return;
+  if (m->arena) cudaFree(m->arena);
+  delete m;
+}
+
+// ====================================================================== dispatch
+namespace {
+
+template <class R, int MODEL, int FORMULA>
+cudaError_t launch_objective(const DevMarket& m, const double* X, long long n, double* f, double* vols, cudaStream_t s) {
+  const int W = 4;
+  const uint32_t sm = smem_bytes<R>(m, W);
+  auto kern = objective_kernel<R, MODEL, FORMULA>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  long long blocks = (n + W - 1) / W;
+  if (blocks > 148 * 64) blocks = 148 * 64;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, W * 32, sm, s>>>(m, X, n, f, vols);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_objective_r(const DevMarket& m, const double* X, long long n, double* f, double* vols, cudaStream_t s) {
+  if (m.model == 0) return m.formula == 0 ? launch_objective<R, 0, 0>(m, X, n, f, vols, s) : launch_objective<R, 0, 1>(m, X, n, f, vols, s);
+  return m.formula == 0 ? launch_objective<R, 1, 0>(m, X, n, f, vols, s) : launch_objective<R, 1, 1>(m, X, n, f, vols, s);
+}
+
+cudaError_t launch_objective_any(const DevMarket& m, int prec, const double* X, long long n, double* f, double* vols,
+                                 cudaStream_t s) {
+  return prec == SABR_LMM_FP64 ? launch_objective_r<double>(m, X, n, f, vols, s)
+                               : launch_objective_r<float>(m, X, n, f, vols, s);
+}
+
+sabr_lmm_status check_call(const sabr_lmm_market* m, int32_t idx, int64_t n, int32_t prec) {
+  if (!m) return fail(SABR_LMM_EINVAL, "market is NULL");
+  if (idx < 0 || idx >= (int)m->dm.size()) return fail(SABR_LMM_EINVAL, "market_idx out of range");
+  if (n < 0) return fail(SABR_LMM_EINVAL, "n must be >= 0");
+  if (prec < SABR_LMM_FP64 || prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
+  if (m->dm[idx].n_swp > 0) return fail(SABR_LMM_ENOTSUP, "swaptions are not enabled in this build");
+  return SABR_LMM_OK;
+}
+
+}  // namespace
+
+extern "C" sabr_lmm_status sabr_lmm_objective(const sabr_lmm_market* m, int32_t idx, const double* X, int64_t n,
+                                              int32_t prec, double* f, void* stream) {
+  sabr_lmm_status st = check_call(m, idx, n, prec);
+  if (st != SABR_LMM_OK) return st;
+  if (n == 0) return SABR_LMM_OK;
+  if (!X || !f) return fail(SABR_LMM_EINVAL, "X and f are required");
+  CUDA_TRY(launch_objective_any(m->dm[idx], prec, X, n, f, nullptr, (cudaStream_t)stream));
+  return SABR_LMM_OK;
+}
+
+extern "C" sabr_lmm_status sabr_lmm_model_vols(const sabr_lmm_market* m, int32_t idx, const double* X, int64_t n,
+                                               int32_t prec, double* vols, void* stream) {
+  sabr_lmm_status st = check_call(m, idx, n, prec);
+  if (st != SABR_LMM_OK) return st;
+  if (n == 0) return SABR_LMM_OK;
+  if (!X || !vols) return fail(SABR_LMM_EINVAL, "X and vols are required");
+  CUDA_TRY(launch_objective_any(m->dm[idx], prec, X, n, nullptr, vols, (cudaStream_t)stream));
+  return SABR_LMM_OK;
+}
+
+extern "C" sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int32_t idx, const double* X, int64_t n,
+                                                   int32_t prec, double* f, double* G, void* stream) {
+  (void)m; (void)idx; (void)X; (void)n; (void)prec; (void)f; (void)G; (void)stream;
+  return fail(SABR_LMM_ENOTSUP, "objective_grad is not enabled in this build");
+}
+
+extern "C" sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t idx, double* X, int64_t n,
+                                              int32_t max_iter, double target, double* f, double* rmse, void* stream) {
+  (void)m; (void)idx; (void)X; (void)n; (void)max_iter; (void)target; (void)f; (void)rmse; (void)stream;
+  return fail(SABR_LMM_ENOTSUP, "lm_polish is not enabled in this build");
+}
+
+// ====================================================================== annealing
+namespace {
+
+// Kernel attributes are set before any launch (outside stream capture); enqueue only launches.
+template <class R, int MODEL, int FORMULA>
+cudaError_t enqueue_anneal_t(const DevMarket& m, const SAState& st, const SAParams& sp, int W, int grid, cudaStream_t s,
+                             bool configure_only) {
+  const uint32_t sm1 = smem_bytes<R>(m, 1), smW = smem_bytes<R>(m, W);
+  auto k0 = sa_start_kernel<R, MODEL, FORMULA>;
+  auto k1 = sa_level_kernel<R, MODEL, FORMULA>;
+  if (configure_only) {
+    cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smW);
+    return e;
+  }
+  k0<<<1, 32, sm1, s>>>(m, st, sp);
+  for (int l = 0; l < sp.L; ++l) k1<<<grid, W * 32, smW, s>>>(m, st, sp, l);
+  sa_final_kernel<<<1, 1024, 0, s>>>(st, sp.C, sp.P);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_anneal(const DevMarket& m, int prec, const SAState& st, const SAParams& sp, int W, int grid,
+                           cudaStream_t s, bool configure_only = false) {
+  const bool f64 = prec == SABR_LMM_FP64;
+#define DISPATCH(R)                                                                                           \
+  if (m.model == 0) return m.formula == 0 ? enqueue_anneal_t<R, 0, 0>(m, st, sp, W, grid, s, configure_only)  \
+                                          : enqueue_anneal_t<R, 0, 1>(m, st, sp, W, grid, s, configure_only); \
+  return m.formula == 0 ? enqueue_anneal_t<R, 1, 0>(m, st, sp, W, grid, s, configure_only)                   \
+                        : enqueue_anneal_t<R, 1, 1>(m, st, sp, W, grid, s, configure_only);
+  if (f64) { DISPATCH(double) } else { DISPATCH(float) }
+#undef DISPATCH
+}
+
+sabr_lmm_status enqueue_plan(sabr_lmm_anneal_plan* p, cudaStream_t s) {
+  const int nm = (int)p->mk->dm.size();
+  for (int j = 0; j < nm; ++j) {
+    cudaError_t e = enqueue_anneal(p->mk->dm[j], p->opts.prec, p->st[j], p->sp[j], p->W, p->grid, s);
+    if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("anneal launch: ") + cudaGetErrorString(e));
+  }
+  return SABR_LMM_OK;
+}
+
+}  // namespace
+
+extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, const sabr_lmm_anneal_opts* o,
+                                                   void* stream, sabr_lmm_anneal_plan** out) {
+  if (!mk || !o || !out) return fail(SABR_LMM_EINVAL, "market, opts and out are required");
+  *out = nullptr;
+  if (o->n_chains < 1 || o->n_levels < 1 || o->steps_per_level < 1) return fail(SABR_LMM_EINVAL, "n_chains, n_levels, steps_per_level must be >= 1");
+  if (!(o->cooling > 0.0 && o->cooling <= 1.0)) return fail(SABR_LMM_EINVAL, "cooling must be in (0, 1]");
+  if (!(o->step_frac > 0.0) || !(o->step_floor >= 0.0)) return fail(SABR_LMM_EINVAL, "step_frac > 0 and step_floor >= 0 required");
+  if (o->prec < SABR_LMM_FP64 || o->prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
+  if (o->warps_per_block < 0 || o->warps_per_block > 16) return fail(SABR_LMM_EINVAL, "warps_per_block must be in [0, 16]");
+  if (o->lm_top_k > 0) return fail(SABR_LMM_ENOTSUP, "the LM polish is not enabled in this build");
+  for (const DevMarket& m : mk->dm)
+    if (m.n_swp > 0) return fail(SABR_LMM_ENOTSUP, "swaptions are not enabled in this build");
+  sabr_lmm_anneal_plan* p = new sabr_lmm_anneal_plan();
+  p->mk = mk;
+  p->opts = *o;
+  p->opts.x0 = nullptr;
+  p->W = o->warps_per_block > 0 ? o->warps_per_block : 4;
+  p->grid = (o->n_chains + p->W - 1) / p->W;
+  const int nm = (int)mk->dm.size();
+  const int P = mk->dm[0].n_param;
+  const size_t C = o->n_chains, L = o->n_levels, N = o->steps_per_level;
+  // per market: xs[P] fs T0 xe[CP] fe[C] xb[CP] fb[C] part_f[grid] part_c[grid] counter trace[L] best_x[P] best_f x0[P]
+  Arena A;
+  struct Off { size_t xs, fs, T0, xe, fe, xb, fb, pf, pc, cnt, tr, bx, bf, x0, bits, vols, rmse; };
+  std::vector<Off> off(nm);
+  for (int j = 0; j < nm; ++j) {
+    const int Pj = mk->dm[j].n_param;
+    Off& q = off[j];
+    q.xs = A.take(Pj * 8); q.fs = A.take(8); q.T0 = A.take(8);
+    q.xe = A.take(C * Pj * 8); q.fe = A.take(C * 8); q.xb = A.take(C * Pj * 8); q.fb = A.take(C * 8);
+    q.pf = A.take((size_t)p->grid * 8); q.pc = A.take((size_t)p->grid * 4); q.cnt = A.take(16);
+    q.tr = A.take(L * 8); q.bx = A.take(Pj * 8); q.bf = A.take(8); q.x0 = A.take(Pj * 8);
+    q.bits = (j == 0 && o->record_accepts) ? A.take(C * L * N) : 0;
+    q.vols = A.take((size_t)(mk->dm[j].n_cap + mk->dm[j].n_swp) * 8);
+    q.rmse = A.take(8);
+  }
+  if (cudaMalloc(&p->state, A.size) != cudaSuccess) { delete p; return fail(SABR_LMM_ENOMEM, "cudaMalloc of the chain state failed"); }
+  char* b = (char*)p->state;
+  p->x0.resize((size_t)nm * P);
+  for (int j = 0; j < nm; ++j) {
+    const DevMarket& m = mk->dm[j];
+    const HostMarket& h = mk->hm[j];
+    const Off& q = off[j];
+    SAState s{};
+    s.xs = (double*)(b + q.xs); s.fs = (double*)(b + q.fs); s.T0 = (double*)(b + q.T0);
+    s.xe = (double*)(b + q.xe); s.fe = (double*)(b + q.fe); s.xb = (double*)(b + q.xb); s.fb = (double*)(b + q.fb);
+    s.part_f = (double*)(b + q.pf); s.part_c = (int*)(b + q.pc); s.counter = (unsigned int*)(b + q.cnt);
+    s.trace_f = (double*)(b + q.tr); s.best_x = (double*)(b + q.bx); s.best_f = (double*)(b + q.bf);
+    s.bits = (j == 0 && o->record_accepts) ? (uint8_t*)(b + q.bits) : nullptr;
+    p->st.push_back(s);
+    SAParams sp{};
+    sp.C = o->n_chains; sp.L = o->n_levels; sp.N = o->steps_per_level; sp.P = m.n_param;
+    sp.cooling = o->cooling; sp.step_frac = o->step_frac; sp.step_floor = o->step_floor; sp.T0_opt = o->T0;
+    sp.seed = o->seed; sp.market_index = (unsigned long long)j;
+    sp.x0 = (const double*)(b + q.x0);
+    p->sp.push_back(sp);
+    for (int k = 0; k < m.n_param; ++k)
+      p->x0[(size_t)j * P + k] = o->x0 ? o->x0[(size_t)j * m.n_param + k] : 0.5 * (h.lo[k] + h.hi[k]);
+  }
+  p->vols_dev = (double*)(b + off[0].vols);
+  p->rmse_dev = (double*)(b + off[0].rmse);
+  p->stream = (cudaStream_t)stream;
+  if (!p->stream && o->use_graph) {
+    cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    p->own_stream = true;
+  }
+  cudaEventCreate(&p->ev0);
+  cudaEventCreate(&p->ev1);
+  for (int j = 0; j < nm; ++j) {
+    cudaError_t e = enqueue_anneal(mk->dm[j], o->prec, p->st[j], p->sp[j], p->W, p->grid, p->stream, true);
+    if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, std::string("configure: ") + cudaGetErrorString(e)); }
+  }
+  for (int j = 0; j < nm; ++j) {
+    cudaError_t e = cudaMemcpyAsync((void*)p->sp[j].x0, p->x0.data() + (size_t)j * P, mk->dm[j].n_param * 8,
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, cudaGetErrorString(e)); }
+  }
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, cudaGetErrorString(e)); }
+  *out = p;
+  return SABR_LMM_OK;
+}
+
+extern "C" sabr_lmm_status sabr_lmm_anneal_launch(sabr_lmm_anneal_plan* p, void* stream) {
+  if (!p) return fail(SABR_LMM_EINVAL, "plan is NULL");
+  cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
+  if (p->opts.use_graph) {
+    if (!s) return fail(SABR_LMM_EINVAL, "graph replay needs a non-default stream");
+    if (!p->gexec) {
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      sabr_lmm_status st = enqueue_plan(p, s);
+      cudaError_t e = cudaStreamEndCapture(s, &g);
+      if (st != SABR_LMM_OK) { if (g) cudaGraphDestroy(g); return st; }
+      if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&p->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaEventRecord(p->ev0, s));
+    CUDA_TRY(cudaGraphLaunch(p->gexec, s));
+    CUDA_TRY(cudaEventRecord(p->ev1, s));
+  } else {
+    CUDA_TRY(cudaEventRecord(p->ev0, s));
+    sabr_lmm_status st = enqueue_plan(p, s);
+    if (st != SABR_LMM_OK) return st;
+    CUDA_TRY(cudaEventRecord(p->ev1, s));
+  }
+  p->stream = s;
+  return SABR_LMM_OK;
+}
+
+extern "C" sabr_lmm_status sabr_lmm_anneal_fetch(sabr_lmm_anneal_plan* p, sabr_lmm_result* out) {
+  if (!p || !out) return fail(SABR_LMM_EINVAL, "plan and out are required");
+  cudaStream_t s = p->stream;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  const sabr_lmm_market* mk = p->mk;
+  const int nm = (int)mk->dm.size();
+  int err = 0;
+  for (int j = 0; j < nm; ++j) {
+    int e = 0;
+    CUDA_TRY(cudaMemcpy(&e, mk->dm[j].err, sizeof(int), cudaMemcpyDeviceToHost));
+    err |= e;
+  }
+  if (err) return fail(SABR_LMM_ETIMEOUT, "a bounded device-side wait gave up");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  out->seconds = ms * 1e-3;
+  out->lm_seconds = 0.0;
+  out->n_evals = (int64_t)p->opts.n_chains * ((int64_t)p->opts.n_levels * p->opts.steps_per_level + 1);
+  for (int j = 0; j < nm; ++j) {
+    const DevMarket& m = mk->dm[j];
+    const int Pj = m.n_param;
+    if (out->x_best) CUDA_TRY(cudaMemcpy(out->x_best + (size_t)j * Pj, p->st[j].best_x, Pj * 8, cudaMemcpyDeviceToHost));
+    if (out->f_best) CUDA_TRY(cudaMemcpy(out->f_best + j, p->st[j].best_f, 8, cudaMemcpyDeviceToHost));
+    if (out->trace_f)
+      CUDA_TRY(cudaMemcpy(out->trace_f + (size_t)j * p->opts.n_levels, p->st[j].trace_f, p->opts.n_levels * 8, cudaMemcpyDeviceToHost));
+    if (j == 0) CUDA_TRY(cudaMemcpy(&out->T0_used, p->st[0].T0, 8, cudaMemcpyDeviceToHost));
+    if (out->rmse_volpt) {
+      CUDA_TRY(launch_objective_any(m, SABR_LMM_FP64, p->st[j].best_x, 1, nullptr, p->vols_dev, s));
+      rmse_from_vols_kernel<<<1, 256, 0, s>>>(p->vols_dev, m.cap_vol, m.swp_vol, m.n_cap, m.n_swp, p->rmse_dev);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaMemcpyAsync(out->rmse_volpt + j, p->rmse_dev, 8, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+    }
+  }
+  if (out->accept_bits && p->st[0].bits)
+    CUDA_TRY(cudaMemcpy(out->accept_bits, p->st[0].bits,
+                        (size_t)p->opts.n_chains * p->opts.n_levels * p->opts.steps_per_level, cudaMemcpyDeviceToHost));
+  return SABR_LMM_OK;
+}
+
+extern "C" void sabr_lmm_anneal_plan_free(sabr_lmm_anneal_plan* p) {
+  if (!p) return;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  if (p->state) cudaFree(p->state);
+  delete p;
+}
+
+extern "C" sabr_lmm_status sabr_lmm_anneal(const sabr_lmm_market* mk, const sabr_lmm_anneal_opts* o, sabr_lmm_result* out) {
+  if (!out) return fail(SABR_LMM_EINVAL, "out is required");
+  sabr_lmm_anneal_plan* p = nullptr;
+  sabr_lmm_status st = sabr_lmm_anneal_prepare(mk, o, nullptr, &p);
+  if (st != SABR_LMM_OK) return st;
+  st = sabr_lmm_anneal_launch(p, nullptr);
+  if (st == SABR_LMM_OK) st = sabr_lmm_anneal_fetch(p, out);
+  sabr_lmm_anneal_plan_free(p);
+  return st;
+}
+
+extern "C" sabr_lmm_status sabr_lmm_quadrature_rule(int32_t q, double* x, double* w) {
+  if (q != 8 || !x || !w) return fail(SABR_LMM_EINVAL, "q must be 8 and x, w non-NULL");
+  for (int i = 0; i < 8; ++i) { x[i] = kGLx[i]; w[i] = kGLw[i]; }
+  return SABR_LMM_OK;
+}
+
+extern "C" const char* sabr_lmm_last_error(void) { return g_err.c_str(); }
+extern "C" const char* sabr_lmm_version(void) { return "sabr_lmm 0.1 (sm_103a)"; }

@@ -1,0 +1,121 @@
+// Device arithmetic of the hot path, templated on the pricing precision R (double or float).
+//
+//   philox4x64_10 ... counter-based uniforms (Salmon et al., SC'11): ten rounds of two
+//                     64x64->128 products with the Weyl key schedule.
+//   z_over_x ........ z / x(z) of Hagan et al. (2002), x(z) = log((sqrt(1-2rz+z^2)+z-r)/(1-r)),
+//                     in a cancellation-free form (see below) with its Taylor series near z = 0.
+//   sabr_* .......... the Hagan (2002) lognormal expansion and Eq. (sigmaHagan) of the paper.
+//   black_otm ....... Black's formula for the out-of-the-money option on a forward or swap rate.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sabr {
+
+// ------------------------------------------------------------------ precision traits
+template <class R> struct Num;
+template <> struct Num<double> {
+  static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+  static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double erfc_(double x) { return erfc(x); }
+  static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+  static __device__ __forceinline__ bool finite_(double x) { return isfinite(x); }
+  static constexpr double zx_series = 1e-6;  // |z| below which z/x(z) uses its series
+};
+template <> struct Num<float> {
+  static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+  static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float erfc_(float x) { return erfcf(x); }
+  static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+  static __device__ __forceinline__ bool finite_(float x) { return isfinite(x); }
+  static constexpr float zx_series = 1e-3f;  // series error O(z^3) < 2^-24 there
+};
+
+// ------------------------------------------------------------------ Philox4x64-10
+struct U4 { uint64_t v[4]; };
+
+__device__ __forceinline__ U4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                            uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  U4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+  return o;
+}
+
+__device__ __forceinline__ double u53(uint64_t w) { return (double)(w >> 11) * 0x1.0p-53; }
+
+// ------------------------------------------------------------------ SABR
+// z / x(z).  With zz = |z| and r = sign(z) rho (x(z; rho) = -x(-z; -rho)), and s = sqrt(1 - 2 r zz
+// + zz^2):  x = log1p(N / (1 - r)),  N = ((s - 1) + zz) = zz (s + 1 - 2r + zz) / (s + 1).
+// For r > 0 the factor s + 1 - 2r + zz = (s - r) + (1 - r) + zz is formed from
+// s - r = ((1 - r)(1 + r) + zz (zz - 2r)) / (s + r), which avoids the cancellation of s against r
+// when r approaches 1; for r <= 0 every term of (zz^2 - 2 r zz)/(s+1) + zz is non-negative.
+template <class R>
+__device__ __forceinline__ R z_over_x(R z, R rho) {
+  typedef Num<R> M;
+  const R zz = M::abs_(z);
+  if (zz < M::zx_series) return R(1) - R(0.5) * rho * z + (R(2) - R(3) * rho * rho) * z * z / R(12);
+  const R r = z < R(0) ? -rho : rho;
+  const R s = M::sqrt_(R(1) - R(2) * r * zz + zz * zz);
+  R num;
+  if (r > R(0)) {
+    const R omr = R(1) - r;
+    const R smr = (omr * (R(1) + r) + zz * (zz - R(2) * r)) / (s + r);
+    num = zz * (smr + omr + zz) / (s + R(1));
+  } else {
+    num = (zz * zz - R(2) * r * zz) / (s + R(1)) + zz;
+  }
+  return zz / M::log1p_(num / (R(1) - r));
+}
+
+// Hagan et al. (2002): sigma = alpha * inv_den * z/x(z) * (1 + c1 alpha^2 + c2 rho nu alpha
+// + c3 (2 - 3 rho^2) nu^2), with z = (nu/alpha) fk l and the market-only constants
+// fk = (FK)^{(1-b)/2}, l = log(F/K), inv_den = 1/(fk (1 + (1-b)^2 l^2/24 + (1-b)^4 l^4/1920)),
+// c1 = (1-b)^2 T / (24 fk^2), c2 = b T / (4 fk), c3 = T / 24.
+template <class R>
+__device__ __forceinline__ R sabr_hagan(R alpha, R rho, R nu, R l, R fk, R inv_den, R c1, R c2, R c3) {
+  const R z = nu / alpha * fk * l;
+  const R zx = z_over_x(z, rho);
+  const R corr = R(1) + c1 * alpha * alpha + c2 * rho * nu * alpha + c3 * (R(2) - R(3) * rho * rho) * nu * nu;
+  return alpha * inv_den * zx * corr;
+}
+
+// Eq. (sigmaHagan): sigma = alpha/fo {1 - (1/2)(omb - rho nu w) m + (1/12)[omb^2 + (2 - 3 rho^2)
+// nu^2 w^2 + 3 (omb - rho nu w)] m^2}, w = fo / alpha, fo = F^{1-b}, m = log(K/F) = -l.
+template <class R>
+__device__ __forceinline__ R sabr_paper(R alpha, R rho, R nu, R l, R fo, R omb) {
+  const R w = fo / alpha;
+  const R rnw = rho * nu * w;
+  const R m = -l;
+  return alpha / fo * (R(1) - R(0.5) * (omb - rnw) * m
+                       + (omb * omb + (R(2) - R(3) * rho * rho) * nu * nu * w * w + R(3) * (omb - rnw)) * (m * m) / R(12));
+}
+
+// ------------------------------------------------------------------ Black
+template <class R>
+__device__ __forceinline__ R ncdf(R x) {
+  return R(0.5) * Num<R>::erfc_(-x * R(0.70710678118654752440));
+}
+
+// Out-of-the-money Black price with sgn = +1 (call, K >= F) or -1 (put, K < F):
+//   P = sgn * DF * (Phi(sgn d1) - KF Phi(sgn d2)),  DF = D F,  KF = K / F,
+//   d1 = l / v + v / 2, d2 = d1 - v, v = sigma sqrt(T), l = log(F/K).
+template <class R>
+__device__ __forceinline__ R black_otm(R sigma, R sqrtT, R l, R DF, R KF, R sgn) {
+  const R v = sigma * sqrtT;
+  const R d1 = l / v + R(0.5) * v;
+  const R d2 = d1 - v;
+  return sgn * DF * (ncdf(sgn * d1) - KF * ncdf(sgn * d2));
+}
+
+}  // namespace sabr

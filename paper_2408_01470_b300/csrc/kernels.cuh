@@ -1,0 +1,419 @@
+// Kernels of the hot path and of market set-up.
+//
+//   setup_*_kernel ......... market-only constants in FP64 (once per load).
+//   objective_kernel ....... f for n parameter sets, one warp per set (grid-stride).
+//   vols_kernel ............ model vols for n parameter sets.
+//   sa_start_kernel ........ f(x0), T0, the first start point.
+//   sa_level_kernel ........ one temperature level: every chain (one warp) runs N Metropolis
+//                            steps (S1 proposal, S2-S7 objective, S8 acceptance), then the
+//                            minimum over the chains' end points is taken by the last CTA to
+//                            finish (no grid-wide wait) and becomes the next start point.
+//   sa_final_kernel ........ the best point ever accepted over all chains.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "device_math.cuh"
+#include "market.cuh"
+#include "objective.cuh"
+
+namespace sabr {
+
+// ------------------------------------------------------------------ market set-up (FP64)
+__global__ void setup_forwards_kernel(DevMarket m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m.n_fwd) {
+    const double tau = m.T[i + 1] - m.T[i];
+    m.tau[i] = tau;
+    m.F[i] = (m.P[i] / m.P[i + 1] - 1.0) / tau;
+  }
+}
+
+__global__ void setup_swaps_kernel(DevMarket m) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= m.n_swap) return;
+  const int a = m.swap_a[s], b = m.swap_b[s];
+  double A = 0.0;
+  for (int k = a; k < b; ++k) A += m.tau[k] * m.P[k + 1];
+  double S = 0.0;
+  for (int k = a; k < b; ++k) S += m.tau[k] * m.P[k + 1] / A * m.F[k];
+  for (int k = a; k < b; ++k)
+    m.swap_W[(size_t)s * m.max_win + (k - a)] = m.tau[k] * m.P[k + 1] / A * pow(m.F[k], m.beta) / pow(S, m.beta);
+  m.swap_A[s] = A;
+  m.swap_S[s] = S;
+  m.swap_TE[s] = m.T[a];
+}
+
+// Pricing constants of one instrument (see sabr_hagan / sabr_paper / black_otm).
+template <class R>
+__device__ void put_instr(void* blk, int npad, int k, double l, double fk, double inv_den, double c1, double c2,
+                          double c3, double sqrtT, double DF, double KF, double sgn, double pm, double sw, int idx) {
+  R* p = (R*)blk;
+  p[k] = (R)l; p[npad + k] = (R)fk; p[2 * npad + k] = (R)inv_den; p[3 * npad + k] = (R)c1;
+  p[4 * npad + k] = (R)c2; p[5 * npad + k] = (R)c3; p[6 * npad + k] = (R)sqrtT; p[7 * npad + k] = (R)DF;
+  p[8 * npad + k] = (R)KF; p[9 * npad + k] = (R)sgn; p[10 * npad + k] = (R)pm; p[11 * npad + k] = (R)sw;
+  ((int*)(p + 12 * npad))[k] = idx;
+}
+
+__device__ void instr_constants(const DevMarket& m, double F, double K, double T, double D, double vol, const double* wu,
+                                int k, double* pm_out, double* w_out, void* b64, void* b32, int npad, int idx) {
+  const double omb = 1.0 - m.beta;
+  const double l = log(F / K);
+  const double fk = (m.formula == 0) ? pow(F * K, 0.5 * omb) : pow(F, omb);
+  const double fkh = pow(F * K, 0.5 * omb);
+  const double den = fkh * (1.0 + omb * omb * l * l / 24.0 + omb * omb * omb * omb * l * l * l * l / 1920.0);
+  const double c1 = omb * omb * T / (24.0 * fkh * fkh);
+  const double c2 = m.beta * T / (4.0 * fkh);
+  const double c3 = T / 24.0;
+  const double sqrtT = sqrt(T);
+  const double sgn = (K < F) ? -1.0 : 1.0;
+  const double pm = black_otm<double>(vol, sqrtT, l, D * F, K / F, sgn);
+  const double v = vol * sqrtT;
+  const double d1 = l / v + 0.5 * v;
+  const double vega = D * F * exp(-0.5 * d1 * d1) * 0.39894228040143267794 * sqrtT;
+  const double w = wu ? wu[k] : 1.0 / (vega * vega);
+  pm_out[k] = pm;
+  w_out[k] = w;
+  const double sw = sqrt(w);
+  put_instr<double>(b64, npad, k, l, fk, 1.0 / den, c1, c2, c3, sqrtT, D * F, K / F, sgn, pm, sw, idx);
+  put_instr<float>(b32, npad, k, l, fk, 1.0 / den, c1, c2, c3, sqrtT, D * F, K / F, sgn, pm, sw, idx);
+}
+
+__global__ void setup_instruments_kernel(DevMarket m) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < m.n_cap) {
+    const int i = m.cap_fwd[k];
+    instr_constants(m, m.F[i], m.cap_K[k], m.T[i], m.tau[i] * m.P[i + 1], m.cap_vol[k], m.cap_wu, k, m.cap_pm,
+                    m.cap_w, m.cblk64, m.cblk32, m.n_cap_pad, i);
+  } else if (k < m.n_cap + m.n_swp) {
+    const int s = k - m.n_cap;
+    const int id = m.swp_swap[s];
+    instr_constants(m, m.swap_S[id], m.swp_K[s], m.swap_TE[id], m.swap_A[id], m.swp_vol[s], m.swp_wu, s, m.swp_pm,
+                    m.swp_w, m.sblk64, m.sblk32, m.n_swp_pad, id);
+  }
+}
+
+// ------------------------------------------------------------------ bulk staging into SMEM
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+constexpr long long kWaitLimit = 1LL << 24;
+
+// Stage `bytes` (multiple of 16, 16-byte aligned both sides) from global memory into shared
+// memory with the bulk-copy engine, completion tracked by an mbarrier.  Called by every thread
+// of the CTA.  Returns false (and raises the error word) if the bounded wait gave up.
+__device__ bool stage_to_smem(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* mbar, int* err) {
+  if (bytes == 0) return true;
+  const uint32_t bar = smem_u32(mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    const uint32_t chunk = 32768;
+    for (uint32_t off = 0; off < bytes; off += chunk) {
+      const uint32_t nb = (bytes - off < chunk) ? (bytes - off) : chunk;
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   ::"r"(smem_u32((char*)sdst + off)), "l"((const char*)gsrc + off), "r"(nb), "r"(bar)
+                   : "memory");
+    }
+  }
+  uint32_t done = 0;
+  long long it = 0;
+  while (!done) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(0u) : "memory");
+    if (!done && ++it > kWaitLimit) break;
+  }
+  const int timed_out = __syncthreads_or(!done);
+  if (timed_out) {
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    // give the copy in flight a second bounded chance to land before the CTA retires
+    it = 0;
+    while (!done && ++it < kWaitLimit) {
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(done) : "r"(bar), "r"(0u) : "memory");
+    }
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+template <class R> __device__ __forceinline__ const void* cap_block(const DevMarket& m);
+template <> __device__ __forceinline__ const void* cap_block<double>(const DevMarket& m) { return m.cblk64; }
+template <> __device__ __forceinline__ const void* cap_block<float>(const DevMarket& m) { return m.cblk32; }
+
+// Shared-memory plan: [caplet block][warp scratch x W][mbarrier (16 B), 32 doubles, 32 ints]
+template <class R>
+__host__ __device__ inline uint32_t smem_bytes(const DevMarket& m, int W) {
+  return instr_block_bytes<R>(m.n_cap_pad) + (uint32_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R) + 512;
+}
+
+struct CtaSmem {
+  void* cap;
+  unsigned char* scratch;
+  uint64_t* mbar;
+  double* red_f;
+  int* red_c;
+};
+
+template <class R>
+__device__ __forceinline__ CtaSmem carve(unsigned char* smem, const DevMarket& m, int W) {
+  CtaSmem s;
+  s.cap = smem;
+  s.scratch = smem + instr_block_bytes<R>(m.n_cap_pad);
+  unsigned char* tail = s.scratch + (size_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R);
+  s.mbar = (uint64_t*)tail;
+  s.red_f = (double*)(tail + 16);
+  s.red_c = (int*)(tail + 16 + 32 * sizeof(double));
+  return s;
+}
+
+// ------------------------------------------------------------------ objective and vols
+template <class R, int MODEL, int FORMULA>
+__global__ void objective_kernel(DevMarket m, const double* __restrict__ X, long long n, double* __restrict__ f,
+                                 double* __restrict__ vols) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  CtaSmem cs = carve<R>(smem, m, W);
+  if (!stage_to_smem(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.mbar, m.err)) return;
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
+  const int n_instr = m.n_cap + m.n_swp;
+  for (long long i = (long long)blockIdx.x * W + warp; i < n; i += (long long)gridDim.x * W) {
+    if (lane < kMaxParam) ws.xs[lane] = lane < m.n_param ? (R)X[i * m.n_param + lane] : R(0);
+    __syncwarp();
+    const double fi = warp_objective<R, MODEL, FORMULA>(m, capB, ws, lane, vols ? vols + i * n_instr : nullptr);
+    if (f && lane == 0) f[i] = fi;
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ simulated annealing
+struct SAState {
+  double* xs;        // [P]  level start point
+  double* fs;        // [1]
+  double* T0;        // [1]
+  double* xe;        // [C x P] chain end points of the current level
+  double* fe;        // [C]
+  double* xb;        // [C x P] chain best-ever points
+  double* fb;        // [C]
+  double* part_f;    // [gridDim] CTA minima
+  int* part_c;
+  unsigned int* counter;
+  double* trace_f;   // [L]
+  uint8_t* bits;     // [C x L x N] or null
+  double* best_x;    // [P]
+  double* best_f;    // [1]
+};
+
+struct SAParams {
+  int C, L, N, P;
+  double cooling, step_frac, step_floor, T0_opt;
+  unsigned long long seed, market_index;
+  const double* x0;  // device [P]
+};
+
+template <class R, int MODEL, int FORMULA>
+__global__ void sa_start_kernel(DevMarket m, SAState st, SAParams sp) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  CtaSmem cs = carve<R>(smem, m, 1);
+  if (!stage_to_smem(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.mbar, m.err)) return;
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch, m.NP, m.n_fwd);
+  if (lane < kMaxParam) ws.xs[lane] = lane < sp.P ? (R)sp.x0[lane] : R(0);
+  __syncwarp();
+  const double f0 = warp_objective<R, MODEL, FORMULA>(m, capB, ws, lane, nullptr);
+  if (lane < sp.P) st.xs[lane] = sp.x0[lane];
+  if (lane == 0) {
+    st.fs[0] = f0;
+    st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
+    st.counter[0] = 0u;
+  }
+}
+
+__device__ __forceinline__ bool lex_less(double fa, int ca, double fb, int cb) {
+  return fa < fb || (fa == fb && ca < cb);
+}
+
+template <class R, int MODEL, int FORMULA>
+__global__ void __launch_bounds__(512) sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  CtaSmem cs = carve<R>(smem, m, W);
+  if (!stage_to_smem(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.mbar, m.err)) return;
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
+
+  const int c = blockIdx.x * W + warp;
+  const bool active = c < sp.C;
+  const int P = sp.P;
+  const double T0 = st.T0[0];
+  double T = T0;
+  for (int j = 0; j < level; ++j) T = T * sp.cooling;   // T_l = T0 cooling^l, as repeated products
+  const double sf = fmax(sp.step_frac * sqrt(T / T0), sp.step_floor);
+
+  double f = st.fs[0];
+  double x = 0.0, lo = 0.0, hi = 0.0, xbk = 0.0;
+  bool freek = false;
+  if (lane < P) {
+    x = st.xs[lane];
+    lo = m.lo[lane];
+    hi = m.hi[lane];
+    freek = m.freem[lane] != 0;
+  }
+  double fbest = f;
+  if (active) {
+    if (level > 0) {
+      fbest = st.fb[c];
+      if (lane < P) xbk = st.xb[(size_t)c * P + lane];
+    } else {
+      xbk = x;
+    }
+    const unsigned long long cw = (unsigned long long)c | (sp.market_index << 32);
+    for (int s = 0; s < sp.N; ++s) {
+      // S1: the step's uniforms (block b on lane b), then slot k's word to lane k
+      const U4 o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)s, (uint64_t)level, cw, sp.seed, 0ull);
+      const int src = (lane >> 2) & 3;
+      const uint64_t w0 = __shfl_sync(0xffffffffu, o.v[0], src);
+      const uint64_t w1 = __shfl_sync(0xffffffffu, o.v[1], src);
+      const uint64_t w2 = __shfl_sync(0xffffffffu, o.v[2], src);
+      const uint64_t w3 = __shfl_sync(0xffffffffu, o.v[3], src);
+      const int wsel = lane & 3;
+      const uint64_t word = wsel == 0 ? w0 : (wsel == 1 ? w1 : (wsel == 2 ? w2 : w3));
+      const double u = u53(word);
+      double y = x;
+      if (lane < P && freek) {
+        // x + sf (hi - lo)(2u - 1), reflected once, clamped; no contraction (same rounding as
+        // the plain sequence of products and sums)
+        double v = __dadd_rn(x, __dmul_rn(__dmul_rn(sf, __dsub_rn(hi, lo)), __dsub_rn(__dmul_rn(2.0, u), 1.0)));
+        if (v < lo) v = __dsub_rn(__dmul_rn(2.0, lo), v);
+        if (v > hi) v = __dsub_rn(__dmul_rn(2.0, hi), v);
+        if (v < lo) v = lo;
+        if (v > hi) v = hi;
+        y = v;
+      }
+      if (lane < kMaxParam) ws.xs[lane] = lane < P ? (R)y : R(0);
+      const double uacc = __shfl_sync(0xffffffffu, u, P);
+      __syncwarp();
+      double fy = warp_objective<R, MODEL, FORMULA>(m, capB, ws, lane, nullptr);
+      if (fy != fy) fy = __longlong_as_double(0x7ff0000000000000LL);
+      // S8: Metropolis in FP64 (warp-uniform: every lane holds the same f, fy, uacc)
+      const bool acc = (fy < f) || (uacc < exp(-(fy - f) / T));
+      if (acc) {
+        x = y;
+        f = fy;
+        if (f < fbest) { fbest = f; xbk = x; }
+      }
+      if (st.bits && lane == 0) st.bits[((size_t)c * sp.L + level) * sp.N + s] = acc ? 1 : 0;
+    }
+    if (lane < P) {
+      st.xe[(size_t)c * P + lane] = x;
+      st.xb[(size_t)c * P + lane] = xbk;
+    }
+    if (lane == 0) {
+      st.fe[c] = f;
+      st.fb[c] = fbest;
+    }
+    __threadfence();
+  }
+  // CTA minimum over its chains' end points, lexicographic in (f, chain)
+  if (lane == 0) {
+    cs.red_f[warp] = active ? f : __longlong_as_double(0x7ff0000000000000LL);
+    cs.red_c[warp] = active ? c : 0x7fffffff;
+  }
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    double bf = cs.red_f[0];
+    int bc = cs.red_c[0];
+    for (int w = 1; w < W; ++w)
+      if (lex_less(cs.red_f[w], cs.red_c[w], bf, bc)) { bf = cs.red_f[w]; bc = cs.red_c[w]; }
+    st.part_f[blockIdx.x] = bf;
+    st.part_c[blockIdx.x] = bc;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(st.counter, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  // the last CTA to finish: minimum over all CTAs, the next start point, the level trace
+  double bf = __longlong_as_double(0x7ff0000000000000LL);
+  int bc = 0x7fffffff;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double pf = __ldcg(st.part_f + b);
+    const int pc = __ldcg(st.part_c + b);
+    if (lex_less(pf, pc, bf, bc)) { bf = pf; bc = pc; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double of = __shfl_xor_sync(0xffffffffu, bf, off);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+    if (lex_less(of, oc, bf, bc)) { bf = of; bc = oc; }
+  }
+  __syncthreads();
+  if (lane == 0) { cs.red_f[warp] = bf; cs.red_c[warp] = bc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < W; ++w)
+      if (lex_less(cs.red_f[w], cs.red_c[w], cs.red_f[0], cs.red_c[0])) { cs.red_f[0] = cs.red_f[w]; cs.red_c[0] = cs.red_c[w]; }
+    st.fs[0] = cs.red_f[0];
+    st.trace_f[level] = cs.red_f[0];
+    cs.red_c[0] = cs.red_c[0];
+  }
+  __syncthreads();
+  const int cbest = cs.red_c[0];
+  if (threadIdx.x < P) st.xs[threadIdx.x] = __ldcg(st.xe + (size_t)cbest * P + threadIdx.x);
+  if (threadIdx.x == 0) st.counter[0] = 0u;
+}
+
+// The best point ever accepted, over all chains (ties to the lowest chain index).
+__global__ void sa_final_kernel(SAState st, int C, int P) {
+  __shared__ double sf[32];
+  __shared__ int sc[32];
+  double bf = __longlong_as_double(0x7ff0000000000000LL);
+  int bc = 0x7fffffff;
+  for (int c = threadIdx.x; c < C; c += blockDim.x)
+    if (lex_less(st.fb[c], c, bf, bc)) { bf = st.fb[c]; bc = c; }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double of = __shfl_xor_sync(0xffffffffu, bf, off);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+    if (lex_less(of, oc, bf, bc)) { bf = of; bc = oc; }
+  }
+  if (lane == 0) { sf[warp] = bf; sc[warp] = bc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (lex_less(sf[w], sc[w], sf[0], sc[0])) { sf[0] = sf[w]; sc[0] = sc[w]; }
+    st.best_f[0] = sf[0];
+  }
+  __syncthreads();
+  if (threadIdx.x < P) st.best_x[threadIdx.x] = st.xb[(size_t)sc[0] * P + threadIdx.x];
+}
+
+// RMSE (vol points) of model vols against market vols for one point per market.
+__global__ void rmse_from_vols_kernel(const double* vols, const double* cap_vol, const double* swp_vol, int n_cap,
+                                      int n_swp, double* out) {
+  __shared__ double part[32];
+  double s = 0.0;
+  const int n = n_cap + n_swp;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double mk = k < n_cap ? cap_vol[k] : swp_vol[k - n_cap];
+    const double e = vols[k] - mk;
+    s += e * e;
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    out[0] = 100.0 * sqrt(t / (double)n);
+  }
+}
+
+}  // namespace sabr

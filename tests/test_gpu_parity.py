@@ -1,0 +1,169 @@
+"""GPU-vs-oracle parity through the C-ABI (run on a B300: pytest -m gpu).
+
+FP64: objective <= 1e-12 relative at points away from the optimum, model vols <= 1e-13 relative,
+and the annealer's accept/reject trajectories identical on the same Philox stream.
+FP32: per-price error stated in vol points, objective compared as an RMS-equivalent.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_01470_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _markets(skel):
+    """The same quotes for both sides: oracle model vols at the generating point plus noise."""
+    import paper_2408_01470_b300 as lib
+    om, vols = oracle.quoted_market(skel)
+    gm = lib.Market(skel, vols)
+    return om, gm, vols
+
+
+def _ragged_caplets():
+    sk = synth.caplet_term_structure(n_fwd=7, n_strikes=5)   # 35 caplets: one full warp + a tail of 3
+    return sk
+
+
+def _single_caplet():
+    sk = synth.caplet_term_structure(n_fwd=3, n_strikes=1)
+    keep = np.array([2])
+    return sk.replace(cap_fwd=sk.cap_fwd[keep], cap_K=sk.cap_K[keep], noise=sk.noise[keep])
+
+
+CASES = {
+    "smile_2y": lambda: synth.smile_2y(),
+    "smile_2y_paper": lambda: synth.smile_2y(formula=synth.FORMULA_PAPER),
+    "caplets_20x15": lambda: synth.caplet_term_structure(),
+    "caplets_20x15_paper": lambda: synth.caplet_term_structure(formula=synth.FORMULA_PAPER),
+    "caplets_7x5_ragged": _ragged_caplets,
+    "one_caplet": _single_caplet,
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_objective_fp64_matches_oracle(gpu_lib, name):
+    sk = CASES[name]()
+    om, gm, _ = _markets(sk)
+    X = synth.uniform_in_box(sk, 200, seed=7)
+    X = np.vstack([X, sk.theta_true[None, :], sk.box_centre()[None, :]])
+    f_gpu = gm.objective(X, "fp64").cpu().numpy()
+    f_orc = om.objective_batch(X)
+    fin = np.isfinite(f_orc)
+    assert np.array_equal(fin, np.isfinite(f_gpu)), "feasibility must agree"
+    # points far from the optimum: 1e-12 relative.  The generating point (row -2, residuals at
+    # the noise level, where rounding of the prices is amplified by P / (P - P_mkt)) is judged by
+    # its RMS error in vol units: 1e-9 vol points.
+    far = fin.copy()
+    far[-2] = False
+    rel = np.abs(f_gpu[far] - f_orc[far]) / np.abs(f_orc[far])
+    assert np.max(rel) <= 1e-12, np.max(rel)
+    if fin[-2]:
+        n = sk.n_instr
+        assert abs(math.sqrt(f_gpu[-2] / n) - math.sqrt(f_orc[-2] / n)) * 100 <= 1e-9
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_model_vols_fp64_match_oracle(gpu_lib, name):
+    sk = CASES[name]()
+    om, gm, _ = _markets(sk)
+    X = synth.uniform_in_box(sk, 50, seed=8)
+    v_gpu = gm.model_vols(X, "fp64").cpu().numpy()
+    for i in range(X.shape[0]):
+        v_orc = om.model_vols(X[i])
+        ok = np.isfinite(v_orc) & (v_orc > 0)
+        assert np.array_equal(ok, np.isfinite(v_gpu[i]))
+        assert np.max(np.abs(v_gpu[i][ok] - v_orc[ok]) / v_orc[ok]) <= 1e-13
+
+
+@pytest.mark.parametrize("name", ["smile_2y", "caplets_20x15", "caplets_7x5_ragged"])
+def test_model_vols_fp32_error_bound(gpu_lib, name):
+    # FP32 pricing: per-quote vol error bounded by 2e-4 vol points (2e-6 in vol units)
+    sk = CASES[name]()
+    om, gm, _ = _markets(sk)
+    X = np.vstack([synth.uniform_in_box(sk, 50, seed=9), sk.theta_true[None, :]])
+    v32 = gm.model_vols(X, "fp32").cpu().numpy()
+    for i in range(X.shape[0]):
+        v_orc = om.model_vols(X[i])
+        ok = np.isfinite(v_orc) & (v_orc > 0) & np.isfinite(v32[i])
+        assert np.max(np.abs(v32[i][ok] - v_orc[ok])) * 100.0 <= 2e-4
+
+
+@pytest.mark.parametrize("name", ["smile_2y", "caplets_20x15"])
+def test_objective_fp32_rms_equivalent(gpu_lib, name):
+    # sqrt(f / n) is an RMS vol error; FP32 pricing moves it by at most 1e-4 vol points
+    sk = CASES[name]()
+    om, gm, _ = _markets(sk)
+    X = np.vstack([synth.uniform_in_box(sk, 100, seed=10), sk.theta_true[None, :]])
+    f32 = gm.objective(X, "fp32").cpu().numpy()
+    f64 = om.objective_batch(X)
+    fin = np.isfinite(f64) & np.isfinite(f32)
+    n = sk.n_instr
+    d = np.abs(np.sqrt(f32[fin] / n) - np.sqrt(f64[fin] / n)) * 100.0
+    assert np.max(d) <= 1e-4, np.max(d)
+
+
+def _anneal_both(sk, C, L, N, cool, seed, prec="fp64"):
+    om, gm, _ = _markets(sk)
+    r_o = om.anneal(C, L, N, cool, seed=seed, want_bits=True, want_chains=True, n_threads=8)
+    r_g = gm.anneal(C, L, N, cool, seed=seed, prec=prec, record_accepts=True)
+    return om, gm, r_o, r_g
+
+
+def test_anneal_fp64_trajectory_identical_smile_full_schedule(gpu_lib):
+    # the single-smile workload at its full schedule: 64 chains x 100 temperatures x 50 steps
+    sk = synth.smile_2y()
+    om, gm, r_o, r_g = _anneal_both(sk, 64, 100, 50, 0.9, seed=240801470)
+    assert r_g["n_evals"] == r_o["n_evals"] == 64 * (100 * 50 + 1)
+    assert r_g["T0"] == pytest.approx(r_o["T0"], rel=1e-12)
+    diff = np.argwhere(r_g["bits"] != r_o["bits"])
+    assert diff.size == 0, f"first differing (chain, level, step): {diff[:1]}"
+    assert np.allclose(r_g["trace_f"][0], r_o["trace_f"], rtol=1e-11, atol=0)
+    assert np.allclose(r_g["x_best"][0], r_o["x_best"], rtol=1e-12, atol=1e-15)
+    assert r_g["f_best"][0] == pytest.approx(r_o["f_best"], rel=1e-11)
+
+
+def test_anneal_fp64_trajectory_identical_caplets(gpu_lib):
+    sk = synth.caplet_term_structure()
+    om, gm, r_o, r_g = _anneal_both(sk, 48, 4, 8, 0.95, seed=3)
+    diff = np.argwhere(r_g["bits"] != r_o["bits"])
+    assert diff.size == 0, f"first differing (chain, level, step): {diff[:1]}"
+    assert np.allclose(r_g["trace_f"][0], r_o["trace_f"], rtol=1e-11, atol=0)
+    assert np.allclose(r_g["x_best"][0], r_o["x_best"], rtol=1e-12, atol=1e-15)
+
+
+def test_anneal_ragged_chain_count_and_graph_replay(gpu_lib):
+    # 37 chains (not a multiple of the CTA's warps), graph capture on, same trajectories
+    sk = synth.smile_2y()
+    om, gm, _ = _markets(sk)
+    r_o = om.anneal(37, 6, 7, 0.8, seed=5, want_bits=True)
+    import torch
+    s = torch.cuda.Stream()
+    plan = gm.anneal_prepare(37, 6, 7, 0.8, seed=5, use_graph=True, stream=s)
+    for _ in range(2):   # replaying the graph twice gives the same search
+        plan.launch(stream=s)
+        r = plan.fetch()
+        assert np.allclose(r["trace_f"][0], r_o["trace_f"], rtol=1e-11)
+        assert np.allclose(r["x_best"][0], r_o["x_best"], rtol=1e-12, atol=1e-15)
+
+
+def test_anneal_fp32_reaches_fp64_quality(gpu_lib):
+    sk = synth.smile_2y()
+    om, gm, _ = _markets(sk)
+    r64 = gm.anneal(64, 100, 50, 0.9, seed=11, prec="fp64")
+    r32 = gm.anneal(64, 100, 50, 0.9, seed=11, prec="fp32")
+    # same search up to FP32 rounding: the final RMSEs agree to 1% of the FP64 value
+    assert r32["rmse_volpt"][0] == pytest.approx(r64["rmse_volpt"][0], rel=1e-2)
+    assert math.isfinite(r32["f_best"][0])
+
+
+def test_load_market_rejects_bad_input(gpu_lib):
+    import paper_2408_01470_b300 as lib
+    sk = synth.smile_2y()
+    bad = sk.replace(cap_K=-sk.cap_K)
+    with pytest.raises(lib.SabrLmmError) as e:
+        lib.Market(bad, np.full(sk.n_cap, 0.2))
+    assert e.value.status == 1 and "cap_K" in str(e.value)

@@ -21,6 +21,13 @@ mp.mp.dps = 50
 # ------------------------------------------------------------------ quadrature nodes
 def test_gauss_legendre_matches_numpy_and_is_exact_to_degree_15():
     x, w = oracle.gl_nodes(8)
+    mp.mp.dps = 40
+    for i in range(8):
+        z = mp.findroot(lambda t: mp.legendre(8, t), mp.mpf(x[i]))
+        dp = 8 * (z * mp.legendre(8, z) - mp.legendre(7, z)) / (z * z - 1)
+        assert abs(x[i] - float(z)) <= 1.2e-16 * abs(float(z))
+        assert abs(w[i] - float(2 / ((1 - z * z) * dp * dp))) <= 1.5e-16 * w[i]
+    mp.mp.dps = 50
     xr, wr = np.polynomial.legendre.leggauss(8)
     assert np.max(np.abs(x - xr)) < 1e-15
     assert np.max(np.abs(w - wr)) < 1e-15
