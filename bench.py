@@ -189,6 +189,25 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile(args):
+    """One search of the bench workload (levels shortened with --levels), for ncu captures."""
+    import torch
+    import paper_2408_01470_b300 as lib
+    from paper_2408_01470_b300 import synth
+    lib.load()
+    skel = synth.caplet_term_structure()
+    gm, _ = market_from_library(lib, skel)
+    L = args.levels or skel.n_levels
+    s = torch.cuda.Stream()
+    plan = gm.anneal_prepare(skel.n_chains, L, skel.steps, skel.cooling, 240801470, prec=args.prec,
+                             use_graph=False, stream=s, warps_per_block=args.warps_per_block)
+    for _ in range(2):
+        plan.launch(stream=s)
+        r = plan.fetch()
+    print(json.dumps({"profile": True, "levels": L, "prec": args.prec, "f_best": float(r["f_best"][0]),
+                      "seconds": r["seconds"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,9 +219,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--warps-per-block", type=int, default=0)
+    ap.add_argument("--profile", action="store_true",
+                    help="run the workload's search once (optionally shortened) and exit: the ncu target")
+    ap.add_argument("--levels", type=int, default=0, help="with --profile: temperature levels (0 = workload's)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
 
     ws, rank, local = dist_setup()
     import torch

@@ -255,11 +255,11 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
       q64.o[q] = oq; q64.w[q] = 0.5 * D * kGLw[q];
       for (int r = 0; r < kQ; ++r) {
         q64.o2[q * kQ + r] = oq + hq * (1.0 + kGLx[r]);
-        q64.w2[q * kQ + r] = hq * kGLw[r];
+        q64.sw2[q * kQ + r] = std::sqrt(hq * kGLw[r]);
       }
     }
     for (int i = 0; i < kQ; ++i) { q32.o[i] = (float)q64.o[i]; q32.w[i] = (float)q64.w[i]; }
-    for (int i = 0; i < kQ * kQ; ++i) { q32.o2[i] = (float)q64.o2[i]; q32.w2[i] = (float)q64.w2[i]; }
+    for (int i = 0; i < kQ * kQ; ++i) { q32.o2[i] = (float)q64.o2[i]; q32.sw2[i] = (float)q64.sw2[i]; }
     put(o.q64, &q64, sizeof q64);
     put(o.q32, &q32, sizeof q32);
   }

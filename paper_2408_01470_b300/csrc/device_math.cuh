@@ -102,9 +102,29 @@ __device__ __forceinline__ R sabr_paper(R alpha, R rho, R nu, R l, R fo, R omb) 
 }
 
 // ------------------------------------------------------------------ Black
-template <class R>
-__device__ __forceinline__ R ncdf(R x) {
-  return R(0.5) * Num<R>::erfc_(-x * R(0.70710678118654752440));
+// Phi(x) = erfc(-x / sqrt 2) / 2.  FP64: the library erfc.  FP32: erfc(y) for y = |x|/sqrt 2 in
+// the Chebyshev-exponent form t exp(-y^2 + P(t)), t = 1 / (1 + y/2), of Press et al. (Numerical
+// Recipes, 2nd ed., Section 6.2), with our own coefficients fitted against 40-digit values
+// (csrc/gen_erfc_fit.py; relative error of erfc <= 5.4e-8 on [0, 12] before FP32 rounding).
+template <class R> __device__ __forceinline__ R ncdf(R x);
+template <> __device__ __forceinline__ double ncdf<double>(double x) {
+  return 0.5 * erfc(-x * 0.70710678118654752440);
+}
+template <> __device__ __forceinline__ float ncdf<float>(float x) {
+  const float y = fabsf(x) * 0.70710678f;
+  const float t = __fdividef(1.0f, fmaf(0.5f, y, 1.0f));
+  float p = +1.539733566e-01f;
+  p = fmaf(p, t, -7.302618493e-01f);
+  p = fmaf(p, t, +1.273531464e+00f);
+  p = fmaf(p, t, -8.523480751e-01f);
+  p = fmaf(p, t, +4.935479974e-02f);
+  p = fmaf(p, t, -6.786663929e-02f);
+  p = fmaf(p, t, +5.818804080e-02f);
+  p = fmaf(p, t, +3.816971254e-01f);
+  p = fmaf(p, t, +9.992080434e-01f);
+  p = fmaf(p, t, -1.265476212e+00f);
+  const float half_erfc = 0.5f * t * __expf(fmaf(-y, y, p));
+  return x < 0.0f ? half_erfc : 1.0f - half_erfc;
 }
 
 // Out-of-the-money Black price with sgn = +1 (call, K >= F) or -1 (put, K < F):

@@ -43,23 +43,27 @@ __global__ void setup_swaps_kernel(DevMarket m) {
   m.swap_TE[s] = m.T[a];
 }
 
-// Pricing constants of one instrument (see sabr_hagan / sabr_paper / black_otm).
+// Pricing constants of one instrument, into the three 4-vector groups of its block.
 template <class R>
 __device__ void put_instr(void* blk, int npad, int k, double l, double fk, double inv_den, double c1, double c2,
                           double c3, double sqrtT, double DF, double KF, double sgn, double pm, double sw, int idx) {
-  R* p = (R*)blk;
-  p[k] = (R)l; p[npad + k] = (R)fk; p[2 * npad + k] = (R)inv_den; p[3 * npad + k] = (R)c1;
-  p[4 * npad + k] = (R)c2; p[5 * npad + k] = (R)c3; p[6 * npad + k] = (R)sqrtT; p[7 * npad + k] = (R)DF;
-  p[8 * npad + k] = (R)KF; p[9 * npad + k] = (R)sgn; p[10 * npad + k] = (R)pm; p[11 * npad + k] = (R)sw;
-  ((int*)(p + 12 * npad))[k] = idx;
+  Q4<R>* p = (Q4<R>*)blk;
+  Q4<R> v0, v1, v2;
+  v0.a = (R)l; v0.b = (R)fk; v0.c = (R)inv_den; v0.d = (R)c1;
+  v1.a = (R)c2; v1.b = (R)c3; v1.c = (R)sqrtT; v1.d = (R)DF;
+  v2.a = (R)KF; v2.b = (R)sgn; v2.c = (R)pm; v2.d = (R)sw;
+  p[k] = v0;
+  p[npad + k] = v1;
+  p[2 * npad + k] = v2;
+  ((int*)(p + 3 * npad))[k] = idx;
 }
 
 __device__ void instr_constants(const DevMarket& m, double F, double K, double T, double D, double vol, const double* wu,
                                 int k, double* pm_out, double* w_out, void* b64, void* b32, int npad, int idx) {
   const double omb = 1.0 - m.beta;
   const double l = log(F / K);
-  const double fk = (m.formula == 0) ? pow(F * K, 0.5 * omb) : pow(F, omb);
   const double fkh = pow(F * K, 0.5 * omb);
+  const double fk = (m.formula == 0) ? fkh * l : pow(F, omb);   // Hagan: (FK)^{(1-b)/2} l; paper: F^{1-b}
   const double den = fkh * (1.0 + omb * omb * l * l / 24.0 + omb * omb * omb * omb * l * l * l * l / 1920.0);
   const double c1 = omb * omb * T / (24.0 * fkh * fkh);
   const double c2 = m.beta * T / (4.0 * fkh);
@@ -97,11 +101,22 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 
 constexpr long long kWaitLimit = 1LL << 24;
 
-// Stage `bytes` (multiple of 16, 16-byte aligned both sides) from global memory into shared
-// memory with the bulk-copy engine, completion tracked by an mbarrier.  Called by every thread
-// of the CTA.  Returns false (and raises the error word) if the bounded wait gave up.
-__device__ bool stage_to_smem(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* mbar, int* err) {
-  if (bytes == 0) return true;
+// Stage two regions (sizes multiples of 16, 16-byte aligned both sides) from global memory into
+// shared memory with the bulk-copy engine, completion tracked by one mbarrier.  Called by every
+// thread of the CTA.  Returns false (and raises the error word) if the bounded wait gave up.
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t bytes, uint32_t bar) {
+  const uint32_t chunk = 32768;
+  for (uint32_t off = 0; off < bytes; off += chunk) {
+    const uint32_t nb = (bytes - off < chunk) ? (bytes - off) : chunk;
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32((char*)sdst + off)), "l"((const char*)gsrc + off), "r"(nb), "r"(bar)
+                 : "memory");
+  }
+}
+
+__device__ bool stage_to_smem2(void* sdst, const void* gsrc, uint32_t bytes, void* sdst2, const void* gsrc2,
+                               uint32_t bytes2, uint64_t* mbar, int* err) {
+  if (bytes + bytes2 == 0) return true;
   const uint32_t bar = smem_u32(mbar);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -109,14 +124,9 @@ __device__ bool stage_to_smem(void* sdst, const void* gsrc, uint32_t bytes, uint
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    const uint32_t chunk = 32768;
-    for (uint32_t off = 0; off < bytes; off += chunk) {
-      const uint32_t nb = (bytes - off < chunk) ? (bytes - off) : chunk;
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                   ::"r"(smem_u32((char*)sdst + off)), "l"((const char*)gsrc + off), "r"(nb), "r"(bar)
-                   : "memory");
-    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes + bytes2) : "memory");
+    bulk_g2s(sdst, gsrc, bytes, bar);
+    bulk_g2s(sdst2, gsrc2, bytes2, bar);
   }
   uint32_t done = 0;
   long long it = 0;
@@ -144,14 +154,22 @@ template <class R> __device__ __forceinline__ const void* cap_block(const DevMar
 template <> __device__ __forceinline__ const void* cap_block<double>(const DevMarket& m) { return m.cblk64; }
 template <> __device__ __forceinline__ const void* cap_block<float>(const DevMarket& m) { return m.cblk32; }
 
-// Shared-memory plan: [caplet block][warp scratch x W][mbarrier (16 B), 32 doubles, 32 ints]
+template <class R> __device__ __forceinline__ const void* quad_block(const DevMarket& m);
+template <> __device__ __forceinline__ const void* quad_block<double>(const DevMarket& m) { return m.q64; }
+template <> __device__ __forceinline__ const void* quad_block<float>(const DevMarket& m) { return m.q32; }
+
+// Shared-memory plan: [caplet block][quadrature table][warp scratch x W][mbarrier (16 B),
+// 32 doubles, 32 ints].  Every region starts on a 16-byte boundary.
 template <class R>
 __host__ __device__ inline uint32_t smem_bytes(const DevMarket& m, int W) {
-  return instr_block_bytes<R>(m.n_cap_pad) + (uint32_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R) + 512;
+  return instr_block_bytes<R>(m.n_cap_pad) + (uint32_t)sizeof(QuadTab<R>) +
+         (uint32_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R) + 512;
 }
 
+template <class R>
 struct CtaSmem {
   void* cap;
+  QuadTab<R>* quad;
   unsigned char* scratch;
   uint64_t* mbar;
   double* red_f;
@@ -159,15 +177,23 @@ struct CtaSmem {
 };
 
 template <class R>
-__device__ __forceinline__ CtaSmem carve(unsigned char* smem, const DevMarket& m, int W) {
-  CtaSmem s;
+__device__ __forceinline__ CtaSmem<R> carve(unsigned char* smem, const DevMarket& m, int W) {
+  CtaSmem<R> s;
   s.cap = smem;
-  s.scratch = smem + instr_block_bytes<R>(m.n_cap_pad);
+  s.quad = (QuadTab<R>*)(smem + instr_block_bytes<R>(m.n_cap_pad));
+  s.scratch = (unsigned char*)s.quad + sizeof(QuadTab<R>);
   unsigned char* tail = s.scratch + (size_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R);
   s.mbar = (uint64_t*)tail;
   s.red_f = (double*)(tail + 16);
   s.red_c = (int*)(tail + 16 + 32 * sizeof(double));
   return s;
+}
+
+// Stage the caplet block and the quadrature table (contiguous in shared memory).
+template <class R>
+__device__ __forceinline__ bool stage_market(const CtaSmem<R>& cs, const DevMarket& m) {
+  return stage_to_smem2(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.quad, quad_block<R>(m),
+                        (uint32_t)sizeof(QuadTab<R>), cs.mbar, m.err);
 }
 
 // ------------------------------------------------------------------ objective and vols
@@ -176,16 +202,16 @@ __global__ void objective_kernel(DevMarket m, const double* __restrict__ X, long
                                  double* __restrict__ vols) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  CtaSmem cs = carve<R>(smem, m, W);
-  if (!stage_to_smem(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.mbar, m.err)) return;
+  CtaSmem<R> cs = carve<R>(smem, m, W);
+  if (!stage_market<R>(cs, m)) return;
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
   const int n_instr = m.n_cap + m.n_swp;
   for (long long i = (long long)blockIdx.x * W + warp; i < n; i += (long long)gridDim.x * W) {
     if (lane < kMaxParam) ws.xs[lane] = lane < m.n_param ? (R)X[i * m.n_param + lane] : R(0);
     __syncwarp();
-    const double fi = warp_objective<R, MODEL, FORMULA>(m, capB, ws, lane, vols ? vols + i * n_instr : nullptr);
-    if (f && lane == 0) f[i] = fi;
+    const auto fi = warp_objective<R, MODEL, FORMULA>(m, capB, *cs.quad, ws, lane, vols ? vols + i * n_instr : nullptr);
+    if (f && lane == 0) f[i] = obj_to_double(fi);
     __syncwarp();
   }
 }
@@ -219,14 +245,16 @@ template <class R, int MODEL, int FORMULA>
 __global__ void sa_start_kernel(DevMarket m, SAState st, SAParams sp) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
-  CtaSmem cs = carve<R>(smem, m, 1);
-  if (!stage_to_smem(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.mbar, m.err)) return;
+  CtaSmem<R> cs = carve<R>(smem, m, 1);
+  if (!stage_market<R>(cs, m)) return;
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch, m.NP, m.n_fwd);
-  if (lane < kMaxParam) ws.xs[lane] = lane < sp.P ? (R)sp.x0[lane] : R(0);
+  // the start point in the chain-state precision (FP32 chains start from the rounded point)
+  const double x0 = lane < sp.P ? (double)(R)sp.x0[lane] : 0.0;
+  if (lane < kMaxParam) ws.xs[lane] = (R)x0;
   __syncwarp();
-  const double f0 = warp_objective<R, MODEL, FORMULA>(m, capB, ws, lane, nullptr);
-  if (lane < sp.P) st.xs[lane] = sp.x0[lane];
+  const double f0 = obj_to_double(warp_objective<R, MODEL, FORMULA>(m, capB, *cs.quad, ws, lane, nullptr));
+  if (lane < sp.P) st.xs[lane] = x0;
   if (lane == 0) {
     st.fs[0] = f0;
     st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
@@ -238,12 +266,58 @@ __device__ __forceinline__ bool lex_less(double fa, int ca, double fb, int cb) {
   return fa < fb || (fa == fb && ca < cb);
 }
 
+// S1: the neighbour of slot k (lane k) from its uniform, in the chain-state precision.
+//   FP64: x + sf (hi - lo)(2u - 1) with no contraction (the rounding of the plain sequence of
+//         products and sums), u = (word >> 11) 2^-53, reflected once, clamped.
+//   FP32: the same in FP32 with u = (word >> 40) 2^-24.
+__device__ __forceinline__ double neighbour(double x, double lo, double hi, double sf, uint64_t word) {
+  const double u = u53(word);
+  double v = __dadd_rn(x, __dmul_rn(__dmul_rn(sf, __dsub_rn(hi, lo)), __dsub_rn(__dmul_rn(2.0, u), 1.0)));
+  if (v < lo) v = __dsub_rn(__dmul_rn(2.0, lo), v);
+  if (v > hi) v = __dsub_rn(__dmul_rn(2.0, hi), v);
+  return fmin(fmax(v, lo), hi);
+}
+__device__ __forceinline__ float neighbour(float x, float lo, float hi, float sf, uint64_t word) {
+  const float u = (float)(uint32_t)(word >> 40) * 0x1.0p-24f;
+  float v = x + sf * (hi - lo) * (2.0f * u - 1.0f);
+  if (v < lo) v = 2.0f * lo - v;
+  if (v > hi) v = 2.0f * hi - v;
+  return fminf(fmaxf(v, lo), hi);
+}
+
+// S8: Metropolis test, identical on every lane.
+//   FP64: accept iff fy < f or u < exp(-(fy - f) / T).
+//   FP32: dE from the float-float values; the test runs in FP32 (e = exp(-dE/T)) and is redone in
+//         FP64 whenever u lies within the FP32 error band of e, so the decision equals the FP64
+//         decision on the same objective values.
+__device__ __forceinline__ bool metropolis(double fy, double f, uint64_t word, double T, float) {
+  return (fy < f) || (u53(word) < exp(-(fy - f) / T));
+}
+__device__ __forceinline__ bool metropolis(FF fy, FF f, uint64_t word, double T, float invT) {
+  const float dE = (fy.hi - f.hi) + (fy.lo - f.lo);
+  if (dE < 0.f) return true;
+  const float t = dE * invT;
+  const float e = __expf(-t);
+  const float uf = (float)(uint32_t)(word >> 40) * 0x1.0p-24f;   // uf <= u < uf + 2^-24
+  const float band = 0x1.0p-24f + e * (1e-6f + 4e-7f * fabsf(t));
+  if (fabsf(uf - e) > band) return uf < e;
+  const double dEd = ((double)fy.hi - (double)f.hi) + ((double)fy.lo - (double)f.lo);
+  return u53(word) < exp(-dEd / T);
+}
+
+template <class R>
+__device__ __forceinline__ R box_lo(const DevMarket& m, int k) { return (R)m.lo[k]; }
+template <class R>
+__device__ __forceinline__ R box_hi(const DevMarket& m, int k) { return (R)m.hi[k]; }
+
 template <class R, int MODEL, int FORMULA>
-__global__ void __launch_bounds__(512) sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
+__global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 4))
+sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
+  typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  CtaSmem cs = carve<R>(smem, m, W);
-  if (!stage_to_smem(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.mbar, m.err)) return;
+  CtaSmem<R> cs = carve<R>(smem, m, W);
+  if (!stage_market<R>(cs, m)) return;
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
 
@@ -254,74 +328,69 @@ __global__ void __launch_bounds__(512) sa_level_kernel(DevMarket m, SAState st, 
   double T = T0;
   for (int j = 0; j < level; ++j) T = T * sp.cooling;   // T_l = T0 cooling^l, as repeated products
   const double sf = fmax(sp.step_frac * sqrt(T / T0), sp.step_floor);
+  const float invT = (float)(1.0 / T);
 
-  double f = st.fs[0];
-  double x = 0.0, lo = 0.0, hi = 0.0, xbk = 0.0;
+  O f;
+  obj_from_double(st.fs[0], f);
+  R x = 0, lo = 0, hi = 0, xbk = 0;
   bool freek = false;
   if (lane < P) {
-    x = st.xs[lane];
-    lo = m.lo[lane];
-    hi = m.hi[lane];
+    x = (R)st.xs[lane];
+    lo = box_lo<R>(m, lane);
+    hi = box_hi<R>(m, lane);
     freek = m.freem[lane] != 0;
   }
-  double fbest = f;
+  O fbest = f;
   if (active) {
     if (level > 0) {
-      fbest = st.fb[c];
-      if (lane < P) xbk = st.xb[(size_t)c * P + lane];
+      obj_from_double(st.fb[c], fbest);
+      if (lane < P) xbk = (R)st.xb[(size_t)c * P + lane];
     } else {
       xbk = x;
     }
     const unsigned long long cw = (unsigned long long)c | (sp.market_index << 32);
+    const int wsel = lane & 3;
+    U4 o;   // Philox block (lane & 3) of step s0 + (lane >> 2), for 8 steps at a time
     for (int s = 0; s < sp.N; ++s) {
-      // S1: the step's uniforms (block b on lane b), then slot k's word to lane k
-      const U4 o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)s, (uint64_t)level, cw, sp.seed, 0ull);
-      const int src = (lane >> 2) & 3;
-      const uint64_t w0 = __shfl_sync(0xffffffffu, o.v[0], src);
-      const uint64_t w1 = __shfl_sync(0xffffffffu, o.v[1], src);
-      const uint64_t w2 = __shfl_sync(0xffffffffu, o.v[2], src);
-      const uint64_t w3 = __shfl_sync(0xffffffffu, o.v[3], src);
-      const int wsel = lane & 3;
-      const uint64_t word = wsel == 0 ? w0 : (wsel == 1 ? w1 : (wsel == 2 ? w2 : w3));
-      const double u = u53(word);
-      double y = x;
-      if (lane < P && freek) {
-        // x + sf (hi - lo)(2u - 1), reflected once, clamped; no contraction (same rounding as
-        // the plain sequence of products and sums)
-        double v = __dadd_rn(x, __dmul_rn(__dmul_rn(sf, __dsub_rn(hi, lo)), __dsub_rn(__dmul_rn(2.0, u), 1.0)));
-        if (v < lo) v = __dsub_rn(__dmul_rn(2.0, lo), v);
-        if (v > hi) v = __dsub_rn(__dmul_rn(2.0, hi), v);
-        if (v < lo) v = lo;
-        if (v > hi) v = hi;
-        y = v;
+      // S1: the step's uniforms; lane k needs word (k & 3) of block (k >> 2) of this step
+      if ((s & 7) == 0) o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)(s + (lane >> 2)), (uint64_t)level, cw, sp.seed, 0ull);
+      uint64_t word;
+      {
+        const int src = ((s & 7) << 2) | ((lane >> 2) & 3);
+        const uint64_t w0 = __shfl_sync(0xffffffffu, o.v[0], src);
+        const uint64_t w1 = __shfl_sync(0xffffffffu, o.v[1], src);
+        const uint64_t w2 = __shfl_sync(0xffffffffu, o.v[2], src);
+        const uint64_t w3 = __shfl_sync(0xffffffffu, o.v[3], src);
+        word = wsel == 0 ? w0 : (wsel == 1 ? w1 : (wsel == 2 ? w2 : w3));
       }
-      if (lane < kMaxParam) ws.xs[lane] = lane < P ? (R)y : R(0);
-      const double uacc = __shfl_sync(0xffffffffu, u, P);
+      R y = x;
+      if (lane < P && freek) y = neighbour(x, lo, hi, (R)sf, word);
+      if (lane < kMaxParam) ws.xs[lane] = lane < P ? y : R(0);
+      const uint64_t wacc = __shfl_sync(0xffffffffu, word, P);
       __syncwarp();
-      double fy = warp_objective<R, MODEL, FORMULA>(m, capB, ws, lane, nullptr);
-      if (fy != fy) fy = __longlong_as_double(0x7ff0000000000000LL);
-      // S8: Metropolis in FP64 (warp-uniform: every lane holds the same f, fy, uacc)
-      const bool acc = (fy < f) || (uacc < exp(-(fy - f) / T));
+      const O fy = warp_objective<R, MODEL, FORMULA>(m, capB, *cs.quad, ws, lane, nullptr);
+      const bool acc = metropolis(fy, f, wacc, T, invT);
       if (acc) {
         x = y;
         f = fy;
-        if (f < fbest) { fbest = f; xbk = x; }
+        if (obj_less(f, fbest)) { fbest = f; xbk = x; }
       }
       if (st.bits && lane == 0) st.bits[((size_t)c * sp.L + level) * sp.N + s] = acc ? 1 : 0;
     }
     if (lane < P) {
-      st.xe[(size_t)c * P + lane] = x;
-      st.xb[(size_t)c * P + lane] = xbk;
+      st.xe[(size_t)c * P + lane] = (double)x;
+      st.xb[(size_t)c * P + lane] = (double)xbk;
     }
     if (lane == 0) {
-      st.fe[c] = f;
-      st.fb[c] = fbest;
+      st.fe[c] = obj_to_double(f);
+      st.fb[c] = obj_to_double(fbest);
     }
     __threadfence();
   }
+  const double fend = active ? obj_to_double(f) : __longlong_as_double(0x7ff0000000000000LL);
   // CTA minimum over its chains' end points, lexicographic in (f, chain)
   if (lane == 0) {
-    cs.red_f[warp] = active ? f : __longlong_as_double(0x7ff0000000000000LL);
+    cs.red_f[warp] = fend;
     cs.red_c[warp] = active ? c : 0x7fffffff;
   }
   __syncthreads();
@@ -361,7 +430,6 @@ __global__ void __launch_bounds__(512) sa_level_kernel(DevMarket m, SAState st, 
       if (lex_less(cs.red_f[w], cs.red_c[w], cs.red_f[0], cs.red_c[0])) { cs.red_f[0] = cs.red_f[w]; cs.red_c[0] = cs.red_c[w]; }
     st.fs[0] = cs.red_f[0];
     st.trace_f[level] = cs.red_f[0];
-    cs.red_c[0] = cs.red_c[0];
   }
   __syncthreads();
   const int cbest = cs.red_c[0];

@@ -15,31 +15,39 @@ namespace sabr {
 
 constexpr int kQ = 8;               // Gauss-Legendre nodes per panel
 constexpr int kMaxParam = 12;       // parameter slots
-constexpr int kBlkArrays = 12;      // R arrays per instrument in a block (+ one int array)
+constexpr int kBlkArrays = 12;      // R values per instrument in a block (+ one int)
 
 // Quadrature table per precision, offsets relative to the start of a panel of width D:
 //   o[q] = (D/2)(1 + xi_q), w[q] = (D/2) w_q             (outer rule on the panel)
-//   o2[q*8+r] = o[q] + h_q (1 + xi_r), w2[q*8+r] = h_q w_r, h_q = (D - o[q]) / 2
+//   o2[q*8+r] = o[q] + h_q (1 + xi_r), sw2[q*8+r] = sqrt(h_q w_r), h_q = (D - o[q]) / 2
 //                                                         (inner rule on [u_q, panel top])
-template <class R> struct QuadTab { R o[kQ]; R w[kQ]; R o2[kQ * kQ]; R w2[kQ * kQ]; };
+template <class R> struct QuadTab { R o[kQ]; R w[kQ]; R o2[kQ * kQ]; R sw2[kQ * kQ]; };
 
-// Pointers into an instrument block of n (padded) instruments.
+template <class R> struct alignas(4 * sizeof(R)) Q4 { R a, b, c, d; };
+
+// An instrument block of n (padded) instruments: three structure-of-arrays groups of 4-vectors
+// (one vector load each per instrument) and the index array.
+//   g0 = {l = log(F/K), fk, inv_den, c1},  g1 = {c2, c3, sqrt(T), D F},  g2 = {K/F, sgn, P_mkt, sqrt(w)}
+// fk is (FK)^{(1-b)/2} l for the Hagan formula and F^{1-b} for Eq. (sigmaHagan).
 template <class R> struct InstrView {
-  const R *l, *fk, *inv_den, *c1, *c2, *c3, *sqrtT, *DF, *KF, *sgn, *pm, *sw;
+  const Q4<R>* g0;
+  const Q4<R>* g1;
+  const Q4<R>* g2;
   const int* idx;
 };
 
 template <class R> __host__ __device__ inline uint32_t instr_block_bytes(int npad) {
-  return (uint32_t)npad * (uint32_t)(kBlkArrays * sizeof(R) + sizeof(int));
+  const uint32_t raw = (uint32_t)npad * (uint32_t)(3 * sizeof(Q4<R>) + sizeof(int));
+  return (raw + 63u) & ~63u;
 }
 
 template <class R> __host__ __device__ inline InstrView<R> instr_view(const void* base, int npad) {
-  const R* p = (const R*)base;
+  const Q4<R>* p = (const Q4<R>*)base;
   InstrView<R> v;
-  v.l = p; v.fk = p + npad; v.inv_den = p + 2 * npad; v.c1 = p + 3 * npad; v.c2 = p + 4 * npad;
-  v.c3 = p + 5 * npad; v.sqrtT = p + 6 * npad; v.DF = p + 7 * npad; v.KF = p + 8 * npad;
-  v.sgn = p + 9 * npad; v.pm = p + 10 * npad; v.sw = p + 11 * npad;
-  v.idx = (const int*)(p + 12 * npad);
+  v.g0 = p;
+  v.g1 = p + npad;
+  v.g2 = p + 2 * npad;
+  v.idx = (const int*)(p + 3 * npad);
   return v;
 }
 

@@ -1,8 +1,9 @@
 // Warp-cooperative evaluation of the calibration objective for one parameter point.
 //
-// One warp owns one parameter point (one annealing chain).  The market's instrument blocks sit
-// in shared memory (staged once per CTA by a bulk copy); each warp has a private scratch region
-// for the per-panel integrals and the per-forward SABR parameters of its point.
+// One warp owns one parameter point (one annealing chain).  The market's instrument blocks and
+// the quadrature table sit in shared memory (staged once per CTA by a bulk copy); each warp has
+// a private scratch region for the per-panel integrals and the per-forward SABR factors of its
+// point.
 //
 //   S2  rebonato_forward_params : Eq. (haganForRebonato) for every caplet forward, by the
 //       composite Gauss-Legendre rule written in time-to-fixing u.  Time homogeneity makes one
@@ -11,82 +12,129 @@
 //         G_i = sum_{p < n_i} Gp[p],   X_i = sum_{p < n_i} (Ap[p] + Gp[p] sum_{p < p' < n_i} Hp[p'])
 //       with Gp = int g^2, Hp = int h^2 over panel p and Ap = int g(u)^2 R(u) over panel p,
 //       R(u) the inner rule on [u, panel top].  (The same discrete sums as a direct rule in
-//       calendar time, reordered.)  Lanes split (panel, node); exponentials factor as
-//       e^{-c(pD + o)} = e^{-c pD} e^{-c o}.
+//       calendar time, reordered.)  Lanes split (panel, node).  With base = pD and a node at
+//       base + o, the exponentials factor as e^{-c(base + o)} = e^{-c base} e^{-c o}, so
+//         g(base + o) = E_g(p) ((a + b base) e_g(o) + b o e_g(o)) + d
+//       and likewise h; the per-node factors e(o), o e(o) (and, for the inner rule, the square
+//       roots of the weights) are tabulated once per evaluation in the warp's scratch.
 //   S4  price_caplets : per caplet, SABR vol -> OTM Black price -> vega-weighted residual.
-//   S7  the squared residuals summed per lane in the pricing precision, across lanes in FP64.
+//   S7  squared residuals summed per lane in the pricing precision; across lanes in FP64 (FP64
+//       path) or in float-float, a 48-bit significand on the FP32 pipes (FP32 path).
 #pragma once
 #include "device_math.cuh"
 #include "market.cuh"
 
 namespace sabr {
 
+template <class R> struct Q2 { R a, b; };
+
+// Per-forward SABR factors consumed by the pricer:
+//   F4 = {alpha, nu / alpha, alpha^2, rho nu alpha},  fA3 = (2 - 3 rho^2) nu^2.
 template <class R> struct WarpScratch {
-  R* xs;   // [16] parameter point in the pricing precision
-  R* Gp;   // [NPc] per-panel integrals
+  R* xs;        // [16] parameter point in the pricing precision
+  R* Gp;        // [NPc] per-panel integrals
   R* Hp;
   R* Ap;
-  R* af;   // [n_fwd] per-forward SABR alpha
-  R* nf;   // [n_fwd] per-forward SABR nu
+  Q4<R>* F4;    // [NFc]
+  R* fA3;       // [NFc]
+  Q2<R>* Ep;    // [NPc] {e^{-c pD}, e^{-gamma_h pD}}
+  Q4<R>* Tq;    // [8]   {e_g(o_q), b o_q e_g(o_q), e_h(o_q), beta_h o_q e_h(o_q)}
+  Q4<R>* T2;    // [8 x 9] inner rule: sqrt(w) {e_h(o2), beta_h o2 e_h(o2), delta_h, 0}
 };
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Elements (of R) of one warp's scratch; a multiple of 4 so that every region stays 16B-aligned.
+// Elements (of R) of one warp's scratch; a multiple of 4 so that every region stays aligned to
+// 4 elements (the alignment of Q4<R>).
 __host__ __device__ inline int warp_scratch_elems(int NP, int n_fwd) {
-  return round_up(16 + 3 * round_up(NP > 0 ? NP : 1, 4) + 2 * round_up(n_fwd, 4), 4);
+  const int NPc = round_up(NP > 0 ? NP : 1, 4), NFc = round_up(n_fwd, 4);
+  return 16 + 3 * NPc + 4 * NFc + NFc + 2 * NPc + 4 * 8 + 4 * 72;
 }
 
 template <class R>
 __device__ __forceinline__ WarpScratch<R> warp_scratch(R* base, int NP, int n_fwd) {
   WarpScratch<R> s;
-  const int NPc = round_up(NP > 0 ? NP : 1, 4);
+  const int NPc = round_up(NP > 0 ? NP : 1, 4), NFc = round_up(n_fwd, 4);
   s.xs = base;
   s.Gp = base + 16;
   s.Hp = s.Gp + NPc;
   s.Ap = s.Hp + NPc;
-  s.af = s.Ap + NPc;
-  s.nf = s.af + round_up(n_fwd, 4);
+  s.F4 = (Q4<R>*)(s.Ap + NPc);
+  s.fA3 = (R*)(s.F4 + NFc);
+  s.Ep = (Q2<R>*)(s.fA3 + NFc);
+  s.Tq = (Q4<R>*)(s.Ep + NPc);
+  s.T2 = s.Tq + 8;
   return s;
 }
 
-template <class R> __device__ __forceinline__ const QuadTab<R>* quad_of(const DevMarket& m);
-template <> __device__ __forceinline__ const QuadTab<double>* quad_of<double>(const DevMarket& m) { return m.q64; }
-template <> __device__ __forceinline__ const QuadTab<float>* quad_of<float>(const DevMarket& m) { return m.q32; }
+// Per-forward factors from (alpha, nu) and the chain's rho.
+template <class R>
+__device__ __forceinline__ void put_forward(const WarpScratch<R>& ws, int i, R al, R nu, R rho) {
+  Q4<R> v;
+  v.a = al;
+  v.b = nu / al;
+  v.c = al * al;
+  v.d = rho * nu * al;
+  ws.F4[i] = v;
+  ws.fA3[i] = (R(2) - R(3) * rho * rho) * nu * nu;
+}
 
 // S2: alpha_i, nu_i of every caplet forward (Rebonato mapping, kappa = 1).
 template <class R>
-__device__ void rebonato_forward_params(const DevMarket& m, const R* th, const WarpScratch<R>& ws, int lane) {
+__device__ void rebonato_forward_params(const DevMarket& m, const QuadTab<R>& qt, const WarpScratch<R>& ws, int lane) {
   typedef Num<R> M;
-  const QuadTab<R>& qt = *quad_of<R>(m);
-  const R a = th[0], b = th[1], c = th[2], d = th[3];
-  const R ah = th[4], bh = th[5], gh = th[6], dh = th[7];
+  const R a = ws.xs[0], b = ws.xs[1], c = ws.xs[2], d = ws.xs[3];
+  const R ah = ws.xs[4], bh = ws.xs[5], gh = ws.xs[6], dh = ws.xs[7];
+  const R rho = ws.xs[8];
   const R D = (R)m.panel;
-  const int q = lane & 7, pg = lane >> 3;
-  const R oq = qt.o[q], wq = qt.w[q];
-  const R eg = M::exp_(-c * oq), eh = M::exp_(-gh * oq);
-  R o2[kQ], w2[kQ], ehs[kQ];
-#pragma unroll
-  for (int r = 0; r < kQ; ++r) {
-    o2[r] = qt.o2[q * kQ + r];
-    w2[r] = qt.w2[q * kQ + r];
-    ehs[r] = M::exp_(-gh * o2[r]);
-  }
   const int NP = m.NP, NPc = round_up(NP, 4);
+  // per-evaluation tables
+  for (int j = lane; j < kQ * kQ; j += 32) {
+    const R o2 = qt.o2[j], sw = qt.sw2[j];
+    const R e = M::exp_(-gh * o2);
+    Q4<R> t;
+    t.a = sw * e;
+    t.b = sw * bh * o2 * e;
+    t.c = sw * dh;
+    t.d = R(0);
+    ws.T2[(j >> 3) * 9 + (j & 7)] = t;
+  }
+  if (lane < kQ) {
+    const R o = qt.o[lane];
+    const R eg = M::exp_(-c * o), eh = M::exp_(-gh * o);
+    Q4<R> t;
+    t.a = eg;
+    t.b = b * o * eg;
+    t.c = eh;
+    t.d = bh * o * eh;
+    ws.Tq[lane] = t;
+  }
+  for (int p = lane; p < NP; p += 32) {
+    const R base = D * (R)p;
+    Q2<R> e;
+    e.a = M::exp_(-c * base);
+    e.b = M::exp_(-gh * base);
+    ws.Ep[p] = e;
+  }
+  __syncwarp();
+  const int q = lane & 7, pg = lane >> 3;
+  const R wq = qt.w[q];
+  const Q4<R> tq = ws.Tq[q];
+  const Q4<R>* t2 = ws.T2 + q * 9;
   for (int p = pg; p < NPc; p += 4) {
     R G = 0, H = 0, A = 0;
     if (p < NP) {
       const R base = D * (R)p;
-      const R Eg = M::exp_(-c * base), Eh = M::exp_(-gh * base);
-      const R u = base + oq;
-      const R g = (a + b * u) * (Eg * eg) + d;
-      const R h = (ah + bh * u) * (Eh * eh) + dh;
+      const Q2<R> E = ws.Ep[p];
+      const R g = E.a * ((a + b * base) * tq.a + tq.b) + d;
+      const R ahp = ah + bh * base;
+      const R h = E.b * (ahp * tq.c + tq.d) + dh;
       R Rin = 0;
 #pragma unroll
       for (int r = 0; r < kQ; ++r) {
-        const R v = base + o2[r];
-        const R hr = (ah + bh * v) * (Eh * ehs[r]) + dh;
-        Rin += w2[r] * hr * hr;
+        const Q4<R> t = t2[r];
+        const R hr = E.b * (ahp * t.a + t.b) + t.c;   // sqrt(w_r) h at the inner node
+        Rin += hr * hr;
       }
       const R gw = wq * g * g;
       G = gw;
@@ -113,35 +161,104 @@ __device__ void rebonato_forward_params(const DevMarket& m, const R* th, const W
       S += ws.Hp[p];
     }
     const R al = M::sqrt_(G / Ti);
-    ws.af[i] = al;
-    ws.nf[i] = M::sqrt_(R(2) * X) / (al * Ti);
+    put_forward<R>(ws, i, al, M::sqrt_(R(2) * X) / (al * Ti), rho);
   }
   __syncwarp();
+}
+
+// z / x(z) with per-chain constants of rho: omr = 1 - r, inv_omr = 1 / (1 - r), omr2 = 1 - r^2
+// for r = rho (z >= 0) and r = -rho (z < 0) (x(z; rho) = -x(-z; -rho)).  With zz = |z| and
+// s = sqrt(1 - 2 r zz + zz^2):  x = log1p(zz Q / ((s + 1)(1 - r))),  Q = s + 1 - 2r + zz,
+// where Q is formed as (s - r) + (1 - r) + zz with s - r = (1 - r^2 + zz (zz - 2r)) / (s + r)
+// when r > 0 (no cancellation of s against r as r -> 1), and directly when r <= 0 (every term
+// non-negative).  Near z = 0 the series 1 - rho z / 2 + (2 - 3 rho^2) z^2 / 12.
+template <class R>
+struct RhoConsts {
+  R rho, omr_p, omr_m, iomr_p, iomr_m, omr2;
+  __device__ __forceinline__ void init(R r) {
+    rho = r;
+    omr_p = R(1) - r;
+    omr_m = R(1) + r;
+    iomr_p = R(1) / omr_p;
+    iomr_m = R(1) / omr_m;
+    omr2 = omr_p * omr_m;
+  }
+};
+
+template <class R> __device__ __forceinline__ R fdiv(R a, R b);
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <class R> __device__ __forceinline__ R fsqrt(R a);
+template <> __device__ __forceinline__ double fsqrt<double>(double a) { return sqrt(a); }
+template <> __device__ __forceinline__ float fsqrt<float>(float a) { return a * rsqrtf(a); }   // a > 0 here
+
+template <class R>
+__device__ __forceinline__ R z_over_x_fast(R z, const RhoConsts<R>& rc) {
+  typedef Num<R> M;
+  const R zz = M::abs_(z);
+  const bool neg = z < R(0);
+  const R r = neg ? -rc.rho : rc.rho;
+  const R omr = neg ? rc.omr_m : rc.omr_p;
+  const R iomr = neg ? rc.iomr_m : rc.iomr_p;
+  const R zq = zz * (zz - R(2) * r);
+  const R s = fsqrt<R>(R(1) + zq);
+  const R smr = fdiv<R>(rc.omr2 + zq, s + r);
+  const R Q = (r > R(0)) ? (smr + omr + zz) : (zz - R(2) * r + s + R(1));
+  const R x = M::log1p_(fdiv<R>(zz * Q, s + R(1)) * iomr);
+  const R series = R(1) - R(0.5) * rc.rho * z + (R(2) - R(3) * rc.rho * rc.rho) * z * z * R(1.0 / 12.0);
+  return (zz < M::zx_series) ? series : fdiv<R>(zz, x);
 }
 
 // S4 + S7 (caplets): lane-strided pricing; returns this lane's partial sum of squared
 // residuals in the pricing precision and clears `ok` on an infeasible vol.  With vols != null
 // the model vols are written instead (NaN where infeasible).
 template <class R, int FORMULA>
-__device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const R* af, const R* nf, R rho,
+__device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const WarpScratch<R>& ws, const RhoConsts<R>& rc,
                                            R omb, int lane, bool& ok, double* vols) {
   typedef Num<R> M;
   R acc = 0;
   for (int k = lane; k < n; k += 32) {
     const int i = B.idx[k];
-    const R al = af[i], nu = nf[i];
-    const R l = B.l[k];
+    const Q4<R> fw = ws.F4[i];
+    const Q4<R> g0 = B.g0[k];   // l, fk, inv_den, c1
+    const Q4<R> g1 = B.g1[k];   // c2, c3, sqrt(T), D F
     R sig;
-    if (FORMULA == 0) sig = sabr_hagan<R>(al, rho, nu, l, B.fk[k], B.inv_den[k], B.c1[k], B.c2[k], B.c3[k]);
-    else sig = sabr_paper<R>(al, rho, nu, l, B.fk[k], omb);
+    if (FORMULA == 0) {
+      const R z = fw.b * g0.b;
+      const R zx = z_over_x_fast<R>(z, rc);
+      const R corr = R(1) + g0.d * fw.c + g1.a * fw.d + g1.b * ws.fA3[i];
+      sig = fw.a * g0.c * zx * corr;
+    } else {
+      sig = sabr_paper<R>(fw.a, rc.rho, fw.b * fw.a, g0.a, g0.b, omb);
+    }
     const bool good = (sig > R(0)) && M::finite_(sig);
     if (vols) { vols[k] = good ? (double)sig : __longlong_as_double(0x7ff8000000000000LL); continue; }
     ok = ok && good;
-    const R p = black_otm<R>(sig, B.sqrtT[k], l, B.DF[k], B.KF[k], B.sgn[k]);
-    const R r = B.sw[k] * (p - B.pm[k]);
+    const Q4<R> g2 = B.g2[k];   // K/F, sgn, P_mkt, sqrt(w)
+    const R v = sig * g1.c;
+    const R d1 = fdiv<R>(g0.a, v) + R(0.5) * v;
+    const R sg = g2.b;
+    const R p = sg * g1.d * (ncdf<R>(sg * d1) - g2.a * ncdf<R>(sg * (d1 - v)));
+    const R r = g2.d * (p - g2.c);
     acc += r * r;
   }
   return acc;
+}
+
+// ------------------------------------------------------------------ objective values
+// FP64 path: a double.  FP32 path: a float-float pair (hi + lo, |lo| <= ulp(hi)/2).
+struct FF { float hi, lo; };
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  // Knuth's two-sum on the high parts, low parts added with the rounding error
+  const float s = a.hi + b.hi;
+  const float bp = s - a.hi;
+  const float e = (a.hi - (s - bp)) + (b.hi - bp);
+  const float lo = e + a.lo + b.lo;
+  FF r;
+  r.hi = s + lo;
+  r.lo = lo - (r.hi - s);
+  return r;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -150,34 +267,59 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+__device__ __forceinline__ FF warp_sum(FF v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    FF o;
+    o.hi = __shfl_xor_sync(0xffffffffu, v.hi, off);
+    o.lo = __shfl_xor_sync(0xffffffffu, v.lo, off);
+    v = ff_add(v, o);
+  }
+  return v;
+}
+
+template <class R> struct ObjOf { typedef double T; };
+template <> struct ObjOf<float> { typedef FF T; };
+
+__device__ __forceinline__ double obj_inf(double) { return __longlong_as_double(0x7ff0000000000000LL); }
+__device__ __forceinline__ FF obj_inf(FF) { FF r; r.hi = __int_as_float(0x7f800000); r.lo = 0.f; return r; }
+__device__ __forceinline__ double obj_lane(double, double p) { return p; }
+__device__ __forceinline__ FF obj_lane(FF, float p) { FF r; r.hi = p; r.lo = 0.f; return r; }
+__device__ __forceinline__ bool obj_finite(double v) { return isfinite(v); }
+__device__ __forceinline__ bool obj_finite(FF v) { return isfinite(v.hi); }
+__device__ __forceinline__ double obj_to_double(double v) { return v; }
+__device__ __forceinline__ double obj_to_double(FF v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ bool obj_less(double a, double b) { return a < b; }
+__device__ __forceinline__ bool obj_less(FF a, FF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ void obj_from_double(double v, double& o) { o = v; }
+__device__ __forceinline__ void obj_from_double(double v, FF& o) {
+  o.hi = (float)v;
+  o.lo = isfinite(v) ? (float)(v - (double)o.hi) : 0.f;
+}
+
 // Objective of the point held in ws.xs (all 32 lanes call; all return the same value).
 // MODEL 0: SABR smile [alpha, rho, nu];  MODEL 1: Rebonato caplets.
 template <class R, int MODEL, int FORMULA>
-__device__ double warp_objective(const DevMarket& m, const InstrView<R>& capB, const WarpScratch<R>& ws,
-                                 int lane, double* vols) {
-  R th[kMaxParam];
-#pragma unroll
-  for (int k = 0; k < kMaxParam; ++k) th[k] = ws.xs[k];
-  R rho;
+__device__ typename ObjOf<R>::T warp_objective(const DevMarket& m, const InstrView<R>& capB, const QuadTab<R>& qt,
+                                               const WarpScratch<R>& ws, int lane, double* vols) {
+  typedef typename ObjOf<R>::T O;
+  RhoConsts<R> rc;
   if (MODEL == 0) {
-    for (int j = lane; j < m.n_capfwd; j += 32) {
-      const int i = m.capfwd_list[j];
-      ws.af[i] = th[0];
-      ws.nf[i] = th[2];
-    }
+    const R al = ws.xs[0], rho = ws.xs[1], nu = ws.xs[2];
+    for (int j = lane; j < m.n_capfwd; j += 32) put_forward<R>(ws, m.capfwd_list[j], al, nu, rho);
     __syncwarp();
-    rho = th[1];
+    rc.init(rho);
   } else {
-    rebonato_forward_params<R>(m, th, ws, lane);
-    rho = th[8];
+    rebonato_forward_params<R>(m, qt, ws, lane);
+    rc.init(ws.xs[8]);
   }
   bool ok = true;
-  const R part = price_caplets<R, FORMULA>(capB, m.n_cap, ws.af, ws.nf, rho, (R)(1.0 - m.beta), lane, ok, vols);
+  const R part = price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);
   __syncwarp();
-  if (vols) return 0.0;
-  const double f = warp_sum((double)part);
+  if (vols) return obj_inf(O());
+  const O f = warp_sum(obj_lane(O(), part));
   const bool bad = __any_sync(0xffffffffu, !ok);
-  if (bad || !isfinite(f)) return __longlong_as_double(0x7ff0000000000000LL);  // +inf
+  if (bad || !obj_finite(f)) return obj_inf(O());
   return f;
 }
 
