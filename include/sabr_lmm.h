@@ -206,6 +206,29 @@ sabr_lmm_status sabr_lmm_anneal_launch(sabr_lmm_anneal_plan* plan, void* stream)
 sabr_lmm_status sabr_lmm_anneal_fetch(sabr_lmm_anneal_plan* plan, sabr_lmm_result* out);
 void sabr_lmm_anneal_plan_free(sabr_lmm_anneal_plan* plan);
 
+/* The annealing search for callers that cannot allocate device memory.  The paper has no
+ * counterpart to this call; it exists for code that is not allowed to call cudaMalloc: for
+ * example a service that hands the whole device memory to its own pool at start-up, a plug-in
+ * host that gives a library a stream but no allocator, or a latency-critical loop where
+ * cudaMalloc's implicit device synchronisation would stall other work.
+ *   It runs the same search as sabr_lmm_anneal on market `market_idx` (same options, same
+ *   uniforms, same kernels, so the same result), keeping all of its working state in one
+ *   fixed-size array inside the library's device image: 3.6 MB, loaded with the library on every
+ *   GPU that uses it and held until the process exits.  It calls no cudaMalloc, cudaFree or other
+ *   allocating routine.
+ *   Limits: n_chains <= 16384, n_levels <= 4096 (EINVAL names the limit otherwise); lm_top_k and
+ *   record_accepts must be 0.  x0 is host memory [n_param] or NULL (box centre).
+ *   Outputs (device, caller-owned): x_best [n_param], f_best [1], trace_f [n_levels] or NULL.
+ *   Stream-ordered: it only enqueues work on `stream`; synchronise before reading the outputs.
+ *   The first call on a device looks up the array's device address (once per device, with that
+ *   device current); make that first call before any stream capture.
+ *   Every call uses the same array: two calls whose work overlaps on the GPU (different streams,
+ *   or different host threads on one device) race and both results are undefined.  Calls on one
+ *   stream are ordered and safe; each call re-initialises everything it reads.                */
+sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* m, int32_t market_idx,
+                                        const sabr_lmm_anneal_opts* opts, double* x_best,
+                                        double* f_best, double* trace_f, void* stream);
+
 /* Levenberg-Marquardt polish of n points X (device [n x n_param], FP64, updated in place):
  * J from a tangent sweep, (J^T J + mu diag J^T J) d = -J^T r by Cholesky over the free slots,
  * projection on the box, mu /10 on success, x10 on failure.  f, rmse: device [n] or NULL.    */

@@ -74,7 +74,7 @@ _lib = None
 
 EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective", "sabr_lmm_model_vols",
            "sabr_lmm_objective_grad", "sabr_lmm_anneal", "sabr_lmm_anneal_prepare", "sabr_lmm_anneal_launch",
-           "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_lm_polish",
+           "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_anneal_noalloc", "sabr_lmm_lm_polish",
            "sabr_lmm_quadrature_rule", "sabr_lmm_last_error", "sabr_lmm_version")
 
 

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -610,3 +611,113 @@ extern "C" sabr_lmm_status sabr_lmm_quadrature_rule(int32_t q, double* x, double
 
 extern "C" const char* sabr_lmm_last_error(void) { return g_err.c_str(); }
 extern "C" const char* sabr_lmm_version(void) { return "sabr_lmm 0.1 (sm_103a)"; }
+
+// ====================================================================== annealing without allocation
+// sabr_lmm_anneal_noalloc runs the same kernels as sabr_lmm_anneal, but keeps every byte of the
+// search's working state in one fixed-size array that lives in the library's own device image
+// (allocated when the library's module is loaded on a device, held until the process exits).  It
+// never calls cudaMalloc or cudaFree, so a caller that must not allocate can still anneal.
+namespace {
+
+constexpr int kNoAllocMaxChains = 16384;
+constexpr int kNoAllocMaxLevels = 4096;
+constexpr int kNoAllocMaxParam = kMaxParam;
+constexpr int kNoAllocW = 4;  // warps (chains) per CTA, as the default plan
+constexpr int kNoAllocMaxGrid = (kNoAllocMaxChains + kNoAllocW - 1) / kNoAllocW;
+
+// Byte offsets of the regions in the array (each 256-byte aligned).
+constexpr size_t kNaHead = 0;  // xs[12] fs T0 x0[12] best_x[12] best_f counter
+constexpr size_t kNaXe = 512;
+constexpr size_t kNaFe = kNaXe + (size_t)kNoAllocMaxChains * kNoAllocMaxParam * 8;
+constexpr size_t kNaXb = kNaFe + (size_t)kNoAllocMaxChains * 8;
+constexpr size_t kNaFb = kNaXb + (size_t)kNoAllocMaxChains * kNoAllocMaxParam * 8;
+constexpr size_t kNaPf = kNaFb + (size_t)kNoAllocMaxChains * 8;
+constexpr size_t kNaPc = kNaPf + (size_t)kNoAllocMaxGrid * 8;
+constexpr size_t kNaTr = kNaPc + (size_t)kNoAllocMaxGrid * 4;
+constexpr size_t kNaBytes = kNaTr + (size_t)kNoAllocMaxLevels * 8;   // 3.60 MB
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+std::mutex g_noalloc_mu;
+std::map<int, unsigned char*> g_noalloc_addr;   // device ordinal -> device address of the array
+
+// The device address of the array on the current device, looked up once per device.  In host
+// code `g_noalloc_scratch` is only a stand-in symbol; a kernel must be given this address.
+sabr_lmm_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  auto it = g_noalloc_addr.find(dev);
+  if (it == g_noalloc_addr.end()) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(SABR_LMM_ECUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+    it = g_noalloc_addr.emplace(dev, (unsigned char*)p).first;
+  }
+  *out = it->second;
+  return SABR_LMM_OK;
+}
+
+}  // namespace
+
+extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, int32_t market_idx,
+                                                   const sabr_lmm_anneal_opts* o, double* x_best, double* f_best,
+                                                   double* trace_f, void* stream) {
+  if (!mk || !o || !x_best || !f_best) return fail(SABR_LMM_EINVAL, "market, opts, x_best and f_best are required");
+  if (market_idx < 0 || market_idx >= (int)mk->dm.size()) return fail(SABR_LMM_EINVAL, "market_idx out of range");
+  if (o->n_chains < 1 || o->n_levels < 1 || o->steps_per_level < 1)
+    return fail(SABR_LMM_EINVAL, "n_chains, n_levels, steps_per_level must be >= 1");
+  if (o->n_chains > kNoAllocMaxChains || o->n_levels > kNoAllocMaxLevels) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "anneal_noalloc: %d chains x %d levels exceeds the static scratch limit of %d chains x %d levels",
+             o->n_chains, o->n_levels, kNoAllocMaxChains, kNoAllocMaxLevels);
+    return fail(SABR_LMM_EINVAL, buf);
+  }
+  if (!(o->cooling > 0.0 && o->cooling <= 1.0)) return fail(SABR_LMM_EINVAL, "cooling must be in (0, 1]");
+  if (!(o->step_frac > 0.0) || !(o->step_floor >= 0.0)) return fail(SABR_LMM_EINVAL, "step_frac > 0 and step_floor >= 0 required");
+  if (o->prec < SABR_LMM_FP64 || o->prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
+  if (o->lm_top_k > 0 || o->record_accepts) return fail(SABR_LMM_EINVAL, "anneal_noalloc supports neither the polish nor accept records");
+  const DevMarket& m = mk->dm[market_idx];
+  const HostMarket& h = mk->hm[market_idx];
+  if (m.n_swp > 0) return fail(SABR_LMM_ENOTSUP, "swaptions are not enabled in this build");
+  const int P = m.n_param;
+  unsigned char* base = nullptr;
+  sabr_lmm_status st0 = noalloc_scratch(&base);
+  if (st0 != SABR_LMM_OK) return st0;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* head = (double*)(base + kNaHead);
+  SAState st{};
+  st.xs = head;
+  st.fs = head + 12;
+  st.T0 = head + 13;
+  double* x0 = head + 14;
+  st.best_x = head + 26;
+  st.best_f = head + 38;
+  st.counter = (unsigned int*)(head + 39);
+  st.xe = (double*)(base + kNaXe);
+  st.fe = (double*)(base + kNaFe);
+  st.xb = (double*)(base + kNaXb);
+  st.fb = (double*)(base + kNaFb);
+  st.part_f = (double*)(base + kNaPf);
+  st.part_c = (int*)(base + kNaPc);
+  st.trace_f = (double*)(base + kNaTr);
+  st.bits = nullptr;
+  SAParams sp{};
+  sp.C = o->n_chains; sp.L = o->n_levels; sp.N = o->steps_per_level; sp.P = P;
+  sp.cooling = o->cooling; sp.step_frac = o->step_frac; sp.step_floor = o->step_floor; sp.T0_opt = o->T0;
+  sp.seed = o->seed; sp.market_index = (unsigned long long)market_idx;
+  sp.x0 = x0;
+  double hx0[kNoAllocMaxParam];
+  for (int k = 0; k < P; ++k) hx0[k] = o->x0 ? o->x0[k] : 0.5 * (h.lo[k] + h.hi[k]);
+  // every value the kernels read before writing is set here or by sa_start_kernel (f(x0), T0,
+  // the first start point and the level counter), so the previous call's contents do not leak in
+  CUDA_TRY(cudaMemcpyAsync(x0, hx0, P * sizeof(double), cudaMemcpyHostToDevice, s));
+  const int grid = (o->n_chains + kNoAllocW - 1) / kNoAllocW;
+  CUDA_TRY(enqueue_anneal(m, o->prec, st, sp, kNoAllocW, grid, s, true));
+  CUDA_TRY(enqueue_anneal(m, o->prec, st, sp, kNoAllocW, grid, s, false));
+  CUDA_TRY(cudaMemcpyAsync(x_best, st.best_x, P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(f_best, st.best_f, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (trace_f) CUDA_TRY(cudaMemcpyAsync(trace_f, st.trace_f, o->n_levels * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return SABR_LMM_OK;
+}
