@@ -61,8 +61,7 @@ typedef enum { SABR_LMM_MODEL_SMILE = 0, SABR_LMM_MODEL_REBONATO = 1 } sabr_lmm_
 
 /* SABR implied-vol formula.
  *   HAGAN2002 : Hagan, Kumar, Lesniewski, Woodward (2002) lognormal expansion with z/x(z) and
- *               the first-order expiry correction ("the Hagan second order approximation
- *               formula", Section 2.1).
+ *               the first-order expiry correction (the formula Section 2.1 attributes to Hagan).
  *   PAPER     : Eq. (sigmaHagan) exactly as printed (no expiry dependence).                */
 typedef enum { SABR_LMM_HAGAN2002 = 0, SABR_LMM_PAPER = 1 } sabr_lmm_formula;
 

@@ -16,9 +16,9 @@
 //                                    cost functions of Section 3).  Pins: closed-form points,
 //                                    put-call parity, the zero-vol and zero-strike limits.
 //   sabr_hagan2002 ................. Hagan et al.'s lognormal expansion with the z/x(z) factor,
-//                                    named as "the Hagan second order approximation" in
-//                                    Section 2.1.  Pins: beta=1,nu=0 gives alpha; ATM limit;
-//                                    mirror symmetry; a 50-digit evaluation of the textbook form.
+//                                    the formula Section 2.1 refers to by Hagan's name.  Pins:
+//                                    beta=1,nu=0 gives alpha; ATM limit; mirror symmetry; a
+//                                    50-digit evaluation of the textbook form.
 //   sabr_paper ..................... Eq. (sigmaHagan) as printed.  Pin: the paper's calibrated
 //                                    parameters (Table tab:paramsHaganVolas) reproduce its model
 //                                    vols (Table tab:haganVolas).
