@@ -39,8 +39,11 @@ typedef enum {
 
 /* Arithmetic of the hot path.
  *   FP64      : every price, integral and sum in FP64 (the plain form).
- *   FP32      : integrals, SABR vols and Black prices in FP32; objective sums, the Metropolis
- *               comparison and the chain state in FP64.
+ *   FP32      : integrals, SABR vols and Black prices in FP32; the objective summed across
+ *               lanes in float-float (48-bit significand); the Metropolis test in FP32 and
+ *               repeated in FP64 whenever the uniform falls inside the FP32 error band (so the
+ *               decision equals the FP64 decision on the same objective values); chain state
+ *               in FP32.  Outputs (f, vols, best points) are returned as FP64.
  *   FP32_TF32X3 / FP32_BF16X3 : FP32, with the swaption quadratic forms contracted on the
  *               tensor cores with split (3-term) products accumulated in FP32.              */
 typedef enum {

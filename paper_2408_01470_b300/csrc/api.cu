@@ -157,14 +157,16 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
   struct Off {
     size_t T, P, cap_K, cap_vol, cap_wu, swp_K, swp_vol, swp_wu, cap_fwd, swp_start, swp_end, swp_swap, swap_a, swap_b,
         capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
-        swp_w, cblk64, cblk32, sblk64, sblk32, q64, q32, err;
+        swp_w, cblk64, cblk32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
+        swap_grp, swap_L, swap_W32;
   };
   std::vector<Off> off(n_markets);
   std::vector<DevMarket> dm(n_markets);
   std::vector<HostMarket> hm(n_markets);
   // host-side integer bookkeeping
   std::vector<std::vector<int>> capfwd(n_markets), fwdnp(n_markets), swp_swap(n_markets), swap_a(n_markets),
-      swap_b(n_markets), swap_np(n_markets);
+      swap_b(n_markets), swap_np(n_markets), grp_a(n_markets), grp_nE(n_markets), grp_L(n_markets),
+      grp_delta(n_markets), grp_swap0(n_markets), swap_grp(n_markets), swap_L(n_markets);
   for (int j = 0; j < n_markets; ++j) {
     const sabr_lmm_market_desc& d = descs[j];
     DevMarket& m = dm[j];
@@ -184,23 +186,50 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
       fwdnp[j][i] = d.model == SABR_LMM_MODEL_REBONATO ? n_panels(d.T[i], m.panel) : 0;
       if (seen[i]) NP = std::max(NP, fwdnp[j][i]);
     }
+    // distinct underlying swaps, numbered in (first forward, last forward) order so that the swaps
+    // of one expiry group are contiguous
     std::map<std::pair<int, int>, int> idx;
-    int max_win = 1;
-    for (int k = 0; k < d.n_swp; ++k) {
-      auto key = std::make_pair(d.swp_start[k], d.swp_end[k]);
-      auto it = idx.find(key);
-      if (it == idx.end()) {
-        int id = (int)swap_a[j].size();
-        idx[key] = id;
-        swap_a[j].push_back(key.first);
-        swap_b[j].push_back(key.second);
-        swap_np[j].push_back(n_panels(d.T[key.first], m.panel));
-        max_win = std::max(max_win, key.second - key.first);
-        swp_swap[j].push_back(id);
-      } else {
-        swp_swap[j].push_back(it->second);
-      }
+    for (int k = 0; k < d.n_swp; ++k) idx[std::make_pair(d.swp_start[k], d.swp_end[k])] = 0;
+    int max_win = 1, nid = 0;
+    for (auto& kv : idx) {
+      kv.second = nid++;
+      swap_a[j].push_back(kv.first.first);
+      swap_b[j].push_back(kv.first.second);
+      swap_np[j].push_back(n_panels(d.T[kv.first.first], m.panel));
+      max_win = std::max(max_win, kv.first.second - kv.first.first);
     }
+    for (int k = 0; k < d.n_swp; ++k) swp_swap[j].push_back(idx[std::make_pair(d.swp_start[k], d.swp_end[k])]);
+    // expiry groups: swaps sharing their first forward share every pair integral G_ij(T_E), X_ij(T_E)
+    int NA = 1, ND = 1, max_gwin = 1;
+    for (int sidx = 0; sidx < (int)swap_a[j].size(); ++sidx) {
+      const int a = swap_a[j][sidx];
+      if (grp_a[j].empty() || grp_a[j].back() != a) {
+        grp_a[j].push_back(a);
+        grp_nE[j].push_back(n_panels(d.T[a], m.panel));
+        grp_L[j].push_back(0);
+        grp_swap0[j].push_back(sidx);
+      }
+      const int g = (int)grp_a[j].size() - 1;
+      swap_grp[j].push_back(g);
+      swap_L[j].push_back(swap_b[j][sidx] - a);
+      grp_L[j][g] = std::max(grp_L[j][g], swap_b[j][sidx] - a);
+    }
+    grp_swap0[j].push_back((int)swap_a[j].size());
+    for (size_t g = 0; g < grp_a[j].size(); ++g) max_gwin = std::max(max_gwin, grp_L[j][g]);
+    for (size_t g = 0; g < grp_a[j].size(); ++g) {
+      const int a = grp_a[j][g];
+      for (int i = 0; i < max_gwin; ++i) {
+        const int dl = i < grp_L[j][g] ? n_panels(d.T[a + i] - d.T[a], m.panel) : 0;
+        grp_delta[j].push_back(dl);
+      }
+      const int dmax = grp_delta[j][g * max_gwin + grp_L[j][g] - 1];
+      NA = std::max(NA, grp_nE[j][g] + dmax);
+      ND = std::max(ND, dmax + 1);
+    }
+    m.n_grp = (int)grp_a[j].size();
+    m.NA = NA;
+    m.ND = ND;
+    m.max_gwin = max_gwin;
     m.n_swap = (int)swap_a[j].size();
     m.max_win = max_win;
     m.NP = std::max(NP, 1);
@@ -230,6 +259,11 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.sblk64 = A.take(instr_block_bytes<double>(m.n_swp_pad)); o.sblk32 = A.take(instr_block_bytes<float>(m.n_swp_pad));
     o.q64 = A.take(sizeof(QuadTab<double>)); o.q32 = A.take(sizeof(QuadTab<float>));
     o.err = A.take(16);
+    const int ng = m.n_grp;
+    o.grp_a = A.take(ng * 4); o.grp_nE = A.take(ng * 4); o.grp_L = A.take(ng * 4);
+    o.grp_delta = A.take((size_t)ng * m.max_gwin * 4); o.grp_swap0 = A.take((ng + 1) * 4);
+    o.swap_grp = A.take(m.n_swap * 4); o.swap_L = A.take(m.n_swap * 4);
+    o.swap_W32 = A.take((size_t)m.n_swap * max_win * 4);
   }
   std::vector<unsigned char> host(A.size, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { if (src && bytes) std::memcpy(host.data() + o, src, bytes); };
@@ -247,19 +281,24 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     put(o.swap_np, swap_np[j].data(), m.n_swap * 4);
     put(o.capfwd_list, capfwd[j].data(), m.n_capfwd * 4); put(o.fwd_np, fwdnp[j].data(), d.n_fwd * 4);
     put(o.lo, d.lo, d.n_param * 8); put(o.hi, d.hi, d.n_param * 8); put(o.freem, d.free_mask, d.n_param);
+    put(o.grp_a, grp_a[j].data(), m.n_grp * 4); put(o.grp_nE, grp_nE[j].data(), m.n_grp * 4);
+    put(o.grp_L, grp_L[j].data(), m.n_grp * 4);
+    put(o.grp_delta, grp_delta[j].data(), (size_t)m.n_grp * m.max_gwin * 4);
+    put(o.grp_swap0, grp_swap0[j].data(), (m.n_grp + 1) * 4);
+    put(o.swap_grp, swap_grp[j].data(), m.n_swap * 4); put(o.swap_L, swap_L[j].data(), m.n_swap * 4);
     QuadTab<double> q64;
     QuadTab<float> q32;
     const double D = m.panel;
     for (int q = 0; q < kQ; ++q) {
       const double oq = 0.5 * D * (1.0 + kGLx[q]);
       const double hq = 0.5 * (D - oq);
-      q64.o[q] = oq; q64.w[q] = 0.5 * D * kGLw[q];
+      q64.o[q] = oq; q64.w[q] = 0.5 * D * kGLw[q]; q64.sw[q] = std::sqrt(0.5 * D * kGLw[q]);
       for (int r = 0; r < kQ; ++r) {
         q64.o2[q * kQ + r] = oq + hq * (1.0 + kGLx[r]);
         q64.sw2[q * kQ + r] = std::sqrt(hq * kGLw[r]);
       }
     }
-    for (int i = 0; i < kQ; ++i) { q32.o[i] = (float)q64.o[i]; q32.w[i] = (float)q64.w[i]; }
+    for (int i = 0; i < kQ; ++i) { q32.o[i] = (float)q64.o[i]; q32.w[i] = (float)q64.w[i]; q32.sw[i] = (float)q64.sw[i]; }
     for (int i = 0; i < kQ * kQ; ++i) { q32.o2[i] = (float)q64.o2[i]; q32.sw2[i] = (float)q64.sw2[i]; }
     put(o.q64, &q64, sizeof q64);
     put(o.q32, &q32, sizeof q32);
@@ -294,6 +333,10 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.cblk64 = base + o.cblk64; m.cblk32 = base + o.cblk32; m.sblk64 = base + o.sblk64; m.sblk32 = base + o.sblk32;
     m.q64 = (const QuadTab<double>*)(base + o.q64); m.q32 = (const QuadTab<float>*)(base + o.q32);
     m.err = (int*)(base + o.err);
+    m.grp_a = (const int*)(base + o.grp_a); m.grp_nE = (const int*)(base + o.grp_nE);
+    m.grp_L = (const int*)(base + o.grp_L); m.grp_delta = (const int*)(base + o.grp_delta);
+    m.grp_swap0 = (const int*)(base + o.grp_swap0); m.swap_grp = (const int*)(base + o.swap_grp);
+    m.swap_L = (const int*)(base + o.swap_L); m.swap_W32 = (float*)(base + o.swap_W32);
     setup_forwards_kernel<<<(m.n_fwd + 127) / 128, 128, 0, s>>>(m);
     if (m.n_swap > 0) setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
     const int ni = m.n_cap + m.n_swp;
@@ -337,10 +380,34 @@ cudaError_t launch_objective_r(const DevMarket& m, const double* X, long long n,
   return m.formula == 0 ? launch_objective<R, 1, 0>(m, X, n, f, vols, s) : launch_objective<R, 1, 1>(m, X, n, f, vols, s);
 }
 
+template <class R, int FORMULA>
+cudaError_t launch_objective_cta(const DevMarket& m, const double* X, long long n, double* f, double* vols, cudaStream_t s) {
+  const uint32_t sm = smem_bytes_cta<R>(m);
+  auto kern = objective_cta_kernel<R, FORMULA>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  long long blocks = n < 148 * 16 ? n : 148 * 16;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, 256, sm, s>>>(m, X, n, f, vols);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_objective_any(const DevMarket& m, int prec, const double* X, long long n, double* f, double* vols,
                                  cudaStream_t s) {
+  if (m.n_swp > 0) {
+    if (prec == SABR_LMM_FP64)
+      return m.formula == 0 ? launch_objective_cta<double, 0>(m, X, n, f, vols, s) : launch_objective_cta<double, 1>(m, X, n, f, vols, s);
+    return m.formula == 0 ? launch_objective_cta<float, 0>(m, X, n, f, vols, s) : launch_objective_cta<float, 1>(m, X, n, f, vols, s);
+  }
   return prec == SABR_LMM_FP64 ? launch_objective_r<double>(m, X, n, f, vols, s)
                                : launch_objective_r<float>(m, X, n, f, vols, s);
+}
+
+// Shared memory a market needs per CTA in the given precision (the caller checks it against the
+// device's opt-in limit).
+uint32_t market_smem(const DevMarket& m, int prec) {
+  if (m.n_swp > 0) return prec == SABR_LMM_FP64 ? smem_bytes_cta<double>(m) : smem_bytes_cta<float>(m);
+  return prec == SABR_LMM_FP64 ? smem_bytes<double>(m, 4) : smem_bytes<float>(m, 4);
 }
 
 sabr_lmm_status check_call(const sabr_lmm_market* m, int32_t idx, int64_t n, int32_t prec) {
@@ -348,7 +415,8 @@ sabr_lmm_status check_call(const sabr_lmm_market* m, int32_t idx, int64_t n, int
   if (idx < 0 || idx >= (int)m->dm.size()) return fail(SABR_LMM_EINVAL, "market_idx out of range");
   if (n < 0) return fail(SABR_LMM_EINVAL, "n must be >= 0");
   if (prec < SABR_LMM_FP64 || prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
-  if (m->dm[idx].n_swp > 0) return fail(SABR_LMM_ENOTSUP, "swaptions are not enabled in this build");
+  if (market_smem(m->dm[idx], prec) > 227 * 1024)
+    return fail(SABR_LMM_ENOTSUP, "the market does not fit in one CTA's shared memory at this precision");
   return SABR_LMM_OK;
 }
 
@@ -407,9 +475,33 @@ cudaError_t enqueue_anneal_t(const DevMarket& m, const SAState& st, const SAPara
   return cudaGetLastError();
 }
 
+// Markets with swaptions: one CTA of 256 threads per chain.
+template <class R, int FORMULA>
+cudaError_t enqueue_anneal_cta_t(const DevMarket& m, const SAState& st, const SAParams& sp, cudaStream_t s,
+                                 bool configure_only) {
+  const uint32_t sm = smem_bytes_cta<R>(m);
+  auto k0 = sa_start_cta_kernel<R, FORMULA>;
+  auto k1 = sa_level_cta_kernel<R, FORMULA>;
+  if (configure_only) {
+    cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return e;
+  }
+  k0<<<1, 256, sm, s>>>(m, st, sp);
+  for (int l = 0; l < sp.L; ++l) k1<<<sp.C, 256, sm, s>>>(m, st, sp, l);
+  sa_final_kernel<<<1, 1024, 0, s>>>(st, sp.C, sp.P);
+  return cudaGetLastError();
+}
+
 cudaError_t enqueue_anneal(const DevMarket& m, int prec, const SAState& st, const SAParams& sp, int W, int grid,
                            cudaStream_t s, bool configure_only = false) {
   const bool f64 = prec == SABR_LMM_FP64;
+  if (m.n_swp > 0) {
+    if (f64) return m.formula == 0 ? enqueue_anneal_cta_t<double, 0>(m, st, sp, s, configure_only)
+                                   : enqueue_anneal_cta_t<double, 1>(m, st, sp, s, configure_only);
+    return m.formula == 0 ? enqueue_anneal_cta_t<float, 0>(m, st, sp, s, configure_only)
+                          : enqueue_anneal_cta_t<float, 1>(m, st, sp, s, configure_only);
+  }
 #define DISPATCH(R)                                                                                           \
   if (m.model == 0) return m.formula == 0 ? enqueue_anneal_t<R, 0, 0>(m, st, sp, W, grid, s, configure_only)  \
                                           : enqueue_anneal_t<R, 0, 1>(m, st, sp, W, grid, s, configure_only); \
@@ -441,7 +533,8 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (o->warps_per_block < 0 || o->warps_per_block > 16) return fail(SABR_LMM_EINVAL, "warps_per_block must be in [0, 16]");
   if (o->lm_top_k > 0) return fail(SABR_LMM_ENOTSUP, "the LM polish is not enabled in this build");
   for (const DevMarket& m : mk->dm)
-    if (m.n_swp > 0) return fail(SABR_LMM_ENOTSUP, "swaptions are not enabled in this build");
+    if (market_smem(m, o->prec) > 227 * 1024)
+      return fail(SABR_LMM_ENOTSUP, "a market does not fit in one CTA's shared memory at this precision");
   sabr_lmm_anneal_plan* p = new sabr_lmm_anneal_plan();
   p->mk = mk;
   p->opts = *o;
@@ -460,7 +553,8 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     Off& q = off[j];
     q.xs = A.take(Pj * 8); q.fs = A.take(8); q.T0 = A.take(8);
     q.xe = A.take(C * Pj * 8); q.fe = A.take(C * 8); q.xb = A.take(C * Pj * 8); q.fb = A.take(C * 8);
-    q.pf = A.take((size_t)p->grid * 8); q.pc = A.take((size_t)p->grid * 4); q.cnt = A.take(16);
+    const size_t nparts = std::max<size_t>((size_t)p->grid, C);   // CTA minima (one CTA per chain with swaptions)
+    q.pf = A.take(nparts * 8); q.pc = A.take(nparts * 4); q.cnt = A.take(16);
     q.tr = A.take(L * 8); q.bx = A.take(Pj * 8); q.bf = A.take(8); q.x0 = A.take(Pj * 8);
     q.bits = (j == 0 && o->record_accepts) ? A.take(C * L * N) : 0;
     q.vols = A.take((size_t)(mk->dm[j].n_cap + mk->dm[j].n_swp) * 8);

@@ -15,6 +15,7 @@
 #include "device_math.cuh"
 #include "market.cuh"
 #include "objective.cuh"
+#include "swaption.cuh"
 
 namespace sabr {
 
@@ -36,8 +37,11 @@ __global__ void setup_swaps_kernel(DevMarket m) {
   for (int k = a; k < b; ++k) A += m.tau[k] * m.P[k + 1];
   double S = 0.0;
   for (int k = a; k < b; ++k) S += m.tau[k] * m.P[k + 1] / A * m.F[k];
-  for (int k = a; k < b; ++k)
-    m.swap_W[(size_t)s * m.max_win + (k - a)] = m.tau[k] * m.P[k + 1] / A * pow(m.F[k], m.beta) / pow(S, m.beta);
+  for (int k = a; k < b; ++k) {
+    const double W = m.tau[k] * m.P[k + 1] / A * pow(m.F[k], m.beta) / pow(S, m.beta);
+    m.swap_W[(size_t)s * m.max_win + (k - a)] = W;
+    m.swap_W32[(size_t)s * m.max_win + (k - a)] = (float)W;
+  }
   m.swap_A[s] = A;
   m.swap_S[s] = S;
   m.swap_TE[s] = m.T[a];
@@ -482,6 +486,241 @@ __global__ void rmse_from_vols_kernel(const double* vols, const double* cap_vol,
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
     out[0] = 100.0 * sqrt(t / (double)n);
   }
+}
+
+
+
+// ====================================================================== markets with swaptions
+// One CTA per parameter point (chain).  Shared-memory plan: [caplet block][swaption block]
+// [quadrature table][chain scratch][32 objective values][mbarrier, 32 doubles, 32 ints].
+
+template <class R> __device__ __forceinline__ const void* swp_block(const DevMarket& m);
+template <> __device__ __forceinline__ const void* swp_block<double>(const DevMarket& m) { return m.sblk64; }
+template <> __device__ __forceinline__ const void* swp_block<float>(const DevMarket& m) { return m.sblk32; }
+
+template <class R>
+__host__ __device__ inline uint32_t smem_bytes_cta(const DevMarket& m) {
+  return instr_block_bytes<R>(m.n_cap_pad) + instr_block_bytes<R>(m.n_swp_pad) + (uint32_t)sizeof(QuadTab<R>) +
+         (uint32_t)cta_scratch_elems(m) * sizeof(R) + 32 * 16 + 512;
+}
+
+template <class R>
+struct CtaSmemS {
+  void* cap;
+  void* swp;
+  QuadTab<R>* quad;
+  R* scratch;
+  void* red;
+  uint64_t* mbar;
+  double* red_f;
+  int* red_c;
+};
+
+template <class R>
+__device__ __forceinline__ CtaSmemS<R> carve_cta(unsigned char* smem, const DevMarket& m) {
+  CtaSmemS<R> s;
+  unsigned char* p = smem;
+  s.cap = p; p += instr_block_bytes<R>(m.n_cap_pad);
+  s.swp = p; p += instr_block_bytes<R>(m.n_swp_pad);
+  s.quad = (QuadTab<R>*)p; p += sizeof(QuadTab<R>);
+  s.scratch = (R*)p; p += (size_t)cta_scratch_elems(m) * sizeof(R);
+  s.red = p; p += 32 * 16;
+  s.mbar = (uint64_t*)p;
+  s.red_f = (double*)(p + 16);
+  s.red_c = (int*)(p + 16 + 32 * sizeof(double));
+  return s;
+}
+
+__device__ bool stage_to_smem3(void* d0, const void* g0, uint32_t b0, void* d1, const void* g1, uint32_t b1, void* d2,
+                               const void* g2, uint32_t b2, uint64_t* mbar, int* err) {
+  const uint32_t bar = smem_u32(mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(b0 + b1 + b2) : "memory");
+    bulk_g2s(d0, g0, b0, bar);
+    bulk_g2s(d1, g1, b1, bar);
+    bulk_g2s(d2, g2, b2, bar);
+  }
+  uint32_t done = 0;
+  long long it = 0;
+  while (!done) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(0u) : "memory");
+    if (!done && ++it > kWaitLimit) break;
+  }
+  const int timed_out = __syncthreads_or(!done);
+  if (timed_out) {
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    it = 0;
+    while (!done && ++it < kWaitLimit) {
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(done) : "r"(bar), "r"(0u) : "memory");
+    }
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+template <class R>
+__device__ __forceinline__ bool stage_market_cta(const CtaSmemS<R>& cs, const DevMarket& m) {
+  return stage_to_smem3(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.swp, swp_block<R>(m),
+                        instr_block_bytes<R>(m.n_swp_pad), cs.quad, quad_block<R>(m), (uint32_t)sizeof(QuadTab<R>),
+                        cs.mbar, m.err);
+}
+
+template <class R, int FORMULA>
+__global__ void __launch_bounds__(256) objective_cta_kernel(DevMarket m, const double* __restrict__ X, long long n,
+                                                            double* __restrict__ f, double* __restrict__ vols) {
+  typedef typename ObjOf<R>::T O;
+  extern __shared__ __align__(128) unsigned char smem[];
+  CtaSmemS<R> cs = carve_cta<R>(smem, m);
+  if (!stage_market_cta<R>(cs, m)) return;
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
+  CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
+  const int n_instr = m.n_cap + m.n_swp;
+  for (long long i = blockIdx.x; i < n; i += gridDim.x) {
+    if (threadIdx.x < kMaxParam) sc.xs[threadIdx.x] = threadIdx.x < m.n_param ? (R)X[i * m.n_param + threadIdx.x] : R(0);
+    __syncthreads();
+    const O fi = cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, vols ? vols + i * n_instr : nullptr);
+    if (f && threadIdx.x == 0) f[i] = obj_to_double(fi);
+    __syncthreads();
+  }
+}
+
+template <class R, int FORMULA>
+__global__ void __launch_bounds__(256) sa_start_cta_kernel(DevMarket m, SAState st, SAParams sp) {
+  typedef typename ObjOf<R>::T O;
+  extern __shared__ __align__(128) unsigned char smem[];
+  CtaSmemS<R> cs = carve_cta<R>(smem, m);
+  if (!stage_market_cta<R>(cs, m)) return;
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
+  CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
+  const double x0 = threadIdx.x < (unsigned)sp.P ? (double)(R)sp.x0[threadIdx.x] : 0.0;
+  if (threadIdx.x < kMaxParam) sc.xs[threadIdx.x] = (R)x0;
+  __syncthreads();
+  const double f0 = obj_to_double(cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr));
+  if (threadIdx.x < (unsigned)sp.P) st.xs[threadIdx.x] = x0;
+  if (threadIdx.x == 0) {
+    st.fs[0] = f0;
+    st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
+    st.counter[0] = 0u;
+  }
+}
+
+template <class R, int FORMULA>
+__global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState st, SAParams sp, int level) {
+  typedef typename ObjOf<R>::T O;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned long long s_wacc;
+  CtaSmemS<R> cs = carve_cta<R>(smem, m);
+  if (!stage_market_cta<R>(cs, m)) return;
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
+  CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x;   // one chain per CTA
+  const int P = sp.P;
+  const double T0 = st.T0[0];
+  double T = T0;
+  for (int j = 0; j < level; ++j) T = T * sp.cooling;
+  const double sf = fmax(sp.step_frac * sqrt(T / T0), sp.step_floor);
+  const float invT = (float)(1.0 / T);
+
+  O f;
+  obj_from_double(st.fs[0], f);
+  R x = 0, lo = 0, hi = 0, xbk = 0;
+  bool freek = false;
+  if (warp == 0 && lane < P) {
+    x = (R)st.xs[lane];
+    lo = box_lo<R>(m, lane);
+    hi = box_hi<R>(m, lane);
+    freek = m.freem[lane] != 0;
+    xbk = level > 0 ? (R)st.xb[(size_t)c * P + lane] : x;
+  }
+  O fbest = f;
+  if (level > 0) obj_from_double(st.fb[c], fbest);
+  const unsigned long long cw = (unsigned long long)c | (sp.market_index << 32);
+  U4 o;
+  R y = x;
+  for (int s = 0; s < sp.N; ++s) {
+    if (warp == 0) {
+      if ((s & 7) == 0) o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)(s + (lane >> 2)), (uint64_t)level, cw, sp.seed, 0ull);
+      const int src = ((s & 7) << 2) | ((lane >> 2) & 3), wsel = lane & 3;
+      const uint64_t w0 = __shfl_sync(0xffffffffu, o.v[0], src);
+      const uint64_t w1 = __shfl_sync(0xffffffffu, o.v[1], src);
+      const uint64_t w2 = __shfl_sync(0xffffffffu, o.v[2], src);
+      const uint64_t w3 = __shfl_sync(0xffffffffu, o.v[3], src);
+      const uint64_t word = wsel == 0 ? w0 : (wsel == 1 ? w1 : (wsel == 2 ? w2 : w3));
+      y = x;
+      if (lane < P && freek) y = neighbour(x, lo, hi, (R)sf, word);
+      if (lane < kMaxParam) sc.xs[lane] = lane < P ? y : R(0);
+      const uint64_t wacc = __shfl_sync(0xffffffffu, word, P);
+      if (lane == 0) s_wacc = wacc;
+    }
+    __syncthreads();
+    const O fy = cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr);
+    const bool acc = metropolis(fy, f, (uint64_t)s_wacc, T, invT);
+    if (acc) {
+      x = y;
+      f = fy;
+      if (obj_less(f, fbest)) { fbest = f; xbk = x; }
+    }
+    if (st.bits && threadIdx.x == 0) st.bits[((size_t)c * sp.L + level) * sp.N + s] = acc ? 1 : 0;
+    __syncthreads();   // s_wacc and the point are rewritten by the next step
+  }
+  if (warp == 0 && lane < P) {
+    st.xe[(size_t)c * P + lane] = (double)x;
+    st.xb[(size_t)c * P + lane] = (double)xbk;
+  }
+  if (threadIdx.x == 0) {
+    st.fe[c] = obj_to_double(f);
+    st.fb[c] = obj_to_double(fbest);
+  }
+  __threadfence();
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    st.part_f[blockIdx.x] = obj_to_double(f);
+    st.part_c[blockIdx.x] = c;
+    __threadfence();
+    const unsigned int ticket = atomicAdd(st.counter, 1u);
+    last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double bf = __longlong_as_double(0x7ff0000000000000LL);
+  int bc = 0x7fffffff;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const double pf = __ldcg(st.part_f + b);
+    const int pc = __ldcg(st.part_c + b);
+    if (lex_less(pf, pc, bf, bc)) { bf = pf; bc = pc; }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double of = __shfl_xor_sync(0xffffffffu, bf, off);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+    if (lex_less(of, oc, bf, bc)) { bf = of; bc = oc; }
+  }
+  if (lane == 0) { cs.red_f[warp] = bf; cs.red_c[warp] = bc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int W = blockDim.x >> 5;
+    for (int w = 1; w < W; ++w)
+      if (lex_less(cs.red_f[w], cs.red_c[w], cs.red_f[0], cs.red_c[0])) { cs.red_f[0] = cs.red_f[w]; cs.red_c[0] = cs.red_c[w]; }
+    st.fs[0] = cs.red_f[0];
+    st.trace_f[level] = cs.red_f[0];
+  }
+  __syncthreads();
+  const int cbest = cs.red_c[0];
+  if (threadIdx.x < (unsigned)P) st.xs[threadIdx.x] = __ldcg(st.xe + (size_t)cbest * P + threadIdx.x);
+  if (threadIdx.x == 0) st.counter[0] = 0u;
 }
 
 }  // namespace sabr

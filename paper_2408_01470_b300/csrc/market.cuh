@@ -18,10 +18,10 @@ constexpr int kMaxParam = 12;       // parameter slots
 constexpr int kBlkArrays = 12;      // R values per instrument in a block (+ one int)
 
 // Quadrature table per precision, offsets relative to the start of a panel of width D:
-//   o[q] = (D/2)(1 + xi_q), w[q] = (D/2) w_q             (outer rule on the panel)
+//   o[q] = (D/2)(1 + xi_q), w[q] = (D/2) w_q, sw[q] = sqrt(w[q])   (outer rule on the panel)
 //   o2[q*8+r] = o[q] + h_q (1 + xi_r), sw2[q*8+r] = sqrt(h_q w_r), h_q = (D - o[q]) / 2
 //                                                         (inner rule on [u_q, panel top])
-template <class R> struct QuadTab { R o[kQ]; R w[kQ]; R o2[kQ * kQ]; R sw2[kQ * kQ]; };
+template <class R> struct QuadTab { R o[kQ]; R w[kQ]; R sw[kQ]; R o2[kQ * kQ]; R sw2[kQ * kQ]; };
 
 template <class R> struct alignas(4 * sizeof(R)) Q4 { R a, b, c, d; };
 
@@ -56,8 +56,20 @@ struct DevMarket {
   int n_cap, n_swp, n_swap;        // caplets, swaptions, distinct underlying swaps
   int n_cap_pad, n_swp_pad;        // multiples of 4
   int n_capfwd;                    // distinct caplet forwards
-  int NP;                          // panels the model mapping needs (max over forwards/expiries)
+  int NP;                          // panels the caplet mapping needs (max over caplet forwards)
   int max_win;                     // longest swap window
+  // swaption geometry (time-homogeneous tables over absolute panels)
+  int n_grp;                       // expiry groups: distinct first forwards of the swaps
+  int NA;                          // absolute panels the swap integrals touch (max n_E + delta)
+  int ND;                          // diagonals of the pair tables (max delta spread + 1)
+  int max_gwin;                    // longest group window
+  const int* grp_a;                // [n_grp] first forward of the group's swaps
+  const int* grp_nE;               // [n_grp] panels to the group's expiry
+  const int* grp_L;                // [n_grp] forwards spanned by the group's longest swap
+  const int* grp_delta;            // [n_grp x max_gwin] (T_i - T_a) / panel for the group's forwards
+  const int* grp_swap0;            // [n_grp + 1] swaps sorted by group: first swap of each group
+  const int* swap_grp;             // [n_swap]
+  const int* swap_L;               // [n_swap] forwards in the swap
   double beta, panel;
   // raw description
   const double *T, *P, *cap_K, *cap_vol, *cap_wu, *swp_K, *swp_vol, *swp_wu;
@@ -71,6 +83,7 @@ struct DevMarket {
   double *F, *tau;                 // [n_fwd]
   double *swap_A, *swap_S, *swap_TE;  // [n_swap]
   double* swap_W;                  // [n_swap x max_win] frozen weights W_i = w_i F_i^b / S^b
+  float* swap_W32;                 // the same in FP32
   int* swap_np;                    // [n_swap] panels to the expiry
   double *cap_pm, *cap_w, *swp_pm, *swp_w;  // market prices and weights (FP64)
   void *cblk64, *cblk32, *sblk64, *sblk32;  // instrument blocks

@@ -281,6 +281,8 @@ __device__ __forceinline__ FF warp_sum(FF v) {
 template <class R> struct ObjOf { typedef double T; };
 template <> struct ObjOf<float> { typedef FF T; };
 
+__device__ __forceinline__ double obj_add(double a, double b) { return a + b; }
+__device__ __forceinline__ FF obj_add(FF a, FF b) { return ff_add(a, b); }
 __device__ __forceinline__ double obj_inf(double) { return __longlong_as_double(0x7ff0000000000000LL); }
 __device__ __forceinline__ FF obj_inf(FF) { FF r; r.hi = __int_as_float(0x7f800000); r.lo = 0.f; return r; }
 __device__ __forceinline__ double obj_lane(double, double p) { return p; }

@@ -1,0 +1,386 @@
+// CTA-cooperative evaluation of the objective for markets with swaptions: one CTA owns one
+// parameter point (one chain); its warps split the swap-rate integrals, the quadratic forms and the
+// instruments.
+//
+// S3  Pair integrals.  Every forward's vol and vol-of-vol are g(T_i - t), h(T_i - t) (time
+//     homogeneity), so on the uniform panel grid the integrand of G_ij(T_E) and X_ij(T_E) at a
+//     quadrature node depends only on the absolute panels A = p + delta_i, B = p + delta_j the
+//     node falls in for forwards i and j (p the panel of time-to-expiry, delta_i = (T_i - T_E)/D).
+//     With the per-chain matrix Y[A][k] (k < 8: sqrt(w_q) g at the outer nodes; 8 <= k < 16:
+//     sqrt(w_q) h there; 16 <= k < 80: sqrt(w_q) g times sqrt(w_qr) h at the inner nodes) the
+//     panel-pair sums are Gram sums
+//       Gd(A,B) = sum_{k<8} Y_A Y_B,  Hd(A,B) = sum_{8<=k<16} Y_A Y_B,  Ad(A,B) = sum_{k>=16} Y_A Y_B,
+//     and along each diagonal e = B - A the prefix sums PG, PA, SH and PGS (of Gd * inclusive SH)
+//     give, for a swap expiring after nE panels and the pair (i, j) with e = delta_j - delta_i,
+//       G_ij = PG(hi) - PG(lo),  X_ij / theta_ij = PA(hi) - PA(lo) + SH(hi)(PG(hi) - PG(lo)) - (PGS(hi) - PGS(lo))
+//     (lo = delta_i, hi = lo + nE): the composite rule of the oracle, calendar time reversed.
+// S5  Quadratic forms per swap: V = sum_{i<=j} (2 - [i=j]) W_i W_j B_ij, B = (rho G, rho X, phi G),
+//     the B matrices built once per expiry group (swaps sharing their first forward).
+// S6  alpha_S = sqrt(V1/T), nu_S = sqrt(2 V2)/(alpha_S T), rho_S = clamp(V3/V1, +-0.999), then
+//     SABR and Black per swaption, with the caplets priced alongside.
+#pragma once
+#include "objective.cuh"
+
+namespace sabr {
+
+template <class R> struct CtaScratch {
+  R* xs;            // [16]
+  WarpScratch<R> cap;  // caplet mapping (warp 0); its xs is a private copy
+  Q2<R>* Ep;        // [NAc] {e^{-c A D}, e^{-gamma_h A D}}
+  Q4<R>* Tq;        // [8]
+  Q4<R>* T2;        // [8 x 9]
+  R* Y;             // [NA x 81]
+  R* PQ;            // [4 x ND x (NA + 1)]: PG, PA, SH, PGS along each diagonal
+  R* corr;          // [3 x ND]: rho_e, theta_e, phi_e
+  R* Bg;            // [3 x Lg (Lg + 1) / 2] of the current expiry group
+  Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
+  R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
+  Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}
+};
+
+__host__ __device__ inline int cta_y_stride() { return 81; }
+__host__ __device__ inline int cta_pq_len(int NA) { return NA + 1; }
+
+__host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
+  const int NAc = round_up(m.NA, 4);
+  const int Lg = m.max_gwin;
+  return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + round_up(m.NA * cta_y_stride(), 4) +
+                      round_up(4 * m.ND * cta_pq_len(m.NA), 4) + round_up(3 * m.ND, 4) +
+                      round_up(3 * (Lg * (Lg + 1) / 2), 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap,
+                  4);
+}
+
+template <class R>
+__device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m) {
+  CtaScratch<R> s;
+  const int NAc = round_up(m.NA, 4);
+  const int Lg = m.max_gwin;
+  R* p = base;
+  s.xs = p; p += 16;
+  s.cap = warp_scratch<R>(p, m.NP, m.n_fwd); p += warp_scratch_elems(m.NP, m.n_fwd);
+  s.Ep = (Q2<R>*)p; p += 2 * NAc;
+  s.Tq = (Q4<R>*)p; p += 32;
+  s.T2 = (Q4<R>*)p; p += 4 * 72;
+  s.Y = p; p += round_up(m.NA * cta_y_stride(), 4);
+  s.PQ = p; p += round_up(4 * m.ND * cta_pq_len(m.NA), 4);
+  s.corr = p; p += round_up(3 * m.ND, 4);
+  s.Bg = p; p += round_up(3 * (Lg * (Lg + 1) / 2), 4);
+  s.F4s = (Q4<R>*)p; p += 4 * m.n_swap;
+  s.A3s = p; p += round_up(m.n_swap, 4);
+  s.RCs = (Q4<R>*)p;
+  return s;
+}
+
+template <class R> __device__ __forceinline__ const R* swap_W_of(const DevMarket& m);
+template <> __device__ __forceinline__ const double* swap_W_of<double>(const DevMarket& m) { return m.swap_W; }
+template <> __device__ __forceinline__ const float* swap_W_of<float>(const DevMarket& m) { return m.swap_W32; }
+
+// Inclusive warp scan (lanes in order).
+template <class R>
+__device__ __forceinline__ R warp_inclusive_scan(R v, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const R o = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += o;
+  }
+  return v;
+}
+
+// Swaption pricing of instrument k of the swaption block (S6 + S4 Black); returns the squared
+// weighted residual, or writes the model vol when vols != null.
+template <class R, int FORMULA>
+__device__ __forceinline__ R price_swaption(const InstrView<R>& B, int k, const CtaScratch<R>& cs, R omb, bool& ok,
+                                            double* vols) {
+  typedef Num<R> M;
+  const int s = B.idx[k];
+  const Q4<R> fw = cs.F4s[s];
+  const Q4<R> rq = cs.RCs[s];
+  RhoConsts<R> rc;
+  rc.rho = rq.a;
+  rc.omr_p = R(1) - rq.a;
+  rc.omr_m = R(1) + rq.a;
+  rc.iomr_p = rq.b;
+  rc.iomr_m = rq.c;
+  rc.omr2 = rq.d;
+  const Q4<R> g0 = B.g0[k];
+  const Q4<R> g1 = B.g1[k];
+  R sig;
+  if (FORMULA == 0) {
+    const R z = fw.b * g0.b;
+    const R zx = z_over_x_fast<R>(z, rc);
+    const R corr = R(1) + g0.d * fw.c + g1.a * fw.d + g1.b * cs.A3s[s];
+    sig = fw.a * g0.c * zx * corr;
+  } else {
+    sig = sabr_paper<R>(fw.a, rc.rho, fw.b * fw.a, g0.a, g0.b, omb);
+  }
+  const bool good = (sig > R(0)) && M::finite_(sig);
+  if (vols) { vols[k] = good ? (double)sig : __longlong_as_double(0x7ff8000000000000LL); return R(0); }
+  ok = ok && good;
+  const Q4<R> g2 = B.g2[k];
+  const R v = sig * g1.c;
+  const R d1 = fdiv<R>(g0.a, v) + R(0.5) * v;
+  const R sg = g2.b;
+  const R p = sg * g1.d * (ncdf<R>(sg * d1) - g2.a * ncdf<R>(sg * (d1 - v)));
+  const R r = g2.d * (p - g2.c);
+  return r * r;
+}
+
+template <class R, int FORMULA>
+__device__ __forceinline__ R price_one_caplet(const InstrView<R>& B, int k, const WarpScratch<R>& ws,
+                                              const RhoConsts<R>& rc, R omb, bool& ok, double* vols) {
+  typedef Num<R> M;
+  const int i = B.idx[k];
+  const Q4<R> fw = ws.F4[i];
+  const Q4<R> g0 = B.g0[k];
+  const Q4<R> g1 = B.g1[k];
+  R sig;
+  if (FORMULA == 0) {
+    const R z = fw.b * g0.b;
+    const R zx = z_over_x_fast<R>(z, rc);
+    const R corr = R(1) + g0.d * fw.c + g1.a * fw.d + g1.b * ws.fA3[i];
+    sig = fw.a * g0.c * zx * corr;
+  } else {
+    sig = sabr_paper<R>(fw.a, rc.rho, fw.b * fw.a, g0.a, g0.b, omb);
+  }
+  const bool good = (sig > R(0)) && M::finite_(sig);
+  if (vols) { vols[k] = good ? (double)sig : __longlong_as_double(0x7ff8000000000000LL); return R(0); }
+  ok = ok && good;
+  const Q4<R> g2 = B.g2[k];
+  const R v = sig * g1.c;
+  const R d1 = fdiv<R>(g0.a, v) + R(0.5) * v;
+  const R sg = g2.b;
+  const R p = sg * g1.d * (ncdf<R>(sg * d1) - g2.a * ncdf<R>(sg * (d1 - v)));
+  const R r = g2.d * (p - g2.c);
+  return r * r;
+}
+
+// Objective of the point in cs.xs (every thread of the CTA calls; all return the same value).
+// `red` is shared scratch of 32 objective values.
+template <class R, int FORMULA>
+__device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrView<R>& capB, const InstrView<R>& swpB,
+                                              const QuadTab<R>& qt, const CtaScratch<R>& cs,
+                                              typename ObjOf<R>::T* red, double* vols) {
+  typedef typename ObjOf<R>::T O;
+  typedef Num<R> M;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+  const R a = cs.xs[0], b = cs.xs[1], c = cs.xs[2], d = cs.xs[3];
+  const R ah = cs.xs[4], bh = cs.xs[5], gh = cs.xs[6], dh = cs.xs[7];
+  const R phi = cs.xs[8], l1 = cs.xs[9], l2 = cs.xs[10], l3 = cs.xs[11];
+  const R D = (R)m.panel;
+  const int NA = m.NA, ND = m.ND, YS = cta_y_stride(), PL = cta_pq_len(NA);
+
+  // ---- phase 1: caplet forwards (warp 0); per-chain exponential tables (other warps)
+  if (warp == 0) {
+    if (m.n_capfwd > 0) {
+      if (lane < kMaxParam) cs.cap.xs[lane] = cs.xs[lane];
+      __syncwarp();
+      rebonato_forward_params<R>(m, qt, cs.cap, lane);
+    }
+  } else {
+    const int t0 = tid - 32, nt = nth - 32;
+    for (int j = t0; j < kQ * kQ; j += nt) {
+      const R o2 = qt.o2[j], sw = qt.sw2[j];
+      const R e = M::exp_(-gh * o2);
+      Q4<R> t;
+      t.a = sw * e;
+      t.b = sw * bh * o2 * e;
+      t.c = sw * dh;
+      t.d = R(0);
+      cs.T2[(j >> 3) * 9 + (j & 7)] = t;
+    }
+    for (int j = t0; j < kQ; j += nt) {
+      const R o = qt.o[j];
+      const R eg = M::exp_(-c * o), eh = M::exp_(-gh * o);
+      Q4<R> t;
+      t.a = eg;
+      t.b = b * o * eg;
+      t.c = eh;
+      t.d = bh * o * eh;
+      cs.Tq[j] = t;
+    }
+    for (int A = t0; A < NA; A += nt) {
+      const R base = D * (R)A;
+      Q2<R> e;
+      e.a = M::exp_(-c * base);
+      e.b = M::exp_(-gh * base);
+      cs.Ep[A] = e;
+    }
+    for (int e = t0; e < ND; e += nt) {
+      const R dt = D * (R)e;
+      cs.corr[e] = M::exp_(-l1 * dt);
+      cs.corr[ND + e] = M::exp_(-l2 * dt);
+      cs.corr[2 * ND + e] = phi * M::exp_(-l3 * dt);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: Y rows
+  for (int it = tid; it < NA * 80; it += nth) {
+    const int A = it / 80, k = it - A * 80;
+    const R base = D * (R)A;
+    const Q2<R> E = cs.Ep[A];
+    R v;
+    if (k < 8) {
+      const Q4<R> t = cs.Tq[k];
+      v = qt.sw[k] * (E.a * ((a + b * base) * t.a + t.b) + d);
+    } else if (k < 16) {
+      const Q4<R> t = cs.Tq[k - 8];
+      v = qt.sw[k - 8] * (E.b * ((ah + bh * base) * t.c + t.d) + dh);
+    } else {
+      const int q = (k - 16) >> 3, r = (k - 16) & 7;
+      const Q4<R> t = cs.Tq[q];
+      const R g = E.a * ((a + b * base) * t.a + t.b) + d;
+      const Q4<R> t2 = cs.T2[q * 9 + r];
+      const R h2 = E.b * ((ah + bh * base) * t2.a + t2.b) + t2.c;
+      v = qt.sw[q] * g * h2;
+    }
+    cs.Y[A * YS + k] = v;
+  }
+  __syncthreads();
+
+  // ---- phase 3: pair sums along the diagonals (raw, then prefix-summed in phase 4)
+  for (int it = tid; it < ND * NA; it += nth) {
+    const int e = it / NA, A = it - e * NA;
+    if (A + e >= NA) continue;
+    const R* ya = cs.Y + A * YS;
+    const R* yb = cs.Y + (A + e) * YS;
+    R G = 0, H = 0, Ad = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) G += ya[k] * yb[k];
+#pragma unroll
+    for (int k = 8; k < 16; ++k) H += ya[k] * yb[k];
+#pragma unroll 16
+    for (int k = 16; k < 80; ++k) Ad += ya[k] * yb[k];
+    cs.PQ[(0 * ND + e) * PL + A] = G;
+    cs.PQ[(1 * ND + e) * PL + A] = Ad;
+    cs.PQ[(2 * ND + e) * PL + A] = H;
+  }
+  __syncthreads();
+
+  // ---- phase 4: exclusive prefix sums along each diagonal (one warp per diagonal)
+  for (int e = warp; e < ND; e += nw) {
+    const int n = NA - e;
+    R* PG = cs.PQ + (0 * ND + e) * PL;
+    R* PA = cs.PQ + (1 * ND + e) * PL;
+    R* SH = cs.PQ + (2 * ND + e) * PL;
+    R* PGS = cs.PQ + (3 * ND + e) * PL;
+    R cg = 0, ca = 0, chh = 0, cgs = 0;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int A = c0 + lane;
+      const bool in = A < n;
+      const R g = in ? PG[A] : R(0), ad = in ? PA[A] : R(0), hh = in ? SH[A] : R(0);
+      const R ig = warp_inclusive_scan(g, lane), ia = warp_inclusive_scan(ad, lane), ih = warp_inclusive_scan(hh, lane);
+      const R gs = g * (ih + chh);   // Gd(A) times the inclusive prefix of Hd at A
+      const R igs = warp_inclusive_scan(gs, lane);
+      __syncwarp();
+      if (in) {
+        PG[A] = cg + ig - g;
+        PA[A] = ca + ia - ad;
+        SH[A] = chh + ih - hh;
+        PGS[A] = cgs + igs - gs;
+      }
+      cg += __shfl_sync(0xffffffffu, ig, 31);
+      ca += __shfl_sync(0xffffffffu, ia, 31);
+      chh += __shfl_sync(0xffffffffu, ih, 31);
+      cgs += __shfl_sync(0xffffffffu, igs, 31);
+      __syncwarp();
+    }
+    if (lane == 0) { PG[n] = cg; PA[n] = ca; SH[n] = chh; PGS[n] = cgs; }
+  }
+  __syncthreads();
+
+  // ---- phase 5: per expiry group, the B matrices, then the quadratic forms of its swaps
+  const R* Wall = swap_W_of<R>(m);
+  for (int g = 0; g < m.n_grp; ++g) {
+    const int Lg = m.grp_L[g], nE = m.grp_nE[g];
+    const int* dl = m.grp_delta + g * m.max_gwin;
+    const int npk = Lg * (Lg + 1) / 2;
+    for (int t = tid; t < Lg * Lg; t += nth) {
+      const int i = t / Lg, j = t - i * Lg;
+      if (j < i) continue;
+      const int e = dl[j] - dl[i];
+      const int lo = dl[i], hi = lo + nE;
+      const R* PG = cs.PQ + (0 * ND + e) * PL;
+      const R* PA = cs.PQ + (1 * ND + e) * PL;
+      const R* SH = cs.PQ + (2 * ND + e) * PL;
+      const R* PGS = cs.PQ + (3 * ND + e) * PL;
+      const R G = PG[hi] - PG[lo];
+      const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
+      const int pk = i * Lg - (i * (i - 1)) / 2 + (j - i);
+      cs.Bg[pk] = cs.corr[e] * G;
+      cs.Bg[npk + pk] = cs.corr[e] * cs.corr[ND + e] * X;
+      cs.Bg[2 * npk + pk] = cs.corr[2 * ND + e] * G;
+    }
+    __syncthreads();
+    const int s0 = m.grp_swap0[g], s1 = m.grp_swap0[g + 1];
+    const R TE = (R)m.T[m.grp_a[g]];
+    for (int s = s0 + warp; s < s1; s += nw) {
+      const int L = m.swap_L[s];
+      const R* W = Wall + (size_t)s * m.max_win;
+      R v1 = 0, v2 = 0, v3 = 0;
+      for (int i = lane; i < L; i += 32) {
+        R r1 = 0, r2 = 0, r3 = 0;
+        const int row = i * Lg - (i * (i - 1)) / 2 - i;
+        for (int j = i; j < L; ++j) {
+          const R wj = (j == i) ? W[j] : R(2) * W[j];
+          r1 += wj * cs.Bg[row + j];
+          r2 += wj * cs.Bg[npk + row + j];
+          r3 += wj * cs.Bg[2 * npk + row + j];
+        }
+        v1 += W[i] * r1;
+        v2 += W[i] * r2;
+        v3 += W[i] * r3;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+        v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+      }
+      if (lane == 0) {
+        const R al = M::sqrt_(v1 / TE);
+        const R nu = M::sqrt_(R(2) * v2) / (al * TE);
+        R rho = v3 / v1;
+        rho = rho > R(0.999) ? R(0.999) : (rho < R(-0.999) ? R(-0.999) : rho);
+        Q4<R> f;
+        f.a = al;
+        f.b = nu / al;
+        f.c = al * al;
+        f.d = rho * nu * al;
+        cs.F4s[s] = f;
+        cs.A3s[s] = (R(2) - R(3) * rho * rho) * nu * nu;
+        Q4<R> q;
+        q.a = rho;
+        q.b = R(1) / (R(1) - rho);
+        q.c = R(1) / (R(1) + rho);
+        q.d = (R(1) - rho) * (R(1) + rho);
+        cs.RCs[s] = q;
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- phase 6: price every caplet and swaption, reduce
+  RhoConsts<R> rc;
+  rc.init(phi);
+  const R omb = (R)(1.0 - m.beta);
+  bool ok = true;
+  R part = 0;
+  const int ntot = m.n_cap + m.n_swp;
+  for (int k = tid; k < ntot; k += nth) {
+    if (k < m.n_cap) part += price_one_caplet<R, FORMULA>(capB, k, cs.cap, rc, omb, ok, vols);
+    else part += price_swaption<R, FORMULA>(swpB, k - m.n_cap, cs, omb, ok, vols ? vols + m.n_cap : nullptr);
+  }
+  const int bad = __syncthreads_or(!ok);
+  if (vols) return obj_inf(O());
+  const O wsum = warp_sum(obj_lane(O(), part));
+  if (lane == 0) red[warp] = wsum;
+  __syncthreads();
+  O f = red[0];
+  for (int w = 1; w < nw; ++w) f = obj_add(f, red[w]);
+  __syncthreads();   // red is reused by the next evaluation
+  if (bad || !obj_finite(f)) return obj_inf(O());
+  return f;
+}
+
+}  // namespace sabr
