@@ -234,6 +234,17 @@ class Market:
                                                  _stream_ptr(stream)))
         return f, G
 
+    def lm_polish(self, X, max_iter=50, target_rmse=0.0, market=0, stream=None):
+        """sabr_lmm_lm_polish: returns (X polished, f, rmse in vol points) as device tensors."""
+        X = self._X(X, market).clone()
+        n = X.shape[0]
+        f = self._torch.empty(n, dtype=self._torch.float64, device="cuda")
+        r = self._torch.empty(n, dtype=self._torch.float64, device="cuda")
+        _check(self._lib.sabr_lmm_lm_polish(self.h, market, C.c_void_p(X.data_ptr()), n, int(max_iter),
+                                            float(target_rmse), C.c_void_p(f.data_ptr()), C.c_void_p(r.data_ptr()),
+                                            _stream_ptr(stream)))
+        return X, f, r
+
     def _opts(self, n_chains, n_levels, steps, cooling, seed, prec, T0, step_frac, step_floor, x0,
               lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, record_accepts):
         o = AnnealOpts()

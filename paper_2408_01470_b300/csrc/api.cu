@@ -14,6 +14,7 @@
 
 #include "../../include/sabr_lmm.h"
 #include "kernels.cuh"
+#include "lm.cuh"
 
 using namespace sabr;
 
@@ -81,7 +82,9 @@ struct sabr_lmm_anneal_plan {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaGraphExec_t gexec = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+  void* lm_buf = nullptr;         // polish buffers (top-k points, selection, LM work) per market
+  std::vector<size_t> lm_off;
 };
 
 namespace {
@@ -442,16 +445,124 @@ extern "C" sabr_lmm_status sabr_lmm_model_vols(const sabr_lmm_market* m, int32_t
   return SABR_LMM_OK;
 }
 
+namespace {
+template <class R, int MODEL, int FORMULA>
+cudaError_t launch_grad(const DevMarket& m, const double* X, long long n, double* f, double* G, cudaStream_t s) {
+  const int W = 4;
+  const uint32_t sm = smem_bytes_grad<R>(m, W);
+  auto kern = grad_kernel<R, MODEL, FORMULA>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  long long blocks = (n + W - 1) / W;
+  if (blocks > 148 * 32) blocks = 148 * 32;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, W * 32, sm, s>>>(m, X, n, f, G);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_grad_r(const DevMarket& m, const double* X, long long n, double* f, double* G, cudaStream_t s) {
+  if (m.model == 0) return m.formula == 0 ? launch_grad<R, 0, 0>(m, X, n, f, G, s) : launch_grad<R, 0, 1>(m, X, n, f, G, s);
+  return m.formula == 0 ? launch_grad<R, 1, 0>(m, X, n, f, G, s) : launch_grad<R, 1, 1>(m, X, n, f, G, s);
+}
+}  // namespace
+
 extern "C" sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int32_t idx, const double* X, int64_t n,
                                                    int32_t prec, double* f, double* G, void* stream) {
-  (void)m; (void)idx; (void)X; (void)n; (void)prec; (void)f; (void)G; (void)stream;
-  return fail(SABR_LMM_ENOTSUP, "objective_grad is not enabled in this build");
+  sabr_lmm_status st = check_call(m, idx, n, prec);
+  if (st != SABR_LMM_OK) return st;
+  if (m->dm[idx].n_swp > 0) return fail(SABR_LMM_ENOTSUP, "the adjoint of the swaption forms is not enabled in this build");
+  if (n == 0) return SABR_LMM_OK;
+  if (!X || !f || !G) return fail(SABR_LMM_EINVAL, "X, f and G are required");
+  const DevMarket& dm = m->dm[idx];
+  CUDA_TRY(prec == SABR_LMM_FP64 ? launch_grad_r<double>(dm, X, n, f, G, (cudaStream_t)stream)
+                                 : launch_grad_r<float>(dm, X, n, f, G, (cudaStream_t)stream));
+  return SABR_LMM_OK;
 }
+
+namespace {
+
+// Device buffers of a polish of n points (allocated by the caller of lm_enqueue).
+struct LmWork {
+  double *Xp, *vols, *res, *grad, *gf, *mu, *f, *ft, *Xt, *rmse;
+  int* done;
+};
+
+size_t lm_work_bytes(const DevMarket& m, int n) {
+  const size_t P = m.n_param, ni = m.n_cap + m.n_swp, S = kLmStencil;
+  return 8 * ((size_t)n * S * P + 2 * (size_t)n * S * ni + (size_t)n * P + 5 * (size_t)n + (size_t)n * P) + 4 * (size_t)n + 16 * 12;
+}
+
+LmWork lm_carve(void* base, const DevMarket& m, int n) {
+  const size_t P = m.n_param, ni = m.n_cap + m.n_swp, S = kLmStencil;
+  double* p = (double*)base;
+  LmWork w;
+  w.Xp = p; p += (size_t)n * S * P;
+  w.vols = p; p += (size_t)n * S * ni;
+  w.res = p; p += (size_t)n * S * ni;
+  w.grad = p; p += (size_t)n * P;
+  w.gf = p; p += n;
+  w.mu = p; p += n;
+  w.f = p; p += n;
+  w.ft = p; p += n;
+  w.rmse = p; p += n;
+  w.Xt = p; p += (size_t)n * P;
+  w.done = (int*)p;
+  return w;
+}
+
+__global__ void lm_init_kernel(int n, double* mu, int* done) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { mu[i] = 1e-3; done[i] = 0; }
+}
+
+// Enqueue max_iter LM iterations on the n points X (device, updated in place).
+cudaError_t lm_enqueue(const DevMarket& m, double* X, int n, int max_iter, double target, const LmWork& w, cudaStream_t s) {
+  const int ni = m.n_cap + m.n_swp;
+  const bool have_adjoint = m.n_swp == 0;
+  cudaError_t e;
+  lm_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w.mu, w.done);
+  if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, w.f, nullptr, s)) != cudaSuccess) return e;
+  if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
+  lm_rmse_kernel<<<n, 256, 0, s>>>(m, n, w.vols, target, w.rmse, w.done);
+  for (int it = 0; it < max_iter; ++it) {
+    lm_perturb_kernel<<<n, 32, 0, s>>>(n, m.n_param, X, w.Xp);
+    if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xp, (long long)n * kLmStencil, nullptr, w.vols, s)) != cudaSuccess) return e;
+    residuals_from_vols_kernel<<<148 * 4, 256, 0, s>>>(m, (long long)n * kLmStencil, w.vols, w.res);
+    if (have_adjoint) {
+      if ((e = launch_grad_r<double>(m, X, n, w.gf, w.grad, s)) != cudaSuccess) return e;
+    }
+    lm_step_kernel<<<n, 128, 0, s>>>(m, n, w.res, have_adjoint ? w.grad : nullptr, w.mu, w.done, X, w.Xt);
+    if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xt, n, w.ft, nullptr, s)) != cudaSuccess) return e;
+    lm_accept_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, m.n_param, X, w.Xt, w.f, w.ft, w.mu, w.done);
+    if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
+    lm_rmse_kernel<<<n, 256, 0, s>>>(m, n, w.vols, target, w.rmse, w.done);
+  }
+  (void)ni;
+  return cudaGetLastError();
+}
+
+}  // namespace
 
 extern "C" sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t idx, double* X, int64_t n,
                                               int32_t max_iter, double target, double* f, double* rmse, void* stream) {
-  (void)m; (void)idx; (void)X; (void)n; (void)max_iter; (void)target; (void)f; (void)rmse; (void)stream;
-  return fail(SABR_LMM_ENOTSUP, "lm_polish is not enabled in this build");
+  sabr_lmm_status st = check_call(m, idx, n, SABR_LMM_FP64);
+  if (st != SABR_LMM_OK) return st;
+  if (n == 0) return SABR_LMM_OK;
+  if (!X) return fail(SABR_LMM_EINVAL, "X is required");
+  if (max_iter < 0 || n > (1 << 20)) return fail(SABR_LMM_EINVAL, "max_iter >= 0 and n <= 2^20 required");
+  const DevMarket& dm = m->dm[idx];
+  cudaStream_t s = (cudaStream_t)stream;
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, lm_work_bytes(dm, (int)n)) != cudaSuccess) return fail(SABR_LMM_ENOMEM, "cudaMalloc of the polish buffers failed");
+  const LmWork w = lm_carve(buf, dm, (int)n);
+  cudaError_t e = lm_enqueue(dm, X, (int)n, max_iter, target, w, s);
+  if (e == cudaSuccess && f) e = cudaMemcpyAsync(f, w.f, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && rmse) e = cudaMemcpyAsync(rmse, w.rmse, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("lm_polish: ") + cudaGetErrorString(e));
+  return SABR_LMM_OK;
 }
 
 // ====================================================================== annealing
@@ -531,7 +642,8 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (!(o->step_frac > 0.0) || !(o->step_floor >= 0.0)) return fail(SABR_LMM_EINVAL, "step_frac > 0 and step_floor >= 0 required");
   if (o->prec < SABR_LMM_FP64 || o->prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
   if (o->warps_per_block < 0 || o->warps_per_block > 16) return fail(SABR_LMM_EINVAL, "warps_per_block must be in [0, 16]");
-  if (o->lm_top_k > 0) return fail(SABR_LMM_ENOTSUP, "the LM polish is not enabled in this build");
+  if (o->lm_top_k < 0 || o->lm_top_k > o->n_chains || o->lm_top_k > 1024) return fail(SABR_LMM_EINVAL, "lm_top_k must be in [0, min(n_chains, 1024)]");
+  if (o->lm_top_k > 0 && o->lm_max_iter < 0) return fail(SABR_LMM_EINVAL, "lm_max_iter must be >= 0");
   for (const DevMarket& m : mk->dm)
     if (market_smem(m, o->prec) > 227 * 1024)
       return fail(SABR_LMM_ENOTSUP, "a market does not fit in one CTA's shared memory at this precision");
@@ -592,6 +704,17 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   }
   cudaEventCreate(&p->ev0);
   cudaEventCreate(&p->ev1);
+  cudaEventCreate(&p->ev2);
+  if (o->lm_top_k > 0) {
+    Arena B;
+    for (int j = 0; j < nm; ++j) {
+      const int k = o->lm_top_k, Pj = mk->dm[j].n_param;
+      p->lm_off.push_back(B.take((size_t)k * Pj * 8));          // points
+      p->lm_off.push_back(B.take((size_t)k * 4));               // selected chains
+      p->lm_off.push_back(B.take(lm_work_bytes(mk->dm[j], k)));  // LM work
+    }
+    if (cudaMalloc(&p->lm_buf, B.size) != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOMEM, "cudaMalloc of the polish buffers failed"); }
+  }
   for (int j = 0; j < nm; ++j) {
     cudaError_t e = enqueue_anneal(mk->dm[j], o->prec, p->st[j], p->sp[j], p->W, p->grid, p->stream, true);
     if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, std::string("configure: ") + cudaGetErrorString(e)); }
@@ -606,6 +729,27 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   *out = p;
   return SABR_LMM_OK;
 }
+
+namespace {
+// The polish of the lm_top_k lowest best-ever chain points of every market, after the search.
+sabr_lmm_status enqueue_polish(sabr_lmm_anneal_plan* p, cudaStream_t s) {
+  const int k = p->opts.lm_top_k;
+  char* b = (char*)p->lm_buf;
+  for (size_t j = 0; j < p->mk->dm.size(); ++j) {
+    const DevMarket& m = p->mk->dm[j];
+    double* X = (double*)(b + p->lm_off[3 * j]);
+    int* sel = (int*)(b + p->lm_off[3 * j + 1]);
+    const LmWork w = lm_carve(b + p->lm_off[3 * j + 2], m, k);
+    select_lowest_kernel<<<1, 1024, 0, s>>>(p->st[j].fb, p->opts.n_chains, k, sel);
+    gather_points_kernel<<<k, 32, 0, s>>>(p->st[j].xb, sel, k, m.n_param, X);
+    cudaError_t e = lm_enqueue(m, X, k, p->opts.lm_max_iter, p->opts.target_rmse_volpt, w, s);
+    if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("polish launch: ") + cudaGetErrorString(e));
+    take_best_kernel<<<1, 32, 0, s>>>(X, w.f, k, m.n_param, p->st[j].best_x, p->st[j].best_f);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return SABR_LMM_OK;
+}
+}  // namespace
 
 extern "C" sabr_lmm_status sabr_lmm_anneal_launch(sabr_lmm_anneal_plan* p, void* stream) {
   if (!p) return fail(SABR_LMM_EINVAL, "plan is NULL");
@@ -632,6 +776,11 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_launch(sabr_lmm_anneal_plan* p, void*
     if (st != SABR_LMM_OK) return st;
     CUDA_TRY(cudaEventRecord(p->ev1, s));
   }
+  if (p->opts.lm_top_k > 0) {
+    sabr_lmm_status st = enqueue_polish(p, s);
+    if (st != SABR_LMM_OK) return st;
+  }
+  CUDA_TRY(cudaEventRecord(p->ev2, s));
   p->stream = s;
   return SABR_LMM_OK;
 }
@@ -652,7 +801,9 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_fetch(sabr_lmm_anneal_plan* p, sabr_l
   float ms = 0.f;
   cudaEventElapsedTime(&ms, p->ev0, p->ev1);
   out->seconds = ms * 1e-3;
-  out->lm_seconds = 0.0;
+  float ms2 = 0.f;
+  cudaEventElapsedTime(&ms2, p->ev1, p->ev2);
+  out->lm_seconds = p->opts.lm_top_k > 0 ? ms2 * 1e-3 : 0.0;
   out->n_evals = (int64_t)p->opts.n_chains * ((int64_t)p->opts.n_levels * p->opts.steps_per_level + 1);
   for (int j = 0; j < nm; ++j) {
     const DevMarket& m = mk->dm[j];
@@ -681,6 +832,8 @@ extern "C" void sabr_lmm_anneal_plan_free(sabr_lmm_anneal_plan* p) {
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
+  if (p->ev2) cudaEventDestroy(p->ev2);
+  if (p->lm_buf) cudaFree(p->lm_buf);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   if (p->state) cudaFree(p->state);
   delete p;

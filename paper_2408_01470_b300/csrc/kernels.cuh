@@ -16,6 +16,7 @@
 #include "market.cuh"
 #include "objective.cuh"
 #include "swaption.cuh"
+#include "adjoint.cuh"
 
 namespace sabr {
 
@@ -721,6 +722,45 @@ __global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState 
   const int cbest = cs.red_c[0];
   if (threadIdx.x < (unsigned)P) st.xs[threadIdx.x] = __ldcg(st.xe + (size_t)cbest * P + threadIdx.x);
   if (threadIdx.x == 0) st.counter[0] = 0u;
+}
+
+
+// ====================================================================== adjoint (caplet markets)
+// One warp per point; shared-memory plan: [caplet block][quadrature table]
+// [W x (warp scratch, adjoint scratch)][tail].
+template <class R>
+__host__ __device__ inline uint32_t grad_warp_bytes(const DevMarket& m) {
+  const uint32_t a = (uint32_t)warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R);
+  const uint32_t b = (uint32_t)adj_scratch_bytes(m.NP, m.n_fwd, sizeof(R));
+  return ((a + 31u) & ~31u) + ((b + 31u) & ~31u);
+}
+
+template <class R>
+__host__ __device__ inline uint32_t smem_bytes_grad(const DevMarket& m, int W) {
+  return instr_block_bytes<R>(m.n_cap_pad) + (uint32_t)sizeof(QuadTab<R>) + (uint32_t)W * grad_warp_bytes<R>(m) + 512;
+}
+
+template <class R, int MODEL, int FORMULA>
+__global__ void grad_kernel(DevMarket m, const double* __restrict__ X, long long n, double* __restrict__ f,
+                            double* __restrict__ G) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  void* cap = smem;
+  QuadTab<R>* quad = (QuadTab<R>*)(smem + instr_block_bytes<R>(m.n_cap_pad));
+  unsigned char* wbase = (unsigned char*)quad + sizeof(QuadTab<R>) + (size_t)warp * grad_warp_bytes<R>(m);
+  uint64_t* mbar = (uint64_t*)((unsigned char*)quad + sizeof(QuadTab<R>) + (size_t)W * grad_warp_bytes<R>(m));
+  if (!stage_to_smem2(cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), quad, quad_block<R>(m),
+                      (uint32_t)sizeof(QuadTab<R>), mbar, m.err))
+    return;
+  const InstrView<R> capB = instr_view<R>(cap, m.n_cap_pad);
+  WarpScratch<R> ws = warp_scratch<R>((R*)wbase, m.NP, m.n_fwd);
+  const uint32_t wbytes = ((uint32_t)warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R) + 31u) & ~31u;
+  AdjScratch<R> as = adj_scratch<R>(wbase + wbytes, m.NP, m.n_fwd);
+  for (long long i = (long long)blockIdx.x * W + warp; i < n; i += (long long)gridDim.x * W) {
+    if (lane < kMaxParam) ws.xs[lane] = lane < m.n_param ? (R)X[i * m.n_param + lane] : R(0);
+    __syncwarp();
+    warp_objective_grad<R, MODEL, FORMULA>(m, capB, *quad, ws, as, lane, f + i, G + i * m.n_param);
+  }
 }
 
 }  // namespace sabr

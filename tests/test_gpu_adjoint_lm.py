@@ -1,0 +1,136 @@
+"""The hand-written adjoint (S9) and the Levenberg-Marquardt polish (S10), through the C-ABI.
+
+Adjoint: FP64 gradient against the oracle's forward-mode dual numbers (an independent route) and
+against central differences of the GPU objective; FP32 gradient against the oracle within the
+FP32 pricing error.  LM: recovery of the generating point on noise-free quotes, agreement with the
+oracle's LM, and the annealer's top-k polish.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_01470_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "smile_2y": lambda: synth.smile_2y(),
+    "smile_2y_paper": lambda: synth.smile_2y(formula=synth.FORMULA_PAPER),
+    "caplets_20x15": lambda: synth.caplet_term_structure(),
+    "caplets_20x15_paper": lambda: synth.caplet_term_structure(formula=synth.FORMULA_PAPER),
+    "caplets_7x5": lambda: synth.caplet_term_structure(n_fwd=7, n_strikes=5),
+}
+
+
+def _markets(sk):
+    import paper_2408_01470_b300 as lib
+    om, vols = oracle.quoted_market(sk)
+    return om, lib.Market(sk, vols)
+
+
+def _points(sk, n, seed):
+    X = synth.uniform_in_box(sk, n, seed=seed)
+    if sk.model == synth.MODEL_REBONATO_LMM:
+        X = 0.5 * (X + sk.theta_true[None, :])   # keep the vols in a sensible range
+    return X
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_fp64_matches_oracle_dual_gradient(gpu_lib, name):
+    sk = CASES[name]()
+    om, gm = _markets(sk)
+    X = _points(sk, 40, seed=31)
+    f, G = gm.objective_grad(X, "fp64")
+    f, G = f.cpu().numpy(), G.cpu().numpy()
+    for i in range(X.shape[0]):
+        fo, go = om.objective_grad(X[i])
+        if not np.isfinite(fo):
+            assert not np.isfinite(f[i])
+            continue
+        assert f[i] == pytest.approx(fo, rel=1e-12)
+        scale = np.max(np.abs(go))
+        assert np.max(np.abs(G[i] - go)) <= 1e-9 * scale, (i, G[i], go)
+
+
+@pytest.mark.parametrize("name", ["smile_2y", "caplets_20x15"])
+def test_adjoint_fp64_matches_central_differences(gpu_lib, name):
+    sk = CASES[name]()
+    om, gm = _markets(sk)
+    X = _points(sk, 4, seed=32)
+    _, G = gm.objective_grad(X, "fp64")
+    G = G.cpu().numpy()
+    P = sk.n_param
+    for i in range(X.shape[0]):
+        h = 1e-6 * np.maximum(np.abs(X[i]), 1.0)
+        Xp = np.repeat(X[i][None, :], 2 * P, axis=0)
+        for k in range(P):
+            Xp[2 * k, k] += h[k]
+            Xp[2 * k + 1, k] -= h[k]
+        fp = gm.objective(Xp, "fp64").cpu().numpy()
+        fd = (fp[0::2] - fp[1::2]) / (2 * h)
+        scale = np.max(np.abs(fd))
+        assert np.max(np.abs(G[i] - fd)) <= 1e-6 * scale, (G[i], fd)
+
+
+@pytest.mark.parametrize("name", ["smile_2y", "caplets_20x15"])
+def test_adjoint_fp32_within_pricing_error(gpu_lib, name):
+    sk = CASES[name]()
+    om, gm = _markets(sk)
+    X = _points(sk, 16, seed=33)
+    _, G = gm.objective_grad(X, "fp32")
+    G = G.cpu().numpy()
+    for i in range(X.shape[0]):
+        fo, go = om.objective_grad(X[i])
+        if not np.isfinite(fo):
+            continue
+        scale = np.max(np.abs(go))
+        assert np.max(np.abs(G[i] - go)) <= 2e-3 * scale
+
+
+def test_adjoint_many_sets_sampled(gpu_lib):
+    # the gradient workload: 65536 parameter sets on the caplet term structure, checked on a sample
+    sk = synth.caplet_term_structure()
+    om, gm = _markets(sk)
+    X = _points(sk, 65536, seed=34)
+    f, G = gm.objective_grad(X, "fp64")
+    f, G = f.cpu().numpy(), G.cpu().numpy()
+    for i in (0, 1, 777, 32768, 65535):
+        fo, go = om.objective_grad(X[i])
+        assert f[i] == pytest.approx(fo, rel=1e-12)
+        assert np.max(np.abs(G[i] - go)) <= 1e-9 * np.max(np.abs(go))
+
+
+def test_lm_recovers_generating_point_noise_free(gpu_lib):
+    sk = synth.caplet_term_structure(noise_free=True, n_fwd=8, n_strikes=5)
+    om, gm = _markets(sk)
+    th0 = sk.theta_true.copy()
+    th0[:9] *= 1.03
+    X, f, r = gm.lm_polish(th0[None, :], max_iter=60)
+    X = X.cpu().numpy()[0]
+    assert r.cpu().numpy()[0] < 1e-6
+    assert om.rmse_volpt(X) < 1e-6
+    po = om.lm(th0, max_iter=200)
+    assert np.max(np.abs(X[:9] - po["theta"][:9]) / np.maximum(np.abs(po["theta"][:9]), 1e-3)) < 1e-4
+
+
+def test_lm_on_swaption_market_improves(gpu_lib):
+    sk = synth.joint_caplet_swaption(expiries=(1, 2, 3), tenors=(1, 2, 3), swp_m=(-0.4, 0.0, 0.4), noise_free=True)
+    om, gm = _markets(sk)
+    th0 = sk.theta_true * 1.02
+    f0 = om.objective(th0)
+    X, f, r = gm.lm_polish(th0[None, :], max_iter=30)
+    assert f.cpu().numpy()[0] < 1e-3 * f0
+    assert om.objective(X.cpu().numpy()[0]) == pytest.approx(f.cpu().numpy()[0], rel=1e-9)
+
+
+def test_anneal_with_top_k_polish(gpu_lib):
+    sk = synth.smile_2y()
+    om, gm = _markets(sk)
+    r0 = gm.anneal(64, 30, 20, 0.85, seed=3, prec="fp32")
+    r1 = gm.anneal(64, 30, 20, 0.85, seed=3, prec="fp32", lm_top_k=8, lm_max_iter=20)
+    assert r1["f_best"][0] <= r0["f_best"][0]
+    assert r1["lm_seconds"] > 0.0
+    # the polished point is a local minimum of the FP64 objective: LM from it moves nowhere
+    p = om.lm(r1["x_best"][0], max_iter=20)
+    assert p["f"] >= r1["f_best"][0] * (1 - 1e-9)
+    assert om.objective(r1["x_best"][0]) == pytest.approx(r1["f_best"][0], rel=1e-12)
