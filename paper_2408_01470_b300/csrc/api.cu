@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -85,6 +86,12 @@ struct sabr_lmm_anneal_plan {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
   void* lm_buf = nullptr;         // polish buffers (top-k points, selection, LM work) per market
   std::vector<size_t> lm_off;
+  // batch mode: one persistent launch per level over every market's chains
+  bool batch = false;
+  void* batch_buf = nullptr;
+  BatchArgs ba{};
+  int bthreads = 256, bgrid = 148;
+  uint32_t bsmem = 0;
 };
 
 namespace {
@@ -622,7 +629,100 @@ cudaError_t enqueue_anneal(const DevMarket& m, int prec, const SAState& st, cons
 #undef DISPATCH
 }
 
+template <class R, int FORMULA>
+cudaError_t enqueue_batch_t(const sabr_lmm_anneal_plan* p, cudaStream_t s, int threads, int grid, int levels,
+                            bool configure_only) {
+  auto k0 = sa_start_batch_kernel<R, FORMULA>;
+  auto k1 = sa_level_batch_kernel<R, FORMULA>;
+  if (configure_only) {
+    cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->bsmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->bsmem);
+    return e;
+  }
+  cudaError_t e = cudaMemsetAsync(p->ba.item_ctr, 0, (size_t)p->opts.n_levels * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  k0<<<p->ba.n_markets, 256, p->bsmem, s>>>(p->ba);
+  for (int l = 0; l < levels; ++l) k1<<<grid, threads, p->bsmem, s>>>(p->ba, l);
+  sa_final_batch_kernel<<<p->ba.n_markets, 1024, 0, s>>>(p->ba);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_batch(const sabr_lmm_anneal_plan* p, cudaStream_t s, int threads, int grid, int levels,
+                          bool configure_only = false) {
+  const bool f64 = p->opts.prec == SABR_LMM_FP64;
+  const int formula = p->mk->dm[0].formula;
+  if (f64) return formula == 0 ? enqueue_batch_t<double, 0>(p, s, threads, grid, levels, configure_only)
+                               : enqueue_batch_t<double, 1>(p, s, threads, grid, levels, configure_only);
+  return formula == 0 ? enqueue_batch_t<float, 0>(p, s, threads, grid, levels, configure_only)
+                      : enqueue_batch_t<float, 1>(p, s, threads, grid, levels, configure_only);
+}
+
+// Autotuner of the batch launch: CTA size x persistent grid, chosen by timing one level of a
+// short probe (4 steps per chain) per candidate; cached per (precision, formula, instrument
+// bucket, market-count bucket).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+sabr_lmm_status tune_batch(sabr_lmm_anneal_plan* p, cudaStream_t s) {
+  int max_instr = 0;
+  for (const DevMarket& m : p->mk->dm) max_instr = std::max(max_instr, m.n_cap + m.n_swp);
+  const auto key = std::make_tuple(p->opts.prec, p->mk->dm[0].formula, (max_instr + 255) / 256,
+                                   (p->ba.n_markets + 63) / 64);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) { p->bthreads = it->second.first; p->bgrid = it->second.second; return SABR_LMM_OK; }
+  }
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<std::pair<int, int>> cand;
+  for (int threads : {128, 256}) {
+    int per_sm = 0;
+    cudaError_t e = p->opts.prec == SABR_LMM_FP64
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<double, 0>, threads, p->bsmem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<float, 0>, threads, p->bsmem);
+    if (e != cudaSuccess || per_sm < 1) continue;
+    cand.push_back({threads, nsm * per_sm});
+    cand.push_back({threads, 2 * nsm * per_sm});
+  }
+  if (cand.empty()) return fail(SABR_LMM_ENOTSUP, "a batch market does not fit in one CTA's shared memory");
+  // probe: the same search shortened to 4 steps, one level
+  std::vector<SAParams> probe(p->sp);
+  for (auto& q : probe) q.N = std::min(q.N, 4);
+  CUDA_TRY(cudaMemcpyAsync((void*)p->ba.sp, probe.data(), probe.size() * sizeof(SAParams), cudaMemcpyHostToDevice, s));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best_ms = 1e30f;
+  std::pair<int, int> best = cand[0];
+  for (const auto& c : cand) {
+    CUDA_TRY(enqueue_batch(p, s, c.first, c.second, 1));   // warm-up
+    CUDA_TRY(cudaEventRecord(a, s));
+    CUDA_TRY(enqueue_batch(p, s, c.first, c.second, 1));
+    CUDA_TRY(cudaEventRecord(b, s));
+    CUDA_TRY(cudaEventSynchronize(b));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  CUDA_TRY(cudaMemcpyAsync((void*)p->ba.sp, p->sp.data(), p->sp.size() * sizeof(SAParams), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  p->bthreads = best.first;
+  p->bgrid = best.second;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return SABR_LMM_OK;
+}
+
 sabr_lmm_status enqueue_plan(sabr_lmm_anneal_plan* p, cudaStream_t s) {
+  if (p->batch) {
+    cudaError_t e = enqueue_batch(p, s, p->bthreads, p->bgrid, p->opts.n_levels);
+    if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    return SABR_LMM_OK;
+  }
   const int nm = (int)p->mk->dm.size();
   for (int j = 0; j < nm; ++j) {
     cudaError_t e = enqueue_anneal(p->mk->dm[j], p->opts.prec, p->st[j], p->sp[j], p->W, p->grid, s);
@@ -669,7 +769,9 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     q.pf = A.take(nparts * 8); q.pc = A.take(nparts * 4); q.cnt = A.take(16);
     q.tr = A.take(L * 8); q.bx = A.take(Pj * 8); q.bf = A.take(8); q.x0 = A.take(Pj * 8);
     q.bits = (j == 0 && o->record_accepts) ? A.take(C * L * N) : 0;
-    q.vols = A.take((size_t)(mk->dm[j].n_cap + mk->dm[j].n_swp) * 8);
+    size_t max_ni = 1;   // the RMSE of every market's best point reuses market 0's buffer
+    for (const DevMarket& mm : mk->dm) max_ni = std::max<size_t>(max_ni, (size_t)(mm.n_cap + mm.n_swp));
+    q.vols = A.take(max_ni * 8);
     q.rmse = A.take(8);
   }
   if (cudaMalloc(&p->state, A.size) != cudaSuccess) { delete p; return fail(SABR_LMM_ENOMEM, "cudaMalloc of the chain state failed"); }
@@ -705,6 +807,42 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   cudaEventCreate(&p->ev0);
   cudaEventCreate(&p->ev1);
   cudaEventCreate(&p->ev2);
+  // batch mode: several Rebonato markets of one formula, one persistent launch per level
+  bool batchable = nm > 1;
+  for (const DevMarket& m : mk->dm)
+    batchable = batchable && m.model == SABR_LMM_MODEL_REBONATO && m.formula == mk->dm[0].formula;
+  if (batchable) {
+    p->batch = true;
+    uint32_t smax = 0;
+    std::vector<std::pair<long long, int>> cost;
+    for (int j = 0; j < nm; ++j) {
+      const DevMarket& m = mk->dm[j];
+      smax = std::max(smax, o->prec == SABR_LMM_FP64 ? smem_bytes_cta<double>(m) : smem_bytes_cta<float>(m));
+      cost.push_back({-(long long)(m.n_cap + 4 * m.n_swp + 60 * m.n_swap), j});
+    }
+    std::sort(cost.begin(), cost.end());
+    std::vector<int> order;
+    for (auto& c : cost) order.push_back(c.second);
+    if (smax > 227 * 1024) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOTSUP, "a batch market does not fit in one CTA's shared memory at this precision"); }
+    p->bsmem = smax;
+    Arena B;
+    const size_t o_mk = B.take(nm * sizeof(DevMarket)), o_st = B.take(nm * sizeof(SAState)),
+                 o_sp = B.take(nm * sizeof(SAParams)), o_or = B.take(nm * sizeof(int)),
+                 o_ct = B.take((size_t)o->n_levels * sizeof(unsigned int));
+    if (cudaMalloc(&p->batch_buf, B.size) != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOMEM, "cudaMalloc of the batch tables failed"); }
+    char* bb = (char*)p->batch_buf;
+    p->ba.mk = (const DevMarket*)(bb + o_mk);
+    p->ba.st = (const SAState*)(bb + o_st);
+    p->ba.sp = (const SAParams*)(bb + o_sp);
+    p->ba.order = (const int*)(bb + o_or);
+    p->ba.item_ctr = (unsigned int*)(bb + o_ct);
+    p->ba.n_markets = nm;
+    p->ba.C = o->n_chains;
+    cudaMemcpyAsync(bb + o_mk, mk->dm.data(), nm * sizeof(DevMarket), cudaMemcpyHostToDevice, p->stream);
+    cudaMemcpyAsync(bb + o_st, p->st.data(), nm * sizeof(SAState), cudaMemcpyHostToDevice, p->stream);
+    cudaMemcpyAsync(bb + o_sp, p->sp.data(), nm * sizeof(SAParams), cudaMemcpyHostToDevice, p->stream);
+    cudaMemcpyAsync(bb + o_or, order.data(), nm * sizeof(int), cudaMemcpyHostToDevice, p->stream);
+  }
   if (o->lm_top_k > 0) {
     Arena B;
     for (int j = 0; j < nm; ++j) {
@@ -715,8 +853,12 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     }
     if (cudaMalloc(&p->lm_buf, B.size) != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOMEM, "cudaMalloc of the polish buffers failed"); }
   }
-  for (int j = 0; j < nm; ++j) {
+  for (int j = 0; j < nm && !p->batch; ++j) {
     cudaError_t e = enqueue_anneal(mk->dm[j], o->prec, p->st[j], p->sp[j], p->W, p->grid, p->stream, true);
+    if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, std::string("configure: ") + cudaGetErrorString(e)); }
+  }
+  if (p->batch) {
+    cudaError_t e = enqueue_batch(p, p->stream, 256, 1, 0, true);
     if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, std::string("configure: ") + cudaGetErrorString(e)); }
   }
   for (int j = 0; j < nm; ++j) {
@@ -726,6 +868,20 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   }
   cudaError_t e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, cudaGetErrorString(e)); }
+  if (p->batch) {
+    if (o->warps_per_block > 0) {
+      p->bthreads = o->warps_per_block >= 8 ? 256 : 128;
+      int dev = 0, nsm = 148, per_sm = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (o->prec == SABR_LMM_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<double, 0>, p->bthreads, p->bsmem);
+      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<float, 0>, p->bthreads, p->bsmem);
+      p->bgrid = nsm * std::max(per_sm, 1);
+    } else {
+      sabr_lmm_status st = tune_batch(p, p->stream);
+      if (st != SABR_LMM_OK) { sabr_lmm_anneal_plan_free(p); return st; }
+    }
+  }
   *out = p;
   return SABR_LMM_OK;
 }
@@ -834,6 +990,7 @@ extern "C" void sabr_lmm_anneal_plan_free(sabr_lmm_anneal_plan* p) {
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->ev2) cudaEventDestroy(p->ev2);
   if (p->lm_buf) cudaFree(p->lm_buf);
+  if (p->batch_buf) cudaFree(p->batch_buf);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   if (p->state) cudaFree(p->state);
   delete p;

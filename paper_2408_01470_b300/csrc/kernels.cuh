@@ -541,6 +541,8 @@ __device__ bool stage_to_smem3(void* d0, const void* g0, uint32_t b0, void* d1, 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // earlier generic-proxy reads of the destination (a previous market) precede the async writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(b0 + b1 + b2) : "memory");
     bulk_g2s(d0, g0, b0, bar);
     bulk_g2s(d1, g1, b1, bar);
@@ -564,6 +566,8 @@ __device__ bool stage_to_smem3(void* d0, const void* g0, uint32_t b0, void* d1, 
     __syncthreads();
     return false;
   }
+  // every thread has seen the phase complete: the barrier may be re-initialised by a later stage
+  if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
   return true;
 }
 
@@ -615,18 +619,16 @@ __global__ void __launch_bounds__(256) sa_start_cta_kernel(DevMarket m, SAState 
   }
 }
 
+// One chain of one market at one temperature level, run by the whole CTA (markets with swaptions
+// and the batch).  The chain's end state is written; the CTA that finishes the market's last chain
+// (counted on st.counter, n_chains arrivals) takes the minimum over the market's chains and sets
+// the next start point and the level trace.
 template <class R, int FORMULA>
-__global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState st, SAParams sp, int level) {
+__device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAParams& sp, int c, int level,
+                                const CtaSmemS<R>& cs, const InstrView<R>& capB, const InstrView<R>& swpB,
+                                const CtaScratch<R>& sc, unsigned long long* s_wacc, bool* s_last) {
   typedef typename ObjOf<R>::T O;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ unsigned long long s_wacc;
-  CtaSmemS<R> cs = carve_cta<R>(smem, m);
-  if (!stage_market_cta<R>(cs, m)) return;
-  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
-  const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
-  CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = blockIdx.x;   // one chain per CTA
   const int P = sp.P;
   const double T0 = st.T0[0];
   double T = T0;
@@ -663,11 +665,11 @@ __global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState 
       if (lane < P && freek) y = neighbour(x, lo, hi, (R)sf, word);
       if (lane < kMaxParam) sc.xs[lane] = lane < P ? y : R(0);
       const uint64_t wacc = __shfl_sync(0xffffffffu, word, P);
-      if (lane == 0) s_wacc = wacc;
+      if (lane == 0) *s_wacc = wacc;
     }
     __syncthreads();
     const O fy = cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr);
-    const bool acc = metropolis(fy, f, (uint64_t)s_wacc, T, invT);
+    const bool acc = metropolis(fy, f, (uint64_t)*s_wacc, T, invT);
     if (acc) {
       x = y;
       f = fy;
@@ -686,19 +688,18 @@ __global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState 
   }
   __threadfence();
   __syncthreads();
-  __shared__ bool last;
   if (threadIdx.x == 0) {
-    st.part_f[blockIdx.x] = obj_to_double(f);
-    st.part_c[blockIdx.x] = c;
+    st.part_f[c] = obj_to_double(f);
+    st.part_c[c] = c;
     __threadfence();
     const unsigned int ticket = atomicAdd(st.counter, 1u);
-    last = (ticket == gridDim.x - 1);
+    *s_last = (ticket == (unsigned)sp.C - 1);
   }
   __syncthreads();
-  if (!last) return;
+  if (!*s_last) return;
   double bf = __longlong_as_double(0x7ff0000000000000LL);
   int bc = 0x7fffffff;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = threadIdx.x; b < sp.C; b += blockDim.x) {
     const double pf = __ldcg(st.part_f + b);
     const int pc = __ldcg(st.part_c + b);
     if (lex_less(pf, pc, bf, bc)) { bf = pf; bc = pc; }
@@ -722,8 +723,126 @@ __global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState 
   const int cbest = cs.red_c[0];
   if (threadIdx.x < (unsigned)P) st.xs[threadIdx.x] = __ldcg(st.xe + (size_t)cbest * P + threadIdx.x);
   if (threadIdx.x == 0) st.counter[0] = 0u;
+  __syncthreads();
 }
 
+template <class R, int FORMULA>
+__global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState st, SAParams sp, int level) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned long long s_wacc;
+  __shared__ bool s_last;
+  CtaSmemS<R> cs = carve_cta<R>(smem, m);
+  if (!stage_market_cta<R>(cs, m)) return;
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
+  CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
+  cta_chain_level<R, FORMULA>(m, st, sp, blockIdx.x, level, cs, capB, swpB, sc, &s_wacc, &s_last);
+}
+
+// ====================================================================== batch of markets
+// A persistent launch per temperature level over every (market, chain) work item of a batch.  CTAs
+// take items from an atomic counter, markets in the given order (largest first); a CTA re-stages
+// the market's blocks only when its next item belongs to another market.  Each market keeps its
+// own chain state and its own best-chain reduction (cta_chain_level).
+struct BatchArgs {
+  const DevMarket* mk;      // [n_markets]
+  const SAState* st;        // [n_markets]
+  const SAParams* sp;       // [n_markets]
+  const int* order;         // [n_markets] processing order
+  int n_markets;
+  int C;                    // chains per market (the same for every market)
+  unsigned int* item_ctr;   // [n_levels] work counters, zero at the start of the search
+};
+
+template <class R, int FORMULA>
+__global__ void __launch_bounds__(256) sa_level_batch_kernel(BatchArgs ba, int level) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ DevMarket sm_m;
+  __shared__ SAState sm_st;
+  __shared__ SAParams sm_sp;
+  __shared__ unsigned long long s_wacc;
+  __shared__ bool s_last;
+  __shared__ int s_item;
+  int cur = -1;
+  const long long total = (long long)ba.n_markets * ba.C;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(ba.item_ctr + level, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int j = ba.order[item / ba.C], c = item % ba.C;
+    if (j != cur) {
+      if (threadIdx.x == 0) { sm_m = ba.mk[j]; sm_st = ba.st[j]; sm_sp = ba.sp[j]; }
+      __syncthreads();
+      CtaSmemS<R> cs0 = carve_cta<R>(smem, sm_m);
+      if (!stage_market_cta<R>(cs0, sm_m)) return;
+      cur = j;
+    }
+    const DevMarket& m = sm_m;
+    CtaSmemS<R> cs = carve_cta<R>(smem, m);
+    const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+    const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
+    CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
+    cta_chain_level<R, FORMULA>(m, sm_st, sm_sp, c, level, cs, capB, swpB, sc, &s_wacc, &s_last);
+  }
+}
+
+// f(x0), T0 and the first start point of every market of the batch (one CTA per market).
+template <class R, int FORMULA>
+__global__ void __launch_bounds__(256) sa_start_batch_kernel(BatchArgs ba) {
+  typedef typename ObjOf<R>::T O;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ DevMarket sm_m;
+  const int j = blockIdx.x;
+  if (threadIdx.x == 0) sm_m = ba.mk[j];
+  __syncthreads();
+  const DevMarket& m = sm_m;
+  const SAState st = ba.st[j];
+  const SAParams sp = ba.sp[j];
+  CtaSmemS<R> cs = carve_cta<R>(smem, m);
+  if (!stage_market_cta<R>(cs, m)) return;
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
+  CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
+  const double x0 = threadIdx.x < (unsigned)sp.P ? (double)(R)sp.x0[threadIdx.x] : 0.0;
+  if (threadIdx.x < kMaxParam) sc.xs[threadIdx.x] = (R)x0;
+  __syncthreads();
+  const double f0 = obj_to_double(cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr));
+  if (threadIdx.x < (unsigned)sp.P) st.xs[threadIdx.x] = x0;
+  if (threadIdx.x == 0) {
+    st.fs[0] = f0;
+    st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
+    st.counter[0] = 0u;
+  }
+}
+
+// The best point ever accepted in each market of the batch (one CTA per market).
+__global__ void sa_final_batch_kernel(BatchArgs ba) {
+  const SAState st = ba.st[blockIdx.x];
+  const SAParams sp = ba.sp[blockIdx.x];
+  __shared__ double sf[32];
+  __shared__ int sc[32];
+  double bf = __longlong_as_double(0x7ff0000000000000LL);
+  int bc = 0x7fffffff;
+  for (int c = threadIdx.x; c < sp.C; c += blockDim.x)
+    if (lex_less(st.fb[c], c, bf, bc)) { bf = st.fb[c]; bc = c; }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double of = __shfl_xor_sync(0xffffffffu, bf, off);
+    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+    if (lex_less(of, oc, bf, bc)) { bf = of; bc = oc; }
+  }
+  if (lane == 0) { sf[warp] = bf; sc[warp] = bc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (lex_less(sf[w], sc[w], sf[0], sc[0])) { sf[0] = sf[w]; sc[0] = sc[w]; }
+    st.best_f[0] = sf[0];
+  }
+  __syncthreads();
+  if (threadIdx.x < (unsigned)sp.P) st.best_x[threadIdx.x] = st.xb[(size_t)sc[0] * sp.P + threadIdx.x];
+}
 
 // ====================================================================== adjoint (caplet markets)
 // One warp per point; shared-memory plan: [caplet block][quadrature table]

@@ -1,0 +1,43 @@
+"""The batch path (S11): several uneven markets annealed by one persistent launch per temperature
+level.  Each market keeps its own Philox stream (market index in the counter), chain state and
+best-chain reduction, so in FP64 every market reproduces the oracle's search run with its index.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_01470_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(js):
+    import paper_2408_01470_b300 as lib
+    sks = [synth.batch_market(j) for j in js]
+    oms, vols = zip(*[oracle.quoted_market(sk) for sk in sks])
+    return sks, oms, lib.Market(list(sks), list(vols))
+
+
+@pytest.mark.parametrize("wpb", [0, 8])
+def test_batch_fp64_reproduces_each_market_search(gpu_lib, wpb):
+    sks, oms, gm = _batch([0, 1, 2, 5])
+    C, L, N = 16, 3, 4
+    r = gm.anneal(C, L, N, 0.9, seed=77, prec="fp64", record_accepts=True, warps_per_block=wpb)
+    for j, om in enumerate(oms):
+        ro = om.anneal(C, L, N, 0.9, seed=77, market_index=j, n_threads=8, want_bits=(j == 0))
+        assert np.allclose(r["trace_f"][j], ro["trace_f"], rtol=1e-11, atol=0), j
+        assert np.allclose(r["x_best"][j], ro["x_best"], rtol=1e-12, atol=1e-15), j
+        assert r["f_best"][j] == pytest.approx(ro["f_best"], rel=1e-11)
+        if j == 0:
+            assert np.array_equal(r["bits"], ro["bits"])
+    assert r["n_evals"] == C * (L * N + 1)
+
+
+def test_batch_fp32_runs_every_market(gpu_lib):
+    sks, oms, gm = _batch(list(range(12)))
+    r = gm.anneal(64, 4, 8, 0.9, seed=3, prec="fp32")
+    for j, om in enumerate(oms):
+        f0 = om.objective(sks[j].box_centre())
+        assert np.isfinite(r["f_best"][j])
+        assert r["f_best"][j] <= f0
+        assert om.objective(r["x_best"][j]) == pytest.approx(r["f_best"][j], rel=1e-3)
