@@ -135,6 +135,33 @@ def barrier(ws: int):
         dist.barrier()
 
 
+WORKLOADS = {
+    "caplets": "rebonato_caplets_20fwd_x_15k_4096ch_x_200T_x_100steps",
+    "joint": "rebonato_joint_40fwd_300caplets_700swaptions_16384ch_x_200T_x_100steps",
+    "batch": "rebonato_batch_256_markets_10to60fwd_50to1000instr_4096ch_x_100T_x_50steps",
+}
+
+
+def workload_markets(lib, name):
+    """(Market, skeletons, vols list, chains, levels, steps, cooling) of a named workload."""
+    from paper_2408_01470_b300 import synth
+    if name == "caplets":
+        sks = [synth.caplet_term_structure()]
+    elif name == "joint":
+        sks = [synth.joint_caplet_swaption()]
+    else:
+        sks = [synth.batch_market(j) for j in range(256)]
+    vols = []
+    for sk in sks:
+        placeholder = lib.Market(sk, np.full(sk.n_instr, 0.2))
+        v = placeholder.model_vols(sk.theta_true, "fp64").cpu().numpy()[0]
+        del placeholder
+        vols.append(v + sk.noise)
+    gm = lib.Market(sks, vols) if len(sks) > 1 else lib.Market(sks[0], vols[0])
+    s0 = sks[0]
+    return gm, sks, vols, s0.n_chains, s0.n_levels, s0.steps, s0.cooling
+
+
 def market_from_library(lib, skel):
     """Quotes for the bench made by the library itself: model vols at the generating point + noise."""
     import torch
@@ -195,17 +222,18 @@ def run_profile(args):
     import paper_2408_01470_b300 as lib
     from paper_2408_01470_b300 import synth
     lib.load()
-    skel = synth.caplet_term_structure()
-    gm, _ = market_from_library(lib, skel)
-    L = args.levels or skel.n_levels
+    gm, sks, _, C, L0, N, cooling = workload_markets(lib, args.workload)
+    L = args.levels or L0
     s = torch.cuda.Stream()
-    plan = gm.anneal_prepare(skel.n_chains, L, skel.steps, skel.cooling, 240801470, prec=args.prec,
+    plan = gm.anneal_prepare(C, L, N, cooling, 240801470, prec=args.prec,
                              use_graph=False, stream=s, warps_per_block=args.warps_per_block)
     for _ in range(2):
         plan.launch(stream=s)
         r = plan.fetch()
-    print(json.dumps({"profile": True, "levels": L, "prec": args.prec, "f_best": float(r["f_best"][0]),
-                      "seconds": r["seconds"]}))
+    prices = sum(sk.n_instr for sk in sks) * r["n_evals"]
+    print(json.dumps({"profile": True, "workload": args.workload, "levels": L, "prec": args.prec,
+                      "f_best": float(r["f_best"][0]), "seconds": r["seconds"],
+                      "prices_per_s": prices / r["seconds"], "ms_per_level": 1e3 * r["seconds"] / L}))
 
 
 def main():
@@ -222,6 +250,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run the workload's search once (optionally shortened) and exit: the ncu target")
     ap.add_argument("--levels", type=int, default=0, help="with --profile: temperature levels (0 = workload's)")
+    ap.add_argument("--workload", default="caplets", choices=list(WORKLOADS),
+                    help="with --profile: the search to run (the timed line is always the caplet workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
