@@ -390,10 +390,14 @@ cudaError_t launch_objective_r(const DevMarket& m, const double* X, long long n,
   return m.formula == 0 ? launch_objective<R, 1, 0>(m, X, n, f, vols, s) : launch_objective<R, 1, 1>(m, X, n, f, vols, s);
 }
 
-template <class R, int FORMULA>
+// The tensor-core contraction of the pair Grams applies when the panel tables fit one MMA tile.
+bool tc_eligible(const DevMarket& m) { return m.n_swp > 0 && m.NA <= 64 && m.ND <= 27; }
+bool use_tc(const DevMarket& m, int prec) { return prec == SABR_LMM_FP32_BF16X3 && tc_eligible(m); }
+
+template <class R, int FORMULA, bool TC>
 cudaError_t launch_objective_cta(const DevMarket& m, const double* X, long long n, double* f, double* vols, cudaStream_t s) {
-  const uint32_t sm = smem_bytes_cta<R>(m);
-  auto kern = objective_cta_kernel<R, FORMULA>;
+  const uint32_t sm = smem_bytes_cta<R>(m, TC);
+  auto kern = objective_cta_kernel<R, FORMULA, TC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   long long blocks = n < 148 * 16 ? n : 148 * 16;
@@ -406,8 +410,10 @@ cudaError_t launch_objective_any(const DevMarket& m, int prec, const double* X, 
                                  cudaStream_t s) {
   if (m.n_swp > 0) {
     if (prec == SABR_LMM_FP64)
-      return m.formula == 0 ? launch_objective_cta<double, 0>(m, X, n, f, vols, s) : launch_objective_cta<double, 1>(m, X, n, f, vols, s);
-    return m.formula == 0 ? launch_objective_cta<float, 0>(m, X, n, f, vols, s) : launch_objective_cta<float, 1>(m, X, n, f, vols, s);
+      return m.formula == 0 ? launch_objective_cta<double, 0, false>(m, X, n, f, vols, s) : launch_objective_cta<double, 1, false>(m, X, n, f, vols, s);
+    if (use_tc(m, prec))
+      return m.formula == 0 ? launch_objective_cta<float, 0, true>(m, X, n, f, vols, s) : launch_objective_cta<float, 1, true>(m, X, n, f, vols, s);
+    return m.formula == 0 ? launch_objective_cta<float, 0, false>(m, X, n, f, vols, s) : launch_objective_cta<float, 1, false>(m, X, n, f, vols, s);
   }
   return prec == SABR_LMM_FP64 ? launch_objective_r<double>(m, X, n, f, vols, s)
                                : launch_objective_r<float>(m, X, n, f, vols, s);
@@ -416,7 +422,7 @@ cudaError_t launch_objective_any(const DevMarket& m, int prec, const double* X, 
 // Shared memory a market needs per CTA in the given precision (the caller checks it against the
 // device's opt-in limit).
 uint32_t market_smem(const DevMarket& m, int prec) {
-  if (m.n_swp > 0) return prec == SABR_LMM_FP64 ? smem_bytes_cta<double>(m) : smem_bytes_cta<float>(m);
+  if (m.n_swp > 0) return prec == SABR_LMM_FP64 ? smem_bytes_cta<double>(m) : smem_bytes_cta<float>(m, use_tc(m, prec));
   return prec == SABR_LMM_FP64 ? smem_bytes<double>(m, 4) : smem_bytes<float>(m, 4);
 }
 
@@ -427,6 +433,10 @@ sabr_lmm_status check_call(const sabr_lmm_market* m, int32_t idx, int64_t n, int
   if (prec < SABR_LMM_FP64 || prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
   if (market_smem(m->dm[idx], prec) > 227 * 1024)
     return fail(SABR_LMM_ENOTSUP, "the market does not fit in one CTA's shared memory at this precision");
+  if (m->dm[idx].n_swp > 0 && prec == SABR_LMM_FP32_TF32X3)
+    return fail(SABR_LMM_ENOTSUP, "the TF32 split contraction is not built; use SABR_LMM_FP32_BF16X3 or SABR_LMM_FP32");
+  if (m->dm[idx].n_swp > 0 && prec == SABR_LMM_FP32_BF16X3 && !tc_eligible(m->dm[idx]))
+    return fail(SABR_LMM_ENOTSUP, "the market's panel tables exceed one tensor-core tile (NA <= 64, ND <= 27)");
   return SABR_LMM_OK;
 }
 
@@ -594,12 +604,12 @@ cudaError_t enqueue_anneal_t(const DevMarket& m, const SAState& st, const SAPara
 }
 
 // Markets with swaptions: one CTA of 256 threads per chain.
-template <class R, int FORMULA>
+template <class R, int FORMULA, bool TC>
 cudaError_t enqueue_anneal_cta_t(const DevMarket& m, const SAState& st, const SAParams& sp, cudaStream_t s,
                                  bool configure_only) {
-  const uint32_t sm = smem_bytes_cta<R>(m);
-  auto k0 = sa_start_cta_kernel<R, FORMULA>;
-  auto k1 = sa_level_cta_kernel<R, FORMULA>;
+  const uint32_t sm = smem_bytes_cta<R>(m, TC);
+  auto k0 = sa_start_cta_kernel<R, FORMULA, TC>;
+  auto k1 = sa_level_cta_kernel<R, FORMULA, TC>;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -615,10 +625,13 @@ cudaError_t enqueue_anneal(const DevMarket& m, int prec, const SAState& st, cons
                            cudaStream_t s, bool configure_only = false) {
   const bool f64 = prec == SABR_LMM_FP64;
   if (m.n_swp > 0) {
-    if (f64) return m.formula == 0 ? enqueue_anneal_cta_t<double, 0>(m, st, sp, s, configure_only)
-                                   : enqueue_anneal_cta_t<double, 1>(m, st, sp, s, configure_only);
-    return m.formula == 0 ? enqueue_anneal_cta_t<float, 0>(m, st, sp, s, configure_only)
-                          : enqueue_anneal_cta_t<float, 1>(m, st, sp, s, configure_only);
+    if (f64) return m.formula == 0 ? enqueue_anneal_cta_t<double, 0, false>(m, st, sp, s, configure_only)
+                                   : enqueue_anneal_cta_t<double, 1, false>(m, st, sp, s, configure_only);
+    if (use_tc(m, prec))
+      return m.formula == 0 ? enqueue_anneal_cta_t<float, 0, true>(m, st, sp, s, configure_only)
+                            : enqueue_anneal_cta_t<float, 1, true>(m, st, sp, s, configure_only);
+    return m.formula == 0 ? enqueue_anneal_cta_t<float, 0, false>(m, st, sp, s, configure_only)
+                          : enqueue_anneal_cta_t<float, 1, false>(m, st, sp, s, configure_only);
   }
 #define DISPATCH(R)                                                                                           \
   if (m.model == 0) return m.formula == 0 ? enqueue_anneal_t<R, 0, 0>(m, st, sp, W, grid, s, configure_only)  \
@@ -744,9 +757,14 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (o->warps_per_block < 0 || o->warps_per_block > 16) return fail(SABR_LMM_EINVAL, "warps_per_block must be in [0, 16]");
   if (o->lm_top_k < 0 || o->lm_top_k > o->n_chains || o->lm_top_k > 1024) return fail(SABR_LMM_EINVAL, "lm_top_k must be in [0, min(n_chains, 1024)]");
   if (o->lm_top_k > 0 && o->lm_max_iter < 0) return fail(SABR_LMM_EINVAL, "lm_max_iter must be >= 0");
-  for (const DevMarket& m : mk->dm)
+  for (const DevMarket& m : mk->dm) {
     if (market_smem(m, o->prec) > 227 * 1024)
       return fail(SABR_LMM_ENOTSUP, "a market does not fit in one CTA's shared memory at this precision");
+    if (m.n_swp > 0 && o->prec == SABR_LMM_FP32_TF32X3)
+      return fail(SABR_LMM_ENOTSUP, "the TF32 split contraction is not built; use SABR_LMM_FP32_BF16X3 or SABR_LMM_FP32");
+    if (m.n_swp > 0 && o->prec == SABR_LMM_FP32_BF16X3 && (!tc_eligible(m) || mk->dm.size() > 1))
+      return fail(SABR_LMM_ENOTSUP, "the tensor-core contraction needs a single market whose panel tables fit one tile");
+  }
   sabr_lmm_anneal_plan* p = new sabr_lmm_anneal_plan();
   p->mk = mk;
   p->opts = *o;

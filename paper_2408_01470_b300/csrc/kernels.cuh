@@ -499,10 +499,17 @@ template <class R> __device__ __forceinline__ const void* swp_block(const DevMar
 template <> __device__ __forceinline__ const void* swp_block<double>(const DevMarket& m) { return m.sblk64; }
 template <> __device__ __forceinline__ const void* swp_block<float>(const DevMarket& m) { return m.sblk32; }
 
+// With tc, the tensor-core operand (kTcBytes), its barrier and the TMEM address slot follow, and the
+// request is at least 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM.
 template <class R>
-__host__ __device__ inline uint32_t smem_bytes_cta(const DevMarket& m) {
-  return instr_block_bytes<R>(m.n_cap_pad) + instr_block_bytes<R>(m.n_swp_pad) + (uint32_t)sizeof(QuadTab<R>) +
-         (uint32_t)cta_scratch_elems(m) * sizeof(R) + 32 * 16 + 512;
+__host__ __device__ inline uint32_t smem_bytes_cta(const DevMarket& m, bool tc = false) {
+  uint32_t b = instr_block_bytes<R>(m.n_cap_pad) + instr_block_bytes<R>(m.n_swp_pad) + (uint32_t)sizeof(QuadTab<R>) +
+               (uint32_t)cta_scratch_elems(m) * sizeof(R) + 32 * 16 + 512;
+  if (tc) {
+    b += kTcBytes + 32;
+    if (b < 80u * 1024u) b = 80u * 1024u;
+  }
+  return b;
 }
 
 template <class R>
@@ -515,6 +522,9 @@ struct CtaSmemS {
   uint64_t* mbar;
   double* red_f;
   int* red_c;
+  unsigned char* tcU;    // tensor-core operand (TC kernels)
+  uint64_t* tc_mbar;
+  uint32_t* tc_slot;
 };
 
 template <class R>
@@ -529,7 +539,40 @@ __device__ __forceinline__ CtaSmemS<R> carve_cta(unsigned char* smem, const DevM
   s.mbar = (uint64_t*)p;
   s.red_f = (double*)(p + 16);
   s.red_c = (int*)(p + 16 + 32 * sizeof(double));
+  s.tcU = p + 512;
+  s.tc_mbar = (uint64_t*)(s.tcU + kTcBytes);
+  s.tc_slot = (uint32_t*)(s.tcU + kTcBytes + 16);
   return s;
+}
+
+// Set up the tensor-core state of a CTA (after staging): completion barrier, TMEM columns, a
+// zeroed operand (its padding rows and columns stay zero).  Every thread calls.
+template <class R>
+__device__ __forceinline__ TcState tc_setup(const CtaSmemS<R>& cs, int* err) {
+  if (threadIdx.x == 0) {
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(cs.tc_mbar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_alloc(cs.tc_slot);
+  for (uint32_t i = threadIdx.x; i < kTcBytes / 16; i += blockDim.x) ((uint4*)cs.tcU)[i] = make_uint4(0, 0, 0, 0);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  TcState tc;
+  tc.U = cs.tcU;
+  tc.tmem = *cs.tc_slot;
+  tc.mbar = cs.tc_mbar;
+  tc.phase = 0;
+  tc.err = err;
+  return tc;
+}
+
+__device__ __forceinline__ void tc_teardown(const TcState& tc) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  tc_dealloc(tc.tmem);
 }
 
 __device__ bool stage_to_smem3(void* d0, const void* g0, uint32_t b0, void* d1, const void* g1, uint32_t b1, void* d2,
@@ -578,13 +621,15 @@ __device__ __forceinline__ bool stage_market_cta(const CtaSmemS<R>& cs, const De
                         cs.mbar, m.err);
 }
 
-template <class R, int FORMULA>
+template <class R, int FORMULA, bool TC>
 __global__ void __launch_bounds__(256) objective_cta_kernel(DevMarket m, const double* __restrict__ X, long long n,
                                                             double* __restrict__ f, double* __restrict__ vols) {
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
   CtaSmemS<R> cs = carve_cta<R>(smem, m);
   if (!stage_market_cta<R>(cs, m)) return;
+  TcState tc{};
+  if (TC) tc = tc_setup<R>(cs, m.err);
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
   CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
@@ -592,41 +637,47 @@ __global__ void __launch_bounds__(256) objective_cta_kernel(DevMarket m, const d
   for (long long i = blockIdx.x; i < n; i += gridDim.x) {
     if (threadIdx.x < kMaxParam) sc.xs[threadIdx.x] = threadIdx.x < m.n_param ? (R)X[i * m.n_param + threadIdx.x] : R(0);
     __syncthreads();
-    const O fi = cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, vols ? vols + i * n_instr : nullptr);
+    const O fi = cta_objective<R, FORMULA, TC>(m, capB, swpB, *cs.quad, sc, (O*)cs.red,
+                                               vols ? vols + i * n_instr : nullptr, &tc);
     if (f && threadIdx.x == 0) f[i] = obj_to_double(fi);
     __syncthreads();
   }
+  if (TC) tc_teardown(tc);
 }
 
-template <class R, int FORMULA>
+template <class R, int FORMULA, bool TC>
 __global__ void __launch_bounds__(256) sa_start_cta_kernel(DevMarket m, SAState st, SAParams sp) {
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
   CtaSmemS<R> cs = carve_cta<R>(smem, m);
   if (!stage_market_cta<R>(cs, m)) return;
+  TcState tc{};
+  if (TC) tc = tc_setup<R>(cs, m.err);
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
   CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
   const double x0 = threadIdx.x < (unsigned)sp.P ? (double)(R)sp.x0[threadIdx.x] : 0.0;
   if (threadIdx.x < kMaxParam) sc.xs[threadIdx.x] = (R)x0;
   __syncthreads();
-  const double f0 = obj_to_double(cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr));
+  const double f0 = obj_to_double(cta_objective<R, FORMULA, TC>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr, &tc));
   if (threadIdx.x < (unsigned)sp.P) st.xs[threadIdx.x] = x0;
   if (threadIdx.x == 0) {
     st.fs[0] = f0;
     st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
     st.counter[0] = 0u;
   }
+  if (TC) tc_teardown(tc);
 }
 
 // One chain of one market at one temperature level, run by the whole CTA (markets with swaptions
 // and the batch).  The chain's end state is written; the CTA that finishes the market's last chain
 // (counted on st.counter, n_chains arrivals) takes the minimum over the market's chains and sets
 // the next start point and the level trace.
-template <class R, int FORMULA>
+template <class R, int FORMULA, bool TC = false>
 __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAParams& sp, int c, int level,
                                 const CtaSmemS<R>& cs, const InstrView<R>& capB, const InstrView<R>& swpB,
-                                const CtaScratch<R>& sc, unsigned long long* s_wacc, bool* s_last) {
+                                const CtaScratch<R>& sc, unsigned long long* s_wacc, bool* s_last,
+                                TcState* tc = nullptr) {
   typedef typename ObjOf<R>::T O;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = sp.P;
@@ -668,7 +719,7 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
       if (lane == 0) *s_wacc = wacc;
     }
     __syncthreads();
-    const O fy = cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr);
+    const O fy = cta_objective<R, FORMULA, TC>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr, tc);
     const bool acc = metropolis(fy, f, (uint64_t)*s_wacc, T, invT);
     if (acc) {
       x = y;
@@ -726,17 +777,20 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
   __syncthreads();
 }
 
-template <class R, int FORMULA>
+template <class R, int FORMULA, bool TC>
 __global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState st, SAParams sp, int level) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned long long s_wacc;
   __shared__ bool s_last;
   CtaSmemS<R> cs = carve_cta<R>(smem, m);
   if (!stage_market_cta<R>(cs, m)) return;
+  TcState tc{};
+  if (TC) tc = tc_setup<R>(cs, m.err);
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
   CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
-  cta_chain_level<R, FORMULA>(m, st, sp, blockIdx.x, level, cs, capB, swpB, sc, &s_wacc, &s_last);
+  cta_chain_level<R, FORMULA, TC>(m, st, sp, blockIdx.x, level, cs, capB, swpB, sc, &s_wacc, &s_last, &tc);
+  if (TC) tc_teardown(tc);
 }
 
 // ====================================================================== batch of markets

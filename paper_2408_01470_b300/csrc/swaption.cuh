@@ -20,6 +20,7 @@
 //     SABR and Black per swaption, with the caplets priced alongside.
 #pragma once
 #include "objective.cuh"
+#include "tcgen05_gram.cuh"
 
 namespace sabr {
 
@@ -156,10 +157,11 @@ __device__ __forceinline__ R price_one_caplet(const InstrView<R>& B, int k, cons
 
 // Objective of the point in cs.xs (every thread of the CTA calls; all return the same value).
 // `red` is shared scratch of 32 objective values.
-template <class R, int FORMULA>
+// TC: the pair Grams of phase 3 on the tensor cores (tcgen05_gram.cuh; FP32 pricing only).
+template <class R, int FORMULA, bool TC = false>
 __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrView<R>& capB, const InstrView<R>& swpB,
                                               const QuadTab<R>& qt, const CtaScratch<R>& cs,
-                                              typename ObjOf<R>::T* red, double* vols) {
+                                              typename ObjOf<R>::T* red, double* vols, TcState* tc = nullptr) {
   typedef typename ObjOf<R>::T O;
   typedef Num<R> M;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
@@ -234,11 +236,45 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const R h2 = E.b * ((ah + bh * base) * t2.a + t2.b) + t2.c;
       v = qt.sw[q] * g * h2;
     }
-    cs.Y[A * YS + k] = v;
+    if (TC) tc_put(*tc, A, k, (float)v);
+    else cs.Y[A * YS + k] = v;
   }
   __syncthreads();
 
   // ---- phase 3: pair sums along the diagonals (raw, then prefix-summed in phase 4)
+  if (TC) {
+    const int N = round_up(NA, 16);
+    tc_gram(*tc, N);
+    // warps 0-3 hold TMEM lanes 0-127: rows 0..63 hi (hi+lo)^T, rows 64..127 lo (hi+lo)^T.
+    // The upper rows go to the raw pair tables, the lower ones to a band buffer (the Y region).
+    R* Tb = cs.Y;
+    if (warp < 4) {
+      const int row = warp * 32 + lane;
+      const bool top = row < 64;
+      const int A = top ? row : row - 64;
+      for (int g = 0; g < 3; ++g) {
+        const int q = g == 0 ? 0 : (g == 1 ? 2 : 1);   // PQ slots: 0 = G, 1 = A-part, 2 = H
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          tc_ld16(tc->tmem + (uint32_t)(g * N + c0) + ((uint32_t)(warp * 32) << 16), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int e = c0 + j - A;
+            if (A < NA && e >= 0 && e < ND && c0 + j < NA) {
+              if (top) cs.PQ[(q * ND + e) * PL + A] = (R)v[j];
+              else Tb[(q * ND + e) * NA + A] = (R)v[j];
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    for (int it = tid; it < 3 * ND * NA; it += nth) {
+      const int q = it / (ND * NA), r = it - q * ND * NA, e = r / NA, A = r - e * NA;
+      if (A + e < NA) cs.PQ[(q * ND + e) * PL + A] += Tb[(q * ND + e) * NA + A];
+    }
+  } else
   for (int it = tid; it < ND * NA; it += nth) {
     const int e = it / NA, A = it - e * NA;
     if (A + e >= NA) continue;
@@ -295,9 +331,13 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     const int Lg = m.grp_L[g], nE = m.grp_nE[g];
     const int* dl = m.grp_delta + g * m.max_gwin;
     const int npk = Lg * (Lg + 1) / 2;
-    for (int t = tid; t < Lg * Lg; t += nth) {
-      const int i = t / Lg, j = t - i * Lg;
-      if (j < i) continue;
+    // B matrices packed by column: pair (i <= j) at j (j + 1) / 2 + i, so the pairs of a swap over
+    // the first L forwards of the group are the first L (L + 1) / 2 entries
+    for (int t = tid; t < npk; t += nth) {
+      int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      if (j * (j + 1) / 2 > t) --j;
+      if ((j + 1) * (j + 2) / 2 <= t) ++j;
+      const int i = t - j * (j + 1) / 2;
       const int e = dl[j] - dl[i];
       const int lo = dl[i], hi = lo + nE;
       const R* PG = cs.PQ + (0 * ND + e) * PL;
@@ -306,10 +346,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const R* PGS = cs.PQ + (3 * ND + e) * PL;
       const R G = PG[hi] - PG[lo];
       const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
-      const int pk = i * Lg - (i * (i - 1)) / 2 + (j - i);
-      cs.Bg[pk] = cs.corr[e] * G;
-      cs.Bg[npk + pk] = cs.corr[e] * cs.corr[ND + e] * X;
-      cs.Bg[2 * npk + pk] = cs.corr[2 * ND + e] * G;
+      cs.Bg[t] = cs.corr[e] * G;
+      cs.Bg[npk + t] = cs.corr[e] * cs.corr[ND + e] * X;
+      cs.Bg[2 * npk + t] = cs.corr[2 * ND + e] * G;
     }
     __syncthreads();
     const int s0 = m.grp_swap0[g], s1 = m.grp_swap0[g + 1];
@@ -318,18 +357,15 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const int L = m.swap_L[s];
       const R* W = Wall + (size_t)s * m.max_win;
       R v1 = 0, v2 = 0, v3 = 0;
-      for (int i = lane; i < L; i += 32) {
-        R r1 = 0, r2 = 0, r3 = 0;
-        const int row = i * Lg - (i * (i - 1)) / 2 - i;
-        for (int j = i; j < L; ++j) {
-          const R wj = (j == i) ? W[j] : R(2) * W[j];
-          r1 += wj * cs.Bg[row + j];
-          r2 += wj * cs.Bg[npk + row + j];
-          r3 += wj * cs.Bg[2 * npk + row + j];
-        }
-        v1 += W[i] * r1;
-        v2 += W[i] * r2;
-        v3 += W[i] * r3;
+      for (int t = lane; t < L * (L + 1) / 2; t += 32) {
+        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        if (j * (j + 1) / 2 > t) --j;
+        if ((j + 1) * (j + 2) / 2 <= t) ++j;
+        const int i = t - j * (j + 1) / 2;
+        const R w = (i == j ? R(1) : R(2)) * W[i] * W[j];
+        v1 += w * cs.Bg[t];
+        v2 += w * cs.Bg[npk + t];
+        v3 += w * cs.Bg[2 * npk + t];
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
