@@ -196,16 +196,10 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
   } else {
     // ---------------- reverse of the mapping: (alpha_i, nu_i) -> (G_i, X_i)
     const int NP = m.NP;
-    if (lane == 0) {
-      R sh = 0, pg = 0;
-      for (int p = 0; p < NP; ++p) {
-        as.SH[p] = sh;
-        as.PG[p] = pg;
-        sh += ws.Hp[p];
-        pg += ws.Gp[p];
-      }
-      as.SH[NP] = sh;
-      as.PG[NP] = pg;
+    // the forward pass leaves inclusive prefix sums over panels in Hp and Gp
+    for (int p = lane; p <= NP; p += 32) {
+      as.SH[p] = p > 0 ? ws.Hp[p - 1] : R(0);
+      as.PG[p] = p > 0 ? ws.Gp[p - 1] : R(0);
     }
     for (int j = lane; j < m.n_capfwd; j += 32) {
       const int i = m.capfwd_list[j];
@@ -225,7 +219,6 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
     const int q = lane & 7, pg = lane >> 3;
     const R wq = qt.w[q];
     const Q4<R> tq = ws.Tq[q];
-    const Q4<R>* t2 = ws.T2 + q * 9;
     R acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0;
@@ -244,38 +237,33 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
         }
       }
       const R base = D * (R)p;
-      const Q2<R> E = ws.Ep[p];
+      Q2<R> E;
+      E.a = Num<R>::exp_(-c * base);
+      E.b = Num<R>::exp_(-gh * base);
       const R u = base + qt.o[q];
       const R eg = E.a * tq.a, eh = E.b * tq.c;      // e^{-c u}, e^{-gamma_h u}
       const R lin_g = a + b * u, lin_h = ah + bh * u;
       const R g = lin_g * eg + d;
       const R h = lin_h * eh + dh;
-      const R ahp = ah + bh * base;
+      const R Rbar = Apb * wq * g * g;
       R Rin = 0;
 #pragma unroll
       for (int r = 0; r < kQ; ++r) {
-        const Q4<R> t = t2[r];
-        const R hr = E.b * (ahp * t.a + t.b) + t.c;
-        Rin += hr * hr;
-      }
-      const R gbar = R(2) * wq * g * (Gpb + Apb * Rin);
-      const R hbar = R(2) * wq * h * Hpb;
-      const R Rbar = Apb * wq * g * g;
-      abcd_bar<R>(gbar, u, eg, lin_g, acc);
-      abcd_bar<R>(hbar, u, eh, lin_h, acc + 4);
-#pragma unroll
-      for (int r = 0; r < kQ; ++r) {
-        // inner node v = base + o2: hr = sqrt(w2) h(v); R = sum hr^2, so h(v)_bar = 2 Rbar w2 h(v)
-        const Q4<R> t = t2[r];
+        // inner node v = base + o2: R = sum w2 h(v)^2, so h(v)_bar = 2 Rbar w2 h(v)
         const R o2 = qt.o2[q * kQ + r];
         const R sw2 = qt.sw2[q * kQ + r];
         const R v = base + o2;
-        const R ev = E.b * (sw2 > R(0) ? t.a / sw2 : R(0));   // e^{-gamma_h v}
+        const R ev = E.b * Num<R>::exp_(-gh * o2);   // e^{-gamma_h v}
         const R lin = ah + bh * v;
         const R hv = lin * ev + dh;
+        Rin += sw2 * sw2 * hv * hv;
         const R hvbar = R(2) * Rbar * sw2 * sw2 * hv;
         abcd_bar<R>(hvbar, v, ev, lin, acc + 4);
       }
+      const R gbar = R(2) * wq * g * (Gpb + Apb * Rin);
+      const R hbar = R(2) * wq * h * Hpb;
+      abcd_bar<R>(gbar, u, eg, lin_g, acc);
+      abcd_bar<R>(hbar, u, eh, lin_h, acc + 4);
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) gacc[k] = (double)acc[k];

@@ -15,8 +15,9 @@
 //       calendar time, reordered.)  Lanes split (panel, node).  With base = pD and a node at
 //       base + o, the exponentials factor as e^{-c(base + o)} = e^{-c base} e^{-c o}, so
 //         g(base + o) = E_g(p) ((a + b base) e_g(o) + b o e_g(o)) + d
-//       and likewise h; the per-node factors e(o), o e(o) (and, for the inner rule, the square
-//       roots of the weights) are tabulated once per evaluation in the warp's scratch.
+//       and likewise h; the per-node factors e(o), o e(o) and, for the inner rule, six weighted
+//       sums per outer node (the square of h expanded in E_h(p)) are tabulated once per
+//       evaluation in the warp's scratch, and the sums over panels are warp prefix scans.
 //   S4  price_caplets : per caplet, SABR vol -> OTM Black price -> vega-weighted residual.
 //   S7  squared residuals summed per lane in the pricing precision; across lanes in FP64 (FP64
 //       path) or in float-float, a 48-bit significand on the FP32 pipes (FP32 path).
@@ -39,7 +40,7 @@ template <class R> struct WarpScratch {
   R* fA3;       // [NFc]
   Q2<R>* Ep;    // [NPc] {e^{-c pD}, e^{-gamma_h pD}}
   Q4<R>* Tq;    // [8]   {e_g(o_q), b o_q e_g(o_q), e_h(o_q), beta_h o_q e_h(o_q)}
-  Q4<R>* T2;    // [8 x 9] inner rule: sqrt(w) {e_h(o2), beta_h o2 e_h(o2), delta_h, 0}
+  Q4<R>* T2;    // [8 x 2]: per outer node, the inner-rule sums {S1..S4}, {S5, S6, -, -}
 };
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -48,7 +49,7 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 // 4 elements (the alignment of Q4<R>).
 __host__ __device__ inline int warp_scratch_elems(int NP, int n_fwd) {
   const int NPc = round_up(NP > 0 ? NP : 1, 4), NFc = round_up(n_fwd, 4);
-  return 16 + 3 * NPc + 4 * NFc + NFc + 2 * NPc + 4 * 8 + 4 * 72;
+  return 16 + 3 * NPc + 4 * NFc + NFc + 2 * NPc + 4 * 8 + 4 * 16;
 }
 
 template <class R>
@@ -80,6 +81,13 @@ __device__ __forceinline__ void put_forward(const WarpScratch<R>& ws, int i, R a
 }
 
 // S2: alpha_i, nu_i of every caplet forward (Rebonato mapping, kappa = 1).
+// The inner rule at outer node q of panel p is R(p, q) = sum_r w_qr h(base + o2_qr)^2 with
+// h(base + o2) = E (a' e_r + b_r) + d_h, E = e^{-gamma_h base}, a' = alpha_h + beta_h base,
+// e_r = e^{-gamma_h o2_qr}, b_r = beta_h o2_qr e_r; expanding the square,
+//   R = E^2 (a'^2 S1 + 2 a' S2 + S3) + 2 E d_h (a' S4 + S5) + d_h^2 S6
+// with the per-node sums S1 = sum w e^2, S2 = sum w e b, S3 = sum w b^2, S4 = sum w e, S5 = sum w b,
+// S6 = sum w, formed once per evaluation.  The per-forward sums over panels come from warp prefix
+// scans: G_i = SG(n_i), X_i = SA(n_i) + SH(n_i) SG(n_i) - SGH(n_i), SGH(n) = sum_{p<n} Gp[p] SH(p+1).
 template <class R>
 __device__ void rebonato_forward_params(const DevMarket& m, const QuadTab<R>& qt, const WarpScratch<R>& ws, int lane) {
   typedef Num<R> M;
@@ -88,16 +96,40 @@ __device__ void rebonato_forward_params(const DevMarket& m, const QuadTab<R>& qt
   const R rho = ws.xs[8];
   const R D = (R)m.panel;
   const int NP = m.NP, NPc = round_up(NP, 4);
-  // per-evaluation tables
-  for (int j = lane; j < kQ * kQ; j += 32) {
-    const R o2 = qt.o2[j], sw = qt.sw2[j];
-    const R e = M::exp_(-gh * o2);
-    Q4<R> t;
-    t.a = sw * e;
-    t.b = sw * bh * o2 * e;
-    t.c = sw * dh;
-    t.d = R(0);
-    ws.T2[(j >> 3) * 9 + (j & 7)] = t;
+  // inner-rule sums: lane -> node q = lane / 4, inner nodes r = lane % 4 and lane % 4 + 4
+  {
+    const int q = lane >> 2, r0 = lane & 3;
+    R s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0, s6 = 0;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int j = q * kQ + r0 + 4 * h2;
+      const R o2 = qt.o2[j], sw = qt.sw2[j];
+      const R w = sw * sw;
+      const R e = M::exp_(-gh * o2);
+      const R bb = bh * o2 * e;
+      s1 += w * e * e;
+      s2 += w * e * bb;
+      s3 += w * bb * bb;
+      s4 += w * e;
+      s5 += w * bb;
+      s6 += w;
+    }
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+      s3 += __shfl_xor_sync(0xffffffffu, s3, off);
+      s4 += __shfl_xor_sync(0xffffffffu, s4, off);
+      s5 += __shfl_xor_sync(0xffffffffu, s5, off);
+      s6 += __shfl_xor_sync(0xffffffffu, s6, off);
+    }
+    if (r0 == 0) {
+      Q4<R> t;
+      t.a = s1; t.b = s2; t.c = s3; t.d = s4;
+      ws.T2[2 * q] = t;
+      t.a = s5; t.b = s6; t.c = R(0); t.d = R(0);
+      ws.T2[2 * q + 1] = t;
+    }
   }
   if (lane < kQ) {
     const R o = qt.o[lane];
@@ -120,7 +152,7 @@ __device__ void rebonato_forward_params(const DevMarket& m, const QuadTab<R>& qt
   const int q = lane & 7, pg = lane >> 3;
   const R wq = qt.w[q];
   const Q4<R> tq = ws.Tq[q];
-  const Q4<R>* t2 = ws.T2 + q * 9;
+  const Q4<R> S14 = ws.T2[2 * q], S56 = ws.T2[2 * q + 1];
   for (int p = pg; p < NPc; p += 4) {
     R G = 0, H = 0, A = 0;
     if (p < NP) {
@@ -129,13 +161,8 @@ __device__ void rebonato_forward_params(const DevMarket& m, const QuadTab<R>& qt
       const R g = E.a * ((a + b * base) * tq.a + tq.b) + d;
       const R ahp = ah + bh * base;
       const R h = E.b * (ahp * tq.c + tq.d) + dh;
-      R Rin = 0;
-#pragma unroll
-      for (int r = 0; r < kQ; ++r) {
-        const Q4<R> t = t2[r];
-        const R hr = E.b * (ahp * t.a + t.b) + t.c;   // sqrt(w_r) h at the inner node
-        Rin += hr * hr;
-      }
+      const R Rin = E.b * E.b * (ahp * (ahp * S14.a + R(2) * S14.b) + S14.c) +
+                    R(2) * E.b * dh * (ahp * S14.d + S56.a) + dh * dh * S56.b;
       const R gw = wq * g * g;
       G = gw;
       H = wq * h * h;
@@ -150,18 +177,48 @@ __device__ void rebonato_forward_params(const DevMarket& m, const QuadTab<R>& qt
     if (q == 0 && p < NP) { ws.Gp[p] = G; ws.Hp[p] = H; ws.Ap[p] = A; }
   }
   __syncwarp();
+  // inclusive prefix scans over panels, in place: Gp -> SG, Ap -> SA, Hp -> SH, and SGH in Ep's slot
+  R cg = 0, ca = 0, chh = 0, cgs = 0;
+  for (int c0 = 0; c0 < NP; c0 += 32) {
+    const int p = c0 + lane;
+    const bool in = p < NP;
+    const R g = in ? ws.Gp[p] : R(0), ap = in ? ws.Ap[p] : R(0), hh = in ? ws.Hp[p] : R(0);
+    R ig = g, ia = ap, ih = hh;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const R og = __shfl_up_sync(0xffffffffu, ig, off);
+      const R oa = __shfl_up_sync(0xffffffffu, ia, off);
+      const R oh = __shfl_up_sync(0xffffffffu, ih, off);
+      if (lane >= off) { ig += og; ia += oa; ih += oh; }
+    }
+    ih += chh;
+    R igs = g * ih;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const R o2 = __shfl_up_sync(0xffffffffu, igs, off);
+      if (lane >= off) igs += o2;
+    }
+    __syncwarp();
+    if (in) {
+      ws.Gp[p] = cg + ig;
+      ws.Ap[p] = ca + ia;
+      ws.Hp[p] = ih;
+      ((R*)ws.Ep)[p] = cgs + igs;
+    }
+    cg += __shfl_sync(0xffffffffu, ig, 31);
+    ca += __shfl_sync(0xffffffffu, ia, 31);
+    chh = __shfl_sync(0xffffffffu, ih, 31);
+    cgs += __shfl_sync(0xffffffffu, igs, 31);
+  }
+  __syncwarp();
   for (int j = lane; j < m.n_capfwd; j += 32) {
     const int i = m.capfwd_list[j];
     const int n = m.fwd_np[i];
     const R Ti = (R)m.T[i];
-    R G = 0, X = 0, S = 0;
-    for (int p = n - 1; p >= 0; --p) {
-      X += ws.Ap[p] + ws.Gp[p] * S;
-      G += ws.Gp[p];
-      S += ws.Hp[p];
-    }
+    const R G = ws.Gp[n - 1];
+    const R X = ws.Ap[n - 1] + ws.Hp[n - 1] * G - ((const R*)ws.Ep)[n - 1];
     const R al = M::sqrt_(G / Ti);
-    put_forward<R>(ws, i, al, M::sqrt_(R(2) * X) / (al * Ti), rho);
+    put_forward<R>(ws, i, al, M::sqrt_(R(2) * (X > R(0) ? X : R(0))) / (al * Ti), rho);
   }
   __syncwarp();
 }
