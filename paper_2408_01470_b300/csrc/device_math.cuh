@@ -33,6 +33,54 @@ template <> struct Num<float> {
   static constexpr float zx_series = 1e-3f;  // series error O(z^3) < 2^-24 there
 };
 
+// ------------------------------------------------------------------ FP32 approximations
+// The FP32 path uses the hardware approximations of PTX (rcp, rsqrt, ex2 .approx.ftz: about 1-2
+// ulp, denormal inputs and results flushed to zero) where its error budget allows.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// e^x = 2^(x log2 e); the rounding of x log2 e adds |x| 2^-24 to the relative error.
+__device__ __forceinline__ float exp_approx(float x) { return ex2_approx(x * 1.44269504088896341f); }
+
+// log1p(y) for y >= 0 in FP32, by argument reduction and the atanh series (the textbook method,
+// e.g. J.-M. Muller, Elementary Functions, ch. 11): with u = 1 + y = 2^k m, m in [0.75, 1.5),
+// f = m - 1 (f = y, k = 0 when y < 0.5, so no rounding of u enters there),
+//   log1p(y) = k ln 2 + 2 atanh(s),  s = f / (2 + f),  |s| <= 0.2,
+//   2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9) + O(s^11),
+// the truncation below 1e-8 relative.  For y >= 0.5 the rounding of u costs at most
+// 2^-24 / log(1.5) = 1.5e-7 relative; with the FP32 roundings of the steps the result stays
+// within 2.3e-7 relative of log1p(y) (checked in FP32 arithmetic over y in [1e-8, 1e6]).
+__device__ __forceinline__ float log1p_pos(float y) {
+  const float u = 1.0f + y;
+  const unsigned bits = __float_as_uint(u);
+  const unsigned k = (bits - 0x3f400000u) >> 23;        // 2^k * 0.75 <= u < 2^k * 1.5 (u >= 1)
+  const bool small = y < 0.5f;
+  const float f = small ? y : __uint_as_float(bits - (k << 23)) - 1.0f;
+  const float kf = small ? 0.0f : (float)k;
+  const float s = f * rcp_approx(2.0f + f);
+  const float s2 = s * s;
+  float p = fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f);
+  p = fmaf(s2, p, 1.0f / 5.0f);
+  p = fmaf(s2, p, 1.0f / 3.0f);
+  p = fmaf(s2, p, 1.0f);
+  const float ln2_hi = 0.693145751953125f, ln2_lo = 1.42860682030941723212e-6f;
+  // (y - y) is 0 for finite y and NaN otherwise: an infinite or NaN argument (an overflowed z)
+  // must not come back finite
+  return fmaf(kf, ln2_hi, fmaf(kf, ln2_lo, 2.0f * s * p)) + (y - y);
+}
+
 // ------------------------------------------------------------------ Philox4x64-10
 struct U4 { uint64_t v[4]; };
 
@@ -110,21 +158,71 @@ template <class R> __device__ __forceinline__ R ncdf(R x);
 template <> __device__ __forceinline__ double ncdf<double>(double x) {
   return 0.5 * erfc(-x * 0.70710678118654752440);
 }
+// Coefficient of t^j in the fitted exponent P(t) (csrc/gen_erfc_fit.py).
+__host__ __device__ constexpr float erfc_fit(int j) {
+  return j == 0 ? -1.265476212e+00f : j == 1 ? +9.992080434e-01f : j == 2 ? +3.816971254e-01f :
+         j == 3 ? +5.818804080e-02f : j == 4 ? -6.786663929e-02f : j == 5 ? +4.935479974e-02f :
+         j == 6 ? -8.523480751e-01f : j == 7 ? +1.273531464e+00f : j == 8 ? -7.302618493e-01f :
+                  +1.539733566e-01f;
+}
 template <> __device__ __forceinline__ float ncdf<float>(float x) {
   const float y = fabsf(x) * 0.70710678f;
-  const float t = __fdividef(1.0f, fmaf(0.5f, y, 1.0f));
-  float p = +1.539733566e-01f;
-  p = fmaf(p, t, -7.302618493e-01f);
-  p = fmaf(p, t, +1.273531464e+00f);
-  p = fmaf(p, t, -8.523480751e-01f);
-  p = fmaf(p, t, +4.935479974e-02f);
-  p = fmaf(p, t, -6.786663929e-02f);
-  p = fmaf(p, t, +5.818804080e-02f);
-  p = fmaf(p, t, +3.816971254e-01f);
-  p = fmaf(p, t, +9.992080434e-01f);
-  p = fmaf(p, t, -1.265476212e+00f);
-  const float half_erfc = 0.5f * t * __expf(fmaf(-y, y, p));
+  const float t = rcp_approx(fmaf(0.5f, y, 1.0f));
+  float p = erfc_fit(9);
+#pragma unroll
+  for (int j = 8; j >= 0; --j) p = fmaf(p, t, erfc_fit(j));
+  const float half_erfc = 0.5f * t * exp_approx(fmaf(-y, y, p));
   return x < 0.0f ? half_erfc : 1.0f - half_erfc;
+}
+
+// ------------------------------------------------------------------ packed FP32 pairs
+// Blackwell issues add, mul and fma on a pair of FP32 values in a register pair (.f32x2) as one
+// instruction.  The FP32 pricer carries two instruments per lane through these; the hardware
+// approximations (rcp, rsqrt, ex2) and the selects act on each half.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrt_approx(a.x), rsqrt_approx(a.y)); }
+__device__ __forceinline__ float2 ex2_2(float2 a) { return make_float2(ex2_approx(a.x), ex2_approx(a.y)); }
+__device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
+  return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+
+// log1p_pos on a pair.  The bit-level reduction runs on 32-bit scalars: with nvcc 13.0 for
+// sm_103a an arithmetic right shift of the bits of the low half of a packed (.f32x2) result came
+// out unshifted, so u is formed by scalar adds and the shifts are logical (u >= 1).
+__device__ __forceinline__ float2 log1p_pos2(float2 y) {
+  const unsigned bx = __float_as_uint(1.0f + y.x), by = __float_as_uint(1.0f + y.y);
+  const unsigned kx = (bx - 0x3f400000u) >> 23, ky = (by - 0x3f400000u) >> 23;
+  const bool sx = y.x < 0.5f, sy = y.y < 0.5f;
+  const float2 m1 = sub2(make_float2(__uint_as_float(bx - (kx << 23)), __uint_as_float(by - (ky << 23))), bc2(1.0f));
+  const float2 f = sel2(sx, sy, y, m1);
+  const float2 kf = make_float2(sx ? 0.0f : (float)kx, sy ? 0.0f : (float)ky);
+  const float2 s = mul2(f, rcp2(add2(bc2(2.0f), f)));
+  const float2 s2 = mul2(s, s);
+  float2 p = fma2(s2, bc2(1.0f / 9.0f), bc2(1.0f / 7.0f));
+  p = fma2(s2, p, bc2(1.0f / 5.0f));
+  p = fma2(s2, p, bc2(1.0f / 3.0f));
+  p = fma2(s2, p, bc2(1.0f));
+  const float2 r = fma2(kf, bc2(0.693145751953125f), fma2(kf, bc2(1.42860682030941723212e-6f), mul2(add2(s, s), p)));
+  return add2(r, sub2(y, y));
+}
+
+// ncdf<float> on a pair.
+__device__ __forceinline__ float2 ncdf2(float2 x) {
+  const float2 ax = abs2(x);
+  const float2 y = mul2(ax, bc2(0.70710678f));
+  const float2 yn = mul2(ax, bc2(-0.70710678f));
+  const float2 t = rcp2(fma2(bc2(0.5f), y, bc2(1.0f)));
+  float2 p = bc2(erfc_fit(9));
+#pragma unroll
+  for (int j = 8; j >= 0; --j) p = fma2(p, t, bc2(erfc_fit(j)));
+  const float2 e = mul2(t, ex2_2(mul2(fma2(yn, y, p), bc2(1.44269504088896341f))));   // erfc(y)
+  return sel2(x.x < 0.0f, x.y < 0.0f, mul2(e, bc2(0.5f)), fma2(e, bc2(-0.5f), bc2(1.0f)));
 }
 
 // Out-of-the-money Black price with sgn = +1 (call, K >= F) or -1 (put, K < F):

@@ -165,10 +165,12 @@ template <> __device__ __forceinline__ const void* quad_block<float>(const DevMa
 
 // Shared-memory plan: [caplet block][quadrature table][warp scratch x W][mbarrier (16 B),
 // 32 doubles, 32 ints].  Every region starts on a 16-byte boundary.
+constexpr uint32_t kRngBytesPerWarp = 32 * 4 * sizeof(uint64_t);
+
 template <class R>
 __host__ __device__ inline uint32_t smem_bytes(const DevMarket& m, int W) {
   return instr_block_bytes<R>(m.n_cap_pad) + (uint32_t)sizeof(QuadTab<R>) +
-         (uint32_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R) + 512;
+         (uint32_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R) + 512 + (uint32_t)W * kRngBytesPerWarp;
 }
 
 template <class R>
@@ -179,6 +181,7 @@ struct CtaSmem {
   uint64_t* mbar;
   double* red_f;
   int* red_c;
+  uint64_t* rng;    // [W x 32 x 4] Philox words of the next 8 steps, per warp
 };
 
 template <class R>
@@ -191,6 +194,7 @@ __device__ __forceinline__ CtaSmem<R> carve(unsigned char* smem, const DevMarket
   s.mbar = (uint64_t*)tail;
   s.red_f = (double*)(tail + 16);
   s.red_c = (int*)(tail + 16 + 32 * sizeof(double));
+  s.rng = (uint64_t*)(tail + 512);
   return s;
 }
 
@@ -302,7 +306,7 @@ __device__ __forceinline__ bool metropolis(FF fy, FF f, uint64_t word, double T,
   const float dE = (fy.hi - f.hi) + (fy.lo - f.lo);
   if (dE < 0.f) return true;
   const float t = dE * invT;
-  const float e = __expf(-t);
+  const float e = exp_approx(-t);
   const float uf = (float)(uint32_t)(word >> 40) * 0x1.0p-24f;   // uf <= u < uf + 2^-24
   const float band = 0x1.0p-24f + e * (1e-6f + 4e-7f * fabsf(t));
   if (fabsf(uf - e) > band) return uf < e;
@@ -316,7 +320,7 @@ template <class R>
 __device__ __forceinline__ R box_hi(const DevMarket& m, int k) { return (R)m.hi[k]; }
 
 template <class R, int MODEL, int FORMULA>
-__global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 4))
+__global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 7 : 4))
 sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -354,24 +358,23 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
       xbk = x;
     }
     const unsigned long long cw = (unsigned long long)c | (sp.market_index << 32);
-    const int wsel = lane & 3;
-    U4 o;   // Philox block (lane & 3) of step s0 + (lane >> 2), for 8 steps at a time
+    // Philox block (lane & 3) of step s0 + (lane >> 2), 8 steps at a time, parked in shared memory
+    uint64_t* rng = cs.rng + (size_t)warp * 128;
     for (int s = 0; s < sp.N; ++s) {
       // S1: the step's uniforms; lane k needs word (k & 3) of block (k >> 2) of this step
-      if ((s & 7) == 0) o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)(s + (lane >> 2)), (uint64_t)level, cw, sp.seed, 0ull);
-      uint64_t word;
-      {
-        const int src = ((s & 7) << 2) | ((lane >> 2) & 3);
-        const uint64_t w0 = __shfl_sync(0xffffffffu, o.v[0], src);
-        const uint64_t w1 = __shfl_sync(0xffffffffu, o.v[1], src);
-        const uint64_t w2 = __shfl_sync(0xffffffffu, o.v[2], src);
-        const uint64_t w3 = __shfl_sync(0xffffffffu, o.v[3], src);
-        word = wsel == 0 ? w0 : (wsel == 1 ? w1 : (wsel == 2 ? w2 : w3));
+      if ((s & 7) == 0) {
+        const U4 o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)(s + (lane >> 2)), (uint64_t)level, cw, sp.seed, 0ull);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rng[lane * 4 + j] = o.v[j];
+        __syncwarp();
       }
+      const int row = (s & 7) << 2;
+      const uint64_t word = rng[(row | ((lane >> 2) & 3)) * 4 + (lane & 3)];
+      const uint64_t wacc = rng[(row | (P >> 2)) * 4 + (P & 3)];
       R y = x;
       if (lane < P && freek) y = neighbour(x, lo, hi, (R)sf, word);
       if (lane < kMaxParam) ws.xs[lane] = lane < P ? y : R(0);
-      const uint64_t wacc = __shfl_sync(0xffffffffu, word, P);
       __syncwarp();
       const O fy = warp_objective<R, MODEL, FORMULA>(m, capB, *cs.quad, ws, lane, nullptr);
       const bool acc = metropolis(fy, f, wacc, T, invT);

@@ -22,6 +22,7 @@
 //   S7  squared residuals summed per lane in the pricing precision; across lanes in FP64 (FP64
 //       path) or in float-float, a 48-bit significand on the FP32 pipes (FP32 path).
 #pragma once
+#include <type_traits>
 #include "device_math.cuh"
 #include "market.cuh"
 
@@ -244,10 +245,14 @@ struct RhoConsts {
 
 template <class R> __device__ __forceinline__ R fdiv(R a, R b);
 template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
-template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return a * rcp_approx(b); }
 template <class R> __device__ __forceinline__ R fsqrt(R a);
 template <> __device__ __forceinline__ double fsqrt<double>(double a) { return sqrt(a); }
-template <> __device__ __forceinline__ float fsqrt<float>(float a) { return a * rsqrtf(a); }   // a > 0 here
+template <> __device__ __forceinline__ float fsqrt<float>(float a) { return a * rsqrt_approx(a); }   // a > 0 here
+// log1p on the non-negative argument of x(z)
+template <class R> __device__ __forceinline__ R log1p_zx(R y);
+template <> __device__ __forceinline__ double log1p_zx<double>(double y) { return log1p(y); }
+template <> __device__ __forceinline__ float log1p_zx<float>(float y) { return log1p_pos(y); }
 
 template <class R>
 __device__ __forceinline__ R z_over_x_fast(R z, const RhoConsts<R>& rc) {
@@ -261,7 +266,7 @@ __device__ __forceinline__ R z_over_x_fast(R z, const RhoConsts<R>& rc) {
   const R s = fsqrt<R>(R(1) + zq);
   const R smr = fdiv<R>(rc.omr2 + zq, s + r);
   const R Q = (r > R(0)) ? (smr + omr + zz) : (zz - R(2) * r + s + R(1));
-  const R x = M::log1p_(fdiv<R>(zz * Q, s + R(1)) * iomr);
+  const R x = log1p_zx<R>(fdiv<R>(zz * Q, s + R(1)) * iomr);
   const R series = R(1) - R(0.5) * rc.rho * z + (R(2) - R(3) * rc.rho * rc.rho) * z * z * R(1.0 / 12.0);
   return (zz < M::zx_series) ? series : fdiv<R>(zz, x);
 }
@@ -300,6 +305,66 @@ __device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const W
     acc += r * r;
   }
   return acc;
+}
+
+// z_over_x_fast on a pair (FP32), with the series coefficients c1 = -rho / 2 and
+// c2 = (2 - 3 rho^2) / 12 of the chain.
+__device__ __forceinline__ float2 z_over_x2(float2 z, const RhoConsts<float>& rc, float c1, float c2) {
+  const float2 zz = abs2(z);
+  const bool nx = z.x < 0.0f, ny = z.y < 0.0f;
+  const float2 r = make_float2(nx ? -rc.rho : rc.rho, ny ? -rc.rho : rc.rho);
+  const float2 omr = make_float2(nx ? rc.omr_m : rc.omr_p, ny ? rc.omr_m : rc.omr_p);
+  const float2 iomr = make_float2(nx ? rc.iomr_m : rc.iomr_p, ny ? rc.iomr_m : rc.iomr_p);
+  const float2 zm2r = fma2(r, bc2(-2.0f), zz);
+  const float2 zq = mul2(zz, zm2r);
+  const float2 s2 = add2(bc2(1.0f), zq);
+  const float2 s = mul2(s2, rsqrt2(s2));
+  const float2 smr = mul2(add2(bc2(rc.omr2), zq), rcp2(add2(s, r)));
+  const float2 sp1 = add2(s, bc2(1.0f));
+  const float2 qa = add2(add2(smr, omr), zz);
+  const float2 qb = add2(zm2r, sp1);
+  const float2 Q = sel2(r.x > 0.0f, r.y > 0.0f, qa, qb);
+  const float2 x = log1p_pos2(mul2(mul2(mul2(zz, Q), rcp2(sp1)), iomr));
+  const float2 ser = fma2(fma2(bc2(c2), z, bc2(c1)), z, bc2(1.0f));
+  const float2 zx = mul2(zz, rcp2(x));
+  return sel2(zz.x < Num<float>::zx_series, zz.y < Num<float>::zx_series, ser, zx);
+}
+
+// price_caplets for FP32 and the Hagan (2002) form, two caplets (k, k + 32) per lane and step
+// on the packed FP32 instructions; the second of the last pair may be absent (masked).
+__device__ __forceinline__ float price_caplets_x2(const InstrView<float>& B, int n, const WarpScratch<float>& ws,
+                                                  const RhoConsts<float>& rc, int lane, bool& ok) {
+  const float c1 = -0.5f * rc.rho, c2 = (2.0f - 3.0f * rc.rho * rc.rho) * (1.0f / 12.0f);
+  float2 acc = bc2(0.0f);
+  for (int k = lane; k < n; k += 64) {
+    const bool has2 = k + 32 < n;
+    const int k2 = has2 ? k + 32 : k;
+    const int ia = B.idx[k], ib = B.idx[k2];
+    const Q4<float> fa = ws.F4[ia], fb = ws.F4[ib];
+    const Q4<float> g0a = B.g0[k], g0b = B.g0[k2];   // l, fk, inv_den, c1
+    const Q4<float> g1a = B.g1[k], g1b = B.g1[k2];   // c2, c3, sqrt(T), D F
+    const float2 z = mul2(make_float2(fa.b, fb.b), make_float2(g0a.b, g0b.b));
+    const float2 zx = z_over_x2(z, rc, c1, c2);
+    float2 corr = fma2(make_float2(g0a.d, g0b.d), make_float2(fa.c, fb.c), bc2(1.0f));
+    corr = fma2(make_float2(g1a.a, g1b.a), make_float2(fa.d, fb.d), corr);
+    corr = fma2(make_float2(g1a.b, g1b.b), make_float2(ws.fA3[ia], ws.fA3[ib]), corr);
+    const float2 sig = mul2(mul2(mul2(make_float2(fa.a, fb.a), make_float2(g0a.c, g0b.c)), zx), corr);
+    const bool gx = (sig.x > 0.0f) && isfinite(sig.x), gy = (sig.y > 0.0f) && isfinite(sig.y);
+    ok = ok && gx && (gy || !has2);
+    const Q4<float> g2a = B.g2[k], g2b = B.g2[k2];   // K/F, sgn, P_mkt, sqrt(w)
+    const float2 v = mul2(sig, make_float2(g1a.c, g1b.c));
+    const float2 d1 = fma2(make_float2(g0a.a, g0b.a), rcp2(v), mul2(bc2(0.5f), v));
+    const float2 sg = make_float2(g2a.b, g2b.b);
+    const float2 n1 = ncdf2(mul2(sg, d1));
+    const float2 n2 = ncdf2(mul2(sg, sub2(d1, v)));
+    // n1 - KF n2 in one rounding (the two nearly cancel far out of the money)
+    const float2 nkf = mul2(make_float2(g2a.a, g2b.a), bc2(-1.0f));
+    const float2 p = mul2(mul2(sg, make_float2(g1a.d, g1b.d)), fma2(nkf, n2, n1));
+    float2 r = mul2(make_float2(g2a.d, g2b.d), sub2(p, make_float2(g2a.c, g2b.c)));
+    r.y = has2 ? r.y : 0.0f;
+    acc = fma2(r, r, acc);
+  }
+  return acc.x + acc.y;
 }
 
 // ------------------------------------------------------------------ objective values
@@ -373,7 +438,13 @@ __device__ typename ObjOf<R>::T warp_objective(const DevMarket& m, const InstrVi
     rc.init(ws.xs[8]);
   }
   bool ok = true;
-  const R part = price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);
+  R part;
+  if constexpr (std::is_same<R, float>::value && FORMULA == 0) {
+    part = vols == nullptr ? price_caplets_x2(capB, m.n_cap, ws, rc, lane, ok)
+                           : price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);
+  } else {
+    part = price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);
+  }
   __syncwarp();
   if (vols) return obj_inf(O());
   const O f = warp_sum(obj_lane(O(), part));
