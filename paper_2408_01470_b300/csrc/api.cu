@@ -167,7 +167,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
   struct Off {
     size_t T, P, cap_K, cap_vol, cap_wu, swp_K, swp_vol, swp_wu, cap_fwd, swp_start, swp_end, swp_swap, swap_a, swap_b,
         capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
-        swp_w, cblk64, cblk32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
+        swp_w, cblk64, cblk32, cpair32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
         swap_grp, swap_L, swap_W32;
   };
   std::vector<Off> off(n_markets);
@@ -266,6 +266,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.cap_pm = A.take(d.n_cap * 8); o.cap_w = A.take(d.n_cap * 8);
     o.swp_pm = A.take(d.n_swp * 8); o.swp_w = A.take(d.n_swp * 8);
     o.cblk64 = A.take(instr_block_bytes<double>(m.n_cap_pad)); o.cblk32 = A.take(instr_block_bytes<float>(m.n_cap_pad));
+    o.cpair32 = A.take(pair_block_bytes(cap_pairs(d.n_cap)));
     o.sblk64 = A.take(instr_block_bytes<double>(m.n_swp_pad)); o.sblk32 = A.take(instr_block_bytes<float>(m.n_swp_pad));
     o.q64 = A.take(sizeof(QuadTab<double>)); o.q32 = A.take(sizeof(QuadTab<float>));
     o.err = A.take(16);
@@ -341,6 +342,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.cap_pm = (double*)(base + o.cap_pm); m.cap_w = (double*)(base + o.cap_w);
     m.swp_pm = (double*)(base + o.swp_pm); m.swp_w = (double*)(base + o.swp_w);
     m.cblk64 = base + o.cblk64; m.cblk32 = base + o.cblk32; m.sblk64 = base + o.sblk64; m.sblk32 = base + o.sblk32;
+    m.cpair32 = base + o.cpair32; m.n_cap_pairs = cap_pairs(m.n_cap);
     m.q64 = (const QuadTab<double>*)(base + o.q64); m.q32 = (const QuadTab<float>*)(base + o.q32);
     m.err = (int*)(base + o.err);
     m.grp_a = (const int*)(base + o.grp_a); m.grp_nE = (const int*)(base + o.grp_nE);
@@ -351,6 +353,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     if (m.n_swap > 0) setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
     const int ni = m.n_cap + m.n_swp;
     setup_instruments_kernel<<<(ni + 127) / 128, 128, 0, s>>>(m);
+    if (m.n_cap > 0) setup_pairs_kernel<<<(m.n_cap_pairs + 127) / 128, 128, 0, s>>>(m);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

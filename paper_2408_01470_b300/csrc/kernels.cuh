@@ -101,6 +101,32 @@ __global__ void setup_instruments_kernel(DevMarket m) {
   }
 }
 
+// The pair-major copy of the FP32 caplet block (PairView), from the scalar FP32 block.
+__global__ void setup_pairs_kernel(DevMarket m) {
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= m.n_cap_pairs) return;
+  const int np = m.n_cap_pairs;
+  const int a = 64 * (P >> 5) + (P & 31), b = a + 32;
+  float4* V = (float4*)m.cpair32;
+  int2* idx = (int2*)(V + 6 * np);
+  if (a >= m.n_cap) {
+    for (int j = 0; j < 6; ++j) V[j * np + P] = make_float4(0.f, 0.f, 0.f, 0.f);
+    idx[P] = make_int2(0, 0);
+    return;
+  }
+  const InstrView<float> S = instr_view<float>(m.cblk32, m.n_cap_pad);
+  const bool hb = b < m.n_cap;
+  const int bb = hb ? b : a;
+  const Q4<float> g0a = S.g0[a], g0b = S.g0[bb], g1a = S.g1[a], g1b = S.g1[bb], g2a = S.g2[a], g2b = S.g2[bb];
+  V[0 * np + P] = make_float4(g0a.a, g0b.a, g0a.b, g0b.b);
+  V[1 * np + P] = make_float4(g0a.c, g0b.c, g0a.d, g0b.d);
+  V[2 * np + P] = make_float4(g1a.a, g1b.a, g1a.b, g1b.b);
+  V[3 * np + P] = make_float4(g1a.c, g1b.c, g1a.d, g1b.d);
+  V[4 * np + P] = make_float4(g2a.a, g2b.a, g2a.b, g2b.b);
+  V[5 * np + P] = make_float4(g2a.c, g2b.c, g2a.d, hb ? g2b.d : 0.0f);
+  idx[P] = make_int2(S.idx[a], S.idx[bb]);
+}
+
 // ------------------------------------------------------------------ bulk staging into SMEM
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -167,9 +193,19 @@ template <> __device__ __forceinline__ const void* quad_block<float>(const DevMa
 // 32 doubles, 32 ints].  Every region starts on a 16-byte boundary.
 constexpr uint32_t kRngBytesPerWarp = 32 * 4 * sizeof(uint64_t);
 
+// Shared-memory room for the caplet block: the scalar block, or in FP32 the pair-major block
+// (whichever is larger).
+template <class R>
+__host__ __device__ inline uint32_t cap_region_bytes(const DevMarket& m) {
+  const uint32_t a = instr_block_bytes<R>(m.n_cap_pad);
+  if (sizeof(R) != 4) return a;
+  const uint32_t b = pair_block_bytes(m.n_cap_pairs);
+  return a > b ? a : b;
+}
+
 template <class R>
 __host__ __device__ inline uint32_t smem_bytes(const DevMarket& m, int W) {
-  return instr_block_bytes<R>(m.n_cap_pad) + (uint32_t)sizeof(QuadTab<R>) +
+  return cap_region_bytes<R>(m) + (uint32_t)sizeof(QuadTab<R>) +
          (uint32_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R) + 512 + (uint32_t)W * kRngBytesPerWarp;
 }
 
@@ -188,7 +224,7 @@ template <class R>
 __device__ __forceinline__ CtaSmem<R> carve(unsigned char* smem, const DevMarket& m, int W) {
   CtaSmem<R> s;
   s.cap = smem;
-  s.quad = (QuadTab<R>*)(smem + instr_block_bytes<R>(m.n_cap_pad));
+  s.quad = (QuadTab<R>*)(smem + cap_region_bytes<R>(m));
   s.scratch = (unsigned char*)s.quad + sizeof(QuadTab<R>);
   unsigned char* tail = s.scratch + (size_t)W * warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R);
   s.mbar = (uint64_t*)tail;
@@ -198,12 +234,21 @@ __device__ __forceinline__ CtaSmem<R> carve(unsigned char* smem, const DevMarket
   return s;
 }
 
-// Stage the caplet block and the quadrature table (contiguous in shared memory).
+// Stage the caplet block (pair-major with `pairs`, for the packed FP32 pricer) and the quadrature
+// table.
 template <class R>
-__device__ __forceinline__ bool stage_market(const CtaSmem<R>& cs, const DevMarket& m) {
+__device__ __forceinline__ bool stage_market(const CtaSmem<R>& cs, const DevMarket& m, bool pairs) {
+  if (pairs)
+    return stage_to_smem2(cs.cap, m.cpair32, pair_block_bytes(m.n_cap_pairs), cs.quad, quad_block<R>(m),
+                          (uint32_t)sizeof(QuadTab<R>), cs.mbar, m.err);
   return stage_to_smem2(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.quad, quad_block<R>(m),
                         (uint32_t)sizeof(QuadTab<R>), cs.mbar, m.err);
 }
+
+// Whether warp_objective prices the caplets with the packed FP32 pricer (and so reads the
+// pair-major block): FP32, the Hagan (2002) form, no model vols requested.
+template <class R, int FORMULA>
+__host__ __device__ constexpr bool packed_pricer() { return sizeof(R) == 4 && FORMULA == 0; }
 
 // ------------------------------------------------------------------ objective and vols
 template <class R, int MODEL, int FORMULA>
@@ -212,7 +257,7 @@ __global__ void objective_kernel(DevMarket m, const double* __restrict__ X, long
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   CtaSmem<R> cs = carve<R>(smem, m, W);
-  if (!stage_market<R>(cs, m)) return;
+  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>() && vols == nullptr)) return;
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
   const int n_instr = m.n_cap + m.n_swp;
@@ -255,7 +300,7 @@ __global__ void sa_start_kernel(DevMarket m, SAState st, SAParams sp) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   CtaSmem<R> cs = carve<R>(smem, m, 1);
-  if (!stage_market<R>(cs, m)) return;
+  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>())) return;
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch, m.NP, m.n_fwd);
   // the start point in the chain-state precision (FP32 chains start from the rounded point)
@@ -326,7 +371,7 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   CtaSmem<R> cs = carve<R>(smem, m, W);
-  if (!stage_market<R>(cs, m)) return;
+  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>())) return;
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
 

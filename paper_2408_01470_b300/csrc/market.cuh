@@ -51,6 +51,30 @@ template <class R> __host__ __device__ inline InstrView<R> instr_view(const void
   return v;
 }
 
+// The FP32 caplet block again, pair-major for the packed pricer: caplets a = 64 i + l and
+// b = a + 32 (l = 0..31) form pair P = 32 i + l, and each 16-byte vector holds two fields of both:
+//   v0 = {l_a, l_b, fk_a, fk_b}        v1 = {inv_den_a, inv_den_b, c1_a, c1_b}
+//   v2 = {c2_a, c2_b, c3_a, c3_b}      v3 = {sqrtT_a, sqrtT_b, DF_a, DF_b}
+//   v4 = {KF_a, KF_b, sgn_a, sgn_b}    v5 = {P_mkt_a, P_mkt_b, sqrtw_a, sqrtw_b}
+// then the forward indices {idx_a, idx_b}.  A missing b (b >= n) repeats a with sqrt(w) = 0.
+__host__ __device__ inline int cap_pairs(int n) { return 32 * ((n + 63) / 64); }
+__host__ __device__ inline uint32_t pair_block_bytes(int npairs) {
+  const uint32_t raw = (uint32_t)npairs * (uint32_t)(6 * 16 + 8);
+  return (raw + 63u) & ~63u;
+}
+struct PairView {
+  const float4* v;   // [6 x npairs]
+  const int2* idx;   // [npairs]
+  int np;
+};
+__host__ __device__ inline PairView pair_view(const void* base, int npairs) {
+  PairView w;
+  w.v = (const float4*)base;
+  w.idx = (const int2*)(w.v + 6 * npairs);
+  w.np = npairs;
+  return w;
+}
+
 struct DevMarket {
   int model, formula, n_param, n_fwd;
   int n_cap, n_swp, n_swap;        // caplets, swaptions, distinct underlying swaps
@@ -87,6 +111,8 @@ struct DevMarket {
   int* swap_np;                    // [n_swap] panels to the expiry
   double *cap_pm, *cap_w, *swp_pm, *swp_w;  // market prices and weights (FP64)
   void *cblk64, *cblk32, *sblk64, *sblk32;  // instrument blocks
+  void* cpair32;                   // the FP32 caplet block, pair-major (PairView)
+  int n_cap_pairs;                 // cap_pairs(n_cap)
   const QuadTab<double>* q64;
   const QuadTab<float>* q32;
   int* err;                        // device error word (nonzero: a bounded wait gave up)

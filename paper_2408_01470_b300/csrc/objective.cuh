@@ -28,6 +28,19 @@
 
 namespace sabr {
 
+// Division and square root of the pricing precision: IEEE in FP64, the hardware approximations
+// in FP32.
+template <class R> __device__ __forceinline__ R fdiv(R a, R b);
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return a * rcp_approx(b); }
+template <class R> __device__ __forceinline__ R fsqrt(R a);
+template <> __device__ __forceinline__ double fsqrt<double>(double a) { return sqrt(a); }
+template <> __device__ __forceinline__ float fsqrt<float>(float a) { return a * rsqrt_approx(a); }   // a > 0 here
+// log1p on the non-negative argument of x(z)
+template <class R> __device__ __forceinline__ R log1p_zx(R y);
+template <> __device__ __forceinline__ double log1p_zx<double>(double y) { return log1p(y); }
+template <> __device__ __forceinline__ float log1p_zx<float>(float y) { return log1p_pos(y); }
+
 template <class R> struct Q2 { R a, b; };
 
 // Per-forward SABR factors consumed by the pricer:
@@ -74,11 +87,62 @@ template <class R>
 __device__ __forceinline__ void put_forward(const WarpScratch<R>& ws, int i, R al, R nu, R rho) {
   Q4<R> v;
   v.a = al;
-  v.b = nu / al;
+  v.b = fdiv<R>(nu, al);
   v.c = al * al;
   v.d = rho * nu * al;
   ws.F4[i] = v;
   ws.fA3[i] = (R(2) - R(3) * rho * rho) * nu * nu;
+}
+
+// Inclusive prefix scans over the panel integrals, in place (Gp -> SG, Ap -> SA, Hp -> SH, and
+// SGH in Ep's slot), then alpha_i and nu_i of every caplet forward.
+template <class R>
+__device__ __forceinline__ void prefix_and_forwards(const DevMarket& m, const WarpScratch<R>& ws, int lane, R rho) {
+  const int NP = m.NP;
+  R cg = 0, ca = 0, chh = 0, cgs = 0;
+  for (int c0 = 0; c0 < NP; c0 += 32) {
+    const int p = c0 + lane;
+    const bool in = p < NP;
+    const R g = in ? ws.Gp[p] : R(0), ap = in ? ws.Ap[p] : R(0), hh = in ? ws.Hp[p] : R(0);
+    R ig = g, ia = ap, ih = hh;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const R og = __shfl_up_sync(0xffffffffu, ig, off);
+      const R oa = __shfl_up_sync(0xffffffffu, ia, off);
+      const R oh = __shfl_up_sync(0xffffffffu, ih, off);
+      if (lane >= off) { ig += og; ia += oa; ih += oh; }
+    }
+    ih += chh;
+    R igs = g * ih;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const R o2 = __shfl_up_sync(0xffffffffu, igs, off);
+      if (lane >= off) igs += o2;
+    }
+    __syncwarp();
+    if (in) {
+      ws.Gp[p] = cg + ig;
+      ws.Ap[p] = ca + ia;
+      ws.Hp[p] = ih;
+      ((R*)ws.Ep)[p] = cgs + igs;
+    }
+    cg += __shfl_sync(0xffffffffu, ig, 31);
+    ca += __shfl_sync(0xffffffffu, ia, 31);
+    chh = __shfl_sync(0xffffffffu, ih, 31);
+    cgs += __shfl_sync(0xffffffffu, igs, 31);
+  }
+  __syncwarp();
+  for (int j = lane; j < m.n_capfwd; j += 32) {
+    const int i = m.capfwd_list[j];
+    const int n = m.fwd_np[i];
+    const R Ti = (R)m.T[i];
+    const R G = ws.Gp[n - 1];
+    const R X = ws.Ap[n - 1] + ws.Hp[n - 1] * G - ((const R*)ws.Ep)[n - 1];
+    const R al = fsqrt<R>(fdiv<R>(G, Ti));
+    const R X2 = R(2) * X;
+    put_forward<R>(ws, i, al, X2 > R(0) ? fdiv<R>(fsqrt<R>(X2), al * Ti) : R(0), rho);
+  }
+  __syncwarp();
 }
 
 // S2: alpha_i, nu_i of every caplet forward (Rebonato mapping, kappa = 1).
@@ -178,50 +242,109 @@ __device__ void rebonato_forward_params(const DevMarket& m, const QuadTab<R>& qt
     if (q == 0 && p < NP) { ws.Gp[p] = G; ws.Hp[p] = H; ws.Ap[p] = A; }
   }
   __syncwarp();
-  // inclusive prefix scans over panels, in place: Gp -> SG, Ap -> SA, Hp -> SH, and SGH in Ep's slot
-  R cg = 0, ca = 0, chh = 0, cgs = 0;
-  for (int c0 = 0; c0 < NP; c0 += 32) {
-    const int p = c0 + lane;
-    const bool in = p < NP;
-    const R g = in ? ws.Gp[p] : R(0), ap = in ? ws.Ap[p] : R(0), hh = in ? ws.Hp[p] : R(0);
-    R ig = g, ia = ap, ih = hh;
+  prefix_and_forwards<R>(m, ws, lane, rho);
+}
+
+// S2 in FP32 on the packed pair instructions.  Same sums as rebonato_forward_params, laid out for
+// pairs of outer nodes (q, q + 1): the per-evaluation tables are pair-major floats
+//   Tq: [4 pairs][e_g, b o e_g, e_h, beta_h o e_h][2]      (32 floats)
+//   T2: [4 pairs][S1, 2 S2, S3, S4, S5, S6][2]             (48 floats)
+// so that one lane owns one panel and walks the 8 nodes as 4 pairs with no shuffles; the
+// exponentials are e^x = 2^(x log2 e) with the rounding of x log2 e carried as a first-order
+// correction.
+__device__ __forceinline__ float exp_fast(float x) {
+  const float L = 1.44269504088896341f, Llo = 1.92596299112661746e-8f;   // log2 e = L + Llo
+  const float hi = x * L;
+  const float lo = fmaf(x, L, -hi) + x * Llo;
+  return ex2_approx(hi) * fmaf(lo, 0.693147180559945309f, 1.0f);
+}
+
+__device__ void rebonato_forward_params_f32(const DevMarket& m, const QuadTab<float>& qt,
+                                            const WarpScratch<float>& ws, int lane) {
+  const float a = ws.xs[0], b = ws.xs[1], c = ws.xs[2], d = ws.xs[3];
+  const float ah = ws.xs[4], bh = ws.xs[5], gh = ws.xs[6], dh = ws.xs[7];
+  const float rho = ws.xs[8];
+  const float D = (float)m.panel;
+  const int NP = m.NP;
+  float* tq = (float*)ws.Tq;
+  float* t2 = (float*)ws.T2;
+  {
+    // inner-rule sums: lane -> outer node q = lane / 4, inner nodes r0 = lane % 4 and r0 + 4
+    const int q = lane >> 2, r0 = lane & 3;
+    const float2 o2 = make_float2(qt.o2[q * kQ + r0], qt.o2[q * kQ + r0 + 4]);
+    const float2 sw = make_float2(qt.sw2[q * kQ + r0], qt.sw2[q * kQ + r0 + 4]);
+    const float2 w = mul2(sw, sw);
+    const float2 e = make_float2(exp_fast(-gh * o2.x), exp_fast(-gh * o2.y));
+    const float2 bb = mul2(mul2(bc2(bh), o2), e);
+    const float2 we = mul2(w, e), wb = mul2(w, bb);
+    const float2 p1 = mul2(we, e), p2 = mul2(we, bb), p3 = mul2(wb, bb);
+    float S[6] = {p1.x + p1.y, p2.x + p2.y, p3.x + p3.y, we.x + we.y, wb.x + wb.y, w.x + w.y};
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const R og = __shfl_up_sync(0xffffffffu, ig, off);
-      const R oa = __shfl_up_sync(0xffffffffu, ia, off);
-      const R oh = __shfl_up_sync(0xffffffffu, ih, off);
-      if (lane >= off) { ig += og; ia += oa; ih += oh; }
-    }
-    ih += chh;
-    R igs = g * ih;
+    for (int off = 1; off < 4; off <<= 1)
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const R o2 = __shfl_up_sync(0xffffffffu, igs, off);
-      if (lane >= off) igs += o2;
+      for (int j = 0; j < 6; ++j) S[j] += __shfl_xor_sync(0xffffffffu, S[j], off);
+    if (r0 == 0) {
+      float* t = t2 + (q >> 1) * 12 + (q & 1);
+      t[0] = S[0];
+      t[2] = 2.0f * S[1];
+      t[4] = S[2];
+      t[6] = S[3];
+      t[8] = S[4];
+      t[10] = S[5];
     }
-    __syncwarp();
-    if (in) {
-      ws.Gp[p] = cg + ig;
-      ws.Ap[p] = ca + ia;
-      ws.Hp[p] = ih;
-      ((R*)ws.Ep)[p] = cgs + igs;
-    }
-    cg += __shfl_sync(0xffffffffu, ig, 31);
-    ca += __shfl_sync(0xffffffffu, ia, 31);
-    chh = __shfl_sync(0xffffffffu, ih, 31);
-    cgs += __shfl_sync(0xffffffffu, igs, 31);
+  }
+  if (lane < kQ) {
+    const float o = qt.o[lane];
+    const float eg = exp_fast(-c * o), eh = exp_fast(-gh * o);
+    float* t = tq + (lane >> 1) * 8 + (lane & 1);
+    t[0] = eg;
+    t[2] = b * o * eg;
+    t[4] = eh;
+    t[6] = bh * o * eh;
   }
   __syncwarp();
-  for (int j = lane; j < m.n_capfwd; j += 32) {
-    const int i = m.capfwd_list[j];
-    const int n = m.fwd_np[i];
-    const R Ti = (R)m.T[i];
-    const R G = ws.Gp[n - 1];
-    const R X = ws.Ap[n - 1] + ws.Hp[n - 1] * G - ((const R*)ws.Ep)[n - 1];
-    const R al = M::sqrt_(G / Ti);
-    put_forward<R>(ws, i, al, M::sqrt_(R(2) * (X > R(0) ? X : R(0))) / (al * Ti), rho);
+  const float2* tq2 = (const float2*)tq;
+  const float2* t22 = (const float2*)t2;
+  const float2* w2 = (const float2*)qt.w;
+  for (int p = lane; p < NP; p += 32) {
+    const float base = D * (float)p;
+    const float Eg = exp_fast(-c * base), Eh = exp_fast(-gh * base);
+    const float2 agp = bc2(a + b * base), ahp = bc2(ah + bh * base);
+    const float2 E2 = bc2(Eh * Eh), c2e = bc2(2.0f * Eh * dh), dh2 = bc2(dh * dh);
+    float2 G = bc2(0.0f), H = bc2(0.0f), A = bc2(0.0f);
+#pragma unroll
+    for (int qp = 0; qp < 4; ++qp) {
+      const float2 wq = w2[qp];
+      const float2* T = tq2 + qp * 4;
+      const float2* S = t22 + qp * 6;
+      const float2 g = fma2(bc2(Eg), fma2(agp, T[0], T[1]), bc2(d));
+      const float2 h = fma2(bc2(Eh), fma2(ahp, T[2], T[3]), bc2(dh));
+      float2 t1 = fma2(ahp, S[0], S[1]);
+      t1 = fma2(ahp, t1, S[2]);
+      const float2 t2v = fma2(ahp, S[3], S[4]);
+      float2 Rin = mul2(E2, t1);
+      Rin = fma2(c2e, t2v, Rin);
+      Rin = fma2(dh2, S[5], Rin);
+      const float2 gw = mul2(mul2(wq, g), g);
+      G = add2(G, gw);
+      H = fma2(mul2(wq, h), h, H);
+      A = fma2(gw, Rin, A);
+    }
+    ws.Gp[p] = G.x + G.y;
+    ws.Hp[p] = H.x + H.y;
+    ws.Ap[p] = A.x + A.y;
   }
   __syncwarp();
+  prefix_and_forwards<float>(m, ws, lane, rho);
+}
+
+// S2 dispatch for the objective: the packed FP32 form, or the plain form in FP64.  (The adjoint
+// keeps the plain form, whose node tables it reads back.)
+template <class R>
+__device__ __forceinline__ void forward_params(const DevMarket& m, const QuadTab<R>& qt, const WarpScratch<R>& ws,
+                                               int lane) {
+  if constexpr (std::is_same<R, float>::value) rebonato_forward_params_f32(m, qt, ws, lane);
+  else rebonato_forward_params<R>(m, qt, ws, lane);
 }
 
 // z / x(z) with per-chain constants of rho: omr = 1 - r, inv_omr = 1 / (1 - r), omr2 = 1 - r^2
@@ -242,17 +365,6 @@ struct RhoConsts {
     omr2 = omr_p * omr_m;
   }
 };
-
-template <class R> __device__ __forceinline__ R fdiv(R a, R b);
-template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
-template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return a * rcp_approx(b); }
-template <class R> __device__ __forceinline__ R fsqrt(R a);
-template <> __device__ __forceinline__ double fsqrt<double>(double a) { return sqrt(a); }
-template <> __device__ __forceinline__ float fsqrt<float>(float a) { return a * rsqrt_approx(a); }   // a > 0 here
-// log1p on the non-negative argument of x(z)
-template <class R> __device__ __forceinline__ R log1p_zx(R y);
-template <> __device__ __forceinline__ double log1p_zx<double>(double y) { return log1p(y); }
-template <> __device__ __forceinline__ float log1p_zx<float>(float y) { return log1p_pos(y); }
 
 template <class R>
 __device__ __forceinline__ R z_over_x_fast(R z, const RhoConsts<R>& rc) {
@@ -308,60 +420,62 @@ __device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const W
 }
 
 // z_over_x_fast on a pair (FP32), with the series coefficients c1 = -rho / 2 and
-// c2 = (2 - 3 rho^2) / 12 of the chain.
-__device__ __forceinline__ float2 z_over_x2(float2 z, const RhoConsts<float>& rc, float c1, float c2) {
+// c2 = (2 - 3 rho^2) / 12 of the chain.  The sign of z is the sign of fk (nu / alpha > 0), so
+// r = +-rho comes from the sign bit of the instrument constant, and 1 / ((s + 1)(1 - r)) is one
+// reciprocal.
+__device__ __forceinline__ float2 z_over_x2(float2 z, float fkx, float fky, const RhoConsts<float>& rc, float c1,
+                                            float c2) {
   const float2 zz = abs2(z);
-  const bool nx = z.x < 0.0f, ny = z.y < 0.0f;
-  const float2 r = make_float2(nx ? -rc.rho : rc.rho, ny ? -rc.rho : rc.rho);
-  const float2 omr = make_float2(nx ? rc.omr_m : rc.omr_p, ny ? rc.omr_m : rc.omr_p);
-  const float2 iomr = make_float2(nx ? rc.iomr_m : rc.iomr_p, ny ? rc.iomr_m : rc.iomr_p);
+  const unsigned rb = __float_as_uint(rc.rho);
+  const float2 r = make_float2(__uint_as_float(rb ^ (__float_as_uint(fkx) & 0x80000000u)),
+                               __uint_as_float(rb ^ (__float_as_uint(fky) & 0x80000000u)));
   const float2 zm2r = fma2(r, bc2(-2.0f), zz);
   const float2 zq = mul2(zz, zm2r);
   const float2 s2 = add2(bc2(1.0f), zq);
   const float2 s = mul2(s2, rsqrt2(s2));
   const float2 smr = mul2(add2(bc2(rc.omr2), zq), rcp2(add2(s, r)));
   const float2 sp1 = add2(s, bc2(1.0f));
+  const float2 omr = sub2(bc2(1.0f), r);
   const float2 qa = add2(add2(smr, omr), zz);
   const float2 qb = add2(zm2r, sp1);
   const float2 Q = sel2(r.x > 0.0f, r.y > 0.0f, qa, qb);
-  const float2 x = log1p_pos2(mul2(mul2(mul2(zz, Q), rcp2(sp1)), iomr));
+  const float2 x = log1p_pos2(mul2(mul2(zz, Q), rcp2(mul2(sp1, omr))));
   const float2 ser = fma2(fma2(bc2(c2), z, bc2(c1)), z, bc2(1.0f));
   const float2 zx = mul2(zz, rcp2(x));
   return sel2(zz.x < Num<float>::zx_series, zz.y < Num<float>::zx_series, ser, zx);
 }
 
-// price_caplets for FP32 and the Hagan (2002) form, two caplets (k, k + 32) per lane and step
-// on the packed FP32 instructions; the second of the last pair may be absent (masked).
-__device__ __forceinline__ float price_caplets_x2(const InstrView<float>& B, int n, const WarpScratch<float>& ws,
+// price_caplets for FP32 and the Hagan (2002) form on the packed instructions: lane l takes the
+// caplet pair P = 32 i + l of the pair-major block (caplets 64 i + l and 64 i + l + 32), so every
+// 16-byte load gives two ready operand pairs.  A missing second caplet carries sqrt(w) = 0.
+__device__ __forceinline__ float price_caplets_x2(const void* blk, int npairs, int n, const WarpScratch<float>& ws,
                                                   const RhoConsts<float>& rc, int lane, bool& ok) {
+  const PairView B = pair_view(blk, npairs);
   const float c1 = -0.5f * rc.rho, c2 = (2.0f - 3.0f * rc.rho * rc.rho) * (1.0f / 12.0f);
   float2 acc = bc2(0.0f);
-  for (int k = lane; k < n; k += 64) {
-    const bool has2 = k + 32 < n;
-    const int k2 = has2 ? k + 32 : k;
-    const int ia = B.idx[k], ib = B.idx[k2];
-    const Q4<float> fa = ws.F4[ia], fb = ws.F4[ib];
-    const Q4<float> g0a = B.g0[k], g0b = B.g0[k2];   // l, fk, inv_den, c1
-    const Q4<float> g1a = B.g1[k], g1b = B.g1[k2];   // c2, c3, sqrt(T), D F
-    const float2 z = mul2(make_float2(fa.b, fb.b), make_float2(g0a.b, g0b.b));
-    const float2 zx = z_over_x2(z, rc, c1, c2);
-    float2 corr = fma2(make_float2(g0a.d, g0b.d), make_float2(fa.c, fb.c), bc2(1.0f));
-    corr = fma2(make_float2(g1a.a, g1b.a), make_float2(fa.d, fb.d), corr);
-    corr = fma2(make_float2(g1a.b, g1b.b), make_float2(ws.fA3[ia], ws.fA3[ib]), corr);
-    const float2 sig = mul2(mul2(mul2(make_float2(fa.a, fb.a), make_float2(g0a.c, g0b.c)), zx), corr);
-    const bool gx = (sig.x > 0.0f) && isfinite(sig.x), gy = (sig.y > 0.0f) && isfinite(sig.y);
-    ok = ok && gx && (gy || !has2);
-    const Q4<float> g2a = B.g2[k], g2b = B.g2[k2];   // K/F, sgn, P_mkt, sqrt(w)
-    const float2 v = mul2(sig, make_float2(g1a.c, g1b.c));
-    const float2 d1 = fma2(make_float2(g0a.a, g0b.a), rcp2(v), mul2(bc2(0.5f), v));
-    const float2 sg = make_float2(g2a.b, g2b.b);
+  for (int it = 0; 64 * it + lane < n; ++it) {
+    const int P = 32 * it + lane;
+    const int2 ix = B.idx[P];
+    const Q4<float> fa = ws.F4[ix.x], fb = ws.F4[ix.y];
+    const float4 v0 = B.v[P], v1 = B.v[npairs + P], v2 = B.v[2 * npairs + P];
+    const float2 l = make_float2(v0.x, v0.y), fk = make_float2(v0.z, v0.w);
+    const float2 z = mul2(make_float2(fa.b, fb.b), fk);
+    const float2 zx = z_over_x2(z, fk.x, fk.y, rc, c1, c2);
+    float2 corr = fma2(make_float2(v1.z, v1.w), make_float2(fa.c, fb.c), bc2(1.0f));
+    corr = fma2(make_float2(v2.x, v2.y), make_float2(fa.d, fb.d), corr);
+    corr = fma2(make_float2(v2.z, v2.w), make_float2(ws.fA3[ix.x], ws.fA3[ix.y]), corr);
+    const float2 sig = mul2(mul2(mul2(make_float2(fa.a, fb.a), make_float2(v1.x, v1.y)), zx), corr);
+    ok = ok && (sig.x > 0.0f) && (sig.x < INFINITY) && (sig.y > 0.0f) && (sig.y < INFINITY);
+    const float4 v3 = B.v[3 * npairs + P], v4 = B.v[4 * npairs + P], v5 = B.v[5 * npairs + P];
+    const float2 v = mul2(sig, make_float2(v3.x, v3.y));
+    const float2 d1 = fma2(l, rcp2(v), mul2(bc2(0.5f), v));
+    const float2 sg = make_float2(v4.z, v4.w);
     const float2 n1 = ncdf2(mul2(sg, d1));
     const float2 n2 = ncdf2(mul2(sg, sub2(d1, v)));
     // n1 - KF n2 in one rounding (the two nearly cancel far out of the money)
-    const float2 nkf = mul2(make_float2(g2a.a, g2b.a), bc2(-1.0f));
-    const float2 p = mul2(mul2(sg, make_float2(g1a.d, g1b.d)), fma2(nkf, n2, n1));
-    float2 r = mul2(make_float2(g2a.d, g2b.d), sub2(p, make_float2(g2a.c, g2b.c)));
-    r.y = has2 ? r.y : 0.0f;
+    const float2 nkf = mul2(make_float2(v4.x, v4.y), bc2(-1.0f));
+    const float2 p = mul2(mul2(sg, make_float2(v3.z, v3.w)), fma2(nkf, n2, n1));
+    const float2 r = mul2(make_float2(v5.z, v5.w), sub2(p, make_float2(v5.x, v5.y)));
     acc = fma2(r, r, acc);
   }
   return acc.x + acc.y;
@@ -434,13 +548,14 @@ __device__ typename ObjOf<R>::T warp_objective(const DevMarket& m, const InstrVi
     __syncwarp();
     rc.init(rho);
   } else {
-    rebonato_forward_params<R>(m, qt, ws, lane);
+    forward_params<R>(m, qt, ws, lane);
     rc.init(ws.xs[8]);
   }
   bool ok = true;
   R part;
   if constexpr (std::is_same<R, float>::value && FORMULA == 0) {
-    part = vols == nullptr ? price_caplets_x2(capB, m.n_cap, ws, rc, lane, ok)
+    // (with no vols requested the caller staged the pair-major block; its base is capB.g0)
+    part = vols == nullptr ? price_caplets_x2(capB.g0, m.n_cap_pairs, m.n_cap, ws, rc, lane, ok)
                            : price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);
   } else {
     part = price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);

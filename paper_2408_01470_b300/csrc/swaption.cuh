@@ -176,7 +176,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     if (m.n_capfwd > 0) {
       if (lane < kMaxParam) cs.cap.xs[lane] = cs.xs[lane];
       __syncwarp();
-      rebonato_forward_params<R>(m, qt, cs.cap, lane);
+      forward_params<R>(m, qt, cs.cap, lane);
     }
   } else {
     const int t0 = tid - 32, nt = nth - 32;
