@@ -234,6 +234,11 @@ class Market:
                                                  _stream_ptr(stream)))
         return f, G
 
+    def calibration_objective(self, X, prec="fp64", market=0):
+        """f(X) as a differentiable torch op: the forward and the backward both come from
+        sabr_lmm_objective_grad (the hand-written adjoint), through CalibrationObjective."""
+        return CalibrationObjective.apply(X, self, prec, market)
+
     def lm_polish(self, X, max_iter=50, target_rmse=0.0, market=0, stream=None):
         """sabr_lmm_lm_polish: returns (X polished, f, rmse in vol points) as device tensors."""
         X = self._X(X, market).clone()
@@ -330,3 +335,40 @@ def quadrature_rule(q: int = 8):
     if st != 0:
         raise SabrLmmError(st, lib.sabr_lmm_last_error().decode())
     return x, w
+
+
+def _autograd_function():
+    import torch
+
+    class CalibrationObjective(torch.autograd.Function):
+        """f = sum_k w_k (P_k(theta) - P_k^mkt)^2 per row of X (n x n_param, float64, CUDA) with the
+        gradient of the library's reverse sweep: forward runs sabr_lmm_objective_grad once and keeps
+        G = df/dtheta; backward returns grad_f[:, None] * G.  Second derivatives are not provided."""
+
+        @staticmethod
+        def forward(ctx, X, market, prec="fp64", index=0):
+            f, G = market.objective_grad(X.detach(), prec=prec, market=index)
+            ctx.save_for_backward(G)
+            return f
+
+        @staticmethod
+        def backward(ctx, grad_f):
+            (G,) = ctx.saved_tensors
+            return grad_f[:, None] * G, None, None, None
+
+    return CalibrationObjective
+
+
+class _LazyFunction:
+    """Defers `import torch` until first use (the binding imports without torch for ABI checks)."""
+
+    def __init__(self):
+        self._cls = None
+
+    def apply(self, *args):
+        if self._cls is None:
+            self._cls = _autograd_function()
+        return self._cls.apply(*args)
+
+
+CalibrationObjective = _LazyFunction()

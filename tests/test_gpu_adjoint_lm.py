@@ -134,3 +134,33 @@ def test_anneal_with_top_k_polish(gpu_lib):
     p = om.lm(r1["x_best"][0], max_iter=20)
     assert p["f"] >= r1["f_best"][0] * (1 - 1e-9)
     assert om.objective(r1["x_best"][0]) == pytest.approx(r1["f_best"][0], rel=1e-12)
+
+
+def test_autograd_function_backward_is_the_adjoint(gpu_lib):
+    # CalibrationObjective: f from the library, X.grad = sum_i c_i df_i/dX_i from the reverse sweep,
+    # compared with the oracle's dual-number gradient
+    import torch
+    sk = CASES["caplets_7x5"]()
+    om, gm = _markets(sk)
+    Xn = _points(sk, 4, seed=77)
+    X = torch.tensor(Xn, dtype=torch.float64, device="cuda", requires_grad=True)
+    f = gm.calibration_objective(X)
+    c = torch.arange(1, 5, dtype=torch.float64, device="cuda")
+    (c * f).sum().backward()
+    g = X.grad.cpu().numpy()
+    for i in range(4):
+        fo, go = om.objective_grad(Xn[i])
+        assert f[i].item() == pytest.approx(fo, rel=1e-12)
+        assert np.max(np.abs(g[i] - (i + 1) * go)) <= 1e-9 * (i + 1) * np.max(np.abs(go))
+
+
+def test_autograd_function_gradcheck(gpu_lib):
+    # torch's own finite-difference check of the op (FP64, central differences)
+    import torch
+    sk = CASES["smile_2y"]()
+    _, gm = _markets(sk)
+    # points near the generating one keep f and its gradient of moderate size for the FD rounding
+    rng = np.random.default_rng(78)
+    Xn = sk.theta_true[None, :] * (1.0 + 0.05 * rng.standard_normal((2, sk.n_param)))
+    X = torch.tensor(Xn, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert torch.autograd.gradcheck(lambda x: gm.calibration_objective(x), (X,), eps=1e-7, atol=1e-6, rtol=1e-4)
