@@ -168,7 +168,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     size_t T, P, cap_K, cap_vol, cap_wu, swp_K, swp_vol, swp_wu, cap_fwd, swp_start, swp_end, swp_swap, swap_a, swap_b,
         capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
         swp_w, cblk64, cblk32, cpair32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
-        swap_grp, swap_L, swap_W32;
+        swap_grp, swap_L, swap_W32, grp_pair, swap_coff, swap_C64, swap_C32;
   };
   std::vector<Off> off(n_markets);
   std::vector<DevMarket> dm(n_markets);
@@ -176,7 +176,8 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
   // host-side integer bookkeeping
   std::vector<std::vector<int>> capfwd(n_markets), fwdnp(n_markets), swp_swap(n_markets), swap_a(n_markets),
       swap_b(n_markets), swap_np(n_markets), grp_a(n_markets), grp_nE(n_markets), grp_L(n_markets),
-      grp_delta(n_markets), grp_swap0(n_markets), swap_grp(n_markets), swap_L(n_markets);
+      grp_delta(n_markets), grp_swap0(n_markets), swap_grp(n_markets), swap_L(n_markets), grp_pair(n_markets),
+      swap_coff(n_markets);
   for (int j = 0; j < n_markets; ++j) {
     const sabr_lmm_market_desc& d = descs[j];
     DevMarket& m = dm[j];
@@ -240,6 +241,21 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.NA = NA;
     m.ND = ND;
     m.max_gwin = max_gwin;
+    // pair tables of the quadratic forms: per group the (offset, diagonal) of every pair of its
+    // window, per swap the offset of its coefficient row
+    m.max_npk = max_gwin * (max_gwin + 1) / 2;
+    if (ND > 255) return fail(SABR_LMM_ENOTSUP, "market " + std::to_string(j) + ": a swap window spans more than 255 panels");
+    for (size_t g = 0; g < grp_a[j].size(); ++g)
+      for (int t = 0; t < m.max_npk; ++t) {
+        int jj = 0;
+        while ((jj + 1) * (jj + 2) / 2 <= t) ++jj;
+        const int ii = t - jj * (jj + 1) / 2;
+        const int* dl = grp_delta[j].data() + g * max_gwin;
+        grp_pair[j].push_back(jj < grp_L[j][g] ? (dl[ii] << 8) | (dl[jj] - dl[ii]) : 0);
+      }
+    swap_coff[j].push_back(0);
+    for (size_t s2 = 0; s2 < swap_L[j].size(); ++s2)
+      swap_coff[j].push_back(swap_coff[j].back() + swap_L[j][s2] * (swap_L[j][s2] + 1) / 2);
     m.n_swap = (int)swap_a[j].size();
     m.max_win = max_win;
     m.NP = std::max(NP, 1);
@@ -275,6 +291,10 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.grp_delta = A.take((size_t)ng * m.max_gwin * 4); o.grp_swap0 = A.take((ng + 1) * 4);
     o.swap_grp = A.take(m.n_swap * 4); o.swap_L = A.take(m.n_swap * 4);
     o.swap_W32 = A.take((size_t)m.n_swap * max_win * 4);
+    o.grp_pair = A.take((size_t)ng * m.max_npk * 4);
+    o.swap_coff = A.take((m.n_swap + 1) * 4);
+    o.swap_C64 = A.take((size_t)swap_coff[j].back() * 8);
+    o.swap_C32 = A.take((size_t)swap_coff[j].back() * 4);
   }
   std::vector<unsigned char> host(A.size, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { if (src && bytes) std::memcpy(host.data() + o, src, bytes); };
@@ -297,6 +317,8 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     put(o.grp_delta, grp_delta[j].data(), (size_t)m.n_grp * m.max_gwin * 4);
     put(o.grp_swap0, grp_swap0[j].data(), (m.n_grp + 1) * 4);
     put(o.swap_grp, swap_grp[j].data(), m.n_swap * 4); put(o.swap_L, swap_L[j].data(), m.n_swap * 4);
+    put(o.grp_pair, grp_pair[j].data(), (size_t)m.n_grp * m.max_npk * 4);
+    put(o.swap_coff, swap_coff[j].data(), (m.n_swap + 1) * 4);
     QuadTab<double> q64;
     QuadTab<float> q32;
     const double D = m.panel;
@@ -349,8 +371,13 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.grp_L = (const int*)(base + o.grp_L); m.grp_delta = (const int*)(base + o.grp_delta);
     m.grp_swap0 = (const int*)(base + o.grp_swap0); m.swap_grp = (const int*)(base + o.swap_grp);
     m.swap_L = (const int*)(base + o.swap_L); m.swap_W32 = (float*)(base + o.swap_W32);
+    m.grp_pair = (const int*)(base + o.grp_pair); m.swap_coff = (const int*)(base + o.swap_coff);
+    m.swap_C64 = (const double*)(base + o.swap_C64); m.swap_C32 = (const float*)(base + o.swap_C32);
     setup_forwards_kernel<<<(m.n_fwd + 127) / 128, 128, 0, s>>>(m);
-    if (m.n_swap > 0) setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
+    if (m.n_swap > 0) {
+      setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
+      setup_swap_coef_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
+    }
     const int ni = m.n_cap + m.n_swp;
     setup_instruments_kernel<<<(ni + 127) / 128, 128, 0, s>>>(m);
     if (m.n_cap > 0) setup_pairs_kernel<<<(m.n_cap_pairs + 127) / 128, 128, 0, s>>>(m);

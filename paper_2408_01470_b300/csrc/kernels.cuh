@@ -48,6 +48,23 @@ __global__ void setup_swaps_kernel(DevMarket m) {
   m.swap_TE[s] = m.T[a];
 }
 
+// Coefficient rows of the swaption quadratic forms: (2 - [i = j]) W_i W_j for the pairs i <= j of
+// each swap's window, packed by column (t = j (j + 1)/2 + i), in FP64 and FP32.
+__global__ void setup_swap_coef_kernel(DevMarket m) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= m.n_swap) return;
+  const int L = m.swap_L[s];
+  const double* W = m.swap_W + (size_t)s * m.max_win;
+  double* c64 = (double*)m.swap_C64 + m.swap_coff[s];
+  float* c32 = (float*)m.swap_C32 + m.swap_coff[s];
+  for (int j = 0; j < L; ++j)
+    for (int i = 0; i <= j; ++i) {
+      const double c = (i == j ? 1.0 : 2.0) * W[i] * W[j];
+      c64[j * (j + 1) / 2 + i] = c;
+      c32[j * (j + 1) / 2 + i] = (float)c;
+    }
+}
+
 // Pricing constants of one instrument, into the three 4-vector groups of its block.
 template <class R>
 __device__ void put_instr(void* blk, int npad, int k, double l, double fk, double inv_den, double c1, double c2,

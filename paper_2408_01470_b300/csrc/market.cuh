@@ -94,6 +94,12 @@ struct DevMarket {
   const int* grp_swap0;            // [n_grp + 1] swaps sorted by group: first swap of each group
   const int* swap_grp;             // [n_swap]
   const int* swap_L;               // [n_swap] forwards in the swap
+  int max_npk;                     // max_gwin (max_gwin + 1) / 2
+  const int* grp_pair;             // [n_grp x max_npk] pair t = j (j + 1)/2 + i (i <= j) of the group's
+                                   //   window: (delta_i << 8) | (delta_j - delta_i)
+  const int* swap_coff;            // [n_swap + 1] offsets of the swaps' coefficient rows
+  const double* swap_C64;          // [swap_coff[n_swap]] (2 - [i = j]) W_i W_j, pair-packed as grp_pair
+  const float* swap_C32;           //   the same in FP32
   double beta, panel;
   // raw description
   const double *T, *P, *cap_K, *cap_vol, *cap_wu, *swp_K, *swp_vol, *swp_wu;

@@ -15,7 +15,8 @@
 //       G_ij = PG(hi) - PG(lo),  X_ij / theta_ij = PA(hi) - PA(lo) + SH(hi)(PG(hi) - PG(lo)) - (PGS(hi) - PGS(lo))
 //     (lo = delta_i, hi = lo + nE): the composite rule of the oracle, calendar time reversed.
 // S5  Quadratic forms per swap: V = sum_{i<=j} (2 - [i=j]) W_i W_j B_ij, B = (rho G, rho X, phi G),
-//     the B matrices built once per expiry group (swaps sharing their first forward).
+//     the B matrices built once per expiry group (swaps sharing their first forward), several
+//     groups per barrier; the coefficient rows (2 - [i=j]) W_i W_j are market constants.
 // S6  alpha_S = sqrt(V1/T), nu_S = sqrt(2 V2)/(alpha_S T), rho_S = clamp(V3/V1, +-0.999), then
 //     SABR and Black per swaption, with the caplets priced alongside.
 #pragma once
@@ -37,6 +38,7 @@ template <class R> struct CtaScratch {
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
   R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
   Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}
+  R* Vs;            // [3 x n_swap] the quadratic forms V1, V2, V3 of every swap
 };
 
 __host__ __device__ inline int cta_y_stride() { return 81; }
@@ -47,7 +49,8 @@ __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int Lg = m.max_gwin;
   return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + round_up(m.NA * cta_y_stride(), 4) +
                       round_up(4 * m.ND * cta_pq_len(m.NA), 4) + round_up(3 * m.ND, 4) +
-                      round_up(3 * (Lg * (Lg + 1) / 2), 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap,
+                      round_up(3 * (Lg * (Lg + 1) / 2), 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
+                      round_up(3 * m.n_swap, 4),
                   4);
 }
 
@@ -68,13 +71,17 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
   s.Bg = p; p += round_up(3 * (Lg * (Lg + 1) / 2), 4);
   s.F4s = (Q4<R>*)p; p += 4 * m.n_swap;
   s.A3s = p; p += round_up(m.n_swap, 4);
-  s.RCs = (Q4<R>*)p;
+  s.RCs = (Q4<R>*)p; p += 4 * m.n_swap;
+  s.Vs = p;
   return s;
 }
 
 template <class R> __device__ __forceinline__ const R* swap_W_of(const DevMarket& m);
 template <> __device__ __forceinline__ const double* swap_W_of<double>(const DevMarket& m) { return m.swap_W; }
 template <> __device__ __forceinline__ const float* swap_W_of<float>(const DevMarket& m) { return m.swap_W32; }
+template <class R> __device__ __forceinline__ const R* swap_C_of(const DevMarket& m);
+template <> __device__ __forceinline__ const double* swap_C_of<double>(const DevMarket& m) { return m.swap_C64; }
+template <> __device__ __forceinline__ const float* swap_C_of<float>(const DevMarket& m) { return m.swap_C32; }
 
 // Inclusive warp scan (lanes in order).
 template <class R>
@@ -325,73 +332,81 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   }
   __syncthreads();
 
-  // ---- phase 5: per expiry group, the B matrices, then the quadratic forms of its swaps
-  const R* Wall = swap_W_of<R>(m);
-  for (int g = 0; g < m.n_grp; ++g) {
-    const int Lg = m.grp_L[g], nE = m.grp_nE[g];
-    const int* dl = m.grp_delta + g * m.max_gwin;
-    const int npk = Lg * (Lg + 1) / 2;
-    // B matrices packed by column: pair (i <= j) at j (j + 1) / 2 + i, so the pairs of a swap over
-    // the first L forwards of the group are the first L (L + 1) / 2 entries
-    for (int t = tid; t < npk; t += nth) {
-      int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-      if (j * (j + 1) / 2 > t) --j;
-      if ((j + 1) * (j + 2) / 2 <= t) ++j;
-      const int i = t - j * (j + 1) / 2;
-      const int e = dl[j] - dl[i];
-      const int lo = dl[i], hi = lo + nE;
-      const R* PG = cs.PQ + (0 * ND + e) * PL;
-      const R* PA = cs.PQ + (1 * ND + e) * PL;
-      const R* SH = cs.PQ + (2 * ND + e) * PL;
-      const R* PGS = cs.PQ + (3 * ND + e) * PL;
-      const R G = PG[hi] - PG[lo];
-      const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
-      cs.Bg[t] = cs.corr[e] * G;
-      cs.Bg[npk + t] = cs.corr[e] * cs.corr[ND + e] * X;
-      cs.Bg[2 * npk + t] = cs.corr[2 * ND + e] * G;
-    }
-    __syncthreads();
-    const int s0 = m.grp_swap0[g], s1 = m.grp_swap0[g + 1];
-    const R TE = (R)m.T[m.grp_a[g]];
-    for (int s = s0 + warp; s < s1; s += nw) {
-      const int L = m.swap_L[s];
-      const R* W = Wall + (size_t)s * m.max_win;
-      R v1 = 0, v2 = 0, v3 = 0;
-      for (int t = lane; t < L * (L + 1) / 2; t += 32) {
-        int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-        if (j * (j + 1) / 2 > t) --j;
-        if ((j + 1) * (j + 2) / 2 <= t) ++j;
-        const int i = t - j * (j + 1) / 2;
-        const R w = (i == j ? R(1) : R(2)) * W[i] * W[j];
-        v1 += w * cs.Bg[t];
-        v2 += w * cs.Bg[npk + t];
-        v3 += w * cs.Bg[2 * npk + t];
+  // ---- phase 5: the B matrices of a batch of expiry groups, then the quadratic forms of the
+  //      batch's swaps (one warp per swap, lanes over the pairs, coefficient rows from the market);
+  //      the batch lives in the Y region (dead since phase 3) when it holds two groups or more
+  {
+    const R* Call = swap_C_of<R>(m);
+    const int npm = m.max_npk;
+    R* Bbuf = cs.Bg;
+    int GB = 1;
+    if (NA * YS >= 6 * npm) { Bbuf = cs.Y; GB = (NA * YS) / (3 * npm); }
+    for (int g0 = 0; g0 < m.n_grp; g0 += GB) {
+      const int g1 = min(m.n_grp, g0 + GB);
+      for (int it = tid; it < (g1 - g0) * npm; it += nth) {
+        const int gl = it / npm, t = it - gl * npm, g = g0 + gl;
+        const int Lg = m.grp_L[g];
+        if (t >= Lg * (Lg + 1) / 2) continue;
+        const int pk = m.grp_pair[g * npm + t];
+        const int e = pk & 255, lo = pk >> 8, hi = lo + m.grp_nE[g];
+        const R* PG = cs.PQ + (0 * ND + e) * PL;
+        const R* PA = cs.PQ + (1 * ND + e) * PL;
+        const R* SH = cs.PQ + (2 * ND + e) * PL;
+        const R* PGS = cs.PQ + (3 * ND + e) * PL;
+        const R G = PG[hi] - PG[lo];
+        const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
+        R* B = Bbuf + gl * 3 * npm;
+        B[t] = cs.corr[e] * G;
+        B[npm + t] = cs.corr[e] * cs.corr[ND + e] * X;
+        B[2 * npm + t] = cs.corr[2 * ND + e] * G;
       }
+      __syncthreads();
+      for (int s = m.grp_swap0[g0] + warp; s < m.grp_swap0[g1]; s += nw) {
+        const R* B = Bbuf + (m.swap_grp[s] - g0) * 3 * npm;
+        const int L = m.swap_L[s];
+        const R* Cs = Call + m.swap_coff[s];
+        R v1 = 0, v2 = 0, v3 = 0;
+        for (int t = lane; t < L * (L + 1) / 2; t += 32) {
+          const R w = Cs[t];
+          v1 += w * B[t];
+          v2 += w * B[npm + t];
+          v3 += w * B[2 * npm + t];
+        }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-        v2 += __shfl_xor_sync(0xffffffffu, v2, off);
-        v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+        for (int off = 16; off > 0; off >>= 1) {
+          v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+          v2 += __shfl_xor_sync(0xffffffffu, v2, off);
+          v3 += __shfl_xor_sync(0xffffffffu, v3, off);
+        }
+        if (lane == 0) {
+          cs.Vs[s] = v1;
+          cs.Vs[m.n_swap + s] = v2;
+          cs.Vs[2 * m.n_swap + s] = v3;
+        }
       }
-      if (lane == 0) {
-        const R al = M::sqrt_(v1 / TE);
-        const R nu = M::sqrt_(R(2) * v2) / (al * TE);
-        R rho = v3 / v1;
-        rho = rho > R(0.999) ? R(0.999) : (rho < R(-0.999) ? R(-0.999) : rho);
-        Q4<R> f;
-        f.a = al;
-        f.b = nu / al;
-        f.c = al * al;
-        f.d = rho * nu * al;
-        cs.F4s[s] = f;
-        cs.A3s[s] = (R(2) - R(3) * rho * rho) * nu * nu;
-        Q4<R> q;
-        q.a = rho;
-        q.b = R(1) / (R(1) - rho);
-        q.c = R(1) / (R(1) + rho);
-        q.d = (R(1) - rho) * (R(1) + rho);
-        cs.RCs[s] = q;
-      }
+      __syncthreads();
+    }
+    // the swap-rate SABR factors, one thread per swap
+    for (int s = tid; s < m.n_swap; s += nth) {
+      const R v1 = cs.Vs[s], v2 = cs.Vs[m.n_swap + s], v3 = cs.Vs[2 * m.n_swap + s];
+      const R TE = (R)m.T[m.swap_a[s]];
+      const R al = M::sqrt_(v1 / TE);
+      const R nu = M::sqrt_(R(2) * v2) / (al * TE);
+      R rho = v3 / v1;
+      rho = rho > R(0.999) ? R(0.999) : (rho < R(-0.999) ? R(-0.999) : rho);
+      Q4<R> f;
+      f.a = al;
+      f.b = nu / al;
+      f.c = al * al;
+      f.d = rho * nu * al;
+      cs.F4s[s] = f;
+      cs.A3s[s] = (R(2) - R(3) * rho * rho) * nu * nu;
+      Q4<R> q;
+      q.a = rho;
+      q.b = R(1) / (R(1) - rho);
+      q.c = R(1) / (R(1) + rho);
+      q.d = (R(1) - rho) * (R(1) + rho);
+      cs.RCs[s] = q;
     }
     __syncthreads();
   }
