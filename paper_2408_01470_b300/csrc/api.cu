@@ -168,7 +168,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     size_t T, P, cap_K, cap_vol, cap_wu, swp_K, swp_vol, swp_wu, cap_fwd, swp_start, swp_end, swp_swap, swap_a, swap_b,
         capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
         swp_w, cblk64, cblk32, cpair32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
-        swap_grp, swap_L, swap_W32, grp_pair, swap_coff, swap_C64, swap_C32;
+        swap_grp, swap_L, swap_W32, grp_pair, swap_coff, swap_C64, swap_C32, chunk, grp_chunk0, swap_chunk0;
   };
   std::vector<Off> off(n_markets);
   std::vector<DevMarket> dm(n_markets);
@@ -177,7 +177,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
   std::vector<std::vector<int>> capfwd(n_markets), fwdnp(n_markets), swp_swap(n_markets), swap_a(n_markets),
       swap_b(n_markets), swap_np(n_markets), grp_a(n_markets), grp_nE(n_markets), grp_L(n_markets),
       grp_delta(n_markets), grp_swap0(n_markets), swap_grp(n_markets), swap_L(n_markets), grp_pair(n_markets),
-      swap_coff(n_markets);
+      swap_coff(n_markets), chunk(n_markets), grp_chunk0(n_markets), swap_chunk0(n_markets);
   for (int j = 0; j < n_markets; ++j) {
     const sabr_lmm_market_desc& d = descs[j];
     DevMarket& m = dm[j];
@@ -256,6 +256,22 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     swap_coff[j].push_back(0);
     for (size_t s2 = 0; s2 < swap_L[j].size(); ++s2)
       swap_coff[j].push_back(swap_coff[j].back() + swap_L[j][s2] * (swap_L[j][s2] + 1) / 2);
+    // chunks of <= kChunk pairs (swaps are ordered by group, so the chunks are too)
+    for (size_t g = 0; g < grp_a[j].size(); ++g) {
+      grp_chunk0[j].push_back((int)chunk[j].size() / 2);
+      for (int s2 = grp_swap0[j][g]; s2 < grp_swap0[j][g + 1]; ++s2) {
+        swap_chunk0[j].push_back((int)chunk[j].size() / 2);
+        const int np = swap_L[j][s2] * (swap_L[j][s2] + 1) / 2;
+        const int nk = (np + kChunk - 1) / kChunk;
+        for (int k = 0; k < nk; ++k) {
+          chunk[j].push_back(s2);
+          chunk[j].push_back(k | (nk << 16));
+        }
+      }
+    }
+    grp_chunk0[j].push_back((int)chunk[j].size() / 2);
+    swap_chunk0[j].push_back((int)chunk[j].size() / 2);
+    m.n_chunk = (int)chunk[j].size() / 2;
     m.n_swap = (int)swap_a[j].size();
     m.max_win = max_win;
     m.NP = std::max(NP, 1);
@@ -295,6 +311,9 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.swap_coff = A.take((m.n_swap + 1) * 4);
     o.swap_C64 = A.take((size_t)swap_coff[j].back() * 8);
     o.swap_C32 = A.take((size_t)swap_coff[j].back() * 4);
+    o.chunk = A.take((size_t)m.n_chunk * 8);
+    o.grp_chunk0 = A.take((m.n_grp + 1) * 4);
+    o.swap_chunk0 = A.take((m.n_swap + 1) * 4);
   }
   std::vector<unsigned char> host(A.size, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { if (src && bytes) std::memcpy(host.data() + o, src, bytes); };
@@ -319,6 +338,9 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     put(o.swap_grp, swap_grp[j].data(), m.n_swap * 4); put(o.swap_L, swap_L[j].data(), m.n_swap * 4);
     put(o.grp_pair, grp_pair[j].data(), (size_t)m.n_grp * m.max_npk * 4);
     put(o.swap_coff, swap_coff[j].data(), (m.n_swap + 1) * 4);
+    put(o.chunk, chunk[j].data(), (size_t)m.n_chunk * 8);
+    put(o.grp_chunk0, grp_chunk0[j].data(), grp_chunk0[j].size() * 4);
+    put(o.swap_chunk0, swap_chunk0[j].data(), swap_chunk0[j].size() * 4);
     QuadTab<double> q64;
     QuadTab<float> q32;
     const double D = m.panel;
@@ -373,6 +395,8 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.swap_L = (const int*)(base + o.swap_L); m.swap_W32 = (float*)(base + o.swap_W32);
     m.grp_pair = (const int*)(base + o.grp_pair); m.swap_coff = (const int*)(base + o.swap_coff);
     m.swap_C64 = (const double*)(base + o.swap_C64); m.swap_C32 = (const float*)(base + o.swap_C32);
+    m.chunk = (const int2*)(base + o.chunk); m.grp_chunk0 = (const int*)(base + o.grp_chunk0);
+    m.swap_chunk0 = (const int*)(base + o.swap_chunk0);
     setup_forwards_kernel<<<(m.n_fwd + 127) / 128, 128, 0, s>>>(m);
     if (m.n_swap > 0) {
       setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);

@@ -687,7 +687,7 @@ __device__ __forceinline__ bool stage_market_cta(const CtaSmemS<R>& cs, const De
 }
 
 template <class R, int FORMULA, bool TC>
-__global__ void __launch_bounds__(256) objective_cta_kernel(DevMarket m, const double* __restrict__ X, long long n,
+__global__ void __launch_bounds__(256, 2) objective_cta_kernel(DevMarket m, const double* __restrict__ X, long long n,
                                                             double* __restrict__ f, double* __restrict__ vols) {
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(256) objective_cta_kernel(DevMarket m, const d
 }
 
 template <class R, int FORMULA, bool TC>
-__global__ void __launch_bounds__(256) sa_start_cta_kernel(DevMarket m, SAState st, SAParams sp) {
+__global__ void __launch_bounds__(256, 2) sa_start_cta_kernel(DevMarket m, SAState st, SAParams sp) {
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
   CtaSmemS<R> cs = carve_cta<R>(smem, m);
@@ -843,7 +843,7 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
 }
 
 template <class R, int FORMULA, bool TC>
-__global__ void __launch_bounds__(256) sa_level_cta_kernel(DevMarket m, SAState st, SAParams sp, int level) {
+__global__ void __launch_bounds__(256, 2) sa_level_cta_kernel(DevMarket m, SAState st, SAParams sp, int level) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned long long s_wacc;
   __shared__ bool s_last;
@@ -874,7 +874,7 @@ struct BatchArgs {
 };
 
 template <class R, int FORMULA>
-__global__ void __launch_bounds__(256) sa_level_batch_kernel(BatchArgs ba, int level) {
+__global__ void __launch_bounds__(256, 2) sa_level_batch_kernel(BatchArgs ba, int level) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ DevMarket sm_m;
   __shared__ SAState sm_st;
@@ -908,7 +908,7 @@ __global__ void __launch_bounds__(256) sa_level_batch_kernel(BatchArgs ba, int l
 
 // f(x0), T0 and the first start point of every market of the batch (one CTA per market).
 template <class R, int FORMULA>
-__global__ void __launch_bounds__(256) sa_start_batch_kernel(BatchArgs ba) {
+__global__ void __launch_bounds__(256, 2) sa_start_batch_kernel(BatchArgs ba) {
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ DevMarket sm_m;

@@ -16,6 +16,7 @@ namespace sabr {
 constexpr int kQ = 8;               // Gauss-Legendre nodes per panel
 constexpr int kMaxParam = 12;       // parameter slots
 constexpr int kBlkArrays = 12;      // R values per instrument in a block (+ one int)
+constexpr int kChunk = 16;          // pairs per chunk of a swaption quadratic form
 
 // Quadrature table per precision, offsets relative to the start of a panel of width D:
 //   o[q] = (D/2)(1 + xi_q), w[q] = (D/2) w_q, sw[q] = sqrt(w[q])   (outer rule on the panel)
@@ -100,6 +101,11 @@ struct DevMarket {
   const int* swap_coff;            // [n_swap + 1] offsets of the swaps' coefficient rows
   const double* swap_C64;          // [swap_coff[n_swap]] (2 - [i = j]) W_i W_j, pair-packed as grp_pair
   const float* swap_C32;           //   the same in FP32
+  int n_chunk;                     // chunks of <= 16 pairs of the swaps' coefficient rows
+  const int2* chunk;               // [n_chunk] {swap, k | (nk << 16)}: chunk k of the swap's nk takes
+                                   //   the pairs t = k, k + nk, ... (ordered by group, then swap)
+  const int* grp_chunk0;           // [n_grp + 1] first chunk of each group
+  const int* swap_chunk0;          // [n_swap + 1] first chunk of each swap
   double beta, panel;
   // raw description
   const double *T, *P, *cap_K, *cap_vol, *cap_wu, *swp_K, *swp_vol, *swp_wu;

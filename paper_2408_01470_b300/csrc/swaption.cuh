@@ -33,24 +33,26 @@ template <class R> struct CtaScratch {
   Q4<R>* T2;        // [8 x 9]
   R* Y;             // [NA x 81]
   R* PQ;            // [4 x ND x (NA + 1)]: PG, PA, SH, PGS along each diagonal
-  R* corr;          // [3 x ND]: rho_e, theta_e, phi_e
+  Q4<R>* crq;       // [ND]: {rho_e, rho_e theta_e, phi_e, 0} per diagonal e
   R* Bg;            // [3 x Lg (Lg + 1) / 2] of the current expiry group
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
   R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
   Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}
-  R* Vs;            // [3 x n_swap] the quadratic forms V1, V2, V3 of every swap
+  R* Pc;            // [3 x n_chunk] partial sums of the quadratic forms, per chunk of pairs
 };
 
-__host__ __device__ inline int cta_y_stride() { return 81; }
-__host__ __device__ inline int cta_pq_len(int NA) { return NA + 1; }
+__host__ __device__ inline int cta_y_stride() { return 84; }   // 16-byte rows, conflict-free 4-vector loads
+// Row pitch of the prefix tables: at least NA + 1, and even, so that the pairs of a window column
+// (address stride 1 - pitch along a column) fall on distinct banks.
+__host__ __device__ inline int cta_pq_len(int NA) { return (NA + 2) & ~1; }
 
 __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int NAc = round_up(m.NA, 4);
   const int Lg = m.max_gwin;
   return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + round_up(m.NA * cta_y_stride(), 4) +
-                      round_up(4 * m.ND * cta_pq_len(m.NA), 4) + round_up(3 * m.ND, 4) +
+                      round_up(4 * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND +
                       round_up(3 * (Lg * (Lg + 1) / 2), 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
-                      round_up(3 * m.n_swap, 4),
+                      round_up(3 * m.n_chunk, 4),
                   4);
 }
 
@@ -67,12 +69,12 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
   s.T2 = (Q4<R>*)p; p += 4 * 72;
   s.Y = p; p += round_up(m.NA * cta_y_stride(), 4);
   s.PQ = p; p += round_up(4 * m.ND * cta_pq_len(m.NA), 4);
-  s.corr = p; p += round_up(3 * m.ND, 4);
+  s.crq = (Q4<R>*)p; p += 4 * m.ND;
   s.Bg = p; p += round_up(3 * (Lg * (Lg + 1) / 2), 4);
   s.F4s = (Q4<R>*)p; p += 4 * m.n_swap;
   s.A3s = p; p += round_up(m.n_swap, 4);
   s.RCs = (Q4<R>*)p; p += 4 * m.n_swap;
-  s.Vs = p;
+  s.Pc = p;
   return s;
 }
 
@@ -216,35 +218,49 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     }
     for (int e = t0; e < ND; e += nt) {
       const R dt = D * (R)e;
-      cs.corr[e] = M::exp_(-l1 * dt);
-      cs.corr[ND + e] = M::exp_(-l2 * dt);
-      cs.corr[2 * ND + e] = phi * M::exp_(-l3 * dt);
+      Q4<R> q;
+      q.a = M::exp_(-l1 * dt);
+      q.b = q.a * M::exp_(-l2 * dt);
+      q.c = phi * M::exp_(-l3 * dt);
+      q.d = R(0);
+      cs.crq[e] = q;
     }
   }
   __syncthreads();
 
-  // ---- phase 2: Y rows
-  for (int it = tid; it < NA * 80; it += nth) {
-    const int A = it / 80, k = it - A * 80;
+  // ---- phase 2: Y rows, one thread per (panel A, outer node q): g and h at the node once, then
+  //      the 8 inner-node products
+  for (int it = tid; it < NA * kQ; it += nth) {
+    const int A = it >> 3, q = it & 7;
     const R base = D * (R)A;
     const Q2<R> E = cs.Ep[A];
-    R v;
-    if (k < 8) {
-      const Q4<R> t = cs.Tq[k];
-      v = qt.sw[k] * (E.a * ((a + b * base) * t.a + t.b) + d);
-    } else if (k < 16) {
-      const Q4<R> t = cs.Tq[k - 8];
-      v = qt.sw[k - 8] * (E.b * ((ah + bh * base) * t.c + t.d) + dh);
-    } else {
-      const int q = (k - 16) >> 3, r = (k - 16) & 7;
-      const Q4<R> t = cs.Tq[q];
-      const R g = E.a * ((a + b * base) * t.a + t.b) + d;
+    const Q4<R> t = cs.Tq[q];
+    const R ahp = ah + bh * base;
+    const R swq = qt.sw[q];
+    const R g = E.a * ((a + b * base) * t.a + t.b) + d;
+    const R vg = swq * g;
+    const R vh = swq * (E.b * (ahp * t.c + t.d) + dh);
+    R v[kQ];
+#pragma unroll
+    for (int r = 0; r < kQ; ++r) {
       const Q4<R> t2 = cs.T2[q * 9 + r];
-      const R h2 = E.b * ((ah + bh * base) * t2.a + t2.b) + t2.c;
-      v = qt.sw[q] * g * h2;
+      v[r] = vg * (E.b * (ahp * t2.a + t2.b) + t2.c);
     }
-    if (TC) tc_put(*tc, A, k, (float)v);
-    else cs.Y[A * YS + k] = v;
+    if (TC) {
+      tc_put(*tc, A, q, (float)vg);
+      tc_put(*tc, A, 8 + q, (float)vh);
+#pragma unroll
+      for (int r = 0; r < kQ; ++r) tc_put(*tc, A, 16 + q * kQ + r, (float)v[r]);
+    } else {
+      R* y = cs.Y + A * YS;
+      y[q] = vg;
+      y[8 + q] = vh;
+      Q4<R> w0, w1;
+      w0.a = v[0]; w0.b = v[1]; w0.c = v[2]; w0.d = v[3];
+      w1.a = v[4]; w1.b = v[5]; w1.c = v[6]; w1.d = v[7];
+      *(Q4<R>*)(y + 16 + q * kQ) = w0;
+      *(Q4<R>*)(y + 20 + q * kQ) = w1;
+    }
   }
   __syncthreads();
 
@@ -281,22 +297,56 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const int q = it / (ND * NA), r = it - q * ND * NA, e = r / NA, A = r - e * NA;
       if (A + e < NA) cs.PQ[(q * ND + e) * PL + A] += Tb[(q * ND + e) * NA + A];
     }
-  } else
-  for (int it = tid; it < ND * NA; it += nth) {
-    const int e = it / NA, A = it - e * NA;
-    if (A + e >= NA) continue;
-    const R* ya = cs.Y + A * YS;
-    const R* yb = cs.Y + (A + e) * YS;
-    R G = 0, H = 0, Ad = 0;
+  } else {
+    // one thread per (panel A, block of 4 diagonals): the Y row of A is loaded once per 4 pairs
+    const int NEB = (ND + 3) >> 2;
+    for (int it = tid; it < NEB * NA; it += nth) {
+      const int eb = it / NA, A = it - eb * NA, e0 = 4 * eb;
+      const R* ya = cs.Y + A * YS;
+      const R* yb[4];
+      bool in[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) G += ya[k] * yb[k];
+      for (int u = 0; u < 4; ++u) {
+        in[u] = e0 + u < ND && A + e0 + u < NA;
+        yb[u] = cs.Y + (in[u] ? A + e0 + u : A) * YS;
+      }
+      R G[4], H[4], Ad[4];
 #pragma unroll
-    for (int k = 8; k < 16; ++k) H += ya[k] * yb[k];
-#pragma unroll 16
-    for (int k = 16; k < 80; ++k) Ad += ya[k] * yb[k];
-    cs.PQ[(0 * ND + e) * PL + A] = G;
-    cs.PQ[(1 * ND + e) * PL + A] = Ad;
-    cs.PQ[(2 * ND + e) * PL + A] = H;
+      for (int u = 0; u < 4; ++u) { G[u] = 0; H[u] = 0; Ad[u] = 0; }
+#pragma unroll
+      for (int k = 0; k < 16; k += 4) {
+        const Q4<R> x = *(const Q4<R>*)(ya + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const Q4<R> y = *(const Q4<R>*)(yb[u] + k);
+          R& acc = k < 8 ? G[u] : H[u];
+          acc += x.a * y.a;
+          acc += x.b * y.b;
+          acc += x.c * y.c;
+          acc += x.d * y.d;
+        }
+      }
+#pragma unroll 4
+      for (int k = 16; k < 80; k += 4) {
+        const Q4<R> x = *(const Q4<R>*)(ya + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const Q4<R> y = *(const Q4<R>*)(yb[u] + k);
+          Ad[u] += x.a * y.a;
+          Ad[u] += x.b * y.b;
+          Ad[u] += x.c * y.c;
+          Ad[u] += x.d * y.d;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (in[u]) {
+          const int e = e0 + u;
+          cs.PQ[(0 * ND + e) * PL + A] = G[u];
+          cs.PQ[(1 * ND + e) * PL + A] = Ad[u];
+          cs.PQ[(2 * ND + e) * PL + A] = H[u];
+        }
+    }
   }
   __syncthreads();
 
@@ -333,8 +383,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   __syncthreads();
 
   // ---- phase 5: the B matrices of a batch of expiry groups, then the quadratic forms of the
-  //      batch's swaps (one warp per swap, lanes over the pairs, coefficient rows from the market);
-  //      the batch lives in the Y region (dead since phase 3) when it holds two groups or more
+  //      batch's swaps in interleaved chunks of <= 16 pairs (one thread per chunk, coefficient rows from the
+  //      market, partial sums per chunk added per swap in chunk order); the batch lives in the Y
+  //      region (dead since phase 3) when it holds two groups or more
   {
     const R* Call = swap_C_of<R>(m);
     const int npm = m.max_npk;
@@ -343,52 +394,55 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     if (NA * YS >= 6 * npm) { Bbuf = cs.Y; GB = (NA * YS) / (3 * npm); }
     for (int g0 = 0; g0 < m.n_grp; g0 += GB) {
       const int g1 = min(m.n_grp, g0 + GB);
-      for (int it = tid; it < (g1 - g0) * npm; it += nth) {
-        const int gl = it / npm, t = it - gl * npm, g = g0 + gl;
-        const int Lg = m.grp_L[g];
-        if (t >= Lg * (Lg + 1) / 2) continue;
-        const int pk = m.grp_pair[g * npm + t];
-        const int e = pk & 255, lo = pk >> 8, hi = lo + m.grp_nE[g];
-        const R* PG = cs.PQ + (0 * ND + e) * PL;
-        const R* PA = cs.PQ + (1 * ND + e) * PL;
-        const R* SH = cs.PQ + (2 * ND + e) * PL;
-        const R* PGS = cs.PQ + (3 * ND + e) * PL;
-        const R G = PG[hi] - PG[lo];
-        const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
-        R* B = Bbuf + gl * 3 * npm;
-        B[t] = cs.corr[e] * G;
-        B[npm + t] = cs.corr[e] * cs.corr[ND + e] * X;
-        B[2 * npm + t] = cs.corr[2 * ND + e] * G;
+      for (int g = g0; g < g1; ++g) {
+        const int Lg = m.grp_L[g], nE = m.grp_nE[g];
+        const int* gp = m.grp_pair + g * npm;
+        R* B = Bbuf + (g - g0) * 3 * npm;
+        for (int t = tid; t < Lg * (Lg + 1) / 2; t += nth) {
+          const int pk = gp[t];
+          const int e = pk & 255, lo = pk >> 8, hi = lo + nE;
+          const R* PG = cs.PQ + e * PL;
+          const R* PA = PG + ND * PL;
+          const R* SH = PA + ND * PL;
+          const R* PGS = SH + ND * PL;
+          const R G = PG[hi] - PG[lo];
+          const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
+          const Q4<R> cr = cs.crq[e];
+          B[t] = cr.a * G;
+          B[npm + t] = cr.b * X;
+          B[2 * npm + t] = cr.c * G;
+        }
       }
       __syncthreads();
-      for (int s = m.grp_swap0[g0] + warp; s < m.grp_swap0[g1]; s += nw) {
+      // chunks of <= 16 pairs, one thread each (partials per chunk, summed per swap below); the
+      // chunks of a swap interleave (stride nk), so neighbouring threads read neighbouring pairs
+      for (int c = m.grp_chunk0[g0] + tid; c < m.grp_chunk0[g1]; c += nth) {
+        const int2 ck = m.chunk[c];
+        const int s = ck.x, k = ck.y & 0xffff, nk = ck.y >> 16, L = m.swap_L[s], np = L * (L + 1) / 2;
         const R* B = Bbuf + (m.swap_grp[s] - g0) * 3 * npm;
-        const int L = m.swap_L[s];
         const R* Cs = Call + m.swap_coff[s];
         R v1 = 0, v2 = 0, v3 = 0;
-        for (int t = lane; t < L * (L + 1) / 2; t += 32) {
+#pragma unroll 4
+        for (int t = k; t < np; t += nk) {
           const R w = Cs[t];
           v1 += w * B[t];
           v2 += w * B[npm + t];
           v3 += w * B[2 * npm + t];
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          v1 += __shfl_xor_sync(0xffffffffu, v1, off);
-          v2 += __shfl_xor_sync(0xffffffffu, v2, off);
-          v3 += __shfl_xor_sync(0xffffffffu, v3, off);
-        }
-        if (lane == 0) {
-          cs.Vs[s] = v1;
-          cs.Vs[m.n_swap + s] = v2;
-          cs.Vs[2 * m.n_swap + s] = v3;
-        }
+        cs.Pc[c] = v1;
+        cs.Pc[m.n_chunk + c] = v2;
+        cs.Pc[2 * m.n_chunk + c] = v3;
       }
       __syncthreads();
     }
     // the swap-rate SABR factors, one thread per swap
     for (int s = tid; s < m.n_swap; s += nth) {
-      const R v1 = cs.Vs[s], v2 = cs.Vs[m.n_swap + s], v3 = cs.Vs[2 * m.n_swap + s];
+      R v1 = 0, v2 = 0, v3 = 0;
+      for (int c = m.swap_chunk0[s]; c < m.swap_chunk0[s + 1]; ++c) {
+        v1 += cs.Pc[c];
+        v2 += cs.Pc[m.n_chunk + c];
+        v3 += cs.Pc[2 * m.n_chunk + c];
+      }
       const R TE = (R)m.T[m.swap_a[s]];
       const R al = M::sqrt_(v1 / TE);
       const R nu = M::sqrt_(R(2) * v2) / (al * TE);
