@@ -272,9 +272,31 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     grp_chunk0[j].push_back((int)chunk[j].size() / 2);
     swap_chunk0[j].push_back((int)chunk[j].size() / 2);
     m.n_chunk = (int)chunk[j].size() / 2;
+
     m.n_swap = (int)swap_a[j].size();
     m.max_win = max_win;
     m.NP = std::max(NP, 1);
+    // batches of expiry groups for the quadratic forms (after every size the CTA scratch depends on)
+    {
+      auto most = [&](int GB) {
+        int mx = 1;
+        for (int g0 = 0; g0 < m.n_grp; g0 += GB)
+          mx = std::max(mx, grp_chunk0[j][std::min(m.n_grp, g0 + GB)] - grp_chunk0[j][g0]);
+        return mx;
+      };
+      const int cap = m.NA * cta_y_stride(), per = 3 * m.max_npk;
+      auto place = [&](int GB) {   // partials after the B matrices in Y if they fit, else their own region
+        m.qf_gb = GB;
+        m.max_batch_chunks = most(GB);
+        const int off = GB > 1 ? (GB * per + 3) / 4 * 4 : 0;   // GB = 1 keeps its B matrices in Bg
+        m.qf_pc_off = off + 3 * m.max_batch_chunks <= cap ? off : -1;
+      };
+      int GB = cap >= 2 * per ? cap / per : 1;
+      while (GB > 1 && most(GB) > kMaxBatchChunks) --GB;
+      place(GB);
+      // the FP64 CTA must fit: give up groups per barrier (the partials then share the Y region)
+      while (GB > 1 && smem_bytes_cta<double>(m) > 227u * 1024u) place(--GB);
+    }
     HostMarket& h = hm[j];
     h.model = d.model; h.formula = d.formula; h.n_param = d.n_param; h.n_fwd = d.n_fwd;
     h.n_cap = d.n_cap; h.n_swp = d.n_swp; h.beta = d.beta;

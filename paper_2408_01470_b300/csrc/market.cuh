@@ -106,6 +106,9 @@ struct DevMarket {
                                    //   the pairs t = k, k + nk, ... (ordered by group, then swap)
   const int* grp_chunk0;           // [n_grp + 1] first chunk of each group
   const int* swap_chunk0;          // [n_swap + 1] first chunk of each swap
+  int qf_gb;                       // expiry groups whose B matrices are built per barrier
+  int max_batch_chunks;            // most chunks in one such batch
+  int qf_pc_off;                   // offset of the chunk partials in the Y region, or -1 (own region)
   double beta, panel;
   // raw description
   const double *T, *P, *cap_K, *cap_vol, *cap_wu, *swp_K, *swp_vol, *swp_wu;

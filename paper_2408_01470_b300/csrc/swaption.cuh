@@ -38,7 +38,7 @@ template <class R> struct CtaScratch {
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
   R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
   Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}
-  R* Pc;            // [3 x n_chunk] partial sums of the quadratic forms, per chunk of pairs
+  R* Pc;            // [3 x max_batch_chunks] partial sums of one batch's chunks of pairs
 };
 
 __host__ __device__ inline int cta_y_stride() { return 84; }   // 16-byte rows, conflict-free 4-vector loads
@@ -46,13 +46,19 @@ __host__ __device__ inline int cta_y_stride() { return 84; }   // 16-byte rows, 
 // (address stride 1 - pitch along a column) fall on distinct banks.
 __host__ __device__ inline int cta_pq_len(int NA) { return (NA + 2) & ~1; }
 
+// The quadratic forms reuse the Y region (dead after the Grams): the B matrices of qf_gb expiry
+// groups (when two or more fit; else one group at a time in Bg) and, after them, the partial sums
+// of the batch's chunks.  The host picks qf_gb (at most kMaxBatchChunks chunks per batch) and the
+// partials' place (qf_pc_off; -1: their own region of 3 x max_batch_chunks).
+constexpr int kMaxBatchChunks = 512;
+
 __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int NAc = round_up(m.NA, 4);
   const int Lg = m.max_gwin;
   return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + round_up(m.NA * cta_y_stride(), 4) +
                       round_up(4 * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND +
                       round_up(3 * (Lg * (Lg + 1) / 2), 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
-                      round_up(3 * m.n_chunk, 4),
+                      (m.qf_pc_off >= 0 ? 0 : round_up(3 * m.max_batch_chunks, 4)),
                   4);
 }
 
@@ -389,9 +395,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   {
     const R* Call = swap_C_of<R>(m);
     const int npm = m.max_npk;
-    R* Bbuf = cs.Bg;
-    int GB = 1;
-    if (NA * YS >= 6 * npm) { Bbuf = cs.Y; GB = (NA * YS) / (3 * npm); }
+    const int GB = m.qf_gb;
+    R* Bbuf = GB > 1 ? cs.Y : cs.Bg;
+    R* Pc = m.qf_pc_off >= 0 ? cs.Y + m.qf_pc_off : cs.Pc;
     for (int g0 = 0; g0 < m.n_grp; g0 += GB) {
       const int g1 = min(m.n_grp, g0 + GB);
       for (int g = g0; g < g1; ++g) {
@@ -416,7 +422,8 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       __syncthreads();
       // chunks of <= 16 pairs, one thread each (partials per chunk, summed per swap below); the
       // chunks of a swap interleave (stride nk), so neighbouring threads read neighbouring pairs
-      for (int c = m.grp_chunk0[g0] + tid; c < m.grp_chunk0[g1]; c += nth) {
+      const int c0 = m.grp_chunk0[g0];
+      for (int c = c0 + tid; c < m.grp_chunk0[g1]; c += nth) {
         const int2 ck = m.chunk[c];
         const int s = ck.x, k = ck.y & 0xffff, nk = ck.y >> 16, L = m.swap_L[s], np = L * (L + 1) / 2;
         const R* B = Bbuf + (m.swap_grp[s] - g0) * 3 * npm;
@@ -429,38 +436,41 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
           v2 += w * B[npm + t];
           v3 += w * B[2 * npm + t];
         }
-        cs.Pc[c] = v1;
-        cs.Pc[m.n_chunk + c] = v2;
-        cs.Pc[2 * m.n_chunk + c] = v3;
+        const int pc = c - c0, nb = m.max_batch_chunks;
+        Pc[pc] = v1;
+        Pc[nb + pc] = v2;
+        Pc[2 * nb + pc] = v3;
       }
       __syncthreads();
-    }
-    // the swap-rate SABR factors, one thread per swap
-    for (int s = tid; s < m.n_swap; s += nth) {
-      R v1 = 0, v2 = 0, v3 = 0;
-      for (int c = m.swap_chunk0[s]; c < m.swap_chunk0[s + 1]; ++c) {
-        v1 += cs.Pc[c];
-        v2 += cs.Pc[m.n_chunk + c];
-        v3 += cs.Pc[2 * m.n_chunk + c];
+      // per swap of the batch: its chunks added in order, then the swap-rate SABR factors (the
+      // next batch overwrites Pc only after its own B-build barrier)
+      for (int s = m.grp_swap0[g0] + tid; s < m.grp_swap0[g1]; s += nth) {
+        const int nb = m.max_batch_chunks;
+        R v1 = 0, v2 = 0, v3 = 0;
+        for (int c = m.swap_chunk0[s]; c < m.swap_chunk0[s + 1]; ++c) {
+          v1 += Pc[c - c0];
+          v2 += Pc[nb + c - c0];
+          v3 += Pc[2 * nb + c - c0];
+        }
+        const R TE = (R)m.T[m.swap_a[s]];
+        const R al = M::sqrt_(v1 / TE);
+        const R nu = M::sqrt_(R(2) * v2) / (al * TE);
+        R rho = v3 / v1;
+        rho = rho > R(0.999) ? R(0.999) : (rho < R(-0.999) ? R(-0.999) : rho);
+        Q4<R> f;
+        f.a = al;
+        f.b = nu / al;
+        f.c = al * al;
+        f.d = rho * nu * al;
+        cs.F4s[s] = f;
+        cs.A3s[s] = (R(2) - R(3) * rho * rho) * nu * nu;
+        Q4<R> q;
+        q.a = rho;
+        q.b = R(1) / (R(1) - rho);
+        q.c = R(1) / (R(1) + rho);
+        q.d = (R(1) - rho) * (R(1) + rho);
+        cs.RCs[s] = q;
       }
-      const R TE = (R)m.T[m.swap_a[s]];
-      const R al = M::sqrt_(v1 / TE);
-      const R nu = M::sqrt_(R(2) * v2) / (al * TE);
-      R rho = v3 / v1;
-      rho = rho > R(0.999) ? R(0.999) : (rho < R(-0.999) ? R(-0.999) : rho);
-      Q4<R> f;
-      f.a = al;
-      f.b = nu / al;
-      f.c = al * al;
-      f.d = rho * nu * al;
-      cs.F4s[s] = f;
-      cs.A3s[s] = (R(2) - R(3) * rho * rho) * nu * nu;
-      Q4<R> q;
-      q.a = rho;
-      q.b = R(1) / (R(1) - rho);
-      q.c = R(1) / (R(1) + rho);
-      q.d = (R(1) - rho) * (R(1) + rho);
-      cs.RCs[s] = q;
     }
     __syncthreads();
   }
