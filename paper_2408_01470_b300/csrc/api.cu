@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -86,12 +87,19 @@ struct sabr_lmm_anneal_plan {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
   void* lm_buf = nullptr;         // polish buffers (top-k points, selection, LM work) per market
   std::vector<size_t> lm_off;
-  // batch mode: one persistent launch per level over every market's chains
+  // batch mode: per temperature level one persistent launch per shared-memory bucket (markets
+  // grouped by the CTAs per SM their shared memory allows), each over its markets' chains
   bool batch = false;
   void* batch_buf = nullptr;
-  BatchArgs ba{};
-  int bthreads = 256, bgrid = 148;
-  uint32_t bsmem = 0;
+  BatchArgs ba{};                 // every market (start and final kernels)
+  uint32_t bsmem = 0;             // the largest market's shared memory
+  struct Bucket {
+    BatchArgs ba;                 // the bucket's markets (order, count, work counters)
+    uint32_t smem = 0;
+    int per_sm = 1, threads = 256, grid = 148;
+    std::vector<int> markets;     // host copy of the bucket's order
+  };
+  std::vector<Bucket> bk;
 };
 
 namespace {
@@ -719,8 +727,7 @@ cudaError_t enqueue_anneal(const DevMarket& m, int prec, const SAState& st, cons
 }
 
 template <class R, int FORMULA>
-cudaError_t enqueue_batch_t(const sabr_lmm_anneal_plan* p, cudaStream_t s, int threads, int grid, int levels,
-                            bool configure_only) {
+cudaError_t enqueue_batch_t(const sabr_lmm_anneal_plan* p, cudaStream_t s, int levels, bool configure_only) {
   auto k0 = sa_start_batch_kernel<R, FORMULA>;
   auto k1 = sa_level_batch_kernel<R, FORMULA>;
   if (configure_only) {
@@ -728,87 +735,102 @@ cudaError_t enqueue_batch_t(const sabr_lmm_anneal_plan* p, cudaStream_t s, int t
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->bsmem);
     return e;
   }
-  cudaError_t e = cudaMemsetAsync(p->ba.item_ctr, 0, (size_t)p->opts.n_levels * sizeof(unsigned int), s);
+  // every bucket's counters are one contiguous run after the first bucket's
+  cudaError_t e = cudaMemsetAsync(p->bk[0].ba.item_ctr, 0,
+                                  p->bk.size() * (size_t)p->opts.n_levels * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   k0<<<p->ba.n_markets, 256, p->bsmem, s>>>(p->ba);
-  for (int l = 0; l < levels; ++l) k1<<<grid, threads, p->bsmem, s>>>(p->ba, l);
+  for (int l = 0; l < levels; ++l)
+    for (const auto& b : p->bk) k1<<<b.grid, b.threads, b.smem, s>>>(b.ba, l);
   sa_final_batch_kernel<<<p->ba.n_markets, 1024, 0, s>>>(p->ba);
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_batch(const sabr_lmm_anneal_plan* p, cudaStream_t s, int threads, int grid, int levels,
-                          bool configure_only = false) {
+cudaError_t enqueue_batch(const sabr_lmm_anneal_plan* p, cudaStream_t s, int levels, bool configure_only = false) {
   const bool f64 = p->opts.prec == SABR_LMM_FP64;
   const int formula = p->mk->dm[0].formula;
-  if (f64) return formula == 0 ? enqueue_batch_t<double, 0>(p, s, threads, grid, levels, configure_only)
-                               : enqueue_batch_t<double, 1>(p, s, threads, grid, levels, configure_only);
-  return formula == 0 ? enqueue_batch_t<float, 0>(p, s, threads, grid, levels, configure_only)
-                      : enqueue_batch_t<float, 1>(p, s, threads, grid, levels, configure_only);
+  if (f64) return formula == 0 ? enqueue_batch_t<double, 0>(p, s, levels, configure_only)
+                               : enqueue_batch_t<double, 1>(p, s, levels, configure_only);
+  return formula == 0 ? enqueue_batch_t<float, 0>(p, s, levels, configure_only)
+                      : enqueue_batch_t<float, 1>(p, s, levels, configure_only);
 }
 
-// Autotuner of the batch launch: CTA size x persistent grid, chosen by timing one level of a
-// short probe (4 steps per chain) per candidate; cached per (precision, formula, instrument
-// bucket, market-count bucket).
+int batch_blocks_per_sm(int prec, int threads, uint32_t smem) {
+  int per_sm = 0;
+  if (prec == SABR_LMM_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<double, 0>, threads, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<float, 0>, threads, smem);
+  return per_sm;
+}
+
+// Autotuner of the batch launches: per shared-memory bucket, CTA size x persistent grid, chosen by
+// timing one level of a short probe (4 steps per chain) per candidate while the other buckets keep
+// their settings; cached per (precision, formula, instrument bucket, market-count bucket, CTAs/SM).
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 sabr_lmm_status tune_batch(sabr_lmm_anneal_plan* p, cudaStream_t s) {
-  int max_instr = 0;
-  for (const DevMarket& m : p->mk->dm) max_instr = std::max(max_instr, m.n_cap + m.n_swp);
-  const auto key = std::make_tuple(p->opts.prec, p->mk->dm[0].formula, (max_instr + 255) / 256,
-                                   (p->ba.n_markets + 63) / 64);
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) { p->bthreads = it->second.first; p->bgrid = it->second.second; return SABR_LMM_OK; }
-  }
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  std::vector<std::pair<int, int>> cand;
-  for (int threads : {128, 256}) {
-    int per_sm = 0;
-    cudaError_t e = p->opts.prec == SABR_LMM_FP64
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<double, 0>, threads, p->bsmem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<float, 0>, threads, p->bsmem);
-    if (e != cudaSuccess || per_sm < 1) continue;
-    cand.push_back({threads, nsm * per_sm});
-    cand.push_back({threads, 2 * nsm * per_sm});
-  }
-  if (cand.empty()) return fail(SABR_LMM_ENOTSUP, "a batch market does not fit in one CTA's shared memory");
-  // probe: the same search shortened to 4 steps, one level
   std::vector<SAParams> probe(p->sp);
   for (auto& q : probe) q.N = std::min(q.N, 4);
-  CUDA_TRY(cudaMemcpyAsync((void*)p->ba.sp, probe.data(), probe.size() * sizeof(SAParams), cudaMemcpyHostToDevice, s));
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  float best_ms = 1e30f;
-  std::pair<int, int> best = cand[0];
-  for (const auto& c : cand) {
-    CUDA_TRY(enqueue_batch(p, s, c.first, c.second, 1));   // warm-up
-    CUDA_TRY(cudaEventRecord(a, s));
-    CUDA_TRY(enqueue_batch(p, s, c.first, c.second, 1));
-    CUDA_TRY(cudaEventRecord(b, s));
-    CUDA_TRY(cudaEventSynchronize(b));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (ms < best_ms) { best_ms = ms; best = c; }
+  bool probing = false;
+  cudaEvent_t a = nullptr, b = nullptr;
+  for (auto& bk : p->bk) {
+    int max_instr = 0;
+    for (int j : bk.markets) max_instr = std::max(max_instr, p->mk->dm[j].n_cap + p->mk->dm[j].n_swp);
+    const auto key = std::make_tuple(p->opts.prec, p->mk->dm[0].formula, (max_instr + 255) / 256,
+                                     (bk.ba.n_markets + 63) / 64, bk.per_sm);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) { bk.threads = it->second.first; bk.grid = it->second.second; continue; }
+    }
+    std::vector<std::pair<int, int>> cand;
+    for (int threads : {128, 256}) {
+      const int per_sm = batch_blocks_per_sm(p->opts.prec, threads, bk.smem);
+      if (per_sm < 1) continue;
+      cand.push_back({threads, nsm * per_sm});
+      cand.push_back({threads, 2 * nsm * per_sm});
+    }
+    if (cand.empty()) return fail(SABR_LMM_ENOTSUP, "a batch market does not fit in one CTA's shared memory");
+    if (!probing) {
+      CUDA_TRY(cudaMemcpyAsync((void*)p->ba.sp, probe.data(), probe.size() * sizeof(SAParams), cudaMemcpyHostToDevice, s));
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      probing = true;
+    }
+    float best_ms = 1e30f;
+    std::pair<int, int> best = cand[0];
+    for (const auto& c : cand) {
+      bk.threads = c.first;
+      bk.grid = c.second;
+      CUDA_TRY(enqueue_batch(p, s, 1));   // warm-up
+      CUDA_TRY(cudaEventRecord(a, s));
+      CUDA_TRY(enqueue_batch(p, s, 1));
+      CUDA_TRY(cudaEventRecord(b, s));
+      CUDA_TRY(cudaEventSynchronize(b));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    bk.threads = best.first;
+    bk.grid = best.second;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  CUDA_TRY(cudaMemcpyAsync((void*)p->ba.sp, p->sp.data(), p->sp.size() * sizeof(SAParams), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  p->bthreads = best.first;
-  p->bgrid = best.second;
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = best;
+  if (probing) {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    CUDA_TRY(cudaMemcpyAsync((void*)p->ba.sp, p->sp.data(), p->sp.size() * sizeof(SAParams), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
   return SABR_LMM_OK;
 }
 
 sabr_lmm_status enqueue_plan(sabr_lmm_anneal_plan* p, cudaStream_t s) {
   if (p->batch) {
-    cudaError_t e = enqueue_batch(p, s, p->bthreads, p->bgrid, p->opts.n_levels);
+    cudaError_t e = enqueue_batch(p, s, p->opts.n_levels);
     if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
     return SABR_LMM_OK;
   }
@@ -908,21 +930,34 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (batchable) {
     p->batch = true;
     uint32_t smax = 0;
-    std::vector<std::pair<long long, int>> cost;
+    // buckets by the CTAs per SM each market's shared memory allows; LPT order inside a bucket
+    std::map<int, std::vector<std::pair<long long, int>>, std::greater<int>> buckets;
+    std::map<int, uint32_t> bsm;
     for (int j = 0; j < nm; ++j) {
       const DevMarket& m = mk->dm[j];
-      smax = std::max(smax, o->prec == SABR_LMM_FP64 ? smem_bytes_cta<double>(m) : smem_bytes_cta<float>(m));
-      cost.push_back({-(long long)(m.n_cap + 4 * m.n_swp + 60 * m.n_swap), j});
+      const uint32_t sm = o->prec == SABR_LMM_FP64 ? smem_bytes_cta<double>(m) : smem_bytes_cta<float>(m);
+      if (sm > 227 * 1024) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOTSUP, "a batch market does not fit in one CTA's shared memory at this precision"); }
+      smax = std::max(smax, sm);
+      const int per_sm = std::max(1, batch_blocks_per_sm(o->prec, 256, sm));
+      buckets[per_sm].push_back({-(long long)(m.n_cap + 4 * m.n_swp + 60 * m.n_swap), j});
+      bsm[per_sm] = std::max(bsm[per_sm], sm);
     }
-    std::sort(cost.begin(), cost.end());
-    std::vector<int> order;
-    for (auto& c : cost) order.push_back(c.second);
-    if (smax > 227 * 1024) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOTSUP, "a batch market does not fit in one CTA's shared memory at this precision"); }
     p->bsmem = smax;
+    std::vector<int> order;
+    for (auto& kv : buckets) {
+      std::sort(kv.second.begin(), kv.second.end());
+      sabr_lmm_anneal_plan::Bucket b;
+      b.per_sm = kv.first;
+      b.smem = bsm[kv.first];
+      b.ba.n_markets = (int)kv.second.size();
+      for (auto& c : kv.second) { order.push_back(c.second); b.markets.push_back(c.second); }
+      p->bk.push_back(b);
+    }
+    const int nb = (int)p->bk.size();
     Arena B;
     const size_t o_mk = B.take(nm * sizeof(DevMarket)), o_st = B.take(nm * sizeof(SAState)),
                  o_sp = B.take(nm * sizeof(SAParams)), o_or = B.take(nm * sizeof(int)),
-                 o_ct = B.take((size_t)o->n_levels * sizeof(unsigned int));
+                 o_ct = B.take((size_t)nb * o->n_levels * sizeof(unsigned int));
     if (cudaMalloc(&p->batch_buf, B.size) != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOMEM, "cudaMalloc of the batch tables failed"); }
     char* bb = (char*)p->batch_buf;
     p->ba.mk = (const DevMarket*)(bb + o_mk);
@@ -932,6 +967,16 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     p->ba.item_ctr = (unsigned int*)(bb + o_ct);
     p->ba.n_markets = nm;
     p->ba.C = o->n_chains;
+    int first = 0;
+    for (int i = 0; i < nb; ++i) {
+      BatchArgs& a = p->bk[i].ba;
+      const int n = a.n_markets;
+      a = p->ba;
+      a.n_markets = n;
+      a.order = p->ba.order + first;
+      a.item_ctr = p->ba.item_ctr + (size_t)i * o->n_levels;
+      first += n;
+    }
     cudaMemcpyAsync(bb + o_mk, mk->dm.data(), nm * sizeof(DevMarket), cudaMemcpyHostToDevice, p->stream);
     cudaMemcpyAsync(bb + o_st, p->st.data(), nm * sizeof(SAState), cudaMemcpyHostToDevice, p->stream);
     cudaMemcpyAsync(bb + o_sp, p->sp.data(), nm * sizeof(SAParams), cudaMemcpyHostToDevice, p->stream);
@@ -952,7 +997,7 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, std::string("configure: ") + cudaGetErrorString(e)); }
   }
   if (p->batch) {
-    cudaError_t e = enqueue_batch(p, p->stream, 256, 1, 0, true);
+    cudaError_t e = enqueue_batch(p, p->stream, 0, true);
     if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, std::string("configure: ") + cudaGetErrorString(e)); }
   }
   for (int j = 0; j < nm; ++j) {
@@ -964,13 +1009,13 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (e != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ECUDA, cudaGetErrorString(e)); }
   if (p->batch) {
     if (o->warps_per_block > 0) {
-      p->bthreads = o->warps_per_block >= 8 ? 256 : 128;
-      int dev = 0, nsm = 148, per_sm = 1;
+      int dev = 0, nsm = 148;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      if (o->prec == SABR_LMM_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<double, 0>, p->bthreads, p->bsmem);
-      else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<float, 0>, p->bthreads, p->bsmem);
-      p->bgrid = nsm * std::max(per_sm, 1);
+      for (auto& b : p->bk) {
+        b.threads = o->warps_per_block >= 8 ? 256 : 128;
+        b.grid = nsm * std::max(batch_blocks_per_sm(o->prec, b.threads, b.smem), 1);
+      }
     } else {
       sabr_lmm_status st = tune_batch(p, p->stream);
       if (st != SABR_LMM_OK) { sabr_lmm_anneal_plan_free(p); return st; }
