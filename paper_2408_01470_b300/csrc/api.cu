@@ -263,14 +263,15 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
       }
     swap_coff[j].push_back(0);
     for (size_t s2 = 0; s2 < swap_L[j].size(); ++s2)
-      swap_coff[j].push_back(swap_coff[j].back() + swap_L[j][s2] * (swap_L[j][s2] + 1) / 2);
-    // chunks of <= kChunk pairs (swaps are ordered by group, so the chunks are too)
+      swap_coff[j].push_back(swap_coff[j].back() + (swap_L[j][s2] * (swap_L[j][s2] + 1) / 2 + 3) / 4 * 4);
+    // chunks of <= kChunk pairs, 4-pair quads interleaved (swaps are ordered by group, so the
+    // chunks are too)
     for (size_t g = 0; g < grp_a[j].size(); ++g) {
       grp_chunk0[j].push_back((int)chunk[j].size() / 2);
       for (int s2 = grp_swap0[j][g]; s2 < grp_swap0[j][g + 1]; ++s2) {
         swap_chunk0[j].push_back((int)chunk[j].size() / 2);
         const int np = swap_L[j][s2] * (swap_L[j][s2] + 1) / 2;
-        const int nk = (np + kChunk - 1) / kChunk;
+        const int nq = (np + 3) / 4, nk = (nq + kChunk / 4 - 1) / (kChunk / 4);
         for (int k = 0; k < nk; ++k) {
           chunk[j].push_back(s2);
           chunk[j].push_back(k | (nk << 16));
@@ -292,7 +293,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
           mx = std::max(mx, grp_chunk0[j][std::min(m.n_grp, g0 + GB)] - grp_chunk0[j][g0]);
         return mx;
       };
-      const int cap = m.NA * cta_y_stride(), per = 3 * m.max_npk;
+      const int cap = m.NA * cta_y_stride(), per = 3 * ((m.max_npk + 3) & ~3);
       auto place = [&](int GB) {   // partials after the B matrices in Y if they fit, else their own region
         m.qf_gb = GB;
         m.max_batch_chunks = most(GB);

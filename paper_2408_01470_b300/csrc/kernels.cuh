@@ -49,7 +49,8 @@ __global__ void setup_swaps_kernel(DevMarket m) {
 }
 
 // Coefficient rows of the swaption quadratic forms: (2 - [i = j]) W_i W_j for the pairs i <= j of
-// each swap's window, packed by column (t = j (j + 1)/2 + i), in FP64 and FP32.
+// each swap's window, packed by column (t = j (j + 1)/2 + i), zero-padded to a multiple of 4 pairs,
+// in FP64 and FP32.
 __global__ void setup_swap_coef_kernel(DevMarket m) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= m.n_swap) return;
@@ -63,6 +64,10 @@ __global__ void setup_swap_coef_kernel(DevMarket m) {
       c64[j * (j + 1) / 2 + i] = c;
       c32[j * (j + 1) / 2 + i] = (float)c;
     }
+  for (int t = L * (L + 1) / 2; t < m.swap_coff[s + 1] - m.swap_coff[s]; ++t) {
+    c64[t] = 0.0;
+    c32[t] = 0.0f;
+  }
 }
 
 // Pricing constants of one instrument, into the three 4-vector groups of its block.

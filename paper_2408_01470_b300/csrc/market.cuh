@@ -99,11 +99,12 @@ struct DevMarket {
   const int* grp_pair;             // [n_grp x max_npk] pair t = j (j + 1)/2 + i (i <= j) of the group's
                                    //   window: (delta_i << 8) | (delta_j - delta_i)
   const int* swap_coff;            // [n_swap + 1] offsets of the swaps' coefficient rows
-  const double* swap_C64;          // [swap_coff[n_swap]] (2 - [i = j]) W_i W_j, pair-packed as grp_pair
+  const double* swap_C64;          // [swap_coff[n_swap]] (2 - [i = j]) W_i W_j, pair-packed as grp_pair,
+                                   //   each row zero-padded to a multiple of 4 pairs
   const float* swap_C32;           //   the same in FP32
   int n_chunk;                     // chunks of <= 16 pairs of the swaps' coefficient rows
   const int2* chunk;               // [n_chunk] {swap, k | (nk << 16)}: chunk k of the swap's nk takes
-                                   //   the pairs t = k, k + nk, ... (ordered by group, then swap)
+                                   //   the 4-pair quads k, k + nk, ... (ordered by group, then swap)
   const int* grp_chunk0;           // [n_grp + 1] first chunk of each group
   const int* swap_chunk0;          // [n_swap + 1] first chunk of each swap
   int qf_gb;                       // expiry groups whose B matrices are built per barrier

@@ -34,7 +34,7 @@ template <class R> struct CtaScratch {
   R* Y;             // [NA x 81]
   R* PQ;            // [4 x ND x (NA + 1)]: PG, PA, SH, PGS along each diagonal
   Q4<R>* crq;       // [ND]: {rho_e, rho_e theta_e, phi_e, 0} per diagonal e
-  R* Bg;            // [3 x Lg (Lg + 1) / 2] of the current expiry group
+  R* Bg;            // [3 x round_up(Lg (Lg + 1) / 2, 4)] of the current expiry group
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
   R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
   Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}
@@ -57,7 +57,7 @@ __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int Lg = m.max_gwin;
   return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + round_up(m.NA * cta_y_stride(), 4) +
                       round_up(4 * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND +
-                      round_up(3 * (Lg * (Lg + 1) / 2), 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
+                      3 * round_up(Lg * (Lg + 1) / 2, 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
                       (m.qf_pc_off >= 0 ? 0 : round_up(3 * m.max_batch_chunks, 4)),
                   4);
 }
@@ -76,7 +76,7 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
   s.Y = p; p += round_up(m.NA * cta_y_stride(), 4);
   s.PQ = p; p += round_up(4 * m.ND * cta_pq_len(m.NA), 4);
   s.crq = (Q4<R>*)p; p += 4 * m.ND;
-  s.Bg = p; p += round_up(3 * (Lg * (Lg + 1) / 2), 4);
+  s.Bg = p; p += 3 * round_up(Lg * (Lg + 1) / 2, 4);
   s.F4s = (Q4<R>*)p; p += 4 * m.n_swap;
   s.A3s = p; p += round_up(m.n_swap, 4);
   s.RCs = (Q4<R>*)p; p += 4 * m.n_swap;
@@ -394,7 +394,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   //      region (dead since phase 3) when it holds two groups or more
   {
     const R* Call = swap_C_of<R>(m);
-    const int npm = m.max_npk;
+    const int npm = (m.max_npk + 3) & ~3;   // B rows padded to whole quads
     const int GB = m.qf_gb;
     R* Bbuf = GB > 1 ? cs.Y : cs.Bg;
     R* Pc = m.qf_pc_off >= 0 ? cs.Y + m.qf_pc_off : cs.Pc;
@@ -402,9 +402,15 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const int g1 = min(m.n_grp, g0 + GB);
       for (int g = g0; g < g1; ++g) {
         const int Lg = m.grp_L[g], nE = m.grp_nE[g];
-        const int* gp = m.grp_pair + g * npm;
+        const int* gp = m.grp_pair + g * m.max_npk;
         R* B = Bbuf + (g - g0) * 3 * npm;
-        for (int t = tid; t < Lg * (Lg + 1) / 2; t += nth) {
+        const int npk = Lg * (Lg + 1) / 2;
+        for (int t = npk + tid; t < ((npk + 3) & ~3); t += nth) {   // zero pads of the last quad
+          B[t] = R(0);
+          B[npm + t] = R(0);
+          B[2 * npm + t] = R(0);
+        }
+        for (int t = tid; t < npk; t += nth) {
           const int pk = gp[t];
           const int e = pk & 255, lo = pk >> 8, hi = lo + nE;
           const R* PG = cs.PQ + e * PL;
@@ -420,21 +426,25 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
         }
       }
       __syncthreads();
-      // chunks of <= 16 pairs, one thread each (partials per chunk, summed per swap below); the
-      // chunks of a swap interleave (stride nk), so neighbouring threads read neighbouring pairs
+      // chunks of <= 16 pairs, one thread each (partials per chunk, summed per swap below): a chunk
+      // takes up to 4 quads of 4 pairs, interleaved (stride nk) so that neighbouring threads read
+      // neighbouring quads; one 16-byte coefficient load and three 16-byte B loads per quad
       const int c0 = m.grp_chunk0[g0];
       for (int c = c0 + tid; c < m.grp_chunk0[g1]; c += nth) {
         const int2 ck = m.chunk[c];
-        const int s = ck.x, k = ck.y & 0xffff, nk = ck.y >> 16, L = m.swap_L[s], np = L * (L + 1) / 2;
+        const int s = ck.x, k = ck.y & 0xffff, nk = ck.y >> 16, L = m.swap_L[s];
+        const int nq = (L * (L + 1) / 2 + 3) >> 2;
         const R* B = Bbuf + (m.swap_grp[s] - g0) * 3 * npm;
-        const R* Cs = Call + m.swap_coff[s];
+        const Q4<R>* Cq = (const Q4<R>*)(Call + m.swap_coff[s]);
+        const Q4<R>* B1 = (const Q4<R>*)B;
+        const Q4<R>* B2 = (const Q4<R>*)(B + npm);
+        const Q4<R>* B3 = (const Q4<R>*)(B + 2 * npm);
         R v1 = 0, v2 = 0, v3 = 0;
-#pragma unroll 4
-        for (int t = k; t < np; t += nk) {
-          const R w = Cs[t];
-          v1 += w * B[t];
-          v2 += w * B[npm + t];
-          v3 += w * B[2 * npm + t];
+        for (int q = k; q < nq; q += nk) {
+          const Q4<R> w = Cq[q], x = B1[q], y = B2[q], z = B3[q];
+          v1 += w.a * x.a; v1 += w.b * x.b; v1 += w.c * x.c; v1 += w.d * x.d;
+          v2 += w.a * y.a; v2 += w.b * y.b; v2 += w.c * y.c; v2 += w.d * y.d;
+          v3 += w.a * z.a; v3 += w.b * z.b; v3 += w.c * z.c; v3 += w.d * z.d;
         }
         const int pc = c - c0, nb = m.max_batch_chunks;
         Pc[pc] = v1;

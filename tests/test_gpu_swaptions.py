@@ -1,7 +1,8 @@
 """GPU-vs-oracle parity for markets with swaptions (S3 pair integrals, S5 quadratic forms, S6
 swaption pricing), through the C-ABI: FP64 objective within 1e-12 relative away from the optimum,
 FP64 vols within 1e-12 (see the prefix-sum note below), identical FP64 accept/reject
-trajectories, FP32 vols within 2e-4 vol-pt.  Markets: the 40-forward joint workload (300 caplets,
+trajectories, FP32 vols within 2e-4 vol-pt, the FP32 RMS-equivalent objective within 1e-4 vol-pt
+plus 1.5e-5 of itself.  Markets: the 40-forward joint workload (300 caplets,
 700 swaptions), a small joint market, a swaptions-only market and two members of the uneven batch
 (random windows and expiry groups).
 """
@@ -86,7 +87,14 @@ def test_swaption_objective_fp32_rms_equivalent(gpu_lib):
     fin = np.isfinite(f64) & np.isfinite(f32)
     n = sk.n_instr
     d = np.abs(np.sqrt(f32[fin] / n) - np.sqrt(f64[fin] / n)) * 100.0
-    assert np.max(d) <= 1e-4, np.max(d)
+    rms = np.sqrt(f64[fin] / n) * 100.0
+    # In FP32 the window integrals are differences of prefix sums along the diagonals, which
+    # cancel by up to ~ (offset + window) / window, so a swaption vol carries a relative error of a
+    # few 1e-6 and the RMS-equivalent objective moves by that fraction of itself (measured up to
+    # 8.2e-6 at random points whose RMS error is hundreds of vol-pt); near the optimum the bar is
+    # the absolute 1e-4 vol-pt
+    assert np.all(d <= 1e-4 + 1.5e-5 * rms), np.max(d - 1.5e-5 * rms)
+    assert d[-1] <= 1e-4                       # the generating point
 
 
 def test_swaption_anneal_fp64_trajectory_identical(gpu_lib):
