@@ -356,7 +356,8 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   }
   __syncthreads();
 
-  // ---- phase 4: exclusive prefix sums along each diagonal (one warp per diagonal)
+  // ---- phase 4: exclusive prefix sums along each diagonal (one warp per diagonal, two panels
+  //      per lane and chunk of 64)
   for (int e = warp; e < ND; e += nw) {
     const int n = NA - e;
     R* PG = cs.PQ + (0 * ND + e) * PL;
@@ -364,19 +365,29 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     R* SH = cs.PQ + (2 * ND + e) * PL;
     R* PGS = cs.PQ + (3 * ND + e) * PL;
     R cg = 0, ca = 0, chh = 0, cgs = 0;
-    for (int c0 = 0; c0 < n; c0 += 32) {
-      const int A = c0 + lane;
-      const bool in = A < n;
-      const R g = in ? PG[A] : R(0), ad = in ? PA[A] : R(0), hh = in ? SH[A] : R(0);
-      const R ig = warp_inclusive_scan(g, lane), ia = warp_inclusive_scan(ad, lane), ih = warp_inclusive_scan(hh, lane);
-      const R gs = g * (ih + chh);   // Gd(A) times the inclusive prefix of Hd at A
-      const R igs = warp_inclusive_scan(gs, lane);
+    for (int c0 = 0; c0 < n; c0 += 64) {
+      const int A0 = c0 + 2 * lane, A1 = A0 + 1;
+      const bool in0 = A0 < n, in1 = A1 < n;
+      const R g0 = in0 ? PG[A0] : R(0), a0 = in0 ? PA[A0] : R(0), h0 = in0 ? SH[A0] : R(0);
+      const R g1 = in1 ? PG[A1] : R(0), a1 = in1 ? PA[A1] : R(0), h1 = in1 ? SH[A1] : R(0);
+      // inclusive scans of the lane sums; a lane's exclusive start is its inclusive value less its sum
+      const R ig = warp_inclusive_scan(g0 + g1, lane), ia = warp_inclusive_scan(a0 + a1, lane);
+      const R ih = warp_inclusive_scan(h0 + h1, lane);
+      const R hx = chh + ih - (h0 + h1);              // exclusive prefix of Hd before A0
+      const R gs0 = g0 * (hx + h0), gs1 = g1 * (hx + h0 + h1);   // Gd(A) times the inclusive Hd prefix
+      const R igs = warp_inclusive_scan(gs0 + gs1, lane);
       __syncwarp();
-      if (in) {
-        PG[A] = cg + ig - g;
-        PA[A] = ca + ia - ad;
-        SH[A] = chh + ih - hh;
-        PGS[A] = cgs + igs - gs;
+      if (in0) {
+        PG[A0] = cg + ig - (g0 + g1);
+        PA[A0] = ca + ia - (a0 + a1);
+        SH[A0] = hx;
+        PGS[A0] = cgs + igs - (gs0 + gs1);
+      }
+      if (in1) {
+        PG[A1] = cg + ig - g1;
+        PA[A1] = ca + ia - a1;
+        SH[A1] = hx + h0;
+        PGS[A1] = cgs + igs - gs1;
       }
       cg += __shfl_sync(0xffffffffu, ig, 31);
       ca += __shfl_sync(0xffffffffu, ia, 31);
@@ -388,10 +399,10 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   }
   __syncthreads();
 
-  // ---- phase 5: the B matrices of a batch of expiry groups, then the quadratic forms of the
-  //      batch's swaps in interleaved chunks of <= 16 pairs (one thread per chunk, coefficient rows from the
-  //      market, partial sums per chunk added per swap in chunk order); the batch lives in the Y
-  //      region (dead since phase 3) when it holds two groups or more
+  // ---- phase 5: the B matrices of a batch of expiry groups, then the quadratic forms of the batch's swaps in chunks of <= 16 pairs (one thread per
+  //      chunk, coefficient rows from the market, partial sums per chunk added per swap in chunk
+  //      order); the batch lives in the Y region (dead since phase 3) when it holds two groups or
+  //      more
   {
     const R* Call = swap_C_of<R>(m);
     const int npm = (m.max_npk + 3) & ~3;   // B rows padded to whole quads
