@@ -245,6 +245,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-variant", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-joint-variant", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--profile", action="store_true",
@@ -351,6 +352,39 @@ def main():
                             "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
                                          "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS}}
         del plan64
+
+    # the mixed-precision, adjoint-polished form: a shortened FP32 search, then the Levenberg-Marquardt
+    # polish (adjoint gradient) of its 64 best chains; the shortest schedule that reaches the target
+    if args.prec == "fp32":
+        pol = None
+        for Ls in (5, 10, 20, 40, 80):
+            rp = gm.anneal(C, Ls, N, skel.cooling, seed, prec="fp32", lm_top_k=64, lm_max_iter=50,
+                           target_rmse=TARGET_RMSE_VOLPT)
+            if rp["rmse_volpt"][0] <= TARGET_RMSE_VOLPT:
+                pol = {"levels": Ls, "search_s": float(rp["seconds"]), "polish_s": float(rp["lm_seconds"]),
+                       "rmse_volpt": float(rp["rmse_volpt"][0])}
+                break
+        ttt["fp32_lm_polished_s"] = pol["search_s"] + pol["polish_s"] if pol else None
+        ttt["fp32_lm_polished"] = pol
+
+    # the joint caplet + swaption market (CTA-per-chain kernels), a shortened search for its rate
+    if args.prec == "fp32" and not args.no_joint_variant:
+        jm, jsks, _, jC, _, jN, jcool = workload_markets(lib, "joint")
+        jL = 5
+        jplan = jm.anneal_prepare(jC, jL, jN, jcool, seed, prec="fp32", use_graph=True, stream=s)
+        jplan.launch(stream=s)
+        s.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        jplan.launch(stream=s)
+        b.record(s)
+        s.synchronize()
+        tj = a.elapsed_time(b) / 1e3
+        rj = jplan.fetch()
+        variants["joint_fp32"] = {"workload": WORKLOADS["joint"], "levels_timed": jL,
+                                  "value": rj["n_evals"] * jsks[0].n_instr / tj, "unit": UNIT,
+                                  "ms_per_level": tj * 1e3 / jL}
+        del jplan, jm
 
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

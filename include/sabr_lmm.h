@@ -156,7 +156,8 @@ sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int32_t market
  *   T0 <= 0  -> T0 = f(x0) (1 if that is not a finite positive number).
  *   x0 NULL  -> box centre.  x0 is host memory [n_markets x n_param].
  *   lm_top_k > 0 -> Levenberg-Marquardt polish of the lm_top_k lowest best-ever chain points
- *   (lm_max_iter trials each, stop at target_rmse_volpt), the best polished point returned. */
+ *   (at most lm_max_iter trials; with target_rmse_volpt > 0 a point stops at the target and the
+ *   polish ends once any point has reached it), the best polished point returned. */
 typedef struct {
   int32_t n_chains;
   int32_t n_levels;

@@ -588,6 +588,7 @@ namespace {
 struct LmWork {
   double *Xp, *vols, *res, *grad, *gf, *mu, *f, *ft, *Xt, *rmse;
   int* done;
+  int* any;     // set once any point has reached the target
 };
 
 size_t lm_work_bytes(const DevMarket& m, int n) {
@@ -610,24 +611,35 @@ LmWork lm_carve(void* base, const DevMarket& m, int n) {
   w.rmse = p; p += n;
   w.Xt = p; p += (size_t)n * P;
   w.done = (int*)p;
+  w.any = w.done + n;   // inside the slack of lm_work_bytes
   return w;
 }
 
-__global__ void lm_init_kernel(int n, double* mu, int* done) {
+__global__ void lm_init_kernel(int n, double* mu, int* done, int* any) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) { mu[i] = 1e-3; done[i] = 0; }
+  if (i == 0) *any = 0;
 }
 
-// Enqueue max_iter LM iterations on the n points X (device, updated in place).
-cudaError_t lm_enqueue(const DevMarket& m, double* X, int n, int max_iter, double target, const LmWork& w, cudaStream_t s) {
+// Enqueue max_iter LM iterations on the n points X (device, updated in place).  With
+// stop_at_first (host-driven, never under stream capture) the iterations end as soon as any point
+// has reached the target RMSE: the host reads one flag per iteration.
+cudaError_t lm_enqueue(const DevMarket& m, double* X, int n, int max_iter, double target, const LmWork& w, cudaStream_t s,
+                       bool stop_at_first = false) {
   const int ni = m.n_cap + m.n_swp;
   const bool have_adjoint = m.n_swp == 0;
   cudaError_t e;
-  lm_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w.mu, w.done);
+  lm_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w.mu, w.done, w.any);
   if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, w.f, nullptr, s)) != cudaSuccess) return e;
   if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
-  lm_rmse_kernel<<<n, 256, 0, s>>>(m, n, w.vols, target, w.rmse, w.done);
+  lm_rmse_kernel<<<n, 256, 0, s>>>(m, n, w.vols, target, w.rmse, w.done, w.any);
+  auto reached = [&]() {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, w.any, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    return cudaStreamSynchronize(s) == cudaSuccess && h != 0;
+  };
   for (int it = 0; it < max_iter; ++it) {
+    if (stop_at_first && target > 0.0 && reached()) break;
     lm_perturb_kernel<<<n, 32, 0, s>>>(n, m.n_param, X, w.Xp);
     if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xp, (long long)n * kLmStencil, nullptr, w.vols, s)) != cudaSuccess) return e;
     residuals_from_vols_kernel<<<148 * 4, 256, 0, s>>>(m, (long long)n * kLmStencil, w.vols, w.res);
@@ -638,7 +650,7 @@ cudaError_t lm_enqueue(const DevMarket& m, double* X, int n, int max_iter, doubl
     if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xt, n, w.ft, nullptr, s)) != cudaSuccess) return e;
     lm_accept_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, m.n_param, X, w.Xt, w.f, w.ft, w.mu, w.done);
     if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
-    lm_rmse_kernel<<<n, 256, 0, s>>>(m, n, w.vols, target, w.rmse, w.done);
+    lm_rmse_kernel<<<n, 256, 0, s>>>(m, n, w.vols, target, w.rmse, w.done, w.any);
   }
   (void)ni;
   return cudaGetLastError();
@@ -1038,7 +1050,7 @@ sabr_lmm_status enqueue_polish(sabr_lmm_anneal_plan* p, cudaStream_t s) {
     const LmWork w = lm_carve(b + p->lm_off[3 * j + 2], m, k);
     select_lowest_kernel<<<1, 1024, 0, s>>>(p->st[j].fb, p->opts.n_chains, k, sel);
     gather_points_kernel<<<k, 32, 0, s>>>(p->st[j].xb, sel, k, m.n_param, X);
-    cudaError_t e = lm_enqueue(m, X, k, p->opts.lm_max_iter, p->opts.target_rmse_volpt, w, s);
+    cudaError_t e = lm_enqueue(m, X, k, p->opts.lm_max_iter, p->opts.target_rmse_volpt, w, s, true);
     if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("polish launch: ") + cudaGetErrorString(e));
     take_best_kernel<<<1, 32, 0, s>>>(X, w.f, k, m.n_param, p->st[j].best_x, p->st[j].best_f);
   }

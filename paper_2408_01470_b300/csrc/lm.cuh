@@ -146,7 +146,8 @@ __global__ void lm_accept_kernel(int n, int P, double* X, const double* Xt, doub
 }
 
 // RMSE in vol points of each point's model vols; marks points at or below the target as done.
-__global__ void lm_rmse_kernel(DevMarket m, int n, const double* vols, double target, double* rmse, int* done) {
+__global__ void lm_rmse_kernel(DevMarket m, int n, const double* vols, double target, double* rmse, int* done,
+                               int* any) {
   const int i = blockIdx.x;
   const int ni = m.n_cap + m.n_swp;
   __shared__ double part[32];
@@ -164,7 +165,10 @@ __global__ void lm_rmse_kernel(DevMarket m, int n, const double* vols, double ta
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
     const double r = 100.0 * sqrt(t / (double)ni);
     if (rmse) rmse[i] = r;
-    if (r <= target) done[i] = 1;
+    if (r <= target) {
+      done[i] = 1;
+      *any = 1;
+    }
   }
 }
 
