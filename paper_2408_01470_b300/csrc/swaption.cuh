@@ -91,6 +91,11 @@ template <class R> __device__ __forceinline__ const R* swap_C_of(const DevMarket
 template <> __device__ __forceinline__ const double* swap_C_of<double>(const DevMarket& m) { return m.swap_C64; }
 template <> __device__ __forceinline__ const float* swap_C_of<float>(const DevMarket& m) { return m.swap_C32; }
 
+// Barrier 1 over the warps 1.. of the CTA (warp 0 is busy with the caplet mapping meanwhile).
+__device__ __forceinline__ void sync_without_warp0(int nth) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nth - 32) : "memory");
+}
+
 // Inclusive warp scan (lanes in order).
 template <class R>
 __device__ __forceinline__ R warp_inclusive_scan(R v, int lane) {
@@ -186,7 +191,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   const R D = (R)m.panel;
   const int NA = m.NA, ND = m.ND, YS = cta_y_stride(), PL = cta_pq_len(NA);
 
-  // ---- phase 1: caplet forwards (warp 0); per-chain exponential tables (other warps)
+  // ---- phase 1: caplet forwards (warp 0); per-chain exponential tables (other warps).  Without
+  //      tensor cores warp 0 stays on the caplet mapping through phases 2-3, which the other
+  //      warps run alone (barrier 1); everyone meets again after the Grams.
   if (warp == 0) {
     if (m.n_capfwd > 0) {
       if (lane < kMaxParam) cs.cap.xs[lane] = cs.xs[lane];
@@ -232,11 +239,15 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       cs.crq[e] = q;
     }
   }
-  __syncthreads();
+  if (TC) __syncthreads();
+  else if (warp != 0) sync_without_warp0(nth);
+  // phases 2 and 3 (ALU form): the warps 1.. only
+  const int ptid = TC ? tid : tid - 32, pnth = TC ? nth : nth - 32;
 
   // ---- phase 2: Y rows, one thread per (panel A, outer node q): g and h at the node once, then
   //      the 8 inner-node products
-  for (int it = tid; it < NA * kQ; it += nth) {
+  if (TC || warp != 0)
+  for (int it = ptid; it < NA * kQ; it += pnth) {
     const int A = it >> 3, q = it & 7;
     const R base = D * (R)A;
     const Q2<R> E = cs.Ep[A];
@@ -268,7 +279,8 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       *(Q4<R>*)(y + 20 + q * kQ) = w1;
     }
   }
-  __syncthreads();
+  if (TC) __syncthreads();
+  else if (warp != 0) sync_without_warp0(nth);
 
   // ---- phase 3: pair sums along the diagonals (raw, then prefix-summed in phase 4)
   if (TC) {
@@ -303,10 +315,10 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const int q = it / (ND * NA), r = it - q * ND * NA, e = r / NA, A = r - e * NA;
       if (A + e < NA) cs.PQ[(q * ND + e) * PL + A] += Tb[(q * ND + e) * NA + A];
     }
-  } else {
+  } else if (warp != 0) {
     // one thread per (panel A, block of 4 diagonals): the Y row of A is loaded once per 4 pairs
     const int NEB = (ND + 3) >> 2;
-    for (int it = tid; it < NEB * NA; it += nth) {
+    for (int it = ptid; it < NEB * NA; it += pnth) {
       const int eb = it / NA, A = it - eb * NA, e0 = 4 * eb;
       const R* ya = cs.Y + A * YS;
       const R* yb[4];
