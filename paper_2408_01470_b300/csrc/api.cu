@@ -688,7 +688,8 @@ cudaError_t enqueue_anneal_t(const DevMarket& m, const SAState& st, const SAPara
                              bool configure_only) {
   const uint32_t sm1 = smem_bytes<R>(m, 1), smW = smem_bytes<R>(m, W);
   auto k0 = sa_start_kernel<R, MODEL, FORMULA>;
-  auto k1 = sa_level_kernel<R, MODEL, FORMULA>;
+  // more than 4 chains per CTA (FP32): the form with one CTA of up to 28 chains per SM
+  auto k1 = (sizeof(R) == 4 && W > 4) ? sa_level_kernel<R, MODEL, FORMULA, true> : sa_level_kernel<R, MODEL, FORMULA, false>;
   if (configure_only) {
     cudaError_t e = cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smW);
@@ -865,7 +866,7 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (!(o->cooling > 0.0 && o->cooling <= 1.0)) return fail(SABR_LMM_EINVAL, "cooling must be in (0, 1]");
   if (!(o->step_frac > 0.0) || !(o->step_floor >= 0.0)) return fail(SABR_LMM_EINVAL, "step_frac > 0 and step_floor >= 0 required");
   if (o->prec < SABR_LMM_FP64 || o->prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
-  if (o->warps_per_block < 0 || o->warps_per_block > 16) return fail(SABR_LMM_EINVAL, "warps_per_block must be in [0, 16]");
+  if (o->warps_per_block < 0 || o->warps_per_block > 28) return fail(SABR_LMM_EINVAL, "warps_per_block must be in [0, 28]");
   if (o->lm_top_k < 0 || o->lm_top_k > o->n_chains || o->lm_top_k > 1024) return fail(SABR_LMM_EINVAL, "lm_top_k must be in [0, min(n_chains, 1024)]");
   if (o->lm_top_k > 0 && o->lm_max_iter < 0) return fail(SABR_LMM_EINVAL, "lm_max_iter must be >= 0");
   for (const DevMarket& m : mk->dm) {
@@ -880,7 +881,17 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   p->mk = mk;
   p->opts = *o;
   p->opts.x0 = nullptr;
-  p->W = o->warps_per_block > 0 ? o->warps_per_block : 4;
+  // chains (warps) per CTA: FP32 one CTA per SM with up to 28 chains, as many as spread the chains
+  // over the SMs in one wave; FP64 (128 registers a thread) 4 chains per CTA
+  int nsm = 148;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  p->W = o->warps_per_block > 0 ? o->warps_per_block
+                                : (o->prec == SABR_LMM_FP64 ? 4 : std::min(28, std::max(1, (o->n_chains + nsm - 1) / nsm)));
+  if (o->prec == SABR_LMM_FP64 && p->W > 4) p->W = 4;
   p->grid = (o->n_chains + p->W - 1) / p->W;
   const int nm = (int)mk->dm.size();
   const int P = mk->dm[0].n_param;
@@ -1178,7 +1189,7 @@ namespace {
 constexpr int kNoAllocMaxChains = 16384;
 constexpr int kNoAllocMaxLevels = 4096;
 constexpr int kNoAllocMaxParam = kMaxParam;
-constexpr int kNoAllocW = 4;  // warps (chains) per CTA, as the default plan
+constexpr int kNoAllocW = 4;  // warps (chains) per CTA: the 4-chain form of the level kernel
 constexpr int kNoAllocMaxGrid = (kNoAllocMaxChains + kNoAllocW - 1) / kNoAllocW;
 
 // Byte offsets of the regions in the array (each 256-byte aligned).

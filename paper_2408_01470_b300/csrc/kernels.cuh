@@ -386,8 +386,10 @@ __device__ __forceinline__ R box_lo(const DevMarket& m, int k) { return (R)m.lo[
 template <class R>
 __device__ __forceinline__ R box_hi(const DevMarket& m, int k) { return (R)m.hi[k]; }
 
-template <class R, int MODEL, int FORMULA>
-__global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 7 : 4))
+// BIG: one CTA of up to 28 chains (the whole SM at 72 registers) instead of 4-chain CTAs, so the
+// market is staged once per SM rather than once per 4 chains.
+template <class R, int MODEL, int FORMULA, bool BIG = false>
+__global__ void __launch_bounds__(BIG ? 896 : 128, BIG ? 1 : (sizeof(R) == 4 ? 7 : 4))
 sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -424,10 +426,12 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
     } else {
       xbk = x;
     }
-    const unsigned long long cw = (unsigned long long)c | (sp.market_index << 32);
-    // Philox block (lane & 3) of step s0 + (lane >> 2), 8 steps at a time, parked in shared memory
-    uint64_t* rng = cs.rng + (size_t)warp * 128;
-    for (int s = 0; s < sp.N; ++s) {
+  }
+  const unsigned long long cw = (unsigned long long)c | (sp.market_index << 32);
+  // Philox block (lane & 3) of step s0 + (lane >> 2), 8 steps at a time, parked in shared memory
+  uint64_t* rng = cs.rng + (size_t)warp * 128;
+  for (int s = 0; s < sp.N; ++s) {
+    if (active) {
       // S1: the step's uniforms; lane k needs word (k & 3) of block (k >> 2) of this step
       if ((s & 7) == 0) {
         const U4 o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)(s + (lane >> 2)), (uint64_t)level, cw, sp.seed, 0ull);
@@ -452,6 +456,8 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
       }
       if (st.bits && lane == 0) st.bits[((size_t)c * sp.L + level) * sp.N + s] = acc ? 1 : 0;
     }
+  }
+  if (active) {
     if (lane < P) {
       st.xe[(size_t)c * P + lane] = (double)x;
       st.xb[(size_t)c * P + lane] = (double)xbk;
