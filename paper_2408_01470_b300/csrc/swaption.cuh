@@ -521,7 +521,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   }
   const int bad = __syncthreads_or(!ok);
   if (vols) return obj_inf(O());
-  const O wsum = warp_sum(obj_lane(O(), part));
+  const O wsum = warp_sum_lanes(part);
   if (lane == 0) red[warp] = wsum;
   __syncthreads();
   O f = red[0];
