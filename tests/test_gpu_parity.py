@@ -167,3 +167,29 @@ def test_load_market_rejects_bad_input(gpu_lib):
     with pytest.raises(lib.SabrLmmError) as e:
         lib.Market(bad, np.full(sk.n_cap, 0.2))
     assert e.value.status == 1 and "cap_K" in str(e.value)
+
+
+@pytest.mark.parametrize("name", ["smile_2y", "caplets_20x15"])
+def test_anneal_fp32_same_search_at_every_cta_size(gpu_lib, name):
+    # the FP32 level kernel comes in 4-chain CTAs and in one CTA of up to 28 chains per SM; a chain
+    # is one warp either way, so every CTA size gives the same search bit for bit (100 chains: the
+    # last 28-chain CTA is partial)
+    sk = CASES[name]()
+    om, gm, _ = _markets(sk)
+    runs = [gm.anneal(100, 4, 12, 0.9, seed=13, prec="fp32", record_accepts=True, warps_per_block=w)
+            for w in (1, 4, 7, 28, 0)]
+    for r in runs[1:]:
+        assert np.array_equal(r["bits"], runs[0]["bits"])
+        assert np.array_equal(r["trace_f"], runs[0]["trace_f"])
+        assert np.array_equal(r["x_best"], runs[0]["x_best"])
+        assert np.array_equal(r["f_best"], runs[0]["f_best"])
+
+
+def test_anneal_fp64_more_than_four_chains_per_cta_is_capped(gpu_lib):
+    # FP64 (128 registers a thread) keeps 4-chain CTAs whatever is asked; the search is unchanged
+    sk = synth.smile_2y()
+    om, gm, _ = _markets(sk)
+    r4 = gm.anneal(40, 3, 6, 0.9, seed=17, prec="fp64", record_accepts=True, warps_per_block=4)
+    r28 = gm.anneal(40, 3, 6, 0.9, seed=17, prec="fp64", record_accepts=True, warps_per_block=28)
+    assert np.array_equal(r4["bits"], r28["bits"])
+    assert np.array_equal(r4["x_best"], r28["x_best"])
