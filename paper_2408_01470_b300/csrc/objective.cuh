@@ -419,30 +419,60 @@ __device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const W
   return acc;
 }
 
-// z_over_x_fast on a pair (FP32), with the series coefficients c1 = -rho / 2 and
-// c2 = (2 - 3 rho^2) / 12 of the chain.  The sign of z is the sign of fk (nu / alpha > 0), so
-// r = +-rho comes from the sign bit of the instrument constant, and 1 / ((s + 1)(1 - r)) is one
-// reciprocal.
-__device__ __forceinline__ float2 z_over_x2(float2 z, float fkx, float fky, const RhoConsts<float>& rc, float c1,
-                                            float c2) {
+// z_over_x_fast on a pair (FP32).  Per element: rho, omr2 = 1 - rho^2 and the series
+// coefficients c1 = -rho / 2, c2 = (2 - 3 rho^2) / 12.  The sign of z is the sign of fk
+// (nu / alpha > 0), so r = +-rho comes from the sign bit of the instrument constant, and
+// 1 / ((s + 1)(1 - r)) is one reciprocal.
+__device__ __forceinline__ float2 z_over_x2(float2 z, float fkx, float fky, float rhox, float rhoy, float2 omr2,
+                                            float2 c1, float2 c2) {
   const float2 zz = abs2(z);
-  const unsigned rb = __float_as_uint(rc.rho);
-  const float2 r = make_float2(__uint_as_float(rb ^ (__float_as_uint(fkx) & 0x80000000u)),
-                               __uint_as_float(rb ^ (__float_as_uint(fky) & 0x80000000u)));
+  const float2 r = make_float2(__uint_as_float(__float_as_uint(rhox) ^ (__float_as_uint(fkx) & 0x80000000u)),
+                               __uint_as_float(__float_as_uint(rhoy) ^ (__float_as_uint(fky) & 0x80000000u)));
   const float2 zm2r = fma2(r, bc2(-2.0f), zz);
   const float2 zq = mul2(zz, zm2r);
   const float2 s2 = add2(bc2(1.0f), zq);
   const float2 s = mul2(s2, rsqrt2(s2));
-  const float2 smr = mul2(add2(bc2(rc.omr2), zq), rcp2(add2(s, r)));
+  const float2 smr = mul2(add2(omr2, zq), rcp2(add2(s, r)));
   const float2 sp1 = add2(s, bc2(1.0f));
   const float2 omr = sub2(bc2(1.0f), r);
   const float2 qa = add2(add2(smr, omr), zz);
   const float2 qb = add2(zm2r, sp1);
   const float2 Q = sel2(r.x > 0.0f, r.y > 0.0f, qa, qb);
   const float2 x = log1p_pos2(mul2(mul2(zz, Q), rcp2(mul2(sp1, omr))));
-  const float2 ser = fma2(fma2(bc2(c2), z, bc2(c1)), z, bc2(1.0f));
+  const float2 ser = fma2(fma2(c2, z, c1), z, bc2(1.0f));
   const float2 zx = mul2(zz, rcp2(x));
   return sel2(zz.x < Num<float>::zx_series, zz.y < Num<float>::zx_series, ser, zx);
+}
+
+// r^2 of a pair of instruments (caplets or swaptions alike) on the packed instructions: per
+// element its SABR factors F = {alpha, nu/alpha, alpha^2, rho nu alpha}, A3 = (2 - 3 rho^2) nu^2,
+// rho, and its three constant vectors g0 = {l, fk, inv_den, c1}, g1 = {c2, c3, sqrt T, D F},
+// g2 = {K/F, sgn, P_mkt, sqrt w}.  Clears ok on an infeasible vol.
+__device__ __forceinline__ float2 price_pair_x2(const Q4<float>& fa, const Q4<float>& fb, float a3a, float a3b,
+                                                float rhoa, float rhob, const Q4<float>& g0a, const Q4<float>& g0b,
+                                                const Q4<float>& g1a, const Q4<float>& g1b, const Q4<float>& g2a,
+                                                const Q4<float>& g2b, bool& ok) {
+  const float2 rho = make_float2(rhoa, rhob);
+  const float2 omr2 = mul2(sub2(bc2(1.0f), rho), add2(bc2(1.0f), rho));
+  const float2 c1 = mul2(bc2(-0.5f), rho);
+  const float2 c2 = mul2(fma2(mul2(bc2(-3.0f), rho), rho, bc2(2.0f)), bc2(1.0f / 12.0f));
+  const float2 fk = make_float2(g0a.b, g0b.b);
+  const float2 z = mul2(make_float2(fa.b, fb.b), fk);
+  const float2 zx = z_over_x2(z, fk.x, fk.y, rhoa, rhob, omr2, c1, c2);
+  float2 corr = fma2(make_float2(g0a.d, g0b.d), make_float2(fa.c, fb.c), bc2(1.0f));
+  corr = fma2(make_float2(g1a.a, g1b.a), make_float2(fa.d, fb.d), corr);
+  corr = fma2(make_float2(g1a.b, g1b.b), make_float2(a3a, a3b), corr);
+  const float2 sig = mul2(mul2(mul2(make_float2(fa.a, fb.a), make_float2(g0a.c, g0b.c)), zx), corr);
+  ok = ok && (sig.x > 0.0f) && (sig.x < INFINITY) && (sig.y > 0.0f) && (sig.y < INFINITY);
+  const float2 v = mul2(sig, make_float2(g1a.c, g1b.c));
+  const float2 d1 = fma2(make_float2(g0a.a, g0b.a), rcp2(v), mul2(bc2(0.5f), v));
+  const float2 sg = make_float2(g2a.b, g2b.b);
+  const float2 n1 = ncdf2(mul2(sg, d1));
+  const float2 n2 = ncdf2(mul2(sg, sub2(d1, v)));
+  const float2 nkf = mul2(make_float2(g2a.a, g2b.a), bc2(-1.0f));
+  const float2 p = mul2(mul2(sg, make_float2(g1a.d, g1b.d)), fma2(nkf, n2, n1));
+  const float2 r = mul2(make_float2(g2a.d, g2b.d), sub2(p, make_float2(g2a.c, g2b.c)));
+  return mul2(r, r);
 }
 
 // price_caplets for FP32 and the Hagan (2002) form on the packed instructions: lane l takes the
@@ -460,7 +490,7 @@ __device__ __forceinline__ float price_caplets_x2(const void* blk, int npairs, i
     const float4 v0 = B.v[P], v1 = B.v[npairs + P], v2 = B.v[2 * npairs + P];
     const float2 l = make_float2(v0.x, v0.y), fk = make_float2(v0.z, v0.w);
     const float2 z = mul2(make_float2(fa.b, fb.b), fk);
-    const float2 zx = z_over_x2(z, fk.x, fk.y, rc, c1, c2);
+    const float2 zx = z_over_x2(z, fk.x, fk.y, rc.rho, rc.rho, bc2(rc.omr2), bc2(c1), bc2(c2));
     float2 corr = fma2(make_float2(v1.z, v1.w), make_float2(fa.c, fb.c), bc2(1.0f));
     corr = fma2(make_float2(v2.x, v2.y), make_float2(fa.d, fb.d), corr);
     corr = fma2(make_float2(v2.z, v2.w), make_float2(ws.fA3[ix.x], ws.fA3[ix.y]), corr);

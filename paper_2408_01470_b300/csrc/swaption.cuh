@@ -515,9 +515,47 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   bool ok = true;
   R part = 0;
   const int ntot = m.n_cap + m.n_swp;
-  for (int k = tid; k < ntot; k += nth) {
-    if (k < m.n_cap) part += price_one_caplet<R, FORMULA>(capB, k, cs.cap, rc, omb, ok, vols);
-    else part += price_swaption<R, FORMULA>(swpB, k - m.n_cap, cs, omb, ok, vols ? vols + m.n_cap : nullptr);
+  if constexpr (std::is_same<R, float>::value && FORMULA == 0) {
+    if (vols == nullptr) {
+      // FP32, Hagan (2002): instruments k and k + nth as a packed pair (either kind)
+      float2 acc = bc2(0.0f);
+      for (int k = tid; k < ntot; k += 2 * nth) {
+        const bool has2 = k + nth < ntot;
+        Q4<float> F[2], g0[2], g1[2], g2[2];
+        float a3[2], rh[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int kk = (u == 1 && has2) ? k + nth : k;
+          if (kk < m.n_cap) {
+            const int i = capB.idx[kk];
+            F[u] = cs.cap.F4[i];
+            a3[u] = cs.cap.fA3[i];
+            rh[u] = phi;
+            g0[u] = capB.g0[kk]; g1[u] = capB.g1[kk]; g2[u] = capB.g2[kk];
+          } else {
+            const int j = kk - m.n_cap, sw = swpB.idx[j];
+            F[u] = cs.F4s[sw];
+            a3[u] = cs.A3s[sw];
+            rh[u] = cs.RCs[sw].a;
+            g0[u] = swpB.g0[j]; g1[u] = swpB.g1[j]; g2[u] = swpB.g2[j];
+          }
+        }
+        float2 r2 = price_pair_x2(F[0], F[1], a3[0], a3[1], rh[0], rh[1], g0[0], g0[1], g1[0], g1[1], g2[0], g2[1], ok);
+        r2.y = has2 ? r2.y : 0.0f;
+        acc = add2(acc, r2);
+      }
+      part = acc.x + acc.y;
+    } else {
+      for (int k = tid; k < ntot; k += nth) {
+        if (k < m.n_cap) part += price_one_caplet<R, FORMULA>(capB, k, cs.cap, rc, omb, ok, vols);
+        else part += price_swaption<R, FORMULA>(swpB, k - m.n_cap, cs, omb, ok, vols + m.n_cap);
+      }
+    }
+  } else {
+    for (int k = tid; k < ntot; k += nth) {
+      if (k < m.n_cap) part += price_one_caplet<R, FORMULA>(capB, k, cs.cap, rc, omb, ok, vols);
+      else part += price_swaption<R, FORMULA>(swpB, k - m.n_cap, cs, omb, ok, vols ? vols + m.n_cap : nullptr);
+    }
   }
   const int bad = __syncthreads_or(!ok);
   if (vols) return obj_inf(O());
