@@ -135,6 +135,18 @@ def barrier(ws: int):
         dist.barrier()
 
 
+def job_rate(local_seconds: float, units_per_rank: float, ws: int):
+    """Whole-job throughput of ws replicas: every rank's units over the slowest rank's time.
+    Returns (units per second, the max-over-ranks seconds)."""
+    t = reduce_max(local_seconds, ws)
+    return ws * units_per_rank / t, t
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """Rank r runs an independent replica of the search with seed base + r."""
+    return base + rank
+
+
 WORKLOADS = {
     "caplets": "rebonato_caplets_20fwd_x_15k_4096ch_x_200T_x_100steps",
     "joint": "rebonato_joint_40fwd_300caplets_700swaptions_16384ch_x_200T_x_100steps",
@@ -271,7 +283,7 @@ def main():
     skel = synth.caplet_term_structure()
     gm, vols = market_from_library(lib, skel)
     C, L, N = skel.n_chains, skel.n_levels, skel.steps
-    seed = 240801470 + rank
+    seed = replica_seed(240801470, rank)
     s = torch.cuda.Stream()
     plan = gm.anneal_prepare(C, L, N, skel.cooling, seed, prec=args.prec, use_graph=True, stream=s,
                              warps_per_block=args.warps_per_block)
@@ -294,11 +306,10 @@ def main():
     barrier(ws)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = sum(step_ms) / 1e3
-    total_s_max = reduce_max(total_s, ws)
     res = plan.fetch()
     n_evals = res["n_evals"]
     prices_per_step = n_evals * skel.n_instr
-    value = ws * args.steps * prices_per_step / total_s_max
+    value, total_s_max = job_rate(total_s, args.steps * prices_per_step, ws)
     ms_per_step = 1e3 * total_s_max / args.steps
 
     # roofline of the dominant kernel (the per-temperature level kernel, >99% of the step)
