@@ -546,16 +546,6 @@ __device__ __forceinline__ FF warp_sum_lanes(float p) {
 }
 __device__ __forceinline__ double warp_sum_lanes(double p) { return warp_sum(p); }
 
-__device__ __forceinline__ FF warp_sum(FF v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    FF o;
-    o.hi = __shfl_xor_sync(0xffffffffu, v.hi, off);
-    o.lo = __shfl_xor_sync(0xffffffffu, v.lo, off);
-    v = ff_add(v, o);
-  }
-  return v;
-}
 
 template <class R> struct ObjOf { typedef double T; };
 template <> struct ObjOf<float> { typedef FF T; };
@@ -564,8 +554,6 @@ __device__ __forceinline__ double obj_add(double a, double b) { return a + b; }
 __device__ __forceinline__ FF obj_add(FF a, FF b) { return ff_add(a, b); }
 __device__ __forceinline__ double obj_inf(double) { return __longlong_as_double(0x7ff0000000000000LL); }
 __device__ __forceinline__ FF obj_inf(FF) { FF r; r.hi = __int_as_float(0x7f800000); r.lo = 0.f; return r; }
-__device__ __forceinline__ double obj_lane(double, double p) { return p; }
-__device__ __forceinline__ FF obj_lane(FF, float p) { FF r; r.hi = p; r.lo = 0.f; return r; }
 __device__ __forceinline__ bool obj_finite(double v) { return isfinite(v); }
 __device__ __forceinline__ bool obj_finite(FF v) { return isfinite(v.hi); }
 __device__ __forceinline__ double obj_to_double(double v) { return v; }
