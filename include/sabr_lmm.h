@@ -172,7 +172,9 @@ typedef struct {
   int32_t lm_top_k;
   int32_t lm_max_iter;
   double target_rmse_volpt;
-  int32_t warps_per_block; /* 0 -> autotuned */
+  int32_t warps_per_block; /* chains (warps) per CTA of the caplet level kernel, 0..28; 0 -> FP32: one
+                              CTA of up to 28 chains per SM, FP64: 4 (FP64 is capped at 4); batch:
+                              0 -> autotuned CTA size, >= 8 -> 256 threads, else 128           */
   int32_t use_graph;       /* 1 -> the level loop is captured once and replayed as a CUDA graph */
   int32_t record_accepts;  /* 1 -> fill sabr_lmm_result.accept_bits (market 0; small runs)     */
 } sabr_lmm_anneal_opts;
