@@ -258,6 +258,7 @@ def main():
     ap.add_argument("--no-fp64-variant", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-joint-variant", action="store_true")
+    ap.add_argument("--no-batch-variant", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--profile", action="store_true",
@@ -396,6 +397,25 @@ def main():
                                   "value": rj["n_evals"] * jsks[0].n_instr / tj, "unit": UNIT,
                                   "ms_per_level": tj * 1e3 / jL}
         del jplan, jm
+
+    # the 256-market batch (one persistent launch per shared-memory bucket and level), one level
+    if args.prec == "fp32" and not args.no_batch_variant:
+        bm, bsks, _, bC, _, bN, bcool = workload_markets(lib, "batch")
+        bL = 1
+        bplan = bm.anneal_prepare(bC, bL, bN, bcool, seed, prec="fp32", use_graph=True, stream=s)
+        bplan.launch(stream=s)
+        s.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        bplan.launch(stream=s)
+        b.record(s)
+        s.synchronize()
+        tb = a.elapsed_time(b) / 1e3
+        rb = bplan.fetch()
+        variants["batch_fp32"] = {"workload": WORKLOADS["batch"], "levels_timed": bL,
+                                  "value": rb["n_evals"] * sum(sk.n_instr for sk in bsks) / tb, "unit": UNIT,
+                                  "ms_per_level": tb * 1e3 / bL}
+        del bplan, bm
 
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
