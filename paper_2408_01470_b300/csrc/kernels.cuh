@@ -1,14 +1,21 @@
 // Kernels of the hot path and of market set-up.
 //
-//   setup_*_kernel ......... market-only constants in FP64 (once per load).
-//   objective_kernel ....... f for n parameter sets, one warp per set (grid-stride).
-//   vols_kernel ............ model vols for n parameter sets.
+//   setup_*_kernel ......... market-only constants in FP64 (once per load), the FP32 pair-major
+//                            caplet block and the swaptions' coefficient rows.
+//   objective_kernel ....... f (or the model vols) for n parameter sets, one warp per set
+//                            (grid-stride); caplet markets.
 //   sa_start_kernel ........ f(x0), T0, the first start point.
 //   sa_level_kernel ........ one temperature level: every chain (one warp) runs N Metropolis
 //                            steps (S1 proposal, S2-S7 objective, S8 acceptance), then the
 //                            minimum over the chains' end points is taken by the last CTA to
-//                            finish (no grid-wide wait) and becomes the next start point.
+//                            finish (no grid-wide wait) and becomes the next start point.  CTAs
+//                            of 4 chains, or (FP32) one CTA of up to 28 chains per SM.
 //   sa_final_kernel ........ the best point ever accepted over all chains.
+//   *_cta_kernel ........... the same for markets with swaptions, one CTA (256 threads) per
+//                            chain or per point (cta_objective in swaption.cuh).
+//   *_batch_kernel ......... many markets: per level a persistent grid over (market, chain)
+//                            items in LPT order.
+//   grad_kernel ............ f and df/dtheta by the reverse sweep (adjoint.cuh).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
