@@ -892,6 +892,11 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   p->W = o->warps_per_block > 0 ? o->warps_per_block
                                 : (o->prec == SABR_LMM_FP64 ? 4 : std::min(28, std::max(1, (o->n_chains + nsm - 1) / nsm)));
   if (o->prec == SABR_LMM_FP64 && p->W > 4) p->W = 4;
+  // fewer chains per CTA if a caplet market's shared memory would not fit (the 4-chain form is
+  // what the load-time check admits)
+  for (const DevMarket& m : mk->dm)
+    if (m.n_swp == 0 && o->prec != SABR_LMM_FP64)
+      while (p->W > 4 && smem_bytes<float>(m, p->W) > 227u * 1024u) --p->W;
   p->grid = (o->n_chains + p->W - 1) / p->W;
   const int nm = (int)mk->dm.size();
   const int P = mk->dm[0].n_param;
