@@ -365,11 +365,12 @@ def main():
                                          "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS}}
         del plan64
 
-    # the mixed-precision, adjoint-polished form: a shortened FP32 search, then the Levenberg-Marquardt
-    # polish (adjoint gradient) of its 64 best chains; the shortest schedule that reaches the target
+    # the mixed-precision, adjoint-polished form: a shortened FP32 search (the same cooling, fewer
+    # levels), then the Levenberg-Marquardt polish (adjoint gradient) of its 64 best chains; the
+    # shortest schedule that reaches the target
     if args.prec == "fp32":
         pol = None
-        for Ls in (5, 10, 20, 40, 80):
+        for Ls in (1, 2, 3, 5, 10, 20, 40, 80):
             rp = gm.anneal(C, Ls, N, skel.cooling, seed, prec="fp32", lm_top_k=64, lm_max_iter=50,
                            target_rmse=TARGET_RMSE_VOLPT)
             if rp["rmse_volpt"][0] <= TARGET_RMSE_VOLPT:
