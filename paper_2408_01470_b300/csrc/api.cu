@@ -624,8 +624,9 @@ __global__ void lm_init_kernel(int n, double* mu, int* done, int* any) {
 // Enqueue max_iter LM iterations on the n points X (device, updated in place).  With
 // stop_at_first (host-driven, never under stream capture) the iterations end as soon as any point
 // has reached the target RMSE: the host reads one flag per iteration.
-cudaError_t lm_enqueue(const DevMarket& m, double* X, int n, int max_iter, double target, const LmWork& w, cudaStream_t s,
-                       bool stop_at_first = false) {
+cudaError_t lm_enqueue(const DevMarket& m, int n_free, double* X, int n, int max_iter, double target, const LmWork& w,
+                       cudaStream_t s, bool stop_at_first = false) {
+  const int S = 1 + n_free;   // stencil: the point and one forward step per free slot
   const int ni = m.n_cap + m.n_swp;
   const bool have_adjoint = m.n_swp == 0;
   cudaError_t e;
@@ -640,13 +641,13 @@ cudaError_t lm_enqueue(const DevMarket& m, double* X, int n, int max_iter, doubl
   };
   for (int it = 0; it < max_iter; ++it) {
     if (stop_at_first && target > 0.0 && reached()) break;
-    lm_perturb_kernel<<<n, 32, 0, s>>>(n, m.n_param, X, w.Xp);
-    if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xp, (long long)n * kLmStencil, nullptr, w.vols, s)) != cudaSuccess) return e;
-    residuals_from_vols_kernel<<<148 * 4, 256, 0, s>>>(m, (long long)n * kLmStencil, w.vols, w.res);
+    lm_perturb_kernel<<<n, 32, 0, s>>>(n, m.n_param, S, m.freem, X, w.Xp);
+    if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xp, (long long)n * S, nullptr, w.vols, s)) != cudaSuccess) return e;
+    residuals_from_vols_kernel<<<148 * 4, 256, 0, s>>>(m, (long long)n * S, w.vols, w.res);
     if (have_adjoint) {
       if ((e = launch_grad_r<double>(m, X, n, w.gf, w.grad, s)) != cudaSuccess) return e;
     }
-    lm_step_kernel<<<n, 128, 0, s>>>(m, n, w.res, have_adjoint ? w.grad : nullptr, w.mu, w.done, X, w.Xt);
+    lm_step_kernel<<<n, 128, 0, s>>>(m, n, S, w.res, have_adjoint ? w.grad : nullptr, w.mu, w.done, X, w.Xt);
     if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xt, n, w.ft, nullptr, s)) != cudaSuccess) return e;
     lm_accept_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, m.n_param, X, w.Xt, w.f, w.ft, w.mu, w.done);
     if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
@@ -670,7 +671,9 @@ extern "C" sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t 
   void* buf = nullptr;
   if (cudaMalloc(&buf, lm_work_bytes(dm, (int)n)) != cudaSuccess) return fail(SABR_LMM_ENOMEM, "cudaMalloc of the polish buffers failed");
   const LmWork w = lm_carve(buf, dm, (int)n);
-  cudaError_t e = lm_enqueue(dm, X, (int)n, max_iter, target, w, s);
+  int n_free = 0;
+  for (unsigned char f : m->hm[idx].freem) n_free += f != 0;
+  cudaError_t e = lm_enqueue(dm, n_free, X, (int)n, max_iter, target, w, s);
   if (e == cudaSuccess && f) e = cudaMemcpyAsync(f, w.f, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && rmse) e = cudaMemcpyAsync(rmse, w.rmse, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1066,7 +1069,9 @@ sabr_lmm_status enqueue_polish(sabr_lmm_anneal_plan* p, cudaStream_t s) {
     const LmWork w = lm_carve(b + p->lm_off[3 * j + 2], m, k);
     select_lowest_kernel<<<1, 1024, 0, s>>>(p->st[j].fb, p->opts.n_chains, k, sel);
     gather_points_kernel<<<k, 32, 0, s>>>(p->st[j].xb, sel, k, m.n_param, X);
-    cudaError_t e = lm_enqueue(m, X, k, p->opts.lm_max_iter, p->opts.target_rmse_volpt, w, s, true);
+    int n_free = 0;
+    for (unsigned char f : p->mk->hm[j].freem) n_free += f != 0;
+    cudaError_t e = lm_enqueue(m, n_free, X, k, p->opts.lm_max_iter, p->opts.target_rmse_volpt, w, s, true);
     if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("polish launch: ") + cudaGetErrorString(e));
     take_best_kernel<<<1, 32, 0, s>>>(X, w.f, k, m.n_param, p->st[j].best_x, p->st[j].best_f);
   }

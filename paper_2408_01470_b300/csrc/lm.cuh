@@ -1,8 +1,8 @@
 // Levenberg-Marquardt polish of annealed points (replaces the Nelder-Mead polish of the hybrid
 // scheme, Section 3).  Per point and iteration:
 //   r      residuals sqrt(w_k)(P_k - P_k^mkt) at theta (FP64, from the model vols);
-//   J      columns by central differences (r(theta + h e_p) - r(theta - h e_p)) / 2h,
-//          h = 1e-6 max(|theta_p|, 1), over the free slots;
+//   J      columns by forward differences (r(theta + h e_p) - r(theta)) / h, h = 1e-7 max(|theta_p|, 1),
+//          over the free slots only (1 + n_free evaluations per point and iteration);
 //   g      J^T r, taken from the hand-written adjoint (g = grad f / 2) when the market has one,
 //          else from the difference Jacobian;
 //   step   (J^T J + mu diag(J^T J)) d = -g by Cholesky over the free slots (a zero diagonal is
@@ -14,18 +14,26 @@
 
 namespace sabr {
 
-constexpr int kLmStencil = 1 + 2 * kMaxParam;   // theta and theta +- h e_p for every slot
+constexpr int kLmStencil = 1 + kMaxParam;   // most points per stencil: theta and theta + h e_p
 
-__device__ __forceinline__ double lm_h(double x) { return 1e-6 * fmax(fabs(x), 1.0); }
+__device__ __forceinline__ double lm_h(double x) { return 1e-7 * fmax(fabs(x), 1.0); }
 
-// Xp[(i * kLmStencil + j) * P + k]: j = 0 the point, j = 1 + 2p (+h e_p), j = 2 + 2p (-h e_p).
-__global__ void lm_perturb_kernel(int n, int P, const double* X, double* Xp) {
+// Slot of the a-th free parameter.
+__device__ __forceinline__ int lm_free_slot(const unsigned char* freem, int P, int a) {
+  for (int k = 0; k < P; ++k)
+    if (freem[k] && a-- == 0) return k;
+  return -1;
+}
+
+// Xp[(i * S + j) * P + k], S = 1 + n_free: j = 0 the point, j = 1 + a the point + h e_(a-th free slot).
+__global__ void lm_perturb_kernel(int n, int P, int S, const unsigned char* freem, const double* X, double* Xp) {
   const int i = blockIdx.x, j = threadIdx.x;
-  if (i >= n || j >= kLmStencil) return;
-  double* out = Xp + ((size_t)i * kLmStencil + j) * P;
+  if (i >= n || j >= S) return;
+  const int slot = j > 0 ? lm_free_slot(freem, P, j - 1) : -1;
+  double* out = Xp + ((size_t)i * S + j) * P;
   for (int k = 0; k < P; ++k) {
     double v = X[(size_t)i * P + k];
-    if (j > 0 && (j - 1) / 2 == k) v += ((j - 1) % 2 == 0 ? 1.0 : -1.0) * lm_h(v);
+    if (k == slot) v += lm_h(v);
     out[k] = v;
   }
 }
@@ -46,7 +54,7 @@ __global__ void residuals_from_vols_kernel(DevMarket m, long long npts, const do
 }
 
 // Normal equations and the damped step, one CTA per point.
-__global__ void lm_step_kernel(DevMarket m, int n, const double* res, const double* grad, const double* mu,
+__global__ void lm_step_kernel(DevMarket m, int n, int S, const double* res, const double* grad, const double* mu,
                                const int* done, const double* X, double* Xt) {
   const int i = blockIdx.x;
   if (i >= n) return;
@@ -61,22 +69,20 @@ __global__ void lm_step_kernel(DevMarket m, int n, const double* res, const doub
     nf = c;
   }
   __syncthreads();
-  const double* r0 = res + (size_t)i * kLmStencil * ni;
+  const double* r0 = res + (size_t)i * S * ni;
   const double* x = X + (size_t)i * P;
   if (threadIdx.x < nf) hs[threadIdx.x] = lm_h(x[fi[threadIdx.x]]);
   __syncthreads();
-  // J[k][a] = (r(+h e_fa) - r(-h e_fa))[k] / (2 h_a)
+  // J[k][a] = (r(theta + h_a e_fa) - r(theta))[k] / h_a, the stencil's row 1 + a
   for (int t = threadIdx.x; t < nf * nf + nf; t += blockDim.x) {
     if (t < nf * nf) {
       const int a = t / nf, b = t - a * nf;
       if (b < a) continue;
-      const double* pa = r0 + (size_t)(1 + 2 * fi[a]) * ni;
-      const double* ma = pa + ni;
-      const double* pb = r0 + (size_t)(1 + 2 * fi[b]) * ni;
-      const double* mb = pb + ni;
+      const double* pa = r0 + (size_t)(1 + a) * ni;
+      const double* pb = r0 + (size_t)(1 + b) * ni;
       double s = 0.0;
-      for (int k = 0; k < ni; ++k) s += (pa[k] - ma[k]) * (pb[k] - mb[k]);
-      s /= (2.0 * hs[a]) * (2.0 * hs[b]);
+      for (int k = 0; k < ni; ++k) s += (pa[k] - r0[k]) * (pb[k] - r0[k]);
+      s /= hs[a] * hs[b];
       A[a * nf + b] = s;
       A[b * nf + a] = s;
     } else {
@@ -84,11 +90,10 @@ __global__ void lm_step_kernel(DevMarket m, int n, const double* res, const doub
       if (grad) {
         g[a] = 0.5 * grad[(size_t)i * P + fi[a]];
       } else {
-        const double* pa = r0 + (size_t)(1 + 2 * fi[a]) * ni;
-        const double* ma = pa + ni;
+        const double* pa = r0 + (size_t)(1 + a) * ni;
         double s = 0.0;
-        for (int k = 0; k < ni; ++k) s += (pa[k] - ma[k]) * r0[k];
-        g[a] = s / (2.0 * hs[a]);
+        for (int k = 0; k < ni; ++k) s += (pa[k] - r0[k]) * r0[k];
+        g[a] = s / hs[a];
       }
     }
   }
