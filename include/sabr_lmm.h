@@ -235,8 +235,10 @@ sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* m, int32_t market
                                         double* f_best, double* trace_f, void* stream);
 
 /* Levenberg-Marquardt polish of n points X (device [n x n_param], FP64, updated in place):
- * J from a tangent sweep, (J^T J + mu diag J^T J) d = -J^T r by Cholesky over the free slots,
- * projection on the box, mu /10 on success, x10 on failure.  f, rmse: device [n] or NULL.    */
+ * J by forward differences over the free slots (step 1e-7 max(|theta_p|, 1)), (J^T J + mu diag
+ * J^T J) d = -J^T r by Cholesky, projection on the box, mu /10 on success, x10 on failure; a
+ * point stops at target_rmse_volpt (if > 0) or once mu exceeds 1e16.  f, rmse: device [n] or
+ * NULL, those of the final points.  Paper: the local polish of the hybrid scheme, Section 3.  */
 sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t market_idx, double* X,
                                    int64_t n, int32_t max_iter, double target_rmse_volpt,
                                    double* f, double* rmse, void* stream);

@@ -457,7 +457,8 @@ namespace {
 
 template <class R, int MODEL, int FORMULA>
 cudaError_t launch_objective(const DevMarket& m, const double* X, long long n, double* f, double* vols, cudaStream_t s) {
-  const int W = 4;
+  // a few sets (a polish's trial points and stencils): one set per CTA spreads them over the SMs
+  const int W = n <= 148 * 8 ? 1 : 4;
   const uint32_t sm = smem_bytes<R>(m, W);
   auto kern = objective_kernel<R, MODEL, FORMULA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -586,14 +587,14 @@ namespace {
 
 // Device buffers of a polish of n points (allocated by the caller of lm_enqueue).
 struct LmWork {
-  double *Xp, *vols, *res, *grad, *gf, *mu, *f, *ft, *Xt, *rmse;
+  double *Xp, *vols, *res, *mu, *f, *ft, *rmse, *rmse_t, *Xt;
   int* done;
   int* any;     // set once any point has reached the target
 };
 
 size_t lm_work_bytes(const DevMarket& m, int n) {
   const size_t P = m.n_param, ni = m.n_cap + m.n_swp, S = kLmStencil;
-  return 8 * ((size_t)n * S * P + 2 * (size_t)n * S * ni + (size_t)n * P + 5 * (size_t)n + (size_t)n * P) + 4 * (size_t)n + 16 * 12;
+  return 8 * ((size_t)n * S * P + 2 * (size_t)n * S * ni + 5 * (size_t)n + (size_t)n * P) + 4 * ((size_t)n + 1) + 16;
 }
 
 LmWork lm_carve(void* base, const DevMarket& m, int n) {
@@ -603,15 +604,14 @@ LmWork lm_carve(void* base, const DevMarket& m, int n) {
   w.Xp = p; p += (size_t)n * S * P;
   w.vols = p; p += (size_t)n * S * ni;
   w.res = p; p += (size_t)n * S * ni;
-  w.grad = p; p += (size_t)n * P;
-  w.gf = p; p += n;
   w.mu = p; p += n;
   w.f = p; p += n;
   w.ft = p; p += n;
   w.rmse = p; p += n;
+  w.rmse_t = p; p += n;
   w.Xt = p; p += (size_t)n * P;
   w.done = (int*)p;
-  w.any = w.done + n;   // inside the slack of lm_work_bytes
+  w.any = w.done + n;
   return w;
 }
 
@@ -621,39 +621,43 @@ __global__ void lm_init_kernel(int n, double* mu, int* done, int* any) {
   if (i == 0) *any = 0;
 }
 
-// Enqueue max_iter LM iterations on the n points X (device, updated in place).  With
-// stop_at_first (host-driven, never under stream capture) the iterations end as soon as any point
-// has reached the target RMSE: the host reads one flag per iteration.
+// Enqueue max_iter LM iterations on the n points X (device, updated in place); f and rmse end as
+// those of the final points.  Per iteration: the stencil's model vols (1 + n_free points per point),
+// residuals, the step, the trial points' model vols with their f and RMSE, accept.  The first
+// iteration's stencil row 0 gives the starting f and RMSE.  With stop_at_first (host-driven,
+// never under stream capture) the iterations end as soon as any point has reached the target
+// RMSE: the host reads one flag after the start and after each iteration.
 cudaError_t lm_enqueue(const DevMarket& m, int n_free, double* X, int n, int max_iter, double target, const LmWork& w,
                        cudaStream_t s, bool stop_at_first = false) {
   const int S = 1 + n_free;   // stencil: the point and one forward step per free slot
-  const int ni = m.n_cap + m.n_swp;
-  const bool have_adjoint = m.n_swp == 0;
   cudaError_t e;
   lm_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w.mu, w.done, w.any);
-  if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, w.f, nullptr, s)) != cudaSuccess) return e;
-  if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
-  lm_rmse_kernel<<<n, 256, 0, s>>>(m, n, w.vols, target, w.rmse, w.done, w.any);
+  if (max_iter == 0) {
+    if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
+    lm_eval_kernel<<<n, 256, 0, s>>>(m, n, 1, w.vols, target, w.f, w.rmse, w.done, w.any);
+    return cudaGetLastError();
+  }
   auto reached = [&]() {
+    if (!stop_at_first || !(target > 0.0)) return false;
     int h = 0;
     if (cudaMemcpyAsync(&h, w.any, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
     return cudaStreamSynchronize(s) == cudaSuccess && h != 0;
   };
   for (int it = 0; it < max_iter; ++it) {
-    if (stop_at_first && target > 0.0 && reached()) break;
     lm_perturb_kernel<<<n, 32, 0, s>>>(n, m.n_param, S, m.freem, X, w.Xp);
     if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xp, (long long)n * S, nullptr, w.vols, s)) != cudaSuccess) return e;
-    residuals_from_vols_kernel<<<148 * 4, 256, 0, s>>>(m, (long long)n * S, w.vols, w.res);
-    if (have_adjoint) {
-      if ((e = launch_grad_r<double>(m, X, n, w.gf, w.grad, s)) != cudaSuccess) return e;
+    if (it == 0) {
+      lm_eval_kernel<<<n, 256, 0, s>>>(m, n, S, w.vols, target, w.f, w.rmse, w.done, w.any);
+      if (reached()) break;
     }
-    lm_step_kernel<<<n, 128, 0, s>>>(m, n, S, w.res, have_adjoint ? w.grad : nullptr, w.mu, w.done, X, w.Xt);
-    if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xt, n, w.ft, nullptr, s)) != cudaSuccess) return e;
-    lm_accept_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, m.n_param, X, w.Xt, w.f, w.ft, w.mu, w.done);
-    if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
-    lm_rmse_kernel<<<n, 256, 0, s>>>(m, n, w.vols, target, w.rmse, w.done, w.any);
+    residuals_from_vols_kernel<<<148 * 4, 256, 0, s>>>(m, (long long)n * S, w.vols, w.res);
+    lm_step_kernel<<<n, 256, 0, s>>>(m, n, S, w.res, w.mu, w.done, X, w.Xt);
+    if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xt, n, nullptr, w.vols, s)) != cudaSuccess) return e;
+    lm_eval_kernel<<<n, 256, 0, s>>>(m, n, 1, w.vols, target, w.ft, w.rmse_t, nullptr, nullptr);
+    lm_accept_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, m.n_param, X, w.Xt, w.f, w.ft, w.rmse, w.rmse_t, target, w.mu,
+                                                     w.done, w.any);
+    if (reached()) break;
   }
-  (void)ni;
   return cudaGetLastError();
 }
 

@@ -123,6 +123,42 @@ def test_lm_on_swaption_market_improves(gpu_lib):
     assert om.objective(X.cpu().numpy()[0]) == pytest.approx(f.cpu().numpy()[0], rel=1e-9)
 
 
+def test_lm_zero_iterations_reports_the_start(gpu_lib):
+    sk = synth.caplet_term_structure(n_fwd=7, n_strikes=5)
+    om, gm = _markets(sk)
+    X0 = _points(sk, 5, seed=11)
+    X, f, r = gm.lm_polish(X0, max_iter=0)
+    X, f, r = X.cpu().numpy(), f.cpu().numpy(), r.cpu().numpy()
+    assert np.array_equal(X, X0)
+    for i in range(5):
+        assert f[i] == pytest.approx(om.objective(X0[i]), rel=1e-12)
+        assert r[i] == pytest.approx(om.rmse_volpt(X0[i]), rel=1e-12)
+
+
+def test_lm_f_and_rmse_are_those_of_the_returned_points(gpu_lib):
+    sk = synth.caplet_term_structure(n_fwd=7, n_strikes=5)
+    om, gm = _markets(sk)
+    X0 = _points(sk, 6, seed=12)
+    X, f, r = gm.lm_polish(X0, max_iter=8)
+    X, f, r = X.cpu().numpy(), f.cpu().numpy(), r.cpu().numpy()
+    for i in range(6):
+        assert f[i] == pytest.approx(om.objective(X[i]), rel=1e-12)
+        assert r[i] == pytest.approx(om.rmse_volpt(X[i]), rel=1e-12)
+        assert f[i] <= om.objective(X0[i])
+        assert np.all(X[i] >= sk.lo) and np.all(X[i] <= sk.hi)
+
+
+@pytest.mark.parametrize("k", [1, 64])
+def test_anneal_polish_top_k_bounds(gpu_lib, k):
+    # k = 1 and k = n_chains (every chain polished) through the top-k selection
+    sk = synth.smile_2y()
+    om, gm = _markets(sk)
+    r0 = gm.anneal(64, 10, 20, 0.85, seed=5, prec="fp32")
+    r1 = gm.anneal(64, 10, 20, 0.85, seed=5, prec="fp32", lm_top_k=k, lm_max_iter=10)
+    assert r1["f_best"][0] <= r0["f_best"][0]
+    assert om.objective(r1["x_best"][0]) == pytest.approx(r1["f_best"][0], rel=1e-12)
+
+
 def test_anneal_with_top_k_polish(gpu_lib):
     sk = synth.smile_2y()
     om, gm = _markets(sk)
