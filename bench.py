@@ -238,14 +238,17 @@ def run_profile(args):
     L = args.levels or L0
     s = torch.cuda.Stream()
     plan = gm.anneal_prepare(C, L, N, cooling, 240801470, prec=args.prec,
-                             use_graph=False, stream=s, warps_per_block=args.warps_per_block)
+                             use_graph=False, stream=s, warps_per_block=args.warps_per_block,
+                             lm_top_k=args.lm_top_k, lm_max_iter=50, target_rmse=TARGET_RMSE_VOLPT)
     for _ in range(2):
         plan.launch(stream=s)
         r = plan.fetch()
     prices = sum(sk.n_instr for sk in sks) * r["n_evals"]
     print(json.dumps({"profile": True, "workload": args.workload, "levels": L, "prec": args.prec,
                       "f_best": float(r["f_best"][0]), "seconds": r["seconds"],
-                      "prices_per_s": prices / r["seconds"], "ms_per_level": 1e3 * r["seconds"] / L}))
+                      "prices_per_s": prices / r["seconds"], "ms_per_level": 1e3 * r["seconds"] / L,
+                      "lm_top_k": args.lm_top_k, "lm_seconds": r["lm_seconds"],
+                      "rmse_volpt": float(r["rmse_volpt"][0])}))
 
 
 def main():
@@ -264,6 +267,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run the workload's search once (optionally shortened) and exit: the ncu target")
     ap.add_argument("--levels", type=int, default=0, help="with --profile: temperature levels (0 = workload's)")
+    ap.add_argument("--lm-top-k", type=int, default=0,
+                    help="with --profile: Levenberg-Marquardt polish of the k best chains after the search")
     ap.add_argument("--workload", default="caplets", choices=list(WORKLOADS),
                     help="with --profile: the search to run (the timed line is always the caplet workload)")
     args = ap.parse_args()
