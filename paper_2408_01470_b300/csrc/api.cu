@@ -551,7 +551,7 @@ extern "C" sabr_lmm_status sabr_lmm_model_vols(const sabr_lmm_market* m, int32_t
 namespace {
 template <class R, int MODEL, int FORMULA>
 cudaError_t launch_grad(const DevMarket& m, const double* X, long long n, double* f, double* G, cudaStream_t s) {
-  const int W = 4;
+  const int W = n <= 148 * 8 ? 1 : 4;   // a few sets: one per CTA
   const uint32_t sm = smem_bytes_grad<R>(m, W);
   auto kern = grad_kernel<R, MODEL, FORMULA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -587,14 +587,14 @@ namespace {
 
 // Device buffers of a polish of n points (allocated by the caller of lm_enqueue).
 struct LmWork {
-  double *Xp, *vols, *res, *mu, *f, *ft, *rmse, *rmse_t, *Xt;
+  double *Xp, *vols, *res, *grad, *gf, *mu, *f, *ft, *rmse, *rmse_t, *Xt;
   int* done;
   int* any;     // set once any point has reached the target
 };
 
 size_t lm_work_bytes(const DevMarket& m, int n) {
   const size_t P = m.n_param, ni = m.n_cap + m.n_swp, S = kLmStencil;
-  return 8 * ((size_t)n * S * P + 2 * (size_t)n * S * ni + 5 * (size_t)n + (size_t)n * P) + 4 * ((size_t)n + 1) + 16;
+  return 8 * ((size_t)n * S * P + 2 * (size_t)n * S * ni + 6 * (size_t)n + 2 * (size_t)n * P) + 4 * ((size_t)n + 1) + 16;
 }
 
 LmWork lm_carve(void* base, const DevMarket& m, int n) {
@@ -604,6 +604,8 @@ LmWork lm_carve(void* base, const DevMarket& m, int n) {
   w.Xp = p; p += (size_t)n * S * P;
   w.vols = p; p += (size_t)n * S * ni;
   w.res = p; p += (size_t)n * S * ni;
+  w.grad = p; p += (size_t)n * P;
+  w.gf = p; p += n;
   w.mu = p; p += n;
   w.f = p; p += n;
   w.ft = p; p += n;
@@ -621,16 +623,47 @@ __global__ void lm_init_kernel(int n, double* mu, int* done, int* any) {
   if (i == 0) *any = 0;
 }
 
+// A non-blocking side stream and a fork/join event pair per device, made on first use: the
+// reverse sweep of a polish runs there beside the stencil evaluation.
+struct LmSide {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_side_mu;
+
+cudaError_t lm_side(LmSide& out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::map<int, LmSide> sides;
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  auto it = sides.find(dev);
+  if (it == sides.end()) {
+    LmSide sd;
+    if ((e = cudaStreamCreateWithFlags(&sd.s2, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    it = sides.emplace(dev, sd).first;
+  }
+  out = it->second;
+  return cudaSuccess;
+}
+
 // Enqueue max_iter LM iterations on the n points X (device, updated in place); f and rmse end as
-// those of the final points.  Per iteration: the stencil's model vols (1 + n_free points per point),
-// residuals, the step, the trial points' model vols with their f and RMSE, accept.  The first
-// iteration's stencil row 0 gives the starting f and RMSE.  With stop_at_first (host-driven,
-// never under stream capture) the iterations end as soon as any point has reached the target
-// RMSE: the host reads one flag after the start and after each iteration.
+// those of the final points.  Per iteration: the stencil's model vols (1 + n_free points per point)
+// and, on caplet markets, the reverse sweep beside them on a side stream; residuals, the step, the
+// trial points' model vols with their f and RMSE, accept.  The first iteration's stencil row 0 gives
+// the starting f and RMSE.  With stop_at_first (host-driven, never under stream capture) the
+// iterations end as soon as any point has reached the target RMSE: the host reads one flag after
+// the start and after each iteration.  Calls sharing a device share the side stream, so polishes
+// on different streams of one device serialise their reverse sweeps.
 cudaError_t lm_enqueue(const DevMarket& m, int n_free, double* X, int n, int max_iter, double target, const LmWork& w,
                        cudaStream_t s, bool stop_at_first = false) {
   const int S = 1 + n_free;   // stencil: the point and one forward step per free slot
+  const bool have_adjoint = m.n_swp == 0;
   cudaError_t e;
+  LmSide side;
+  if (have_adjoint && max_iter > 0 && (e = lm_side(side)) != cudaSuccess) return e;
   lm_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, w.mu, w.done, w.any);
   if (max_iter == 0) {
     if ((e = launch_objective_any(m, SABR_LMM_FP64, X, n, nullptr, w.vols, s)) != cudaSuccess) return e;
@@ -644,14 +677,31 @@ cudaError_t lm_enqueue(const DevMarket& m, int n_free, double* X, int n, int max
     return cudaStreamSynchronize(s) == cudaSuccess && h != 0;
   };
   for (int it = 0; it < max_iter; ++it) {
+    if (have_adjoint) {   // fork: the reverse sweep at X on the side stream, beside the stencil
+      if ((e = cudaEventRecord(side.fork, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(side.s2, side.fork, 0)) != cudaSuccess) return e;
+      e = launch_grad_r<double>(m, X, n, w.gf, w.grad, side.s2);
+      const cudaError_t e2 = cudaEventRecord(side.join, side.s2);
+      if (e != cudaSuccess) return e;
+      if (e2 != cudaSuccess) return e2;
+    }
+    // join before anything that reads the gradient, and before leaving (the caller may free w)
+    auto join = [&]() { return have_adjoint ? cudaStreamWaitEvent(s, side.join, 0) : cudaSuccess; };
     lm_perturb_kernel<<<n, 32, 0, s>>>(n, m.n_param, S, m.freem, X, w.Xp);
-    if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xp, (long long)n * S, nullptr, w.vols, s)) != cudaSuccess) return e;
+    if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xp, (long long)n * S, nullptr, w.vols, s)) != cudaSuccess) {
+      join();
+      return e;
+    }
     if (it == 0) {
       lm_eval_kernel<<<n, 256, 0, s>>>(m, n, S, w.vols, target, w.f, w.rmse, w.done, w.any);
-      if (reached()) break;
+      if (reached()) {
+        if ((e = join()) != cudaSuccess) return e;
+        break;
+      }
     }
     residuals_from_vols_kernel<<<148 * 4, 256, 0, s>>>(m, (long long)n * S, w.vols, w.res);
-    lm_step_kernel<<<n, 256, 0, s>>>(m, n, S, w.res, w.mu, w.done, X, w.Xt);
+    if ((e = join()) != cudaSuccess) return e;
+    lm_step_kernel<<<n, 256, 0, s>>>(m, n, S, w.res, have_adjoint ? w.grad : nullptr, w.mu, w.done, X, w.Xt);
     if ((e = launch_objective_any(m, SABR_LMM_FP64, w.Xt, n, nullptr, w.vols, s)) != cudaSuccess) return e;
     lm_eval_kernel<<<n, 256, 0, s>>>(m, n, 1, w.vols, target, w.ft, w.rmse_t, nullptr, nullptr);
     lm_accept_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, m.n_param, X, w.Xt, w.f, w.ft, w.rmse, w.rmse_t, target, w.mu,

@@ -3,7 +3,8 @@
 //   r      residuals sqrt(w_k)(P_k - P_k^mkt) at theta (FP64, from the model vols);
 //   J      columns by forward differences (r(theta + h e_p) - r(theta)) / h, h = 1e-7 max(|theta_p|, 1),
 //          over the free slots only (1 + n_free evaluations per point and iteration);
-//   g      J^T r from the same J;
+//   g      half the gradient from the reverse sweep where the market has one (caplet markets; it
+//          runs on a side stream beside the stencil), else J^T r from the same J;
 //   step   (J^T J + mu diag(J^T J)) d = -g by Cholesky over the free slots (a zero diagonal is
 //          floored at 1e-12 of the largest), theta' = clamp(theta + d) on the box;
 //   accept if f(theta') < f(theta): theta = theta', mu = max(mu / 10, 1e-12); else mu *= 10.
@@ -55,12 +56,12 @@ __global__ void residuals_from_vols_kernel(DevMarket m, long long npts, const do
 
 // Normal equations and the damped step, one CTA (256 threads) per point.  The residual rows of the
 // stencil pass through shared memory in tiles of kLmTile instruments; thread t < n_free (n_free + 1) / 2
-// accumulates one entry (a, b >= a) of J^T J, the next n_free threads one entry of J^T r.  Warp 0
-// factors the damped matrix in shared memory.
+// accumulates one entry (a, b >= a) of J^T J, the next n_free threads one entry of J^T r (replaced
+// by grad / 2 when grad is given).  Warp 0 factors the damped matrix in shared memory.
 constexpr int kLmTile = 64;
 
-__global__ void __launch_bounds__(256) lm_step_kernel(DevMarket m, int n, int S, const double* res, const double* mu,
-                                                      const int* done, const double* X, double* Xt) {
+__global__ void __launch_bounds__(256) lm_step_kernel(DevMarket m, int n, int S, const double* res, const double* grad,
+                                                      const double* mu, const int* done, const double* X, double* Xt) {
   const int i = blockIdx.x;
   if (i >= n) return;
   const int P = m.n_param, ni = m.n_cap + m.n_swp;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) lm_step_kernel(DevMarket m, int n, int S,
       A[ra * nf + rb] = acc;
       A[rb * nf + ra] = acc;
     } else {
-      g[ra] = acc;
+      g[ra] = grad ? 0.5 * grad[(size_t)i * P + fi[ra]] : acc;
     }
   }
   __syncthreads();
