@@ -222,6 +222,10 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
     R acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0;
+    // e^{-gamma_h o2} of this lane's inner nodes: the same for every panel
+    R eo2[kQ];
+#pragma unroll
+    for (int r = 0; r < kQ; ++r) eo2[r] = Num<R>::exp_(-gh * qt.o2[q * kQ + r]);
     const int NPc = round_up(NP, 4);
     for (int p = pg; p < NPc; p += 4) {
       if (p >= NP) continue;
@@ -253,7 +257,7 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
         const R o2 = qt.o2[q * kQ + r];
         const R sw2 = qt.sw2[q * kQ + r];
         const R v = base + o2;
-        const R ev = E.b * Num<R>::exp_(-gh * o2);   // e^{-gamma_h v}
+        const R ev = E.b * eo2[r];                   // e^{-gamma_h v}
         const R lin = ah + bh * v;
         const R hv = lin * ev + dh;
         Rin += sw2 * sw2 * hv * hv;
