@@ -1077,6 +1077,11 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
       p->lm_off.push_back(B.take(lm_work_bytes(mk->dm[j], k)));  // LM work
     }
     if (cudaMalloc(&p->lm_buf, B.size) != cudaSuccess) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOMEM, "cudaMalloc of the polish buffers failed"); }
+    LmSide side;   // the polish's side stream, made here rather than inside a timed launch
+    if (cudaError_t e = lm_side(side); e != cudaSuccess) {
+      sabr_lmm_anneal_plan_free(p);
+      return fail(SABR_LMM_ECUDA, std::string("polish side stream: ") + cudaGetErrorString(e));
+    }
   }
   for (int j = 0; j < nm && !p->batch; ++j) {
     cudaError_t e = enqueue_anneal(mk->dm[j], o->prec, p->st[j], p->sp[j], p->W, p->grid, p->stream, true);

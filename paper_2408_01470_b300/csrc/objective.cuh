@@ -546,6 +546,18 @@ __device__ __forceinline__ FF warp_sum_lanes(float p) {
 }
 __device__ __forceinline__ double warp_sum_lanes(double p) { return warp_sum(p); }
 
+// The per-lane FP32 partials of one warp summed by an FP32 butterfly (the same value in every lane:
+// each level adds the same two operands in both lanes).  Relative error <= 5 u, below the
+// per-lane accumulation's; no FP64 instruction.
+__device__ __forceinline__ FF warp_sum_lanes_f32(float p) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
+  FF r;
+  r.hi = p;
+  r.lo = 0.0f;
+  return r;
+}
+
 
 template <class R> struct ObjOf { typedef double T; };
 template <> struct ObjOf<float> { typedef FF T; };
@@ -593,7 +605,9 @@ __device__ typename ObjOf<R>::T warp_objective(const DevMarket& m, const InstrVi
   }
   __syncwarp();
   if (vols) return obj_inf(O());
-  const O f = warp_sum_lanes(part);
+  O f;
+  if constexpr (std::is_same<R, float>::value) f = warp_sum_lanes_f32(part);
+  else f = warp_sum_lanes(part);
   const bool bad = __any_sync(0xffffffffu, !ok);
   if (bad || !obj_finite(f)) return obj_inf(O());
   return f;
