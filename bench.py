@@ -236,6 +236,7 @@ def run_profile(args):
     lib.load()
     gm, sks, _, C, L0, N, cooling = workload_markets(lib, args.workload)
     L = args.levels or L0
+    C = args.chains or C
     s = torch.cuda.Stream()
     plan = gm.anneal_prepare(C, L, N, cooling, 240801470, prec=args.prec,
                              use_graph=False, stream=s, warps_per_block=args.warps_per_block,
@@ -244,7 +245,7 @@ def run_profile(args):
         plan.launch(stream=s)
         r = plan.fetch()
     prices = sum(sk.n_instr for sk in sks) * r["n_evals"]
-    print(json.dumps({"profile": True, "workload": args.workload, "levels": L, "prec": args.prec,
+    print(json.dumps({"profile": True, "workload": args.workload, "chains": C, "levels": L, "prec": args.prec,
                       "f_best": float(r["f_best"][0]), "seconds": r["seconds"],
                       "prices_per_s": prices / r["seconds"], "ms_per_level": 1e3 * r["seconds"] / L,
                       "lm_top_k": args.lm_top_k, "lm_seconds": r["lm_seconds"],
@@ -267,6 +268,7 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="run the workload's search once (optionally shortened) and exit: the ncu target")
     ap.add_argument("--levels", type=int, default=0, help="with --profile: temperature levels (0 = workload's)")
+    ap.add_argument("--chains", type=int, default=0, help="with --profile: chains per market (0 = workload's)")
     ap.add_argument("--lm-top-k", type=int, default=0,
                     help="with --profile: Levenberg-Marquardt polish of the k best chains after the search")
     ap.add_argument("--workload", default="caplets", choices=list(WORKLOADS),

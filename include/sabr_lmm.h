@@ -243,6 +243,20 @@ sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t market_idx,
                                    int64_t n, int32_t max_iter, double target_rmse_volpt,
                                    double* f, double* rmse, void* stream);
 
+/* Introspection: the geometry of market market_idx and what its kernels need per CTA.
+ *   n_panels, n_diag: absolute 0.5y panels and forward-index diagonals of the swaption tables;
+ *   n_swap: distinct swaps behind the swaptions; max_window: most forwards in one expiry group;
+ *   smem_fp64, smem_fp32: dynamic shared memory per CTA (one chain per CTA with swaptions, four
+ *   chains per CTA for caplet markets); batch_ctas_per_sm_*: 256-thread CTAs of the batch kernel
+ *   that fit one SM at that precision (0 if the market does not fit).  out is host memory.  */
+typedef struct {
+  int32_t n_fwd, n_cap, n_swp, n_swap, n_panels, n_diag, max_window;
+  uint32_t smem_fp64, smem_fp32;
+  int32_t batch_ctas_per_sm_fp64, batch_ctas_per_sm_fp32;
+} sabr_lmm_market_info_t;
+sabr_lmm_status sabr_lmm_market_info(const sabr_lmm_market* m, int32_t market_idx,
+                                     sabr_lmm_market_info_t* out);
+
 /* Introspection: the Gauss-Legendre rule the kernels use (nodes on [-1,1], weights), q = 8. */
 sabr_lmm_status sabr_lmm_quadrature_rule(int32_t q, double* x, double* w);
 

@@ -69,13 +69,22 @@ class Result(C.Structure):
     ]
 
 
+class MarketInfo(C.Structure):
+    _fields_ = [
+        ("n_fwd", C.c_int32), ("n_cap", C.c_int32), ("n_swp", C.c_int32), ("n_swap", C.c_int32),
+        ("n_panels", C.c_int32), ("n_diag", C.c_int32), ("max_window", C.c_int32),
+        ("smem_fp64", C.c_uint32), ("smem_fp32", C.c_uint32),
+        ("batch_ctas_per_sm_fp64", C.c_int32), ("batch_ctas_per_sm_fp32", C.c_int32),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
 EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective", "sabr_lmm_model_vols",
            "sabr_lmm_objective_grad", "sabr_lmm_anneal", "sabr_lmm_anneal_prepare", "sabr_lmm_anneal_launch",
            "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_anneal_noalloc", "sabr_lmm_lm_polish",
-           "sabr_lmm_quadrature_rule", "sabr_lmm_last_error", "sabr_lmm_version")
+           "sabr_lmm_market_info", "sabr_lmm_quadrature_rule", "sabr_lmm_last_error", "sabr_lmm_version")
 
 
 def open_library(path: str = LIB_PATH):
@@ -99,6 +108,7 @@ def open_library(path: str = LIB_PATH):
     lib.sabr_lmm_anneal_plan_free.restype = None
     lib.sabr_lmm_lm_polish.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_double,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_market_info.argtypes = [C.c_void_p, C.c_int32, C.POINTER(MarketInfo)]
     lib.sabr_lmm_quadrature_rule.argtypes = [C.c_int32, _D, _D]
     lib.sabr_lmm_last_error.restype = C.c_char_p
     lib.sabr_lmm_version.restype = C.c_char_p
@@ -238,6 +248,12 @@ class Market:
         """f(X) as a differentiable torch op: the forward and the backward both come from
         sabr_lmm_objective_grad (the hand-written adjoint), through CalibrationObjective."""
         return CalibrationObjective.apply(X, self, prec, market)
+
+    def info(self, market=0):
+        """sabr_lmm_market_info: geometry and per-CTA resources of one market, as a dict."""
+        out = MarketInfo()
+        _check(self._lib.sabr_lmm_market_info(self.h, market, C.byref(out)))
+        return {name: getattr(out, name) for name, _ in MarketInfo._fields_}
 
     def lm_polish(self, X, max_iter=50, target_rmse=0.0, market=0, stream=None):
         """sabr_lmm_lm_polish: returns (X polished, f, rmse in vol points) as device tensors."""

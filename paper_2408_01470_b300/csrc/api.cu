@@ -826,11 +826,27 @@ cudaError_t enqueue_batch(const sabr_lmm_anneal_plan* p, cudaStream_t s, int lev
                       : enqueue_batch_t<float, 1>(p, s, levels, configure_only);
 }
 
-int batch_blocks_per_sm(int prec, int threads, uint32_t smem) {
-  int per_sm = 0;
-  if (prec == SABR_LMM_FP64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<double, 0>, threads, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sa_level_batch_kernel<float, 0>, threads, smem);
+// CTAs of a kernel per SM at this CTA size and dynamic shared memory (0 if one does not fit).
+// The occupancy query counts no CTA whose request exceeds the kernel's opt-in limit, so the
+// limit is raised first to the device maximum less the kernel's static shared memory.
+template <class K>
+int blocks_per_sm(K kern, int threads, uint32_t smem) {
+  int dev = 0, optin = 0, per_sm = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
+    return 0;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
+  if ((int)smem > dyn_max) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess) return 0;
   return per_sm;
+}
+
+int batch_blocks_per_sm(int prec, int threads, uint32_t smem) {
+  return prec == SABR_LMM_FP64 ? blocks_per_sm(sa_level_batch_kernel<double, 0>, threads, smem)
+                               : blocks_per_sm(sa_level_batch_kernel<float, 0>, threads, smem);
 }
 
 // Autotuner of the batch launches: per shared-memory bucket, CTA size x persistent grid, chosen by
@@ -1024,7 +1040,9 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
       const uint32_t sm = o->prec == SABR_LMM_FP64 ? smem_bytes_cta<double>(m) : smem_bytes_cta<float>(m);
       if (sm > 227 * 1024) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOTSUP, "a batch market does not fit in one CTA's shared memory at this precision"); }
       smax = std::max(smax, sm);
-      const int per_sm = std::max(1, batch_blocks_per_sm(o->prec, 256, sm));
+      // keyed at 128 threads (1-4 CTAs per SM; at 256 the registers cap every market at 2)
+      const int per_sm = batch_blocks_per_sm(o->prec, 128, sm);
+      if (per_sm < 1) { sabr_lmm_anneal_plan_free(p); return fail(SABR_LMM_ENOTSUP, "a batch market does not fit in one CTA's shared memory at this precision"); }
       buckets[per_sm].push_back({-(long long)(m.n_cap + 4 * m.n_swp + 60 * m.n_swap), j});
       bsm[per_sm] = std::max(bsm[per_sm], sm);
     }
@@ -1237,6 +1255,30 @@ extern "C" sabr_lmm_status sabr_lmm_anneal(const sabr_lmm_market* mk, const sabr
   if (st == SABR_LMM_OK) st = sabr_lmm_anneal_fetch(p, out);
   sabr_lmm_anneal_plan_free(p);
   return st;
+}
+
+extern "C" sabr_lmm_status sabr_lmm_market_info(const sabr_lmm_market* m, int32_t idx, sabr_lmm_market_info_t* out) {
+  if (!m || !out) return fail(SABR_LMM_EINVAL, "market and out are required");
+  if (idx < 0 || idx >= (int)m->dm.size()) return fail(SABR_LMM_EINVAL, "market_idx out of range");
+  const DevMarket& d = m->dm[idx];
+  out->n_fwd = d.n_fwd;
+  out->n_cap = d.n_cap;
+  out->n_swp = d.n_swp;
+  out->n_swap = d.n_swap;
+  out->n_panels = d.NA;
+  out->n_diag = d.ND;
+  out->max_window = d.max_gwin;
+  out->smem_fp64 = market_smem(d, SABR_LMM_FP64);
+  out->smem_fp32 = market_smem(d, SABR_LMM_FP32);
+  auto per_sm = [&](int prec, uint32_t sm) {
+    if (d.model != SABR_LMM_MODEL_REBONATO || sm > 227u * 1024u) return 0;
+    return std::max(0, batch_blocks_per_sm(prec, 256, prec == SABR_LMM_FP64 ? smem_bytes_cta<double>(d)
+                                                                              : smem_bytes_cta<float>(d)));
+  };
+  out->batch_ctas_per_sm_fp64 = per_sm(SABR_LMM_FP64, out->smem_fp64);
+  out->batch_ctas_per_sm_fp32 = per_sm(SABR_LMM_FP32, out->smem_fp32);
+  CUDA_TRY(cudaGetLastError());
+  return SABR_LMM_OK;
 }
 
 extern "C" sabr_lmm_status sabr_lmm_quadrature_rule(int32_t q, double* x, double* w) {

@@ -122,3 +122,19 @@ def test_swaption_anneal_fp32_runs_and_improves(gpu_lib):
     assert np.isfinite(r["f_best"][0]) and r["f_best"][0] < f0
     # the returned point is scored consistently by the oracle
     assert om.objective(r["x_best"][0]) == pytest.approx(r["f_best"][0], rel=1e-3)
+
+
+def test_market_info_geometry(gpu_lib):
+    import paper_2408_01470_b300 as lib
+    sk = synth.joint_caplet_swaption()
+    gm = lib.Market(sk, np.full(sk.n_instr, 0.2))
+    d = gm.info()
+    assert (d["n_fwd"], d["n_cap"], d["n_swp"]) == (40, 300, 700)
+    assert d["n_swap"] == len(set(zip(sk.swp_start.tolist(), sk.swp_end.tolist()))) == 100
+    # panels up to the last expiry (10y = 20) plus the widest offset inside a window (19)
+    assert d["n_panels"] == 39 and 1 <= d["n_diag"] <= 20 and d["max_window"] <= 20
+    assert 0 < d["smem_fp32"] < d["smem_fp64"] <= 227 * 1024
+    assert d["batch_ctas_per_sm_fp32"] >= d["batch_ctas_per_sm_fp64"] >= 1
+    cap = synth.caplet_term_structure()
+    c = lib.Market(cap, np.full(cap.n_instr, 0.2)).info()
+    assert (c["n_fwd"], c["n_cap"], c["n_swp"], c["n_swap"]) == (20, 300, 0, 0)
