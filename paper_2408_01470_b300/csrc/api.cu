@@ -798,7 +798,7 @@ cudaError_t enqueue_anneal(const DevMarket& m, int prec, const SAState& st, cons
 }
 
 template <class R, int FORMULA>
-cudaError_t enqueue_batch_t(const sabr_lmm_anneal_plan* p, cudaStream_t s, int levels, bool configure_only) {
+cudaError_t enqueue_batch_t(const sabr_lmm_anneal_plan* p, cudaStream_t s, int levels, bool configure_only, int only) {
   auto k0 = sa_start_batch_kernel<R, FORMULA>;
   auto k1 = sa_level_batch_kernel<R, FORMULA>;
   if (configure_only) {
@@ -812,18 +812,24 @@ cudaError_t enqueue_batch_t(const sabr_lmm_anneal_plan* p, cudaStream_t s, int l
   if (e != cudaSuccess) return e;
   k0<<<p->ba.n_markets, 256, p->bsmem, s>>>(p->ba);
   for (int l = 0; l < levels; ++l)
-    for (const auto& b : p->bk) k1<<<b.grid, b.threads, b.smem, s>>>(b.ba, l);
+    for (int i = 0; i < (int)p->bk.size(); ++i) {
+      if (only >= 0 && i != only) continue;
+      const auto& b = p->bk[i];
+      k1<<<b.grid, b.threads, b.smem, s>>>(b.ba, l);
+    }
   sa_final_batch_kernel<<<p->ba.n_markets, 1024, 0, s>>>(p->ba);
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_batch(const sabr_lmm_anneal_plan* p, cudaStream_t s, int levels, bool configure_only = false) {
+// The batch search: start, levels x (one launch per bucket, or only bucket `only`), final.
+cudaError_t enqueue_batch(const sabr_lmm_anneal_plan* p, cudaStream_t s, int levels, bool configure_only = false,
+                          int only = -1) {
   const bool f64 = p->opts.prec == SABR_LMM_FP64;
   const int formula = p->mk->dm[0].formula;
-  if (f64) return formula == 0 ? enqueue_batch_t<double, 0>(p, s, levels, configure_only)
-                               : enqueue_batch_t<double, 1>(p, s, levels, configure_only);
-  return formula == 0 ? enqueue_batch_t<float, 0>(p, s, levels, configure_only)
-                      : enqueue_batch_t<float, 1>(p, s, levels, configure_only);
+  if (f64) return formula == 0 ? enqueue_batch_t<double, 0>(p, s, levels, configure_only, only)
+                               : enqueue_batch_t<double, 1>(p, s, levels, configure_only, only);
+  return formula == 0 ? enqueue_batch_t<float, 0>(p, s, levels, configure_only, only)
+                      : enqueue_batch_t<float, 1>(p, s, levels, configure_only, only);
 }
 
 // CTAs of a kernel per SM at this CTA size and dynamic shared memory (0 if one does not fit).
@@ -850,8 +856,8 @@ int batch_blocks_per_sm(int prec, int threads, uint32_t smem) {
 }
 
 // Autotuner of the batch launches: per shared-memory bucket, CTA size x persistent grid, chosen by
-// timing one level of a short probe (4 steps per chain) per candidate while the other buckets keep
-// their settings; cached per (precision, formula, instrument bucket, market-count bucket, CTAs/SM).
+// timing that bucket's launch on one level of a short probe (4 steps per chain) per candidate;
+// cached per (precision, formula, instrument bucket, market-count bucket, CTAs/SM).
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
@@ -863,7 +869,8 @@ sabr_lmm_status tune_batch(sabr_lmm_anneal_plan* p, cudaStream_t s) {
   for (auto& q : probe) q.N = std::min(q.N, 4);
   bool probing = false;
   cudaEvent_t a = nullptr, b = nullptr;
-  for (auto& bk : p->bk) {
+  for (int bi = 0; bi < (int)p->bk.size(); ++bi) {
+    auto& bk = p->bk[bi];
     int max_instr = 0;
     for (int j : bk.markets) max_instr = std::max(max_instr, p->mk->dm[j].n_cap + p->mk->dm[j].n_swp);
     const auto key = std::make_tuple(p->opts.prec, p->mk->dm[0].formula, (max_instr + 255) / 256,
@@ -892,9 +899,9 @@ sabr_lmm_status tune_batch(sabr_lmm_anneal_plan* p, cudaStream_t s) {
     for (const auto& c : cand) {
       bk.threads = c.first;
       bk.grid = c.second;
-      CUDA_TRY(enqueue_batch(p, s, 1));   // warm-up
+      CUDA_TRY(enqueue_batch(p, s, 1, false, bi));   // warm-up
       CUDA_TRY(cudaEventRecord(a, s));
-      CUDA_TRY(enqueue_batch(p, s, 1));
+      CUDA_TRY(enqueue_batch(p, s, 1, false, bi));
       CUDA_TRY(cudaEventRecord(b, s));
       CUDA_TRY(cudaEventSynchronize(b));
       float ms = 0.f;

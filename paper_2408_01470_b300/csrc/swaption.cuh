@@ -463,11 +463,17 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
         const Q4<R>* B2 = (const Q4<R>*)(B + npm);
         const Q4<R>* B3 = (const Q4<R>*)(B + 2 * npm);
         R v1 = 0, v2 = 0, v3 = 0;
-        for (int q = k; q < nq; q += nk) {
-          const Q4<R> w = Cq[q], x = B1[q], y = B2[q], z = B3[q];
-          v1 += w.a * x.a; v1 += w.b * x.b; v1 += w.c * x.c; v1 += w.d * x.d;
-          v2 += w.a * y.a; v2 += w.b * y.b; v2 += w.c * y.c; v2 += w.d * y.d;
-          v3 += w.a * z.a; v3 += w.b * z.b; v3 += w.c * z.c; v3 += w.d * z.d;
+        // the chunk's <= kChunk / 4 quads, unrolled so that the coefficient loads (global memory)
+        // can be issued together
+#pragma unroll
+        for (int i = 0; i < kChunk / 4; ++i) {
+          const int q = k + i * nk;
+          if (q < nq) {
+            const Q4<R> w = Cq[q], x = B1[q], y = B2[q], z = B3[q];
+            v1 += w.a * x.a; v1 += w.b * x.b; v1 += w.c * x.c; v1 += w.d * x.d;
+            v2 += w.a * y.a; v2 += w.b * y.b; v2 += w.c * y.c; v2 += w.d * y.d;
+            v3 += w.a * z.a; v3 += w.b * z.b; v3 += w.c * z.c; v3 += w.d * z.d;
+          }
         }
         const int pc = c - c0, nb = m.max_batch_chunks;
         Pc[pc] = v1;
