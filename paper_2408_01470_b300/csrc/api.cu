@@ -267,20 +267,22 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     // chunks of <= kChunk pairs, 4-pair quads interleaved (swaps are ordered by group, so the
     // chunks are too)
     for (size_t g = 0; g < grp_a[j].size(); ++g) {
-      grp_chunk0[j].push_back((int)chunk[j].size() / 2);
+      grp_chunk0[j].push_back((int)chunk[j].size() / 4);
       for (int s2 = grp_swap0[j][g]; s2 < grp_swap0[j][g + 1]; ++s2) {
-        swap_chunk0[j].push_back((int)chunk[j].size() / 2);
+        swap_chunk0[j].push_back((int)chunk[j].size() / 4);
         const int np = swap_L[j][s2] * (swap_L[j][s2] + 1) / 2;
         const int nq = (np + 3) / 4, nk = (nq + kChunk / 4 - 1) / (kChunk / 4);
-        for (int k = 0; k < nk; ++k) {
-          chunk[j].push_back(s2);
+        for (int k = 0; k < nk; ++k) {   // {coefficient row offset, group, k | nk << 16, quads}
+          chunk[j].push_back(swap_coff[j][s2]);
+          chunk[j].push_back((int)g);
           chunk[j].push_back(k | (nk << 16));
+          chunk[j].push_back(nq);
         }
       }
     }
-    grp_chunk0[j].push_back((int)chunk[j].size() / 2);
-    swap_chunk0[j].push_back((int)chunk[j].size() / 2);
-    m.n_chunk = (int)chunk[j].size() / 2;
+    grp_chunk0[j].push_back((int)chunk[j].size() / 4);
+    swap_chunk0[j].push_back((int)chunk[j].size() / 4);
+    m.n_chunk = (int)chunk[j].size() / 4;
 
     m.n_swap = (int)swap_a[j].size();
     m.max_win = max_win;
@@ -342,7 +344,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.swap_coff = A.take((m.n_swap + 1) * 4);
     o.swap_C64 = A.take((size_t)swap_coff[j].back() * 8);
     o.swap_C32 = A.take((size_t)swap_coff[j].back() * 4);
-    o.chunk = A.take((size_t)m.n_chunk * 8);
+    o.chunk = A.take((size_t)m.n_chunk * 16);
     o.grp_chunk0 = A.take((m.n_grp + 1) * 4);
     o.swap_chunk0 = A.take((m.n_swap + 1) * 4);
   }
@@ -369,7 +371,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     put(o.swap_grp, swap_grp[j].data(), m.n_swap * 4); put(o.swap_L, swap_L[j].data(), m.n_swap * 4);
     put(o.grp_pair, grp_pair[j].data(), (size_t)m.n_grp * m.max_npk * 4);
     put(o.swap_coff, swap_coff[j].data(), (m.n_swap + 1) * 4);
-    put(o.chunk, chunk[j].data(), (size_t)m.n_chunk * 8);
+    put(o.chunk, chunk[j].data(), (size_t)m.n_chunk * 16);
     put(o.grp_chunk0, grp_chunk0[j].data(), grp_chunk0[j].size() * 4);
     put(o.swap_chunk0, swap_chunk0[j].data(), swap_chunk0[j].size() * 4);
     QuadTab<double> q64;
@@ -426,7 +428,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.swap_L = (const int*)(base + o.swap_L); m.swap_W32 = (float*)(base + o.swap_W32);
     m.grp_pair = (const int*)(base + o.grp_pair); m.swap_coff = (const int*)(base + o.swap_coff);
     m.swap_C64 = (const double*)(base + o.swap_C64); m.swap_C32 = (const float*)(base + o.swap_C32);
-    m.chunk = (const int2*)(base + o.chunk); m.grp_chunk0 = (const int*)(base + o.grp_chunk0);
+    m.chunk = (const int4*)(base + o.chunk); m.grp_chunk0 = (const int*)(base + o.grp_chunk0);
     m.swap_chunk0 = (const int*)(base + o.swap_chunk0);
     setup_forwards_kernel<<<(m.n_fwd + 127) / 128, 128, 0, s>>>(m);
     if (m.n_swap > 0) {

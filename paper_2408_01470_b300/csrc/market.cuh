@@ -103,8 +103,9 @@ struct DevMarket {
                                    //   each row zero-padded to a multiple of 4 pairs
   const float* swap_C32;           //   the same in FP32
   int n_chunk;                     // chunks of <= 16 pairs of the swaps' coefficient rows
-  const int2* chunk;               // [n_chunk] {swap, k | (nk << 16)}: chunk k of the swap's nk takes
-                                   //   the 4-pair quads k, k + nk, ... (ordered by group, then swap)
+  const int4* chunk;               // [n_chunk] {coefficient row offset, group, k | (nk << 16), quads}:
+                                   //   chunk k of its swap's nk takes the swap's 4-pair quads
+                                   //   k, k + nk, ... < quads (ordered by group, then swap)
   const int* grp_chunk0;           // [n_grp + 1] first chunk of each group
   const int* swap_chunk0;          // [n_swap + 1] first chunk of each swap
   int qf_gb;                       // expiry groups whose B matrices are built per barrier

@@ -454,11 +454,10 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       // neighbouring quads; one 16-byte coefficient load and three 16-byte B loads per quad
       const int c0 = m.grp_chunk0[g0];
       for (int c = c0 + tid; c < m.grp_chunk0[g1]; c += nth) {
-        const int2 ck = m.chunk[c];
-        const int s = ck.x, k = ck.y & 0xffff, nk = ck.y >> 16, L = m.swap_L[s];
-        const int nq = (L * (L + 1) / 2 + 3) >> 2;
-        const R* B = Bbuf + (m.swap_grp[s] - g0) * 3 * npm;
-        const Q4<R>* Cq = (const Q4<R>*)(Call + m.swap_coff[s]);
+        const int4 ck = m.chunk[c];   // one load: no dependent per-swap lookups before the rows
+        const int k = ck.z & 0xffff, nk = ck.z >> 16, nq = ck.w;
+        const R* B = Bbuf + (ck.y - g0) * 3 * npm;
+        const Q4<R>* Cq = (const Q4<R>*)(Call + ck.x);
         const Q4<R>* B1 = (const Q4<R>*)B;
         const Q4<R>* B2 = (const Q4<R>*)(B + npm);
         const Q4<R>* B3 = (const Q4<R>*)(B + 2 * npm);
