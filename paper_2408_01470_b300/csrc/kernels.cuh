@@ -699,9 +699,13 @@ __device__ bool stage_to_smem3(void* d0, const void* g0, uint32_t b0, void* d1, 
 
 template <class R>
 __device__ __forceinline__ bool stage_market_cta(const CtaSmemS<R>& cs, const DevMarket& m) {
-  return stage_to_smem3(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.swp, swp_block<R>(m),
-                        instr_block_bytes<R>(m.n_swp_pad), cs.quad, quad_block<R>(m), (uint32_t)sizeof(QuadTab<R>),
-                        cs.mbar, m.err);
+  if (!stage_to_smem3(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.swp, swp_block<R>(m),
+                      instr_block_bytes<R>(m.n_swp_pad), cs.quad, quad_block<R>(m), (uint32_t)sizeof(QuadTab<R>),
+                      cs.mbar, m.err))
+    return false;
+  stage_group_tables<R>(cta_scratch<R>(cs.scratch, m), m);
+  __syncthreads();
+  return true;
 }
 
 template <class R, int FORMULA, bool TC>
@@ -756,7 +760,7 @@ __global__ void __launch_bounds__(256, 2) sa_start_cta_kernel(DevMarket m, SASta
 // and the batch).  The chain's end state is written; the CTA that finishes the market's last chain
 // (counted on st.counter, n_chains arrivals) takes the minimum over the market's chains and sets
 // the next start point and the level trace.
-template <class R, int FORMULA, bool TC = false>
+template <class R, int FORMULA, bool TC = false, bool GT = false>
 __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAParams& sp, int c, int level,
                                 const CtaSmemS<R>& cs, const InstrView<R>& capB, const InstrView<R>& swpB,
                                 const CtaScratch<R>& sc, unsigned long long* s_wacc, bool* s_last,
@@ -802,7 +806,7 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
       if (lane == 0) *s_wacc = wacc;
     }
     __syncthreads();
-    const O fy = cta_objective<R, FORMULA, TC>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr, tc);
+    const O fy = cta_objective<R, FORMULA, TC, GT>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr, tc);
     const bool acc = metropolis(fy, f, (uint64_t)*s_wacc, T, invT);
     if (acc) {
       x = y;
@@ -920,7 +924,7 @@ __global__ void __launch_bounds__(256, 2) sa_level_batch_kernel(BatchArgs ba, in
     const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
     const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
     CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
-    cta_chain_level<R, FORMULA>(m, sm_st, sm_sp, c, level, cs, capB, swpB, sc, &s_wacc, &s_last);
+    cta_chain_level<R, FORMULA, false, true>(m, sm_st, sm_sp, c, level, cs, capB, swpB, sc, &s_wacc, &s_last);
   }
 }
 

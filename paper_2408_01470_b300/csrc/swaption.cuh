@@ -37,9 +37,18 @@ template <class R> struct CtaScratch {
   R* Bg;            // [3 x round_up(Lg (Lg + 1) / 2, 4)] of the current expiry group
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
   R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
-  Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}
+  Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}, then the group table
+                    //   (group_table below)
   R* Pc;            // [3 x max_batch_chunks] partial sums of one batch's chunks of pairs
 };
+
+// [n_grp + 1] per group {first chunk, first swap, window, expiry panel}, right after RCs: copied
+// once per market, so no global loads precede the phase-5 loops.  Its address is derived from RCs
+// rather than held in the scratch record (one live pointer fewer across the chain loop).
+template <class R>
+__device__ __forceinline__ int4* group_table(const CtaScratch<R>& sc, const DevMarket& m) {
+  return (int4*)(sc.RCs + m.n_swap);
+}
 
 __host__ __device__ inline int cta_y_stride() { return 84; }   // 16-byte rows, conflict-free 4-vector loads
 // Row pitch of the prefix tables: at least NA + 1, and even, so that the pairs of a window column
@@ -58,7 +67,7 @@ __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + round_up(m.NA * cta_y_stride(), 4) +
                       round_up(4 * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND +
                       3 * round_up(Lg * (Lg + 1) / 2, 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
-                      (m.qf_pc_off >= 0 ? 0 : round_up(3 * m.max_batch_chunks, 4)),
+                      4 * round_up(m.n_grp + 1, 4) + (m.qf_pc_off >= 0 ? 0 : round_up(3 * m.max_batch_chunks, 4)),
                   4);
 }
 
@@ -80,8 +89,17 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
   s.F4s = (Q4<R>*)p; p += 4 * m.n_swap;
   s.A3s = p; p += round_up(m.n_swap, 4);
   s.RCs = (Q4<R>*)p; p += 4 * m.n_swap;
+  p += 4 * round_up(m.n_grp + 1, 4);   // the group table
   s.Pc = p;
   return s;
+}
+
+// The group tables of phase 5 into the chain scratch (all threads; the caller synchronises).
+template <class R>
+__device__ __forceinline__ void stage_group_tables(const CtaScratch<R>& sc, const DevMarket& m) {
+  int4* gt = group_table<R>(sc, m);
+  for (int i = threadIdx.x; i <= m.n_grp; i += blockDim.x)
+    gt[i] = make_int4(m.grp_chunk0[i], m.grp_swap0[i], i < m.n_grp ? m.grp_L[i] : 0, i < m.n_grp ? m.grp_nE[i] : 0);
 }
 
 template <class R> __device__ __forceinline__ const R* swap_W_of(const DevMarket& m);
@@ -178,7 +196,9 @@ __device__ __forceinline__ R price_one_caplet(const InstrView<R>& B, int k, cons
 // Objective of the point in cs.xs (every thread of the CTA calls; all return the same value).
 // `red` is shared scratch of 32 objective values.
 // TC: the pair Grams of phase 3 on the tensor cores (tcgen05_gram.cuh; FP32 pricing only).
-template <class R, int FORMULA, bool TC = false>
+// GT: phase 5 takes its group bounds from the staged group table (the batch kernel, whose market
+// record itself lives in shared memory) rather than from the market's global arrays.
+template <class R, int FORMULA, bool TC = false, bool GT = false>
 __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrView<R>& capB, const InstrView<R>& swpB,
                                               const QuadTab<R>& qt, const CtaScratch<R>& cs,
                                               typename ObjOf<R>::T* red, double* vols, TcState* tc = nullptr) {
@@ -424,7 +444,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     for (int g0 = 0; g0 < m.n_grp; g0 += GB) {
       const int g1 = min(m.n_grp, g0 + GB);
       for (int g = g0; g < g1; ++g) {
-        const int Lg = m.grp_L[g], nE = m.grp_nE[g];
+        const int Lg = m.grp_L[g], nE = m.grp_nE[g];   // uniform loads
         const int* gp = m.grp_pair + g * m.max_npk;
         R* B = Bbuf + (g - g0) * 3 * npm;
         const int npk = Lg * (Lg + 1) / 2;
@@ -452,8 +472,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       // chunks of <= 16 pairs, one thread each (partials per chunk, summed per swap below): a chunk
       // takes up to 4 quads of 4 pairs, interleaved (stride nk) so that neighbouring threads read
       // neighbouring quads; one 16-byte coefficient load and three 16-byte B loads per quad
-      const int c0 = m.grp_chunk0[g0];
-      for (int c = c0 + tid; c < m.grp_chunk0[g1]; c += nth) {
+      const int c0 = GT ? group_table<R>(cs, m)[g0].x : m.grp_chunk0[g0];
+      const int c1 = GT ? group_table<R>(cs, m)[g1].x : m.grp_chunk0[g1];
+      for (int c = c0 + tid; c < c1; c += nth) {
         const int4 ck = m.chunk[c];   // one load: no dependent per-swap lookups before the rows
         const int k = ck.z & 0xffff, nk = ck.z >> 16, nq = ck.w;
         const R* B = Bbuf + (ck.y - g0) * 3 * npm;
@@ -482,7 +503,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       __syncthreads();
       // per swap of the batch: its chunks added in order, then the swap-rate SABR factors (the
       // next batch overwrites Pc only after its own B-build barrier)
-      for (int s = m.grp_swap0[g0] + tid; s < m.grp_swap0[g1]; s += nth) {
+      const int s0 = GT ? group_table<R>(cs, m)[g0].y : m.grp_swap0[g0];
+      const int s1 = GT ? group_table<R>(cs, m)[g1].y : m.grp_swap0[g1];
+      for (int s = s0 + tid; s < s1; s += nth) {
         const int nb = m.max_batch_chunks;
         R v1 = 0, v2 = 0, v3 = 0;
         for (int c = m.swap_chunk0[s]; c < m.swap_chunk0[s + 1]; ++c) {
@@ -490,7 +513,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
           v2 += Pc[nb + c - c0];
           v3 += Pc[2 * nb + c - c0];
         }
-        const R TE = (R)m.T[m.swap_a[s]];
+        const R TE = (R)m.swap_TE[s];
         const R al = M::sqrt_(v1 / TE);
         const R nu = M::sqrt_(R(2) * v2) / (al * TE);
         R rho = v3 / v1;
