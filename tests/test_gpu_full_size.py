@@ -1,0 +1,106 @@
+"""Parity at the benchmark's full sizes, in the launch configurations bench.py times.
+
+* FP64 caplet term structure at the full chain count and level length (4096 chains x 100 steps,
+  4-chain CTAs): every accept bit of two levels against the oracle, so the level-end reduction
+  over all 4096 chains is covered.
+* FP32 caplet search at the full schedule (4096 x 200 x 100, one 28-chain CTA per SM): the
+  evaluation count, the oracle's FP64 objective at the returned point, the target RMSE.
+* FP32 joint caplet + swaption market at its chain count (16384, one CTA per chain), one level.
+* FP32 batch of all 256 markets (4096 chains each, 50 steps), one level: every market's returned
+  point checked for the box and the start, every 8th market's objective by the oracle.
+FP32 searches are not bit-comparable with the oracle; their outputs are checked where the oracle
+can compute them one by one.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_01470_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+
+def _rms_close(f32, f64, n):
+    """FP32 objective against the FP64 oracle at the same point, in RMS-equivalent vol points
+    (100 sqrt(f / n)): the bar of the objective tests, 1e-4 vol-pt plus 1.5e-5 of the RMS (the
+    swaption windows' prefix-sum cancellation in FP32)."""
+    a, b = 100.0 * np.sqrt(f32 / n), 100.0 * np.sqrt(f64 / n)
+    return abs(a - b) <= 1e-4 + 1.5e-5 * b
+
+
+def _quoted(sk):
+    import paper_2408_01470_b300 as lib
+    om, vols = oracle.quoted_market(sk)
+    return om, lib.Market(sk, vols)
+
+
+def test_fp64_caplet_search_full_chain_count_two_levels(gpu_lib):
+    sk = synth.caplet_term_structure()
+    om, gm = _quoted(sk)
+    C, L, N = sk.n_chains, 2, sk.steps
+    assert (C, N) == (4096, 100)
+    r_g = gm.anneal(C, L, N, sk.cooling, seed=240801470, prec="fp64", record_accepts=True)
+    r_o = om.anneal(C, L, N, sk.cooling, seed=240801470, want_bits=True, n_threads=os.cpu_count() or 1)
+    assert r_g["n_evals"] == r_o["n_evals"] == C * (L * N + 1)
+    diff = np.argwhere(r_g["bits"] != r_o["bits"])
+    assert diff.size == 0, f"first differing (chain, level, step): {diff[:1]}"
+    assert np.allclose(r_g["trace_f"][0], r_o["trace_f"], rtol=1e-11, atol=0)
+    assert np.allclose(r_g["x_best"][0], r_o["x_best"], rtol=1e-12, atol=1e-15)
+    assert r_g["f_best"][0] == pytest.approx(r_o["f_best"], rel=1e-11)
+
+
+def test_fp32_caplet_search_full_schedule(gpu_lib):
+    sk = synth.caplet_term_structure()
+    om, gm = _quoted(sk)
+    C, L, N = sk.n_chains, sk.n_levels, sk.steps
+    assert (C, L, N) == (4096, 200, 100)
+    r = gm.anneal(C, L, N, sk.cooling, seed=240801470, prec="fp32")
+    assert r["n_evals"] == C * (L * N + 1) == 81_924_096
+    x = r["x_best"][0]
+    assert np.all(x >= sk.lo) and np.all(x <= sk.hi)
+    f64 = om.objective(x)
+    assert _rms_close(r["f_best"][0], f64, sk.n_instr), (r["f_best"][0], f64)
+    assert r["rmse_volpt"][0] == pytest.approx(om.rmse_volpt(x), rel=1e-6)
+    assert r["rmse_volpt"][0] <= 0.05   # the calibration target in vol points
+    assert r["trace_f"][0][-1] <= r["trace_f"][0][0]
+
+
+def test_fp32_joint_market_full_chain_count(gpu_lib):
+    sk = synth.joint_caplet_swaption()
+    om, gm = _quoted(sk)
+    assert sk.n_chains == 16384 and sk.n_instr == 1000
+    r = gm.anneal(sk.n_chains, 1, sk.steps, sk.cooling, seed=7, prec="fp32")
+    assert r["n_evals"] == sk.n_chains * (sk.steps + 1)
+    x = r["x_best"][0]
+    f64 = om.objective(x)
+    assert _rms_close(r["f_best"][0], f64, sk.n_instr), (r["f_best"][0], f64)
+    assert f64 < om.objective(sk.box_centre())
+
+
+def test_fp32_batch_all_markets_one_level(gpu_lib):
+    # all 256 markets at 4096 chains; seeded synthetic quotes (no model evaluation needed to make
+    # them), every market's point checked for the box and for improving on the start, every 8th
+    # market's objective recomputed by the oracle
+    import paper_2408_01470_b300 as lib
+    sks = [synth.batch_market(j) for j in range(256)]
+    rng = np.random.default_rng(240801470)
+    vols = [np.clip(0.2 + 0.03 * rng.standard_normal(sk.n_instr), 0.05, 0.6) for sk in sks]
+    gm = lib.Market(sks, vols)
+    C, N = sks[0].n_chains, sks[0].steps
+    assert (C, N) == (4096, 50)
+    r = gm.anneal(C, 1, N, sks[0].cooling, seed=11, prec="fp32")
+    assert r["n_evals"] == C * (N + 1)
+    X0 = np.stack([sk.box_centre() for sk in sks])
+    for j, sk in enumerate(sks):
+        x = r["x_best"][j]
+        assert np.all(x >= sk.lo) and np.all(x <= sk.hi), j
+        assert np.isfinite(r["f_best"][j]), j
+        f0 = gm.objective(X0[j][None, :], "fp32", market=j).cpu().numpy()[0]
+        assert r["f_best"][j] <= f0, j
+        if j % 8 == 0:
+            om = oracle.Market(sk, vols[j])
+            f64 = om.objective(x)
+            assert _rms_close(r["f_best"][j], f64, sk.n_instr), (j, r["f_best"][j], f64)
