@@ -51,6 +51,12 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// log2 x on the MUFU (PTX lg2.approx; flushes subnormals).
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 // e^x = 2^(x log2 e); the rounding of x log2 e adds |x| 2^-24 to the relative error.
 __device__ __forceinline__ float exp_approx(float x) { return ex2_approx(x * 1.44269504088896341f); }
 
@@ -192,24 +198,22 @@ __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
   return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
 }
 
-// log1p_pos on a pair.  The bit-level reduction runs on 32-bit scalars: with nvcc 13.0 for
-// sm_103a an arithmetic right shift of the bits of the low half of a packed (.f32x2) result came
-// out unshifted, so u is formed by scalar adds and the shifts are logical (u >= 1).
+// log1p on a pair of non-negative arguments.  y < 1/2: the atanh series 2 s (1 + s^2/3 + ... + s^8/9)
+// in s = y / (2 + y) (|s| <= 1/5, truncation below 2e-9 relative); y >= 1/2: log2(1 + y) ln 2 on
+// the MUFU, where 1 + y carries no cancellation (relative error a few 1e-7).  Both are formed and
+// one is selected, so the pair needs no bit-level argument reduction.  An infinite or NaN argument
+// takes the second form and comes back infinite or NaN.
 __device__ __forceinline__ float2 log1p_pos2(float2 y) {
-  const unsigned bx = __float_as_uint(1.0f + y.x), by = __float_as_uint(1.0f + y.y);
-  const unsigned kx = (bx - 0x3f400000u) >> 23, ky = (by - 0x3f400000u) >> 23;
-  const bool sx = y.x < 0.5f, sy = y.y < 0.5f;
-  const float2 m1 = sub2(make_float2(__uint_as_float(bx - (kx << 23)), __uint_as_float(by - (ky << 23))), bc2(1.0f));
-  const float2 f = sel2(sx, sy, y, m1);
-  const float2 kf = make_float2(sx ? 0.0f : (float)kx, sy ? 0.0f : (float)ky);
-  const float2 s = mul2(f, rcp2(add2(bc2(2.0f), f)));
+  const float2 s = mul2(y, rcp2(add2(bc2(2.0f), y)));
   const float2 s2 = mul2(s, s);
   float2 p = fma2(s2, bc2(1.0f / 9.0f), bc2(1.0f / 7.0f));
   p = fma2(s2, p, bc2(1.0f / 5.0f));
   p = fma2(s2, p, bc2(1.0f / 3.0f));
   p = fma2(s2, p, bc2(1.0f));
-  const float2 r = fma2(kf, bc2(0.693145751953125f), fma2(kf, bc2(1.42860682030941723212e-6f), mul2(add2(s, s), p)));
-  return add2(r, sub2(y, y));
+  const float2 ser = mul2(add2(s, s), p);
+  const float2 u = add2(bc2(1.0f), y);
+  const float2 big = mul2(make_float2(lg2_approx(u.x), lg2_approx(u.y)), bc2(0.693147180559945309f));
+  return sel2(y.x < 0.5f, y.y < 0.5f, ser, big);
 }
 
 // ncdf<float> on a pair.
