@@ -587,7 +587,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   }
   const int bad = __syncthreads_or(!ok);
   if (vols) return obj_inf(O());
-  const O wsum = warp_sum_lanes(part);
+  O wsum;
+  if constexpr (std::is_same<R, float>::value) wsum = warp_sum_lanes_f32(part);
+  else wsum = warp_sum_lanes(part);
   if (lane == 0) red[warp] = wsum;
   __syncthreads();
   O f = red[0];
