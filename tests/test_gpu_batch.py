@@ -41,3 +41,16 @@ def test_batch_fp32_runs_every_market(gpu_lib):
         assert np.isfinite(r["f_best"][j])
         assert r["f_best"][j] <= f0
         assert om.objective(r["x_best"][j]) == pytest.approx(r["f_best"][j], rel=1e-3)
+
+
+def test_batch_fp32_search_with_polish(gpu_lib):
+    # the mixed-precision form on a batch: FP32 search, then the FP64 Levenberg-Marquardt polish of
+    # each market's 8 best chains; every market's result is no worse and is the oracle's objective
+    # at the returned point
+    sks, oms, gm = _batch([0, 3, 4, 7])
+    r0 = gm.anneal(64, 4, 8, 0.9, seed=21, prec="fp32")
+    r1 = gm.anneal(64, 4, 8, 0.9, seed=21, prec="fp32", lm_top_k=8, lm_max_iter=10)
+    assert r1["lm_seconds"] > 0.0
+    for j, om in enumerate(oms):
+        assert r1["f_best"][j] <= r0["f_best"][j], j
+        assert om.objective(r1["x_best"][j]) == pytest.approx(r1["f_best"][j], rel=1e-9), j
