@@ -60,31 +60,21 @@ __device__ __forceinline__ float lg2_approx(float x) {
 // e^x = 2^(x log2 e); the rounding of x log2 e adds |x| 2^-24 to the relative error.
 __device__ __forceinline__ float exp_approx(float x) { return ex2_approx(x * 1.44269504088896341f); }
 
-// log1p(y) for y >= 0 in FP32, by argument reduction and the atanh series (the textbook method,
-// e.g. J.-M. Muller, Elementary Functions, ch. 11): with u = 1 + y = 2^k m, m in [0.75, 1.5),
-// f = m - 1 (f = y, k = 0 when y < 0.5, so no rounding of u enters there),
-//   log1p(y) = k ln 2 + 2 atanh(s),  s = f / (2 + f),  |s| <= 0.2,
-//   2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9) + O(s^11),
-// the truncation below 1e-8 relative.  For y >= 0.5 the rounding of u costs at most
-// 2^-24 / log(1.5) = 1.5e-7 relative; with the FP32 roundings of the steps the result stays
-// within 2.3e-7 relative of log1p(y) (checked in FP32 arithmetic over y in [1e-8, 1e6]).
+// log1p of a non-negative argument (the argument of x(z)).  y < 1/2: the atanh series
+// 2 s (1 + s^2/3 + ... + s^8/9) in s = y / (2 + y) (|s| <= 1/5, truncation below 1e-8 relative);
+// y >= 1/2: log2(1 + y) ln 2 on the MUFU (PTX lg2.approx), where 1 + y carries no cancellation
+// (a few 1e-7 relative).  An infinite or NaN argument takes the second form and stays so.
 __device__ __forceinline__ float log1p_pos(float y) {
-  const float u = 1.0f + y;
-  const unsigned bits = __float_as_uint(u);
-  const unsigned k = (bits - 0x3f400000u) >> 23;        // 2^k * 0.75 <= u < 2^k * 1.5 (u >= 1)
-  const bool small = y < 0.5f;
-  const float f = small ? y : __uint_as_float(bits - (k << 23)) - 1.0f;
-  const float kf = small ? 0.0f : (float)k;
-  const float s = f * rcp_approx(2.0f + f);
-  const float s2 = s * s;
-  float p = fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f);
-  p = fmaf(s2, p, 1.0f / 5.0f);
-  p = fmaf(s2, p, 1.0f / 3.0f);
-  p = fmaf(s2, p, 1.0f);
-  const float ln2_hi = 0.693145751953125f, ln2_lo = 1.42860682030941723212e-6f;
-  // (y - y) is 0 for finite y and NaN otherwise: an infinite or NaN argument (an overflowed z)
-  // must not come back finite
-  return fmaf(kf, ln2_hi, fmaf(kf, ln2_lo, 2.0f * s * p)) + (y - y);
+  if (y < 0.5f) {
+    const float s = y * rcp_approx(2.0f + y);
+    const float s2 = s * s;
+    float p = fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f);
+    p = fmaf(s2, p, 1.0f / 5.0f);
+    p = fmaf(s2, p, 1.0f / 3.0f);
+    p = fmaf(s2, p, 1.0f);
+    return 2.0f * s * p;
+  }
+  return lg2_approx(1.0f + y) * 0.693147180559945309f;
 }
 
 // ------------------------------------------------------------------ Philox4x64-10
@@ -159,7 +149,7 @@ __device__ __forceinline__ R sabr_paper(R alpha, R rho, R nu, R l, R fo, R omb) 
 // Phi(x) = erfc(-x / sqrt 2) / 2.  FP64: the library erfc.  FP32: erfc(y) for y = |x|/sqrt 2 in
 // the Chebyshev-exponent form t exp(-y^2 + P(t)), t = 1 / (1 + y/2), of Press et al. (Numerical
 // Recipes, 2nd ed., Section 6.2), with our own coefficients fitted against 40-digit values
-// (csrc/gen_erfc_fit.py; relative error of erfc <= 5.4e-8 on [0, 12] before FP32 rounding).
+// (csrc/gen_erfc_fit.py; relative error of erfc <= 5.5e-8 on [0, 12] before FP32 rounding).
 template <class R> __device__ __forceinline__ R ncdf(R x);
 template <> __device__ __forceinline__ double ncdf<double>(double x) {
   return 0.5 * erfc(-x * 0.70710678118654752440);
@@ -199,7 +189,7 @@ __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b) {
 }
 
 // log1p on a pair of non-negative arguments.  y < 1/2: the atanh series 2 s (1 + s^2/3 + ... + s^8/9)
-// in s = y / (2 + y) (|s| <= 1/5, truncation below 2e-9 relative); y >= 1/2: log2(1 + y) ln 2 on
+// in s = y / (2 + y) (|s| <= 1/5, truncation below 1e-8 relative); y >= 1/2: log2(1 + y) ln 2 on
 // the MUFU, where 1 + y carries no cancellation (relative error a few 1e-7).  Both are formed and
 // one is selected, so the pair needs no bit-level argument reduction.  An infinite or NaN argument
 // takes the second form and comes back infinite or NaN.
