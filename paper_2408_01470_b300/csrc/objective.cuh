@@ -533,17 +533,6 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// The per-lane FP32 partials summed across the warp in FP64 (five shuffled DADDs), returned as a
-// float-float pair: cheaper in issue slots than the float-float tree and at least as accurate.
-__device__ __forceinline__ FF warp_sum_lanes(float p) {
-  double d = (double)p;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-  FF r;
-  r.hi = (float)d;
-  r.lo = (float)(d - (double)r.hi);
-  return r;
-}
 __device__ __forceinline__ double warp_sum_lanes(double p) { return warp_sum(p); }
 
 // The per-lane FP32 partials of one warp summed by an FP32 butterfly (the same value in every lane:
