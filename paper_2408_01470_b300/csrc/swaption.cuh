@@ -31,6 +31,7 @@ template <class R> struct CtaScratch {
   Q2<R>* Ep;        // [NAc] {e^{-c A D}, e^{-gamma_h A D}}
   Q4<R>* Tq;        // [8]
   Q4<R>* T2;        // [8 x 9]
+  Q4<R>* Sq;        // [8 x 2] per outer node q the inner-rule sums {Saa, Sab, Sbb, Sac}, {Sbc, Scc, 0, 0}
   R* Y;             // [NA x 81]
   R* PQ;            // [4 x ND x (NA + 1)]: PG, PA, SH, PGS along each diagonal
   Q4<R>* crq;       // [ND]: {rho_e, rho_e theta_e, phi_e, 0} per diagonal e
@@ -50,7 +51,10 @@ __device__ __forceinline__ int4* group_table(const CtaScratch<R>& sc, const DevM
   return (int4*)(sc.RCs + m.n_swap);
 }
 
-__host__ __device__ inline int cta_y_stride() { return 84; }   // 16-byte rows, conflict-free 4-vector loads
+// Y row pitch: 16-byte rows, conflict-free 4-vector loads.  The tensor-core form fills all 80 values
+// of a row (g, h and the 64 inner-node products); the ALU form only the first 16 (g and h), the rest
+// of the region serving phase 5's buffers.
+__host__ __device__ inline int cta_y_stride() { return 84; }
 // Row pitch of the prefix tables: at least NA + 1, and even, so that the pairs of a window column
 // (address stride 1 - pitch along a column) fall on distinct banks.
 __host__ __device__ inline int cta_pq_len(int NA) { return (NA + 2) & ~1; }
@@ -64,7 +68,7 @@ constexpr int kMaxBatchChunks = 512;
 __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int NAc = round_up(m.NA, 4);
   const int Lg = m.max_gwin;
-  return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + round_up(m.NA * cta_y_stride(), 4) +
+  return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + 4 * 16 + round_up(m.NA * cta_y_stride(), 4) +
                       round_up(4 * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND +
                       3 * round_up(Lg * (Lg + 1) / 2, 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
                       4 * round_up(m.n_grp + 1, 4) + (m.qf_pc_off >= 0 ? 0 : round_up(3 * m.max_batch_chunks, 4)),
@@ -82,6 +86,7 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
   s.Ep = (Q2<R>*)p; p += 2 * NAc;
   s.Tq = (Q4<R>*)p; p += 32;
   s.T2 = (Q4<R>*)p; p += 4 * 72;
+  s.Sq = (Q4<R>*)p; p += 4 * 16;
   s.Y = p; p += round_up(m.NA * cta_y_stride(), 4);
   s.PQ = p; p += round_up(4 * m.ND * cta_pq_len(m.NA), 4);
   s.crq = (Q4<R>*)p; p += 4 * m.ND;
@@ -264,8 +269,24 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   // phases 2 and 3 (ALU form): the warps 1.. only
   const int ptid = TC ? tid : tid - 32, pnth = TC ? nth : nth - 32;
 
-  // ---- phase 2: Y rows, one thread per (panel A, outer node q): g and h at the node once, then
-  //      the 8 inner-node products
+  // ---- phase 2: Y rows, one thread per (panel A, outer node q): g and h at the node once; the
+  //      tensor-core form also the 8 inner-node products.  The ALU form keeps the inner rule in
+  //      closed form instead: with hin(A, q, r) = alpha_A a_qr + beta_A b_qr + c_qr (alpha_A =
+  //      E_h(A) a'(A), beta_A = E_h(A), {a, b, c}_qr the T2 table), the pair sum over r of
+  //      hin(A) hin(B) is a bilinear form in (alpha, beta, 1) with the six per-node sums
+  //      S_xy(q) = sum_r x_qr y_qr, formed here once per evaluation.
+  if (!TC && warp != 0 && ptid < 6 * kQ) {
+    const int q = ptid / 6, kd = ptid - 6 * q;   // kd: aa, ab, bb, ac, bc, cc
+    R acc = 0;
+#pragma unroll
+    for (int r = 0; r < kQ; ++r) {
+      const Q4<R> t = cs.T2[q * 9 + r];
+      const R x = (kd == 0 || kd == 1 || kd == 3) ? t.a : (kd == 5 ? t.c : t.b);
+      const R y = kd == 0 ? t.a : ((kd == 1 || kd == 2) ? t.b : t.c);
+      acc += x * y;
+    }
+    ((R*)cs.Sq)[q * 8 + kd] = acc;
+  }
   if (TC || warp != 0)
   for (int it = ptid; it < NA * kQ; it += pnth) {
     const int A = it >> 3, q = it & 7;
@@ -277,26 +298,18 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     const R g = E.a * ((a + b * base) * t.a + t.b) + d;
     const R vg = swq * g;
     const R vh = swq * (E.b * (ahp * t.c + t.d) + dh);
-    R v[kQ];
-#pragma unroll
-    for (int r = 0; r < kQ; ++r) {
-      const Q4<R> t2 = cs.T2[q * 9 + r];
-      v[r] = vg * (E.b * (ahp * t2.a + t2.b) + t2.c);
-    }
     if (TC) {
       tc_put(*tc, A, q, (float)vg);
       tc_put(*tc, A, 8 + q, (float)vh);
 #pragma unroll
-      for (int r = 0; r < kQ; ++r) tc_put(*tc, A, 16 + q * kQ + r, (float)v[r]);
+      for (int r = 0; r < kQ; ++r) {
+        const Q4<R> t2 = cs.T2[q * 9 + r];
+        tc_put(*tc, A, 16 + q * kQ + r, (float)(vg * (E.b * (ahp * t2.a + t2.b) + t2.c)));
+      }
     } else {
       R* y = cs.Y + A * YS;
       y[q] = vg;
       y[8 + q] = vh;
-      Q4<R> w0, w1;
-      w0.a = v[0]; w0.b = v[1]; w0.c = v[2]; w0.d = v[3];
-      w1.a = v[4]; w1.b = v[5]; w1.c = v[6]; w1.d = v[7];
-      *(Q4<R>*)(y + 16 + q * kQ) = w0;
-      *(Q4<R>*)(y + 20 + q * kQ) = w1;
     }
   }
   if (TC) __syncthreads();
@@ -351,29 +364,48 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       R G[4], H[4], Ad[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) { G[u] = 0; H[u] = 0; Ad[u] = 0; }
+      // (alpha, beta) of panel A and of the 4 partner panels: the pair coefficients of the form
+      const R bA = cs.Ep[A].b, aA = bA * (ah + bh * (D * (R)A));
+      R cp[4], cq[4], cr[4], cu[4], cv[4];
 #pragma unroll
-      for (int k = 0; k < 16; k += 4) {
+      for (int u = 0; u < 4; ++u) {
+        const int B = in[u] ? A + e0 + u : A;
+        const R bB = cs.Ep[B].b, aB = bB * (ah + bh * (D * (R)B));
+        cp[u] = aA * aB;
+        cq[u] = aA * bB + bA * aB;
+        cr[u] = bA * bB;
+        cu[u] = aA + aB;
+        cv[u] = bA + bB;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; k += 4) {
         const Q4<R> x = *(const Q4<R>*)(ya + k);
+        Q4<R> y[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const Q4<R> y = *(const Q4<R>*)(yb[u] + k);
-          R& acc = k < 8 ? G[u] : H[u];
-          acc += x.a * y.a;
-          acc += x.b * y.b;
-          acc += x.c * y.c;
-          acc += x.d * y.d;
+        for (int u = 0; u < 4; ++u) y[u] = *(const Q4<R>*)(yb[u] + k);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const Q4<R> s0 = cs.Sq[2 * (k + j)], s1 = cs.Sq[2 * (k + j) + 1];
+          const R xa = j == 0 ? x.a : (j == 1 ? x.b : (j == 2 ? x.c : x.d));
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const R ya_ = j == 0 ? y[u].a : (j == 1 ? y[u].b : (j == 2 ? y[u].c : y[u].d));
+            G[u] += xa * ya_;
+            const R form = cp[u] * s0.a + cq[u] * s0.b + cr[u] * s0.c + cu[u] * s0.d + cv[u] * s1.a + s1.b;
+            Ad[u] += (xa * ya_) * form;
+          }
         }
       }
-#pragma unroll 4
-      for (int k = 16; k < 80; k += 4) {
+#pragma unroll
+      for (int k = 8; k < 16; k += 4) {
         const Q4<R> x = *(const Q4<R>*)(ya + k);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const Q4<R> y = *(const Q4<R>*)(yb[u] + k);
-          Ad[u] += x.a * y.a;
-          Ad[u] += x.b * y.b;
-          Ad[u] += x.c * y.c;
-          Ad[u] += x.d * y.d;
+          H[u] += x.a * y.a;
+          H[u] += x.b * y.b;
+          H[u] += x.c * y.c;
+          H[u] += x.d * y.d;
         }
       }
 #pragma unroll
