@@ -104,3 +104,19 @@ def test_fp32_batch_all_markets_one_level(gpu_lib):
             om = oracle.Market(sk, vols[j])
             f64 = om.objective(x)
             assert _rms_close(r["f_best"][j], f64, sk.n_instr), (j, r["f_best"][j], f64)
+
+
+def test_caplet_search_at_the_chain_limit(gpu_lib):
+    # 16384 chains (the library's limit): FP32 runs 585 CTAs of 28 chains, several waves, and the
+    # level-end argmin is taken by the last CTA over all of them; FP64 checked bit for bit
+    sk = synth.caplet_term_structure()
+    om, gm = _quoted(sk)
+    C, L, N = 16384, 2, 5
+    r64 = gm.anneal(C, L, N, sk.cooling, seed=99, prec="fp64", record_accepts=True)
+    ro = om.anneal(C, L, N, sk.cooling, seed=99, want_bits=True, n_threads=os.cpu_count() or 1)
+    assert np.array_equal(r64["bits"], ro["bits"])
+    assert np.allclose(r64["trace_f"][0], ro["trace_f"], rtol=1e-11, atol=0)
+    assert np.allclose(r64["x_best"][0], ro["x_best"], rtol=1e-12, atol=1e-15)
+    r32 = gm.anneal(C, L, N, sk.cooling, seed=99, prec="fp32")
+    assert r32["n_evals"] == C * (L * N + 1)
+    assert _rms_close(r32["f_best"][0], om.objective(r32["x_best"][0]), sk.n_instr)
