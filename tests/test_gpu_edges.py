@@ -1,0 +1,69 @@
+"""Edge cases through the C-ABI: empty point sets, infeasible points, invalid options, one chain."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_01470_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _markets(sk):
+    import paper_2408_01470_b300 as lib
+    om, vols = oracle.quoted_market(sk)
+    return om, lib.Market(sk, vols)
+
+
+def test_empty_point_sets(gpu_lib):
+    sk = synth.caplet_term_structure(n_fwd=7, n_strikes=5)
+    om, gm = _markets(sk)
+    X = np.zeros((0, sk.n_param))
+    for prec in ("fp64", "fp32"):
+        assert gm.objective(X, prec).numel() == 0
+        assert gm.model_vols(X, prec).shape[0] == 0
+    f, G = gm.objective_grad(X, "fp64")
+    assert f.numel() == 0 and G.shape[0] == 0
+    Xp, f, r = gm.lm_polish(X, max_iter=3)
+    assert Xp.shape[0] == 0 and f.numel() == 0
+
+
+def test_infeasible_points_are_infinite_like_the_oracle(gpu_lib):
+    # alpha = 0, alpha < 0, rho > 1 (a negative radicand in x(z)), a Hagan correction that turns
+    # the vol negative, a NaN parameter; the last point is feasible
+    sk = synth.smile_2y()
+    om, gm = _markets(sk)
+    X = np.array([[0.03, 1.5, 2.0], [0.0, -0.3, 0.4], [-0.01, 0.2, 0.4], [0.03, 0.999999, 50.0],
+                  [math.nan, 0.1, 0.2], [0.03, -0.3, 0.4]])
+    fo = np.array([om.objective(x) for x in X])
+    assert np.all(np.isinf(fo[:-1])) and np.isfinite(fo[-1])
+    f64 = gm.objective(X, "fp64").cpu().numpy()
+    f32 = gm.objective(X, "fp32").cpu().numpy()
+    assert np.all(np.isposinf(f64[:-1])) and np.all(np.isposinf(f32[:-1]))
+    assert f64[-1] == pytest.approx(fo[-1], rel=1e-12)
+    assert f32[-1] == pytest.approx(fo[-1], rel=1e-3)
+
+
+def test_anneal_rejects_invalid_options(gpu_lib):
+    import paper_2408_01470_b300 as lib
+    sk = synth.smile_2y()
+    om, gm = _markets(sk)
+    bad = [dict(n_chains=0, n_levels=1, steps=1), dict(n_chains=4, n_levels=0, steps=1),
+           dict(n_chains=4, n_levels=1, steps=0), dict(n_chains=4, n_levels=1, steps=1, lm_top_k=5)]
+    for b in bad:
+        kw = {k: v for k, v in b.items() if k == "lm_top_k"}
+        with pytest.raises(lib.SabrLmmError) as e:
+            gm.anneal(b["n_chains"], b["n_levels"], b["steps"], 0.9, seed=1, **kw)
+        assert e.value.status == 1, b   # EINVAL
+
+
+def test_single_chain_fp64_trajectory(gpu_lib):
+    sk = synth.caplet_term_structure(n_fwd=7, n_strikes=5)
+    om, gm = _markets(sk)
+    r_g = gm.anneal(1, 5, 20, 0.9, seed=4, prec="fp64", record_accepts=True)
+    r_o = om.anneal(1, 5, 20, 0.9, seed=4, want_bits=True)
+    assert r_g["n_evals"] == r_o["n_evals"] == 1 * (5 * 20 + 1)
+    assert np.array_equal(r_g["bits"], r_o["bits"])
+    assert np.allclose(r_g["x_best"][0], r_o["x_best"], rtol=1e-12, atol=1e-15)
+    assert r_g["f_best"][0] == pytest.approx(r_o["f_best"], rel=1e-11)
