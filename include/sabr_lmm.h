@@ -236,7 +236,9 @@ sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* m, int32_t market
 
 /* Levenberg-Marquardt polish of n points X (device [n x n_param], FP64, updated in place):
  * J by forward differences over the free slots (step 1e-7 max(|theta_p|, 1)), (J^T J + mu diag
- * J^T J) d = -J^T r by Cholesky, projection on the box, mu /10 on success, x10 on failure; a
+ * J^T J) d = -J^T r by Cholesky (J^T r from the reverse sweep of sabr_lmm_objective_grad on caplet
+ * markets, run beside the difference stencil; else from J), projection on the box, mu /10 on
+ * success, x10 on failure; a
  * point stops at target_rmse_volpt (if > 0) or once mu exceeds 1e16.  f, rmse: device [n] or
  * NULL, those of the final points.  Paper: the local polish of the hybrid scheme, Section 3.  */
 sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t market_idx, double* X,
