@@ -8,6 +8,11 @@ reduction (S8).  Inputs are synthetic (seeded), resident in HBM before the timed
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64] [--impl reference]
 
+Besides the headline value the line carries `variants` (the FP64 plain form of the same search;
+the joint caplet + swaption market in FP32, FP64 and with the BF16-split tensor-core Grams; one
+level of the 256-market batch) and `time_to_target` (0.05 vol-pt RMS: FP64 plain, FP32, and the
+FP32 search with the Levenberg-Marquardt polish).
+
 Multi-GPU runs (torchrun, one process per GPU) are independent replicas: the search does not
 shard, so no collective touches the data path; rank r anneals with seed + r and the aggregate
 counts every rank's prices over the slowest rank's time.
@@ -388,24 +393,28 @@ def main():
         ttt["fp32_lm_polished_s"] = pol["search_s"] + pol["polish_s"] if pol else None
         ttt["fp32_lm_polished"] = pol
 
-    # the joint caplet + swaption market (CTA-per-chain kernels), a shortened search for its rate
+    # the joint caplet + swaption market (CTA-per-chain kernels), a shortened search for its rate in
+    # each precision form: FP32 (5 levels), FP64 plain and FP32 with the BF16-split tensor-core
+    # Grams (1 level each)
     if args.prec == "fp32" and not args.no_joint_variant:
         jm, jsks, _, jC, _, jN, jcool = workload_markets(lib, "joint")
-        jL = 5
-        jplan = jm.anneal_prepare(jC, jL, jN, jcool, seed, prec="fp32", use_graph=True, stream=s)
-        jplan.launch(stream=s)
-        s.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(s)
-        jplan.launch(stream=s)
-        b.record(s)
-        s.synchronize()
-        tj = a.elapsed_time(b) / 1e3
-        rj = jplan.fetch()
-        variants["joint_fp32"] = {"workload": WORKLOADS["joint"], "levels_timed": jL,
-                                  "value": rj["n_evals"] * jsks[0].n_instr / tj, "unit": UNIT,
-                                  "ms_per_level": tj * 1e3 / jL}
-        del jplan, jm
+        for jprec, jL in (("fp32", 5), ("fp64", 1), ("bf16x3", 1)):
+            jplan = jm.anneal_prepare(jC, jL, jN, jcool, seed, prec=jprec, use_graph=True, stream=s)
+            jplan.launch(stream=s)
+            s.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            jplan.launch(stream=s)
+            b.record(s)
+            s.synchronize()
+            tj = a.elapsed_time(b) / 1e3
+            rj = jplan.fetch()
+            variants["joint_" + jprec] = {"workload": WORKLOADS["joint"], "levels_timed": jL,
+                                          "value": rj["n_evals"] * jsks[0].n_instr / tj, "unit": UNIT,
+                                          "ms_per_level": tj * 1e3 / jL,
+                                          "rmse_volpt": float(rj["rmse_volpt"][0])}
+            del jplan
+        del jm
 
     # the 256-market batch (one persistent launch per shared-memory bucket and level), one level
     if args.prec == "fp32" and not args.no_batch_variant:
