@@ -475,29 +475,75 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     R* Pc = m.qf_pc_off >= 0 ? cs.Y + m.qf_pc_off : cs.Pc;
     for (int g0 = 0; g0 < m.n_grp; g0 += GB) {
       const int g1 = min(m.n_grp, g0 + GB);
-      for (int g = g0; g < g1; ++g) {
-        const int Lg = m.grp_L[g], nE = m.grp_nE[g];   // uniform loads
-        const int* gp = m.grp_pair + g * m.max_npk;
-        R* B = Bbuf + (g - g0) * 3 * npm;
-        const int npk = Lg * (Lg + 1) / 2;
-        for (int t = npk + tid; t < ((npk + 3) & ~3); t += nth) {   // zero pads of the last quad
-          B[t] = R(0);
-          B[npm + t] = R(0);
-          B[2 * npm + t] = R(0);
+      if constexpr (GT) {
+        // B-build in the batch kernel, kPf groups at a time: every pair word of those groups (global
+        // memory, mostly from L2 beside the batch's coefficient rows) is loaded before the first is
+        // used, so the groups share one load latency
+        constexpr int kPf = 4;
+        for (int gb = g0; gb < g1; gb += kPf) {
+          int nE[kPf], npk[kPf];
+#pragma unroll
+          for (int i = 0; i < kPf; ++i) {
+            const int g = gb + i;
+            const int Lg = g < g1 ? m.grp_L[g] : 0;
+            nE[i] = g < g1 ? m.grp_nE[g] : 0;
+            npk[i] = Lg * (Lg + 1) / 2;
+            R* B = Bbuf + (g - g0) * 3 * npm;
+            for (int t = npk[i] + tid; t < ((npk[i] + 3) & ~3); t += nth) {   // zero pads of the last quad
+              B[t] = R(0);
+              B[npm + t] = R(0);
+              B[2 * npm + t] = R(0);
+            }
+          }
+          for (int t0 = 0; t0 < m.max_npk; t0 += nth) {
+            const int t = t0 + tid;
+            int pk[kPf];
+#pragma unroll
+            for (int i = 0; i < kPf; ++i) pk[i] = t < npk[i] ? m.grp_pair[(gb + i) * m.max_npk + t] : 0;
+#pragma unroll
+            for (int i = 0; i < kPf; ++i) {
+              if (t >= npk[i]) continue;
+              const int e = pk[i] & 255, lo = pk[i] >> 8, hi = lo + nE[i];
+              const R* PG = cs.PQ + e * PL;
+              const R* PA = PG + ND * PL;
+              const R* SH = PA + ND * PL;
+              const R* PGS = SH + ND * PL;
+              const R G = PG[hi] - PG[lo];
+              const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
+              const Q4<R> cr = cs.crq[e];
+              R* B = Bbuf + (gb + i - g0) * 3 * npm;
+              B[t] = cr.a * G;
+              B[npm + t] = cr.b * X;
+              B[2 * npm + t] = cr.c * G;
+            }
+          }
         }
-        for (int t = tid; t < npk; t += nth) {
-          const int pk = gp[t];
-          const int e = pk & 255, lo = pk >> 8, hi = lo + nE;
-          const R* PG = cs.PQ + e * PL;
-          const R* PA = PG + ND * PL;
-          const R* SH = PA + ND * PL;
-          const R* PGS = SH + ND * PL;
-          const R G = PG[hi] - PG[lo];
-          const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
-          const Q4<R> cr = cs.crq[e];
-          B[t] = cr.a * G;
-          B[npm + t] = cr.b * X;
-          B[2 * npm + t] = cr.c * G;
+      } else {
+        // B-build, one group after the other (the pair words are L1-resident for a single market)
+        for (int g = g0; g < g1; ++g) {
+          const int Lg = m.grp_L[g], nE = m.grp_nE[g];   // uniform loads
+          const int* gp = m.grp_pair + g * m.max_npk;
+          R* B = Bbuf + (g - g0) * 3 * npm;
+          const int npk = Lg * (Lg + 1) / 2;
+          for (int t = npk + tid; t < ((npk + 3) & ~3); t += nth) {   // zero pads of the last quad
+            B[t] = R(0);
+            B[npm + t] = R(0);
+            B[2 * npm + t] = R(0);
+          }
+          for (int t = tid; t < npk; t += nth) {
+            const int pk = gp[t];
+            const int e = pk & 255, lo = pk >> 8, hi = lo + nE;
+            const R* PG = cs.PQ + e * PL;
+            const R* PA = PG + ND * PL;
+            const R* SH = PA + ND * PL;
+            const R* PGS = SH + ND * PL;
+            const R G = PG[hi] - PG[lo];
+            const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
+            const Q4<R> cr = cs.crq[e];
+            B[t] = cr.a * G;
+            B[npm + t] = cr.b * X;
+            B[2 * npm + t] = cr.c * G;
+          }
         }
       }
       __syncthreads();
