@@ -475,6 +475,21 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     R* Pc = m.qf_pc_off >= 0 ? cs.Y + m.qf_pc_off : cs.Pc;
     for (int g0 = 0; g0 < m.n_grp; g0 += GB) {
       const int g1 = min(m.n_grp, g0 + GB);
+      // batch kernel: this thread's first chunk descriptor and first swap's chunk range and expiry,
+      // loaded now so that their latency passes under the B-build
+      int4 ck_pf = make_int4(0, 0, 0, 0);
+      int sc_pf0 = 0, sc_pf1 = 0;
+      double te_pf = 1.0;
+      if constexpr (GT) {
+        const int4* gt = group_table<R>(cs, m);
+        if (gt[g0].x + tid < gt[g1].x) ck_pf = m.chunk[gt[g0].x + tid];
+        const int sp = gt[g0].y + tid;
+        if (sp < gt[g1].y) {
+          sc_pf0 = m.swap_chunk0[sp];
+          sc_pf1 = m.swap_chunk0[sp + 1];
+          te_pf = m.swap_TE[sp];
+        }
+      }
       if constexpr (GT) {
         // B-build in the batch kernel, kPf groups at a time: every pair word of those groups (global
         // memory, mostly from L2 beside the batch's coefficient rows) is loaded before the first is
@@ -553,7 +568,8 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const int c0 = GT ? group_table<R>(cs, m)[g0].x : m.grp_chunk0[g0];
       const int c1 = GT ? group_table<R>(cs, m)[g1].x : m.grp_chunk0[g1];
       for (int c = c0 + tid; c < c1; c += nth) {
-        const int4 ck = m.chunk[c];   // one load: no dependent per-swap lookups before the rows
+        // one load: no dependent per-swap lookups before the rows
+        const int4 ck = (GT && c == c0 + tid) ? ck_pf : m.chunk[c];
         const int k = ck.z & 0xffff, nk = ck.z >> 16, nq = ck.w;
         const R* B = Bbuf + (ck.y - g0) * 3 * npm;
         const Q4<R>* Cq = (const Q4<R>*)(Call + ck.x);
@@ -585,13 +601,15 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const int s1 = GT ? group_table<R>(cs, m)[g1].y : m.grp_swap0[g1];
       for (int s = s0 + tid; s < s1; s += nth) {
         const int nb = m.max_batch_chunks;
+        const bool first = GT && s == s0 + tid;
+        const int ca = first ? sc_pf0 : m.swap_chunk0[s], cb = first ? sc_pf1 : m.swap_chunk0[s + 1];
         R v1 = 0, v2 = 0, v3 = 0;
-        for (int c = m.swap_chunk0[s]; c < m.swap_chunk0[s + 1]; ++c) {
+        for (int c = ca; c < cb; ++c) {
           v1 += Pc[c - c0];
           v2 += Pc[nb + c - c0];
           v3 += Pc[2 * nb + c - c0];
         }
-        const R TE = (R)m.swap_TE[s];
+        const R TE = (R)(first ? te_pf : m.swap_TE[s]);
         const R al = M::sqrt_(v1 / TE);
         const R nu = M::sqrt_(R(2) * v2) / (al * TE);
         R rho = v3 / v1;
