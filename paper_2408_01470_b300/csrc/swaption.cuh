@@ -609,22 +609,25 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
           v2 += Pc[nb + c - c0];
           v3 += Pc[2 * nb + c - c0];
         }
+        // (FP32: the hardware reciprocal and reciprocal square root, as in the caplet mapping; FP64
+        // exact.  nu = 0 stays 0.)
         const R TE = (R)(first ? te_pf : m.swap_TE[s]);
-        const R al = M::sqrt_(v1 / TE);
-        const R nu = M::sqrt_(R(2) * v2) / (al * TE);
-        R rho = v3 / v1;
+        const R al = fsqrt<R>(fdiv<R>(v1, TE));
+        const R v2x = R(2) * v2;
+        const R nu = v2x > R(0) ? fdiv<R>(fsqrt<R>(v2x), al * TE) : R(0);
+        R rho = fdiv<R>(v3, v1);
         rho = rho > R(0.999) ? R(0.999) : (rho < R(-0.999) ? R(-0.999) : rho);
         Q4<R> f;
         f.a = al;
-        f.b = nu / al;
+        f.b = fdiv<R>(nu, al);
         f.c = al * al;
         f.d = rho * nu * al;
         cs.F4s[s] = f;
         cs.A3s[s] = (R(2) - R(3) * rho * rho) * nu * nu;
         Q4<R> q;
         q.a = rho;
-        q.b = R(1) / (R(1) - rho);
-        q.c = R(1) / (R(1) + rho);
+        q.b = fdiv<R>(R(1), R(1) - rho);
+        q.c = fdiv<R>(R(1), R(1) + rho);
         q.d = (R(1) - rho) * (R(1) + rho);
         cs.RCs[s] = q;
       }
