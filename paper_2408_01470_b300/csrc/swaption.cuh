@@ -420,46 +420,69 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   }
   __syncthreads();
 
-  // ---- phase 4: exclusive prefix sums along each diagonal (one warp per diagonal, two panels
-  //      per lane and chunk of 64)
-  for (int e = warp; e < ND; e += nw) {
-    const int n = NA - e;
-    R* PG = cs.PQ + (0 * ND + e) * PL;
-    R* PA = cs.PQ + (1 * ND + e) * PL;
-    R* SH = cs.PQ + (2 * ND + e) * PL;
-    R* PGS = cs.PQ + (3 * ND + e) * PL;
-    R cg = 0, ca = 0, chh = 0, cgs = 0;
-    for (int c0 = 0; c0 < n; c0 += 64) {
-      const int A0 = c0 + 2 * lane, A1 = A0 + 1;
-      const bool in0 = A0 < n, in1 = A1 < n;
-      const R g0 = in0 ? PG[A0] : R(0), a0 = in0 ? PA[A0] : R(0), h0 = in0 ? SH[A0] : R(0);
-      const R g1 = in1 ? PG[A1] : R(0), a1 = in1 ? PA[A1] : R(0), h1 = in1 ? SH[A1] : R(0);
-      // inclusive scans of the lane sums; a lane's exclusive start is its inclusive value less its sum
-      const R ig = warp_inclusive_scan(g0 + g1, lane), ia = warp_inclusive_scan(a0 + a1, lane);
-      const R ih = warp_inclusive_scan(h0 + h1, lane);
-      const R hx = chh + ih - (h0 + h1);              // exclusive prefix of Hd before A0
-      const R gs0 = g0 * (hx + h0), gs1 = g1 * (hx + h0 + h1);   // Gd(A) times the inclusive Hd prefix
-      const R igs = warp_inclusive_scan(gs0 + gs1, lane);
-      __syncwarp();
-      if (in0) {
-        PG[A0] = cg + ig - (g0 + g1);
-        PA[A0] = ca + ia - (a0 + a1);
-        SH[A0] = hx;
-        PGS[A0] = cgs + igs - (gs0 + gs1);
+  // ---- phase 4: exclusive prefix sums along each diagonal, one diagonal per half-warp (16 lanes,
+  //      three panels per lane and chunk of 48): two diagonals per warp at a time
+  {
+    const int hw = lane >> 4, l16 = lane & 15;
+    auto scan16 = [l16](R v) {   // inclusive scan within each 16-lane half
+#pragma unroll
+      for (int off = 1; off < 16; off <<= 1) {
+        const R o = __shfl_up_sync(0xffffffffu, v, off, 16);
+        if (l16 >= off) v += o;
       }
-      if (in1) {
-        PG[A1] = cg + ig - g1;
-        PA[A1] = ca + ia - a1;
-        SH[A1] = hx + h0;
-        PGS[A1] = cgs + igs - gs1;
+      return v;
+    };
+    for (int eb = 2 * warp; eb < ND; eb += 2 * nw) {
+      const int e = eb + hw;
+      const int n = e < ND ? NA - e : 0;   // a half without a diagonal reads and writes nothing
+      const int nmax = NA - eb;            // the first half's diagonal is the longer one
+      R* PG = cs.PQ + (0 * ND + (e < ND ? e : eb)) * PL;
+      R* PA = cs.PQ + (1 * ND + (e < ND ? e : eb)) * PL;
+      R* SH = cs.PQ + (2 * ND + (e < ND ? e : eb)) * PL;
+      R* PGS = cs.PQ + (3 * ND + (e < ND ? e : eb)) * PL;
+      R cg = 0, ca = 0, chh = 0, cgs = 0;
+      for (int c0 = 0; c0 < nmax; c0 += 48) {
+        const int A0 = c0 + 3 * l16;
+        R g[3], a[3], h[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const bool in = A0 + j < n;
+          g[j] = in ? PG[A0 + j] : R(0);
+          a[j] = in ? PA[A0 + j] : R(0);
+          h[j] = in ? SH[A0 + j] : R(0);
+        }
+        const R sg = g[0] + g[1] + g[2], sa = a[0] + a[1] + a[2], sh = h[0] + h[1] + h[2];
+        const R ig = scan16(sg), ia = scan16(sa), ih = scan16(sh);
+        const R hx = chh + ih - sh;   // exclusive prefix of H before A0
+        R gs[3];
+        gs[0] = g[0] * (hx + h[0]);   // G(A) times the inclusive H prefix at A
+        gs[1] = g[1] * (hx + h[0] + h[1]);
+        gs[2] = g[2] * (hx + h[0] + h[1] + h[2]);
+        const R sgs = gs[0] + gs[1] + gs[2];
+        const R igs = scan16(sgs);
+        __syncwarp();
+        R pg = cg + ig - sg, pa = ca + ia - sa, ph = hx, pgs = cgs + igs - sgs;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if (A0 + j < n) {
+            PG[A0 + j] = pg;
+            PA[A0 + j] = pa;
+            SH[A0 + j] = ph;
+            PGS[A0 + j] = pgs;
+          }
+          pg += g[j];
+          pa += a[j];
+          ph += h[j];
+          pgs += gs[j];
+        }
+        cg += __shfl_sync(0xffffffffu, ig, 15, 16);
+        ca += __shfl_sync(0xffffffffu, ia, 15, 16);
+        chh += __shfl_sync(0xffffffffu, ih, 15, 16);
+        cgs += __shfl_sync(0xffffffffu, igs, 15, 16);
+        __syncwarp();
       }
-      cg += __shfl_sync(0xffffffffu, ig, 31);
-      ca += __shfl_sync(0xffffffffu, ia, 31);
-      chh += __shfl_sync(0xffffffffu, ih, 31);
-      cgs += __shfl_sync(0xffffffffu, igs, 31);
-      __syncwarp();
+      if (e < ND && l16 == 0) { PG[n] = cg; PA[n] = ca; SH[n] = chh; PGS[n] = cgs; }
     }
-    if (lane == 0) { PG[n] = cg; PA[n] = ca; SH[n] = chh; PGS[n] = cgs; }
   }
   __syncthreads();
 
