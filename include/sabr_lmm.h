@@ -259,6 +259,13 @@ typedef struct {
 sabr_lmm_status sabr_lmm_market_info(const sabr_lmm_market* m, int32_t market_idx,
                                      sabr_lmm_market_info_t* out);
 
+/* Check of the device-side failure detection: one CTA waits, with the library's bounded mbarrier
+ * wait limited to `polls` polls (1..2^24), on a phase that never completes (16 bytes announced,
+ * none sent).  The wait gives up, raises its error word and the call returns SABR_LMM_ETIMEOUT
+ * (SABR_LMM_OK would mean the wait did not give up).  Nothing faults or hangs and the CUDA
+ * context stays usable.  Synchronises `stream`.                                              */
+sabr_lmm_status sabr_lmm_selftest_wait(int64_t polls, void* stream);
+
 /* Introspection: the Gauss-Legendre rule the kernels use (nodes on [-1,1], weights), q = 8. */
 sabr_lmm_status sabr_lmm_quadrature_rule(int32_t q, double* x, double* w);
 

@@ -84,7 +84,8 @@ _lib = None
 EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective", "sabr_lmm_model_vols",
            "sabr_lmm_objective_grad", "sabr_lmm_anneal", "sabr_lmm_anneal_prepare", "sabr_lmm_anneal_launch",
            "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_anneal_noalloc", "sabr_lmm_lm_polish",
-           "sabr_lmm_market_info", "sabr_lmm_quadrature_rule", "sabr_lmm_last_error", "sabr_lmm_version")
+           "sabr_lmm_market_info", "sabr_lmm_selftest_wait", "sabr_lmm_quadrature_rule", "sabr_lmm_last_error",
+           "sabr_lmm_version")
 
 
 def open_library(path: str = LIB_PATH):
@@ -109,6 +110,7 @@ def open_library(path: str = LIB_PATH):
     lib.sabr_lmm_lm_polish.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_double,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
     lib.sabr_lmm_market_info.argtypes = [C.c_void_p, C.c_int32, C.POINTER(MarketInfo)]
+    lib.sabr_lmm_selftest_wait.argtypes = [C.c_int64, C.c_void_p]
     lib.sabr_lmm_quadrature_rule.argtypes = [C.c_int32, _D, _D]
     lib.sabr_lmm_last_error.restype = C.c_char_p
     lib.sabr_lmm_version.restype = C.c_char_p
@@ -137,6 +139,13 @@ def _stream_ptr(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def selftest_wait(polls=4096, stream=None):
+    """sabr_lmm_selftest_wait: the status of a bounded device wait that cannot complete (4 =
+    SABR_LMM_ETIMEOUT is the expected outcome)."""
+    lib = load()
+    return lib.sabr_lmm_selftest_wait(int(polls), _stream_ptr(stream))
 
 
 def _prec(p):

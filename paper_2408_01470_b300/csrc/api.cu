@@ -1290,6 +1290,25 @@ extern "C" sabr_lmm_status sabr_lmm_market_info(const sabr_lmm_market* m, int32_
   return SABR_LMM_OK;
 }
 
+extern "C" sabr_lmm_status sabr_lmm_selftest_wait(int64_t polls, void* stream) {
+  if (polls < 1 || polls > kWaitLimit) return fail(SABR_LMM_EINVAL, "polls must be in [1, 2^24]");
+  int* err = nullptr;
+  CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<1, 64, 0, s>>>(err, (long long)polls);
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(err);
+  if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("selftest_wait: ") + cudaGetErrorString(e));
+  if (h) return fail(SABR_LMM_ETIMEOUT, "a bounded device-side wait gave up (the self-test's expected outcome)");
+  return SABR_LMM_OK;
+}
+
 extern "C" sabr_lmm_status sabr_lmm_quadrature_rule(int32_t q, double* x, double* w) {
   if (q != 8 || !x || !w) return fail(SABR_LMM_EINVAL, "q must be 8 and x, w non-NULL");
   for (int i = 0; i < 8; ++i) { x[i] = kGLx[i]; w[i] = kGLw[i]; }

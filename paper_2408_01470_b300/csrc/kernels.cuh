@@ -174,6 +174,47 @@ __device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t 
   }
 }
 
+// The bounded wait on phase 0 of an mbarrier, called by every thread of the CTA: true once the
+// phase has completed; after `limit` polls without completion the error word is raised, the
+// copies in flight get a second bounded chance to land, and false is returned (the same value in
+// every thread).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, int* err, long long limit = kWaitLimit) {
+  uint32_t done = 0;
+  long long it = 0;
+  while (!done) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(0u) : "memory");
+    if (!done && ++it > limit) break;
+  }
+  const int timed_out = __syncthreads_or(!done);
+  if (timed_out) {
+    if (threadIdx.x == 0) atomicOr(err, 1);
+    it = 0;
+    while (!done && ++it < limit) {
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(done) : "r"(bar), "r"(0u) : "memory");
+    }
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+// Check of the bounded wait itself: one CTA arms an mbarrier for 16 bytes that are never sent (no
+// copy is issued, so nothing can land after the CTA retires); the wait gives up after `limit`
+// polls and raises *err.
+__global__ void wait_selftest_kernel(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t mbar;
+  const uint32_t bar = smem_u32(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 16;" ::"r"(bar) : "memory");
+  mbar_wait_bounded(bar, err, limit);
+}
+
 __device__ bool stage_to_smem2(void* sdst, const void* gsrc, uint32_t bytes, void* sdst2, const void* gsrc2,
                                uint32_t bytes2, uint64_t* mbar, int* err) {
   if (bytes + bytes2 == 0) return true;
@@ -188,26 +229,7 @@ __device__ bool stage_to_smem2(void* sdst, const void* gsrc, uint32_t bytes, voi
     bulk_g2s(sdst, gsrc, bytes, bar);
     bulk_g2s(sdst2, gsrc2, bytes2, bar);
   }
-  uint32_t done = 0;
-  long long it = 0;
-  while (!done) {
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done) : "r"(bar), "r"(0u) : "memory");
-    if (!done && ++it > kWaitLimit) break;
-  }
-  const int timed_out = __syncthreads_or(!done);
-  if (timed_out) {
-    if (threadIdx.x == 0) atomicOr(err, 1);
-    // give the copy in flight a second bounded chance to land before the CTA retires
-    it = 0;
-    while (!done && ++it < kWaitLimit) {
-      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                   : "=r"(done) : "r"(bar), "r"(0u) : "memory");
-    }
-    __syncthreads();
-    return false;
-  }
-  return true;
+  return mbar_wait_bounded(bar, err);
 }
 
 template <class R> __device__ __forceinline__ const void* cap_block(const DevMarket& m);
@@ -674,24 +696,7 @@ __device__ bool stage_to_smem3(void* d0, const void* g0, uint32_t b0, void* d1, 
     bulk_g2s(d1, g1, b1, bar);
     bulk_g2s(d2, g2, b2, bar);
   }
-  uint32_t done = 0;
-  long long it = 0;
-  while (!done) {
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done) : "r"(bar), "r"(0u) : "memory");
-    if (!done && ++it > kWaitLimit) break;
-  }
-  const int timed_out = __syncthreads_or(!done);
-  if (timed_out) {
-    if (threadIdx.x == 0) atomicOr(err, 1);
-    it = 0;
-    while (!done && ++it < kWaitLimit) {
-      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                   : "=r"(done) : "r"(bar), "r"(0u) : "memory");
-    }
-    __syncthreads();
-    return false;
-  }
+  if (!mbar_wait_bounded(bar, err)) return false;
   // every thread has seen the phase complete: the barrier may be re-initialised by a later stage
   if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
   return true;

@@ -67,3 +67,15 @@ def test_single_chain_fp64_trajectory(gpu_lib):
     assert np.array_equal(r_g["bits"], r_o["bits"])
     assert np.allclose(r_g["x_best"][0], r_o["x_best"], rtol=1e-12, atol=1e-15)
     assert r_g["f_best"][0] == pytest.approx(r_o["f_best"], rel=1e-11)
+
+
+def test_bounded_device_wait_gives_up_and_reports(gpu_lib):
+    # a wait on an mbarrier phase that never completes: the library's bounded wait gives up, raises
+    # its error word, and the call returns SABR_LMM_ETIMEOUT; the context stays usable
+    import paper_2408_01470_b300 as lib
+    assert lib.selftest_wait(4096) == 4
+    assert lib.selftest_wait(1) == 4
+    sk = synth.smile_2y()
+    om, gm = _markets(sk)
+    x = sk.theta_true[None, :]
+    assert gm.objective(x, "fp64").cpu().numpy()[0] == pytest.approx(om.objective(x[0]), rel=1e-12)
