@@ -154,7 +154,8 @@ sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int32_t market
  * slots 0..n_param-1 and word n_param decides acceptance.  Every chain evaluates f(x0) once,
  * so C (L N + 1) objective evaluations are made.
  *   T0 <= 0  -> T0 = f(x0) (1 if that is not a finite positive number).
- *   x0 NULL  -> box centre.  x0 is host memory [n_markets x n_param].
+ *   x0 NULL  -> box centre.  x0 is host memory [n_markets x n_param], finite, inside the box on
+ *   the free slots (EINVAL otherwise; fixed slots keep their given values).
  *   lm_top_k > 0 -> Levenberg-Marquardt polish of the lm_top_k lowest best-ever chain points
  *   (at most lm_max_iter trials; with target_rmse_volpt > 0 a point stops at the target and the
  *   polish ends once any point has reached it), the best polished point returned. */

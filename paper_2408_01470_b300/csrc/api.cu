@@ -938,6 +938,17 @@ sabr_lmm_status enqueue_plan(sabr_lmm_anneal_plan* p, cudaStream_t s) {
   return SABR_LMM_OK;
 }
 
+// One market's start point (host, n_param values): finite, and inside the box on the free slots
+// (fixed slots keep their given values).
+sabr_lmm_status check_x0(const HostMarket& h, const double* x0) {
+  for (int k = 0; k < h.n_param; ++k) {
+    const double v = x0[k];
+    if (!std::isfinite(v)) return fail(SABR_LMM_EINVAL, "x0 must be finite");
+    if (h.freem[k] && (v < h.lo[k] || v > h.hi[k])) return fail(SABR_LMM_EINVAL, "x0 must lie in the box on the free slots");
+  }
+  return SABR_LMM_OK;
+}
+
 }  // namespace
 
 extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, const sabr_lmm_anneal_opts* o,
@@ -951,6 +962,8 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (o->warps_per_block < 0 || o->warps_per_block > 28) return fail(SABR_LMM_EINVAL, "warps_per_block must be in [0, 28]");
   if (o->lm_top_k < 0 || o->lm_top_k > o->n_chains || o->lm_top_k > 1024) return fail(SABR_LMM_EINVAL, "lm_top_k must be in [0, min(n_chains, 1024)]");
   if (o->lm_top_k > 0 && o->lm_max_iter < 0) return fail(SABR_LMM_EINVAL, "lm_max_iter must be >= 0");
+  for (size_t j = 0; o->x0 && j < mk->dm.size(); ++j)
+    if (sabr_lmm_status st = check_x0(mk->hm[j], o->x0 + j * (size_t)mk->hm[j].n_param); st != SABR_LMM_OK) return st;
   for (const DevMarket& m : mk->dm) {
     if (market_smem(m, o->prec) > 227 * 1024)
       return fail(SABR_LMM_ENOTSUP, "a market does not fit in one CTA's shared memory at this precision");
@@ -1386,6 +1399,8 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, in
   if (o->lm_top_k > 0 || o->record_accepts) return fail(SABR_LMM_EINVAL, "anneal_noalloc supports neither the polish nor accept records");
   const DevMarket& m = mk->dm[market_idx];
   const HostMarket& h = mk->hm[market_idx];
+  if (o->x0)
+    if (sabr_lmm_status st = check_x0(h, o->x0); st != SABR_LMM_OK) return st;
   if (m.n_swp > 0) return fail(SABR_LMM_ENOTSUP, "swaptions are not enabled in this build");
   const int P = m.n_param;
   unsigned char* base = nullptr;

@@ -79,3 +79,20 @@ def test_bounded_device_wait_gives_up_and_reports(gpu_lib):
     om, gm = _markets(sk)
     x = sk.theta_true[None, :]
     assert gm.objective(x, "fp64").cpu().numpy()[0] == pytest.approx(om.objective(x[0]), rel=1e-12)
+
+
+def test_bad_start_points_and_quotes_are_rejected(gpu_lib):
+    import paper_2408_01470_b300 as lib
+    sk = synth.smile_2y()
+    om, gm = _markets(sk)
+    for x0 in (sk.hi + 0.1, np.array([math.nan, 0.0, 0.4])):
+        with pytest.raises(lib.SabrLmmError) as e:
+            gm.anneal(8, 1, 2, 0.9, seed=1, x0=x0)
+        assert e.value.status == 1 and "x0" in str(e.value)
+    r = gm.anneal(8, 1, 2, 0.9, seed=1, x0=sk.box_centre())   # inside: accepted
+    assert np.isfinite(r["f_best"][0])
+    vols = np.full(sk.n_cap, 0.2)
+    vols[3] = math.nan
+    with pytest.raises(lib.SabrLmmError) as e:
+        lib.Market(sk, vols)
+    assert e.value.status == 1 and "cap_vol" in str(e.value)
