@@ -229,7 +229,10 @@ __device__ bool stage_to_smem2(void* sdst, const void* gsrc, uint32_t bytes, voi
     bulk_g2s(sdst, gsrc, bytes, bar);
     bulk_g2s(sdst2, gsrc2, bytes2, bar);
   }
-  return mbar_wait_bounded(bar, err);
+  if (!mbar_wait_bounded(bar, err)) return false;
+  // every thread has seen the phase complete: the barrier may be re-initialised by a later stage
+  if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+  return true;
 }
 
 template <class R> __device__ __forceinline__ const void* cap_block(const DevMarket& m);
@@ -608,7 +611,7 @@ template <> __device__ __forceinline__ const void* swp_block<float>(const DevMar
 // request is at least 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM.
 template <class R>
 __host__ __device__ inline uint32_t smem_bytes_cta(const DevMarket& m, bool tc = false) {
-  uint32_t b = instr_block_bytes<R>(m.n_cap_pad) + instr_block_bytes<R>(m.n_swp_pad) + (uint32_t)sizeof(QuadTab<R>) +
+  uint32_t b = instr_block_bytes<R>(m.n_cap_pad) + (uint32_t)sizeof(QuadTab<R>) +
                (uint32_t)cta_scratch_elems(m) * sizeof(R) + 32 * 16 + 512;
   if (tc) {
     b += kTcBytes + 32;
@@ -637,7 +640,9 @@ __device__ __forceinline__ CtaSmemS<R> carve_cta(unsigned char* smem, const DevM
   CtaSmemS<R> s;
   unsigned char* p = smem;
   s.cap = p; p += instr_block_bytes<R>(m.n_cap_pad);
-  s.swp = p; p += instr_block_bytes<R>(m.n_swp_pad);
+  // the swaption block is read in place from global memory (read once per evaluation, by the
+  // pricing phase): the shared memory it would take is worth more as L1 for the coefficient rows
+  s.swp = const_cast<void*>(swp_block<R>(m));
   s.quad = (QuadTab<R>*)p; p += sizeof(QuadTab<R>);
   s.scratch = (R*)p; p += (size_t)cta_scratch_elems(m) * sizeof(R);
   s.red = p; p += 32 * 16;
@@ -704,9 +709,8 @@ __device__ bool stage_to_smem3(void* d0, const void* g0, uint32_t b0, void* d1, 
 
 template <class R>
 __device__ __forceinline__ bool stage_market_cta(const CtaSmemS<R>& cs, const DevMarket& m) {
-  if (!stage_to_smem3(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.swp, swp_block<R>(m),
-                      instr_block_bytes<R>(m.n_swp_pad), cs.quad, quad_block<R>(m), (uint32_t)sizeof(QuadTab<R>),
-                      cs.mbar, m.err))
+  if (!stage_to_smem2(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.quad, quad_block<R>(m),
+                      (uint32_t)sizeof(QuadTab<R>), cs.mbar, m.err))
     return false;
   stage_group_tables<R>(cta_scratch<R>(cs.scratch, m), m);
   __syncthreads();
