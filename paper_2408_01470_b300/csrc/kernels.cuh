@@ -611,7 +611,7 @@ template <> __device__ __forceinline__ const void* swp_block<float>(const DevMar
 // request is at least 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM.
 template <class R>
 __host__ __device__ inline uint32_t smem_bytes_cta(const DevMarket& m, bool tc = false) {
-  uint32_t b = instr_block_bytes<R>(m.n_cap_pad) + (uint32_t)sizeof(QuadTab<R>) +
+  uint32_t b = (uint32_t)sizeof(QuadTab<R>) +
                (uint32_t)cta_scratch_elems(m) * sizeof(R) + 32 * 16 + 512;
   if (tc) {
     b += kTcBytes + 32;
@@ -639,9 +639,9 @@ template <class R>
 __device__ __forceinline__ CtaSmemS<R> carve_cta(unsigned char* smem, const DevMarket& m) {
   CtaSmemS<R> s;
   unsigned char* p = smem;
-  s.cap = p; p += instr_block_bytes<R>(m.n_cap_pad);
-  // the swaption block is read in place from global memory (read once per evaluation, by the
-  // pricing phase): the shared memory it would take is worth more as L1 for the coefficient rows
+  // the instrument blocks are read in place from global memory (read once per evaluation, by the
+  // pricing phase): the shared memory they would take is worth more as L1 and occupancy
+  s.cap = const_cast<void*>(cap_block<R>(m));
   s.swp = const_cast<void*>(swp_block<R>(m));
   s.quad = (QuadTab<R>*)p; p += sizeof(QuadTab<R>);
   s.scratch = (R*)p; p += (size_t)cta_scratch_elems(m) * sizeof(R);
@@ -709,8 +709,7 @@ __device__ bool stage_to_smem3(void* d0, const void* g0, uint32_t b0, void* d1, 
 
 template <class R>
 __device__ __forceinline__ bool stage_market_cta(const CtaSmemS<R>& cs, const DevMarket& m) {
-  if (!stage_to_smem2(cs.cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), cs.quad, quad_block<R>(m),
-                      (uint32_t)sizeof(QuadTab<R>), cs.mbar, m.err))
+  if (!stage_to_smem2(cs.quad, quad_block<R>(m), (uint32_t)sizeof(QuadTab<R>), nullptr, nullptr, 0u, cs.mbar, m.err))
     return false;
   stage_group_tables<R>(cta_scratch<R>(cs.scratch, m), m);
   __syncthreads();
