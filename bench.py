@@ -25,6 +25,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -66,10 +67,10 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu: int):
+    def __init__(self, gpu: int, out_dir: str = ""):
         self.gpu = gpu
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+        self.path = os.path.join(out_dir or tempfile.gettempdir(), f"clocks_gpu{gpu}.csv")
 
     def __enter__(self):
         try:
@@ -269,6 +270,7 @@ def main():
     ap.add_argument("--no-joint-variant", action="store_true")
     ap.add_argument("--no-batch-variant", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--clocks-dir", default="", help="folder for the raw nvidia-smi clock samples (default: temp dir)")
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--profile", action="store_true",
                     help="run the workload's search once (optionally shortened) and exit: the ncu target")
@@ -307,7 +309,7 @@ def main():
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(ws)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_dir) as clk:
         for k in range(args.steps):
             with torch.cuda.stream(s):
                 flush.zero_()          # L2 flush between timed steps (outside the events)
