@@ -39,6 +39,10 @@ UNIT = "prices/s"
 WORKLOAD = "rebonato_caplets_20fwd_x_15k_4096ch_x_200T_x_100steps"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 rate
+# DRAM bytes (read + write) of one FP32 level launch of sa_level_kernel on this workload, from an ncu
+# capture of the kernel as it is built now (dram__bytes_read.sum 512,768 B, dram__bytes_write.sum 0 B,
+# second level of a 3-level search); the market and chain state stay in L2 across launches
+LEVEL_TRAFFIC_BYTES_FP32 = 512_768
 TARGET_RMSE_VOLPT = 0.05
 
 
@@ -333,7 +337,7 @@ def main():
     peak = FP32_PEAK_TFLOPS if args.prec == "fp32" else FP64_PEAK_TFLOPS
     achieved = flops_launch / level_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": LEVEL_TRAFFIC_BYTES_FP32 if args.prec == "fp32" and not args.warps_per_block else None,
                 "kernel": "sa_level_kernel", "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"
                 if args.prec == "fp32" else "nominal B300 FP64 1.25 TFLOP/s"}
 
