@@ -491,21 +491,25 @@ __device__ __forceinline__ float price_caplets_x2(const void* blk, int npairs, i
     const float2 l = make_float2(v0.x, v0.y), fk = make_float2(v0.z, v0.w);
     const float2 z = mul2(make_float2(fa.b, fb.b), fk);
     const float2 zx = z_over_x2(z, fk.x, fk.y, rc.rho, rc.rho, bc2(rc.omr2), bc2(c1), bc2(c2));
-    float2 corr = fma2(make_float2(v1.z, v1.w), make_float2(fa.c, fb.c), bc2(1.0f));
+    // inv_den (1 + c1 alpha^2 + c2 rho nu alpha + c3 A3), inv_den folded into the constants
+    float2 corr = fma2(make_float2(v1.z, v1.w), make_float2(fa.c, fb.c), make_float2(v1.x, v1.y));
     corr = fma2(make_float2(v2.x, v2.y), make_float2(fa.d, fb.d), corr);
     corr = fma2(make_float2(v2.z, v2.w), make_float2(ws.fA3[ix.x], ws.fA3[ix.y]), corr);
-    const float2 sig = mul2(mul2(mul2(make_float2(fa.a, fb.a), make_float2(v1.x, v1.y)), zx), corr);
+    const float2 sig = mul2(mul2(make_float2(fa.a, fb.a), zx), corr);
     ok = ok && (sig.x > 0.0f) && (sig.x < INFINITY) && (sig.y > 0.0f) && (sig.y < INFINITY);
-    const float4 v3 = B.v[3 * npairs + P], v4 = B.v[4 * npairs + P], v5 = B.v[5 * npairs + P];
+    const float4 v3 = B.v[3 * npairs + P], v4 = B.v[4 * npairs + P];
+    const float2 v5 = *(const float2*)(B.v + 5 * npairs + P);
+    // sgn d1 = (sgn l) / v + (sgn sqrtT / 2) sigma,  sgn d2 = sgn d1 - 2 (sgn sqrtT / 2) sigma
     const float2 v = mul2(sig, make_float2(v3.x, v3.y));
-    const float2 d1 = fma2(l, rcp2(v), mul2(bc2(0.5f), v));
-    const float2 sg = make_float2(v4.z, v4.w);
-    const float2 n1 = ncdf2(mul2(sg, d1));
-    const float2 n2 = ncdf2(mul2(sg, sub2(d1, v)));
-    // n1 - KF n2 in one rounding (the two nearly cancel far out of the money)
-    const float2 nkf = mul2(make_float2(v4.x, v4.y), bc2(-1.0f));
-    const float2 p = mul2(mul2(sg, make_float2(v3.z, v3.w)), fma2(nkf, n2, n1));
-    const float2 r = mul2(make_float2(v5.z, v5.w), sub2(p, make_float2(v5.x, v5.y)));
+    const float2 b = mul2(make_float2(v4.z, v4.w), sig);
+    const float2 x1 = fma2(l, rcp2(v), b);
+    const float2 x2 = fma2(b, bc2(-2.0f), x1);
+    const float2 n1 = ncdf2(x1);
+    const float2 n2 = ncdf2(x2);
+    // n1 - KF n2 in one rounding (the two nearly cancel far out of the money), and the weighted
+    // residual C (n1 - KF n2) - sqrt(w) P_mkt in one more
+    const float2 nn = fma2(make_float2(v4.x, v4.y), n2, n1);
+    const float2 r = fma2(make_float2(v3.z, v3.w), nn, v5);
     acc = fma2(r, r, acc);
   }
   return acc.x + acc.y;

@@ -3,9 +3,14 @@
 * erfc: the Chebyshev-exponent form t exp(-y^2 + P(t)), t = 1/(1 + y/2), with the coefficients
   read from the kernel header, against scipy's erfc in FP64: relative error <= 5.5e-8 on [0, 12],
   the bound the header states.
-* log1p below 1/2: the atanh series 2 s (1 + s^2/3 + ... + s^8/9), s = y/(2 + y), evaluated step by
-  step in float32 as the kernel does (one rounding per operation; the kernel's reciprocal is the
-  hardware approximation, emulated here by a correctly rounded one), against log1p in FP64.
+* the packed normal CDF: the same fit rearranged (u = 1/(2 + y), coefficients 2^j c_j log2 e, the
+  exponent in base 2), evaluated step by step in float32 as the kernel does, against 0.5 erfc in
+  FP64: the rearrangement adds no error over the fit beyond the float32 roundings of the exponent.
+* log1p below 1/2: the atanh series 2 s (1 + s^2/3 + ... + s^8/9), s = y/(2 + y), with the factor 2
+  on the coefficients, evaluated step by step in float32 as the kernel does (one rounding per
+  operation), against log1p in FP64.
+In both the kernel's hardware approximations (reciprocal, 2^x) are emulated by correctly rounded
+ones.
   Above 1/2 the kernels take the hardware log2 of 1 + y, which has no host counterpart; the GPU
   vol tests bound the result.
 """
@@ -46,16 +51,51 @@ def test_erfc_fit_within_stated_bound():
     assert np.abs(t * np.exp(-y * y + p2) / erfc(y) - 1.0).max() > 5.5e-8
 
 
+def _fma32(a, b, c):
+    # float32 fused multiply-add: the product of two float32 values is exact in FP64
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _ncdf_pair_form_f32(x):
+    f = np.float32
+    c = _erfc_coefficients()
+    d = [f(float(f(c[j])) * (1 << j) * 1.44269504088896341) for j in range(10)]
+    ax = f(abs(f(x)))
+    u = f(1.0 / np.float64(_fma32(ax, f(0.70710678), f(2.0))))
+    p = d[9]
+    for j in range(8, -1, -1):
+        p = _fma32(p, u, d[j])
+    m = f(ax * f(-0.721347520444481703))
+    h = f(u * f(2.0 ** np.float64(_fma32(m, ax, p))))
+    return h if x < 0 else f(f(1.0) - h)
+
+
+def test_ncdf_pair_form_float32():
+    xs = np.linspace(-12.0, 0.0, 24001)
+    got = np.array([_ncdf_pair_form_f32(v) for v in xs], dtype=np.float64)
+    ref = 0.5 * erfc(-xs.astype(np.float32).astype(np.float64) / np.sqrt(2.0))
+    rel = np.abs(got / ref - 1.0)
+    # near the centre the fit and a few float32 roundings; far out the two roundings of the base-2
+    # exponent a = -x^2 log2(e) / 2 dominate (m, then the fma), each <= 2^-24 |a| absolute, i.e.
+    # 2^-24 |a| ln 2 = 2^-24 x^2 / 2 relative in 2^a
+    assert rel[xs > -1.0].max() <= 4e-7, rel[xs > -1.0].max()
+    bound = 4e-7 + xs ** 2 * 2.0 ** -24
+    assert np.all(rel <= bound), (rel / bound).max()
+    # the upper half is 1 - Phi(-x) to float32 rounding
+    for v in (0.1, 0.7, 1.5, 3.0):
+        assert abs(float(_ncdf_pair_form_f32(v)) - (1.0 - 0.5 * erfc(v / np.sqrt(2.0)))) <= 1.2e-7
+
+
 def _log1p_series_f32(y):
     f = np.float32
     y = f(y)
     s = f(y * f(f(1.0) / f(f(2.0) + y)))
     s2 = f(s * s)
-    p = f(f(s2 * f(1.0 / 9.0)) + f(1.0 / 7.0))
-    p = f(f(s2 * p) + f(1.0 / 5.0))
-    p = f(f(s2 * p) + f(1.0 / 3.0))
-    p = f(f(s2 * p) + f(1.0))
-    return f(f(f(2.0) * s) * p)
+    p = f(f(s2 * f(2.0 / 9.0)) + f(2.0 / 7.0))
+    p = f(f(s2 * p) + f(2.0 / 5.0))
+    p = f(f(s2 * p) + f(2.0 / 3.0))
+    p = f(f(s2 * p) + f(2.0))
+    return f(s * p)
 
 
 def test_log1p_series_branch_float32():
