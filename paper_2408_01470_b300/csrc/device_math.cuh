@@ -224,6 +224,16 @@ __device__ __forceinline__ float2 ncdf2(float2 x) {
   const float2 h = mul2(u, ex2_2(fma2(m, ax, p)));          // erfc(|x| / sqrt 2) / 2
   return sel2(x.x < 0.0f, x.y < 0.0f, h, sub2(bc2(1.0f), h));
 }
+// ncdf2 for arguments known not to be positive (the far-side Black argument): erfc(-x / sqrt 2) / 2
+// with |x| = -x, no select.
+__device__ __forceinline__ float2 ncdf2_nonpos(float2 x) {
+  const float2 u = rcp2(fma2(x, bc2(-0.70710678f), bc2(2.0f)));
+  float2 p = bc2(erfc_fit_u2(9));
+#pragma unroll
+  for (int j = 8; j >= 0; --j) p = fma2(p, u, bc2(erfc_fit_u2(j)));
+  const float2 m = mul2(x, bc2(-0.721347520444481703f));   // -x log2(e) / 2
+  return mul2(u, ex2_2(fma2(m, x, p)));
+}
 
 // Out-of-the-money Black price with sgn = +1 (call, K >= F) or -1 (put, K < F):
 //   P = sgn * DF * (Phi(sgn d1) - KF Phi(sgn d2)),  DF = D F,  KF = K / F,

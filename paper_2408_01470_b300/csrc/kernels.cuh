@@ -148,11 +148,16 @@ __global__ void setup_pairs_kernel(DevMarket m) {
   const int bb = hb ? b : a;
   const Q4<float> g0a = S.g0[a], g0b = S.g0[bb], g1a = S.g1[a], g1b = S.g1[bb], g2a = S.g2[a], g2b = S.g2[bb];
   const float swa = g2a.d, swb = hb ? g2b.d : 0.0f;
-  V[0 * np + P] = make_float4(g2a.b * g0a.a, g2b.b * g0b.a, g0a.b, g0b.b);
+  // call (sgn = +1): r = DF sw (Phi(xf) - KF Phi(xs)) - sw P_mkt;
+  // put (sgn = -1):  r = KF DF sw (Phi(xf) - Phi(xs) / KF) - sw P_mkt
+  const bool ca = g2a.b > 0.0f, cb = g2b.b > 0.0f;
+  const float Ca = ca ? g1a.d * swa : g2a.a * g1a.d * swa, Cb = cb ? g1b.d * swb : g2b.a * g1b.d * swb;
+  const float Ba = ca ? -g2a.a : -1.0f / g2a.a, Bb = cb ? -g2b.a : -1.0f / g2b.a;
+  V[0 * np + P] = make_float4(-fabsf(g0a.a), -fabsf(g0b.a), g0a.b, g0b.b);
   V[1 * np + P] = make_float4(g0a.c, g0b.c, g0a.c * g0a.d, g0b.c * g0b.d);
   V[2 * np + P] = make_float4(g0a.c * g1a.a, g0b.c * g1b.a, g0a.c * g1a.b, g0b.c * g1b.b);
-  V[3 * np + P] = make_float4(g1a.c, g1b.c, g2a.b * g1a.d * swa, g2b.b * g1b.d * swb);
-  V[4 * np + P] = make_float4(-g2a.a, -g2b.a, 0.5f * g2a.b * g1a.c, 0.5f * g2b.b * g1b.c);
+  V[3 * np + P] = make_float4(g1a.c, g1b.c, Ca, Cb);
+  V[4 * np + P] = make_float4(Ba, Bb, 0.5f * g1a.c, 0.5f * g1b.c);
   V[5 * np + P] = make_float4(-swa * g2a.c, -swb * g2b.c, 0.0f, 0.0f);
   idx[P] = make_int2(S.idx[a], S.idx[bb]);
 }

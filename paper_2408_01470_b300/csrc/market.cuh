@@ -55,11 +55,14 @@ template <class R> __host__ __device__ inline InstrView<R> instr_view(const void
 // The FP32 caplet block again, pair-major for the packed pricer: caplets a = 64 i + l and
 // b = a + 32 (l = 0..31) form pair P = 32 i + l, and each 16-byte vector holds two fields of both,
 // with the constants that the pricer multiplies together folded in advance:
-//   v0 = {sgn l_a, sgn l_b, fk_a, fk_b}          v1 = {e_a, e_b, e c1_a, e c1_b}
+//   v0 = {-|l|_a, -|l|_b, fk_a, fk_b}            v1 = {e_a, e_b, e c1_a, e c1_b}
 //   v2 = {e c2_a, e c2_b, e c3_a, e c3_b}        v3 = {sqrtT_a, sqrtT_b, C_a, C_b}
-//   v4 = {-KF_a, -KF_b, sgn sqrtT_a / 2, ..b}    v5 = {-sqrtw P_mkt_a, -sqrtw P_mkt_b, 0, 0}
-// with e = inv_den (so that sigma = alpha (z / x) (e + e c1 alpha^2 + ...)) and C = sgn DF sqrt(w)
-// (so that the weighted residual is C (Phi(sgn d1) - KF Phi(sgn d2)) - sqrt(w) P_mkt); then the
+//   v4 = {B_a, B_b, sqrtT_a / 2, sqrtT_b / 2}    v5 = {-sqrtw P_mkt_a, -sqrtw P_mkt_b, 0, 0}
+// with e = inv_den (so that sigma = alpha (z / x) (e + e c1 alpha^2 + ...)).  An out-of-the-money
+// option has sgn l = -|l|, so of its two Black arguments sgn d1, sgn d2 the one on the far side,
+// xs = -|l| / v - v / 2, is never positive and the other is xf = -|l| / v + v / 2 (xf = sgn d1 for
+// a call, sgn d2 for a put).  The weighted residual is C (Phi(xf) + B Phi(xs)) - sqrt(w) P_mkt with
+// C = DF sqrt(w), B = -KF for a call and C = KF DF sqrt(w), B = -1 / KF for a put.  Then the
 // forward indices {idx_a, idx_b}.  A missing b (b >= n) repeats a with sqrt(w) = 0.
 __host__ __device__ inline int cap_pairs(int n) { return 32 * ((n + 63) / 64); }
 __host__ __device__ inline uint32_t pair_block_bytes(int npairs) {

@@ -499,16 +499,16 @@ __device__ __forceinline__ float price_caplets_x2(const void* blk, int npairs, i
     ok = ok && (sig.x > 0.0f) && (sig.x < INFINITY) && (sig.y > 0.0f) && (sig.y < INFINITY);
     const float4 v3 = B.v[3 * npairs + P], v4 = B.v[4 * npairs + P];
     const float2 v5 = *(const float2*)(B.v + 5 * npairs + P);
-    // sgn d1 = (sgn l) / v + (sgn sqrtT / 2) sigma,  sgn d2 = sgn d1 - 2 (sgn sqrtT / 2) sigma
+    // xf = -|l| / v + v / 2 and xs = xf - v <= 0 (v = sigma sqrtT, v / 2 = (sqrtT / 2) sigma)
     const float2 v = mul2(sig, make_float2(v3.x, v3.y));
-    const float2 b = mul2(make_float2(v4.z, v4.w), sig);
-    const float2 x1 = fma2(l, rcp2(v), b);
-    const float2 x2 = fma2(b, bc2(-2.0f), x1);
-    const float2 n1 = ncdf2(x1);
-    const float2 n2 = ncdf2(x2);
-    // n1 - KF n2 in one rounding (the two nearly cancel far out of the money), and the weighted
-    // residual C (n1 - KF n2) - sqrt(w) P_mkt in one more
-    const float2 nn = fma2(make_float2(v4.x, v4.y), n2, n1);
+    const float2 hv = mul2(make_float2(v4.z, v4.w), sig);
+    const float2 xf = fma2(l, rcp2(v), hv);
+    const float2 xs = fma2(hv, bc2(-2.0f), xf);
+    const float2 nf = ncdf2(xf);
+    const float2 ns = ncdf2_nonpos(xs);
+    // Phi(xf) + B Phi(xs) in one rounding (the two nearly cancel far out of the money), and the
+    // weighted residual C (Phi(xf) + B Phi(xs)) - sqrt(w) P_mkt in one more
+    const float2 nn = fma2(make_float2(v4.x, v4.y), ns, nf);
     const float2 r = fma2(make_float2(v3.z, v3.w), nn, v5);
     acc = fma2(r, r, acc);
   }
