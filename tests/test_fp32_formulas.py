@@ -6,6 +6,8 @@
 * the packed normal CDF: the same fit rearranged (u = 1/(2 + y), coefficients 2^j c_j log2 e, the
   exponent in base 2), evaluated step by step in float32 as the kernel does, against 0.5 erfc in
   FP64: the rearrangement adds no error over the fit beyond the float32 roundings of the exponent.
+  For x <= 0 these are also the steps of the select-free form the caplet pricer takes for the
+  far-side Black argument (the same operations on -x, bit for bit).
 * log1p below 1/2: the atanh series 2 s (1 + s^2/3 + ... + s^8/9), s = y/(2 + y), with the factor 2
   on the coefficients, evaluated step by step in float32 as the kernel does (one rounding per
   operation), against log1p in FP64.
