@@ -18,6 +18,13 @@
  *     raised after launch, where device outputs are unspecified.
  *   - A parameter point whose model vol for some instrument is not a finite positive number is
  *     infeasible: its objective is +inf.  That is a value, not an error.
+ *   - Device-side failure detection: every wait of a kernel on its own asynchronous copies is
+ *     bounded.  A wait that gives up raises the market's error word, the affected outputs are set
+ *     to NaN (an annealing chain of the affected CTA ends the level with f = +inf), and the kernel
+ *     returns normally.  The word is reported, and then cleared, by the next sabr_lmm_sync,
+ *     sabr_lmm_anneal_fetch or sabr_lmm_anneal on that market, which returns SABR_LMM_ETIMEOUT
+ *     once; stream-ordered calls (objective, residuals, model_vols, objective_grad, lm_polish)
+ *     return SABR_LMM_OK at enqueue time and are checked by sabr_lmm_sync.
  */
 #ifndef SABR_LMM_H
 #define SABR_LMM_H
@@ -39,8 +46,9 @@ typedef enum {
 
 /* Arithmetic of the hot path.
  *   FP64      : every price, integral and sum in FP64 (the plain form).
- *   FP32      : integrals, SABR vols and Black prices in FP32; the objective summed across
- *               lanes in float-float (48-bit significand); the Metropolis test in FP32 and
+ *   FP32      : integrals, SABR vols and Black prices in FP32; the squared residuals summed per
+ *               lane and across a warp's lanes in FP32 (markets with swaptions: the warps' sums
+ *               added in float-float, a 48-bit significand); the Metropolis test in FP32 and
  *               repeated in FP64 whenever the uniform falls inside the FP32 error band (so the
  *               decision equals the FP64 decision on the same objective values); chain state
  *               in FP32.  Outputs (f, vols, best points) are returned as FP64.
@@ -130,6 +138,17 @@ void sabr_lmm_free_market(sabr_lmm_market* m);
 sabr_lmm_status sabr_lmm_objective(const sabr_lmm_market* m, int32_t market_idx, const double* X,
                                    int64_t n, int32_t prec, double* f, void* stream);
 
+/* The weighted residuals r_k = sqrt(w_k) (P_k(X[i]) - P_k^mkt) of every instrument (caplets first,
+ * then swaptions) for n parameter sets: res device [n x (n_cap + n_swp)], FP64, row-major; f
+ * (device [n] or NULL) receives sum_k r_k^2 as sabr_lmm_objective would.  The residuals come from
+ * the same pricer the annealer's objective runs at this precision (in FP32 the packed-pair
+ * pricer), so they are the per-price terms of f.  With the default weights w_k = 1/vega_k^2 at the
+ * quoted vol, r_k is the price error in vol units to first order.  Entries whose model vol is not
+ * a finite positive number are NaN.  Paper: the terms of f_c and f_s of Section 3.  Same errors
+ * as sabr_lmm_objective.                                                                     */
+sabr_lmm_status sabr_lmm_residuals(const sabr_lmm_market* m, int32_t market_idx, const double* X,
+                                   int64_t n, int32_t prec, double* f, double* res, void* stream);
+
 /* Model Black vols of every instrument (caplets first, then swaptions) for n parameter sets:
  * vols device [n x (n_cap + n_swp)], FP64.  Infeasible entries are NaN.  Same errors.        */
 sabr_lmm_status sabr_lmm_model_vols(const sabr_lmm_market* m, int32_t market_idx, const double* X,
@@ -212,18 +231,31 @@ sabr_lmm_status sabr_lmm_anneal_launch(sabr_lmm_anneal_plan* plan, void* stream)
 sabr_lmm_status sabr_lmm_anneal_fetch(sabr_lmm_anneal_plan* plan, sabr_lmm_result* out);
 void sabr_lmm_anneal_plan_free(sabr_lmm_anneal_plan* plan);
 
+/* Synchronise `stream`, then read and clear the error word of every market of m: returns
+ * SABR_LMM_ETIMEOUT if a bounded device-side wait of a call on these markets gave up since the
+ * word was last read (the outputs of that call are NaN), else SABR_LMM_OK.  The check for the
+ * stream-ordered calls.                                                                      */
+sabr_lmm_status sabr_lmm_sync(const sabr_lmm_market* m, void* stream);
+
+/* Test hook of the failure detection: raises market_idx's error word on `stream` (stream-ordered)
+ * as a device wait that gave up would, without any device wait.  The next sabr_lmm_sync,
+ * sabr_lmm_anneal_fetch or sabr_lmm_anneal on the market then reports SABR_LMM_ETIMEOUT once.  */
+sabr_lmm_status sabr_lmm_test_raise_error(const sabr_lmm_market* m, int32_t market_idx, void* stream);
+
 /* The annealing search for callers that cannot allocate device memory.  The paper has no
  * counterpart to this call; it exists for code that is not allowed to call cudaMalloc: for
  * example a service that hands the whole device memory to its own pool at start-up, a plug-in
  * host that gives a library a stream but no allocator, or a latency-critical loop where
  * cudaMalloc's implicit device synchronisation would stall other work.
- *   It runs the same search as sabr_lmm_anneal on market `market_idx` (same options, same
- *   uniforms, same kernels, so the same result), keeping all of its working state in one
- *   fixed-size array inside the library's device image: 3.6 MB, loaded with the library on every
- *   GPU that uses it and held until the process exits.  It calls no cudaMalloc, cudaFree or other
- *   allocating routine.
+ *   It runs the same search as sabr_lmm_anneal on market `market_idx` (caplet markets and markets
+ *   with swaptions; same options, same uniforms, same kernels, so the same result), keeping all of
+ *   its working state in one fixed-size array inside the library's device image: 3,637,760 bytes
+ *   (3.64 MB), loaded with the library on every GPU that uses it and held until the process exits.
+ *   It calls no cudaMalloc, cudaFree or other allocating routine, and enqueues no host copy (the
+ *   start point travels as a kernel argument).
  *   Limits: n_chains <= 16384, n_levels <= 4096 (EINVAL names the limit otherwise); lm_top_k and
- *   record_accepts must be 0.  x0 is host memory [n_param] or NULL (box centre).
+ *   record_accepts must be 0; the market must fit one CTA's shared memory at `prec` (ENOTSUP, as
+ *   for sabr_lmm_anneal).  x0 is host memory [n_param] or NULL (box centre).
  *   Outputs (device, caller-owned): x_best [n_param], f_best [1], trace_f [n_levels] or NULL.
  *   Stream-ordered: it only enqueues work on `stream`; synchronise before reading the outputs.
  *   The first call on a device looks up the array's device address (once per device, with that

@@ -9,6 +9,8 @@ Entry points (same names as the C-ABI, without the ``sabr_lmm_`` prefix):
     Market(...)                 sabr_lmm_load_market / sabr_lmm_free_market
     Market.objective(X, prec)   sabr_lmm_objective
     Market.model_vols(X, prec)  sabr_lmm_model_vols
+    Market.residuals(X, prec)   sabr_lmm_residuals
+    Market.sync(stream)         sabr_lmm_sync (device-side wait timeouts of stream-ordered calls)
     Market.objective_grad(...)  sabr_lmm_objective_grad
     Market.anneal(...)          sabr_lmm_anneal
     Market.anneal_prepare(...)  sabr_lmm_anneal_prepare / _launch / _fetch / _plan_free
@@ -85,7 +87,7 @@ EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective",
            "sabr_lmm_objective_grad", "sabr_lmm_anneal", "sabr_lmm_anneal_prepare", "sabr_lmm_anneal_launch",
            "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_anneal_noalloc", "sabr_lmm_lm_polish",
            "sabr_lmm_market_info", "sabr_lmm_selftest_wait", "sabr_lmm_quadrature_rule", "sabr_lmm_last_error",
-           "sabr_lmm_version")
+           "sabr_lmm_version", "sabr_lmm_residuals", "sabr_lmm_sync", "sabr_lmm_test_raise_error")
 
 
 def open_library(path: str = LIB_PATH):
@@ -101,6 +103,10 @@ def open_library(path: str = LIB_PATH):
         getattr(lib, name).argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]
     lib.sabr_lmm_objective_grad.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                                             C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_residuals.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_sync.argtypes = [C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_test_raise_error.argtypes = [C.c_void_p, C.c_int32, C.c_void_p]
     lib.sabr_lmm_anneal.argtypes = [C.c_void_p, C.POINTER(AnnealOpts), C.POINTER(Result)]
     lib.sabr_lmm_anneal_prepare.argtypes = [C.c_void_p, C.POINTER(AnnealOpts), C.c_void_p, C.POINTER(C.c_void_p)]
     lib.sabr_lmm_anneal_launch.argtypes = [C.c_void_p, C.c_void_p]
@@ -242,6 +248,27 @@ class Market:
         _check(self._lib.sabr_lmm_model_vols(self.h, market, C.c_void_p(X.data_ptr()), X.shape[0], _prec(prec),
                                              C.c_void_p(v.data_ptr()), _stream_ptr(stream)))
         return v
+
+    def residuals(self, X, prec="fp64", market=0, stream=None):
+        """sabr_lmm_residuals: (f, r) with r[i, k] = sqrt(w_k) (P_k(X[i]) - P_k^mkt) from the pricer
+        the search runs at this precision (device tensors)."""
+        X = self._X(X, market)
+        n_instr = self.skels[market].n_instr
+        f = self._torch.empty(X.shape[0], dtype=self._torch.float64, device="cuda")
+        r = self._torch.empty((X.shape[0], n_instr), dtype=self._torch.float64, device="cuda")
+        _check(self._lib.sabr_lmm_residuals(self.h, market, C.c_void_p(X.data_ptr()), X.shape[0], _prec(prec),
+                                            C.c_void_p(f.data_ptr()), C.c_void_p(r.data_ptr()), _stream_ptr(stream)))
+        return f, r
+
+    def sync(self, stream=None):
+        """sabr_lmm_sync: synchronise the stream and raise SabrLmmError (ETIMEOUT) if a device-side
+        wait of a call on these markets gave up since the last check."""
+        _check(self._lib.sabr_lmm_sync(self.h, _stream_ptr(stream)))
+
+    def test_raise_error(self, market=0, stream=None):
+        """sabr_lmm_test_raise_error: raise the market's error word from the host (failure-detection
+        tests)."""
+        _check(self._lib.sabr_lmm_test_raise_error(self.h, market, _stream_ptr(stream)))
 
     def objective_grad(self, X, prec="fp64", market=0, stream=None):
         X = self._X(X, market)

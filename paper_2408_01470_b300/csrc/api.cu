@@ -458,7 +458,8 @@ extern "C" void sabr_lmm_free_market(sabr_lmm_market* m) {
 namespace {
 
 template <class R, int MODEL, int FORMULA>
-cudaError_t launch_objective(const DevMarket& m, const double* X, long long n, double* f, double* vols, cudaStream_t s) {
+cudaError_t launch_objective(const DevMarket& m, const double* X, long long n, double* f, double* vols, double* res,
+                             cudaStream_t s) {
   // a few sets (a polish's trial points and stencils): one set per CTA spreads them over the SMs
   const int W = n <= 148 * 8 ? 1 : 4;
   const uint32_t sm = smem_bytes<R>(m, W);
@@ -468,14 +469,15 @@ cudaError_t launch_objective(const DevMarket& m, const double* X, long long n, d
   long long blocks = (n + W - 1) / W;
   if (blocks > 148 * 64) blocks = 148 * 64;
   if (blocks < 1) blocks = 1;
-  kern<<<(unsigned)blocks, W * 32, sm, s>>>(m, X, n, f, vols);
+  kern<<<(unsigned)blocks, W * 32, sm, s>>>(m, X, n, f, vols, res);
   return cudaGetLastError();
 }
 
 template <class R>
-cudaError_t launch_objective_r(const DevMarket& m, const double* X, long long n, double* f, double* vols, cudaStream_t s) {
-  if (m.model == 0) return m.formula == 0 ? launch_objective<R, 0, 0>(m, X, n, f, vols, s) : launch_objective<R, 0, 1>(m, X, n, f, vols, s);
-  return m.formula == 0 ? launch_objective<R, 1, 0>(m, X, n, f, vols, s) : launch_objective<R, 1, 1>(m, X, n, f, vols, s);
+cudaError_t launch_objective_r(const DevMarket& m, const double* X, long long n, double* f, double* vols, double* res,
+                               cudaStream_t s) {
+  if (m.model == 0) return m.formula == 0 ? launch_objective<R, 0, 0>(m, X, n, f, vols, res, s) : launch_objective<R, 0, 1>(m, X, n, f, vols, res, s);
+  return m.formula == 0 ? launch_objective<R, 1, 0>(m, X, n, f, vols, res, s) : launch_objective<R, 1, 1>(m, X, n, f, vols, res, s);
 }
 
 // The tensor-core contraction of the pair Grams applies when the panel tables fit one MMA tile.
@@ -483,28 +485,29 @@ bool tc_eligible(const DevMarket& m) { return m.n_swp > 0 && m.NA <= 64 && m.ND 
 bool use_tc(const DevMarket& m, int prec) { return prec == SABR_LMM_FP32_BF16X3 && tc_eligible(m); }
 
 template <class R, int FORMULA, bool TC>
-cudaError_t launch_objective_cta(const DevMarket& m, const double* X, long long n, double* f, double* vols, cudaStream_t s) {
+cudaError_t launch_objective_cta(const DevMarket& m, const double* X, long long n, double* f, double* vols, double* res,
+                                 cudaStream_t s) {
   const uint32_t sm = smem_bytes_cta<R>(m, TC);
   auto kern = objective_cta_kernel<R, FORMULA, TC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   long long blocks = n < 148 * 16 ? n : 148 * 16;
   if (blocks < 1) blocks = 1;
-  kern<<<(unsigned)blocks, 256, sm, s>>>(m, X, n, f, vols);
+  kern<<<(unsigned)blocks, 256, sm, s>>>(m, X, n, f, vols, res);
   return cudaGetLastError();
 }
 
 cudaError_t launch_objective_any(const DevMarket& m, int prec, const double* X, long long n, double* f, double* vols,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, double* res = nullptr) {
   if (m.n_swp > 0) {
     if (prec == SABR_LMM_FP64)
-      return m.formula == 0 ? launch_objective_cta<double, 0, false>(m, X, n, f, vols, s) : launch_objective_cta<double, 1, false>(m, X, n, f, vols, s);
+      return m.formula == 0 ? launch_objective_cta<double, 0, false>(m, X, n, f, vols, res, s) : launch_objective_cta<double, 1, false>(m, X, n, f, vols, res, s);
     if (use_tc(m, prec))
-      return m.formula == 0 ? launch_objective_cta<float, 0, true>(m, X, n, f, vols, s) : launch_objective_cta<float, 1, true>(m, X, n, f, vols, s);
-    return m.formula == 0 ? launch_objective_cta<float, 0, false>(m, X, n, f, vols, s) : launch_objective_cta<float, 1, false>(m, X, n, f, vols, s);
+      return m.formula == 0 ? launch_objective_cta<float, 0, true>(m, X, n, f, vols, res, s) : launch_objective_cta<float, 1, true>(m, X, n, f, vols, res, s);
+    return m.formula == 0 ? launch_objective_cta<float, 0, false>(m, X, n, f, vols, res, s) : launch_objective_cta<float, 1, false>(m, X, n, f, vols, res, s);
   }
-  return prec == SABR_LMM_FP64 ? launch_objective_r<double>(m, X, n, f, vols, s)
-                               : launch_objective_r<float>(m, X, n, f, vols, s);
+  return prec == SABR_LMM_FP64 ? launch_objective_r<double>(m, X, n, f, vols, res, s)
+                               : launch_objective_r<float>(m, X, n, f, vols, res, s);
 }
 
 // Shared memory a market needs per CTA in the given precision (the caller checks it against the
@@ -537,6 +540,16 @@ extern "C" sabr_lmm_status sabr_lmm_objective(const sabr_lmm_market* m, int32_t 
   if (n == 0) return SABR_LMM_OK;
   if (!X || !f) return fail(SABR_LMM_EINVAL, "X and f are required");
   CUDA_TRY(launch_objective_any(m->dm[idx], prec, X, n, f, nullptr, (cudaStream_t)stream));
+  return SABR_LMM_OK;
+}
+
+extern "C" sabr_lmm_status sabr_lmm_residuals(const sabr_lmm_market* m, int32_t idx, const double* X, int64_t n,
+                                              int32_t prec, double* f, double* res, void* stream) {
+  sabr_lmm_status st = check_call(m, idx, n, prec);
+  if (st != SABR_LMM_OK) return st;
+  if (n == 0) return SABR_LMM_OK;
+  if (!X || !res) return fail(SABR_LMM_EINVAL, "X and res are required");
+  CUDA_TRY(launch_objective_any(m->dm[idx], prec, X, n, f, nullptr, (cudaStream_t)stream, res));
   return SABR_LMM_OK;
 }
 
@@ -1213,19 +1226,44 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_launch(sabr_lmm_anneal_plan* p, void*
   return SABR_LMM_OK;
 }
 
+namespace {
+// Read and clear the error word of every market of mk after `s` has been synchronised: a raised
+// word (a bounded device-side wait gave up since the last read) is reported once, as ETIMEOUT.
+sabr_lmm_status take_error_words(const sabr_lmm_market* mk, cudaStream_t s) {
+  int err = 0;
+  for (const DevMarket& m : mk->dm) {
+    int e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, m.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (e) CUDA_TRY(cudaMemsetAsync(m.err, 0, sizeof(int), s));
+    err |= e;
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (err) return fail(SABR_LMM_ETIMEOUT, "a bounded device-side wait gave up (outputs of the affected calls are NaN)");
+  return SABR_LMM_OK;
+}
+}  // namespace
+
+extern "C" sabr_lmm_status sabr_lmm_sync(const sabr_lmm_market* m, void* stream) {
+  if (!m) return fail(SABR_LMM_EINVAL, "market is NULL");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  return take_error_words(m, (cudaStream_t)stream);
+}
+
+extern "C" sabr_lmm_status sabr_lmm_test_raise_error(const sabr_lmm_market* m, int32_t idx, void* stream) {
+  if (!m) return fail(SABR_LMM_EINVAL, "market is NULL");
+  if (idx < 0 || idx >= (int)m->dm.size()) return fail(SABR_LMM_EINVAL, "market_idx out of range");
+  CUDA_TRY(cudaMemsetAsync(m->dm[idx].err, 0x01, 1, (cudaStream_t)stream));
+  return SABR_LMM_OK;
+}
+
 extern "C" sabr_lmm_status sabr_lmm_anneal_fetch(sabr_lmm_anneal_plan* p, sabr_lmm_result* out) {
   if (!p || !out) return fail(SABR_LMM_EINVAL, "plan and out are required");
   cudaStream_t s = p->stream;
   CUDA_TRY(cudaStreamSynchronize(s));
   const sabr_lmm_market* mk = p->mk;
   const int nm = (int)mk->dm.size();
-  int err = 0;
-  for (int j = 0; j < nm; ++j) {
-    int e = 0;
-    CUDA_TRY(cudaMemcpy(&e, mk->dm[j].err, sizeof(int), cudaMemcpyDeviceToHost));
-    err |= e;
-  }
-  if (err) return fail(SABR_LMM_ETIMEOUT, "a bounded device-side wait gave up");
+  if (sabr_lmm_status st = take_error_words(mk, s); st != SABR_LMM_OK) return st;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, p->ev0, p->ev1);
   out->seconds = ms * 1e-3;
@@ -1341,8 +1379,9 @@ namespace {
 constexpr int kNoAllocMaxChains = 16384;
 constexpr int kNoAllocMaxLevels = 4096;
 constexpr int kNoAllocMaxParam = kMaxParam;
-constexpr int kNoAllocW = 4;  // warps (chains) per CTA: the 4-chain form of the level kernel
-constexpr int kNoAllocMaxGrid = (kNoAllocMaxChains + kNoAllocW - 1) / kNoAllocW;
+constexpr int kNoAllocW = 4;  // warps (chains) per CTA: the 4-chain form of the caplet level kernel
+// level-minimum slots: one per CTA of the caplet kernel, one per chain for markets with swaptions
+constexpr int kNoAllocMaxParts = kNoAllocMaxChains;
 
 // Byte offsets of the regions in the array (each 256-byte aligned).
 constexpr size_t kNaHead = 0;  // xs[12] fs T0 x0[12] best_x[12] best_f counter
@@ -1351,9 +1390,16 @@ constexpr size_t kNaFe = kNaXe + (size_t)kNoAllocMaxChains * kNoAllocMaxParam * 
 constexpr size_t kNaXb = kNaFe + (size_t)kNoAllocMaxChains * 8;
 constexpr size_t kNaFb = kNaXb + (size_t)kNoAllocMaxChains * kNoAllocMaxParam * 8;
 constexpr size_t kNaPf = kNaFb + (size_t)kNoAllocMaxChains * 8;
-constexpr size_t kNaPc = kNaPf + (size_t)kNoAllocMaxGrid * 8;
-constexpr size_t kNaTr = kNaPc + (size_t)kNoAllocMaxGrid * 4;
-constexpr size_t kNaBytes = kNaTr + (size_t)kNoAllocMaxLevels * 8;   // 3.60 MB
+constexpr size_t kNaPc = kNaPf + (size_t)kNoAllocMaxParts * 8;
+constexpr size_t kNaTr = kNaPc + (size_t)kNoAllocMaxParts * 4;
+constexpr size_t kNaBytes = kNaTr + (size_t)kNoAllocMaxLevels * 8;   // 3,637,760 B (3.64 MB)
+static_assert(kNaBytes == 3637760, "the size quoted in sabr_lmm.h");
+
+// The start point travels as a kernel argument (no host copy is enqueued).
+struct NoAllocX0 { double v[kNoAllocMaxParam]; };
+__global__ void noalloc_put_x0_kernel(double* dst, NoAllocX0 x0, int P) {
+  if ((int)threadIdx.x < P) dst[threadIdx.x] = x0.v[threadIdx.x];
+}
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -1397,11 +1443,11 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, in
   if (!(o->step_frac > 0.0) || !(o->step_floor >= 0.0)) return fail(SABR_LMM_EINVAL, "step_frac > 0 and step_floor >= 0 required");
   if (o->prec < SABR_LMM_FP64 || o->prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
   if (o->lm_top_k > 0 || o->record_accepts) return fail(SABR_LMM_EINVAL, "anneal_noalloc supports neither the polish nor accept records");
+  if (sabr_lmm_status st = check_call(mk, market_idx, 0, o->prec); st != SABR_LMM_OK) return st;
   const DevMarket& m = mk->dm[market_idx];
   const HostMarket& h = mk->hm[market_idx];
   if (o->x0)
     if (sabr_lmm_status st = check_x0(h, o->x0); st != SABR_LMM_OK) return st;
-  if (m.n_swp > 0) return fail(SABR_LMM_ENOTSUP, "swaptions are not enabled in this build");
   const int P = m.n_param;
   unsigned char* base = nullptr;
   sabr_lmm_status st0 = noalloc_scratch(&base);
@@ -1429,11 +1475,12 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, in
   sp.cooling = o->cooling; sp.step_frac = o->step_frac; sp.step_floor = o->step_floor; sp.T0_opt = o->T0;
   sp.seed = o->seed; sp.market_index = (unsigned long long)market_idx;
   sp.x0 = x0;
-  double hx0[kNoAllocMaxParam];
-  for (int k = 0; k < P; ++k) hx0[k] = o->x0 ? o->x0[k] : 0.5 * (h.lo[k] + h.hi[k]);
-  // every value the kernels read before writing is set here or by sa_start_kernel (f(x0), T0,
+  NoAllocX0 hx0{};
+  for (int k = 0; k < P; ++k) hx0.v[k] = o->x0 ? o->x0[k] : 0.5 * (h.lo[k] + h.hi[k]);
+  // every value the kernels read before writing is set here or by the start kernel (f(x0), T0,
   // the first start point and the level counter), so the previous call's contents do not leak in
-  CUDA_TRY(cudaMemcpyAsync(x0, hx0, P * sizeof(double), cudaMemcpyHostToDevice, s));
+  noalloc_put_x0_kernel<<<1, 32, 0, s>>>(x0, hx0, P);
+  CUDA_TRY(cudaGetLastError());
   const int grid = (o->n_chains + kNoAllocW - 1) / kNoAllocW;
   CUDA_TRY(enqueue_anneal(m, o->prec, st, sp, kNoAllocW, grid, s, true));
   CUDA_TRY(enqueue_anneal(m, o->prec, st, sp, kNoAllocW, grid, s, false));

@@ -311,20 +311,39 @@ template <class R, int FORMULA>
 __host__ __device__ constexpr bool packed_pricer() { return sizeof(R) == 4 && FORMULA == 0; }
 
 // ------------------------------------------------------------------ objective and vols
+// When a CTA's staging gave up (the error word is raised), its points' outputs are set to NaN
+// rather than left unwritten: point i of the grid-stride loop starting at i0 with stride `step`,
+// thread t of nt per point.
+__device__ __forceinline__ void nan_outputs(long long i0, long long step, long long n, int t, int nt, double* f,
+                                            double* v1, int w1, double* v2, int w2) {
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  for (long long i = i0; i < n; i += step) {
+    if (f && t == 0) f[i] = qnan;
+    if (v1) for (int k = t; k < w1; k += nt) v1[i * w1 + k] = qnan;
+    if (v2) for (int k = t; k < w2; k += nt) v2[i * w2 + k] = qnan;
+  }
+}
+
+// f, the model vols (vols != null) or the weighted residuals (res != null) of n points; one warp
+// per point, grid-stride.
 template <class R, int MODEL, int FORMULA>
 __global__ void objective_kernel(DevMarket m, const double* __restrict__ X, long long n, double* __restrict__ f,
-                                 double* __restrict__ vols) {
+                                 double* __restrict__ vols, double* __restrict__ res) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   CtaSmem<R> cs = carve<R>(smem, m, W);
-  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>() && vols == nullptr)) return;
+  const int n_instr = m.n_cap + m.n_swp;
+  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>() && vols == nullptr)) {
+    nan_outputs((long long)blockIdx.x * W + warp, (long long)gridDim.x * W, n, lane, 32, f, vols, n_instr, res, n_instr);
+    return;
+  }
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
-  const int n_instr = m.n_cap + m.n_swp;
   for (long long i = (long long)blockIdx.x * W + warp; i < n; i += (long long)gridDim.x * W) {
     if (lane < kMaxParam) ws.xs[lane] = lane < m.n_param ? (R)X[i * m.n_param + lane] : R(0);
     __syncwarp();
-    const auto fi = warp_objective<R, MODEL, FORMULA>(m, capB, *cs.quad, ws, lane, vols ? vols + i * n_instr : nullptr);
+    const auto fi = warp_objective<R, MODEL, FORMULA>(m, capB, *cs.quad, ws, lane, vols ? vols + i * n_instr : nullptr,
+                                                      res ? res + i * n_instr : nullptr);
     if (f && lane == 0) f[i] = obj_to_double(fi);
     __syncwarp();
   }
@@ -355,25 +374,35 @@ struct SAParams {
   const double* x0;  // device [P]
 };
 
+// The search's start (f(x0), T0, the first start point, the level counter).  If the staging gave up
+// (error word raised) f(x0) is taken as +inf, so that the level kernels still run to completion and
+// the caller reads SABR_LMM_ETIMEOUT.
+__device__ __forceinline__ void sa_start_write(const SAState& st, const SAParams& sp, int t, double x0, double f0) {
+  if (t < sp.P) st.xs[t] = x0;
+  if (t == 0) {
+    st.fs[0] = f0;
+    st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
+    st.counter[0] = 0u;
+  }
+}
+
 template <class R, int MODEL, int FORMULA>
 __global__ void sa_start_kernel(DevMarket m, SAState st, SAParams sp) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   CtaSmem<R> cs = carve<R>(smem, m, 1);
-  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>())) return;
-  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
-  WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch, m.NP, m.n_fwd);
   // the start point in the chain-state precision (FP32 chains start from the rounded point)
   const double x0 = lane < sp.P ? (double)(R)sp.x0[lane] : 0.0;
+  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>())) {
+    sa_start_write(st, sp, lane, x0, __longlong_as_double(0x7ff0000000000000LL));
+    return;
+  }
+  const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
+  WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch, m.NP, m.n_fwd);
   if (lane < kMaxParam) ws.xs[lane] = (R)x0;
   __syncwarp();
   const double f0 = obj_to_double(warp_objective<R, MODEL, FORMULA>(m, capB, *cs.quad, ws, lane, nullptr));
-  if (lane < sp.P) st.xs[lane] = x0;
-  if (lane == 0) {
-    st.fs[0] = f0;
-    st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
-    st.counter[0] = 0u;
-  }
+  sa_start_write(st, sp, lane, x0, f0);
 }
 
 __device__ __forceinline__ bool lex_less(double fa, int ca, double fb, int cb) {
@@ -433,12 +462,25 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   CtaSmem<R> cs = carve<R>(smem, m, W);
-  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>())) return;
+  // a CTA whose staging gave up (error word raised) runs no step: its chains end the level at the
+  // start point with f = +inf, and it still takes its level ticket, so the level-end minimum over
+  // the other CTAs completes
+  const bool staged = stage_market<R>(cs, m, packed_pricer<R, FORMULA>());
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
 
   const int c = blockIdx.x * W + warp;
-  const bool active = c < sp.C;
+  const bool active = staged && c < sp.C;
+  if (!staged && c < sp.C) {
+    if (lane < sp.P) {
+      st.xe[(size_t)c * sp.P + lane] = st.xs[lane];
+      if (level == 0) st.xb[(size_t)c * sp.P + lane] = st.xs[lane];
+    }
+    if (lane == 0) {
+      st.fe[c] = __longlong_as_double(0x7ff0000000000000LL);
+      if (level == 0) st.fb[c] = __longlong_as_double(0x7ff0000000000000LL);
+    }
+  }
   const int P = sp.P;
   const double T0 = st.T0[0];
   double T = T0;
@@ -618,7 +660,7 @@ template <> __device__ __forceinline__ const void* swp_block<float>(const DevMar
 template <class R>
 __host__ __device__ inline uint32_t smem_bytes_cta(const DevMarket& m, bool tc = false) {
   uint32_t b = (uint32_t)sizeof(QuadTab<R>) +
-               (uint32_t)cta_scratch_elems(m) * sizeof(R) + 32 * 16 + 512;
+               (uint32_t)cta_scratch_elems<R>(m) * sizeof(R) + 32 * 16 + 512;
   if (tc) {
     b += kTcBytes + 32;
     if (b < 80u * 1024u) b = 80u * 1024u;
@@ -650,7 +692,7 @@ __device__ __forceinline__ CtaSmemS<R> carve_cta(unsigned char* smem, const DevM
   s.cap = const_cast<void*>(cap_block<R>(m));
   s.swp = const_cast<void*>(swp_block<R>(m));
   s.quad = (QuadTab<R>*)p; p += sizeof(QuadTab<R>);
-  s.scratch = (R*)p; p += (size_t)cta_scratch_elems(m) * sizeof(R);
+  s.scratch = (R*)p; p += (size_t)cta_scratch_elems<R>(m) * sizeof(R);
   s.red = p; p += 32 * 16;
   s.mbar = (uint64_t*)p;
   s.red_f = (double*)(p + 16);
@@ -724,22 +766,27 @@ __device__ __forceinline__ bool stage_market_cta(const CtaSmemS<R>& cs, const De
 
 template <class R, int FORMULA, bool TC>
 __global__ void __launch_bounds__(256, 2) objective_cta_kernel(DevMarket m, const double* __restrict__ X, long long n,
-                                                            double* __restrict__ f, double* __restrict__ vols) {
+                                                            double* __restrict__ f, double* __restrict__ vols,
+                                                            double* __restrict__ res) {
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
   CtaSmemS<R> cs = carve_cta<R>(smem, m);
-  if (!stage_market_cta<R>(cs, m)) return;
+  const int n_instr = m.n_cap + m.n_swp;
+  if (!stage_market_cta<R>(cs, m)) {
+    nan_outputs(blockIdx.x, gridDim.x, n, threadIdx.x, blockDim.x, f, vols, n_instr, res, n_instr);
+    return;
+  }
   TcState tc{};
   if (TC) tc = tc_setup<R>(cs, m.err);
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
   CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
-  const int n_instr = m.n_cap + m.n_swp;
   for (long long i = blockIdx.x; i < n; i += gridDim.x) {
     if (threadIdx.x < kMaxParam) sc.xs[threadIdx.x] = threadIdx.x < m.n_param ? (R)X[i * m.n_param + threadIdx.x] : R(0);
     __syncthreads();
     const O fi = cta_objective<R, FORMULA, TC>(m, capB, swpB, *cs.quad, sc, (O*)cs.red,
-                                               vols ? vols + i * n_instr : nullptr, &tc);
+                                               vols ? vols + i * n_instr : nullptr, &tc,
+                                               res ? res + i * n_instr : nullptr);
     if (f && threadIdx.x == 0) f[i] = obj_to_double(fi);
     __syncthreads();
   }
@@ -751,22 +798,20 @@ __global__ void __launch_bounds__(256, 2) sa_start_cta_kernel(DevMarket m, SASta
   typedef typename ObjOf<R>::T O;
   extern __shared__ __align__(128) unsigned char smem[];
   CtaSmemS<R> cs = carve_cta<R>(smem, m);
-  if (!stage_market_cta<R>(cs, m)) return;
+  const double x0 = threadIdx.x < (unsigned)sp.P ? (double)(R)sp.x0[threadIdx.x] : 0.0;
+  if (!stage_market_cta<R>(cs, m)) {
+    sa_start_write(st, sp, threadIdx.x, x0, __longlong_as_double(0x7ff0000000000000LL));
+    return;
+  }
   TcState tc{};
   if (TC) tc = tc_setup<R>(cs, m.err);
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
   CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
-  const double x0 = threadIdx.x < (unsigned)sp.P ? (double)(R)sp.x0[threadIdx.x] : 0.0;
   if (threadIdx.x < kMaxParam) sc.xs[threadIdx.x] = (R)x0;
   __syncthreads();
   const double f0 = obj_to_double(cta_objective<R, FORMULA, TC>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr, &tc));
-  if (threadIdx.x < (unsigned)sp.P) st.xs[threadIdx.x] = x0;
-  if (threadIdx.x == 0) {
-    st.fs[0] = f0;
-    st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
-    st.counter[0] = 0u;
-  }
+  sa_start_write(st, sp, threadIdx.x, x0, f0);
   if (TC) tc_teardown(tc);
 }
 
@@ -774,11 +819,14 @@ __global__ void __launch_bounds__(256, 2) sa_start_cta_kernel(DevMarket m, SASta
 // and the batch).  The chain's end state is written; the CTA that finishes the market's last chain
 // (counted on st.counter, n_chains arrivals) takes the minimum over the market's chains and sets
 // the next start point and the level trace.
+// With staged == false (the CTA's staging gave up and raised the error word) the chain runs no
+// step: it ends the level at the start point with f = +inf, and the ticket is still taken so that
+// the market's level-end minimum completes.
 template <class R, int FORMULA, bool TC = false, bool GT = false>
 __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAParams& sp, int c, int level,
                                 const CtaSmemS<R>& cs, const InstrView<R>& capB, const InstrView<R>& swpB,
                                 const CtaScratch<R>& sc, unsigned long long* s_wacc, bool* s_last,
-                                TcState* tc = nullptr) {
+                                TcState* tc = nullptr, bool staged = true) {
   typedef typename ObjOf<R>::T O;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = sp.P;
@@ -801,10 +849,14 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
   }
   O fbest = f;
   if (level > 0) obj_from_double(st.fb[c], fbest);
+  if (!staged) {
+    f = obj_inf(O());
+    if (level == 0) fbest = f;
+  }
   const unsigned long long cw = (unsigned long long)c | (sp.market_index << 32);
   U4 o;
   R y = x;
-  for (int s = 0; s < sp.N; ++s) {
+  for (int s = 0; s < (staged ? sp.N : 0); ++s) {
     if (warp == 0) {
       if ((s & 7) == 0) o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)(s + (lane >> 2)), (uint64_t)level, cw, sp.seed, 0ull);
       const int src = ((s & 7) << 2) | ((lane >> 2) & 3), wsel = lane & 3;
@@ -884,14 +936,14 @@ __global__ void __launch_bounds__(256, 2) sa_level_cta_kernel(DevMarket m, SASta
   __shared__ unsigned long long s_wacc;
   __shared__ bool s_last;
   CtaSmemS<R> cs = carve_cta<R>(smem, m);
-  if (!stage_market_cta<R>(cs, m)) return;
+  const bool staged = stage_market_cta<R>(cs, m);
   TcState tc{};
-  if (TC) tc = tc_setup<R>(cs, m.err);
+  if (TC && staged) tc = tc_setup<R>(cs, m.err);
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
   CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
-  cta_chain_level<R, FORMULA, TC>(m, st, sp, blockIdx.x, level, cs, capB, swpB, sc, &s_wacc, &s_last, &tc);
-  if (TC) tc_teardown(tc);
+  cta_chain_level<R, FORMULA, TC>(m, st, sp, blockIdx.x, level, cs, capB, swpB, sc, &s_wacc, &s_last, &tc, staged);
+  if (TC && staged) tc_teardown(tc);
 }
 
 // ====================================================================== batch of markets
@@ -919,6 +971,7 @@ __global__ void __launch_bounds__(256, 2) sa_level_batch_kernel(BatchArgs ba, in
   __shared__ bool s_last;
   __shared__ int s_item;
   int cur = -1;
+  bool staged = true;   // whether the current market's staging completed (else its items run no step)
   const long long total = (long long)ba.n_markets * ba.C;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(ba.item_ctr + level, 1u);
@@ -930,7 +983,7 @@ __global__ void __launch_bounds__(256, 2) sa_level_batch_kernel(BatchArgs ba, in
       if (threadIdx.x == 0) { sm_m = ba.mk[j]; sm_st = ba.st[j]; sm_sp = ba.sp[j]; }
       __syncthreads();
       CtaSmemS<R> cs0 = carve_cta<R>(smem, sm_m);
-      if (!stage_market_cta<R>(cs0, sm_m)) return;
+      staged = stage_market_cta<R>(cs0, sm_m);
       cur = j;
     }
     const DevMarket& m = sm_m;
@@ -938,7 +991,8 @@ __global__ void __launch_bounds__(256, 2) sa_level_batch_kernel(BatchArgs ba, in
     const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
     const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
     CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
-    cta_chain_level<R, FORMULA, false, true>(m, sm_st, sm_sp, c, level, cs, capB, swpB, sc, &s_wacc, &s_last);
+    cta_chain_level<R, FORMULA, false, true>(m, sm_st, sm_sp, c, level, cs, capB, swpB, sc, &s_wacc, &s_last, nullptr,
+                                             staged);
   }
 }
 
@@ -955,20 +1009,18 @@ __global__ void __launch_bounds__(256, 2) sa_start_batch_kernel(BatchArgs ba) {
   const SAState st = ba.st[j];
   const SAParams sp = ba.sp[j];
   CtaSmemS<R> cs = carve_cta<R>(smem, m);
-  if (!stage_market_cta<R>(cs, m)) return;
+  const double x0 = threadIdx.x < (unsigned)sp.P ? (double)(R)sp.x0[threadIdx.x] : 0.0;
+  if (!stage_market_cta<R>(cs, m)) {
+    sa_start_write(st, sp, threadIdx.x, x0, __longlong_as_double(0x7ff0000000000000LL));
+    return;
+  }
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
   CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
-  const double x0 = threadIdx.x < (unsigned)sp.P ? (double)(R)sp.x0[threadIdx.x] : 0.0;
   if (threadIdx.x < kMaxParam) sc.xs[threadIdx.x] = (R)x0;
   __syncthreads();
   const double f0 = obj_to_double(cta_objective<R, FORMULA>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr));
-  if (threadIdx.x < (unsigned)sp.P) st.xs[threadIdx.x] = x0;
-  if (threadIdx.x == 0) {
-    st.fs[0] = f0;
-    st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
-    st.counter[0] = 0u;
-  }
+  sa_start_write(st, sp, threadIdx.x, x0, f0);
 }
 
 // The best point ever accepted in each market of the batch (one CTA per market).
@@ -1024,8 +1076,10 @@ __global__ void grad_kernel(DevMarket m, const double* __restrict__ X, long long
   unsigned char* wbase = (unsigned char*)quad + sizeof(QuadTab<R>) + (size_t)warp * grad_warp_bytes<R>(m);
   uint64_t* mbar = (uint64_t*)((unsigned char*)quad + sizeof(QuadTab<R>) + (size_t)W * grad_warp_bytes<R>(m));
   if (!stage_to_smem2(cap, cap_block<R>(m), instr_block_bytes<R>(m.n_cap_pad), quad, quad_block<R>(m),
-                      (uint32_t)sizeof(QuadTab<R>), mbar, m.err))
+                      (uint32_t)sizeof(QuadTab<R>), mbar, m.err)) {
+    nan_outputs((long long)blockIdx.x * W + warp, (long long)gridDim.x * W, n, lane, 32, f, G, m.n_param, nullptr, 0);
     return;
+  }
   const InstrView<R> capB = instr_view<R>(cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)wbase, m.NP, m.n_fwd);
   const uint32_t wbytes = ((uint32_t)warp_scratch_elems(m.NP, m.n_fwd) * sizeof(R) + 31u) & ~31u;

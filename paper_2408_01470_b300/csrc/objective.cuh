@@ -385,10 +385,11 @@ __device__ __forceinline__ R z_over_x_fast(R z, const RhoConsts<R>& rc) {
 
 // S4 + S7 (caplets): lane-strided pricing; returns this lane's partial sum of squared
 // residuals in the pricing precision and clears `ok` on an infeasible vol.  With vols != null
-// the model vols are written instead (NaN where infeasible).
+// the model vols are written instead (NaN where infeasible); with res != null the weighted
+// residuals sqrt(w_k) (P_k - P_k^mkt) are written as well (NaN where infeasible).
 template <class R, int FORMULA>
 __device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const WarpScratch<R>& ws, const RhoConsts<R>& rc,
-                                           R omb, int lane, bool& ok, double* vols) {
+                                           R omb, int lane, bool& ok, double* vols, double* res = nullptr) {
   typedef Num<R> M;
   R acc = 0;
   for (int k = lane; k < n; k += 32) {
@@ -414,6 +415,7 @@ __device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const W
     const R sg = g2.b;
     const R p = sg * g1.d * (ncdf<R>(sg * d1) - g2.a * ncdf<R>(sg * (d1 - v)));
     const R r = g2.d * (p - g2.c);
+    if (res) res[k] = good ? (double)r : __longlong_as_double(0x7ff8000000000000LL);
     acc += r * r;
   }
   return acc;
@@ -444,14 +446,15 @@ __device__ __forceinline__ float2 z_over_x2(float2 z, float fkx, float fky, floa
   return sel2(zz.x < Num<float>::zx_series, zz.y < Num<float>::zx_series, ser, zx);
 }
 
-// r^2 of a pair of instruments (caplets or swaptions alike) on the packed instructions: per
-// element its SABR factors F = {alpha, nu/alpha, alpha^2, rho nu alpha}, A3 = (2 - 3 rho^2) nu^2,
-// rho, and its three constant vectors g0 = {l, fk, inv_den, c1}, g1 = {c2, c3, sqrt T, D F},
-// g2 = {K/F, sgn, P_mkt, sqrt w}.  Clears ok on an infeasible vol.
+// The weighted residuals r = sqrt(w) (P - P_mkt) of a pair of instruments (caplets or swaptions
+// alike) on the packed instructions: per element its SABR factors F = {alpha, nu/alpha, alpha^2,
+// rho nu alpha}, A3 = (2 - 3 rho^2) nu^2, rho, and its three constant vectors g0 = {l, fk, inv_den,
+// c1}, g1 = {c2, c3, sqrt T, D F}, g2 = {K/F, sgn, P_mkt, sqrt w}.  Clears oka / okb on an
+// infeasible vol of the first / second element.
 __device__ __forceinline__ float2 price_pair_x2(const Q4<float>& fa, const Q4<float>& fb, float a3a, float a3b,
                                                 float rhoa, float rhob, const Q4<float>& g0a, const Q4<float>& g0b,
                                                 const Q4<float>& g1a, const Q4<float>& g1b, const Q4<float>& g2a,
-                                                const Q4<float>& g2b, bool& ok) {
+                                                const Q4<float>& g2b, bool& oka, bool& okb) {
   const float2 rho = make_float2(rhoa, rhob);
   const float2 omr2 = mul2(sub2(bc2(1.0f), rho), add2(bc2(1.0f), rho));
   const float2 c1 = mul2(bc2(-0.5f), rho);
@@ -463,7 +466,8 @@ __device__ __forceinline__ float2 price_pair_x2(const Q4<float>& fa, const Q4<fl
   corr = fma2(make_float2(g1a.a, g1b.a), make_float2(fa.d, fb.d), corr);
   corr = fma2(make_float2(g1a.b, g1b.b), make_float2(a3a, a3b), corr);
   const float2 sig = mul2(mul2(mul2(make_float2(fa.a, fb.a), make_float2(g0a.c, g0b.c)), zx), corr);
-  ok = ok && (sig.x > 0.0f) && (sig.x < INFINITY) && (sig.y > 0.0f) && (sig.y < INFINITY);
+  oka = (sig.x > 0.0f) && (sig.x < INFINITY);
+  okb = (sig.y > 0.0f) && (sig.y < INFINITY);
   const float2 v = mul2(sig, make_float2(g1a.c, g1b.c));
   const float2 d1 = fma2(make_float2(g0a.a, g0b.a), rcp2(v), mul2(bc2(0.5f), v));
   const float2 sg = make_float2(g2a.b, g2b.b);
@@ -471,15 +475,18 @@ __device__ __forceinline__ float2 price_pair_x2(const Q4<float>& fa, const Q4<fl
   const float2 n2 = ncdf2(mul2(sg, sub2(d1, v)));
   const float2 nkf = mul2(make_float2(g2a.a, g2b.a), bc2(-1.0f));
   const float2 p = mul2(mul2(sg, make_float2(g1a.d, g1b.d)), fma2(nkf, n2, n1));
-  const float2 r = mul2(make_float2(g2a.d, g2b.d), sub2(p, make_float2(g2a.c, g2b.c)));
-  return mul2(r, r);
+  return mul2(make_float2(g2a.d, g2b.d), sub2(p, make_float2(g2a.c, g2b.c)));
 }
 
 // price_caplets for FP32 and the Hagan (2002) form on the packed instructions: lane l takes the
 // caplet pair P = 32 i + l of the pair-major block (caplets 64 i + l and 64 i + l + 32), so every
 // 16-byte load gives two ready operand pairs.  A missing second caplet carries sqrt(w) = 0.
+// RES: also write each caplet's weighted residual sqrt(w) (P - P_mkt) to res (NaN where the vol
+// is infeasible), from the same arithmetic the search runs.
+template <bool RES = false>
 __device__ __forceinline__ float price_caplets_x2(const void* blk, int npairs, int n, const WarpScratch<float>& ws,
-                                                  const RhoConsts<float>& rc, int lane, bool& ok) {
+                                                  const RhoConsts<float>& rc, int lane, bool& ok,
+                                                  double* res = nullptr) {
   const PairView B = pair_view(blk, npairs);
   const float c1 = -0.5f * rc.rho, c2 = (2.0f - 3.0f * rc.rho * rc.rho) * (1.0f / 12.0f);
   float2 acc = bc2(0.0f);
@@ -510,6 +517,13 @@ __device__ __forceinline__ float price_caplets_x2(const void* blk, int npairs, i
     // weighted residual C (Phi(xf) + B Phi(xs)) - sqrt(w) P_mkt in one more
     const float2 nn = fma2(make_float2(v4.x, v4.y), ns, nf);
     const float2 r = fma2(make_float2(v3.z, v3.w), nn, v5);
+    if constexpr (RES) {
+      const int a = 64 * it + lane, b = a + 32;
+      const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+      const bool ga = (sig.x > 0.0f) && (sig.x < INFINITY), gb = (sig.y > 0.0f) && (sig.y < INFINITY);
+      res[a] = ga ? (double)r.x : qnan;
+      if (b < n) res[b] = gb ? (double)r.y : qnan;
+    }
     acc = fma2(r, r, acc);
   }
   return acc.x + acc.y;
@@ -525,6 +539,25 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   const float bp = s - a.hi;
   const float e = (a.hi - (s - bp)) + (b.hi - bp);
   const float lo = e + a.lo + b.lo;
+  FF r;
+  r.hi = s + lo;
+  r.lo = lo - (r.hi - s);
+  return r;
+}
+
+__device__ __forceinline__ FF ff_of(float a) {
+  FF r;
+  r.hi = a;
+  r.lo = 0.0f;
+  return r;
+}
+
+// float-float plus float (two-sum, then the low parts added and renormalised)
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+  const float s = a.hi + b;
+  const float bp = s - a.hi;
+  const float e = (a.hi - (s - bp)) + (b - bp);
+  const float lo = e + a.lo;
   FF r;
   r.hi = s + lo;
   r.lo = lo - (r.hi - s);
@@ -573,9 +606,12 @@ __device__ __forceinline__ void obj_from_double(double v, FF& o) {
 
 // Objective of the point held in ws.xs (all 32 lanes call; all return the same value).
 // MODEL 0: SABR smile [alpha, rho, nu];  MODEL 1: Rebonato caplets.
+// vols != null: the model vols are written instead.  res != null: the weighted residuals are
+// written as well, by the pricer the search uses (the packed one in FP32 with the Hagan form).
 template <class R, int MODEL, int FORMULA>
 __device__ typename ObjOf<R>::T warp_objective(const DevMarket& m, const InstrView<R>& capB, const QuadTab<R>& qt,
-                                               const WarpScratch<R>& ws, int lane, double* vols) {
+                                               const WarpScratch<R>& ws, int lane, double* vols,
+                                               double* res = nullptr) {
   typedef typename ObjOf<R>::T O;
   RhoConsts<R> rc;
   if (MODEL == 0) {
@@ -591,10 +627,14 @@ __device__ typename ObjOf<R>::T warp_objective(const DevMarket& m, const InstrVi
   R part;
   if constexpr (std::is_same<R, float>::value && FORMULA == 0) {
     // (with no vols requested the caller staged the pair-major block; its base is capB.g0)
-    part = vols == nullptr ? price_caplets_x2(capB.g0, m.n_cap_pairs, m.n_cap, ws, rc, lane, ok)
-                           : price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);
+    if (vols != nullptr)
+      part = price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);
+    else if (res != nullptr)
+      part = price_caplets_x2<true>(capB.g0, m.n_cap_pairs, m.n_cap, ws, rc, lane, ok, res);
+    else
+      part = price_caplets_x2<false>(capB.g0, m.n_cap_pairs, m.n_cap, ws, rc, lane, ok);
   } else {
-    part = price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);
+    part = price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols, res);
   }
   __syncwarp();
   if (vols) return obj_inf(O());

@@ -33,7 +33,8 @@ template <class R> struct CtaScratch {
   Q4<R>* T2;        // [8 x 9]
   Q4<R>* Sq;        // [8 x 2] per outer node q the inner-rule sums {Saa, Sab, Sbb, Sac}, {Sbc, Scc, 0, 0}
   R* Y;             // [NA x 81]
-  R* PQ;            // [4 x ND x (NA + 1)]: PG, PA, SH, PGS along each diagonal
+  R* PQ;            // [kPQ x ND x PL]: PG, PA, SH, PGS along each diagonal (FP32: then PGl, PGSl,
+                    //   the low words of float-float PG and PGS)
   Q4<R>* crq;       // [ND]: {rho_e, rho_e theta_e, phi_e, 0} per diagonal e
   R* Bg;            // [3 x round_up(Lg (Lg + 1) / 2, 4)] of the current expiry group
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
@@ -65,11 +66,15 @@ __host__ __device__ inline int cta_pq_len(int NA) { return (NA + 2) & ~1; }
 // partials' place (qf_pc_off; -1: their own region of 3 x max_batch_chunks).
 constexpr int kMaxBatchChunks = 512;
 
+// Prefix tables per diagonal: 4 (FP64), 6 (FP32: float-float PG and PGS).
+template <class R> __host__ __device__ constexpr int cta_pq_tables() { return sizeof(R) == 4 ? 6 : 4; }
+
+template <class R>
 __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int NAc = round_up(m.NA, 4);
   const int Lg = m.max_gwin;
   return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + 4 * 16 + round_up(m.NA * cta_y_stride(), 4) +
-                      round_up(4 * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND +
+                      round_up(cta_pq_tables<R>() * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND +
                       3 * round_up(Lg * (Lg + 1) / 2, 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
                       4 * round_up(m.n_grp + 1, 4) + (m.qf_pc_off >= 0 ? 0 : round_up(3 * m.max_batch_chunks, 4)),
                   4);
@@ -88,7 +93,7 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
   s.T2 = (Q4<R>*)p; p += 4 * 72;
   s.Sq = (Q4<R>*)p; p += 4 * 16;
   s.Y = p; p += round_up(m.NA * cta_y_stride(), 4);
-  s.PQ = p; p += round_up(4 * m.ND * cta_pq_len(m.NA), 4);
+  s.PQ = p; p += round_up(cta_pq_tables<R>() * m.ND * cta_pq_len(m.NA), 4);
   s.crq = (Q4<R>*)p; p += 4 * m.ND;
   s.Bg = p; p += 3 * round_up(Lg * (Lg + 1) / 2, 4);
   s.F4s = (Q4<R>*)p; p += 4 * m.n_swap;
@@ -131,10 +136,11 @@ __device__ __forceinline__ R warp_inclusive_scan(R v, int lane) {
 }
 
 // Swaption pricing of instrument k of the swaption block (S6 + S4 Black); returns the squared
-// weighted residual, or writes the model vol when vols != null.
+// weighted residual, or writes the model vol when vols != null; with res != null it also writes the
+// weighted residual sqrt(w) (P - P_mkt) (NaN where the vol is infeasible).
 template <class R, int FORMULA>
 __device__ __forceinline__ R price_swaption(const InstrView<R>& B, int k, const CtaScratch<R>& cs, R omb, bool& ok,
-                                            double* vols) {
+                                            double* vols, double* res = nullptr) {
   typedef Num<R> M;
   const int s = B.idx[k];
   const Q4<R> fw = cs.F4s[s];
@@ -166,12 +172,14 @@ __device__ __forceinline__ R price_swaption(const InstrView<R>& B, int k, const 
   const R sg = g2.b;
   const R p = sg * g1.d * (ncdf<R>(sg * d1) - g2.a * ncdf<R>(sg * (d1 - v)));
   const R r = g2.d * (p - g2.c);
+  if (res) res[k] = good ? (double)r : __longlong_as_double(0x7ff8000000000000LL);
   return r * r;
 }
 
 template <class R, int FORMULA>
 __device__ __forceinline__ R price_one_caplet(const InstrView<R>& B, int k, const WarpScratch<R>& ws,
-                                              const RhoConsts<R>& rc, R omb, bool& ok, double* vols) {
+                                              const RhoConsts<R>& rc, R omb, bool& ok, double* vols,
+                                              double* res = nullptr) {
   typedef Num<R> M;
   const int i = B.idx[k];
   const Q4<R> fw = ws.F4[i];
@@ -195,7 +203,35 @@ __device__ __forceinline__ R price_one_caplet(const InstrView<R>& B, int k, cons
   const R sg = g2.b;
   const R p = sg * g1.d * (ncdf<R>(sg * d1) - g2.a * ncdf<R>(sg * (d1 - v)));
   const R r = g2.d * (p - g2.c);
+  if (res) res[k] = good ? (double)r : __longlong_as_double(0x7ff8000000000000LL);
   return r * r;
+}
+
+// The window integrals of a pair on diagonal e over the absolute panels [lo, hi), from the prefix
+// tables of phase 4: G = PG(hi) - PG(lo) and X / theta = PA(hi) - PA(lo) + SH(hi) G - (PGS(hi) -
+// PGS(lo)).  FP32: PG and PGS are float-float, so G is formed to a few ulp of itself, SH(hi) G is
+// split exactly by an fma into hi + lo, and SH(hi) G - (PGS(hi) - PGS(lo)) cancels between
+// operands within a factor 2 of each other (an exact subtraction), leaving an error ~ (window
+// offset / window) ulp of X rather than its square.
+template <class R>
+__device__ __forceinline__ void window_integrals(const R* PQ, int e, int ND, int PL, int lo, int hi, R& G, R& X) {
+  const R* PG = PQ + e * PL;
+  const R* PA = PG + ND * PL;
+  const R* SH = PA + ND * PL;
+  const R* PGS = SH + ND * PL;
+  if constexpr (sizeof(R) == 4) {
+    const R* PGl = PGS + ND * PL;
+    const R* PGSl = PGl + ND * PL;
+    G = (PG[hi] - PG[lo]) + (PGl[hi] - PGl[lo]);
+    const R sh = SH[hi];
+    const R p = sh * G;
+    const R pe = fmaf(sh, G, -p);
+    const R dh = PGS[hi] - PGS[lo], dl = PGSl[hi] - PGSl[lo];
+    X = (PA[hi] - PA[lo]) + ((p - dh) + (pe - dl));
+  } else {
+    G = PG[hi] - PG[lo];
+    X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
+  }
 }
 
 // Objective of the point in cs.xs (every thread of the CTA calls; all return the same value).
@@ -203,10 +239,13 @@ __device__ __forceinline__ R price_one_caplet(const InstrView<R>& B, int k, cons
 // TC: the pair Grams of phase 3 on the tensor cores (tcgen05_gram.cuh; FP32 pricing only).
 // GT: phase 5 takes its group bounds from the staged group table (the batch kernel, whose market
 // record itself lives in shared memory) rather than from the market's global arrays.
+// res != null: the weighted residuals of every instrument (caplets first) are written as well, by
+// the pricer the search uses.
 template <class R, int FORMULA, bool TC = false, bool GT = false>
 __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrView<R>& capB, const InstrView<R>& swpB,
                                               const QuadTab<R>& qt, const CtaScratch<R>& cs,
-                                              typename ObjOf<R>::T* red, double* vols, TcState* tc = nullptr) {
+                                              typename ObjOf<R>::T* red, double* vols, TcState* tc = nullptr,
+                                              double* res = nullptr) {
   typedef typename ObjOf<R>::T O;
   typedef Num<R> M;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
@@ -421,8 +460,12 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   __syncthreads();
 
   // ---- phase 4: exclusive prefix sums along each diagonal, one diagonal per half-warp (16 lanes,
-  //      three panels per lane and chunk of 48): two diagonals per warp at a time
+  //      three panels per lane and chunk of 48): two diagonals per warp at a time.  In FP32 the
+  //      prefix sums of G and of G x (inclusive H prefix) are float-float (hi in PG / PGS, lo in
+  //      PGl / PGSl): the B-build forms window sums as their differences, which would otherwise
+  //      lose a factor (offset + window) / window of G's bits, and its square in X.
   {
+    constexpr bool kFF = sizeof(R) == 4;
     const int hw = lane >> 4, l16 = lane & 15;
     auto scan16 = [l16](R v) {   // inclusive scan within each 16-lane half
 #pragma unroll
@@ -432,15 +475,29 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       }
       return v;
     };
+    auto scan16_ff = [l16](FF v) {   // inclusive float-float scan within each 16-lane half
+#pragma unroll
+      for (int off = 1; off < 16; off <<= 1) {
+        FF o;
+        o.hi = __shfl_up_sync(0xffffffffu, v.hi, off, 16);
+        o.lo = __shfl_up_sync(0xffffffffu, v.lo, off, 16);
+        if (l16 >= off) v = ff_add(v, o);
+      }
+      return v;
+    };
     for (int eb = 2 * warp; eb < ND; eb += 2 * nw) {
       const int e = eb + hw;
       const int n = e < ND ? NA - e : 0;   // a half without a diagonal reads and writes nothing
       const int nmax = NA - eb;            // the first half's diagonal is the longer one
-      R* PG = cs.PQ + (0 * ND + (e < ND ? e : eb)) * PL;
-      R* PA = cs.PQ + (1 * ND + (e < ND ? e : eb)) * PL;
-      R* SH = cs.PQ + (2 * ND + (e < ND ? e : eb)) * PL;
-      R* PGS = cs.PQ + (3 * ND + (e < ND ? e : eb)) * PL;
+      const int ee = e < ND ? e : eb;
+      R* PG = cs.PQ + (0 * ND + ee) * PL;
+      R* PA = cs.PQ + (1 * ND + ee) * PL;
+      R* SH = cs.PQ + (2 * ND + ee) * PL;
+      R* PGS = cs.PQ + (3 * ND + ee) * PL;
+      R* PGl = cs.PQ + (4 * ND + ee) * PL;    // FP32 only
+      R* PGSl = cs.PQ + (5 * ND + ee) * PL;
       R cg = 0, ca = 0, chh = 0, cgs = 0;
+      FF cgf = {0.f, 0.f}, cgsf = {0.f, 0.f};
       for (int c0 = 0; c0 < nmax; c0 += 48) {
         const int A0 = c0 + 3 * l16;
         R g[3], a[3], h[3];
@@ -451,37 +508,90 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
           a[j] = in ? PA[A0 + j] : R(0);
           h[j] = in ? SH[A0 + j] : R(0);
         }
-        const R sg = g[0] + g[1] + g[2], sa = a[0] + a[1] + a[2], sh = h[0] + h[1] + h[2];
-        const R ig = scan16(sg), ia = scan16(sa), ih = scan16(sh);
+        const R sa = a[0] + a[1] + a[2], sh = h[0] + h[1] + h[2];
+        const R ia = scan16(sa), ih = scan16(sh);
         const R hx = chh + ih - sh;   // exclusive prefix of H before A0
         R gs[3];
         gs[0] = g[0] * (hx + h[0]);   // G(A) times the inclusive H prefix at A
         gs[1] = g[1] * (hx + h[0] + h[1]);
         gs[2] = g[2] * (hx + h[0] + h[1] + h[2]);
-        const R sgs = gs[0] + gs[1] + gs[2];
-        const R igs = scan16(sgs);
-        __syncwarp();
-        R pg = cg + ig - sg, pa = ca + ia - sa, ph = hx, pgs = cgs + igs - sgs;
+        if constexpr (kFF) {
+          FF lg = ff_add_f(ff_of(g[0]), g[1]);
+          lg = ff_add_f(lg, g[2]);
+          FF lgs = ff_add_f(ff_of(gs[0]), gs[1]);
+          lgs = ff_add_f(lgs, gs[2]);
+          const FF ig = scan16_ff(lg), igs = scan16_ff(lgs);
+          FF xg, xgs;   // exclusive prefixes at A0 within the chunk
+          xg.hi = __shfl_up_sync(0xffffffffu, ig.hi, 1, 16);
+          xg.lo = __shfl_up_sync(0xffffffffu, ig.lo, 1, 16);
+          xgs.hi = __shfl_up_sync(0xffffffffu, igs.hi, 1, 16);
+          xgs.lo = __shfl_up_sync(0xffffffffu, igs.lo, 1, 16);
+          if (l16 == 0) { xg = ff_of(0.f); xgs = ff_of(0.f); }
+          __syncwarp();
+          FF pg = ff_add(cgf, xg), pgs = ff_add(cgsf, xgs);
+          R pa = ca + ia - sa, ph = hx;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          if (A0 + j < n) {
-            PG[A0 + j] = pg;
-            PA[A0 + j] = pa;
-            SH[A0 + j] = ph;
-            PGS[A0 + j] = pgs;
+          for (int j = 0; j < 3; ++j) {
+            if (A0 + j < n) {
+              PG[A0 + j] = pg.hi;
+              PGl[A0 + j] = pg.lo;
+              PA[A0 + j] = pa;
+              SH[A0 + j] = ph;
+              PGS[A0 + j] = pgs.hi;
+              PGSl[A0 + j] = pgs.lo;
+            }
+            pg = ff_add_f(pg, g[j]);
+            pa += a[j];
+            ph += h[j];
+            pgs = ff_add_f(pgs, gs[j]);
           }
-          pg += g[j];
-          pa += a[j];
-          ph += h[j];
-          pgs += gs[j];
+          FF tg, tgs;
+          tg.hi = __shfl_sync(0xffffffffu, ig.hi, 15, 16);
+          tg.lo = __shfl_sync(0xffffffffu, ig.lo, 15, 16);
+          tgs.hi = __shfl_sync(0xffffffffu, igs.hi, 15, 16);
+          tgs.lo = __shfl_sync(0xffffffffu, igs.lo, 15, 16);
+          cgf = ff_add(cgf, tg);
+          cgsf = ff_add(cgsf, tgs);
+        } else {
+          const R sg = g[0] + g[1] + g[2];
+          const R ig = scan16(sg);
+          const R sgs = gs[0] + gs[1] + gs[2];
+          const R igs = scan16(sgs);
+          __syncwarp();
+          R pg = cg + ig - sg, pa = ca + ia - sa, ph = hx, pgs = cgs + igs - sgs;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            if (A0 + j < n) {
+              PG[A0 + j] = pg;
+              PA[A0 + j] = pa;
+              SH[A0 + j] = ph;
+              PGS[A0 + j] = pgs;
+            }
+            pg += g[j];
+            pa += a[j];
+            ph += h[j];
+            pgs += gs[j];
+          }
+          cg += __shfl_sync(0xffffffffu, ig, 15, 16);
+          cgs += __shfl_sync(0xffffffffu, igs, 15, 16);
         }
-        cg += __shfl_sync(0xffffffffu, ig, 15, 16);
         ca += __shfl_sync(0xffffffffu, ia, 15, 16);
         chh += __shfl_sync(0xffffffffu, ih, 15, 16);
-        cgs += __shfl_sync(0xffffffffu, igs, 15, 16);
         __syncwarp();
       }
-      if (e < ND && l16 == 0) { PG[n] = cg; PA[n] = ca; SH[n] = chh; PGS[n] = cgs; }
+      if (e < ND && l16 == 0) {
+        PA[n] = ca;
+        SH[n] = chh;
+        if constexpr (kFF) {
+          PG[n] = cgf.hi;
+          PGl[n] = cgf.lo;
+          PGS[n] = cgsf.hi;
+          PGSl[n] = cgsf.lo;
+        } else {
+          PG[n] = cg;
+          PGS[n] = cgs;
+        }
+      }
     }
   }
   __syncthreads();
@@ -542,12 +652,8 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
             for (int i = 0; i < kPf; ++i) {
               if (t >= npk[i]) continue;
               const int e = pk[i] & 255, lo = pk[i] >> 8, hi = lo + nE[i];
-              const R* PG = cs.PQ + e * PL;
-              const R* PA = PG + ND * PL;
-              const R* SH = PA + ND * PL;
-              const R* PGS = SH + ND * PL;
-              const R G = PG[hi] - PG[lo];
-              const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
+              R G, X;
+              window_integrals<R>(cs.PQ, e, ND, PL, lo, hi, G, X);
               const Q4<R> cr = cs.crq[e];
               R* B = Bbuf + (gb + i - g0) * 3 * npm;
               B[t] = cr.a * G;
@@ -571,12 +677,8 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
           for (int t = tid; t < npk; t += nth) {
             const int pk = gp[t];
             const int e = pk & 255, lo = pk >> 8, hi = lo + nE;
-            const R* PG = cs.PQ + e * PL;
-            const R* PA = PG + ND * PL;
-            const R* SH = PA + ND * PL;
-            const R* PGS = SH + ND * PL;
-            const R G = PG[hi] - PG[lo];
-            const R X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
+            R G, X;
+            window_integrals<R>(cs.PQ, e, ND, PL, lo, hi, G, X);
             const Q4<R> cr = cs.crq[e];
             B[t] = cr.a * G;
             B[npm + t] = cr.b * X;
@@ -690,9 +792,17 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
             g0[u] = swpB.g0[j]; g1[u] = swpB.g1[j]; g2[u] = swpB.g2[j];
           }
         }
-        float2 r2 = price_pair_x2(F[0], F[1], a3[0], a3[1], rh[0], rh[1], g0[0], g0[1], g1[0], g1[1], g2[0], g2[1], ok);
-        r2.y = has2 ? r2.y : 0.0f;
-        acc = add2(acc, r2);
+        bool oka = true, okb = true;
+        float2 r = price_pair_x2(F[0], F[1], a3[0], a3[1], rh[0], rh[1], g0[0], g0[1], g1[0], g1[1], g2[0], g2[1],
+                                 oka, okb);
+        r.y = has2 ? r.y : 0.0f;
+        ok = ok && oka && (okb || !has2);
+        if (res) {
+          const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+          res[k] = oka ? (double)r.x : qnan;
+          if (has2) res[k + nth] = okb ? (double)r.y : qnan;
+        }
+        acc = fma2(r, r, acc);
       }
       part = acc.x + acc.y;
     } else {
@@ -703,8 +813,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     }
   } else {
     for (int k = tid; k < ntot; k += nth) {
-      if (k < m.n_cap) part += price_one_caplet<R, FORMULA>(capB, k, cs.cap, rc, omb, ok, vols);
-      else part += price_swaption<R, FORMULA>(swpB, k - m.n_cap, cs, omb, ok, vols ? vols + m.n_cap : nullptr);
+      if (k < m.n_cap) part += price_one_caplet<R, FORMULA>(capB, k, cs.cap, rc, omb, ok, vols, res);
+      else part += price_swaption<R, FORMULA>(swpB, k - m.n_cap, cs, omb, ok, vols ? vols + m.n_cap : nullptr,
+                                              res ? res + m.n_cap : nullptr);
     }
   }
   const int bad = __syncthreads_or(!ok);

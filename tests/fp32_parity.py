@@ -1,0 +1,75 @@
+"""Shared rules of the reduced-precision parity tests (imported by the GPU test modules).
+
+Feasibility.  A point is infeasible when some model vol is not a finite positive number (the
+objective is then +inf).  The FP32 path must classify every instrument of every point exactly as
+the FP64 oracle does, with one stated exception: an instrument whose oracle vol lies within
+NEAR_ZERO_REL of zero, relative to the largest |vol| of the same point, sits on the feasibility
+boundary (the Hagan correction factor crosses zero there), and FP32 rounding may decide its sign
+either way.  `feasibility_mismatches` returns the disagreements; `assert_feasibility_rule` fails on
+any that is not on that boundary.
+
+Per-price error.  The library's residuals are r_k = sqrt(w_k) (P_k - P_k^mkt) with the default
+weights w_k = 1 / vega_k^2 at the quoted vol, so r_k is a price error in vol units and
+|r_k^FP32 - r_k^oracle| is |dP_k| / vega_k, the per-price error in vol units (x 100: vol points).
+"""
+import numpy as np
+
+NEAR_ZERO_REL = 1e-5
+
+
+def feasible(v):
+    v = np.asarray(v, dtype=np.float64)
+    return np.isfinite(v) & (v > 0)
+
+
+def feasibility_mismatches(ok_lo, v_oracle):
+    """Instruments whose reduced-precision feasibility (ok_lo, bool) differs from the oracle's."""
+    return np.nonzero(np.asarray(ok_lo, bool) != feasible(v_oracle))[0]
+
+
+def on_boundary(v_oracle, k):
+    v = np.asarray(v_oracle, dtype=np.float64)
+    scale = np.max(np.abs(v[np.isfinite(v)])) if np.any(np.isfinite(v)) else 0.0
+    return bool(np.isfinite(v[k]) and abs(v[k]) <= NEAR_ZERO_REL * scale)
+
+
+def assert_feasibility_rule(ok_lo, v_oracle, where=""):
+    """Every disagreement must be an instrument on the boundary; returns their count."""
+    bad = feasibility_mismatches(ok_lo, v_oracle)
+    for k in bad:
+        assert on_boundary(v_oracle, k), (
+            f"{where}: instrument {k} feasible={bool(ok_lo[k])} in reduced precision, "
+            f"oracle vol {v_oracle[k]!r} is not within {NEAR_ZERO_REL} of zero")
+    return len(bad)
+
+
+def assert_point_feasibility_rule(f_lo, f_oracle, om, X, where=""):
+    """Point level: finite objective in reduced precision iff finite in the oracle, except at points
+    with an instrument on the boundary.  Returns the number of disagreeing points."""
+    fin_lo, fin_or = np.isfinite(f_lo), np.isfinite(f_oracle)
+    bad = np.nonzero(fin_lo != fin_or)[0]
+    for i in bad:
+        v = om.model_vols(X[i])
+        assert any(on_boundary(v, k) for k in range(len(v))), (
+            f"{where}: point {i} objective finite={bool(fin_lo[i])} in reduced precision but "
+            f"{bool(fin_or[i])} in the oracle, with no instrument on the feasibility boundary")
+    return len(bad)
+
+
+def residual_errors(gm, om, X, prec, market=0):
+    """|r_lo - r_oracle| per (point, instrument) in vol points over the points both sides find
+    feasible, after checking the feasibility rule per instrument.  Returns (errors, |r_oracle|)."""
+    _, r_lo = gm.residuals(X, prec, market=market)
+    r_lo = r_lo.cpu().numpy()
+    errs, mags = [], []
+    for i in range(X.shape[0]):
+        v_or = om.model_vols(X[i])
+        assert_feasibility_rule(np.isfinite(r_lo[i]), v_or, where=f"point {i}")
+        r_or, _ = om.residuals_jac(X[i])
+        if r_or is None or not np.all(np.isfinite(r_lo[i])):
+            continue
+        errs.append(np.abs(r_lo[i] - r_or) * 100.0)
+        mags.append(np.abs(r_or) * 100.0)
+    if not errs:
+        return np.zeros(0), np.zeros(0)
+    return np.concatenate(errs), np.concatenate(mags)

@@ -96,3 +96,44 @@ def test_bad_start_points_and_quotes_are_rejected(gpu_lib):
     with pytest.raises(lib.SabrLmmError) as e:
         lib.Market(sk, vols)
     assert e.value.status == 1 and "cap_vol" in str(e.value)
+
+
+@pytest.mark.parametrize("maker", [synth.smile_2y,
+                                   lambda: synth.joint_caplet_swaption(expiries=(1, 2), tenors=(1, 2),
+                                                                       swp_m=(0.0,))])
+def test_error_word_is_reported_once_then_cleared(gpu_lib, maker):
+    # host-side injection only (no device wait is run out here): the market's error word is raised
+    # from the host; the next sync reports ETIMEOUT once, the one after it OK; the same for the
+    # annealing call, which reads and clears the word after its search; stream-ordered calls made
+    # meanwhile still run and return their values
+    import paper_2408_01470_b300 as lib
+    sk = maker()
+    om, gm = _markets(sk)
+    x = sk.theta_true[None, :]
+    gm.sync()
+    gm.test_raise_error()
+    f = gm.objective(x, "fp64").cpu().numpy()[0]
+    assert f == pytest.approx(om.objective(x[0]), rel=1e-12)
+    with pytest.raises(lib.SabrLmmError) as e:
+        gm.sync()
+    assert e.value.status == 4
+    gm.sync()
+    gm.test_raise_error()
+    with pytest.raises(lib.SabrLmmError) as e:
+        gm.anneal(8, 2, 3, 0.9, seed=1)
+    assert e.value.status == 4
+    r = gm.anneal(8, 2, 3, 0.9, seed=1)
+    assert np.isfinite(r["f_best"][0])
+    gm.sync()
+
+
+def test_residuals_rows_of_infeasible_points_are_nan(gpu_lib):
+    sk = synth.smile_2y()
+    om, gm = _markets(sk)
+    X = np.array([[0.0, -0.3, 0.4], [0.03, -0.3, 0.4]])
+    for prec in ("fp64", "fp32"):
+        f, r = gm.residuals(X, prec)
+        f, r = f.cpu().numpy(), r.cpu().numpy()
+        assert np.isposinf(f[0]) and np.all(np.isnan(r[0]))
+        r_or, _ = om.residuals_jac(X[1])
+        assert np.all(np.isfinite(r[1])) and np.max(np.abs(r[1] - r_or)) <= (1e-12 if prec == "fp64" else 2e-6)

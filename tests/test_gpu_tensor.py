@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_2408_01470_b300 import synth
+from fp32_parity import assert_feasibility_rule, assert_point_feasibility_rule, feasible
 
 pytestmark = pytest.mark.gpu
 
@@ -34,8 +35,9 @@ def test_bf16x3_swaption_vols_against_oracle(gpu_lib, name):
     worst, worst32 = 0.0, 0.0
     for i in range(X.shape[0]):
         vo = om.model_vols(X[i])
-        ok = np.isfinite(vo) & (vo > 0) & np.isfinite(vt[i])
-        assert ok.sum() >= 0.9 * len(ok)
+        assert_feasibility_rule(np.isfinite(vt[i]), vo, where=f"{name} bf16x3 point {i}")
+        assert_feasibility_rule(np.isfinite(v32[i]), vo, where=f"{name} fp32 point {i}")
+        ok = feasible(vo) & np.isfinite(vt[i]) & np.isfinite(v32[i])
         worst = max(worst, np.max(np.abs(vt[i][ok] - vo[ok])) * 100)
         worst32 = max(worst32, np.max(np.abs(v32[i][ok] - vo[ok])) * 100)
     print(f"{name}: bf16x3 max vol error {worst:.3e} vol-pt, fp32 {worst32:.3e} vol-pt")
@@ -48,6 +50,7 @@ def test_bf16x3_objective_close_to_fp32(gpu_lib):
     X = np.vstack([synth.uniform_in_box(sk, 16, seed=42), sk.theta_true[None, :]])
     ft = gm.objective(X, "bf16x3").cpu().numpy()
     f64 = om.objective_batch(X, n_threads=8)
+    assert_point_feasibility_rule(ft, f64, om, X, where="bf16x3")
     fin = np.isfinite(f64) & np.isfinite(ft)
     n = sk.n_instr
     d = np.abs(np.sqrt(ft[fin] / n) - np.sqrt(f64[fin] / n)) * 100.0
