@@ -46,23 +46,71 @@ LEVEL_TRAFFIC_BYTES_FP32 = 513_280
 TARGET_RMSE_VOLPT = 0.05
 
 
-def flops_per_chain_step(skel) -> float:
+def flops_per_chain_step(skel, info=None) -> float:
     """Algorithmic floating-point operations of one objective evaluation plus one Metropolis step.
 
     Counted from the arithmetic as written (add, mul = 1; fma = 2; div, sqrt, exp, log1p, erfc = 1):
-      S2, per (panel, node): g and h (5 each), eight inner nodes (8 each), three weighted sums (5)
-          = 79; per forward: 4 per panel + 6;
-      S4, per caplet: SABR with z/x(z) 35, Black 15, weighted residual 3 = 53;
-      S1 + S8: 6 per free slot + 4.
+      S2 (caplet forwards), per (panel, node): g and h (5 each), eight inner nodes (8 each), three
+          weighted sums (5) = 79; per forward: 4 per panel + 6;
+      S4 / S6, per instrument: SABR with z/x(z) 35, Black 15, weighted residual 3 = 53;
+      S1 + S8: 6 per free slot + 4;
+    and for markets with swaptions (info = the market's geometry, sabr_lmm_market_info):
+      S3, Y rows: per (absolute panel, outer node) g and h at the node = 24;
+          pair Grams per (diagonal, panel) cell: G and H (8 products each, 16 flop each) and the
+          inner-rule bilinear form at 8 nodes (6 fma + 2) = 144; prefix sums 24 per cell
+          (float-float G and G x H prefixes);
+          window integrals per (expiry group, pair of its window) 16;
+      S5, per swap: 3 quadratic forms over its window's L (L + 1) / 2 pairs (1 fma each);
+      swap-rate SABR parameters per swap 20.
     """
-    NP = int(round(max(skel.T[i] for i in set(skel.cap_fwd.tolist())) / skel.panel))
-    if skel.model == 1:
-        s2 = NP * 8 * 79 + sum(4 * int(round(skel.T[i] / skel.panel)) + 6 for i in set(skel.cap_fwd.tolist()))
-    else:
-        s2 = 0
-    s4 = 53 * skel.n_cap
-    s1 = 6 * int(skel.free.sum()) + 4
-    return float(s2 + s4 + s1)
+    free = int(np.asarray(skel.free).sum())
+    s1 = 6 * free + 4
+    s4 = 53 * (skel.n_cap + skel.n_swp)
+    s2 = 0
+    if skel.model == 1 and skel.n_cap > 0:
+        fwds = sorted(set(np.asarray(skel.cap_fwd).tolist()))
+        NP = int(round(max(skel.T[i] for i in fwds) / skel.panel))
+        s2 = NP * 8 * 79 + sum(4 * int(round(skel.T[i] / skel.panel)) + 6 for i in fwds)
+    s3 = s5 = 0
+    if skel.n_swp > 0:
+        NA, ND = int(info["n_panels"]), int(info["n_diag"])
+        cells = sum(NA - e for e in range(ND))
+        swaps = sorted(set(zip(np.asarray(skel.swp_start).tolist(), np.asarray(skel.swp_end).tolist())))
+        glen = {}
+        for a, b in swaps:
+            glen[a] = max(glen.get(a, 0), b - a)
+        pairs_g = sum(L * (L + 1) // 2 for L in glen.values())
+        s3 = NA * 8 * 24 + cells * (144 + 24) + 16 * pairs_g + 20 * len(swaps)
+        s5 = sum(3 * 2 * ((b - a) * (b - a + 1) // 2) for a, b in swaps)
+    return float(s1 + s2 + s3 + s4 + s5)
+
+
+def measure_peaks(stream_ptr=None):
+    """Pipe throughputs measured on this GPU (libsabr_peaks.so, CUDA events, 8 CTAs of 256 threads
+    per SM, 8 independent chains per thread, best of 3): FP32 FMA (scalar and on register pairs),
+    FP64 FMA, MUFU ex2.  TFLOP/s count 2 flop per FMA."""
+    import ctypes as C
+    import torch
+    from paper_2408_01470_b300 import build
+    lib = C.CDLL(build.PEAKS_LIB)
+    lib.sabr_peak_probe.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    iters = {0: 1 << 15, 1: 1 << 14, 2: 1 << 9, 3: 1 << 13}
+    out = {}
+    for kind, name in ((0, "fp32_fma"), (1, "fp32x2_fma"), (2, "fp64_fma"), (3, "mufu_ex2")):
+        best = 0.0
+        for _ in range(3):
+            sec, ops = C.c_double(), C.c_double()
+            rc = lib.sabr_peak_probe(kind, nsm * 8, 256, iters[kind], stream_ptr, C.byref(sec), C.byref(ops))
+            if rc != 0:
+                raise RuntimeError(f"sabr_peak_probe({kind}) failed: CUDA error {rc}")
+            best = max(best, ops.value / sec.value)
+        out[name] = best
+    return {"fp32_tflops": 2 * max(out["fp32_fma"], out["fp32x2_fma"]) / 1e12,
+            "fp32_scalar_tflops": 2 * out["fp32_fma"] / 1e12, "fp32x2_tflops": 2 * out["fp32x2_fma"] / 1e12,
+            "fp64_tflops": 2 * out["fp64_fma"] / 1e12, "mufu_gops": out["mufu_ex2"] / 1e9, "sms": nsm,
+            "how": "libsabr_peaks.so: FMA / ex2 chains, 8 CTAs x 256 threads per SM, best of 3, CUDA events"}
 
 
 class ClockSampler:
@@ -162,10 +210,12 @@ WORKLOADS = {
     "joint": "rebonato_joint_40fwd_300caplets_700swaptions_16384ch_x_200T_x_100steps",
     "batch": "rebonato_batch_256_markets_10to60fwd_50to1000instr_4096ch_x_100T_x_50steps",
 }
+PREC_DTYPE = {"fp32": "f32", "fp64": "f64", "bf16x3": "f32+bf16x3", "tf32x3": "f32+tf32x3"}
 
 
 def workload_markets(lib, name):
-    """(Market, skeletons, vols list, chains, levels, steps, cooling) of a named workload."""
+    """(Market, skeletons, quotes list, chains, levels, steps, cooling) of a named workload.  The
+    quotes are the library's own FP64 model vols at the generating point plus the noise draws."""
     from paper_2408_01470_b300 import synth
     if name == "caplets":
         sks = [synth.caplet_term_structure()]
@@ -206,8 +256,9 @@ def cpu_baseline(skel, vols, levels=1, steps=100, chains=None, threads=None):
     dt = time.perf_counter() - t0
     prices = r["n_evals"] * skel.n_instr
     return {"value": prices / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "chain_steps_per_s": chains * levels * steps / dt,
             "sample": f"{chains} chains x {levels} temperature level x {steps} steps of the same market "
-                      f"({r['n_evals']} objective evaluations, {dt:.1f} s wall)"}
+                      f"({r['n_evals']} objective evaluations, {dt:.1f} s wall, {threads} threads)"}
 
 
 def run_reference(args):
@@ -220,7 +271,7 @@ def run_reference(args):
     skel = synth.caplet_term_structure()
     om0 = oracle.Market(skel)
     vols = om0.model_vols(skel.theta_true) + skel.noise
-    times, vals = [], []
+    vals = []
     base = None
     for i in range(args.warmup + args.steps):
         b = cpu_baseline(skel, vols, levels=1, steps=20)
@@ -233,16 +284,18 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": base["sample"]},
+            "extrapolated": {"ms_per_step": True, "value": False,
+                             "how": "value is measured on the sample; ms_per_step is the full workload "
+                                    "(4096 x (200 x 100 + 1) evaluations x 300 caplets) at that rate"},
             "cpu_baseline": {**base, "value": value},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 def run_profile(args):
-    """One search of the bench workload (levels shortened with --levels), for ncu captures."""
-    import torch
+    """One search of a workload (levels shortened with --levels), for ncu captures."""
     import paper_2408_01470_b300 as lib
-    from paper_2408_01470_b300 import synth
+    import torch
     lib.load()
     gm, sks, _, C, L0, N, cooling = workload_markets(lib, args.workload)
     L = args.levels or L0
@@ -262,12 +315,164 @@ def run_profile(args):
                       "rmse_volpt": float(r["rmse_volpt"][0])}))
 
 
+def rmse_per_level(gm, trace_x, quotes, market=0):
+    """The true vol RMSE (vol points) of each level's start point: FP64 model vols against the quotes."""
+    v = gm.model_vols(trace_x, "fp64", market=market).cpu().numpy()
+    return 100.0 * np.sqrt(np.mean((v - np.asarray(quotes)[None, :]) ** 2, axis=1))
+
+
+def first_hit(rmse, seconds, target):
+    """(level, device seconds from the search's start) of the first level whose best point reaches
+    the target RMSE, or None."""
+    hit = np.nonzero(rmse <= target)[0]
+    return None if hit.size == 0 else {"level": int(hit[0]) + 1, "seconds": float(seconds[hit[0]])}
+
+
+def roofline_alu(flops_per_launch, level_s, peak_tflops, traffic, kernel, source):
+    achieved = flops_per_launch / level_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": traffic, "kernel": kernel, "peak_source": source}
+
+
+def search_record(lib, name, prec, seed, stream, peaks, levels=None, cpu=None, e2e=True, chains=None):
+    """One timed search of a named workload (after a 2-level warm-up of the same kernels), with its
+    rate, roofline, quality, end-to-end rate and (cpu = dict of sample sizes) the oracle baseline."""
+    import torch
+    gm, sks, vols, C, L0, N, cool = workload_markets(lib, name)
+    C = chains or C
+    L = levels or L0
+    warm = gm.anneal_prepare(C, min(2, L), N, cool, seed, prec=prec, use_graph=True, stream=stream)
+    warm.launch(stream=stream)
+    warm.fetch()
+    del warm
+    plan = gm.anneal_prepare(C, L, N, cool, seed, prec=prec, use_graph=True, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plan.launch(stream=stream)
+    b.record(stream)
+    stream.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    r = plan.fetch()
+    del plan
+    n_instr = sum(sk.n_instr for sk in sks)
+    rec = {"workload": WORKLOADS[name] if L == L0 and C == sks[0].n_chains else
+           f"{name}: {C} chains x {L} levels x {N} steps", "prec": prec, "chains": C, "levels_timed": L,
+           "levels_of_schedule": L0, "extrapolated": L != L0, "value": r["n_evals"] * n_instr / t, "unit": UNIT,
+           "seconds": t, "ms_per_level": 1e3 * t / L, "chain_steps_per_s": C * L * N * len(sks) / t,
+           "rmse_volpt": float(np.median(r["rmse_volpt"]))}
+    if len(sks) == 1:
+        info = gm.info()
+        fl = C * N * flops_per_chain_step(sks[0], info)
+        peak, src = ((peaks["fp32_tflops"], "measured FP32 FMA rate (libsabr_peaks.so)") if prec != "fp64" else
+                     (peaks["fp64_tflops"], "measured FP64 FMA rate (libsabr_peaks.so)"))
+        kern = "sa_level_cta_kernel" if sks[0].n_swp > 0 else "sa_level_kernel"
+        rec["roofline"] = roofline_alu(fl, t / L, peak, None, kern, src)
+        rec["flops_per_chain_step"] = flops_per_chain_step(sks[0], info)
+    if cpu:
+        rec["cpu_baseline"] = cpu_baseline(sks[0], vols[0], **cpu)
+    if e2e:
+        h2d = sum(np.asarray(x).nbytes for sk, v in zip(sks, vols)
+                  for x in (sk.T, sk.P, sk.cap_fwd, sk.cap_K, sk.swp_start, sk.swp_end, sk.swp_K, v, sk.lo, sk.hi,
+                            sk.free))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = lib.Market(sks if len(sks) > 1 else sks[0], vols if len(sks) > 1 else vols[0])
+        r2 = m2.anneal(C, L, N, cool, seed, prec=prec)
+        del m2
+        te = time.perf_counter() - t0
+        rec["e2e"] = {"value": r2["n_evals"] * n_instr / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(len(sks) * (sks[0].n_param + 2 + L) * 8)}
+    return rec, r, gm, sks, vols
+
+
+def lm_schedule_to_target(gm, C, N, cool, seed, target, schedule=(1, 2, 3, 5, 10, 20, 40, 80, 200)):
+    """The mixed-precision, adjoint-polished form: the shortest FP32 search of the schedule (the same
+    cooling, fewer levels) whose Levenberg-Marquardt polish of its 64 best chains reaches the target
+    vol RMSE; device time of that search plus its polish, both measured (each run once untimed)."""
+    for Ls in schedule:
+        for _ in range(2):
+            rp = gm.anneal(C, Ls, N, cool, seed, prec="fp32", lm_top_k=64, lm_max_iter=50, target_rmse=target)
+        if rp["rmse_volpt"][0] <= target:
+            return {"levels": Ls, "search_s": float(rp["seconds"]), "polish_s": float(rp["lm_seconds"]),
+                    "seconds": float(rp["seconds"] + rp["lm_seconds"]), "rmse_volpt": float(rp["rmse_volpt"][0])}
+    return None
+
+
+def run_quality(args):
+    """FP32 against FP64: the final vol RMSE of seeds 0..n-1 of a workload's search, without and with
+    the polish of the 64 best chains, on one GPU.  Prints one JSON line."""
+    import paper_2408_01470_b300 as lib
+    lib.load()
+    gm, sks, vols, C, L, N, cool = workload_markets(lib, args.workload)
+    C = args.chains or C
+    rows = []
+    for k in range(args.seeds):
+        seed = 240801470 + 7919 * k
+        row = {"seed": seed}
+        for prec in ("fp64", "fp32"):
+            r = gm.anneal(C, L, N, cool, seed, prec=prec)
+            rp = gm.anneal(C, L, N, cool, seed, prec=prec, lm_top_k=64, lm_max_iter=50)
+            row[prec] = {"rmse_volpt": float(r["rmse_volpt"][0]), "seconds": float(r["seconds"]),
+                         "polished_rmse_volpt": float(rp["rmse_volpt"][0]), "polish_s": float(rp["lm_seconds"])}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    out = {"quality": True, "workload": args.workload, "chains": C, "levels": L, "steps": N, "seeds": args.seeds}
+    for key in ("rmse_volpt", "polished_rmse_volpt"):
+        a64 = np.array([r["fp64"][key] for r in rows])
+        a32 = np.array([r["fp32"][key] for r in rows])
+        out[key] = {"fp64_mean": float(a64.mean()), "fp32_mean": float(a32.mean()),
+                    "fp64_std": float(a64.std(ddof=1)) if len(a64) > 1 else 0.0,
+                    "fp32_std": float(a32.std(ddof=1)) if len(a32) > 1 else 0.0,
+                    "mean_ratio_fp32_over_fp64": float(a32.mean() / a64.mean()),
+                    "fp64": a64.tolist(), "fp32": a32.tolist()}
+    out["seconds_fp64_mean"] = float(np.mean([r["fp64"]["seconds"] for r in rows]))
+    out["seconds_fp32_mean"] = float(np.mean([r["fp32"]["seconds"] for r in rows]))
+    print(json.dumps(out))
+
+
+def run_workload_line(args):
+    """--workload joint|batch without --profile: that workload's full schedule as its own line."""
+    import paper_2408_01470_b300 as lib
+    import torch
+    lib.load()
+    peaks = measure_peaks()
+    s = torch.cuda.Stream()
+    cpu = ({"chains": 64, "levels": 1, "steps": 16} if args.workload == "joint" else
+           {"chains": 4096, "levels": 1, "steps": 20} if args.workload == "caplets" else None)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), args.clocks_dir) as clk:
+        rec, r, gm, sks, vols = search_record(lib, args.workload, args.prec, 240801470, s, peaks, cpu=None,
+                                              e2e=True)
+    if args.workload == "batch":
+        sub = [synth_market for synth_market in sks[:4]]
+        import oracle
+        t0 = time.perf_counter()
+        n_ev = 0
+        for sk, v in zip(sub, vols[:4]):
+            rr = oracle.Market(sk, v).anneal(16, 1, 4, sk.cooling, seed=240801470, n_threads=os.cpu_count() or 1)
+            n_ev += rr["n_evals"] * sk.n_instr
+        dt = time.perf_counter() - t0
+        rec["cpu_baseline"] = {"value": n_ev / dt, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": f"batch markets 0-3, 16 chains x 1 level x 4 steps each ({dt:.1f} s wall)"}
+    elif cpu:
+        rec["cpu_baseline"] = cpu_baseline(sks[0], vols[0], **cpu)
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": rec["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": PREC_DTYPE[args.prec], "data": "synthetic",
+            "config": {"workload": rec["workload"], "precision": args.prec,
+                       "l2": "inputs resident; warm-up: a 2-level search of the same kernels"},
+            **{k: rec[k] for k in rec if k in ("roofline", "e2e", "cpu_baseline")},
+            "chain_steps_per_s": rec["chain_steps_per_s"], "ms_per_level": rec["ms_per_level"],
+            "rmse_volpt_median": rec["rmse_volpt"], "clocks": clk.summary(), "peaks": peaks,
+            "gpu_launches": r["n_evals"] and (rec["levels_timed"] + 2)}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16x3"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-variant", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -278,17 +483,26 @@ def main():
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--profile", action="store_true",
                     help="run the workload's search once (optionally shortened) and exit: the ncu target")
+    ap.add_argument("--quality", action="store_true",
+                    help="FP32 against FP64 final RMSE over --seeds seeds of --workload (one JSON line)")
+    ap.add_argument("--seeds", type=int, default=8)
     ap.add_argument("--levels", type=int, default=0, help="with --profile: temperature levels (0 = workload's)")
-    ap.add_argument("--chains", type=int, default=0, help="with --profile: chains per market (0 = workload's)")
+    ap.add_argument("--chains", type=int, default=0, help="with --profile / --quality: chains per market")
     ap.add_argument("--lm-top-k", type=int, default=0,
                     help="with --profile: Levenberg-Marquardt polish of the k best chains after the search")
-    ap.add_argument("--workload", default="caplets", choices=list(WORKLOADS),
-                    help="with --profile: the search to run (the timed line is always the caplet workload)")
+    ap.add_argument("--workload", default="", choices=[""] + list(WORKLOADS),
+                    help="with --profile / --quality: the search to run; alone: that workload's full line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
+        args.workload = args.workload or "caplets"
         return run_profile(args)
+    if args.quality:
+        args.workload = args.workload or "caplets"
+        return run_quality(args)
+    if args.workload:
+        return run_workload_line(args)
 
     ws, rank, local = dist_setup()
     import torch
@@ -298,6 +512,7 @@ def main():
     import paper_2408_01470_b300 as lib
     from paper_2408_01470_b300 import synth
     lib.load()
+    peaks = measure_peaks()
 
     skel = synth.caplet_term_structure()
     gm, vols = market_from_library(lib, skel)
@@ -331,21 +546,20 @@ def main():
     value, total_s_max = job_rate(total_s, args.steps * prices_per_step, ws)
     ms_per_step = 1e3 * total_s_max / args.steps
 
-    # roofline of the dominant kernel (the per-temperature level kernel, >99% of the step)
+    # roofline of the dominant kernel (the per-temperature level kernel, >99% of the step) against
+    # the FP32 (FP64) FMA rate measured on this GPU
     level_s = (total_s / args.steps) / L
-    flops_launch = C * N * flops_per_chain_step(skel)
-    peak = FP32_PEAK_TFLOPS if args.prec == "fp32" else FP64_PEAK_TFLOPS
-    achieved = flops_launch / level_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": LEVEL_TRAFFIC_BYTES_FP32 if args.prec == "fp32" and not args.warps_per_block else None,
-                "kernel": "sa_level_kernel", "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"
-                if args.prec == "fp32" else "nominal B300 FP64 1.25 TFLOP/s"}
+    info = gm.info()
+    flops_launch = C * N * flops_per_chain_step(skel, info)
+    peak, src = ((peaks["fp32_tflops"], "measured FP32 FMA rate (libsabr_peaks.so)") if args.prec != "fp64" else
+                 (peaks["fp64_tflops"], "measured FP64 FMA rate (libsabr_peaks.so)"))
+    roofline = roofline_alu(flops_launch, level_s, peak,
+                            LEVEL_TRAFFIC_BYTES_FP32 if args.prec == "fp32" and not args.warps_per_block else None,
+                            "sa_level_kernel", src)
 
-    quality = {"f_best": float(res["f_best"][0]), "rmse_volpt": float(res["rmse_volpt"][0])}
-    trace_rmse = 100.0 * np.sqrt(np.maximum(res["trace_f"][0], 0.0) / skel.n_instr)
-    hit = np.nonzero(trace_rmse <= TARGET_RMSE_VOLPT)[0]
-    ttt = {"target_rmse_volpt": TARGET_RMSE_VOLPT,
-           args.prec + "_s": (float((hit[0] + 1) * level_s) if hit.size else None)}
+    rmse32 = rmse_per_level(gm, res["trace_x"][0], vols)
+    quality = {"f_best": float(res["f_best"][0]), "rmse_volpt": float(res["rmse_volpt"][0]),
+               "rmse_volpt_last_level": float(rmse32[-1])}
 
     # e2e: through the public API from host buffers (H2D of the market, D2H of the results)
     e2e_vals = []
@@ -361,11 +575,15 @@ def main():
     e2e_local = statistics.median(e2e_vals) if e2e_vals else float("nan")
     e2e = {"value": ws * e2e_local, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # time to target, measured on the device: each level's best point is recorded with the GPU's
+    # global timer when the level ends; its true vol RMSE (FP64 model vols against the quotes) decides
+    # when a target is reached.  Targets: 0.05 vol-pt and the final RMSE of the plain FP64 form.
     variants = {}
-    if not args.no_fp64_variant and args.prec == "fp32":
+    ttt = {"how": "device global timer at the end of the first level whose best point's true vol RMSE "
+                  "reaches the target (searches); search + polish device time of the shortest schedule "
+                  "reaching it (polished form)"}
+    if args.prec == "fp32" and not args.no_fp64_variant:
         plan64 = gm.anneal_prepare(C, L, N, skel.cooling, seed, prec="fp64", use_graph=True, stream=s)
-        plan64.launch(stream=s)
-        s.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s)
         plan64.launch(stream=s)
@@ -373,86 +591,50 @@ def main():
         s.synchronize()
         t64 = a.elapsed_time(b) / 1e3
         r64 = plan64.fetch()
-        tr64 = 100.0 * np.sqrt(np.maximum(r64["trace_f"][0], 0.0) / skel.n_instr)
-        hit64 = np.nonzero(tr64 <= TARGET_RMSE_VOLPT)[0]
-        ttt["fp64_s"] = float((hit64[0] + 1) * t64 / L) if hit64.size else None
-        ach64 = flops_launch / (t64 / L) / 1e12
-        variants["fp64"] = {"value": prices_per_step / t64, "ms_per_step": t64 * 1e3,
-                            "rmse_volpt": float(r64["rmse_volpt"][0]), "f_best": float(r64["f_best"][0]),
-                            "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
-                                         "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS}}
         del plan64
+        rmse64 = rmse_per_level(gm, r64["trace_x"][0], vols)
+        R64 = float(r64["rmse_volpt"][0])
+        variants["fp64"] = {"value": prices_per_step / t64, "ms_per_step": t64 * 1e3, "rmse_volpt": R64,
+                            "f_best": float(r64["f_best"][0]), "chain_steps_per_s": C * L * N / t64,
+                            "roofline": roofline_alu(flops_launch, t64 / L, peaks["fp64_tflops"], None,
+                                                     "sa_level_kernel", "measured FP64 FMA rate (libsabr_peaks.so)")}
+        for name, target in (("target_0p05", TARGET_RMSE_VOLPT), ("target_fp64_final", R64)):
+            ttt[name] = {"target_rmse_volpt": target,
+                         "fp64": first_hit(rmse64, r64["trace_seconds"][0], target),
+                         "fp32": first_hit(rmse32, res["trace_seconds"][0], target),
+                         "fp32_lm_polished": lm_schedule_to_target(gm, C, N, skel.cooling, seed, target)}
 
-    # the mixed-precision, adjoint-polished form: a shortened FP32 search (the same cooling, fewer
-    # levels), then the Levenberg-Marquardt polish (adjoint gradient) of its 64 best chains; the
-    # shortest schedule that reaches the target
-    if args.prec == "fp32":
-        pol = None
-        for Ls in (1, 2, 3, 5, 10, 20, 40, 80):
-            for _ in range(2):   # the first call of a schedule is its warm-up
-                rp = gm.anneal(C, Ls, N, skel.cooling, seed, prec="fp32", lm_top_k=64, lm_max_iter=50,
-                               target_rmse=TARGET_RMSE_VOLPT)
-            if rp["rmse_volpt"][0] <= TARGET_RMSE_VOLPT:
-                pol = {"levels": Ls, "search_s": float(rp["seconds"]), "polish_s": float(rp["lm_seconds"]),
-                       "rmse_volpt": float(rp["rmse_volpt"][0])}
-                break
-        ttt["fp32_lm_polished_s"] = pol["search_s"] + pol["polish_s"] if pol else None
-        ttt["fp32_lm_polished"] = pol
-
-    # the joint caplet + swaption market (CTA-per-chain kernels), a shortened search for its rate in
-    # each precision form: FP32 (5 levels), FP64 plain and FP32 with the BF16-split tensor-core
-    # Grams (1 level each)
+    # the joint caplet + swaption market (CTA-per-chain kernels) over its full schedule, and shortened
+    # samples of the other precision forms (labelled extrapolated)
+    workloads = {}
     if args.prec == "fp32" and not args.no_joint_variant:
-        jm, jsks, _, jC, _, jN, jcool = workload_markets(lib, "joint")
-        for jprec, jL in (("fp32", 5), ("fp64", 1), ("bf16x3", 1)):
-            jplan = jm.anneal_prepare(jC, jL, jN, jcool, seed, prec=jprec, use_graph=True, stream=s)
-            jplan.launch(stream=s)
-            s.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(s)
-            jplan.launch(stream=s)
-            b.record(s)
-            s.synchronize()
-            tj = a.elapsed_time(b) / 1e3
-            rj = jplan.fetch()
-            variants["joint_" + jprec] = {"workload": WORKLOADS["joint"], "levels_timed": jL,
-                                          "value": rj["n_evals"] * jsks[0].n_instr / tj, "unit": UNIT,
-                                          "ms_per_level": tj * 1e3 / jL,
-                                          "rmse_volpt": float(rj["rmse_volpt"][0])}
-            del jplan
-        del jm
-
-    # the 256-market batch (one persistent launch per shared-memory bucket and level), one level
+        rec, _, _, _, _ = search_record(lib, "joint", "fp32", seed, s, peaks,
+                                        cpu=None if args.no_cpu_baseline else {"chains": 64, "levels": 1, "steps": 16})
+        workloads["joint_fp32"] = rec
+        for jprec in ("fp64", "bf16x3"):
+            rec, _, _, _, _ = search_record(lib, "joint", jprec, seed, s, peaks, levels=1, e2e=False)
+            workloads["joint_" + jprec] = rec
+    # the 256-market batch: one level (its full 100-level schedule: bench.py --workload batch)
     if args.prec == "fp32" and not args.no_batch_variant:
-        bm, bsks, _, bC, _, bN, bcool = workload_markets(lib, "batch")
-        bL = 1
-        bplan = bm.anneal_prepare(bC, bL, bN, bcool, seed, prec="fp32", use_graph=True, stream=s)
-        bplan.launch(stream=s)
-        s.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(s)
-        bplan.launch(stream=s)
-        b.record(s)
-        s.synchronize()
-        tb = a.elapsed_time(b) / 1e3
-        rb = bplan.fetch()
-        variants["batch_fp32"] = {"workload": WORKLOADS["batch"], "levels_timed": bL,
-                                  "value": rb["n_evals"] * sum(sk.n_instr for sk in bsks) / tb, "unit": UNIT,
-                                  "ms_per_level": tb * 1e3 / bL}
-        del bplan, bm
+        rec, _, _, _, _ = search_record(lib, "batch", "fp32", seed, s, peaks, levels=1, e2e=False)
+        workloads["batch_fp32"] = rec
 
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": PREC_DTYPE[args.prec], "data": "synthetic",
             "config": {"workload": WORKLOAD, "chains": C, "levels": L, "steps_per_level": N,
                        "instruments": skel.n_instr, "n_evals_per_step": n_evals, "precision": args.prec,
                        "l2": "flushed between timed steps (256 MB write)", "graph": True,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps * (L + 2), "clocks": clocks,
-            "quality": quality, "time_to_target": ttt, "variants": variants}
+            "chain_steps_per_s": ws * C * L * N * args.steps / total_s_max, "peaks": peaks,
+            "quality": quality, "time_to_target": ttt, "variants": variants, "workloads": workloads}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(skel, vols, levels=1, steps=100)
+        cb = cpu_baseline(skel, vols, levels=1, steps=100)
+        cb1 = cpu_baseline(skel, vols, levels=1, steps=4, threads=1)
+        cb["single_thread"] = {k: cb1[k] for k in ("value", "chain_steps_per_s", "cores", "sample")}
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

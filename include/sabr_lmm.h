@@ -205,7 +205,11 @@ typedef struct {
  *   trace_f [n_markets x n_levels]: the start objective of each next level (the per-level min).
  *   accept_bits [n_chains x n_levels x steps] (market 0 only; for tests, small runs).
  *   n_evals: objective evaluations made by the annealer (C (L N + 1) per market).
- *   seconds: device time of the annealing loop; lm_seconds: device time of the polish.      */
+ *   seconds: device time of the annealing loop; lm_seconds: device time of the polish.
+ *   trace_x [n_markets x n_levels x n_param]: the start point of each next level (the best end
+ *   point of the level; before any polish).
+ *   trace_seconds [n_markets x n_levels]: device time from the search's start (f(x0)) to the end
+ *   of each level, read from the GPU's global timer by the CTA that closes the level.          */
 typedef struct {
   double* x_best;
   double* f_best;
@@ -216,6 +220,8 @@ typedef struct {
   double seconds;
   double lm_seconds;
   double T0_used;
+  double* trace_x;
+  double* trace_seconds;
 } sabr_lmm_result;
 
 sabr_lmm_status sabr_lmm_anneal(const sabr_lmm_market* m, const sabr_lmm_anneal_opts* opts,

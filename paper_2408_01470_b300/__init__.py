@@ -67,7 +67,7 @@ class Result(C.Structure):
     _fields_ = [
         ("x_best", _D), ("f_best", _D), ("rmse_volpt", _D), ("trace_f", _D),
         ("accept_bits", _U8), ("n_evals", C.c_int64), ("seconds", C.c_double),
-        ("lm_seconds", C.c_double), ("T0_used", C.c_double),
+        ("lm_seconds", C.c_double), ("T0_used", C.c_double), ("trace_x", _D), ("trace_seconds", _D),
     ]
 
 
@@ -321,13 +321,16 @@ class Market:
         nm = len(self.skels)
         P = self.skels[0].n_param
         arrs = dict(x_best=np.zeros((nm, P)), f_best=np.zeros(nm), rmse=np.zeros(nm),
-                    trace_f=np.zeros((nm, n_levels)))
+                    trace_f=np.zeros((nm, n_levels)), trace_x=np.zeros((nm, n_levels, P)),
+                    trace_seconds=np.zeros((nm, n_levels)))
         bits = np.zeros((n_chains, n_levels, steps), np.uint8) if record_accepts else None
         r = Result()
         r.x_best = arrs["x_best"].ctypes.data_as(_D)
         r.f_best = arrs["f_best"].ctypes.data_as(_D)
         r.rmse_volpt = arrs["rmse"].ctypes.data_as(_D)
         r.trace_f = arrs["trace_f"].ctypes.data_as(_D)
+        r.trace_x = arrs["trace_x"].ctypes.data_as(_D)
+        r.trace_seconds = arrs["trace_seconds"].ctypes.data_as(_D)
         if bits is not None:
             r.accept_bits = bits.ctypes.data_as(_U8)
         return r, arrs, bits
@@ -335,8 +338,8 @@ class Market:
     @staticmethod
     def _pack(r, arrs, bits):
         return dict(x_best=arrs["x_best"], f_best=arrs["f_best"], rmse_volpt=arrs["rmse"],
-                    trace_f=arrs["trace_f"], bits=bits, n_evals=r.n_evals, seconds=r.seconds,
-                    lm_seconds=r.lm_seconds, T0=r.T0_used)
+                    trace_f=arrs["trace_f"], trace_x=arrs["trace_x"], trace_seconds=arrs["trace_seconds"],
+                    bits=bits, n_evals=r.n_evals, seconds=r.seconds, lm_seconds=r.lm_seconds, T0=r.T0_used)
 
     def anneal(self, n_chains, n_levels, steps, cooling, seed, prec="fp64", T0=0.0, step_frac=0.1,
                step_floor=1e-3, x0=None, lm_top_k=0, lm_max_iter=50, target_rmse=0.0,

@@ -1011,7 +1011,7 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   const size_t C = o->n_chains, L = o->n_levels, N = o->steps_per_level;
   // per market: xs[P] fs T0 xe[CP] fe[C] xb[CP] fb[C] part_f[grid] part_c[grid] counter trace[L] best_x[P] best_f x0[P]
   Arena A;
-  struct Off { size_t xs, fs, T0, xe, fe, xb, fb, pf, pc, cnt, tr, bx, bf, x0, bits, vols, rmse; };
+  struct Off { size_t xs, fs, T0, xe, fe, xb, fb, pf, pc, cnt, tr, trx, trt, bx, bf, x0, bits, vols, rmse; };
   std::vector<Off> off(nm);
   for (int j = 0; j < nm; ++j) {
     const int Pj = mk->dm[j].n_param;
@@ -1020,7 +1020,8 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     q.xe = A.take(C * Pj * 8); q.fe = A.take(C * 8); q.xb = A.take(C * Pj * 8); q.fb = A.take(C * 8);
     const size_t nparts = std::max<size_t>((size_t)p->grid, C);   // CTA minima (one CTA per chain with swaptions)
     q.pf = A.take(nparts * 8); q.pc = A.take(nparts * 4); q.cnt = A.take(16);
-    q.tr = A.take(L * 8); q.bx = A.take(Pj * 8); q.bf = A.take(8); q.x0 = A.take(Pj * 8);
+    q.tr = A.take(L * 8); q.trx = A.take(L * Pj * 8); q.trt = A.take((L + 1) * 8);
+    q.bx = A.take(Pj * 8); q.bf = A.take(8); q.x0 = A.take(Pj * 8);
     q.bits = (j == 0 && o->record_accepts) ? A.take(C * L * N) : 0;
     size_t max_ni = 1;   // the RMSE of every market's best point reuses market 0's buffer
     for (const DevMarket& mm : mk->dm) max_ni = std::max<size_t>(max_ni, (size_t)(mm.n_cap + mm.n_swp));
@@ -1039,6 +1040,7 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     s.xe = (double*)(b + q.xe); s.fe = (double*)(b + q.fe); s.xb = (double*)(b + q.xb); s.fb = (double*)(b + q.fb);
     s.part_f = (double*)(b + q.pf); s.part_c = (int*)(b + q.pc); s.counter = (unsigned int*)(b + q.cnt);
     s.trace_f = (double*)(b + q.tr); s.best_x = (double*)(b + q.bx); s.best_f = (double*)(b + q.bf);
+    s.trace_x = (double*)(b + q.trx); s.trace_t = (unsigned long long*)(b + q.trt);
     s.bits = (j == 0 && o->record_accepts) ? (uint8_t*)(b + q.bits) : nullptr;
     p->st.push_back(s);
     SAParams sp{};
@@ -1276,8 +1278,16 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_fetch(sabr_lmm_anneal_plan* p, sabr_l
     const int Pj = m.n_param;
     if (out->x_best) CUDA_TRY(cudaMemcpy(out->x_best + (size_t)j * Pj, p->st[j].best_x, Pj * 8, cudaMemcpyDeviceToHost));
     if (out->f_best) CUDA_TRY(cudaMemcpy(out->f_best + j, p->st[j].best_f, 8, cudaMemcpyDeviceToHost));
+    const size_t L = p->opts.n_levels;
     if (out->trace_f)
-      CUDA_TRY(cudaMemcpy(out->trace_f + (size_t)j * p->opts.n_levels, p->st[j].trace_f, p->opts.n_levels * 8, cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemcpy(out->trace_f + (size_t)j * L, p->st[j].trace_f, L * 8, cudaMemcpyDeviceToHost));
+    if (out->trace_x)
+      CUDA_TRY(cudaMemcpy(out->trace_x + (size_t)j * L * Pj, p->st[j].trace_x, L * Pj * 8, cudaMemcpyDeviceToHost));
+    if (out->trace_seconds) {
+      std::vector<unsigned long long> t(L + 1);
+      CUDA_TRY(cudaMemcpy(t.data(), p->st[j].trace_t, (L + 1) * 8, cudaMemcpyDeviceToHost));
+      for (size_t l = 0; l < L; ++l) out->trace_seconds[(size_t)j * L + l] = (double)(t[l + 1] - t[0]) * 1e-9;
+    }
     if (j == 0) CUDA_TRY(cudaMemcpy(&out->T0_used, p->st[0].T0, 8, cudaMemcpyDeviceToHost));
     if (out->rmse_volpt) {
       CUDA_TRY(launch_objective_any(m, SABR_LMM_FP64, p->st[j].best_x, 1, nullptr, p->vols_dev, s));

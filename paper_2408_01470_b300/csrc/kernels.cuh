@@ -362,6 +362,8 @@ struct SAState {
   int* part_c;
   unsigned int* counter;
   double* trace_f;   // [L]
+  double* trace_x;   // [L x P] the start point after each level (the best end point), or null
+  unsigned long long* trace_t;   // [L + 1] global timer (ns) at the start and at each level's end, or null
   uint8_t* bits;     // [C x L x N] or null
   double* best_x;    // [P]
   double* best_f;    // [1]
@@ -377,13 +379,27 @@ struct SAParams {
 // The search's start (f(x0), T0, the first start point, the level counter).  If the staging gave up
 // (error word raised) f(x0) is taken as +inf, so that the level kernels still run to completion and
 // the caller reads SABR_LMM_ETIMEOUT.
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ void sa_start_write(const SAState& st, const SAParams& sp, int t, double x0, double f0) {
   if (t < sp.P) st.xs[t] = x0;
   if (t == 0) {
     st.fs[0] = f0;
     st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
     st.counter[0] = 0u;
+    if (st.trace_t) st.trace_t[0] = global_timer_ns();
   }
+}
+
+// The level's trace after its minimum is known: the next start point (read back from the best end
+// point) and the time the level ended.  Called by the threads of the last CTA of the level.
+__device__ __forceinline__ void level_trace_write(const SAState& st, int P, int level, int t, double x) {
+  if (st.trace_x && t < P) st.trace_x[(size_t)level * P + t] = x;
+  if (st.trace_t && t == 0) st.trace_t[level + 1] = global_timer_ns();
 }
 
 template <class R, int MODEL, int FORMULA>
@@ -594,7 +610,13 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
   }
   __syncthreads();
   const int cbest = cs.red_c[0];
-  if (threadIdx.x < P) st.xs[threadIdx.x] = __ldcg(st.xe + (size_t)cbest * P + threadIdx.x);
+  if (threadIdx.x < P) {
+    const double xn = __ldcg(st.xe + (size_t)cbest * P + threadIdx.x);
+    st.xs[threadIdx.x] = xn;
+    level_trace_write(st, P, level, threadIdx.x, xn);
+  } else {
+    level_trace_write(st, P, level, threadIdx.x, 0.0);
+  }
   if (threadIdx.x == 0) st.counter[0] = 0u;
 }
 
@@ -925,7 +947,13 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
   }
   __syncthreads();
   const int cbest = cs.red_c[0];
-  if (threadIdx.x < (unsigned)P) st.xs[threadIdx.x] = __ldcg(st.xe + (size_t)cbest * P + threadIdx.x);
+  if (threadIdx.x < (unsigned)P) {
+    const double xn = __ldcg(st.xe + (size_t)cbest * P + threadIdx.x);
+    st.xs[threadIdx.x] = xn;
+    level_trace_write(st, P, level, threadIdx.x, xn);
+  } else {
+    level_trace_write(st, P, level, threadIdx.x, 0.0);
+  }
   if (threadIdx.x == 0) st.counter[0] = 0u;
   __syncthreads();
 }
