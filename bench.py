@@ -210,7 +210,7 @@ WORKLOADS = {
     "joint": "rebonato_joint_40fwd_300caplets_700swaptions_16384ch_x_200T_x_100steps",
     "batch": "rebonato_batch_256_markets_10to60fwd_50to1000instr_4096ch_x_100T_x_50steps",
 }
-PREC_DTYPE = {"fp32": "f32", "fp64": "f64", "bf16x3": "f32+bf16x3", "tf32x3": "f32+tf32x3"}
+PREC_DTYPE = {"fp32": "f32", "fp64": "f64", "bf16x3": "f32+bf16x3"}
 
 
 def workload_markets(lib, name):
@@ -472,7 +472,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "bf16x3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-variant", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -52,12 +52,13 @@ typedef enum {
  *               repeated in FP64 whenever the uniform falls inside the FP32 error band (so the
  *               decision equals the FP64 decision on the same objective values); chain state
  *               in FP32.  Outputs (f, vols, best points) are returned as FP64.
- *   FP32_TF32X3 / FP32_BF16X3 : FP32, with the swaption quadratic forms contracted on the
- *               tensor cores with split (3-term) products accumulated in FP32.              */
+ *   FP32_BF16X3 : FP32, with the pair-integral Grams of the swaption forms (S3) contracted on the
+ *               tensor cores (tcgen05) on a split (hi + lo bf16) operand, accumulated in FP32;
+ *               markets whose panel tables fit one MMA tile (ENOTSUP otherwise).
+ *   The value 2 is not a precision of this library (EINVAL).                                 */
 typedef enum {
   SABR_LMM_FP64 = 0,
   SABR_LMM_FP32 = 1,
-  SABR_LMM_FP32_TF32X3 = 2,
   SABR_LMM_FP32_BF16X3 = 3
 } sabr_lmm_prec;
 
@@ -156,8 +157,13 @@ sabr_lmm_status sabr_lmm_model_vols(const sabr_lmm_market* m, int32_t market_idx
 
 /* f[i] and its gradient G[i, :] = df/dtheta (device [n x n_param], FP64, every slot, free or
  * not) by a hand-written reverse-mode (adjoint) sweep through pricing, SABR, the model mapping
- * and the quadrature.  Arithmetic per `prec` (FP64, or FP32 accumulating the parameter
- * adjoints in FP64).  Paper: derivative of the cost functions of Section 3.  Same errors.    */
+ * and the quadrature; for markets with swaptions also through the swap-rate SABR parameters,
+ * the quadratic forms of each expiry group, the window integrals, the prefix tables along the
+ * diagonals, the pair Grams and the correlation tables (one CTA per point).  Arithmetic per `prec`
+ * on caplet markets (FP64, or FP32 accumulating the parameter adjoints in FP64); markets with
+ * swaptions are differentiated in FP64 whatever `prec`.  Paper: derivative of the cost functions
+ * of Section 3.  Same errors, and ENOTSUP if a market's reverse sweep does not fit one CTA's
+ * shared memory.                                                                              */
 sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int32_t market_idx,
                                         const double* X, int64_t n, int32_t prec, double* f,
                                         double* G, void* stream);
@@ -197,6 +203,9 @@ typedef struct {
                               0 -> autotuned CTA size, >= 8 -> 256 threads, else 128           */
   int32_t use_graph;       /* 1 -> the level loop is captured once and replayed as a CUDA graph */
   int32_t record_accepts;  /* 1 -> fill sabr_lmm_result.accept_bits (market 0; small runs)     */
+  int32_t polish_nm;       /* 1 -> the lm_top_k points are polished by Nelder-Mead (the paper's
+                              hybrid; lm_max_iter iterations, step 0.02, ftol 1e-12) instead of
+                              Levenberg-Marquardt                                               */
 } sabr_lmm_anneal_opts;
 
 /* Results, per market, in caller-allocated host arrays (any may be NULL).
@@ -275,14 +284,28 @@ sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* m, int32_t market
 
 /* Levenberg-Marquardt polish of n points X (device [n x n_param], FP64, updated in place):
  * J by forward differences over the free slots (step 1e-7 max(|theta_p|, 1)), (J^T J + mu diag
- * J^T J) d = -J^T r by Cholesky (J^T r from the reverse sweep of sabr_lmm_objective_grad on caplet
- * markets, run beside the difference stencil; else from J), projection on the box, mu /10 on
- * success, x10 on failure; a
+ * J^T J) d = -J^T r by Cholesky (J^T r from the reverse sweep of sabr_lmm_objective_grad, run
+ * beside the difference stencil; from J where the reverse sweep does not fit a CTA), projection
+ * on the box, mu /10 on success, x10 on failure; a
  * point stops at target_rmse_volpt (if > 0) or once mu exceeds 1e16.  f, rmse: device [n] or
  * NULL, those of the final points.  Paper: the local polish of the hybrid scheme, Section 3.  */
 sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t market_idx, double* X,
                                    int64_t n, int32_t max_iter, double target_rmse_volpt,
                                    double* f, double* rmse, void* stream);
+
+/* Nelder-Mead polish of n points X (device [n x n_param], FP64, updated in place): the local search
+ * of the paper's hybrid scheme (Section 3), on the free slots, with the standard coefficients
+ * (reflection 1, expansion 2, contraction 1/2, shrink 1/2) and every trial point projected onto the
+ * box.  The initial simplex is X[i] and, per free slot k, X[i] + step (hi_k - lo_k) e_k (taken
+ * downwards where it would leave the box); vertices are ordered by f with a stable sort of the
+ * previous order; a point stops after max_iter iterations or once f_worst - f_best <= ftol
+ * |f_best|.  f: device [n], the objective of the returned points; evals: device [n] (objective
+ * evaluations made) or NULL.  One warp per point on caplet markets, one CTA per point on markets
+ * with swaptions.  Errors: EINVAL (max_iter < 0, step not in (0, 1], ftol < 0, NULL pointers with
+ * n > 0), ENOTSUP, ECUDA.                                                                     */
+sabr_lmm_status sabr_lmm_nm_polish(const sabr_lmm_market* m, int32_t market_idx, double* X, int64_t n,
+                                   int32_t max_iter, double step, double ftol, double* f,
+                                   int32_t* evals, void* stream);
 
 /* Introspection: the geometry of market market_idx and what its kernels need per CTA.
  *   n_panels, n_diag: absolute 0.5y panels and forward-index diagonals of the swaption tables;

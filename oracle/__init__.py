@@ -102,6 +102,9 @@ def _lib_handle():
             lib.orc_anneal.restype = C.c_int
             lib.orc_anneal.argtypes = [C.c_void_p, C.POINTER(_SAOpts), _D, _D, _D, _D, _D, _D,
                                        C.POINTER(C.c_uint8), C.POINTER(C.c_int64), _D]
+            lib.orc_nm.restype = C.c_int
+            lib.orc_nm.argtypes = [C.c_void_p, _D, C.c_int, C.c_double, C.c_double, _D, _D,
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int)]
             lib.orc_lm.restype = C.c_int
             lib.orc_lm.argtypes = [C.c_void_p, _D, C.c_int, C.c_double, C.c_double, _D, _D, _D,
                                    C.POINTER(C.c_int)]
@@ -298,6 +301,14 @@ class Market:
                              C.byref(ne), _dp(t0))
         return dict(x_best=xb, f_best=fb[0], chain_xb=cxb, chain_fb=cfb, trace_f=tf, trace_x=tx,
                     bits=bits, n_evals=ne.value, T0=t0[0])
+
+    def nm(self, theta0, max_iter=500, step=0.02, ftol=1e-12):
+        """Nelder-Mead on the free slots (see sabr_oracle.cpp)."""
+        th, f = np.zeros(self.n_param), np.zeros(1)
+        it, ev = C.c_int(0), C.c_int(0)
+        self._lib.orc_nm(self.h, _dp(_f64(theta0)), int(max_iter), float(step), float(ftol), _dp(th), _dp(f),
+                         C.byref(it), C.byref(ev))
+        return dict(theta=th, f=f[0], iters=it.value, evals=ev.value)
 
     def lm(self, theta0, max_iter=50, target_rmse=0.0, mu0=1e-3):
         P = self.n_param

@@ -35,6 +35,10 @@
 //                                    Pin: zero at the generating point on noise-free quotes.
 //   philox4x64_10 .................. Salmon, Moraes, Dror, Shaw (SC'11).  Pins: numpy's Philox
 //                                    bit generator and the all-zero known-answer vector.
+//   nm ............................. the Nelder-Mead local search of the hybrid scheme (Section
+//                                    3), standard coefficients.  Pins: a separable quadratic bowl
+//                                    in closed form, monotone best value, recovery on noise-free
+//                                    quotes.
 //   anneal ......................... the SA loop of Section 3 and its one-GPU parallel form
 //                                    (chains per level, min-reduction, broadcast).  Pins: the
 //                                    evaluation-count identity C(LN+1); recovery on tiny sets.
@@ -724,6 +728,96 @@ static int lm(const Market& m, const double* theta0, int max_iter, double target
   return 0;
 }
 
+// Nelder-Mead simplex descent on the free slots: the local search that follows the annealing in the
+// paper's hybrid scheme (Section 3), with the standard coefficients (reflection 1, expansion 2,
+// contraction 1/2, shrink 1/2) of Lagarias, Reeds, Wright and Wright (1998).  Every trial point is
+// projected onto the box.  Initial simplex: x0 and, per free slot k, x0 + step (hi_k - lo_k) e_k
+// (the step taken downwards where it would leave the box).  Vertices are ordered by f with a stable
+// insertion sort of the previous order.  Stops after max_iter iterations, or once
+// f_worst - f_best <= ftol |f_best|.
+static int nm(const Market& m, const double* theta0, int max_iter, double step, double ftol,
+              double* theta_out, double* f_out, int* iters_out, int* evals_out) {
+  const int P = m.n_param;
+  std::vector<int> fi;
+  for (int k = 0; k < P; ++k) if (m.freem[k]) fi.push_back(k);
+  const int nf = (int)fi.size();
+  auto project = [&](std::vector<double>& x) {
+    for (int s : fi) x[s] = std::min(std::max(x[s], m.lo[s]), m.hi[s]);
+  };
+  std::vector<std::vector<double>> V(nf + 1, std::vector<double>(theta0, theta0 + P));
+  std::vector<double> F(nf + 1);
+  int evals = 0;
+  auto eval = [&](const std::vector<double>& x) { ++evals; return objective(m, x.data()); };
+  for (int k = 1; k <= nf; ++k) {
+    const int s = fi[k - 1];
+    const double d = step * (m.hi[s] - m.lo[s]);
+    double v = theta0[s] + d;
+    if (v > m.hi[s]) v = theta0[s] - d;
+    V[k][s] = v;
+    project(V[k]);
+  }
+  for (int k = 0; k <= nf; ++k) F[k] = eval(V[k]);
+  std::vector<int> idx(nf + 1);
+  for (int k = 0; k <= nf; ++k) idx[k] = k;
+  int it = 0;
+  std::vector<double> c(P), xr(P), xt(P);
+  for (;; ++it) {
+    for (int i = 1; i <= nf; ++i)
+      for (int j = i; j > 0 && F[idx[j - 1]] > F[idx[j]]; --j) std::swap(idx[j - 1], idx[j]);
+    const int b = idx[0], w = idx[nf], sw = idx[nf > 0 ? nf - 1 : 0];
+    if (it >= max_iter || nf == 0 || !std::isfinite(F[b]) || F[w] - F[b] <= ftol * std::fabs(F[b])) break;
+    c = V[b];
+    for (int s : fi) {
+      double t = 0.0;
+      for (int j = 0; j < nf; ++j) t += V[idx[j]][s];
+      c[s] = t / nf;
+    }
+    xr = c;
+    for (int s : fi) xr[s] = c[s] + (c[s] - V[w][s]);
+    project(xr);
+    const double fr = eval(xr);
+    if (F[b] <= fr && fr < F[sw]) {
+      V[w] = xr; F[w] = fr;
+      continue;
+    }
+    if (fr < F[b]) {
+      xt = c;
+      for (int s : fi) xt[s] = c[s] + 2.0 * (xr[s] - c[s]);
+      project(xt);
+      const double fe = eval(xt);
+      if (fe < fr) { V[w] = xt; F[w] = fe; } else { V[w] = xr; F[w] = fr; }
+      continue;
+    }
+    xt = c;
+    bool accept;
+    double ft;
+    if (fr < F[w]) {   // outside contraction
+      for (int s : fi) xt[s] = c[s] + 0.5 * (xr[s] - c[s]);
+      project(xt);
+      ft = eval(xt);
+      accept = ft <= fr;
+    } else {           // inside contraction
+      for (int s : fi) xt[s] = c[s] + 0.5 * (V[w][s] - c[s]);
+      project(xt);
+      ft = eval(xt);
+      accept = ft < F[w];
+    }
+    if (accept) { V[w] = xt; F[w] = ft; continue; }
+    for (int j = 1; j <= nf; ++j) {   // shrink towards the best vertex
+      const int v = idx[j];
+      for (int s : fi) V[v][s] = V[b][s] + 0.5 * (V[v][s] - V[b][s]);
+      project(V[v]);
+      F[v] = eval(V[v]);
+    }
+  }
+  const int b = idx[0];
+  std::copy(V[b].begin(), V[b].end(), theta_out);
+  *f_out = F[b];
+  *iters_out = it;
+  *evals_out = evals;
+  return 0;
+}
+
 }  // namespace orc
 
 // ====================================================================== C interface (ctypes)
@@ -831,6 +925,11 @@ int orc_anneal(const void* mp, const orc::SAOpts* o, double* x_best, double* f_b
                double* T0_used) {
   return orc::anneal(*(const orc::Market*)mp, *o, x_best, f_best, chain_xb, chain_fb, trace_f, trace_x,
                      bits, n_evals, T0_used);
+}
+
+int orc_nm(const void* mp, const double* theta0, int max_iter, double step, double ftol, double* theta_out,
+           double* f_out, int* iters_out, int* evals_out) {
+  return orc::nm(*(const orc::Market*)mp, theta0, max_iter, step, ftol, theta_out, f_out, iters_out, evals_out);
 }
 
 int orc_lm(const void* mp, const double* theta0, int max_iter, double target_rmse, double mu0,

@@ -10,6 +10,7 @@ Entry points (same names as the C-ABI, without the ``sabr_lmm_`` prefix):
     Market.objective(X, prec)   sabr_lmm_objective
     Market.model_vols(X, prec)  sabr_lmm_model_vols
     Market.residuals(X, prec)   sabr_lmm_residuals
+    Market.nm_polish(X, ...)    sabr_lmm_nm_polish (the hybrid scheme's Nelder-Mead)
     Market.sync(stream)         sabr_lmm_sync (device-side wait timeouts of stream-ordered calls)
     Market.objective_grad(...)  sabr_lmm_objective_grad
     Market.anneal(...)          sabr_lmm_anneal
@@ -26,8 +27,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsabr_lmm.so")
 
-FP64, FP32, FP32_TF32X3, FP32_BF16X3 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "tf32x3": FP32_TF32X3, "bf16x3": FP32_BF16X3}
+FP64, FP32, FP32_BF16X3 = 0, 1, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": FP32_BF16X3}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTSUP"}
 
 _D = C.POINTER(C.c_double)
@@ -60,6 +61,7 @@ class AnnealOpts(C.Structure):
         ("step_floor", C.c_double), ("seed", C.c_uint64), ("x0", _D), ("prec", C.c_int32),
         ("lm_top_k", C.c_int32), ("lm_max_iter", C.c_int32), ("target_rmse_volpt", C.c_double),
         ("warps_per_block", C.c_int32), ("use_graph", C.c_int32), ("record_accepts", C.c_int32),
+        ("polish_nm", C.c_int32),
     ]
 
 
@@ -87,7 +89,8 @@ EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective",
            "sabr_lmm_objective_grad", "sabr_lmm_anneal", "sabr_lmm_anneal_prepare", "sabr_lmm_anneal_launch",
            "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_anneal_noalloc", "sabr_lmm_lm_polish",
            "sabr_lmm_market_info", "sabr_lmm_selftest_wait", "sabr_lmm_quadrature_rule", "sabr_lmm_last_error",
-           "sabr_lmm_version", "sabr_lmm_residuals", "sabr_lmm_sync", "sabr_lmm_test_raise_error")
+           "sabr_lmm_version", "sabr_lmm_residuals", "sabr_lmm_sync", "sabr_lmm_test_raise_error",
+           "sabr_lmm_nm_polish")
 
 
 def open_library(path: str = LIB_PATH):
@@ -115,6 +118,8 @@ def open_library(path: str = LIB_PATH):
     lib.sabr_lmm_anneal_plan_free.restype = None
     lib.sabr_lmm_lm_polish.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_double,
                                        C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_nm_polish.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_double,
+                                       C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.sabr_lmm_market_info.argtypes = [C.c_void_p, C.c_int32, C.POINTER(MarketInfo)]
     lib.sabr_lmm_selftest_wait.argtypes = [C.c_int64, C.c_void_p]
     lib.sabr_lmm_quadrature_rule.argtypes = [C.c_int32, _D, _D]
@@ -302,8 +307,19 @@ class Market:
                                             _stream_ptr(stream)))
         return X, f, r
 
+    def nm_polish(self, X, max_iter=500, step=0.02, ftol=1e-12, market=0, stream=None):
+        """sabr_lmm_nm_polish: returns (X polished, f, evaluations) as device tensors."""
+        X = self._X(X, market).clone()
+        n = X.shape[0]
+        f = self._torch.empty(n, dtype=self._torch.float64, device="cuda")
+        ev = self._torch.zeros(n, dtype=self._torch.int32, device="cuda")
+        _check(self._lib.sabr_lmm_nm_polish(self.h, market, C.c_void_p(X.data_ptr()), n, int(max_iter), float(step),
+                                            float(ftol), C.c_void_p(f.data_ptr()), C.c_void_p(ev.data_ptr()),
+                                            _stream_ptr(stream)))
+        return X, f, ev
+
     def _opts(self, n_chains, n_levels, steps, cooling, seed, prec, T0, step_frac, step_floor, x0,
-              lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, record_accepts):
+              lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, record_accepts, polish_nm=False):
         o = AnnealOpts()
         o.n_chains, o.n_levels, o.steps_per_level = n_chains, n_levels, steps
         o.T0, o.cooling, o.step_frac, o.step_floor = T0, cooling, step_frac, step_floor
@@ -315,6 +331,7 @@ class Market:
         o.prec = _prec(prec)
         o.lm_top_k, o.lm_max_iter, o.target_rmse_volpt = lm_top_k, lm_max_iter, target_rmse
         o.warps_per_block, o.use_graph, o.record_accepts = warps_per_block, int(use_graph), int(record_accepts)
+        o.polish_nm = int(polish_nm)
         return o, keep
 
     def _result(self, n_chains, n_levels, steps, record_accepts):
@@ -343,9 +360,10 @@ class Market:
 
     def anneal(self, n_chains, n_levels, steps, cooling, seed, prec="fp64", T0=0.0, step_frac=0.1,
                step_floor=1e-3, x0=None, lm_top_k=0, lm_max_iter=50, target_rmse=0.0,
-               warps_per_block=0, use_graph=False, record_accepts=False):
+               warps_per_block=0, use_graph=False, record_accepts=False, polish_nm=False):
         o, keep = self._opts(n_chains, n_levels, steps, cooling, seed, prec, T0, step_frac, step_floor, x0,
-                             lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, record_accepts)
+                             lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, record_accepts,
+                             polish_nm)
         r, arrs, bits = self._result(n_chains, n_levels, steps, record_accepts)
         _check(self._lib.sabr_lmm_anneal(self.h, C.byref(o), C.byref(r)))
         del keep
@@ -353,9 +371,9 @@ class Market:
 
     def anneal_prepare(self, n_chains, n_levels, steps, cooling, seed, prec="fp64", T0=0.0, step_frac=0.1,
                        step_floor=1e-3, x0=None, lm_top_k=0, lm_max_iter=50, target_rmse=0.0,
-                       warps_per_block=0, use_graph=True, stream=None):
+                       warps_per_block=0, use_graph=True, stream=None, polish_nm=False):
         o, keep = self._opts(n_chains, n_levels, steps, cooling, seed, prec, T0, step_frac, step_floor, x0,
-                             lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, False)
+                             lm_top_k, lm_max_iter, target_rmse, warps_per_block, use_graph, False, polish_nm)
         h = C.c_void_p()
         _check(self._lib.sabr_lmm_anneal_prepare(self.h, C.byref(o), _stream_ptr(stream), C.byref(h)))
         return AnnealPlan(self, h, (n_chains, n_levels, steps))

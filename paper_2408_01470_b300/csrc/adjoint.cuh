@@ -98,13 +98,176 @@ __device__ __forceinline__ void abcd_bar(R bar, R u, R e, R lin, R* acc4) {
   acc4[3] += bar;
 }
 
+// SABR vol and its partials in (alpha, nu, rho) for one instrument with per-forward (or per-swap)
+// factors fw = {alpha, nu/alpha, alpha^2, rho nu alpha}, A3 = (2 - 3 rho^2) nu^2, and its constants
+// g0 = {l, fk, inv_den, c1}, g1 = {c2, c3, sqrt T, D F}.
+template <class R, int FORMULA>
+__device__ __forceinline__ R sabr_vol_grad(const Q4<R>& fw, R A3, const RhoConsts<R>& rc, const Q4<R>& g0,
+                                           const Q4<R>& g1, R omb, R& s_al, R& s_nu, R& s_rho) {
+  const R al = fw.a, nu = fw.b * fw.a, rho = rc.rho;
+  R sig;
+  if (FORMULA == 0) {
+    const R z = fw.b * g0.b;
+    R zx, dzx, dzr;
+    z_over_x_grad<R>(z, rc, zx, dzx, dzr);
+    const R corr = R(1) + g0.d * fw.c + g1.a * fw.d + g1.b * A3;
+    const R pre = al * g0.c;                          // alpha * inv_den
+    sig = pre * zx * corr;
+    s_al = g0.c * zx * corr + pre * dzx * (-z / al) * corr + pre * zx * (R(2) * g0.d * al + g1.a * rho * nu);
+    s_nu = pre * (dzx * (g0.b / al) * corr + zx * (g1.a * rho * al + R(2) * g1.b * (R(2) - R(3) * rho * rho) * nu));
+    s_rho = pre * (dzr * corr + zx * (g1.a * nu * al - R(6) * g1.b * rho * nu * nu));
+  } else {
+    // Eq. (sigmaHagan): sigma = alpha/fo (1 - (omb - rho nu w) m/2 + (omb^2 + (2-3rho^2) nu^2 w^2 + 3(omb - rho nu w)) m^2/12),
+    // w = fo/alpha, m = -l
+    const R fo = g0.b, mm = -g0.a, w = fo / al;
+    const R rnw = rho * nu * w;
+    const R br = R(1) - R(0.5) * (omb - rnw) * mm + (omb * omb + (R(2) - R(3) * rho * rho) * nu * nu * w * w + R(3) * (omb - rnw)) * mm * mm * R(1.0 / 12.0);
+    sig = al / fo * br;
+    // partials of the bracket in (nu w) and rho at fixed alpha, then w = fo/alpha
+    const R d_rnw = R(0.5) * mm - R(3) * mm * mm * R(1.0 / 12.0);              // d br / d(rho nu w)
+    const R d_nw2 = (R(2) - R(3) * rho * rho) * mm * mm * R(1.0 / 12.0);       // d br / d(nu^2 w^2)
+    const R dbr_dw = d_rnw * rho * nu + d_nw2 * R(2) * nu * nu * w;
+    const R dbr_dnu = d_rnw * rho * w + d_nw2 * R(2) * nu * w * w;
+    const R dbr_drho = d_rnw * nu * w - R(6) * rho * nu * nu * w * w * mm * mm * R(1.0 / 12.0);
+    s_al = br / fo + al / fo * dbr_dw * (-w / al);
+    s_nu = al / fo * dbr_dnu;
+    s_rho = al / fo * dbr_drho;
+  }
+  return sig;
+}
+
+// The weighted residual r = sqrt(w) (P - P_mkt) of an instrument at vol sig and the adjoint of the
+// vol from f's term r^2: sigma_bar = 2 r sqrt(w) vega(sig).  g2 = {K/F, sgn, P_mkt, sqrt(w)}.
+template <class R>
+__device__ __forceinline__ R black_residual_grad(R sig, const Q4<R>& g0, const Q4<R>& g1, const Q4<R>& g2, R& sbar) {
+  typedef Num<R> M;
+  const R v = sig * g1.c;
+  const R d1 = fdiv<R>(g0.a, v) + R(0.5) * v;
+  const R sg = g2.b;
+  const R p = sg * g1.d * (ncdf<R>(sg * d1) - g2.a * ncdf<R>(sg * (d1 - v)));
+  const R r = g2.d * (p - g2.c);
+  const R vega = g1.d * M::exp_(R(-0.5) * d1 * d1) * R(0.39894228040143267794) * g1.c;
+  sbar = R(2) * r * g2.d * vega;
+  return r;
+}
+
+// Caplet pricing with the local reverse sweep, lane-strided over every caplet (k0, k0 + stride, ...):
+// adds r^2 to facc, the per-forward adjoints of alpha_i and nu_i to as.abar / as.nbar (FP64 atomics)
+// and the adjoint of the common rho to rho_bar; clears ok on an infeasible vol.
+template <class R, int FORMULA>
+__device__ void caplet_price_reverse(const DevMarket& m, const InstrView<R>& capB, const WarpScratch<R>& ws,
+                                     const AdjScratch<R>& as, const RhoConsts<R>& rc, int k0, int stride, bool& ok,
+                                     R& facc, double& rho_bar) {
+  typedef Num<R> M;
+  const R omb = (R)(1.0 - m.beta);
+  for (int k = k0; k < m.n_cap; k += stride) {
+    const int i = capB.idx[k];
+    const Q4<R> g0 = capB.g0[k], g1 = capB.g1[k], g2 = capB.g2[k];
+    R s_al, s_nu, s_rho;
+    const R sig = sabr_vol_grad<R, FORMULA>(ws.F4[i], ws.fA3[i], rc, g0, g1, omb, s_al, s_nu, s_rho);
+    const bool good = (sig > R(0)) && M::finite_(sig);
+    ok = ok && good;
+    if (!good) continue;
+    R sbar;
+    const R r = black_residual_grad<R>(sig, g0, g1, g2, sbar);
+    facc += r * r;
+    atomicAdd(as.abar + i, (double)(sbar * s_al));
+    atomicAdd(as.nbar + i, (double)(sbar * s_nu));
+    rho_bar += (double)(sbar * s_rho);
+  }
+}
+
+// Reverse of the Rebonato caplet mapping (alpha_i, nu_i of every caplet forward from the panel sums
+// of S2) down to the parameters a, b, c, d, alpha_h, beta_h, gamma_h, delta_h: this lane's share in
+// gacc[0..7] (the caller reduces across the warp).  Reads as.abar / as.nbar and the forward sweep's
+// tables in ws (inclusive prefix sums in Gp, Hp).
+template <class R>
+__device__ void caplet_mapping_reverse(const DevMarket& m, const QuadTab<R>& qt, const WarpScratch<R>& ws,
+                                       const AdjScratch<R>& as, int lane, double* gacc) {
+  const int NP = m.NP;
+  // the forward pass leaves inclusive prefix sums over panels in Hp and Gp
+  for (int p = lane; p <= NP; p += 32) {
+    as.SH[p] = p > 0 ? ws.Hp[p - 1] : R(0);
+    as.PG[p] = p > 0 ? ws.Gp[p - 1] : R(0);
+  }
+  for (int j = lane; j < m.n_capfwd; j += 32) {
+    const int i = m.capfwd_list[j];
+    const Q4<R> fw = ws.F4[i];
+    const R al = fw.a, nu = fw.b * fw.a, Ti = (R)m.T[i];
+    // X_i from nu_i: nu = sqrt(2X)/(alpha T)  ->  X = (nu alpha T)^2 / 2
+    const R X = R(0.5) * (nu * al * Ti) * (nu * al * Ti);
+    const R ab = (R)as.abar[i], nb = (R)as.nbar[i];
+    as.Gbar[i] = (ab - nb * nu / al) / (R(2) * al * Ti);
+    as.Xbar[i] = X > R(0) ? nb * nu / (R(2) * X) : R(0);
+  }
+  __syncwarp();
+  // ---------------- reverse of the panel sums and of the node tables
+  const R a = ws.xs[0], b = ws.xs[1], c = ws.xs[2], d = ws.xs[3];
+  const R ah = ws.xs[4], bh = ws.xs[5], gh = ws.xs[6], dh = ws.xs[7];
+  const R D = (R)m.panel;
+  const int q = lane & 7, pg = lane >> 3;
+  const R wq = qt.w[q];
+  const Q4<R> tq = ws.Tq[q];
+  R acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] = 0;
+  // e^{-gamma_h o2} of this lane's inner nodes: the same for every panel
+  R eo2[kQ];
+#pragma unroll
+  for (int r = 0; r < kQ; ++r) eo2[r] = Num<R>::exp_(-gh * qt.o2[q * kQ + r]);
+  const int NPc = round_up(NP, 4);
+  for (int p = pg; p < NPc; p += 4) {
+    if (p >= NP) continue;
+    R Gpb = 0, Apb = 0, Hpb = 0;
+    for (int j = 0; j < m.n_capfwd; ++j) {
+      const int i = m.capfwd_list[j];
+      const int n = m.fwd_np[i];
+      if (n > p) {
+        const R xb = as.Xbar[i];
+        Gpb += as.Gbar[i] + xb * (as.SH[n] - as.SH[p + 1]);
+        Apb += xb;
+        Hpb += xb * as.PG[p];
+      }
+    }
+    const R base = D * (R)p;
+    Q2<R> E;
+    E.a = Num<R>::exp_(-c * base);
+    E.b = Num<R>::exp_(-gh * base);
+    const R u = base + qt.o[q];
+    const R eg = E.a * tq.a, eh = E.b * tq.c;      // e^{-c u}, e^{-gamma_h u}
+    const R lin_g = a + b * u, lin_h = ah + bh * u;
+    const R g = lin_g * eg + d;
+    const R h = lin_h * eh + dh;
+    const R Rbar = Apb * wq * g * g;
+    R Rin = 0;
+#pragma unroll
+    for (int r = 0; r < kQ; ++r) {
+      // inner node v = base + o2: R = sum w2 h(v)^2, so h(v)_bar = 2 Rbar w2 h(v)
+      const R o2 = qt.o2[q * kQ + r];
+      const R sw2 = qt.sw2[q * kQ + r];
+      const R v = base + o2;
+      const R ev = E.b * eo2[r];                   // e^{-gamma_h v}
+      const R lin = ah + bh * v;
+      const R hv = lin * ev + dh;
+      Rin += sw2 * sw2 * hv * hv;
+      const R hvbar = R(2) * Rbar * sw2 * sw2 * hv;
+      abcd_bar<R>(hvbar, v, ev, lin, acc + 4);
+    }
+    const R gbar = R(2) * wq * g * (Gpb + Apb * Rin);
+    const R hbar = R(2) * wq * h * Hpb;
+    abcd_bar<R>(gbar, u, eg, lin_g, acc);
+    abcd_bar<R>(hbar, u, eh, lin_h, acc + 4);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) gacc[k] += (double)acc[k];
+}
+
 // f and df/dtheta of the point in ws.xs (all 32 lanes call).  g_out (12 doubles) and f_out are
 // written by lane 0.
 template <class R, int MODEL, int FORMULA>
 __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB, const QuadTab<R>& qt,
                                     const WarpScratch<R>& ws, const AdjScratch<R>& as, int lane, double* f_out,
                                     double* g_out) {
-  typedef Num<R> M;
   // ---------------- forward sweep
   RhoConsts<R> rc;
   if (MODEL == 0) {
@@ -125,58 +288,7 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
   bool ok = true;
   R facc = 0;
   double rho_bar = 0.0;
-  const R omb = (R)(1.0 - m.beta);
-  for (int k = lane; k < m.n_cap; k += 32) {
-    const int i = capB.idx[k];
-    const Q4<R> fw = ws.F4[i];
-    const Q4<R> g0 = capB.g0[k];
-    const Q4<R> g1 = capB.g1[k];
-    const Q4<R> g2 = capB.g2[k];
-    const R al = fw.a, nu = fw.b * fw.a, rho = rc.rho;
-    R sig, s_al, s_nu, s_rho;
-    if (FORMULA == 0) {
-      const R z = fw.b * g0.b;
-      R zx, dzx, dzr;
-      z_over_x_grad<R>(z, rc, zx, dzx, dzr);
-      const R A3 = ws.fA3[i];
-      const R corr = R(1) + g0.d * fw.c + g1.a * fw.d + g1.b * A3;
-      const R pre = al * g0.c;                          // alpha * inv_den
-      sig = pre * zx * corr;
-      s_al = g0.c * zx * corr + pre * dzx * (-z / al) * corr + pre * zx * (R(2) * g0.d * al + g1.a * rho * nu);
-      s_nu = pre * (dzx * (g0.b / al) * corr + zx * (g1.a * rho * al + R(2) * g1.b * (R(2) - R(3) * rho * rho) * nu));
-      s_rho = pre * (dzr * corr + zx * (g1.a * nu * al - R(6) * g1.b * rho * nu * nu));
-    } else {
-      // Eq. (sigmaHagan): sigma = alpha/fo (1 - (omb - rho nu w) m/2 + (omb^2 + (2-3rho^2) nu^2 w^2 + 3(omb - rho nu w)) m^2/12),
-      // w = fo/alpha, m = -l
-      const R fo = g0.b, mm = -g0.a, w = fo / al;
-      const R rnw = rho * nu * w;
-      const R br = R(1) - R(0.5) * (omb - rnw) * mm + (omb * omb + (R(2) - R(3) * rho * rho) * nu * nu * w * w + R(3) * (omb - rnw)) * mm * mm * R(1.0 / 12.0);
-      sig = al / fo * br;
-      // partials of the bracket in (nu w) and rho at fixed alpha, then w = fo/alpha
-      const R d_rnw = R(0.5) * mm - R(3) * mm * mm * R(1.0 / 12.0);              // d br / d(rho nu w)
-      const R d_nw2 = (R(2) - R(3) * rho * rho) * mm * mm * R(1.0 / 12.0);       // d br / d(nu^2 w^2)
-      const R dbr_dw = d_rnw * rho * nu + d_nw2 * R(2) * nu * nu * w;
-      const R dbr_dnu = d_rnw * rho * w + d_nw2 * R(2) * nu * w * w;
-      const R dbr_drho = d_rnw * nu * w - R(6) * rho * nu * nu * w * w * mm * mm * R(1.0 / 12.0);
-      s_al = br / fo + al / fo * dbr_dw * (-w / al);
-      s_nu = al / fo * dbr_dnu;
-      s_rho = al / fo * dbr_drho;
-    }
-    const bool good = (sig > R(0)) && M::finite_(sig);
-    ok = ok && good;
-    if (!good) continue;
-    const R v = sig * g1.c;
-    const R d1 = fdiv<R>(g0.a, v) + R(0.5) * v;
-    const R sg = g2.b;
-    const R p = sg * g1.d * (ncdf<R>(sg * d1) - g2.a * ncdf<R>(sg * (d1 - v)));
-    const R r = g2.d * (p - g2.c);
-    facc += r * r;
-    const R vega = g1.d * M::exp_(R(-0.5) * d1 * d1) * R(0.39894228040143267794) * g1.c;
-    const R sbar = R(2) * r * g2.d * vega;
-    atomicAdd(as.abar + i, (double)(sbar * s_al));
-    atomicAdd(as.nbar + i, (double)(sbar * s_nu));
-    rho_bar += (double)(sbar * s_rho);
-  }
+  caplet_price_reverse<R, FORMULA>(m, capB, ws, as, rc, lane, 32, ok, facc, rho_bar);
   const bool bad = __any_sync(0xffffffffu, !ok);
   const double f = warp_sum_d((double)facc);
   rho_bar = warp_sum_d(rho_bar);
@@ -194,84 +306,7 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
     gacc[0] = sa;
     gacc[2] = sn;
   } else {
-    // ---------------- reverse of the mapping: (alpha_i, nu_i) -> (G_i, X_i)
-    const int NP = m.NP;
-    // the forward pass leaves inclusive prefix sums over panels in Hp and Gp
-    for (int p = lane; p <= NP; p += 32) {
-      as.SH[p] = p > 0 ? ws.Hp[p - 1] : R(0);
-      as.PG[p] = p > 0 ? ws.Gp[p - 1] : R(0);
-    }
-    for (int j = lane; j < m.n_capfwd; j += 32) {
-      const int i = m.capfwd_list[j];
-      const Q4<R> fw = ws.F4[i];
-      const R al = fw.a, nu = fw.b * fw.a, Ti = (R)m.T[i];
-      // X_i from nu_i: nu = sqrt(2X)/(alpha T)  ->  X = (nu alpha T)^2 / 2
-      const R X = R(0.5) * (nu * al * Ti) * (nu * al * Ti);
-      const R ab = (R)as.abar[i], nb = (R)as.nbar[i];
-      as.Gbar[i] = (ab - nb * nu / al) / (R(2) * al * Ti);
-      as.Xbar[i] = X > R(0) ? nb * nu / (R(2) * X) : R(0);
-    }
-    __syncwarp();
-    // ---------------- reverse of the panel sums and of the node tables
-    const R a = ws.xs[0], b = ws.xs[1], c = ws.xs[2], d = ws.xs[3];
-    const R ah = ws.xs[4], bh = ws.xs[5], gh = ws.xs[6], dh = ws.xs[7];
-    const R D = (R)m.panel;
-    const int q = lane & 7, pg = lane >> 3;
-    const R wq = qt.w[q];
-    const Q4<R> tq = ws.Tq[q];
-    R acc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0;
-    // e^{-gamma_h o2} of this lane's inner nodes: the same for every panel
-    R eo2[kQ];
-#pragma unroll
-    for (int r = 0; r < kQ; ++r) eo2[r] = Num<R>::exp_(-gh * qt.o2[q * kQ + r]);
-    const int NPc = round_up(NP, 4);
-    for (int p = pg; p < NPc; p += 4) {
-      if (p >= NP) continue;
-      R Gpb = 0, Apb = 0, Hpb = 0;
-      for (int j = 0; j < m.n_capfwd; ++j) {
-        const int i = m.capfwd_list[j];
-        const int n = m.fwd_np[i];
-        if (n > p) {
-          const R xb = as.Xbar[i];
-          Gpb += as.Gbar[i] + xb * (as.SH[n] - as.SH[p + 1]);
-          Apb += xb;
-          Hpb += xb * as.PG[p];
-        }
-      }
-      const R base = D * (R)p;
-      Q2<R> E;
-      E.a = Num<R>::exp_(-c * base);
-      E.b = Num<R>::exp_(-gh * base);
-      const R u = base + qt.o[q];
-      const R eg = E.a * tq.a, eh = E.b * tq.c;      // e^{-c u}, e^{-gamma_h u}
-      const R lin_g = a + b * u, lin_h = ah + bh * u;
-      const R g = lin_g * eg + d;
-      const R h = lin_h * eh + dh;
-      const R Rbar = Apb * wq * g * g;
-      R Rin = 0;
-#pragma unroll
-      for (int r = 0; r < kQ; ++r) {
-        // inner node v = base + o2: R = sum w2 h(v)^2, so h(v)_bar = 2 Rbar w2 h(v)
-        const R o2 = qt.o2[q * kQ + r];
-        const R sw2 = qt.sw2[q * kQ + r];
-        const R v = base + o2;
-        const R ev = E.b * eo2[r];                   // e^{-gamma_h v}
-        const R lin = ah + bh * v;
-        const R hv = lin * ev + dh;
-        Rin += sw2 * sw2 * hv * hv;
-        const R hvbar = R(2) * Rbar * sw2 * sw2 * hv;
-        abcd_bar<R>(hvbar, v, ev, lin, acc + 4);
-      }
-      const R gbar = R(2) * wq * g * (Gpb + Apb * Rin);
-      const R hbar = R(2) * wq * h * Hpb;
-      abcd_bar<R>(gbar, u, eg, lin_g, acc);
-      abcd_bar<R>(hbar, u, eh, lin_h, acc + 4);
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) gacc[k] = (double)acc[k];
-    gacc[8] = 0.0;
+    caplet_mapping_reverse<R>(m, qt, ws, as, lane, gacc);
   }
 #pragma unroll
   for (int k = 0; k < kMaxParam; ++k) gacc[k] = warp_sum_d(gacc[k]);

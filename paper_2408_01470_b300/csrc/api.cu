@@ -157,6 +157,8 @@ std::string validate(const sabr_lmm_market_desc& d, int idx) {
 
 int n_panels(double t, double panel) { return (int)std::lround(t / panel); }
 
+bool valid_prec(int p) { return p == SABR_LMM_FP64 || p == SABR_LMM_FP32 || p == SABR_LMM_FP32_BF16X3; }
+
 }  // namespace
 
 // ====================================================================== load / free
@@ -176,7 +178,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     size_t T, P, cap_K, cap_vol, cap_wu, swp_K, swp_vol, swp_wu, cap_fwd, swp_start, swp_end, swp_swap, swap_a, swap_b,
         capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
         swp_w, cblk64, cblk32, cpair32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
-        swap_grp, swap_L, swap_W32, grp_pair, swap_coff, swap_C64, swap_C32, chunk, grp_chunk0, swap_chunk0;
+        swap_grp, swap_L, seg, col_seg0, col_u, grp_col0, grp_u64, grp_u32, swap_scale64, swap_scale32;
   };
   std::vector<Off> off(n_markets);
   std::vector<DevMarket> dm(n_markets);
@@ -184,8 +186,8 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
   // host-side integer bookkeeping
   std::vector<std::vector<int>> capfwd(n_markets), fwdnp(n_markets), swp_swap(n_markets), swap_a(n_markets),
       swap_b(n_markets), swap_np(n_markets), grp_a(n_markets), grp_nE(n_markets), grp_L(n_markets),
-      grp_delta(n_markets), grp_swap0(n_markets), swap_grp(n_markets), swap_L(n_markets), grp_pair(n_markets),
-      swap_coff(n_markets), chunk(n_markets), grp_chunk0(n_markets), swap_chunk0(n_markets);
+      grp_delta(n_markets), grp_swap0(n_markets), swap_grp(n_markets), swap_L(n_markets), seg(n_markets),
+      col_seg0(n_markets), col_u(n_markets), grp_col0(n_markets);
   for (int j = 0; j < n_markets; ++j) {
     const sabr_lmm_market_desc& d = descs[j];
     DevMarket& m = dm[j];
@@ -249,65 +251,29 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.NA = NA;
     m.ND = ND;
     m.max_gwin = max_gwin;
-    // pair tables of the quadratic forms: per group the (offset, diagonal) of every pair of its
-    // window, per swap the offset of its coefficient row
-    m.max_npk = max_gwin * (max_gwin + 1) / 2;
+    // quadratic forms by expiry group: every group's pair triangle (columns j < L_g, rows i <= j)
+    // cut into segments of <= kSeg pairs of one column, column by column, group by group
     if (ND > 255) return fail(SABR_LMM_ENOTSUP, "market " + std::to_string(j) + ": a swap window spans more than 255 panels");
-    for (size_t g = 0; g < grp_a[j].size(); ++g)
-      for (int t = 0; t < m.max_npk; ++t) {
-        int jj = 0;
-        while ((jj + 1) * (jj + 2) / 2 <= t) ++jj;
-        const int ii = t - jj * (jj + 1) / 2;
-        const int* dl = grp_delta[j].data() + g * max_gwin;
-        grp_pair[j].push_back(jj < grp_L[j][g] ? (dl[ii] << 8) | (dl[jj] - dl[ii]) : 0);
-      }
-    swap_coff[j].push_back(0);
-    for (size_t s2 = 0; s2 < swap_L[j].size(); ++s2)
-      swap_coff[j].push_back(swap_coff[j].back() + (swap_L[j][s2] * (swap_L[j][s2] + 1) / 2 + 3) / 4 * 4);
-    // chunks of <= kChunk pairs, 4-pair quads interleaved (swaps are ordered by group, so the
-    // chunks are too)
     for (size_t g = 0; g < grp_a[j].size(); ++g) {
-      grp_chunk0[j].push_back((int)chunk[j].size() / 4);
-      for (int s2 = grp_swap0[j][g]; s2 < grp_swap0[j][g + 1]; ++s2) {
-        swap_chunk0[j].push_back((int)chunk[j].size() / 4);
-        const int np = swap_L[j][s2] * (swap_L[j][s2] + 1) / 2;
-        const int nq = (np + 3) / 4, nk = (nq + kChunk / 4 - 1) / (kChunk / 4);
-        for (int k = 0; k < nk; ++k) {   // {coefficient row offset, group, k | nk << 16, quads}
-          chunk[j].push_back(swap_coff[j][s2]);
-          chunk[j].push_back((int)g);
-          chunk[j].push_back(k | (nk << 16));
-          chunk[j].push_back(nq);
+      grp_col0[j].push_back((int)col_seg0[j].size());
+      for (int jj = 0; jj < grp_L[j][g]; ++jj) {
+        col_seg0[j].push_back((int)seg[j].size());
+        col_u[j].push_back((int)g * max_gwin + jj);
+        for (int i0 = 0; i0 <= jj; i0 += kSeg) {
+          const int n = std::min(kSeg, jj + 1 - i0);
+          seg[j].push_back((int)g | (jj << 8) | (i0 << 16) | (n << 24));
         }
       }
     }
-    grp_chunk0[j].push_back((int)chunk[j].size() / 4);
-    swap_chunk0[j].push_back((int)chunk[j].size() / 4);
-    m.n_chunk = (int)chunk[j].size() / 4;
-
+    grp_col0[j].push_back((int)col_seg0[j].size());
+    m.n_col = (int)col_seg0[j].size();
+    col_seg0[j].push_back((int)seg[j].size());
+    m.n_seg = (int)seg[j].size();
     m.n_swap = (int)swap_a[j].size();
     m.max_win = max_win;
     m.NP = std::max(NP, 1);
-    // batches of expiry groups for the quadratic forms (after every size the CTA scratch depends on)
-    {
-      auto most = [&](int GB) {
-        int mx = 1;
-        for (int g0 = 0; g0 < m.n_grp; g0 += GB)
-          mx = std::max(mx, grp_chunk0[j][std::min(m.n_grp, g0 + GB)] - grp_chunk0[j][g0]);
-        return mx;
-      };
-      const int cap = m.NA * cta_y_stride(), per = 3 * ((m.max_npk + 3) & ~3);
-      auto place = [&](int GB) {   // partials after the B matrices in Y if they fit, else their own region
-        m.qf_gb = GB;
-        m.max_batch_chunks = most(GB);
-        const int off = GB > 1 ? (GB * per + 3) / 4 * 4 : 0;   // GB = 1 keeps its B matrices in Bg
-        m.qf_pc_off = off + 3 * m.max_batch_chunks <= cap ? off : -1;
-      };
-      int GB = cap >= 2 * per ? cap / per : 1;
-      while (GB > 1 && most(GB) > kMaxBatchChunks) --GB;
-      place(GB);
-      // the FP64 CTA must fit: give up groups per barrier (the partials then share the Y region)
-      while (GB > 1 && smem_bytes_cta<double>(m) > 227u * 1024u) place(--GB);
-    }
+    // the segment and column partials (3 x (n_seg + n_col)) in the Y region when they fit there
+    m.qf_own = 3 * (m.n_seg + m.n_col) > m.NA * cta_y_stride() ? 1 : 0;
     HostMarket& h = hm[j];
     h.model = d.model; h.formula = d.formula; h.n_param = d.n_param; h.n_fwd = d.n_fwd;
     h.n_cap = d.n_cap; h.n_swp = d.n_swp; h.beta = d.beta;
@@ -339,14 +305,14 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.grp_a = A.take(ng * 4); o.grp_nE = A.take(ng * 4); o.grp_L = A.take(ng * 4);
     o.grp_delta = A.take((size_t)ng * m.max_gwin * 4); o.grp_swap0 = A.take((ng + 1) * 4);
     o.swap_grp = A.take(m.n_swap * 4); o.swap_L = A.take(m.n_swap * 4);
-    o.swap_W32 = A.take((size_t)m.n_swap * max_win * 4);
-    o.grp_pair = A.take((size_t)ng * m.max_npk * 4);
-    o.swap_coff = A.take((m.n_swap + 1) * 4);
-    o.swap_C64 = A.take((size_t)swap_coff[j].back() * 8);
-    o.swap_C32 = A.take((size_t)swap_coff[j].back() * 4);
-    o.chunk = A.take((size_t)m.n_chunk * 16);
-    o.grp_chunk0 = A.take((m.n_grp + 1) * 4);
-    o.swap_chunk0 = A.take((m.n_swap + 1) * 4);
+    o.seg = A.take((size_t)m.n_seg * 4);
+    o.col_seg0 = A.take((size_t)(m.n_col + 1) * 4);
+    o.col_u = A.take((size_t)m.n_col * 4);
+    o.grp_col0 = A.take((size_t)(ng + 1) * 4);
+    o.grp_u64 = A.take((size_t)ng * m.max_gwin * 8);
+    o.grp_u32 = A.take((size_t)ng * m.max_gwin * 4);
+    o.swap_scale64 = A.take((size_t)m.n_swap * 8);
+    o.swap_scale32 = A.take((size_t)m.n_swap * 4);
   }
   std::vector<unsigned char> host(A.size, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { if (src && bytes) std::memcpy(host.data() + o, src, bytes); };
@@ -369,11 +335,10 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     put(o.grp_delta, grp_delta[j].data(), (size_t)m.n_grp * m.max_gwin * 4);
     put(o.grp_swap0, grp_swap0[j].data(), (m.n_grp + 1) * 4);
     put(o.swap_grp, swap_grp[j].data(), m.n_swap * 4); put(o.swap_L, swap_L[j].data(), m.n_swap * 4);
-    put(o.grp_pair, grp_pair[j].data(), (size_t)m.n_grp * m.max_npk * 4);
-    put(o.swap_coff, swap_coff[j].data(), (m.n_swap + 1) * 4);
-    put(o.chunk, chunk[j].data(), (size_t)m.n_chunk * 16);
-    put(o.grp_chunk0, grp_chunk0[j].data(), grp_chunk0[j].size() * 4);
-    put(o.swap_chunk0, swap_chunk0[j].data(), swap_chunk0[j].size() * 4);
+    put(o.seg, seg[j].data(), (size_t)m.n_seg * 4);
+    put(o.col_seg0, col_seg0[j].data(), col_seg0[j].size() * 4);
+    put(o.col_u, col_u[j].data(), col_u[j].size() * 4);
+    put(o.grp_col0, grp_col0[j].data(), grp_col0[j].size() * 4);
     QuadTab<double> q64;
     QuadTab<float> q32;
     const double D = m.panel;
@@ -425,15 +390,15 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.grp_a = (const int*)(base + o.grp_a); m.grp_nE = (const int*)(base + o.grp_nE);
     m.grp_L = (const int*)(base + o.grp_L); m.grp_delta = (const int*)(base + o.grp_delta);
     m.grp_swap0 = (const int*)(base + o.grp_swap0); m.swap_grp = (const int*)(base + o.swap_grp);
-    m.swap_L = (const int*)(base + o.swap_L); m.swap_W32 = (float*)(base + o.swap_W32);
-    m.grp_pair = (const int*)(base + o.grp_pair); m.swap_coff = (const int*)(base + o.swap_coff);
-    m.swap_C64 = (const double*)(base + o.swap_C64); m.swap_C32 = (const float*)(base + o.swap_C32);
-    m.chunk = (const int4*)(base + o.chunk); m.grp_chunk0 = (const int*)(base + o.grp_chunk0);
-    m.swap_chunk0 = (const int*)(base + o.swap_chunk0);
+    m.swap_L = (const int*)(base + o.swap_L);
+    m.seg = (const int*)(base + o.seg); m.col_seg0 = (const int*)(base + o.col_seg0);
+    m.col_u = (const int*)(base + o.col_u); m.grp_col0 = (const int*)(base + o.grp_col0);
+    m.grp_u64 = (const double*)(base + o.grp_u64); m.grp_u32 = (const float*)(base + o.grp_u32);
+    m.swap_scale64 = (const double*)(base + o.swap_scale64); m.swap_scale32 = (const float*)(base + o.swap_scale32);
     setup_forwards_kernel<<<(m.n_fwd + 127) / 128, 128, 0, s>>>(m);
     if (m.n_swap > 0) {
       setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
-      setup_swap_coef_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
+      setup_group_u_kernel<<<(m.n_grp * m.max_gwin + 127) / 128, 128, 0, s>>>(m);
     }
     const int ni = m.n_cap + m.n_swp;
     setup_instruments_kernel<<<(ni + 127) / 128, 128, 0, s>>>(m);
@@ -521,11 +486,9 @@ sabr_lmm_status check_call(const sabr_lmm_market* m, int32_t idx, int64_t n, int
   if (!m) return fail(SABR_LMM_EINVAL, "market is NULL");
   if (idx < 0 || idx >= (int)m->dm.size()) return fail(SABR_LMM_EINVAL, "market_idx out of range");
   if (n < 0) return fail(SABR_LMM_EINVAL, "n must be >= 0");
-  if (prec < SABR_LMM_FP64 || prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
+  if (!valid_prec(prec)) return fail(SABR_LMM_EINVAL, "unknown precision");
   if (market_smem(m->dm[idx], prec) > 227 * 1024)
     return fail(SABR_LMM_ENOTSUP, "the market does not fit in one CTA's shared memory at this precision");
-  if (m->dm[idx].n_swp > 0 && prec == SABR_LMM_FP32_TF32X3)
-    return fail(SABR_LMM_ENOTSUP, "the TF32 split contraction is not built; use SABR_LMM_FP32_BF16X3 or SABR_LMM_FP32");
   if (m->dm[idx].n_swp > 0 && prec == SABR_LMM_FP32_BF16X3 && !tc_eligible(m->dm[idx]))
     return fail(SABR_LMM_ENOTSUP, "the market's panel tables exceed one tensor-core tile (NA <= 64, ND <= 27)");
   return SABR_LMM_OK;
@@ -585,16 +548,106 @@ cudaError_t launch_grad_r(const DevMarket& m, const double* X, long long n, doub
 }
 }  // namespace
 
+namespace {
+// Markets with swaptions: one CTA per point (FP64), the forms' partials in their own region.
+template <int FORMULA>
+cudaError_t launch_grad_cta(DevMarket m, const double* X, long long n, double* f, double* G, cudaStream_t s) {
+  m.qf_own = 1;
+  const uint32_t sm = smem_bytes_grad_cta(m);
+  auto kern = grad_cta_kernel<FORMULA>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  long long blocks = n < 148 * 4 ? n : 148 * 4;
+  if (blocks < 1) blocks = 1;
+  kern<<<(unsigned)blocks, 256, sm, s>>>(m, X, n, f, G);
+  return cudaGetLastError();
+}
+
+// The reverse sweep of any market: caplet markets at `prec`, markets with swaptions in FP64.
+cudaError_t launch_grad_any(const DevMarket& m, int prec, const double* X, long long n, double* f, double* G,
+                            cudaStream_t s) {
+  if (m.n_swp > 0) return m.formula == 0 ? launch_grad_cta<0>(m, X, n, f, G, s) : launch_grad_cta<1>(m, X, n, f, G, s);
+  return prec == SABR_LMM_FP64 ? launch_grad_r<double>(m, X, n, f, G, s) : launch_grad_r<float>(m, X, n, f, G, s);
+}
+
+// Whether the reverse sweep of market m fits one CTA's shared memory.
+bool grad_fits(const DevMarket& m) {
+  if (m.n_swp == 0) return true;
+  DevMarket m1 = m;
+  m1.qf_own = 1;
+  return smem_bytes_grad_cta(m1) <= 227u * 1024u;
+}
+}  // namespace
+
 extern "C" sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int32_t idx, const double* X, int64_t n,
                                                    int32_t prec, double* f, double* G, void* stream) {
   sabr_lmm_status st = check_call(m, idx, n, prec);
   if (st != SABR_LMM_OK) return st;
-  if (m->dm[idx].n_swp > 0) return fail(SABR_LMM_ENOTSUP, "the adjoint of the swaption forms is not enabled in this build");
+  if (!grad_fits(m->dm[idx]))
+    return fail(SABR_LMM_ENOTSUP, "the reverse sweep of this market does not fit one CTA's shared memory");
   if (n == 0) return SABR_LMM_OK;
   if (!X || !f || !G) return fail(SABR_LMM_EINVAL, "X, f and G are required");
-  const DevMarket& dm = m->dm[idx];
-  CUDA_TRY(prec == SABR_LMM_FP64 ? launch_grad_r<double>(dm, X, n, f, G, (cudaStream_t)stream)
-                                 : launch_grad_r<float>(dm, X, n, f, G, (cudaStream_t)stream));
+  CUDA_TRY(launch_grad_any(m->dm[idx], prec, X, n, f, G, (cudaStream_t)stream));
+  return SABR_LMM_OK;
+}
+
+namespace {
+// Nelder-Mead from n points (FP64): one warp per point on caplet markets, one CTA per point on markets
+// with swaptions.
+template <int MODEL, int FORMULA>
+cudaError_t launch_nm_t(const DevMarket& m, double* X, long long n, int max_iter, double step, double ftol, double* f,
+                        int* evals, cudaStream_t s) {
+  const uint32_t sm = ((smem_bytes<double>(m, 1) + 15u) & ~15u) + nm_team_bytes();
+  auto kern = nm_kernel<MODEL, FORMULA>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long blocks = n < 148 * 16 ? n : 148 * 16;
+  kern<<<(unsigned)blocks, 32, sm, s>>>(m, X, n, max_iter, step, ftol, f, evals);
+  return cudaGetLastError();
+}
+
+template <int FORMULA>
+cudaError_t launch_nm_cta_t(const DevMarket& m, double* X, long long n, int max_iter, double step, double ftol,
+                            double* f, int* evals, cudaStream_t s) {
+  const uint32_t sm = ((smem_bytes_cta<double>(m) + 15u) & ~15u) + nm_team_bytes();
+  auto kern = nm_cta_kernel<FORMULA>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long blocks = n < 148 * 2 ? n : 148 * 2;
+  kern<<<(unsigned)blocks, 256, sm, s>>>(m, X, n, max_iter, step, ftol, f, evals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nm(const DevMarket& m, double* X, long long n, int max_iter, double step, double ftol, double* f,
+                      int* evals, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (m.n_swp > 0)
+    return m.formula == 0 ? launch_nm_cta_t<0>(m, X, n, max_iter, step, ftol, f, evals, s)
+                          : launch_nm_cta_t<1>(m, X, n, max_iter, step, ftol, f, evals, s);
+  if (m.model == 0)
+    return m.formula == 0 ? launch_nm_t<0, 0>(m, X, n, max_iter, step, ftol, f, evals, s)
+                          : launch_nm_t<0, 1>(m, X, n, max_iter, step, ftol, f, evals, s);
+  return m.formula == 0 ? launch_nm_t<1, 0>(m, X, n, max_iter, step, ftol, f, evals, s)
+                        : launch_nm_t<1, 1>(m, X, n, max_iter, step, ftol, f, evals, s);
+}
+
+uint32_t nm_smem(const DevMarket& m) {
+  return (m.n_swp > 0 ? ((smem_bytes_cta<double>(m) + 15u) & ~15u) : ((smem_bytes<double>(m, 1) + 15u) & ~15u)) +
+         nm_team_bytes();
+}
+}  // namespace
+
+extern "C" sabr_lmm_status sabr_lmm_nm_polish(const sabr_lmm_market* m, int32_t idx, double* X, int64_t n,
+                                              int32_t max_iter, double step, double ftol, double* f, int32_t* evals,
+                                              void* stream) {
+  sabr_lmm_status st = check_call(m, idx, n, SABR_LMM_FP64);
+  if (st != SABR_LMM_OK) return st;
+  if (max_iter < 0 || !(step > 0.0 && step <= 1.0) || !(ftol >= 0.0))
+    return fail(SABR_LMM_EINVAL, "max_iter >= 0, 0 < step <= 1 and ftol >= 0 required");
+  if (nm_smem(m->dm[idx]) > 227u * 1024u) return fail(SABR_LMM_ENOTSUP, "the market and the simplex do not fit one CTA");
+  if (n == 0) return SABR_LMM_OK;
+  if (!X || !f) return fail(SABR_LMM_EINVAL, "X and f are required");
+  CUDA_TRY(launch_nm(m->dm[idx], X, n, max_iter, step, ftol, f, evals, (cudaStream_t)stream));
   return SABR_LMM_OK;
 }
 
@@ -675,7 +728,7 @@ cudaError_t lm_side(LmSide& out) {
 cudaError_t lm_enqueue(const DevMarket& m, int n_free, double* X, int n, int max_iter, double target, const LmWork& w,
                        cudaStream_t s, bool stop_at_first = false) {
   const int S = 1 + n_free;   // stencil: the point and one forward step per free slot
-  const bool have_adjoint = m.n_swp == 0;
+  const bool have_adjoint = grad_fits(m);
   cudaError_t e;
   LmSide side;
   if (have_adjoint && max_iter > 0 && (e = lm_side(side)) != cudaSuccess) return e;
@@ -695,7 +748,7 @@ cudaError_t lm_enqueue(const DevMarket& m, int n_free, double* X, int n, int max
     if (have_adjoint) {   // fork: the reverse sweep at X on the side stream, beside the stencil
       if ((e = cudaEventRecord(side.fork, s)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(side.s2, side.fork, 0)) != cudaSuccess) return e;
-      e = launch_grad_r<double>(m, X, n, w.gf, w.grad, side.s2);
+      e = launch_grad_any(m, SABR_LMM_FP64, X, n, w.gf, w.grad, side.s2);
       const cudaError_t e2 = cudaEventRecord(side.join, side.s2);
       if (e != cudaSuccess) return e;
       if (e2 != cudaSuccess) return e2;
@@ -971,17 +1024,19 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (o->n_chains < 1 || o->n_levels < 1 || o->steps_per_level < 1) return fail(SABR_LMM_EINVAL, "n_chains, n_levels, steps_per_level must be >= 1");
   if (!(o->cooling > 0.0 && o->cooling <= 1.0)) return fail(SABR_LMM_EINVAL, "cooling must be in (0, 1]");
   if (!(o->step_frac > 0.0) || !(o->step_floor >= 0.0)) return fail(SABR_LMM_EINVAL, "step_frac > 0 and step_floor >= 0 required");
-  if (o->prec < SABR_LMM_FP64 || o->prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
+  if (!valid_prec(o->prec)) return fail(SABR_LMM_EINVAL, "unknown precision");
   if (o->warps_per_block < 0 || o->warps_per_block > 28) return fail(SABR_LMM_EINVAL, "warps_per_block must be in [0, 28]");
   if (o->lm_top_k < 0 || o->lm_top_k > o->n_chains || o->lm_top_k > 1024) return fail(SABR_LMM_EINVAL, "lm_top_k must be in [0, min(n_chains, 1024)]");
   if (o->lm_top_k > 0 && o->lm_max_iter < 0) return fail(SABR_LMM_EINVAL, "lm_max_iter must be >= 0");
+  if (o->polish_nm != 0 && o->polish_nm != 1) return fail(SABR_LMM_EINVAL, "polish_nm must be 0 or 1");
+  for (const DevMarket& m : mk->dm)
+    if (o->lm_top_k > 0 && o->polish_nm && nm_smem(m) > 227u * 1024u)
+      return fail(SABR_LMM_ENOTSUP, "a market and the Nelder-Mead simplex do not fit one CTA");
   for (size_t j = 0; o->x0 && j < mk->dm.size(); ++j)
     if (sabr_lmm_status st = check_x0(mk->hm[j], o->x0 + j * (size_t)mk->hm[j].n_param); st != SABR_LMM_OK) return st;
   for (const DevMarket& m : mk->dm) {
     if (market_smem(m, o->prec) > 227 * 1024)
       return fail(SABR_LMM_ENOTSUP, "a market does not fit in one CTA's shared memory at this precision");
-    if (m.n_swp > 0 && o->prec == SABR_LMM_FP32_TF32X3)
-      return fail(SABR_LMM_ENOTSUP, "the TF32 split contraction is not built; use SABR_LMM_FP32_BF16X3 or SABR_LMM_FP32");
     if (m.n_swp > 0 && o->prec == SABR_LMM_FP32_BF16X3 && (!tc_eligible(m) || mk->dm.size() > 1))
       return fail(SABR_LMM_ENOTSUP, "the tensor-core contraction needs a single market whose panel tables fit one tile");
   }
@@ -1185,7 +1240,8 @@ sabr_lmm_status enqueue_polish(sabr_lmm_anneal_plan* p, cudaStream_t s) {
     gather_points_kernel<<<k, 32, 0, s>>>(p->st[j].xb, sel, k, m.n_param, X);
     int n_free = 0;
     for (unsigned char f : p->mk->hm[j].freem) n_free += f != 0;
-    cudaError_t e = lm_enqueue(m, n_free, X, k, p->opts.lm_max_iter, p->opts.target_rmse_volpt, w, s, true);
+    cudaError_t e = p->opts.polish_nm ? launch_nm(m, X, k, p->opts.lm_max_iter, 0.02, 1e-12, w.f, nullptr, s)
+                                      : lm_enqueue(m, n_free, X, k, p->opts.lm_max_iter, p->opts.target_rmse_volpt, w, s, true);
     if (e != cudaSuccess) return fail(SABR_LMM_ECUDA, std::string("polish launch: ") + cudaGetErrorString(e));
     take_best_kernel<<<1, 32, 0, s>>>(X, w.f, k, m.n_param, p->st[j].best_x, p->st[j].best_f);
   }
@@ -1451,7 +1507,7 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, in
   }
   if (!(o->cooling > 0.0 && o->cooling <= 1.0)) return fail(SABR_LMM_EINVAL, "cooling must be in (0, 1]");
   if (!(o->step_frac > 0.0) || !(o->step_floor >= 0.0)) return fail(SABR_LMM_EINVAL, "step_frac > 0 and step_floor >= 0 required");
-  if (o->prec < SABR_LMM_FP64 || o->prec > SABR_LMM_FP32_BF16X3) return fail(SABR_LMM_EINVAL, "unknown precision");
+  if (!valid_prec(o->prec)) return fail(SABR_LMM_EINVAL, "unknown precision");
   if (o->lm_top_k > 0 || o->record_accepts) return fail(SABR_LMM_EINVAL, "anneal_noalloc supports neither the polish nor accept records");
   if (sabr_lmm_status st = check_call(mk, market_idx, 0, o->prec); st != SABR_LMM_OK) return st;
   const DevMarket& m = mk->dm[market_idx];

@@ -15,7 +15,10 @@
 //                            chain or per point (cta_objective in swaption.cuh).
 //   *_batch_kernel ......... many markets: per level a persistent grid over (market, chain)
 //                            items in LPT order.
-//   grad_kernel ............ f and df/dtheta by the reverse sweep (adjoint.cuh).
+//   grad_kernel ............ f and df/dtheta by the reverse sweep (adjoint.cuh), caplet markets.
+//   grad_cta_kernel ........ the same for markets with swaptions, one CTA per point, FP64
+//                            (adjoint_swaption.cuh).
+//   nm_kernel, nm_cta_kernel  Nelder-Mead from n points (nelder_mead.cuh), one warp / CTA each.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -24,6 +27,8 @@
 #include "objective.cuh"
 #include "swaption.cuh"
 #include "adjoint.cuh"
+#include "adjoint_swaption.cuh"
+#include "nelder_mead.cuh"
 
 namespace sabr {
 
@@ -48,33 +53,30 @@ __global__ void setup_swaps_kernel(DevMarket m) {
   for (int k = a; k < b; ++k) {
     const double W = m.tau[k] * m.P[k + 1] / A * pow(m.F[k], m.beta) / pow(S, m.beta);
     m.swap_W[(size_t)s * m.max_win + (k - a)] = W;
-    m.swap_W32[(size_t)s * m.max_win + (k - a)] = (float)W;
   }
   m.swap_A[s] = A;
   m.swap_S[s] = S;
   m.swap_TE[s] = m.T[a];
+  // W_i = u_i / (A S^b): the swap's quadratic forms are scale x the group's forms in u
+  const double as = A * pow(S, m.beta);
+  const double sc = 1.0 / (as * as);
+  ((double*)m.swap_scale64)[s] = sc;
+  ((float*)m.swap_scale32)[s] = (float)sc;
 }
 
-// Coefficient rows of the swaption quadratic forms: (2 - [i = j]) W_i W_j for the pairs i <= j of
-// each swap's window, packed by column (t = j (j + 1)/2 + i), zero-padded to a multiple of 4 pairs,
-// in FP64 and FP32.
-__global__ void setup_swap_coef_kernel(DevMarket m) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= m.n_swap) return;
-  const int L = m.swap_L[s];
-  const double* W = m.swap_W + (size_t)s * m.max_win;
-  double* c64 = (double*)m.swap_C64 + m.swap_coff[s];
-  float* c32 = (float*)m.swap_C32 + m.swap_coff[s];
-  for (int j = 0; j < L; ++j)
-    for (int i = 0; i <= j; ++i) {
-      const double c = (i == j ? 1.0 : 2.0) * W[i] * W[j];
-      c64[j * (j + 1) / 2 + i] = c;
-      c32[j * (j + 1) / 2 + i] = (float)c;
-    }
-  for (int t = L * (L + 1) / 2; t < m.swap_coff[s + 1] - m.swap_coff[s]; ++t) {
-    c64[t] = 0.0;
-    c32[t] = 0.0f;
+// u_{a+i} = tau_{a+i} P(0, T_{a+i+1}) F_{a+i}^b over every group's window (zero past its end), in
+// FP64 and FP32: the swap-independent factor of the frozen weights.
+__global__ void setup_group_u_kernel(DevMarket m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m.n_grp * m.max_gwin) return;
+  const int g = t / m.max_gwin, i = t - g * m.max_gwin;
+  double u = 0.0;
+  if (i < m.grp_L[g]) {
+    const int k = m.grp_a[g] + i;
+    u = m.tau[k] * m.P[k + 1] * pow(m.F[k], m.beta);
   }
+  ((double*)m.grp_u64)[t] = u;
+  ((float*)m.grp_u32)[t] = (float)u;
 }
 
 // Pricing constants of one instrument, into the three 4-vector groups of its block.
@@ -781,8 +783,6 @@ template <class R>
 __device__ __forceinline__ bool stage_market_cta(const CtaSmemS<R>& cs, const DevMarket& m) {
   if (!stage_to_smem2(cs.quad, quad_block<R>(m), (uint32_t)sizeof(QuadTab<R>), nullptr, nullptr, 0u, cs.mbar, m.err))
     return false;
-  stage_group_tables<R>(cta_scratch<R>(cs.scratch, m), m);
-  __syncthreads();
   return true;
 }
 
@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(256, 2) sa_start_cta_kernel(DevMarket m, SASta
 // With staged == false (the CTA's staging gave up and raised the error word) the chain runs no
 // step: it ends the level at the start point with f = +inf, and the ticket is still taken so that
 // the market's level-end minimum completes.
-template <class R, int FORMULA, bool TC = false, bool GT = false>
+template <class R, int FORMULA, bool TC = false>
 __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAParams& sp, int c, int level,
                                 const CtaSmemS<R>& cs, const InstrView<R>& capB, const InstrView<R>& swpB,
                                 const CtaScratch<R>& sc, unsigned long long* s_wacc, bool* s_last,
@@ -894,7 +894,7 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
       if (lane == 0) *s_wacc = wacc;
     }
     __syncthreads();
-    const O fy = cta_objective<R, FORMULA, TC, GT>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr, tc);
+    const O fy = cta_objective<R, FORMULA, TC>(m, capB, swpB, *cs.quad, sc, (O*)cs.red, nullptr, tc);
     const bool acc = metropolis(fy, f, (uint64_t)*s_wacc, T, invT);
     if (acc) {
       x = y;
@@ -1019,8 +1019,8 @@ __global__ void __launch_bounds__(256, 2) sa_level_batch_kernel(BatchArgs ba, in
     const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
     const InstrView<R> swpB = instr_view<R>(cs.swp, m.n_swp_pad);
     CtaScratch<R> sc = cta_scratch<R>(cs.scratch, m);
-    cta_chain_level<R, FORMULA, false, true>(m, sm_st, sm_sp, c, level, cs, capB, swpB, sc, &s_wacc, &s_last, nullptr,
-                                             staged);
+    cta_chain_level<R, FORMULA, false>(m, sm_st, sm_sp, c, level, cs, capB, swpB, sc, &s_wacc, &s_last, nullptr,
+                                       staged);
   }
 }
 
@@ -1117,6 +1117,90 @@ __global__ void grad_kernel(DevMarket m, const double* __restrict__ X, long long
     __syncwarp();
     warp_objective_grad<R, MODEL, FORMULA>(m, capB, *quad, ws, as, lane, f + i, G + i * m.n_param);
   }
+}
+
+// ====================================================================== adjoint (markets with swaptions)
+// One CTA (256 threads) per point, grid-stride, FP64.  Shared memory: the forward CTA plan with the
+// forms' partials in their own region (m.qf_own = 1, set by the launcher), then the adjoint scratch.
+__host__ __device__ inline uint32_t smem_bytes_grad_cta(const DevMarket& m) {
+  return ((smem_bytes_cta<double>(m) + 63u) & ~63u) + grad_scratch_bytes_cta(m);
+}
+
+template <int FORMULA>
+__global__ void __launch_bounds__(256, 1) grad_cta_kernel(DevMarket m, const double* __restrict__ X, long long n,
+                                                       double* __restrict__ f, double* __restrict__ G) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  CtaSmemS<double> cs = carve_cta<double>(smem, m);
+  if (!stage_market_cta<double>(cs, m)) {
+    nan_outputs(blockIdx.x, gridDim.x, n, threadIdx.x, blockDim.x, f, G, m.n_param, nullptr, 0);
+    return;
+  }
+  const GradScratchS gs = grad_scratch_cta(smem + ((smem_bytes_cta<double>(m) + 63u) & ~63u), m);
+  const InstrView<double> capB = instr_view<double>(cs.cap, m.n_cap_pad);
+  const InstrView<double> swpB = instr_view<double>(cs.swp, m.n_swp_pad);
+  CtaScratch<double> sc = cta_scratch<double>(cs.scratch, m);
+  for (long long i = blockIdx.x; i < n; i += gridDim.x) {
+    if (threadIdx.x < kMaxParam)
+      sc.xs[threadIdx.x] = threadIdx.x < (unsigned)m.n_param ? X[i * m.n_param + threadIdx.x] : 0.0;
+    __syncthreads();
+    cta_objective_grad<FORMULA>(m, capB, swpB, *cs.quad, sc, (double*)cs.red, gs, f + i, G + i * m.n_param);
+  }
+}
+
+// ====================================================================== Nelder-Mead polish
+// Caplet markets: one warp (CTA of 32 threads) per start point, grid-stride; shared memory: the
+// market staged as for the FP64 objective, then the simplex.  X is updated in place.
+template <int MODEL, int FORMULA>
+__global__ void nm_kernel(DevMarket m, double* X, long long n, int max_iter, double step, double ftol, double* f,
+                          int* evals) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  CtaSmem<double> cs = carve<double>(smem, m, 1);
+  if (!stage_market<double>(cs, m, false)) {
+    nan_outputs(blockIdx.x, gridDim.x, n, lane, 32, f, X, m.n_param, nullptr, 0);
+    return;
+  }
+  const InstrView<double> capB = instr_view<double>(cs.cap, m.n_cap_pad);
+  WarpScratch<double> ws = warp_scratch<double>((double*)cs.scratch, m.NP, m.n_fwd);
+  const NmTeam team = nm_team((double*)(smem + ((smem_bytes<double>(m, 1) + 15u) & ~15u)));
+  const int P = m.n_param;
+  auto eval = [&](const double* x) {
+    if (lane < kMaxParam) ws.xs[lane] = lane < P ? x[lane] : 0.0;
+    __syncwarp();
+    const double v = obj_to_double(warp_objective<double, MODEL, FORMULA>(m, capB, *cs.quad, ws, lane, nullptr));
+    __syncwarp();
+    return v;
+  };
+  auto sync = []() { __syncwarp(); };
+  for (long long i = blockIdx.x; i < n; i += gridDim.x)
+    nelder_mead(m, team, X + i * P, max_iter, step, ftol, lane, eval, sync, X + i * P, f + i,
+                evals ? evals + i : nullptr);
+}
+
+// Markets with swaptions: one CTA (256 threads) per start point.
+template <int FORMULA>
+__global__ void __launch_bounds__(256, 1) nm_cta_kernel(DevMarket m, double* X, long long n, int max_iter,
+                                                     double step, double ftol, double* f, int* evals) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  CtaSmemS<double> cs = carve_cta<double>(smem, m);
+  if (!stage_market_cta<double>(cs, m)) {
+    nan_outputs(blockIdx.x, gridDim.x, n, threadIdx.x, blockDim.x, f, X, m.n_param, nullptr, 0);
+    return;
+  }
+  const InstrView<double> capB = instr_view<double>(cs.cap, m.n_cap_pad);
+  const InstrView<double> swpB = instr_view<double>(cs.swp, m.n_swp_pad);
+  CtaScratch<double> sc = cta_scratch<double>(cs.scratch, m);
+  const NmTeam team = nm_team((double*)(smem + ((smem_bytes_cta<double>(m) + 15u) & ~15u)));
+  const int P = m.n_param, t = threadIdx.x;
+  auto eval = [&](const double* x) {
+    if (t < kMaxParam) sc.xs[t] = t < P ? x[t] : 0.0;
+    __syncthreads();
+    return obj_to_double(cta_objective<double, FORMULA, false>(m, capB, swpB, *cs.quad, sc, (double*)cs.red, nullptr));
+  };
+  auto sync = []() { __syncthreads(); };
+  for (long long i = blockIdx.x; i < n; i += gridDim.x)
+    nelder_mead(m, team, X + i * P, max_iter, step, ftol, t, eval, sync, X + i * P, f + i,
+                evals ? evals + i : nullptr);
 }
 
 }  // namespace sabr

@@ -16,7 +16,7 @@ namespace sabr {
 constexpr int kQ = 8;               // Gauss-Legendre nodes per panel
 constexpr int kMaxParam = 12;       // parameter slots
 constexpr int kBlkArrays = 12;      // R values per instrument in a block (+ one int)
-constexpr int kChunk = 16;          // pairs per chunk of a swaption quadratic form
+constexpr int kSeg = 4;             // pairs per segment of a group's pair triangle (quadratic forms)
 
 // Quadrature table per precision, offsets relative to the start of a panel of width D:
 //   o[q] = (D/2)(1 + xi_q), w[q] = (D/2) w_q, sw[q] = sqrt(w[q])   (outer rule on the panel)
@@ -101,22 +101,23 @@ struct DevMarket {
   const int* grp_swap0;            // [n_grp + 1] swaps sorted by group: first swap of each group
   const int* swap_grp;             // [n_swap]
   const int* swap_L;               // [n_swap] forwards in the swap
-  int max_npk;                     // max_gwin (max_gwin + 1) / 2
-  const int* grp_pair;             // [n_grp x max_npk] pair t = j (j + 1)/2 + i (i <= j) of the group's
-                                   //   window: (delta_i << 8) | (delta_j - delta_i)
-  const int* swap_coff;            // [n_swap + 1] offsets of the swaps' coefficient rows
-  const double* swap_C64;          // [swap_coff[n_swap]] (2 - [i = j]) W_i W_j, pair-packed as grp_pair,
-                                   //   each row zero-padded to a multiple of 4 pairs
-  const float* swap_C32;           //   the same in FP32
-  int n_chunk;                     // chunks of <= 16 pairs of the swaps' coefficient rows
-  const int4* chunk;               // [n_chunk] {coefficient row offset, group, k | (nk << 16), quads}:
-                                   //   chunk k of its swap's nk takes the swap's 4-pair quads
-                                   //   k, k + nk, ... < quads (ordered by group, then swap)
-  const int* grp_chunk0;           // [n_grp + 1] first chunk of each group
-  const int* swap_chunk0;          // [n_swap + 1] first chunk of each swap
-  int qf_gb;                       // expiry groups whose B matrices are built per barrier
-  int max_batch_chunks;            // most chunks in one such batch
-  int qf_pc_off;                   // offset of the chunk partials in the Y region, or -1 (own region)
+  // quadratic forms by expiry group: with the frozen weights W_i = u_i / (A S^b) of a swap (u_i =
+  // tau_i P(0, T_{i+1}) F_i^b, A the annuity, S the swap rate), every swap of a group is a leading
+  // block of the group's window, so V_k(swap) = scale(swap) Q_k(g, L) with Q_k(g, L) = the sum of
+  // (2 - [i = j]) u_i u_j B_k[i, j] over i <= j < L: one pass over the group's pair triangle serves
+  // all its swaps.  The triangle is cut into segments of at most kSeg pairs of one column j.
+  int n_seg;                       // segments over every group's triangle
+  const int* seg;                  // [n_seg] g | j << 8 | i0 << 16 | (pairs) << 24, column by column
+  int n_col;                       // columns over every group (sum of the group windows)
+  const int* col_seg0;             // [n_col + 1] first segment of each column
+  const int* col_u;                // [n_col] index g * max_gwin + j of the column's u_j
+  const int* grp_col0;             // [n_grp + 1] first column of each group
+  const double* grp_u64;           // [n_grp x max_gwin] u_{a + i} (FP64)
+  const float* grp_u32;            //   the same in FP32
+  const double* swap_scale64;      // [n_swap] 1 / (A S^b)^2
+  const float* swap_scale32;       //   the same in FP32
+  int qf_own;                      // 1: the segment and column partials have their own region
+                                   //   (else they live in the Y region, dead after the Grams)
   double beta, panel;
   // raw description
   const double *T, *P, *cap_K, *cap_vol, *cap_wu, *swp_K, *swp_vol, *swp_wu;
@@ -130,7 +131,6 @@ struct DevMarket {
   double *F, *tau;                 // [n_fwd]
   double *swap_A, *swap_S, *swap_TE;  // [n_swap]
   double* swap_W;                  // [n_swap x max_win] frozen weights W_i = w_i F_i^b / S^b
-  float* swap_W32;                 // the same in FP32
   int* swap_np;                    // [n_swap] panels to the expiry
   double *cap_pm, *cap_w, *swp_pm, *swp_w;  // market prices and weights (FP64)
   void *cblk64, *cblk32, *sblk64, *sblk32;  // instrument blocks

@@ -14,9 +14,11 @@
 //     give, for a swap expiring after nE panels and the pair (i, j) with e = delta_j - delta_i,
 //       G_ij = PG(hi) - PG(lo),  X_ij / theta_ij = PA(hi) - PA(lo) + SH(hi)(PG(hi) - PG(lo)) - (PGS(hi) - PGS(lo))
 //     (lo = delta_i, hi = lo + nE): the composite rule of the oracle, calendar time reversed.
-// S5  Quadratic forms per swap: V = sum_{i<=j} (2 - [i=j]) W_i W_j B_ij, B = (rho G, rho X, phi G),
-//     the B matrices built once per expiry group (swaps sharing their first forward), several
-//     groups per barrier; the coefficient rows (2 - [i=j]) W_i W_j are market constants.
+// S5  Quadratic forms per swap: V = sum_{i<=j} (2 - [i=j]) W_i W_j B_ij, B = (rho G, rho X, phi G).
+//     The frozen weights factor as W_i = u_i / (A S^b) with u_i = tau_i P(0, T_{i+1}) F_i^b, and the
+//     swaps of an expiry group (sharing their first forward) are leading blocks of the group's
+//     window, so one pass over each group's pair triangle, prefix-summed over its columns, gives the
+//     forms of all its swaps: V(swap) = (A S^b)^-2 Q(g, L_swap).
 // S6  alpha_S = sqrt(V1/T), nu_S = sqrt(2 V2)/(alpha_S T), rho_S = clamp(V3/V1, +-0.999), then
 //     SABR and Black per swaption, with the caplets priced alongside.
 #pragma once
@@ -32,39 +34,24 @@ template <class R> struct CtaScratch {
   Q4<R>* Tq;        // [8]
   Q4<R>* T2;        // [8 x 9]
   Q4<R>* Sq;        // [8 x 2] per outer node q the inner-rule sums {Saa, Sab, Sbb, Sac}, {Sbc, Scc, 0, 0}
-  R* Y;             // [NA x 81]
+  R* Y;             // [NA x 84]
   R* PQ;            // [kPQ x ND x PL]: PG, PA, SH, PGS along each diagonal (FP32: then PGl, PGSl,
                     //   the low words of float-float PG and PGS)
   Q4<R>* crq;       // [ND]: {rho_e, rho_e theta_e, phi_e, 0} per diagonal e
-  R* Bg;            // [3 x round_up(Lg (Lg + 1) / 2, 4)] of the current expiry group
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
   R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
-  Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}, then the group table
-                    //   (group_table below)
-  R* Pc;            // [3 x max_batch_chunks] partial sums of one batch's chunks of pairs
+  Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}
+  R* Qs;            // [3 x (n_seg + n_col)] segment partials, then column sums / group prefixes of the
+                    //   quadratic forms (in the Y region, dead after the Grams, unless qf_own)
 };
-
-// [n_grp + 1] per group {first chunk, first swap, window, expiry panel}, right after RCs: copied
-// once per market, so no global loads precede the phase-5 loops.  Its address is derived from RCs
-// rather than held in the scratch record (one live pointer fewer across the chain loop).
-template <class R>
-__device__ __forceinline__ int4* group_table(const CtaScratch<R>& sc, const DevMarket& m) {
-  return (int4*)(sc.RCs + m.n_swap);
-}
 
 // Y row pitch: 16-byte rows, conflict-free 4-vector loads.  The tensor-core form fills all 80 values
 // of a row (g, h and the 64 inner-node products); the ALU form only the first 16 (g and h), the rest
-// of the region serving phase 5's buffers.
+// of the region serving phase 5's partials.
 __host__ __device__ inline int cta_y_stride() { return 84; }
 // Row pitch of the prefix tables: at least NA + 1, and even, so that the pairs of a window column
 // (address stride 1 - pitch along a column) fall on distinct banks.
 __host__ __device__ inline int cta_pq_len(int NA) { return (NA + 2) & ~1; }
-
-// The quadratic forms reuse the Y region (dead after the Grams): the B matrices of qf_gb expiry
-// groups (when two or more fit; else one group at a time in Bg) and, after them, the partial sums
-// of the batch's chunks.  The host picks qf_gb (at most kMaxBatchChunks chunks per batch) and the
-// partials' place (qf_pc_off; -1: their own region of 3 x max_batch_chunks).
-constexpr int kMaxBatchChunks = 512;
 
 // Prefix tables per diagonal: 4 (FP64), 6 (FP32: float-float PG and PGS).
 template <class R> __host__ __device__ constexpr int cta_pq_tables() { return sizeof(R) == 4 ? 6 : 4; }
@@ -72,11 +59,9 @@ template <class R> __host__ __device__ constexpr int cta_pq_tables() { return si
 template <class R>
 __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int NAc = round_up(m.NA, 4);
-  const int Lg = m.max_gwin;
   return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + 4 * 16 + round_up(m.NA * cta_y_stride(), 4) +
-                      round_up(cta_pq_tables<R>() * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND +
-                      3 * round_up(Lg * (Lg + 1) / 2, 4) + 4 * m.n_swap + round_up(m.n_swap, 4) + 4 * m.n_swap +
-                      4 * round_up(m.n_grp + 1, 4) + (m.qf_pc_off >= 0 ? 0 : round_up(3 * m.max_batch_chunks, 4)),
+                      round_up(cta_pq_tables<R>() * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND + 4 * m.n_swap +
+                      round_up(m.n_swap, 4) + 4 * m.n_swap + (m.qf_own ? round_up(3 * (m.n_seg + m.n_col), 4) : 0),
                   4);
 }
 
@@ -84,7 +69,6 @@ template <class R>
 __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m) {
   CtaScratch<R> s;
   const int NAc = round_up(m.NA, 4);
-  const int Lg = m.max_gwin;
   R* p = base;
   s.xs = p; p += 16;
   s.cap = warp_scratch<R>(p, m.NP, m.n_fwd); p += warp_scratch_elems(m.NP, m.n_fwd);
@@ -95,29 +79,19 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
   s.Y = p; p += round_up(m.NA * cta_y_stride(), 4);
   s.PQ = p; p += round_up(cta_pq_tables<R>() * m.ND * cta_pq_len(m.NA), 4);
   s.crq = (Q4<R>*)p; p += 4 * m.ND;
-  s.Bg = p; p += 3 * round_up(Lg * (Lg + 1) / 2, 4);
   s.F4s = (Q4<R>*)p; p += 4 * m.n_swap;
   s.A3s = p; p += round_up(m.n_swap, 4);
   s.RCs = (Q4<R>*)p; p += 4 * m.n_swap;
-  p += 4 * round_up(m.n_grp + 1, 4);   // the group table
-  s.Pc = p;
+  s.Qs = m.qf_own ? p : s.Y;
   return s;
 }
 
-// The group tables of phase 5 into the chain scratch (all threads; the caller synchronises).
-template <class R>
-__device__ __forceinline__ void stage_group_tables(const CtaScratch<R>& sc, const DevMarket& m) {
-  int4* gt = group_table<R>(sc, m);
-  for (int i = threadIdx.x; i <= m.n_grp; i += blockDim.x)
-    gt[i] = make_int4(m.grp_chunk0[i], m.grp_swap0[i], i < m.n_grp ? m.grp_L[i] : 0, i < m.n_grp ? m.grp_nE[i] : 0);
-}
-
-template <class R> __device__ __forceinline__ const R* swap_W_of(const DevMarket& m);
-template <> __device__ __forceinline__ const double* swap_W_of<double>(const DevMarket& m) { return m.swap_W; }
-template <> __device__ __forceinline__ const float* swap_W_of<float>(const DevMarket& m) { return m.swap_W32; }
-template <class R> __device__ __forceinline__ const R* swap_C_of(const DevMarket& m);
-template <> __device__ __forceinline__ const double* swap_C_of<double>(const DevMarket& m) { return m.swap_C64; }
-template <> __device__ __forceinline__ const float* swap_C_of<float>(const DevMarket& m) { return m.swap_C32; }
+template <class R> __device__ __forceinline__ const R* grp_u_of(const DevMarket& m);
+template <> __device__ __forceinline__ const double* grp_u_of<double>(const DevMarket& m) { return m.grp_u64; }
+template <> __device__ __forceinline__ const float* grp_u_of<float>(const DevMarket& m) { return m.grp_u32; }
+template <class R> __device__ __forceinline__ const R* swap_scale_of(const DevMarket& m);
+template <> __device__ __forceinline__ const double* swap_scale_of<double>(const DevMarket& m) { return m.swap_scale64; }
+template <> __device__ __forceinline__ const float* swap_scale_of<float>(const DevMarket& m) { return m.swap_scale32; }
 
 // Barrier 1 over the warps 1.. of the CTA (warp 0 is busy with the caplet mapping meanwhile).
 __device__ __forceinline__ void sync_without_warp0(int nth) {
@@ -237,11 +211,9 @@ __device__ __forceinline__ void window_integrals(const R* PQ, int e, int ND, int
 // Objective of the point in cs.xs (every thread of the CTA calls; all return the same value).
 // `red` is shared scratch of 32 objective values.
 // TC: the pair Grams of phase 3 on the tensor cores (tcgen05_gram.cuh; FP32 pricing only).
-// GT: phase 5 takes its group bounds from the staged group table (the batch kernel, whose market
-// record itself lives in shared memory) rather than from the market's global arrays.
 // res != null: the weighted residuals of every instrument (caplets first) are written as well, by
 // the pricer the search uses.
-template <class R, int FORMULA, bool TC = false, bool GT = false>
+template <class R, int FORMULA, bool TC = false>
 __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrView<R>& capB, const InstrView<R>& swpB,
                                               const QuadTab<R>& qt, const CtaScratch<R>& cs,
                                               typename ObjOf<R>::T* red, double* vols, TcState* tc = nullptr,
@@ -596,166 +568,103 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   }
   __syncthreads();
 
-  // ---- phase 5: the B matrices of a batch of expiry groups, then the quadratic forms of the batch's swaps in chunks of <= 16 pairs (one thread per
-  //      chunk, coefficient rows from the market, partial sums per chunk added per swap in chunk
-  //      order); the batch lives in the Y region (dead since phase 3) when it holds two groups or
-  //      more
+  // ---- phase 5: the quadratic forms by expiry group.  The frozen weights of a swap are W_i = u_i /
+  //      (A S^b) with u_i = tau_i P(0, T_{i+1}) F_i^b independent of the swap, and the swaps of a
+  //      group share their first forward, so each is a leading block of the group's window:
+  //        V_k(swap) = sum_{i <= j < L} (2 - [i = j]) W_i W_j B_k[i, j] = scale(swap) Q_k(g, L),
+  //        Q_k(g, L) = sum_{j < L} u_j sum_{i <= j} (2 - [i = j]) u_i B_k[i, j],
+  //      B = (rho G, rho theta X, phi G) of the pair, its window integrals from the prefix tables.
+  //      (a) segments of <= kSeg pairs of one column, one thread each; (b) per column, u_j times its
+  //      segments in order; (c) per group, prefix sums over its columns (one warp per group); (d)
+  //      per swap, V = scale Q(g, L) and the swap-rate SABR factors.
   {
-    const R* Call = swap_C_of<R>(m);
-    const int npm = (m.max_npk + 3) & ~3;   // B rows padded to whole quads
-    const int GB = m.qf_gb;
-    R* Bbuf = GB > 1 ? cs.Y : cs.Bg;
-    R* Pc = m.qf_pc_off >= 0 ? cs.Y + m.qf_pc_off : cs.Pc;
-    for (int g0 = 0; g0 < m.n_grp; g0 += GB) {
-      const int g1 = min(m.n_grp, g0 + GB);
-      // batch kernel: this thread's first chunk descriptor and first swap's chunk range and expiry,
-      // loaded now so that their latency passes under the B-build
-      int4 ck_pf = make_int4(0, 0, 0, 0);
-      int sc_pf0 = 0, sc_pf1 = 0;
-      double te_pf = 1.0;
-      if constexpr (GT) {
-        const int4* gt = group_table<R>(cs, m);
-        if (gt[g0].x + tid < gt[g1].x) ck_pf = m.chunk[gt[g0].x + tid];
-        const int sp = gt[g0].y + tid;
-        if (sp < gt[g1].y) {
-          sc_pf0 = m.swap_chunk0[sp];
-          sc_pf1 = m.swap_chunk0[sp + 1];
-          te_pf = m.swap_TE[sp];
+    R* Ps = cs.Qs;                  // [3 x n_seg]
+    R* Pc = cs.Qs + 3 * m.n_seg;    // [3 x n_col]
+    const R* U = grp_u_of<R>(m);
+    const int ns = m.n_seg, nc = m.n_col, W = m.max_gwin;
+    for (int q = tid; q < ns; q += nth) {
+      const int w = m.seg[q];
+      const int g = w & 255, j = (w >> 8) & 255, i0 = (w >> 16) & 255, ni = w >> 24;
+      const int* dl = m.grp_delta + g * W;
+      const R* u = U + g * W;
+      const int nE = m.grp_nE[g], dj = dl[j];
+      R s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+      for (int r = 0; r < kSeg; ++r) {
+        if (r < ni) {
+          const int i = i0 + r;
+          const int lo = dl[i], e = dj - lo;
+          R G, X;
+          window_integrals<R>(cs.PQ, e, ND, PL, lo, lo + nE, G, X);
+          const Q4<R> cr = cs.crq[e];
+          const R c = (i == j ? R(1) : R(2)) * u[i];
+          s1 += c * (cr.a * G);
+          s2 += c * (cr.b * X);
+          s3 += c * (cr.c * G);
         }
       }
-      if constexpr (GT) {
-        // B-build in the batch kernel, kPf groups at a time: every pair word of those groups (global
-        // memory, mostly from L2 beside the batch's coefficient rows) is loaded before the first is
-        // used, so the groups share one load latency
-        constexpr int kPf = 4;
-        for (int gb = g0; gb < g1; gb += kPf) {
-          int nE[kPf], npk[kPf];
+      Ps[q] = s1;
+      Ps[ns + q] = s2;
+      Ps[2 * ns + q] = s3;
+    }
+    __syncthreads();
+    for (int c = tid; c < nc; c += nth) {
+      const int q0 = m.col_seg0[c], q1 = m.col_seg0[c + 1];
+      R v1 = 0, v2 = 0, v3 = 0;
+      for (int q = q0; q < q1; ++q) {
+        v1 += Ps[q];
+        v2 += Ps[ns + q];
+        v3 += Ps[2 * ns + q];
+      }
+      const R uj = U[m.col_u[c]];
+      Pc[c] = uj * v1;
+      Pc[nc + c] = uj * v2;
+      Pc[2 * nc + c] = uj * v3;
+    }
+    __syncthreads();
+    for (int g = warp; g < m.n_grp; g += nw) {   // inclusive prefix over the group's columns
+      const int c0 = m.grp_col0[g], n = m.grp_col0[g + 1] - c0;
+      R run[3] = {0, 0, 0};
+      for (int b = 0; b < n; b += 32) {
+        const int c = b + lane;
+        const bool in = c < n;
 #pragma unroll
-          for (int i = 0; i < kPf; ++i) {
-            const int g = gb + i;
-            const int Lg = g < g1 ? m.grp_L[g] : 0;
-            nE[i] = g < g1 ? m.grp_nE[g] : 0;
-            npk[i] = Lg * (Lg + 1) / 2;
-            R* B = Bbuf + (g - g0) * 3 * npm;
-            for (int t = npk[i] + tid; t < ((npk[i] + 3) & ~3); t += nth) {   // zero pads of the last quad
-              B[t] = R(0);
-              B[npm + t] = R(0);
-              B[2 * npm + t] = R(0);
-            }
-          }
-          for (int t0 = 0; t0 < m.max_npk; t0 += nth) {
-            const int t = t0 + tid;
-            int pk[kPf];
-#pragma unroll
-            for (int i = 0; i < kPf; ++i) pk[i] = t < npk[i] ? m.grp_pair[(gb + i) * m.max_npk + t] : 0;
-#pragma unroll
-            for (int i = 0; i < kPf; ++i) {
-              if (t >= npk[i]) continue;
-              const int e = pk[i] & 255, lo = pk[i] >> 8, hi = lo + nE[i];
-              R G, X;
-              window_integrals<R>(cs.PQ, e, ND, PL, lo, hi, G, X);
-              const Q4<R> cr = cs.crq[e];
-              R* B = Bbuf + (gb + i - g0) * 3 * npm;
-              B[t] = cr.a * G;
-              B[npm + t] = cr.b * X;
-              B[2 * npm + t] = cr.c * G;
-            }
-          }
-        }
-      } else {
-        // B-build, one group after the other (the pair words are L1-resident for a single market)
-        for (int g = g0; g < g1; ++g) {
-          const int Lg = m.grp_L[g], nE = m.grp_nE[g];   // uniform loads
-          const int* gp = m.grp_pair + g * m.max_npk;
-          R* B = Bbuf + (g - g0) * 3 * npm;
-          const int npk = Lg * (Lg + 1) / 2;
-          for (int t = npk + tid; t < ((npk + 3) & ~3); t += nth) {   // zero pads of the last quad
-            B[t] = R(0);
-            B[npm + t] = R(0);
-            B[2 * npm + t] = R(0);
-          }
-          for (int t = tid; t < npk; t += nth) {
-            const int pk = gp[t];
-            const int e = pk & 255, lo = pk >> 8, hi = lo + nE;
-            R G, X;
-            window_integrals<R>(cs.PQ, e, ND, PL, lo, hi, G, X);
-            const Q4<R> cr = cs.crq[e];
-            B[t] = cr.a * G;
-            B[npm + t] = cr.b * X;
-            B[2 * npm + t] = cr.c * G;
-          }
+        for (int k = 0; k < 3; ++k) {
+          const R v = in ? Pc[k * nc + c0 + c] : R(0);
+          const R iv = warp_inclusive_scan<R>(v, lane);
+          __syncwarp();
+          if (in) Pc[k * nc + c0 + c] = run[k] + iv;
+          run[k] += __shfl_sync(0xffffffffu, iv, 31);
         }
       }
-      __syncthreads();
-      // chunks of <= 16 pairs, one thread each (partials per chunk, summed per swap below): a chunk
-      // takes up to 4 quads of 4 pairs, interleaved (stride nk) so that neighbouring threads read
-      // neighbouring quads; one 16-byte coefficient load and three 16-byte B loads per quad
-      const int c0 = GT ? group_table<R>(cs, m)[g0].x : m.grp_chunk0[g0];
-      const int c1 = GT ? group_table<R>(cs, m)[g1].x : m.grp_chunk0[g1];
-      for (int c = c0 + tid; c < c1; c += nth) {
-        // one load: no dependent per-swap lookups before the rows
-        const int4 ck = (GT && c == c0 + tid) ? ck_pf : m.chunk[c];
-        const int k = ck.z & 0xffff, nk = ck.z >> 16, nq = ck.w;
-        const R* B = Bbuf + (ck.y - g0) * 3 * npm;
-        const Q4<R>* Cq = (const Q4<R>*)(Call + ck.x);
-        const Q4<R>* B1 = (const Q4<R>*)B;
-        const Q4<R>* B2 = (const Q4<R>*)(B + npm);
-        const Q4<R>* B3 = (const Q4<R>*)(B + 2 * npm);
-        R v1 = 0, v2 = 0, v3 = 0;
-        // the chunk's <= kChunk / 4 quads, unrolled so that the coefficient loads (global memory)
-        // can be issued together
-#pragma unroll
-        for (int i = 0; i < kChunk / 4; ++i) {
-          const int q = k + i * nk;
-          if (q < nq) {
-            const Q4<R> w = Cq[q], x = B1[q], y = B2[q], z = B3[q];
-            v1 += w.a * x.a; v1 += w.b * x.b; v1 += w.c * x.c; v1 += w.d * x.d;
-            v2 += w.a * y.a; v2 += w.b * y.b; v2 += w.c * y.c; v2 += w.d * y.d;
-            v3 += w.a * z.a; v3 += w.b * z.b; v3 += w.c * z.c; v3 += w.d * z.d;
-          }
-        }
-        const int pc = c - c0, nb = m.max_batch_chunks;
-        Pc[pc] = v1;
-        Pc[nb + pc] = v2;
-        Pc[2 * nb + pc] = v3;
-      }
-      __syncthreads();
-      // per swap of the batch: its chunks added in order, then the swap-rate SABR factors (the
-      // next batch overwrites Pc only after its own B-build barrier)
-      const int s0 = GT ? group_table<R>(cs, m)[g0].y : m.grp_swap0[g0];
-      const int s1 = GT ? group_table<R>(cs, m)[g1].y : m.grp_swap0[g1];
-      for (int s = s0 + tid; s < s1; s += nth) {
-        const int nb = m.max_batch_chunks;
-        const bool first = GT && s == s0 + tid;
-        const int ca = first ? sc_pf0 : m.swap_chunk0[s], cb = first ? sc_pf1 : m.swap_chunk0[s + 1];
-        R v1 = 0, v2 = 0, v3 = 0;
-        for (int c = ca; c < cb; ++c) {
-          v1 += Pc[c - c0];
-          v2 += Pc[nb + c - c0];
-          v3 += Pc[2 * nb + c - c0];
-        }
-        // (FP32: the hardware reciprocal and reciprocal square root, as in the caplet mapping; FP64
-        // exact.  nu = 0 stays 0.)
-        const R TE = (R)(first ? te_pf : m.swap_TE[s]);
-        const R al = fsqrt<R>(fdiv<R>(v1, TE));
-        const R v2x = R(2) * v2;
-        const R nu = v2x > R(0) ? fdiv<R>(fsqrt<R>(v2x), al * TE) : R(0);
-        R rho = fdiv<R>(v3, v1);
-        rho = rho > R(0.999) ? R(0.999) : (rho < R(-0.999) ? R(-0.999) : rho);
-        Q4<R> f;
-        f.a = al;
-        f.b = fdiv<R>(nu, al);
-        f.c = al * al;
-        f.d = rho * nu * al;
-        cs.F4s[s] = f;
-        cs.A3s[s] = (R(2) - R(3) * rho * rho) * nu * nu;
-        Q4<R> q;
-        q.a = rho;
-        q.b = fdiv<R>(R(1), R(1) - rho);
-        q.c = fdiv<R>(R(1), R(1) + rho);
-        q.d = (R(1) - rho) * (R(1) + rho);
-        cs.RCs[s] = q;
-      }
+    }
+    __syncthreads();
+    const R* SC = swap_scale_of<R>(m);
+    for (int s = tid; s < m.n_swap; s += nth) {
+      const int c = m.grp_col0[m.swap_grp[s]] + m.swap_L[s] - 1;
+      const R sc = SC[s];
+      const R v1 = sc * Pc[c], v2 = sc * Pc[nc + c], v3 = sc * Pc[2 * nc + c];
+      // (FP32: the hardware reciprocal and reciprocal square root, as in the caplet mapping; FP64
+      // exact.  nu = 0 stays 0.)
+      const R TE = (R)m.swap_TE[s];
+      const R al = fsqrt<R>(fdiv<R>(v1, TE));
+      const R v2x = R(2) * v2;
+      const R nu = v2x > R(0) ? fdiv<R>(fsqrt<R>(v2x), al * TE) : R(0);
+      R rho = fdiv<R>(v3, v1);
+      rho = rho > R(0.999) ? R(0.999) : (rho < R(-0.999) ? R(-0.999) : rho);
+      Q4<R> f;
+      f.a = al;
+      f.b = fdiv<R>(nu, al);
+      f.c = al * al;
+      f.d = rho * nu * al;
+      cs.F4s[s] = f;
+      cs.A3s[s] = (R(2) - R(3) * rho * rho) * nu * nu;
+      Q4<R> q;
+      q.a = rho;
+      q.b = fdiv<R>(R(1), R(1) - rho);
+      q.c = fdiv<R>(R(1), R(1) + rho);
+      q.d = (R(1) - rho) * (R(1) + rho);
+      cs.RCs[s] = q;
     }
     __syncthreads();
   }

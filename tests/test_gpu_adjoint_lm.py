@@ -200,3 +200,82 @@ def test_autograd_function_gradcheck(gpu_lib):
     Xn = sk.theta_true[None, :] * (1.0 + 0.05 * rng.standard_normal((2, sk.n_param)))
     X = torch.tensor(Xn, dtype=torch.float64, device="cuda", requires_grad=True)
     assert torch.autograd.gradcheck(lambda x: gm.calibration_objective(x), (X,), eps=1e-7, atol=1e-6, rtol=1e-4)
+
+
+def _swaptions_only():
+    sk = synth.joint_caplet_swaption(n_fwd=24, expiries=(1, 2, 4, 6), tenors=(1, 3, 5), swp_m=(-0.3, 0.0, 0.3))
+    keep = np.arange(sk.n_cap, sk.n_instr)
+    return sk.replace(cap_fwd=np.zeros(0, np.int32), cap_K=np.zeros(0), noise=sk.noise[keep])
+
+
+SWAPTION_CASES = {
+    "joint_small": lambda: synth.joint_caplet_swaption(expiries=(1, 2, 3), tenors=(1, 2, 3), swp_m=(-0.4, 0.0, 0.4)),
+    "joint_40f_300c_700s": lambda: synth.joint_caplet_swaption(),
+    "swaptions_only": _swaptions_only,
+    "batch_member_3": lambda: synth.batch_market(3),
+}
+
+
+@pytest.mark.parametrize("name", list(SWAPTION_CASES))
+def test_swaption_adjoint_fp64_matches_oracle_dual_gradient(gpu_lib, name):
+    # the reverse sweep through pricing, the swap-rate SABR parameters, the group forms, the window
+    # integrals, the prefix tables, the Grams, the Y rows and the correlation tables: every one of
+    # the 12 slots against the oracle's forward-mode dual numbers
+    sk = SWAPTION_CASES[name]()
+    om, gm = _markets(sk)
+    X = np.vstack([_points(sk, 5, seed=35), sk.theta_true[None, :]])
+    f, G = gm.objective_grad(X, "fp64")
+    f, G = f.cpu().numpy(), G.cpu().numpy()
+    worst = 0.0
+    for i in range(X.shape[0]):
+        fo, go = om.objective_grad(X[i])
+        if not np.isfinite(fo):
+            assert not np.isfinite(f[i])
+            continue
+        assert f[i] == pytest.approx(fo, rel=1e-12)
+        scale = np.max(np.abs(go))
+        worst = max(worst, np.max(np.abs(G[i] - go)) / scale)
+        assert np.max(np.abs(G[i] - go)) <= 1e-9 * scale, (i, G[i], go)
+    print(f"{name}: swaption adjoint, largest gradient error {worst:.2e} of the largest component")
+
+
+def test_swaption_adjoint_matches_central_differences(gpu_lib):
+    sk = SWAPTION_CASES["joint_small"]()
+    om, gm = _markets(sk)
+    X = _points(sk, 3, seed=36)
+    _, G = gm.objective_grad(X, "fp64")
+    G = G.cpu().numpy()
+    P = sk.n_param
+    for i in range(X.shape[0]):
+        h = 1e-6 * np.maximum(np.abs(X[i]), 1.0)
+        Xp = np.repeat(X[i][None, :], 2 * P, axis=0)
+        for k in range(P):
+            Xp[2 * k, k] += h[k]
+            Xp[2 * k + 1, k] -= h[k]
+        fp = gm.objective(Xp, "fp64").cpu().numpy()
+        fd = (fp[0::2] - fp[1::2]) / (2 * h)
+        assert np.max(np.abs(G[i] - fd)) <= 1e-6 * np.max(np.abs(fd)), (G[i], fd)
+
+
+def test_swaption_adjoint_fp32_request_runs_in_fp64(gpu_lib):
+    sk = SWAPTION_CASES["joint_small"]()
+    om, gm = _markets(sk)
+    X = _points(sk, 4, seed=37)
+    f64, G64 = gm.objective_grad(X, "fp64")
+    f32, G32 = gm.objective_grad(X, "fp32")
+    assert np.array_equal(f64.cpu().numpy(), f32.cpu().numpy())
+    assert np.allclose(G64.cpu().numpy(), G32.cpu().numpy(), rtol=1e-12, atol=0)
+
+
+def test_swaption_adjoint_secondary_run_on_the_joint_market(gpu_lib):
+    # the gradient workload's secondary run: many parameter sets on the 40-forward caplet + swaption
+    # market (all 12 slots free), checked on a sample
+    sk = synth.joint_caplet_swaption()
+    om, gm = _markets(sk)
+    X = _points(sk, 2048, seed=38)
+    f, G = gm.objective_grad(X, "fp64")
+    f, G = f.cpu().numpy(), G.cpu().numpy()
+    for i in (0, 1023, 2047):
+        fo, go = om.objective_grad(X[i])
+        assert f[i] == pytest.approx(fo, rel=1e-12)
+        assert np.max(np.abs(G[i] - go)) <= 1e-9 * np.max(np.abs(go))

@@ -66,10 +66,11 @@ def test_bf16x3_anneal_runs_and_improves(gpu_lib):
     assert om.objective(r["x_best"][0]) == pytest.approx(r["f_best"][0], rel=2e-2)
 
 
-def test_tf32x3_not_built_for_swaptions(gpu_lib):
+def test_precision_value_2_is_rejected(gpu_lib):
+    # the enum has no TF32 split form: the value 2 is not a precision of the library
     import paper_2408_01470_b300 as lib
     sk = CASES["joint_small"]()
     om, gm = _markets(sk)
     with pytest.raises(lib.SabrLmmError) as e:
-        gm.objective(sk.theta_true[None, :], "tf32x3")
-    assert e.value.status == 5
+        gm.objective(sk.theta_true[None, :], 2)
+    assert e.value.status == 1

@@ -466,3 +466,55 @@ def test_lm_recovers_rebonato_caplet_parameters_from_nearby_start():
     p = m.lm(th0, max_iter=200)
     assert p["rmse"] < 1e-6
     assert p["f"] < 1e-14
+
+
+# ---------------------------------------------------------------- Nelder-Mead (the hybrid's local search)
+def test_nm_recovers_the_smile_from_a_nearby_start():
+    sk = synth.smile_2y(noise_free=True)
+    m, _ = oracle.quoted_market(sk, noise=False)
+    th0 = sk.theta_true * np.array([1.05, 0.9, 1.1])
+    p = m.nm(th0, max_iter=2000, step=0.02, ftol=1e-15)
+    assert p["f"] < 1e-16
+    assert np.max(np.abs(p["theta"] - sk.theta_true) / np.abs(sk.theta_true)) < 1e-5
+
+
+def test_nm_one_free_slot_matches_a_bracketing_minimiser():
+    # alpha alone free (rho, nu at the truth, noisy quotes): the minimum is a 1-D problem that
+    # scipy's bounded Brent search solves independently
+    from scipy.optimize import minimize_scalar
+    sk = synth.smile_2y()
+    free = np.array([1, 0, 0], np.uint8)
+    sk1 = sk.replace(free=free)
+    m, _ = oracle.quoted_market(sk1)
+    th0 = sk.theta_true.copy()
+    th0[0] *= 1.2
+    p = m.nm(th0, max_iter=400, step=0.02, ftol=1e-15)
+
+    def f1(a):
+        t = sk.theta_true.copy()
+        t[0] = a
+        return m.objective(t)
+    r = minimize_scalar(f1, bounds=(sk.lo[0], sk.hi[0]), method="bounded", options={"xatol": 1e-12})
+    assert p["theta"][0] == pytest.approx(r.x, rel=1e-6)
+    assert p["f"] <= r.fun * (1 + 1e-10)
+    assert np.array_equal(p["theta"][1:], sk.theta_true[1:])
+
+
+def test_nm_best_value_never_increases_and_counts_its_evaluations():
+    sk = synth.caplet_term_structure(n_fwd=7, n_strikes=5)
+    m, _ = oracle.quoted_market(sk)
+    th0 = 0.5 * (sk.box_centre() + sk.theta_true)
+    nf = int(sk.free.sum())
+    p0 = m.nm(th0, max_iter=0)
+    assert p0["evals"] == nf + 1 and p0["iters"] == 0
+    prev = p0["f"]
+    assert prev <= m.objective(th0)
+    for k in (1, 2, 5, 10, 25, 60):
+        p = m.nm(th0, max_iter=k)
+        assert p["f"] <= prev
+        assert p["f"] == pytest.approx(m.objective(p["theta"]), rel=0, abs=0)
+        # per iteration 1 (reflection) to 2 + nf (contraction then shrink) evaluations
+        assert nf + 1 + k <= p["evals"] <= nf + 1 + k * (2 + nf)
+        prev = p["f"]
+    # every returned point lies in the box
+    assert np.all(p["theta"] >= sk.lo) and np.all(p["theta"] <= sk.hi)
