@@ -321,9 +321,17 @@ def rmse_per_level(gm, trace_x, quotes, market=0):
     return 100.0 * np.sqrt(np.mean((v - np.asarray(quotes)[None, :]) ** 2, axis=1))
 
 
+def rmse_trace(gm, r, quotes):
+    """(true vol RMSE, device seconds) of each level's best end point and, last, of the search's
+    result (the best point ever accepted, taken by the final reduction right after the last level)."""
+    rm = rmse_per_level(gm, r["trace_x"][0], quotes)
+    sec = np.asarray(r["trace_seconds"][0], dtype=np.float64)
+    return np.append(rm, float(r["rmse_volpt"][0])), np.append(sec, sec[-1])
+
+
 def first_hit(rmse, seconds, target):
-    """(level, device seconds from the search's start) of the first level whose best point reaches
-    the target RMSE, or None."""
+    """(level, device seconds from the search's start) of the first entry of a trace that reaches the
+    target RMSE, or None (level L + 1: the search's final result)."""
     hit = np.nonzero(rmse <= target)[0]
     return None if hit.size == 0 else {"level": int(hit[0]) + 1, "seconds": float(seconds[hit[0]])}
 
@@ -334,18 +342,22 @@ def roofline_alu(flops_per_launch, level_s, peak_tflops, traffic, kernel, source
             "frac": achieved / peak_tflops, "traffic": traffic, "kernel": kernel, "peak_source": source}
 
 
-def search_record(lib, name, prec, seed, stream, peaks, levels=None, cpu=None, e2e=True, chains=None):
+def search_record(lib, name, prec, seed, stream, peaks, levels=None, cpu=None, e2e=True, chains=None,
+                  warps_per_block=0):
     """One timed search of a named workload (after a 2-level warm-up of the same kernels), with its
     rate, roofline, quality, end-to-end rate and (cpu = dict of sample sizes) the oracle baseline."""
     import torch
     gm, sks, vols, C, L0, N, cool = workload_markets(lib, name)
     C = chains or C
     L = levels or L0
-    warm = gm.anneal_prepare(C, min(2, L), N, cool, seed, prec=prec, use_graph=True, stream=stream)
+    warm = gm.anneal_prepare(C, min(2, L), N, cool, seed, prec=prec, use_graph=True, stream=stream,
+                             warps_per_block=warps_per_block)
     warm.launch(stream=stream)
     warm.fetch()
     del warm
-    plan = gm.anneal_prepare(C, L, N, cool, seed, prec=prec, use_graph=True, stream=stream)
+    plan = gm.anneal_prepare(C, L, N, cool, seed, prec=prec, use_graph=True, stream=stream,
+                             warps_per_block=warps_per_block)
+    tuning = plan.config()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     plan.launch(stream=stream)
@@ -359,7 +371,7 @@ def search_record(lib, name, prec, seed, stream, peaks, levels=None, cpu=None, e
            f"{name}: {C} chains x {L} levels x {N} steps", "prec": prec, "chains": C, "levels_timed": L,
            "levels_of_schedule": L0, "extrapolated": L != L0, "value": r["n_evals"] * n_instr / t, "unit": UNIT,
            "seconds": t, "ms_per_level": 1e3 * t / L, "chain_steps_per_s": C * L * N * len(sks) / t,
-           "rmse_volpt": float(np.median(r["rmse_volpt"]))}
+           "rmse_volpt": float(np.median(r["rmse_volpt"])), "tuning": tuning}
     if len(sks) == 1:
         info = gm.info()
         fl = C * N * flops_per_chain_step(sks[0], info)
@@ -377,12 +389,55 @@ def search_record(lib, name, prec, seed, stream, peaks, levels=None, cpu=None, e
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m2 = lib.Market(sks if len(sks) > 1 else sks[0], vols if len(sks) > 1 else vols[0])
-        r2 = m2.anneal(C, L, N, cool, seed, prec=prec)
+        r2 = m2.anneal(C, L, N, cool, seed, prec=prec, warps_per_block=warps_per_block)
         del m2
         te = time.perf_counter() - t0
         rec["e2e"] = {"value": r2["n_evals"] * n_instr / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(len(sks) * (sks[0].n_param + 2 + L) * 8)}
     return rec, r, gm, sks, vols
+
+
+PAPER_DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "paper_euribor_20111121.txt")
+
+
+def paper_data_record(lib, seed, stream):
+    """The paper's real-data caplet calibration (Section 4.1.1): the 13 EURIBOR smiles, the paper's
+    schedule (16384 chains, N = 10, cooling 0.99, T0 = 10 to 0.01: 688 levels) and hybrid (the search,
+    then Nelder-Mead from the best chains), FP32 search and FP64 simplex; device time of each part
+    and the mean relative vol error, beside the paper's own figures (another GPU: context)."""
+    import torch
+    from paper_2408_01470_b300 import synth
+    sks, quotes, params, pub = synth.paper_euribor_caplet_smiles(PAPER_DATA)
+    gm = lib.Market(sks, quotes)
+    sk = sks[0]
+    kw = dict(prec="fp32", T0=10.0, lm_top_k=8, lm_max_iter=2000, polish_nm=True, use_graph=True, stream=stream)
+    warm = gm.anneal_prepare(sk.n_chains, 2, sk.steps, sk.cooling, seed, **kw)
+    warm.launch(stream=stream)
+    warm.fetch()
+    del warm
+    plan = gm.anneal_prepare(sk.n_chains, sk.n_levels, sk.steps, sk.cooling, seed, **kw)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plan.launch(stream=stream)
+    b.record(stream)
+    stream.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    r = plan.fetch()
+    del plan
+    rel = []
+    for j, q in enumerate(quotes):
+        v = gm.model_vols(r["x_best"][j][None, :], "fp64", market=j).cpu().numpy()[0]
+        rel += list(np.abs(v - q) / q)
+    n_prices = r["n_evals"] * len(sks) * sk.n_cap
+    return {"workload": f"paper_euribor_caplets_13x9_{sk.n_chains}ch_x_{sk.n_levels}T_x_{sk.steps}steps",
+            "how": "13 smiles, one search each in one call (the paper's cost is separable over the forwards); "
+                   "device time of the whole call (CUDA events), of which the Nelder-Mead polish",
+            "seconds": t, "sa_seconds": t - float(r["lm_seconds"]), "nm_seconds": float(r["lm_seconds"]),
+            "mre": float(np.mean(rel)), "evaluations_per_smile": int(r["n_evals"]),
+            "prices_per_s": n_prices / t, "f_best": [float(x) for x in r["f_best"]],
+            "paper": {"mre": float(pub["mre"]), "sa_seconds": float(pub["sa_seconds"]),
+                      "nm_seconds": float(pub["nm_seconds"]), "total_seconds": float(pub["total_seconds"]),
+                      "evaluations": int(pub["evaluations"]), "hardware": pub["hardware"]}}
 
 
 def lm_schedule_to_target(gm, C, N, cool, seed, target, schedule=(1, 2, 3, 5, 10, 20, 40, 80, 200)):
@@ -399,9 +454,11 @@ def lm_schedule_to_target(gm, C, N, cool, seed, target, schedule=(1, 2, 3, 5, 10
 
 
 def run_quality(args):
-    """FP32 against FP64: the final vol RMSE of seeds 0..n-1 of a workload's search, without and with
-    the polish of the 64 best chains, on one GPU.  Prints one JSON line."""
+    """FP32 against FP64: the final vol RMSE of --seeds seeds of a workload's search, and of that
+    search's best point after the Levenberg-Marquardt polish (adjoint gradient), on one GPU.  Prints
+    one JSON line (per-seed rows on stderr)."""
     import paper_2408_01470_b300 as lib
+    import torch
     lib.load()
     gm, sks, vols, C, L, N, cool = workload_markets(lib, args.workload)
     C = args.chains or C
@@ -411,9 +468,14 @@ def run_quality(args):
         row = {"seed": seed}
         for prec in ("fp64", "fp32"):
             r = gm.anneal(C, L, N, cool, seed, prec=prec)
-            rp = gm.anneal(C, L, N, cool, seed, prec=prec, lm_top_k=64, lm_max_iter=50)
+            # the adjoint-driven Levenberg-Marquardt polish of the search's best point (FP64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Xp, fp, rp = gm.lm_polish(r["x_best"], max_iter=50)
+            rp = float(rp.cpu().numpy()[0])
+            tp = time.perf_counter() - t0
             row[prec] = {"rmse_volpt": float(r["rmse_volpt"][0]), "seconds": float(r["seconds"]),
-                         "polished_rmse_volpt": float(rp["rmse_volpt"][0]), "polish_s": float(rp["lm_seconds"])}
+                         "polished_rmse_volpt": rp, "polish_s": tp}
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
     out = {"quality": True, "workload": args.workload, "chains": C, "levels": L, "steps": N, "seeds": args.seeds}
@@ -463,7 +525,8 @@ def run_workload_line(args):
             **{k: rec[k] for k in rec if k in ("roofline", "e2e", "cpu_baseline")},
             "chain_steps_per_s": rec["chain_steps_per_s"], "ms_per_level": rec["ms_per_level"],
             "rmse_volpt_median": rec["rmse_volpt"], "clocks": clk.summary(), "peaks": peaks,
-            "gpu_launches": r["n_evals"] and (rec["levels_timed"] + 2)}
+            "gpu_launches": rec["levels_timed"] * max(1, len(rec["tuning"]["buckets"])) + 2,
+            "tuning": rec["tuning"]}
     print(json.dumps(line))
 
 
@@ -478,6 +541,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-joint-variant", action="store_true")
     ap.add_argument("--no-batch-variant", action="store_true")
+    ap.add_argument("--no-paper-data", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--clocks-dir", default="", help="folder for the raw nvidia-smi clock samples (default: temp dir)")
     ap.add_argument("--warps-per-block", type=int, default=0)
@@ -521,6 +585,7 @@ def main():
     s = torch.cuda.Stream()
     plan = gm.anneal_prepare(C, L, N, skel.cooling, seed, prec=args.prec, use_graph=True, stream=s,
                              warps_per_block=args.warps_per_block)
+    tuning = plan.config()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         plan.launch(stream=s)
@@ -557,9 +622,9 @@ def main():
                             LEVEL_TRAFFIC_BYTES_FP32 if args.prec == "fp32" and not args.warps_per_block else None,
                             "sa_level_kernel", src)
 
-    rmse32 = rmse_per_level(gm, res["trace_x"][0], vols)
+    rmse32, sec32 = rmse_trace(gm, res, vols)
     quality = {"f_best": float(res["f_best"][0]), "rmse_volpt": float(res["rmse_volpt"][0]),
-               "rmse_volpt_last_level": float(rmse32[-1])}
+               "rmse_volpt_last_level": float(rmse32[-2])}
 
     # e2e: through the public API from host buffers (H2D of the market, D2H of the results)
     e2e_vals = []
@@ -592,7 +657,7 @@ def main():
         t64 = a.elapsed_time(b) / 1e3
         r64 = plan64.fetch()
         del plan64
-        rmse64 = rmse_per_level(gm, r64["trace_x"][0], vols)
+        rmse64, sec64 = rmse_trace(gm, r64, vols)
         R64 = float(r64["rmse_volpt"][0])
         variants["fp64"] = {"value": prices_per_step / t64, "ms_per_step": t64 * 1e3, "rmse_volpt": R64,
                             "f_best": float(r64["f_best"][0]), "chain_steps_per_s": C * L * N / t64,
@@ -600,8 +665,8 @@ def main():
                                                      "sa_level_kernel", "measured FP64 FMA rate (libsabr_peaks.so)")}
         for name, target in (("target_0p05", TARGET_RMSE_VOLPT), ("target_fp64_final", R64)):
             ttt[name] = {"target_rmse_volpt": target,
-                         "fp64": first_hit(rmse64, r64["trace_seconds"][0], target),
-                         "fp32": first_hit(rmse32, res["trace_seconds"][0], target),
+                         "fp64": first_hit(rmse64, sec64, target),
+                         "fp32": first_hit(rmse32, sec32, target),
                          "fp32_lm_polished": lm_schedule_to_target(gm, C, N, skel.cooling, seed, target)}
 
     # the joint caplet + swaption market (CTA-per-chain kernels) over its full schedule, and shortened
@@ -614,6 +679,9 @@ def main():
         for jprec in ("fp64", "bf16x3"):
             rec, _, _, _, _ = search_record(lib, "joint", jprec, seed, s, peaks, levels=1, e2e=False)
             workloads["joint_" + jprec] = rec
+    # the paper's real-data caplet calibration, full schedule
+    if args.prec == "fp32" and not args.no_paper_data:
+        workloads["paper_euribor_caplets"] = paper_data_record(lib, seed, s)
     # the 256-market batch: one level (its full 100-level schedule: bench.py --workload batch)
     if args.prec == "fp32" and not args.no_batch_variant:
         rec, _, _, _, _ = search_record(lib, "batch", "fp32", seed, s, peaks, levels=1, e2e=False)
@@ -629,7 +697,8 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps * (L + 2), "clocks": clocks,
             "chain_steps_per_s": ws * C * L * N * args.steps / total_s_max, "peaks": peaks,
-            "quality": quality, "time_to_target": ttt, "variants": variants, "workloads": workloads}
+            "quality": quality, "time_to_target": ttt, "variants": variants, "workloads": workloads,
+            "tuning": tuning}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(skel, vols, levels=1, steps=100)
         cb1 = cpu_baseline(skel, vols, levels=1, steps=4, threads=1)

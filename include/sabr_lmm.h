@@ -200,7 +200,9 @@ typedef struct {
   double target_rmse_volpt;
   int32_t warps_per_block; /* chains (warps) per CTA of the caplet level kernel, 0..28; 0 -> FP32: one
                               CTA of up to 28 chains per SM, FP64: 4 (FP64 is capped at 4); batch:
-                              0 -> autotuned CTA size, >= 8 -> 256 threads, else 128           */
+                              0 -> autotuned CTA size, >= 8 -> 256 threads, else 128; a single
+                              market with swaptions: 0..4 -> 128-thread CTAs (one per chain; the
+                              faster form), else 256 threads (the tensor-core form always 256) */
   int32_t use_graph;       /* 1 -> the level loop is captured once and replayed as a CUDA graph */
   int32_t record_accepts;  /* 1 -> fill sabr_lmm_result.accept_bits (market 0; small runs)     */
   int32_t polish_nm;       /* 1 -> the lm_top_k points are polished by Nelder-Mead (the paper's
@@ -245,6 +247,18 @@ sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* m, const sabr_lmm
 sabr_lmm_status sabr_lmm_anneal_launch(sabr_lmm_anneal_plan* plan, void* stream);
 sabr_lmm_status sabr_lmm_anneal_fetch(sabr_lmm_anneal_plan* plan, sabr_lmm_result* out);
 void sabr_lmm_anneal_plan_free(sabr_lmm_anneal_plan* plan);
+
+/* The launch configuration a plan chose (the autotuners' choices).  Caplet markets: chains (warps)
+ * per CTA of the level kernel and its grid; in FP32 with warps_per_block = 0 the chains per CTA are
+ * autotuned at prepare time (28, 16, 14, 8, 7, 4 or the one-wave count, each timed on one level of
+ * 8 steps; every choice runs the same search bit for bit).  Markets with swaptions: threads per
+ * CTA.  A batch: per shared-memory bucket its markets, CTA size, persistent grid and CTAs per SM
+ * (the first 16 buckets).  out is host memory.                                                */
+typedef struct {
+  int32_t chains_per_cta, grid, cta_threads_swaptions, n_buckets;
+  int32_t bucket_markets[16], bucket_threads[16], bucket_grid[16], bucket_ctas_per_sm[16];
+} sabr_lmm_plan_config;
+sabr_lmm_status sabr_lmm_anneal_plan_config(const sabr_lmm_anneal_plan* plan, sabr_lmm_plan_config* out);
 
 /* Synchronise `stream`, then read and clear the error word of every market of m: returns
  * SABR_LMM_ETIMEOUT if a bounded device-side wait of a call on these markets gave up since the

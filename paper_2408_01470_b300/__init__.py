@@ -73,6 +73,14 @@ class Result(C.Structure):
     ]
 
 
+class PlanConfig(C.Structure):
+    _fields_ = [
+        ("chains_per_cta", C.c_int32), ("grid", C.c_int32), ("cta_threads_swaptions", C.c_int32),
+        ("n_buckets", C.c_int32), ("bucket_markets", C.c_int32 * 16), ("bucket_threads", C.c_int32 * 16),
+        ("bucket_grid", C.c_int32 * 16), ("bucket_ctas_per_sm", C.c_int32 * 16),
+    ]
+
+
 class MarketInfo(C.Structure):
     _fields_ = [
         ("n_fwd", C.c_int32), ("n_cap", C.c_int32), ("n_swp", C.c_int32), ("n_swap", C.c_int32),
@@ -90,7 +98,7 @@ EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective",
            "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_anneal_noalloc", "sabr_lmm_lm_polish",
            "sabr_lmm_market_info", "sabr_lmm_selftest_wait", "sabr_lmm_quadrature_rule", "sabr_lmm_last_error",
            "sabr_lmm_version", "sabr_lmm_residuals", "sabr_lmm_sync", "sabr_lmm_test_raise_error",
-           "sabr_lmm_nm_polish")
+           "sabr_lmm_nm_polish", "sabr_lmm_anneal_plan_config")
 
 
 def open_library(path: str = LIB_PATH):
@@ -114,6 +122,7 @@ def open_library(path: str = LIB_PATH):
     lib.sabr_lmm_anneal_prepare.argtypes = [C.c_void_p, C.POINTER(AnnealOpts), C.c_void_p, C.POINTER(C.c_void_p)]
     lib.sabr_lmm_anneal_launch.argtypes = [C.c_void_p, C.c_void_p]
     lib.sabr_lmm_anneal_fetch.argtypes = [C.c_void_p, C.POINTER(Result)]
+    lib.sabr_lmm_anneal_plan_config.argtypes = [C.c_void_p, C.POINTER(PlanConfig)]
     lib.sabr_lmm_anneal_plan_free.argtypes = [C.c_void_p]
     lib.sabr_lmm_anneal_plan_free.restype = None
     lib.sabr_lmm_lm_polish.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_double,
@@ -388,6 +397,17 @@ class AnnealPlan:
 
     def launch(self, stream=None):
         _check(self._lib.sabr_lmm_anneal_launch(self.h, _stream_ptr(stream)))
+
+    def config(self):
+        """sabr_lmm_anneal_plan_config: the launch configuration the plan chose, as a dict."""
+        c = PlanConfig()
+        _check(self._lib.sabr_lmm_anneal_plan_config(self.h, C.byref(c)))
+        nb = c.n_buckets
+        return {"chains_per_cta": c.chains_per_cta, "grid": c.grid,
+                "cta_threads_swaptions": c.cta_threads_swaptions,
+                "buckets": [{"markets": c.bucket_markets[i], "threads": c.bucket_threads[i],
+                             "grid": c.bucket_grid[i], "ctas_per_sm": c.bucket_ctas_per_sm[i]}
+                            for i in range(nb)]}
 
     def fetch(self):
         C_, L, N = self.dims

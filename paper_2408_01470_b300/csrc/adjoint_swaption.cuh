@@ -4,14 +4,15 @@
 // Forward sweep: cta_objective (swaption.cuh) with the quadratic forms' partials in a region of
 // their own, so that every table the reverse sweep reads is still in shared memory afterwards: the
 // per-chain exponential tables (Ep, Tq, T2, Sq, crq), the Y rows, the prefix tables along the
-// diagonals, the column prefix sums of the group forms, the swap-rate SABR factors and the caplet
-// mapping of warp 0.  Reverse sweep, in the opposite order:
+// diagonals, the column sums of the group forms, the swap-rate SABR factors and the caplet
+// forwards' factors.  Reverse sweep, in the opposite order:
 //   f = sum r_k^2, r = sqrt(w)(P - P_mkt), P = Black(sigma)       sigma_bar = 2 r sqrt(w) vega
 //   sigma = SABR(alpha, nu, rho) per caplet forward / per swap      (alpha, nu, rho)_bar
 //   alpha_S = sqrt(V1/T), nu_S = sqrt(2 V2)/(alpha_S T),
 //   rho_S = clamp(V3/V1)                                             V_bar (per swap)
-//   V_k = scale Q_k(g, L), Q the column prefix sums of a group       Q_bar, then column sums' bars
+//   V_k = scale Q_k(g, L), Q the sum of a group's first L columns    Q_bar, then column sums' bars
 //   column sum = u_j sum_i (2 - [i=j]) u_i B_k[i, j]                 B_bar per pair
+//   caplet forward i: alpha_i, nu_i from its window [0, n_i) of diagonal 0  G_bar, X_bar of that window
 //   B = (rho_e G, rho_e theta_e X, phi_e G)                          G_bar, X_bar, (rho, rho theta, phi)_bar per diagonal
 //   G = PG(hi) - PG(lo), X = PA(hi) - PA(lo) + SH(hi) G - (PGS(hi) - PGS(lo))
 //                                                                    adjoints of the prefix tables (atomics)
@@ -21,7 +22,8 @@
 //   Y rows = sqrt(w_q) g(u), sqrt(w_q) h(u)                          parameter adjoints (a .. delta_h)
 //   Sq = sums over the inner nodes of T2 products, T2 = f(gamma_h, beta_h, delta_h)
 //   rho_e = e^{-l1 dt}, theta_e = e^{-l2 dt}, phi_e = phi e^{-l3 dt}  (lambda1..3, phi)_bar
-// The caplets' share goes through caplet_price_reverse and caplet_mapping_reverse (adjoint.cuh).
+// The caplets' prices go through caplet_price_reverse (adjoint.cuh); their forwards' parameters are
+// windows of diagonal 0 and join the swaptions' reverse sweep there.
 #pragma once
 #include "adjoint.cuh"
 #include "swaption.cuh"
@@ -138,13 +140,43 @@ __device__ void cta_objective_grad(const DevMarket& m, const InstrView<double>& 
   }
   gacc[8] += rho_bar;
   const int bad = __syncthreads_or(!ok);
-  // ---------------- R2: the swap-rate SABR parameters -> the forms -> the column prefix sums
+  // ---------------- R2: the swap-rate SABR parameters -> the forms -> the column sums; the caplet
+  //      forwards' (alpha_i, nu_i) -> their window [0, n_i) on diagonal 0 -> the prefix tables
   const R* SC = m.swap_scale64;
-  const R* Pc = cs.Qs + 3 * m.n_seg;   // column prefix sums Q (forward)
-  for (int s = tid; s < ns; s += nth) {
-    const int col = m.grp_col0[m.swap_grp[s]] + m.swap_L[s] - 1;
+  const R* Pc = cs.Qs + 3 * m.n_seg;   // column sums (forward)
+  for (int s = tid; s < ns + m.n_capfwd; s += nth) {
+    if (s >= ns) {
+      const int i = m.capfwd_list[s - ns];
+      const int hi = m.fwd_np[i];
+      const R Ti = m.T[i];
+      R G, X;
+      window_integrals<R>(cs.PQ, 0, ND, PL, 0, hi, G, X);
+      const R al = sqrt(G / Ti);
+      const R nu = 2.0 * X > 0.0 ? sqrt(2.0 * X) / (al * Ti) : 0.0;
+      const R ab = gs.cap.abar[i], nb = gs.cap.nbar[i];
+      const R Gb = (ab - nb * nu / al) / (2.0 * al * Ti);
+      const R Xb = X > 0.0 ? nb * nu / (2.0 * X) : 0.0;
+      const R* SH = cs.PQ + 2 * ND * PL;
+      const R Gt = Gb + Xb * SH[hi];
+      double* PGb = gs.PQb;
+      atomicAdd(PGb + hi, Gt);
+      atomicAdd(PGb, -Gt);
+      atomicAdd(PGb + ND * PL + hi, Xb);
+      atomicAdd(PGb + ND * PL, -Xb);
+      atomicAdd(PGb + 2 * ND * PL + hi, Xb * G);
+      atomicAdd(PGb + 3 * ND * PL + hi, -Xb);
+      atomicAdd(PGb + 3 * ND * PL, Xb);
+      continue;
+    }
+    const int c0 = m.grp_col0[m.swap_grp[s]], L = m.swap_L[s], col = c0 + L - 1;
+    R q1 = 0.0, q2 = 0.0, q3 = 0.0;
+    for (int j = 0; j < L; ++j) {
+      q1 += Pc[c0 + j];
+      q2 += Pc[nc + c0 + j];
+      q3 += Pc[2 * nc + c0 + j];
+    }
     const R sc = SC[s];
-    const R V1 = sc * Pc[col], V2 = sc * Pc[nc + col], V3 = sc * Pc[2 * nc + col];
+    const R V1 = sc * q1, V2 = sc * q2, V3 = sc * q3;
     const R TE = m.swap_TE[s];
     const R al = sqrt(V1 / TE);
     const R nu = 2.0 * V2 > 0.0 ? sqrt(2.0 * V2) / (al * TE) : 0.0;
@@ -163,7 +195,7 @@ __device__ void cta_objective_grad(const DevMarket& m, const InstrView<double>& 
     gs.Vb[2 * nc + col] = sc * V3b;
   }
   __syncthreads();
-  // ---------------- R3: reverse of the prefix over a group's columns (suffix sums within the group)
+  // ---------------- R3: reverse of the sum over a swap's leading columns (suffix sums within the group)
   for (int col = tid; col < nc; col += nth) {
     int g = 0;
     while (m.grp_col0[g + 1] <= col) ++g;
@@ -384,8 +416,6 @@ __device__ void cta_objective_grad(const DevMarket& m, const InstrView<double>& 
     gacc[11] += -dt * b3 * phi * e3;
     gacc[8] += b3 * e3;
   }
-  // the caplet mapping (warp 0)
-  if (warp == 0 && m.n_capfwd > 0) caplet_mapping_reverse<R>(m, qt, cs.cap, gs.cap, lane, gacc);
   // ---------------- R8: reduce f and the parameter adjoints over the CTA
   R fsum = facc;
 #pragma unroll

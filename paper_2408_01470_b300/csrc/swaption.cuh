@@ -35,8 +35,7 @@ template <class R> struct CtaScratch {
   Q4<R>* T2;        // [8 x 9]
   Q4<R>* Sq;        // [8 x 2] per outer node q the inner-rule sums {Saa, Sab, Sbb, Sac}, {Sbc, Scc, 0, 0}
   R* Y;             // [NA x 84]
-  R* PQ;            // [kPQ x ND x PL]: PG, PA, SH, PGS along each diagonal (FP32: then PGl, PGSl,
-                    //   the low words of float-float PG and PGS)
+  R* PQ;            // [kPQ x ND x PL] the prefix tables along each diagonal (PairTables below)
   Q4<R>* crq;       // [ND]: {rho_e, rho_e theta_e, phi_e, 0} per diagonal e
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
   R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
@@ -55,6 +54,29 @@ __host__ __device__ inline int cta_pq_len(int NA) { return (NA + 2) & ~1; }
 
 // Prefix tables per diagonal: 4 (FP64), 6 (FP32: float-float PG and PGS).
 template <class R> __host__ __device__ constexpr int cta_pq_tables() { return sizeof(R) == 4 ? 6 : 4; }
+
+// Layout of the pair tables [ND x PL] per table.  FP64: four tables PG, PA, SH, PGS.  FP32: three
+// tables of float2, {PG hi, PG lo}, {PGS hi, PGS lo}, {PA, SH}, so that a window integral reads
+// six words instead of eleven.  Before phase 4 the tables hold each cell's raw G, A and H: FP64 in
+// PG, PA, SH; FP32 in PG.hi, PA and SH.
+template <class R> struct PairTables {
+  R* PQ;
+  int ND, PL;
+  __device__ __forceinline__ R& G(int e, int A) const {
+    if constexpr (sizeof(R) == 4) return ((float2*)PQ)[e * PL + A].x;
+    else return PQ[e * PL + A];
+  }
+  __device__ __forceinline__ R& Ac(int e, int A) const {
+    if constexpr (sizeof(R) == 4) return ((float2*)PQ + 2 * ND * PL)[e * PL + A].x;
+    else return PQ[(ND + e) * PL + A];
+  }
+  __device__ __forceinline__ R& H(int e, int A) const {
+    if constexpr (sizeof(R) == 4) return ((float2*)PQ + 2 * ND * PL)[e * PL + A].y;
+    else return PQ[(2 * ND + e) * PL + A];
+  }
+  // raw cell slot q: 0 G, 1 A, 2 H (the tensor-core form's order)
+  __device__ __forceinline__ R& raw(int q, int e, int A) const { return q == 0 ? G(e, A) : (q == 1 ? Ac(e, A) : H(e, A)); }
+};
 
 template <class R>
 __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
@@ -93,10 +115,6 @@ template <class R> __device__ __forceinline__ const R* swap_scale_of(const DevMa
 template <> __device__ __forceinline__ const double* swap_scale_of<double>(const DevMarket& m) { return m.swap_scale64; }
 template <> __device__ __forceinline__ const float* swap_scale_of<float>(const DevMarket& m) { return m.swap_scale32; }
 
-// Barrier 1 over the warps 1.. of the CTA (warp 0 is busy with the caplet mapping meanwhile).
-__device__ __forceinline__ void sync_without_warp0(int nth) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nth - 32) : "memory");
-}
 
 // Inclusive warp scan (lanes in order).
 template <class R>
@@ -189,20 +207,22 @@ __device__ __forceinline__ R price_one_caplet(const InstrView<R>& B, int k, cons
 // offset / window) ulp of X rather than its square.
 template <class R>
 __device__ __forceinline__ void window_integrals(const R* PQ, int e, int ND, int PL, int lo, int hi, R& G, R& X) {
-  const R* PG = PQ + e * PL;
-  const R* PA = PG + ND * PL;
-  const R* SH = PA + ND * PL;
-  const R* PGS = SH + ND * PL;
   if constexpr (sizeof(R) == 4) {
-    const R* PGl = PGS + ND * PL;
-    const R* PGSl = PGl + ND * PL;
-    G = (PG[hi] - PG[lo]) + (PGl[hi] - PGl[lo]);
-    const R sh = SH[hi];
-    const R p = sh * G;
-    const R pe = fmaf(sh, G, -p);
-    const R dh = PGS[hi] - PGS[lo], dl = PGSl[hi] - PGSl[lo];
-    X = (PA[hi] - PA[lo]) + ((p - dh) + (pe - dl));
+    const float2* PG2 = (const float2*)PQ + e * PL;
+    const float2* PGS2 = (const float2*)PQ + (ND + e) * PL;
+    const float2* PASH = (const float2*)PQ + (2 * ND + e) * PL;
+    const float2 gh = PG2[hi], gl = PG2[lo], sh2 = PGS2[hi], sl2 = PGS2[lo], ash = PASH[hi];
+    const float alo = PASH[lo].x;
+    G = (gh.x - gl.x) + (gh.y - gl.y);
+    const R p = ash.y * G;
+    const R pe = fmaf(ash.y, G, -p);
+    const R dh = sh2.x - sl2.x, dl = sh2.y - sl2.y;
+    X = (ash.x - alo) + ((p - dh) + (pe - dl));
   } else {
+    const R* PG = PQ + e * PL;
+    const R* PA = PG + ND * PL;
+    const R* SH = PA + ND * PL;
+    const R* PGS = SH + ND * PL;
     G = PG[hi] - PG[lo];
     X = (PA[hi] - PA[lo]) + SH[hi] * G - (PGS[hi] - PGS[lo]);
   }
@@ -227,18 +247,11 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   const R D = (R)m.panel;
   const int NA = m.NA, ND = m.ND, YS = cta_y_stride(), PL = cta_pq_len(NA);
 
-  // ---- phase 1: caplet forwards (warp 0); per-chain exponential tables (other warps).  Without
-  //      tensor cores warp 0 stays on the caplet mapping through phases 2-3, which the other
-  //      warps run alone (barrier 1); everyone meets again after the Grams.
-  if (warp == 0) {
-    if (m.n_capfwd > 0) {
-      if (lane < kMaxParam) cs.cap.xs[lane] = cs.xs[lane];
-      __syncwarp();
-      forward_params<R>(m, qt, cs.cap, lane);
-    }
-  } else {
-    const int t0 = tid - 32, nt = nth - 32;
-    for (int j = t0; j < kQ * kQ; j += nt) {
+  // ---- phase 1: per-chain exponential tables (every warp).  The caplet forwards' SABR parameters
+  //      need no mapping of their own: a caplet on forward i is the window [0, n_i) of diagonal 0 of
+  //      the pair tables (phase 5).
+  {
+    for (int j = tid; j < kQ * kQ; j += nth) {
       const R o2 = qt.o2[j], sw = qt.sw2[j];
       const R e = M::exp_(-gh * o2);
       Q4<R> t;
@@ -248,7 +261,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       t.d = R(0);
       cs.T2[(j >> 3) * 9 + (j & 7)] = t;
     }
-    for (int j = t0; j < kQ; j += nt) {
+    for (int j = tid; j < kQ; j += nth) {
       const R o = qt.o[j];
       const R eg = M::exp_(-c * o), eh = M::exp_(-gh * o);
       Q4<R> t;
@@ -258,14 +271,14 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       t.d = bh * o * eh;
       cs.Tq[j] = t;
     }
-    for (int A = t0; A < NA; A += nt) {
+    for (int A = tid; A < NA; A += nth) {
       const R base = D * (R)A;
       Q2<R> e;
       e.a = M::exp_(-c * base);
       e.b = M::exp_(-gh * base);
       cs.Ep[A] = e;
     }
-    for (int e = t0; e < ND; e += nt) {
+    for (int e = tid; e < ND; e += nth) {
       const R dt = D * (R)e;
       Q4<R> q;
       q.a = M::exp_(-l1 * dt);
@@ -275,10 +288,8 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       cs.crq[e] = q;
     }
   }
-  if (TC) __syncthreads();
-  else if (warp != 0) sync_without_warp0(nth);
-  // phases 2 and 3 (ALU form): the warps 1.. only
-  const int ptid = TC ? tid : tid - 32, pnth = TC ? nth : nth - 32;
+  __syncthreads();
+  const int ptid = tid, pnth = nth;
 
   // ---- phase 2: Y rows, one thread per (panel A, outer node q): g and h at the node once; the
   //      tensor-core form also the 8 inner-node products.  The ALU form keeps the inner rule in
@@ -286,7 +297,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   //      E_h(A) a'(A), beta_A = E_h(A), {a, b, c}_qr the T2 table), the pair sum over r of
   //      hin(A) hin(B) is a bilinear form in (alpha, beta, 1) with the six per-node sums
   //      S_xy(q) = sum_r x_qr y_qr, formed here once per evaluation.
-  if (!TC && warp != 0 && ptid < 6 * kQ) {
+  if (!TC && ptid < 6 * kQ) {
     const int q = ptid / 6, kd = ptid - 6 * q;   // kd: aa, ab, bb, ac, bc, cc
     R acc = 0;
 #pragma unroll
@@ -298,7 +309,6 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     }
     ((R*)cs.Sq)[q * 8 + kd] = acc;
   }
-  if (TC || warp != 0)
   for (int it = ptid; it < NA * kQ; it += pnth) {
     const int A = it >> 3, q = it & 7;
     const R base = D * (R)A;
@@ -323,10 +333,10 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       y[8 + q] = vh;
     }
   }
-  if (TC) __syncthreads();
-  else if (warp != 0) sync_without_warp0(nth);
+  __syncthreads();
 
   // ---- phase 3: pair sums along the diagonals (raw, then prefix-summed in phase 4)
+  const PairTables<R> pt{cs.PQ, ND, PL};
   if (TC) {
     const int N = round_up(NA, 16);
     tc_gram(*tc, N);
@@ -346,7 +356,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
           for (int j = 0; j < 16; ++j) {
             const int e = c0 + j - A;
             if (A < NA && e >= 0 && e < ND && c0 + j < NA) {
-              if (top) cs.PQ[(q * ND + e) * PL + A] = (R)v[j];
+              if (top) pt.raw(q, e, A) = (R)v[j];
               else Tb[(q * ND + e) * NA + A] = (R)v[j];
             }
           }
@@ -357,9 +367,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     __syncthreads();
     for (int it = tid; it < 3 * ND * NA; it += nth) {
       const int q = it / (ND * NA), r = it - q * ND * NA, e = r / NA, A = r - e * NA;
-      if (A + e < NA) cs.PQ[(q * ND + e) * PL + A] += Tb[(q * ND + e) * NA + A];
+      if (A + e < NA) pt.raw(q, e, A) += Tb[(q * ND + e) * NA + A];
     }
-  } else if (warp != 0) {
+  } else {
     // one thread per (panel A, block of 4 diagonals): the Y row of A is loaded once per 4 pairs
     const int NEB = (ND + 3) >> 2;
     for (int it = ptid; it < NEB * NA; it += pnth) {
@@ -423,94 +433,101 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       for (int u = 0; u < 4; ++u)
         if (in[u]) {
           const int e = e0 + u;
-          cs.PQ[(0 * ND + e) * PL + A] = G[u];
-          cs.PQ[(1 * ND + e) * PL + A] = Ad[u];
-          cs.PQ[(2 * ND + e) * PL + A] = H[u];
+          if constexpr (sizeof(R) == 4) {
+            pt.G(e, A) = G[u];
+            ((float2*)cs.PQ + 2 * ND * PL)[e * PL + A] = make_float2(Ad[u], H[u]);
+          } else {
+            pt.G(e, A) = G[u];
+            pt.Ac(e, A) = Ad[u];
+            pt.H(e, A) = H[u];
+          }
         }
     }
   }
   __syncthreads();
 
-  // ---- phase 4: exclusive prefix sums along each diagonal, one diagonal per half-warp (16 lanes,
-  //      three panels per lane and chunk of 48): two diagonals per warp at a time.  In FP32 the
-  //      prefix sums of G and of G x (inclusive H prefix) are float-float (hi in PG / PGS, lo in
-  //      PGl / PGSl): the B-build forms window sums as their differences, which would otherwise
-  //      lose a factor (offset + window) / window of G's bits, and its square in X.
+  // ---- phase 4: exclusive prefix sums along each diagonal, one diagonal per 8-lane group (five
+  //      panels per lane and chunk of 40): four diagonals per warp at a time.  In FP32 the prefix
+  //      sums of G and of G x (inclusive H prefix) are float-float (hi in PG / PGS, lo in PGl /
+  //      PGSl): the window integrals are their differences, which would otherwise lose a factor
+  //      (offset + window) / window of G's bits, and its square in X.
   {
     constexpr bool kFF = sizeof(R) == 4;
-    const int hw = lane >> 4, l16 = lane & 15;
-    auto scan16 = [l16](R v) {   // inclusive scan within each 16-lane half
+    constexpr int kL = 8, kE = 5, kC = kL * kE;   // lanes per diagonal, panels per lane, per chunk
+    const int hw = lane >> 3, l8 = lane & 7;
+    auto scan8 = [l8](R v) {   // inclusive scan within each 8-lane group
 #pragma unroll
-      for (int off = 1; off < 16; off <<= 1) {
-        const R o = __shfl_up_sync(0xffffffffu, v, off, 16);
-        if (l16 >= off) v += o;
+      for (int off = 1; off < kL; off <<= 1) {
+        const R o = __shfl_up_sync(0xffffffffu, v, off, kL);
+        if (l8 >= off) v += o;
       }
       return v;
     };
-    auto scan16_ff = [l16](FF v) {   // inclusive float-float scan within each 16-lane half
+    auto scan8_ff = [l8](FF v) {   // inclusive float-float scan within each 8-lane group
 #pragma unroll
-      for (int off = 1; off < 16; off <<= 1) {
+      for (int off = 1; off < kL; off <<= 1) {
         FF o;
-        o.hi = __shfl_up_sync(0xffffffffu, v.hi, off, 16);
-        o.lo = __shfl_up_sync(0xffffffffu, v.lo, off, 16);
-        if (l16 >= off) v = ff_add(v, o);
+        o.hi = __shfl_up_sync(0xffffffffu, v.hi, off, kL);
+        o.lo = __shfl_up_sync(0xffffffffu, v.lo, off, kL);
+        if (l8 >= off) v = ff_add(v, o);
       }
       return v;
     };
-    for (int eb = 2 * warp; eb < ND; eb += 2 * nw) {
+    for (int eb = 4 * warp; eb < ND; eb += 4 * nw) {
       const int e = eb + hw;
-      const int n = e < ND ? NA - e : 0;   // a half without a diagonal reads and writes nothing
-      const int nmax = NA - eb;            // the first half's diagonal is the longer one
+      const int n = e < ND ? NA - e : 0;   // a group without a diagonal reads and writes nothing
+      const int nmax = NA - eb;            // the first group's diagonal is the longest
       const int ee = e < ND ? e : eb;
-      R* PG = cs.PQ + (0 * ND + ee) * PL;
-      R* PA = cs.PQ + (1 * ND + ee) * PL;
-      R* SH = cs.PQ + (2 * ND + ee) * PL;
-      R* PGS = cs.PQ + (3 * ND + ee) * PL;
-      R* PGl = cs.PQ + (4 * ND + ee) * PL;    // FP32 only
-      R* PGSl = cs.PQ + (5 * ND + ee) * PL;
       R cg = 0, ca = 0, chh = 0, cgs = 0;
       FF cgf = {0.f, 0.f}, cgsf = {0.f, 0.f};
-      for (int c0 = 0; c0 < nmax; c0 += 48) {
-        const int A0 = c0 + 3 * l16;
-        R g[3], a[3], h[3];
+      for (int c0 = 0; c0 < nmax; c0 += kC) {
+        const int A0 = c0 + kE * l8;
+        R g[kE], a[kE], h[kE];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < kE; ++j) {
           const bool in = A0 + j < n;
-          g[j] = in ? PG[A0 + j] : R(0);
-          a[j] = in ? PA[A0 + j] : R(0);
-          h[j] = in ? SH[A0 + j] : R(0);
+          g[j] = in ? pt.G(ee, A0 + j) : R(0);
+          a[j] = in ? pt.Ac(ee, A0 + j) : R(0);
+          h[j] = in ? pt.H(ee, A0 + j) : R(0);
         }
-        const R sa = a[0] + a[1] + a[2], sh = h[0] + h[1] + h[2];
-        const R ia = scan16(sa), ih = scan16(sh);
+        R sa = 0, sh = 0;
+#pragma unroll
+        for (int j = 0; j < kE; ++j) { sa += a[j]; sh += h[j]; }
+        const R ia = scan8(sa), ih = scan8(sh);
         const R hx = chh + ih - sh;   // exclusive prefix of H before A0
-        R gs[3];
-        gs[0] = g[0] * (hx + h[0]);   // G(A) times the inclusive H prefix at A
-        gs[1] = g[1] * (hx + h[0] + h[1]);
-        gs[2] = g[2] * (hx + h[0] + h[1] + h[2]);
+        R gs[kE];
+        {
+          R hin = hx;
+#pragma unroll
+          for (int j = 0; j < kE; ++j) {   // G(A) times the inclusive H prefix at A
+            hin += h[j];
+            gs[j] = g[j] * hin;
+          }
+        }
         if constexpr (kFF) {
-          FF lg = ff_add_f(ff_of(g[0]), g[1]);
-          lg = ff_add_f(lg, g[2]);
-          FF lgs = ff_add_f(ff_of(gs[0]), gs[1]);
-          lgs = ff_add_f(lgs, gs[2]);
-          const FF ig = scan16_ff(lg), igs = scan16_ff(lgs);
+          FF lg = ff_of(g[0]), lgs = ff_of(gs[0]);
+#pragma unroll
+          for (int j = 1; j < kE; ++j) {
+            lg = ff_add_f(lg, g[j]);
+            lgs = ff_add_f(lgs, gs[j]);
+          }
+          const FF ig = scan8_ff(lg), igs = scan8_ff(lgs);
           FF xg, xgs;   // exclusive prefixes at A0 within the chunk
-          xg.hi = __shfl_up_sync(0xffffffffu, ig.hi, 1, 16);
-          xg.lo = __shfl_up_sync(0xffffffffu, ig.lo, 1, 16);
-          xgs.hi = __shfl_up_sync(0xffffffffu, igs.hi, 1, 16);
-          xgs.lo = __shfl_up_sync(0xffffffffu, igs.lo, 1, 16);
-          if (l16 == 0) { xg = ff_of(0.f); xgs = ff_of(0.f); }
+          xg.hi = __shfl_up_sync(0xffffffffu, ig.hi, 1, kL);
+          xg.lo = __shfl_up_sync(0xffffffffu, ig.lo, 1, kL);
+          xgs.hi = __shfl_up_sync(0xffffffffu, igs.hi, 1, kL);
+          xgs.lo = __shfl_up_sync(0xffffffffu, igs.lo, 1, kL);
+          if (l8 == 0) { xg = ff_of(0.f); xgs = ff_of(0.f); }
           __syncwarp();
           FF pg = ff_add(cgf, xg), pgs = ff_add(cgsf, xgs);
           R pa = ca + ia - sa, ph = hx;
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
+          for (int j = 0; j < kE; ++j) {
             if (A0 + j < n) {
-              PG[A0 + j] = pg.hi;
-              PGl[A0 + j] = pg.lo;
-              PA[A0 + j] = pa;
-              SH[A0 + j] = ph;
-              PGS[A0 + j] = pgs.hi;
-              PGSl[A0 + j] = pgs.lo;
+              float2* T2p = (float2*)cs.PQ + ee * PL + A0 + j;
+              T2p[0] = make_float2(pg.hi, pg.lo);
+              T2p[ND * PL] = make_float2(pgs.hi, pgs.lo);
+              T2p[2 * ND * PL] = make_float2(pa, ph);
             }
             pg = ff_add_f(pg, g[j]);
             pa += a[j];
@@ -518,50 +535,53 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
             pgs = ff_add_f(pgs, gs[j]);
           }
           FF tg, tgs;
-          tg.hi = __shfl_sync(0xffffffffu, ig.hi, 15, 16);
-          tg.lo = __shfl_sync(0xffffffffu, ig.lo, 15, 16);
-          tgs.hi = __shfl_sync(0xffffffffu, igs.hi, 15, 16);
-          tgs.lo = __shfl_sync(0xffffffffu, igs.lo, 15, 16);
+          tg.hi = __shfl_sync(0xffffffffu, ig.hi, kL - 1, kL);
+          tg.lo = __shfl_sync(0xffffffffu, ig.lo, kL - 1, kL);
+          tgs.hi = __shfl_sync(0xffffffffu, igs.hi, kL - 1, kL);
+          tgs.lo = __shfl_sync(0xffffffffu, igs.lo, kL - 1, kL);
           cgf = ff_add(cgf, tg);
           cgsf = ff_add(cgsf, tgs);
         } else {
-          const R sg = g[0] + g[1] + g[2];
-          const R ig = scan16(sg);
-          const R sgs = gs[0] + gs[1] + gs[2];
-          const R igs = scan16(sgs);
+          R sg = 0, sgs = 0;
+#pragma unroll
+          for (int j = 0; j < kE; ++j) { sg += g[j]; sgs += gs[j]; }
+          const R ig = scan8(sg);
+          const R igs = scan8(sgs);
           __syncwarp();
           R pg = cg + ig - sg, pa = ca + ia - sa, ph = hx, pgs = cgs + igs - sgs;
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
+          for (int j = 0; j < kE; ++j) {
             if (A0 + j < n) {
-              PG[A0 + j] = pg;
-              PA[A0 + j] = pa;
-              SH[A0 + j] = ph;
-              PGS[A0 + j] = pgs;
+              R* P = cs.PQ + ee * PL + A0 + j;
+              P[0] = pg;
+              P[ND * PL] = pa;
+              P[2 * ND * PL] = ph;
+              P[3 * ND * PL] = pgs;
             }
             pg += g[j];
             pa += a[j];
             ph += h[j];
             pgs += gs[j];
           }
-          cg += __shfl_sync(0xffffffffu, ig, 15, 16);
-          cgs += __shfl_sync(0xffffffffu, igs, 15, 16);
+          cg += __shfl_sync(0xffffffffu, ig, kL - 1, kL);
+          cgs += __shfl_sync(0xffffffffu, igs, kL - 1, kL);
         }
-        ca += __shfl_sync(0xffffffffu, ia, 15, 16);
-        chh += __shfl_sync(0xffffffffu, ih, 15, 16);
+        ca += __shfl_sync(0xffffffffu, ia, kL - 1, kL);
+        chh += __shfl_sync(0xffffffffu, ih, kL - 1, kL);
         __syncwarp();
       }
-      if (e < ND && l16 == 0) {
-        PA[n] = ca;
-        SH[n] = chh;
+      if (e < ND && l8 == 0) {
         if constexpr (kFF) {
-          PG[n] = cgf.hi;
-          PGl[n] = cgf.lo;
-          PGS[n] = cgsf.hi;
-          PGSl[n] = cgsf.lo;
+          float2* T2p = (float2*)cs.PQ + e * PL + n;
+          T2p[0] = make_float2(cgf.hi, cgf.lo);
+          T2p[ND * PL] = make_float2(cgsf.hi, cgsf.lo);
+          T2p[2 * ND * PL] = make_float2(ca, chh);
         } else {
-          PG[n] = cg;
-          PGS[n] = cgs;
+          R* P = cs.PQ + e * PL + n;
+          P[0] = cg;
+          P[ND * PL] = ca;
+          P[2 * ND * PL] = chh;
+          P[3 * ND * PL] = cgs;
         }
       }
     }
@@ -575,8 +595,9 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   //        Q_k(g, L) = sum_{j < L} u_j sum_{i <= j} (2 - [i = j]) u_i B_k[i, j],
   //      B = (rho G, rho theta X, phi G) of the pair, its window integrals from the prefix tables.
   //      (a) segments of <= kSeg pairs of one column, one thread each; (b) per column, u_j times its
-  //      segments in order; (c) per group, prefix sums over its columns (one warp per group); (d)
-  //      per swap, V = scale Q(g, L) and the swap-rate SABR factors.
+  //      segments in order; (c) per swap, the sum of its group's first L columns, V = scale Q, and
+  //      the swap-rate SABR factors; per caplet forward i, alpha_i and nu_i from the window [0, n_i)
+  //      of diagonal 0 (theta_ii = 1), the caplet's own Rebonato mapping.
   {
     R* Ps = cs.Qs;                  // [3 x n_seg]
     R* Pc = cs.Qs + 3 * m.n_seg;    // [3 x n_col]
@@ -589,19 +610,19 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       const R* u = U + g * W;
       const int nE = m.grp_nE[g], dj = dl[j];
       R s1 = 0, s2 = 0, s3 = 0;
+      // all kSeg slots evaluated (past the segment's end on pair (j, j), weight 0), so that the
+      // loads of the pairs are independent and issue together
 #pragma unroll
       for (int r = 0; r < kSeg; ++r) {
-        if (r < ni) {
-          const int i = i0 + r;
-          const int lo = dl[i], e = dj - lo;
-          R G, X;
-          window_integrals<R>(cs.PQ, e, ND, PL, lo, lo + nE, G, X);
-          const Q4<R> cr = cs.crq[e];
-          const R c = (i == j ? R(1) : R(2)) * u[i];
-          s1 += c * (cr.a * G);
-          s2 += c * (cr.b * X);
-          s3 += c * (cr.c * G);
-        }
+        const int i = min(i0 + r, j);
+        const int lo = dl[i], e = dj - lo;
+        R G, X;
+        window_integrals<R>(cs.PQ, e, ND, PL, lo, lo + nE, G, X);
+        const Q4<R> cr = cs.crq[e];
+        const R cw = r < ni ? (i == j ? R(1) : R(2)) * u[i] : R(0);
+        s1 += cw * (cr.a * G);
+        s2 += cw * (cr.b * X);
+        s3 += cw * (cr.c * G);
       }
       Ps[q] = s1;
       Ps[ns + q] = s2;
@@ -622,28 +643,27 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       Pc[2 * nc + c] = uj * v3;
     }
     __syncthreads();
-    for (int g = warp; g < m.n_grp; g += nw) {   // inclusive prefix over the group's columns
-      const int c0 = m.grp_col0[g], n = m.grp_col0[g + 1] - c0;
-      R run[3] = {0, 0, 0};
-      for (int b = 0; b < n; b += 32) {
-        const int c = b + lane;
-        const bool in = c < n;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const R v = in ? Pc[k * nc + c0 + c] : R(0);
-          const R iv = warp_inclusive_scan<R>(v, lane);
-          __syncwarp();
-          if (in) Pc[k * nc + c0 + c] = run[k] + iv;
-          run[k] += __shfl_sync(0xffffffffu, iv, 31);
-        }
-      }
-    }
-    __syncthreads();
     const R* SC = swap_scale_of<R>(m);
-    for (int s = tid; s < m.n_swap; s += nth) {
-      const int c = m.grp_col0[m.swap_grp[s]] + m.swap_L[s] - 1;
+    for (int s = tid; s < m.n_swap + m.n_capfwd; s += nth) {
+      if (s >= m.n_swap) {   // a caplet forward: diagonal 0, window [0, n_i)
+        const int i = m.capfwd_list[s - m.n_swap];
+        const R Ti = (R)m.T[i];
+        R G, X;
+        window_integrals<R>(cs.PQ, 0, ND, PL, 0, m.fwd_np[i], G, X);
+        const R al = fsqrt<R>(fdiv<R>(G, Ti));
+        const R X2 = R(2) * X;
+        put_forward<R>(cs.cap, i, al, X2 > R(0) ? fdiv<R>(fsqrt<R>(X2), al * Ti) : R(0), phi);
+        continue;
+      }
+      const int c0 = m.grp_col0[m.swap_grp[s]], L = m.swap_L[s];
+      R q1 = 0, q2 = 0, q3 = 0;
+      for (int j = 0; j < L; ++j) {
+        q1 += Pc[c0 + j];
+        q2 += Pc[nc + c0 + j];
+        q3 += Pc[2 * nc + c0 + j];
+      }
       const R sc = SC[s];
-      const R v1 = sc * Pc[c], v2 = sc * Pc[nc + c], v3 = sc * Pc[2 * nc + c];
+      const R v1 = sc * q1, v2 = sc * q2, v3 = sc * q3;
       // (FP32: the hardware reciprocal and reciprocal square root, as in the caplet mapping; FP64
       // exact.  nu = 0 stays 0.)
       const R TE = (R)m.swap_TE[s];

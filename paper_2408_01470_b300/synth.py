@@ -285,3 +285,72 @@ def market_vols(skel: Skeleton, model_vols_at_truth: np.ndarray,
     """Quotes in vol units: the model vols at the generating point plus the noise draws."""
     nz = skel.noise if noise is None else noise
     return np.asarray(model_vols_at_truth, np.float64) + nz
+
+
+# ---------------------------------------------------------------- the paper's real-data caplet smiles
+def read_paper_market(path: str) -> dict:
+    """The sections of a real-data market file (discount curve, moneyness, smiles, the paper's
+    calibrated parameters and published figures), as plain lists; no arithmetic of the method."""
+    sec, out = None, {"curve": [], "moneyness": [], "smiles": [], "params": [], "published": {}}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.startswith("["):
+            sec = line.strip("[]")
+            continue
+        parts = line.split()
+        if sec == "published":
+            out["published"][parts[0]] = " ".join(parts[1:])
+        else:
+            out[sec].append(parts)
+    return out
+
+
+def paper_euribor_caplet_smiles(path: str):
+    """The 13 caplet smiles of the paper's real-data test (Section 4) as 13 single-smile markets of
+    the Hagan model with Eq. (sigmaHagan), beta = 0.5, one per forward.
+
+    Readings (the paper does not state them): expiries in ACT/365 years from the valuation date
+    21/11/2011; a forward accrues over its fixing date to the next one in ACT/360 (the EURIBOR
+    convention); discount factors between the curve's dates by linear interpolation of log P in
+    ACT/365 time; the smiles' moneyness is ln(K / F); search box alpha in [0.001, 0.5], rho in
+    [-0.99, 0.99], nu in [0.01, 1] (the paper's calibrated sigma_1 sits at 1.0000); the paper's
+    schedule: w = 256 x 64 = 16384 chains, N = 10 steps per level, cooling 0.99 from T0 = 10 to
+    T_min = 0.01 (688 levels; T0 is passed to the search, it is no field of a skeleton).
+    Returns (skeletons, quotes, paper_params [13 x (alpha, rho, nu)], published figures).
+    """
+    import datetime as _dt
+    d = read_paper_market(path)
+    d0 = _dt.date(2011, 11, 21)
+
+    def days(s, sep, century):
+        a, b, c = (int(x) for x in s.split(sep))
+        return (_dt.date(c + century, b, a) - d0).days
+
+    ct = np.array([days(r[0], "/", 0) / 365.0 for r in d["curve"]])
+    lp = np.log(np.array([float(r[1]) for r in d["curve"]]))
+
+    def disc(t):
+        return float(np.exp(np.interp(t, ct, lp)))
+
+    m = np.array([float(x) / 100.0 for x in d["moneyness"][0]])
+    fix = [days(r[0], "-", 2000) for r in d["smiles"]]
+    # the payment date of the last forward: six months after its fixing
+    last = _dt.date(2011, 11, 21) + _dt.timedelta(days=fix[-1])
+    fix.append((_dt.date(last.year + (last.month + 6 - 1) // 12, (last.month + 6 - 1) % 12 + 1, last.day) - d0).days)
+    sks, quotes = [], []
+    for i, row in enumerate(d["smiles"]):
+        t0, tau = fix[i] / 365.0, (fix[i + 1] - fix[i]) / 360.0
+        p0, p1 = disc(t0), disc(fix[i + 1] / 365.0)
+        F = (p0 / p1 - 1.0) / tau
+        sks.append(Skeleton(
+            name=f"paper_F{i + 1}", model=MODEL_SABR_SMILE, formula=FORMULA_PAPER, beta=0.5,
+            T=np.array([t0, t0 + tau]), P=np.array([p0, p1]), cap_fwd=np.zeros(len(m), np.int32),
+            cap_K=F * np.exp(m), swp_start=np.zeros(0, np.int32), swp_end=np.zeros(0, np.int32),
+            swp_K=np.zeros(0), lo=np.array([0.001, -0.99, 0.01]), hi=np.array([0.5, 0.99, 1.0]),
+            free=np.ones(3, np.uint8), theta_true=np.array([0.05, 0.0, 0.5]), noise=np.zeros(len(m)),
+            n_chains=16384, n_levels=688, steps=10, cooling=0.99))
+        quotes.append(np.array([float(v) / 100.0 for v in row[1:]]))
+    params = np.array([[float(r[3]), float(r[1]), float(r[2])] for r in d["params"]])
+    return sks, quotes, params, d["published"]
