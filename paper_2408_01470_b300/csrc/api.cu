@@ -179,7 +179,8 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     size_t T, P, cap_K, cap_vol, cap_wu, swp_K, swp_vol, swp_wu, cap_fwd, swp_start, swp_end, swp_swap, swap_a, swap_b,
         capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
         swp_w, cblk64, cblk32, cpair32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
-        swap_grp, swap_L, seg, col_seg0, col_u, grp_col0, grp_u64, grp_u32, swap_scale64, swap_scale32;
+        swap_grp, swap_L, seg, col_seg0, col_u, grp_col0, grp_u64, grp_u32, swap_scale64, swap_scale32, seg_dsc,
+        seg_uix, seg_w64, seg_w32;
   };
   std::vector<Off> off(n_markets);
   std::vector<DevMarket> dm(n_markets);
@@ -188,7 +189,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
   std::vector<std::vector<int>> capfwd(n_markets), fwdnp(n_markets), swp_swap(n_markets), swap_a(n_markets),
       swap_b(n_markets), swap_np(n_markets), grp_a(n_markets), grp_nE(n_markets), grp_L(n_markets),
       grp_delta(n_markets), grp_swap0(n_markets), swap_grp(n_markets), swap_L(n_markets), seg(n_markets),
-      col_seg0(n_markets), col_u(n_markets), grp_col0(n_markets);
+      col_seg0(n_markets), col_u(n_markets), grp_col0(n_markets), sdsc(n_markets), suix(n_markets);
   for (int j = 0; j < n_markets; ++j) {
     const sabr_lmm_market_desc& d = descs[j];
     DevMarket& m = dm[j];
@@ -273,6 +274,35 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.n_col = (int)col_seg0[j].size();
     col_seg0[j].push_back((int)seg[j].size());
     m.n_seg = (int)seg[j].size();
+    // the forward sweep's segment descriptors: segment s of S in column jj takes the pairs
+    // i = s + S r (r = 0..3, i <= jj); an empty slot repeats pair (jj, jj) with weight 0
+    {
+      std::vector<int>& dv = sdsc[j];
+      std::vector<int>& uv = suix[j];
+      dv.assign((size_t)m.n_seg * 4, 0);
+      uv.assign((size_t)m.n_seg * 4, 0);
+      int q = 0;
+      for (size_t g = 0; g < grp_a[j].size(); ++g) {
+        const int nE = grp_nE[j][g];
+        const int* dl = grp_delta[j].data() + g * max_gwin;
+        for (int jj = 0; jj < grp_L[j][g]; ++jj) {
+          const int S = (jj + 1 + kSeg - 1) / kSeg;
+          for (int sg = 0; sg < S; ++sg, ++q) {
+            for (int r = 0; r < kSeg; ++r) {
+              const int i = sg + S * r;
+              const bool valid = i <= jj;
+              const int ii = valid ? i : jj;
+              const int lo = dl[ii], e = dl[jj] - lo;
+              if (lo + nE > 255) return fail(SABR_LMM_ENOTSUP, "market " + std::to_string(j) + ": a swap window ends beyond panel 255");
+              dv[(size_t)q * 4 + 0] |= lo << (8 * r);
+              dv[(size_t)q * 4 + 1] |= e << (8 * r);
+              uv[(size_t)q * 4 + r] = ((int)g * max_gwin + ii) | ((ii == jj ? 1 : 0) << 20) | ((valid ? 1 : 0) << 21);
+            }
+            dv[(size_t)q * 4 + 2] = nE;
+          }
+        }
+      }
+    }
     m.n_swap = (int)swap_a[j].size();
     m.max_win = max_win;
     m.NP = std::max(NP, 1);
@@ -311,6 +341,10 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.swap_grp = A.take(m.n_swap * 4); o.swap_L = A.take(m.n_swap * 4);
     o.seg = A.take((size_t)m.n_seg * 4);
     o.col_seg0 = A.take((size_t)(m.n_col + 1) * 4);
+    o.seg_dsc = A.take((size_t)m.n_seg * 16);
+    o.seg_uix = A.take((size_t)m.n_seg * 16);
+    o.seg_w64 = A.take((size_t)m.n_seg * 32);
+    o.seg_w32 = A.take((size_t)m.n_seg * 16);
     o.col_u = A.take((size_t)m.n_col * 4);
     o.grp_col0 = A.take((size_t)(ng + 1) * 4);
     o.grp_u64 = A.take((size_t)ng * m.max_gwin * 8);
@@ -341,6 +375,8 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     put(o.swap_grp, swap_grp[j].data(), m.n_swap * 4); put(o.swap_L, swap_L[j].data(), m.n_swap * 4);
     put(o.seg, seg[j].data(), (size_t)m.n_seg * 4);
     put(o.col_seg0, col_seg0[j].data(), col_seg0[j].size() * 4);
+    put(o.seg_dsc, sdsc[j].data(), sdsc[j].size() * 4);
+    put(o.seg_uix, suix[j].data(), suix[j].size() * 4);
     put(o.col_u, col_u[j].data(), col_u[j].size() * 4);
     put(o.grp_col0, grp_col0[j].data(), grp_col0[j].size() * 4);
     QuadTab<double> q64;
@@ -396,6 +432,8 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.grp_swap0 = (const int*)(base + o.grp_swap0); m.swap_grp = (const int*)(base + o.swap_grp);
     m.swap_L = (const int*)(base + o.swap_L);
     m.seg = (const int*)(base + o.seg); m.col_seg0 = (const int*)(base + o.col_seg0);
+    m.seg_dsc = (const int4*)(base + o.seg_dsc); m.seg_uix = (const int4*)(base + o.seg_uix);
+    m.seg_w64 = (const double*)(base + o.seg_w64); m.seg_w32 = (const float*)(base + o.seg_w32);
     m.col_u = (const int*)(base + o.col_u); m.grp_col0 = (const int*)(base + o.grp_col0);
     m.grp_u64 = (const double*)(base + o.grp_u64); m.grp_u32 = (const float*)(base + o.grp_u32);
     m.swap_scale64 = (const double*)(base + o.swap_scale64); m.swap_scale32 = (const float*)(base + o.swap_scale32);
@@ -403,6 +441,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     if (m.n_swap > 0) {
       setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
       setup_group_u_kernel<<<(m.n_grp * m.max_gwin + 127) / 128, 128, 0, s>>>(m);
+      setup_seg_weights_kernel<<<(m.n_seg + 127) / 128, 128, 0, s>>>(m);
     }
     const int ni = m.n_cap + m.n_swp;
     setup_instruments_kernel<<<(ni + 127) / 128, 128, 0, s>>>(m);
@@ -867,6 +906,11 @@ cudaError_t enqueue_anneal_cta_t(const DevMarket& m, const SAState& st, const SA
   return cudaGetLastError();
 }
 
+// Warps per CTA of the kernels of markets with swaptions: 4 (the default, 18 % faster per level than
+// 8 on the 40-forward joint market: four CTAs per SM instead of two hide each other's barriers), or
+// 8 when asked (warps_per_block >= 5).
+int cta_warps_of(const sabr_lmm_anneal_opts* o) { return o->warps_per_block <= 4 ? 4 : 8; }
+
 // cta_warps: warps per CTA of the kernels of markets with swaptions (4 or 8).
 cudaError_t enqueue_anneal(const DevMarket& m, int prec, const SAState& st, const SAParams& sp, int W, int grid,
                            cudaStream_t s, bool configure_only = false, int cta_warps = 8) {
@@ -1158,21 +1202,18 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     if (m.n_swp == 0 && o->prec != SABR_LMM_FP64)
       while (p->W > 4 && smem_bytes<float>(m, p->W) > 227u * 1024u) --p->W;
   p->grid = (o->n_chains + p->W - 1) / p->W;
-  // markets with swaptions: 4 warps per chain's CTA (the default, 18 % faster per level than 8 on
-  // the 40-forward joint market: four CTAs per SM instead of two hide each other's barriers), or 8
-  // when asked (warps_per_block >= 5)
-  p->cta_warps = o->warps_per_block <= 4 ? 4 : 8;
+  p->cta_warps = cta_warps_of(o);
   const int nm = (int)mk->dm.size();
   const int P = mk->dm[0].n_param;
   const size_t C = o->n_chains, L = o->n_levels, N = o->steps_per_level;
   // per market: xs[P] fs T0 xe[CP] fe[C] xb[CP] fb[C] part_f[grid] part_c[grid] counter trace[L] best_x[P] best_f x0[P]
   Arena A;
-  struct Off { size_t xs, fs, T0, xe, fe, xb, fb, pf, pc, cnt, tr, trx, trt, bx, bf, x0, bits, vols, rmse; };
+  struct Off { size_t xs, fs, T0, lvl, xe, fe, xb, fb, pf, pc, cnt, tr, trx, trt, bx, bf, x0, bits, vols, rmse; };
   std::vector<Off> off(nm);
   for (int j = 0; j < nm; ++j) {
     const int Pj = mk->dm[j].n_param;
     Off& q = off[j];
-    q.xs = A.take(Pj * 8); q.fs = A.take(8); q.T0 = A.take(8);
+    q.xs = A.take(Pj * 8); q.fs = A.take(8); q.T0 = A.take(8); q.lvl = A.take(3 * 8);
     q.xe = A.take(C * Pj * 8); q.fe = A.take(C * 8); q.xb = A.take(C * Pj * 8); q.fb = A.take(C * 8);
     const size_t nparts = std::max<size_t>((size_t)p->grid, C);   // CTA minima (one CTA per chain with swaptions)
     q.pf = A.take(nparts * 8); q.pc = A.take(nparts * 4); q.cnt = A.take(16);
@@ -1192,7 +1233,7 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
     const HostMarket& h = mk->hm[j];
     const Off& q = off[j];
     SAState s{};
-    s.xs = (double*)(b + q.xs); s.fs = (double*)(b + q.fs); s.T0 = (double*)(b + q.T0);
+    s.xs = (double*)(b + q.xs); s.fs = (double*)(b + q.fs); s.T0 = (double*)(b + q.T0); s.lvl = (double*)(b + q.lvl);
     s.xe = (double*)(b + q.xe); s.fe = (double*)(b + q.fe); s.xb = (double*)(b + q.xb); s.fb = (double*)(b + q.fb);
     s.part_f = (double*)(b + q.pf); s.part_c = (int*)(b + q.pc); s.counter = (unsigned int*)(b + q.cnt);
     s.trace_f = (double*)(b + q.tr); s.best_x = (double*)(b + q.bx); s.best_f = (double*)(b + q.bf);
@@ -1571,7 +1612,7 @@ constexpr int kNoAllocW = 4;  // warps (chains) per CTA: the 4-chain form of the
 constexpr int kNoAllocMaxParts = kNoAllocMaxChains;
 
 // Byte offsets of the regions in the array (each 256-byte aligned).
-constexpr size_t kNaHead = 0;  // xs[12] fs T0 x0[12] best_x[12] best_f counter
+constexpr size_t kNaHead = 0;  // xs[12] fs T0 x0[12] best_x[12] best_f counter lvl[3]
 constexpr size_t kNaXe = 512;
 constexpr size_t kNaFe = kNaXe + (size_t)kNoAllocMaxChains * kNoAllocMaxParam * 8;
 constexpr size_t kNaXb = kNaFe + (size_t)kNoAllocMaxChains * 8;
@@ -1649,6 +1690,7 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, in
   st.best_x = head + 26;
   st.best_f = head + 38;
   st.counter = (unsigned int*)(head + 39);
+  st.lvl = head + 40;
   st.xe = (double*)(base + kNaXe);
   st.fe = (double*)(base + kNaFe);
   st.xb = (double*)(base + kNaXb);
@@ -1669,8 +1711,8 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, in
   noalloc_put_x0_kernel<<<1, 32, 0, s>>>(x0, hx0, P);
   CUDA_TRY(cudaGetLastError());
   const int grid = (o->n_chains + kNoAllocW - 1) / kNoAllocW;
-  CUDA_TRY(enqueue_anneal(m, o->prec, st, sp, kNoAllocW, grid, s, true));
-  CUDA_TRY(enqueue_anneal(m, o->prec, st, sp, kNoAllocW, grid, s, false));
+  CUDA_TRY(enqueue_anneal(m, o->prec, st, sp, kNoAllocW, grid, s, true, cta_warps_of(o)));
+  CUDA_TRY(enqueue_anneal(m, o->prec, st, sp, kNoAllocW, grid, s, false, cta_warps_of(o)));
   CUDA_TRY(cudaMemcpyAsync(x_best, st.best_x, P * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(f_best, st.best_f, sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (trace_f) CUDA_TRY(cudaMemcpyAsync(trace_f, st.trace_f, o->n_levels * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -79,6 +79,20 @@ __global__ void setup_group_u_kernel(DevMarket m) {
   ((float*)m.grp_u32)[t] = (float)u;
 }
 
+// The four slot weights (2 - [i = j]) u_i of every segment of the forward sweep (0 on an empty slot).
+__global__ void setup_seg_weights_kernel(DevMarket m) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m.n_seg) return;
+  const int4 x = m.seg_uix[q];
+  const int v[4] = {x.x, x.y, x.z, x.w};
+  for (int r = 0; r < 4; ++r) {
+    const int ix = v[r] & 0xfffff;
+    const double w = (v[r] >> 21) & 1 ? (((v[r] >> 20) & 1) ? 1.0 : 2.0) * m.grp_u64[ix] : 0.0;
+    ((double*)m.seg_w64)[4 * q + r] = w;
+    ((float*)m.seg_w32)[4 * q + r] = (float)w;
+  }
+}
+
 // Pricing constants of one instrument, into the three 4-vector groups of its block.
 template <class R>
 __device__ void put_instr(void* blk, int npad, int k, double l, double fk, double inv_den, double c1, double c2,
@@ -369,6 +383,7 @@ struct SAState {
   uint8_t* bits;     // [C x L x N] or null
   double* best_x;    // [P]
   double* best_f;    // [1]
+  double* lvl;       // [3] of the level about to run: T_l, its step scale, 1 / T_l
 };
 
 struct SAParams {
@@ -387,11 +402,22 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
   return t;
 }
 
+// The constants of a level: T_l = T0 cooling^l as repeated products (each level's last CTA
+// multiplies the previous T once, so no thread runs the product chain), the step scale
+// max(step_frac sqrt(T_l / T0), step_floor) and 1 / T_l.  One thread writes them.
+__device__ __forceinline__ void level_consts_write(const SAState& st, const SAParams& sp, double T, double T0) {
+  st.lvl[0] = T;
+  st.lvl[1] = fmax(sp.step_frac * sqrt(T / T0), sp.step_floor);
+  st.lvl[2] = 1.0 / T;
+}
+
 __device__ __forceinline__ void sa_start_write(const SAState& st, const SAParams& sp, int t, double x0, double f0) {
   if (t < sp.P) st.xs[t] = x0;
   if (t == 0) {
     st.fs[0] = f0;
-    st.T0[0] = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
+    const double T0 = sp.T0_opt > 0.0 ? sp.T0_opt : ((isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
+    st.T0[0] = T0;
+    level_consts_write(st, sp, T0, T0);
     st.counter[0] = 0u;
     if (st.trace_t) st.trace_t[0] = global_timer_ns();
   }
@@ -500,11 +526,8 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
     }
   }
   const int P = sp.P;
-  const double T0 = st.T0[0];
-  double T = T0;
-  for (int j = 0; j < level; ++j) T = T * sp.cooling;   // T_l = T0 cooling^l, as repeated products
-  const double sf = fmax(sp.step_frac * sqrt(T / T0), sp.step_floor);
-  const float invT = (float)(1.0 / T);
+  const double T = st.lvl[0], sf = st.lvl[1];
+  const float invT = (float)st.lvl[2];
 
   O f;
   obj_from_double(st.fs[0], f);
@@ -609,6 +632,7 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
       if (lex_less(cs.red_f[w], cs.red_c[w], cs.red_f[0], cs.red_c[0])) { cs.red_f[0] = cs.red_f[w]; cs.red_c[0] = cs.red_c[w]; }
     st.fs[0] = cs.red_f[0];
     st.trace_f[level] = cs.red_f[0];
+    level_consts_write(st, sp, T * sp.cooling, st.T0[0]);
   }
   __syncthreads();
   const int cbest = cs.red_c[0];
@@ -852,11 +876,8 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
   typedef typename ObjOf<R>::T O;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = sp.P;
-  const double T0 = st.T0[0];
-  double T = T0;
-  for (int j = 0; j < level; ++j) T = T * sp.cooling;
-  const double sf = fmax(sp.step_frac * sqrt(T / T0), sp.step_floor);
-  const float invT = (float)(1.0 / T);
+  const double T = st.lvl[0], sf = st.lvl[1];
+  const float invT = (float)st.lvl[2];
 
   O f;
   obj_from_double(st.fs[0], f);
@@ -944,6 +965,7 @@ __device__ void cta_chain_level(const DevMarket& m, const SAState& st, const SAP
       if (lex_less(cs.red_f[w], cs.red_c[w], cs.red_f[0], cs.red_c[0])) { cs.red_f[0] = cs.red_f[w]; cs.red_c[0] = cs.red_c[w]; }
     st.fs[0] = cs.red_f[0];
     st.trace_f[level] = cs.red_f[0];
+    level_consts_write(st, sp, T * sp.cooling, st.T0[0]);
   }
   __syncthreads();
   const int cbest = cs.red_c[0];

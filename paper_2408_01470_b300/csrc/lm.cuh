@@ -319,12 +319,15 @@ __global__ void gather_points_kernel(const double* xb, const int* sel, int k, in
   if (i < k && j < P) X[(size_t)i * P + j] = xb[(size_t)sel[i] * P + j];
 }
 
-// The best polished point replaces the annealer's best point if it is better.
+// The best polished point becomes the search's result.  The polish starts from the k lowest chain
+// bests, the search's best point among them, and never raises a value, so its best FP64 value is at
+// most the FP64 objective of the search's best point; an FP32 search's own best value is an FP32
+// evaluation and is not compared with it.  A polish without a finite value keeps the search's.
 __global__ void take_best_kernel(const double* X, const double* f, int k, int P, double* best_x, double* best_f) {
   if (threadIdx.x != 0) return;
   int b = 0;
   for (int i = 1; i < k; ++i) if (f[i] < f[b]) b = i;
-  if (f[b] < best_f[0] || !(best_f[0] == best_f[0])) {
+  if (f[b] == f[b] && f[b] < __longlong_as_double(0x7ff0000000000000LL)) {
     best_f[0] = f[b];
     for (int j = 0; j < P; ++j) best_x[j] = X[(size_t)b * P + j];
   }

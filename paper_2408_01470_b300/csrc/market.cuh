@@ -110,6 +110,15 @@ struct DevMarket {
   const int* seg;                  // [n_seg] g | j << 8 | i0 << 16 | (pairs) << 24, column by column
   int n_col;                       // columns over every group (sum of the group windows)
   const int* col_seg0;             // [n_col + 1] first segment of each column
+  // The forward sweep's segments: the same count per column, but segment s of a column with S
+  // segments takes the pairs i = s, s + S, s + 2S, s + 3S (i <= j), so that the lanes of a warp,
+  // which hold consecutive segments of a column, read consecutive diagonals at consecutive panel
+  // offsets (prefix-table addresses on distinct banks).  One 16-byte descriptor per segment and its
+  // four weights (2 - [i = j]) u_i (0 on an empty slot, whose offsets repeat pair (j, j)).
+  const int4* seg_dsc;             // [n_seg] x: lo_r << 8r, y: e_r << 8r (r = 0..3), z: the window nE
+  const int4* seg_uix;             // [n_seg] per slot r: g * max_gwin + i | (i == j) << 20 | valid << 21
+  const double* seg_w64;           // [n_seg x 4] the slot weights (FP64)
+  const float* seg_w32;            //   the same in FP32
   const int* col_u;                // [n_col] index g * max_gwin + j of the column's u_j
   const int* grp_col0;             // [n_grp + 1] first column of each group
   const double* grp_u64;           // [n_grp x max_gwin] u_{a + i} (FP64)

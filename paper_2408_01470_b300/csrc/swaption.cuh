@@ -111,6 +111,13 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
 template <class R> __device__ __forceinline__ const R* grp_u_of(const DevMarket& m);
 template <> __device__ __forceinline__ const double* grp_u_of<double>(const DevMarket& m) { return m.grp_u64; }
 template <> __device__ __forceinline__ const float* grp_u_of<float>(const DevMarket& m) { return m.grp_u32; }
+template <class R> __device__ __forceinline__ const Q4<R>* seg_w_of(const DevMarket& m);
+template <> __device__ __forceinline__ const Q4<double>* seg_w_of<double>(const DevMarket& m) {
+  return (const Q4<double>*)m.seg_w64;
+}
+template <> __device__ __forceinline__ const Q4<float>* seg_w_of<float>(const DevMarket& m) {
+  return (const Q4<float>*)m.seg_w32;
+}
 template <class R> __device__ __forceinline__ const R* swap_scale_of(const DevMarket& m);
 template <> __device__ __forceinline__ const double* swap_scale_of<double>(const DevMarket& m) { return m.swap_scale64; }
 template <> __device__ __forceinline__ const float* swap_scale_of<float>(const DevMarket& m) { return m.swap_scale32; }
@@ -382,6 +389,81 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
         in[u] = e0 + u < ND && A + e0 + u < NA;
         yb[u] = cs.Y + (in[u] ? A + e0 + u : A) * YS;
       }
+      if constexpr (sizeof(R) == 4) {
+        // FP32: the four diagonals as two packed pairs (u = 0, 1 and 2, 3), one .f32x2 instruction
+        // per pair of products, sums and fmas
+        const float bA = cs.Ep[A].b, aA = bA * (ah + bh * (D * (float)A));
+        float2 cp[2], cq[2], cr[2], cu[2], cv[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float a2[2], b2[2];
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const int u = 2 * h + t;
+            const int B = in[u] ? A + e0 + u : A;
+            b2[t] = cs.Ep[B].b;
+            a2[t] = b2[t] * (ah + bh * (D * (float)B));
+          }
+          const float2 aB = make_float2(a2[0], a2[1]), bB = make_float2(b2[0], b2[1]);
+          cp[h] = mul2(bc2(aA), aB);
+          cq[h] = fma2(bc2(aA), bB, mul2(bc2(bA), aB));
+          cr[h] = mul2(bc2(bA), bB);
+          cu[h] = add2(bc2(aA), aB);
+          cv[h] = add2(bc2(bA), bB);
+        }
+        float2 G2[2] = {bc2(0.f), bc2(0.f)}, H2[2] = {bc2(0.f), bc2(0.f)}, A2[2] = {bc2(0.f), bc2(0.f)};
+#pragma unroll
+        for (int k = 0; k < 8; k += 4) {
+          const float4 x = *(const float4*)(ya + k);
+          float4 y[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) y[u] = *(const float4*)(yb[u] + k);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 s0 = *(const float4*)&cs.Sq[2 * (k + j)];
+            const float4 s1 = *(const float4*)&cs.Sq[2 * (k + j) + 1];
+            const float xa = j == 0 ? x.x : (j == 1 ? x.y : (j == 2 ? x.z : x.w));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float4& p = y[2 * h];
+              const float4& q = y[2 * h + 1];
+              const float2 yy = j == 0 ? make_float2(p.x, q.x)
+                                       : (j == 1 ? make_float2(p.y, q.y) : (j == 2 ? make_float2(p.z, q.z) : make_float2(p.w, q.w)));
+              const float2 pr = mul2(bc2(xa), yy);
+              G2[h] = add2(G2[h], pr);
+              float2 form = fma2(cv[h], bc2(s1.x), bc2(s1.y));
+              form = fma2(cu[h], bc2(s0.w), form);
+              form = fma2(cr[h], bc2(s0.z), form);
+              form = fma2(cq[h], bc2(s0.y), form);
+              form = fma2(cp[h], bc2(s0.x), form);
+              A2[h] = fma2(pr, form, A2[h]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 8; k < 16; k += 4) {
+          const float4 x = *(const float4*)(ya + k);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float4 p = *(const float4*)(yb[2 * h] + k);
+            const float4 q = *(const float4*)(yb[2 * h + 1] + k);
+            H2[h] = fma2(bc2(x.x), make_float2(p.x, q.x), H2[h]);
+            H2[h] = fma2(bc2(x.y), make_float2(p.y, q.y), H2[h]);
+            H2[h] = fma2(bc2(x.z), make_float2(p.z, q.z), H2[h]);
+            H2[h] = fma2(bc2(x.w), make_float2(p.w, q.w), H2[h]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (in[u]) {
+            const int e = e0 + u, h = u >> 1;
+            const float g = (u & 1) ? G2[h].y : G2[h].x;
+            const float ad = (u & 1) ? A2[h].y : A2[h].x;
+            const float hh = (u & 1) ? H2[h].y : H2[h].x;
+            pt.G(e, A) = g;
+            ((float2*)cs.PQ + 2 * ND * PL)[e * PL + A] = make_float2(ad, hh);
+          }
+      } else {
       R G[4], H[4], Ad[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) { G[u] = 0; H[u] = 0; Ad[u] = 0; }
@@ -442,6 +524,7 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
             pt.H(e, A) = H[u];
           }
         }
+      }
     }
   }
   __syncthreads();
@@ -594,7 +677,8 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   //        V_k(swap) = sum_{i <= j < L} (2 - [i = j]) W_i W_j B_k[i, j] = scale(swap) Q_k(g, L),
   //        Q_k(g, L) = sum_{j < L} u_j sum_{i <= j} (2 - [i = j]) u_i B_k[i, j],
   //      B = (rho G, rho theta X, phi G) of the pair, its window integrals from the prefix tables.
-  //      (a) segments of <= kSeg pairs of one column, one thread each; (b) per column, u_j times its
+  //      (a) segments of <= kSeg pairs of one column, one thread each (segment s of S takes the
+  //      pairs s + S r: consecutive lanes read consecutive diagonals); (b) per column, u_j times its
   //      segments in order; (c) per swap, the sum of its group's first L columns, V = scale Q, and
   //      the swap-rate SABR factors; per caplet forward i, alpha_i and nu_i from the window [0, n_i)
   //      of diagonal 0 (theta_ii = 1), the caplet's own Rebonato mapping.
@@ -602,27 +686,23 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
     R* Ps = cs.Qs;                  // [3 x n_seg]
     R* Pc = cs.Qs + 3 * m.n_seg;    // [3 x n_col]
     const R* U = grp_u_of<R>(m);
-    const int ns = m.n_seg, nc = m.n_col, W = m.max_gwin;
+    const int ns = m.n_seg, nc = m.n_col;
     for (int q = tid; q < ns; q += nth) {
-      const int w = m.seg[q];
-      const int g = w & 255, j = (w >> 8) & 255, i0 = (w >> 16) & 255, ni = w >> 24;
-      const int* dl = m.grp_delta + g * W;
-      const R* u = U + g * W;
-      const int nE = m.grp_nE[g], dj = dl[j];
+      const int4 d = m.seg_dsc[q];
+      const Q4<R> w = seg_w_of<R>(m)[q];
+      const R wr[4] = {w.a, w.b, w.c, w.d};
       R s1 = 0, s2 = 0, s3 = 0;
-      // all kSeg slots evaluated (past the segment's end on pair (j, j), weight 0), so that the
+      // all kSeg slots evaluated (an empty slot repeats pair (j, j) with weight 0), so that the
       // loads of the pairs are independent and issue together
 #pragma unroll
       for (int r = 0; r < kSeg; ++r) {
-        const int i = min(i0 + r, j);
-        const int lo = dl[i], e = dj - lo;
+        const int lo = (d.x >> (8 * r)) & 255, e = (d.y >> (8 * r)) & 255;
         R G, X;
-        window_integrals<R>(cs.PQ, e, ND, PL, lo, lo + nE, G, X);
+        window_integrals<R>(cs.PQ, e, ND, PL, lo, lo + d.z, G, X);
         const Q4<R> cr = cs.crq[e];
-        const R cw = r < ni ? (i == j ? R(1) : R(2)) * u[i] : R(0);
-        s1 += cw * (cr.a * G);
-        s2 += cw * (cr.b * X);
-        s3 += cw * (cr.c * G);
+        s1 += wr[r] * (cr.a * G);
+        s2 += wr[r] * (cr.b * X);
+        s3 += wr[r] * (cr.c * G);
       }
       Ps[q] = s1;
       Ps[ns + q] = s2;

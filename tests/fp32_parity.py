@@ -108,3 +108,11 @@ def objective_bound_at_noise_floor(f_oracle, n_instr):
     |sum (r + dr)^2 - sum r^2| <= 2 ||r|| ||dr|| + ||dr||^2 <= 2 sqrt(f n) a + n a^2."""
     a = GEN_BAR_VOLPT / 100.0
     return 2.0 * np.sqrt(f_oracle * n_instr) * a + n_instr * a * a
+
+
+def objective_bound(f_oracle, n_instr):
+    """|f_lo - f_oracle| allowed at any feasible point where every price meets the far bar
+    |dr_k| <= a + b |r_k| (a = FAR_ABS_VOLPT, b = FAR_REL, in vol units): ||dr|| <= a sqrt(n) + b sqrt(f),
+    so |sum (r + dr)^2 - sum r^2| <= 2 sqrt(f) d + d^2 with d = a sqrt(n) + b sqrt(f)."""
+    d = FAR_ABS_VOLPT / 100.0 * np.sqrt(n_instr) + FAR_REL * np.sqrt(f_oracle)
+    return 2.0 * np.sqrt(f_oracle) * d + d * d

@@ -155,7 +155,8 @@ def test_anneal_polish_top_k_bounds(gpu_lib, k):
     om, gm = _markets(sk)
     r0 = gm.anneal(64, 10, 20, 0.85, seed=5, prec="fp32")
     r1 = gm.anneal(64, 10, 20, 0.85, seed=5, prec="fp32", lm_top_k=k, lm_max_iter=10)
-    assert r1["f_best"][0] <= r0["f_best"][0]
+    # the polished result is an FP64 value, at most the FP64 objective of the search's best point
+    assert r1["f_best"][0] <= om.objective(r0["x_best"][0]) * (1 + 1e-11)
     assert om.objective(r1["x_best"][0]) == pytest.approx(r1["f_best"][0], rel=1e-12)
 
 
@@ -164,7 +165,7 @@ def test_anneal_with_top_k_polish(gpu_lib):
     om, gm = _markets(sk)
     r0 = gm.anneal(64, 30, 20, 0.85, seed=3, prec="fp32")
     r1 = gm.anneal(64, 30, 20, 0.85, seed=3, prec="fp32", lm_top_k=8, lm_max_iter=20)
-    assert r1["f_best"][0] <= r0["f_best"][0]
+    assert r1["f_best"][0] <= om.objective(r0["x_best"][0]) * (1 + 1e-11)
     assert r1["lm_seconds"] > 0.0
     # the polished point is a local minimum of the FP64 objective: LM from it moves nowhere
     p = om.lm(r1["x_best"][0], max_iter=20)

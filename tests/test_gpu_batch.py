@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from fp32_parity import FAR_ABS_VOLPT, FAR_REL, objective_bound, residual_errors
 from paper_2408_01470_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -37,23 +38,32 @@ def test_batch_fp64_reproduces_each_market_search(gpu_lib, wpb):
 
 
 def test_batch_fp32_runs_every_market(gpu_lib):
+    # every market's result: the FP32 search's value against the oracle's objective at the returned
+    # point within the bound the per-price bars imply, and every price of that point (the search's
+    # own pricer, through the residuals entry point) within the far-point bar
     sks, oms, gm = _batch(list(range(12)))
     r = gm.anneal(64, 4, 8, 0.9, seed=3, prec="fp32")
     for j, om in enumerate(oms):
         f0 = om.objective(sks[j].box_centre())
+        x = r["x_best"][j]
         assert np.isfinite(r["f_best"][j])
         assert r["f_best"][j] <= f0
-        assert om.objective(r["x_best"][j]) == pytest.approx(r["f_best"][j], rel=1e-3)
+        f64 = om.objective(x)
+        assert abs(r["f_best"][j] - f64) <= objective_bound(f64, sks[j].n_instr), (j, r["f_best"][j], f64)
+        err, mag = residual_errors(gm, om, x[None, :], "fp32", market=j)
+        ok = np.isfinite(err)
+        assert ok.all(), j
+        assert np.all(err[ok] <= FAR_ABS_VOLPT + FAR_REL * mag[ok]), (j, float(np.max(err)))
 
 
 def test_batch_fp32_search_with_polish(gpu_lib):
     # the mixed-precision form on a batch: FP32 search, then the FP64 Levenberg-Marquardt polish of
-    # each market's 8 best chains; every market's result is no worse and is the oracle's objective
-    # at the returned point
+    # each market's 8 best chains; every market's result is an FP64 value no worse than the FP64
+    # objective of its search's best point, and is the oracle's objective at the returned point
     sks, oms, gm = _batch([0, 3, 4, 7])
     r0 = gm.anneal(64, 4, 8, 0.9, seed=21, prec="fp32")
     r1 = gm.anneal(64, 4, 8, 0.9, seed=21, prec="fp32", lm_top_k=8, lm_max_iter=10)
     assert r1["lm_seconds"] > 0.0
     for j, om in enumerate(oms):
-        assert r1["f_best"][j] <= r0["f_best"][j], j
-        assert om.objective(r1["x_best"][j]) == pytest.approx(r1["f_best"][j], rel=1e-9), j
+        assert r1["f_best"][j] <= om.objective(r0["x_best"][j]) * (1 + 1e-11), j
+        assert om.objective(r1["x_best"][j]) == pytest.approx(r1["f_best"][j], rel=1e-12), j

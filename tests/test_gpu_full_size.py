@@ -17,18 +17,19 @@ import numpy as np
 import pytest
 
 import oracle
+from fp32_parity import objective_bound
 from paper_2408_01470_b300 import synth
 
 pytestmark = pytest.mark.gpu
 
 
 
-def _rms_close(f32, f64, n):
-    """FP32 objective against the FP64 oracle at the same point, in RMS-equivalent vol points
-    (100 sqrt(f / n)): the bar of the objective tests, 1e-4 vol-pt plus 1.5e-5 of the RMS (the
-    swaption windows' prefix-sum cancellation in FP32)."""
-    a, b = 100.0 * np.sqrt(f32 / n), 100.0 * np.sqrt(f64 / n)
-    return abs(a - b) <= 1e-4 + 1.5e-5 * b
+def _rms_close(f32, f64, n, far=False):
+    """FP32 objective against the FP64 oracle at the same point: 1e-4 relative at the end of a search
+    of the benchmark markets (300 and 1,000 instruments); far from the market (a one-level search of
+    a batch member), the bound the far per-price bar implies where that is wider
+    (fp32_parity.objective_bound)."""
+    return abs(f32 - f64) <= (max(1e-4 * f64, objective_bound(f64, n)) if far else 1e-4 * f64)
 
 
 def _quoted(sk):
@@ -103,7 +104,7 @@ def test_fp32_batch_all_markets_one_level(gpu_lib):
         if j % 8 == 0:
             om = oracle.Market(sk, vols[j])
             f64 = om.objective(x)
-            assert _rms_close(r["f_best"][j], f64, sk.n_instr), (j, r["f_best"][j], f64)
+            assert _rms_close(r["f_best"][j], f64, sk.n_instr, far=True), (j, r["f_best"][j], f64)
 
 
 def test_caplet_search_at_the_chain_limit(gpu_lib):
