@@ -8,10 +8,17 @@ reduction (S8).  Inputs are synthetic (seeded), resident in HBM before the timed
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64] [--impl reference]
 
-Besides the headline value the line carries `variants` (the FP64 plain form of the same search;
-the joint caplet + swaption market in FP32, FP64 and with the BF16-split tensor-core Grams; one
-level of the 256-market batch) and `time_to_target` (0.05 vol-pt RMS: FP64 plain, FP32, and the
-FP32 search with the Levenberg-Marquardt polish).
+Besides the headline value the line carries `variants.fp64` (the FP64 plain form of the same
+search), `workloads` (the joint 40-forward caplet + swaption market over its full 200-level
+schedule in FP32 with its own roofline and oracle baseline, one level of it in FP64 and with the
+BF16-split tensor-core Grams, the paper's real-data caplet calibration over its full schedule, one
+level of the 256-market batch) and `time_to_target` (0.05 vol-pt and the FP64 form's final true
+vol RMSE: FP64 plain, FP32, and the FP32 search with the Levenberg-Marquardt polish).  Shortened
+samples say so (`extrapolated`, `levels_timed` against `levels_of_schedule`).
+
+Other modes: `--workload joint|batch|caplets` (that workload's full schedule as its own line),
+`--quality --workload W --seeds S` (final true vol RMSE of FP32 against FP64 over S seeds, with and
+without the polish), `--profile` (one search, for ncu launch lists).
 
 Multi-GPU runs (torchrun, one process per GPU) are independent replicas: the search does not
 shard, so no collective touches the data path; rank r anneals with seed + r and the aggregate
@@ -40,9 +47,10 @@ WORKLOAD = "rebonato_caplets_20fwd_x_15k_4096ch_x_200T_x_100steps"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 1.25                              # nominal B300 FP64 rate
 # DRAM bytes (read + write) of one FP32 level launch of sa_level_kernel on this workload, from an ncu
-# capture of the kernel as it is built now (dram__bytes_read.sum 513,280 B, dram__bytes_write.sum 0 B,
-# second level of a 3-level search); the market and chain state stay in L2 across launches
-LEVEL_TRAFFIC_BYTES_FP32 = 513_280
+# capture of the kernel as it is built now (dram__bytes_read.sum 510,976 B, dram__bytes_write.sum 0 B,
+# second level of a 3-level search of 28-chain CTAs); the market and chain state stay in L2 across
+# launches
+LEVEL_TRAFFIC_BYTES_FP32 = 510_976
 TARGET_RMSE_VOLPT = 0.05
 
 

@@ -251,8 +251,9 @@ void sabr_lmm_anneal_plan_free(sabr_lmm_anneal_plan* plan);
 /* The launch configuration a plan chose (the autotuners' choices).  Caplet markets: chains (warps)
  * per CTA of the level kernel and its grid; in FP32 with warps_per_block = 0 the chains per CTA are
  * autotuned at prepare time (28, 16, 14, 8, 7, 4 or the one-wave count, each timed on one level of
- * 8 steps; every choice runs the same search bit for bit).  Markets with swaptions: threads per
- * CTA.  A batch: per shared-memory bucket its markets, CTA size, persistent grid and CTAs per SM
+ * the search's length, at most 100 steps; the one-wave count stays unless another is 2 % faster;
+ * every choice runs the same search bit for bit).  Markets with swaptions: threads per CTA (128
+ * unless warps_per_block asks for 256; not tuned, since the CTA size orders the partial sums).  A batch: per shared-memory bucket its markets, CTA size, persistent grid and CTAs per SM
  * (the first 16 buckets).  out is host memory.                                                */
 typedef struct {
   int32_t chains_per_cta, grid, cta_threads_swaptions, n_buckets;

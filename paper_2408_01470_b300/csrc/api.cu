@@ -1062,8 +1062,11 @@ sabr_lmm_status tune_batch(sabr_lmm_anneal_plan* p, cudaStream_t s) {
 // Autotuner of the caplet level kernel's tile: chains (warps) per CTA, for a single caplet market in
 // FP32.  Every CTA size runs the same search bit for bit (a chain is one warp either way), so the
 // choice changes the time only.  Candidates: the one-wave heuristic, 28, 16, 14, 8, 7 and 4 chains
-// (those whose shared memory fits); each is timed on one level of 8 steps of the plan's own chains
-// (after one untimed run); cached per (caplet pairs, panels, forwards, chains).
+// (those whose shared memory fits); each is timed on one level of the plan's own length (at most
+// 100 steps), best of three after one untimed run; the heuristic stays unless another is 2 %
+// faster; cached per (caplet pairs, panels, forwards, chains).  (Markets with swaptions get no such
+// tuner: there the CTA size changes the order of the partial sums, and a timing-dependent choice
+// would make a search differ in its last bits from one process to the next.)
 std::map<std::tuple<int, int, int, int>, int> g_tune_w_cache;
 
 sabr_lmm_status tune_caplet_w(sabr_lmm_anneal_plan* p, cudaStream_t s) {
