@@ -143,7 +143,8 @@ __device__ void cta_objective_grad(const DevMarket& m, const InstrView<double>& 
   // ---------------- R2: the swap-rate SABR parameters -> the forms -> the column sums; the caplet
   //      forwards' (alpha_i, nu_i) -> their window [0, n_i) on diagonal 0 -> the prefix tables
   const R* SC = m.swap_scale64;
-  const R* Pc = cs.Qs + 3 * m.n_seg;   // column sums (forward)
+  const R* Ps = cs.Qs;   // segment partials (forward), weights (2 - [i = j]) u_i u_j
+  const int nseg = m.n_seg;
   for (int s = tid; s < ns + m.n_capfwd; s += nth) {
     if (s >= ns) {
       const int i = m.capfwd_list[s - ns];
@@ -168,12 +169,13 @@ __device__ void cta_objective_grad(const DevMarket& m, const InstrView<double>& 
       atomicAdd(PGb + 3 * ND * PL, Xb);
       continue;
     }
-    const int c0 = m.grp_col0[m.swap_grp[s]], L = m.swap_L[s], col = c0 + L - 1;
+    const int col = m.grp_col0[m.swap_grp[s]] + m.swap_L[s] - 1;
+    const int2 sr = m.swap_segs[s];
     R q1 = 0.0, q2 = 0.0, q3 = 0.0;
-    for (int j = 0; j < L; ++j) {
-      q1 += Pc[c0 + j];
-      q2 += Pc[nc + c0 + j];
-      q3 += Pc[2 * nc + c0 + j];
+    for (int q = sr.x; q < sr.y; ++q) {
+      q1 += Ps[q];
+      q2 += Ps[nseg + q];
+      q3 += Ps[2 * nseg + q];
     }
     const R sc = SC[s];
     const R V1 = sc * q1, V2 = sc * q2, V3 = sc * q3;

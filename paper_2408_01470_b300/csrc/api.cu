@@ -180,7 +180,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
         capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
         swp_w, cblk64, cblk32, cpair32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
         swap_grp, swap_L, seg, col_seg0, col_u, grp_col0, grp_u64, grp_u32, swap_scale64, swap_scale32, seg_dsc,
-        seg_uix, seg_w64, seg_w32;
+        seg_uix, seg_w64, seg_w32, swap_segs;
   };
   std::vector<Off> off(n_markets);
   std::vector<DevMarket> dm(n_markets);
@@ -189,7 +189,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
   std::vector<std::vector<int>> capfwd(n_markets), fwdnp(n_markets), swp_swap(n_markets), swap_a(n_markets),
       swap_b(n_markets), swap_np(n_markets), grp_a(n_markets), grp_nE(n_markets), grp_L(n_markets),
       grp_delta(n_markets), grp_swap0(n_markets), swap_grp(n_markets), swap_L(n_markets), seg(n_markets),
-      col_seg0(n_markets), col_u(n_markets), grp_col0(n_markets), sdsc(n_markets), suix(n_markets);
+      col_seg0(n_markets), col_u(n_markets), grp_col0(n_markets), sdsc(n_markets), suix(n_markets), sseg(n_markets);
   for (int j = 0; j < n_markets; ++j) {
     const sabr_lmm_market_desc& d = descs[j];
     DevMarket& m = dm[j];
@@ -274,6 +274,11 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.n_col = (int)col_seg0[j].size();
     col_seg0[j].push_back((int)seg[j].size());
     m.n_seg = (int)seg[j].size();
+    for (size_t sidx = 0; sidx < swap_a[j].size(); ++sidx) {
+      const int c0 = grp_col0[j][swap_grp[j][sidx]];
+      sseg[j].push_back(col_seg0[j][c0]);
+      sseg[j].push_back(col_seg0[j][c0 + swap_L[j][sidx]]);
+    }
     // the forward sweep's segment descriptors: segment s of S in column jj takes the pairs
     // i = s + S r (r = 0..3, i <= jj); an empty slot repeats pair (jj, jj) with weight 0
     {
@@ -299,6 +304,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
               uv[(size_t)q * 4 + r] = ((int)g * max_gwin + ii) | ((ii == jj ? 1 : 0) << 20) | ((valid ? 1 : 0) << 21);
             }
             dv[(size_t)q * 4 + 2] = nE;
+            dv[(size_t)q * 4 + 3] = (int)g * max_gwin + jj;
           }
         }
       }
@@ -306,8 +312,8 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.n_swap = (int)swap_a[j].size();
     m.max_win = max_win;
     m.NP = std::max(NP, 1);
-    // the segment and column partials (3 x (n_seg + n_col)) in the Y region when they fit there
-    m.qf_own = 3 * (m.n_seg + m.n_col) > m.NA * cta_y_stride() ? 1 : 0;
+    // the segment partials (3 x n_seg) in the Y region when they fit there
+    m.qf_own = 3 * m.n_seg > m.NA * cta_y_stride() ? 1 : 0;
     HostMarket& h = hm[j];
     h.model = d.model; h.formula = d.formula; h.n_param = d.n_param; h.n_fwd = d.n_fwd;
     h.n_cap = d.n_cap; h.n_swp = d.n_swp; h.beta = d.beta;
@@ -345,6 +351,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.seg_uix = A.take((size_t)m.n_seg * 16);
     o.seg_w64 = A.take((size_t)m.n_seg * 32);
     o.seg_w32 = A.take((size_t)m.n_seg * 16);
+    o.swap_segs = A.take((size_t)m.n_swap * 8);
     o.col_u = A.take((size_t)m.n_col * 4);
     o.grp_col0 = A.take((size_t)(ng + 1) * 4);
     o.grp_u64 = A.take((size_t)ng * m.max_gwin * 8);
@@ -377,6 +384,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     put(o.col_seg0, col_seg0[j].data(), col_seg0[j].size() * 4);
     put(o.seg_dsc, sdsc[j].data(), sdsc[j].size() * 4);
     put(o.seg_uix, suix[j].data(), suix[j].size() * 4);
+    put(o.swap_segs, sseg[j].data(), sseg[j].size() * 4);
     put(o.col_u, col_u[j].data(), col_u[j].size() * 4);
     put(o.grp_col0, grp_col0[j].data(), grp_col0[j].size() * 4);
     QuadTab<double> q64;
@@ -434,6 +442,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.seg = (const int*)(base + o.seg); m.col_seg0 = (const int*)(base + o.col_seg0);
     m.seg_dsc = (const int4*)(base + o.seg_dsc); m.seg_uix = (const int4*)(base + o.seg_uix);
     m.seg_w64 = (const double*)(base + o.seg_w64); m.seg_w32 = (const float*)(base + o.seg_w32);
+    m.swap_segs = (const int2*)(base + o.swap_segs);
     m.col_u = (const int*)(base + o.col_u); m.grp_col0 = (const int*)(base + o.grp_col0);
     m.grp_u64 = (const double*)(base + o.grp_u64); m.grp_u32 = (const float*)(base + o.grp_u32);
     m.swap_scale64 = (const double*)(base + o.swap_scale64); m.swap_scale32 = (const float*)(base + o.swap_scale32);

@@ -79,15 +79,17 @@ __global__ void setup_group_u_kernel(DevMarket m) {
   ((float*)m.grp_u32)[t] = (float)u;
 }
 
-// The four slot weights (2 - [i = j]) u_i of every segment of the forward sweep (0 on an empty slot).
+// The four slot weights (2 - [i = j]) u_i u_j of every segment of the forward sweep (0 on an empty
+// slot).
 __global__ void setup_seg_weights_kernel(DevMarket m) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= m.n_seg) return;
   const int4 x = m.seg_uix[q];
+  const double uj = m.grp_u64[m.seg_dsc[q].w];
   const int v[4] = {x.x, x.y, x.z, x.w};
   for (int r = 0; r < 4; ++r) {
     const int ix = v[r] & 0xfffff;
-    const double w = (v[r] >> 21) & 1 ? (((v[r] >> 20) & 1) ? 1.0 : 2.0) * m.grp_u64[ix] : 0.0;
+    const double w = (v[r] >> 21) & 1 ? (((v[r] >> 20) & 1) ? 1.0 : 2.0) * m.grp_u64[ix] * uj : 0.0;
     ((double*)m.seg_w64)[4 * q + r] = w;
     ((float*)m.seg_w32)[4 * q + r] = (float)w;
   }

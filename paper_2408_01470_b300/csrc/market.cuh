@@ -115,10 +115,15 @@ struct DevMarket {
   // which hold consecutive segments of a column, read consecutive diagonals at consecutive panel
   // offsets (prefix-table addresses on distinct banks).  One 16-byte descriptor per segment and its
   // four weights (2 - [i = j]) u_i (0 on an empty slot, whose offsets repeat pair (j, j)).
-  const int4* seg_dsc;             // [n_seg] x: lo_r << 8r, y: e_r << 8r (r = 0..3), z: the window nE
+  // The weights carry u_j as well, (2 - [i = j]) u_i u_j, so a segment's sums are already terms of
+  // Q_k(g, L), and a swap's forms are the sums over the segments of its group's first L columns, a
+  // contiguous range.
+  const int4* seg_dsc;             // [n_seg] x: lo_r << 8r, y: e_r << 8r (r = 0..3), z: the window nE,
+                                   //   w: g * max_gwin + j (the index of u_j)
   const int4* seg_uix;             // [n_seg] per slot r: g * max_gwin + i | (i == j) << 20 | valid << 21
   const double* seg_w64;           // [n_seg x 4] the slot weights (FP64)
   const float* seg_w32;            //   the same in FP32
+  const int2* swap_segs;           // [n_swap] the segments [x, y) of the swap's group's first L columns
   const int* col_u;                // [n_col] index g * max_gwin + j of the column's u_j
   const int* grp_col0;             // [n_grp + 1] first column of each group
   const double* grp_u64;           // [n_grp x max_gwin] u_{a + i} (FP64)

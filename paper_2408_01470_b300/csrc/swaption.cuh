@@ -40,8 +40,8 @@ template <class R> struct CtaScratch {
   Q4<R>* F4s;       // [n_swap] {alpha, nu/alpha, alpha^2, rho nu alpha}
   R* A3s;           // [n_swap] (2 - 3 rho^2) nu^2
   Q4<R>* RCs;       // [n_swap] {rho, 1/(1 - rho), 1/(1 + rho), 1 - rho^2}
-  R* Qs;            // [3 x (n_seg + n_col)] segment partials, then column sums / group prefixes of the
-                    //   quadratic forms (in the Y region, dead after the Grams, unless qf_own)
+  R* Qs;            // [3 x n_seg] segment partials of the quadratic forms (in the Y region, dead
+                    //   after the Grams, unless qf_own)
 };
 
 // Y row pitch: 16-byte rows, conflict-free 4-vector loads.  The tensor-core form fills all 80 values
@@ -83,7 +83,7 @@ __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int NAc = round_up(m.NA, 4);
   return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + 4 * 16 + round_up(m.NA * cta_y_stride(), 4) +
                       round_up(cta_pq_tables<R>() * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND + 4 * m.n_swap +
-                      round_up(m.n_swap, 4) + 4 * m.n_swap + (m.qf_own ? round_up(3 * (m.n_seg + m.n_col), 4) : 0),
+                      round_up(m.n_swap, 4) + 4 * m.n_swap + (m.qf_own ? round_up(3 * m.n_seg, 4) : 0),
                   4);
 }
 
@@ -678,15 +678,13 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
   //        Q_k(g, L) = sum_{j < L} u_j sum_{i <= j} (2 - [i = j]) u_i B_k[i, j],
   //      B = (rho G, rho theta X, phi G) of the pair, its window integrals from the prefix tables.
   //      (a) segments of <= kSeg pairs of one column, one thread each (segment s of S takes the
-  //      pairs s + S r: consecutive lanes read consecutive diagonals); (b) per column, u_j times its
-  //      segments in order; (c) per swap, the sum of its group's first L columns, V = scale Q, and
-  //      the swap-rate SABR factors; per caplet forward i, alpha_i and nu_i from the window [0, n_i)
-  //      of diagonal 0 (theta_ii = 1), the caplet's own Rebonato mapping.
+  //      pairs s + S r: consecutive lanes read consecutive diagonals), weights (2 - [i = j]) u_i u_j;
+  //      (b) per swap, the sum of the segments of its group's first L columns (a contiguous range),
+  //      V = scale Q, and the swap-rate SABR factors; per caplet forward i, alpha_i and nu_i from the
+  //      window [0, n_i) of diagonal 0 (theta_ii = 1), the caplet's own Rebonato mapping.
   {
     R* Ps = cs.Qs;                  // [3 x n_seg]
-    R* Pc = cs.Qs + 3 * m.n_seg;    // [3 x n_col]
-    const R* U = grp_u_of<R>(m);
-    const int ns = m.n_seg, nc = m.n_col;
+    const int ns = m.n_seg;
     for (int q = tid; q < ns; q += nth) {
       const int4 d = m.seg_dsc[q];
       const Q4<R> w = seg_w_of<R>(m)[q];
@@ -709,20 +707,6 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
       Ps[2 * ns + q] = s3;
     }
     __syncthreads();
-    for (int c = tid; c < nc; c += nth) {
-      const int q0 = m.col_seg0[c], q1 = m.col_seg0[c + 1];
-      R v1 = 0, v2 = 0, v3 = 0;
-      for (int q = q0; q < q1; ++q) {
-        v1 += Ps[q];
-        v2 += Ps[ns + q];
-        v3 += Ps[2 * ns + q];
-      }
-      const R uj = U[m.col_u[c]];
-      Pc[c] = uj * v1;
-      Pc[nc + c] = uj * v2;
-      Pc[2 * nc + c] = uj * v3;
-    }
-    __syncthreads();
     const R* SC = swap_scale_of<R>(m);
     for (int s = tid; s < m.n_swap + m.n_capfwd; s += nth) {
       if (s >= m.n_swap) {   // a caplet forward: diagonal 0, window [0, n_i)
@@ -735,12 +719,13 @@ __device__ typename ObjOf<R>::T cta_objective(const DevMarket& m, const InstrVie
         put_forward<R>(cs.cap, i, al, X2 > R(0) ? fdiv<R>(fsqrt<R>(X2), al * Ti) : R(0), phi);
         continue;
       }
-      const int c0 = m.grp_col0[m.swap_grp[s]], L = m.swap_L[s];
+      // the segments of the group's first L columns (their weights carry u_i u_j)
+      const int2 sr = m.swap_segs[s];
       R q1 = 0, q2 = 0, q3 = 0;
-      for (int j = 0; j < L; ++j) {
-        q1 += Pc[c0 + j];
-        q2 += Pc[nc + c0 + j];
-        q3 += Pc[2 * nc + c0 + j];
+      for (int q = sr.x; q < sr.y; ++q) {
+        q1 += Ps[q];
+        q2 += Ps[ns + q];
+        q3 += Ps[2 * ns + q];
       }
       const R sc = SC[s];
       const R v1 = sc * q1, v2 = sc * q2, v3 = sc * q3;
