@@ -31,6 +31,13 @@
 //                                    but does not print it; this is the reading fixed for this
 //                                    project.  Pins: one-period swap == caplet; rho=1 with equal
 //                                    vols gives the caplet vol; V1 >= 0.
+//   mm_alpha ....................... Eq. (haganForMercurio), the Mercurio & Morini mapping: the
+//                                    drift integral interval by interval between fixing dates.
+//                                    Pins: the closed form -sigma sum_j c_j T_j of that integral;
+//                                    sigma = 0 gives the smile formula at alpha_i; the paper's
+//                                    calibrated parameters (Table tab:paramsMercurioVolas) against
+//                                    its model vols (Table tab:mercurioVolas) and the descent from
+//                                    them to its published MRE.
 //   objective ...................... f_c and f_s of Section 3 in price space with vega weights.
 //                                    Pin: zero at the generating point on noise-free quotes.
 //   philox4x64_10 .................. Salmon, Moraes, Dror, Shaw (SC'11).  Pins: numpy's Philox
@@ -417,6 +424,29 @@ void swap_params(const Market& m, const S* th, int id, S& alpha, S& nu, S& rho, 
 }
 
 // ------------------------------------------------------------------ model vols, objective
+// ------------------------------------------------------------------ Mercurio & Morini model
+// Eq. (haganForMercurio): forward i's SABR alpha is alpha_i exp(int_0^{T_i} M_i(s) ds) with
+//   M_i(t) = -sigma sum_{j = h(t)}^{i} tau_j phi_j alpha_j F_j(0)^b / (1 + tau_j F_j(0)),
+// h(t) the first forward not yet fixed at t (Eq. h_t: forward j fixes at T_j, so h(t) = k on
+// [T_{k-1}, T_k), with T_{-1} = 0).  M_i is constant on each of those intervals, so the integral
+// is, interval by interval, its length times the value of M_i there.  The smile of forward i is
+// Eq. (sigmaHagan) with beta_i = beta, phi_ii = phi_i, sigma_i = sigma.
+// Parameter slots: [phi_0 .. phi_{M-1}, sigma, alpha_0 .. alpha_{M-1}] (M forwards).
+template <class S>
+S mm_alpha(const Market& m, const S* th, int i) {
+  const int M = (int)m.F.size();
+  const S& sigma = th[M];
+  S integral = 0.0;
+  for (int k = 0; k <= i; ++k) {
+    const double len = m.T[k] - (k == 0 ? 0.0 : m.T[k - 1]);
+    S Mi = 0.0;
+    for (int j = k; j <= i; ++j)
+      Mi += m.tau[j] * th[j] * th[M + 1 + j] * std::pow(m.F[j], m.beta) / (1.0 + m.tau[j] * m.F[j]);
+    integral += len * (-sigma * Mi);
+  }
+  return th[M + 1 + i] * exp(integral);
+}
+
 template <class S>
 S model_vol(const Market& m, double F, double K, double T, const S& alpha, const S& rho, const S& nu) {
   if (m.formula == 1) return sabr_paper(F, K, alpha, m.beta, rho, nu);
@@ -435,6 +465,9 @@ void all_vols(const Market& m, const S* th, std::vector<S>& vols) {
     double F = m.F[i], K = m.cK[k], T = m.T[i];
     if (m.model == 0) {
       vols[k] = model_vol(m, F, K, T, th[0], th[1], th[2]);
+    } else if (m.model == 2) {
+      const int M = (int)m.F.size();
+      vols[k] = model_vol(m, F, K, T, mm_alpha(m, th, i), th[i], th[M]);
     } else {
       auto it = fwd_par.find(i);
       if (it == fwd_par.end()) {
@@ -894,6 +927,7 @@ double orc_rmse_volpt(const void* mp, const double* th) { return orc::rmse_volpt
 // f and df/dtheta (all slots, free or not) by forward-mode dual numbers.
 double orc_objective_grad(const void* mp, const double* th, double* grad) {
   const orc::Market& m = *(const orc::Market*)mp;
+  if (m.n_param > orc::ND) return std::numeric_limits<double>::quiet_NaN();   // more slots than duals
   std::vector<orc::Dual> x;
   orc::seed_duals(m, th, x);
   orc::Dual f = orc::objective_t<orc::Dual>(m, x.data());
@@ -904,6 +938,7 @@ double orc_objective_grad(const void* mp, const double* th, double* grad) {
 // Residuals r_k and their Jacobian J[k, p] (row-major, n_instr x n_param); returns 0 if feasible.
 int orc_residuals_jac(const void* mp, const double* th, double* r, double* J) {
   const orc::Market& m = *(const orc::Market*)mp;
+  if (m.n_param > orc::ND) return 2;   // more slots than dual components
   std::vector<orc::Dual> x, rr;
   orc::seed_duals(m, th, x);
   if (!orc::residuals(m, x.data(), rr)) return 1;
@@ -934,6 +969,7 @@ int orc_nm(const void* mp, const double* theta0, int max_iter, double step, doub
 
 int orc_lm(const void* mp, const double* theta0, int max_iter, double target_rmse, double mu0,
            double* theta_out, double* f_out, double* rmse_out, int* iters_out) {
+  if (((const orc::Market*)mp)->n_param > orc::ND) return 2;   // the Jacobian's duals hold 12 slots
   return orc::lm(*(const orc::Market*)mp, theta0, max_iter, target_rmse, mu0, theta_out, f_out, rmse_out, iters_out);
 }
 

@@ -24,6 +24,7 @@ import numpy as np
 
 MODEL_SABR_SMILE = 0
 MODEL_REBONATO_LMM = 1
+MODEL_MERCURIO_MORINI = 2
 
 FORMULA_HAGAN2002 = 0
 FORMULA_PAPER = 1
@@ -34,6 +35,12 @@ FORMULA_PAPER = 1
 REBONATO_SLOTS = ("a", "b", "c", "d", "alpha_h", "beta_h", "gamma_h", "delta_h",
                   "phi", "lambda1", "lambda2", "lambda3")
 SMILE_SLOTS = ("alpha", "rho", "nu")
+
+
+def mm_slots(n_fwd: int):
+    """Parameter slots of the Mercurio & Morini model on n_fwd forwards (Section 2.2 and the
+    parameter classes of Section 3): phi_0..phi_{M-1}, the common sigma, alpha_0..alpha_{M-1}."""
+    return tuple([f"phi_{i}" for i in range(n_fwd)] + ["sigma"] + [f"alpha_{i}" for i in range(n_fwd)])
 
 BASE_SEED = 240801470
 
@@ -271,6 +278,35 @@ def batch_market(j: int, noise_volpt: float = 0.02) -> Skeleton:
         n_chains=4096, n_levels=100, steps=50, cooling=0.9)
 
 
+def mercurio_morini_caplets(seed: int = BASE_SEED + 3, noise_volpt: float = 0.02, n_fwd: int = 13,
+                            n_strikes: int = 9, formula: int = FORMULA_PAPER,
+                            noise_free: bool = False) -> Skeleton:
+    """Mercurio & Morini caplet smiles: n_fwd semi-annual forwards (fixings 0.5, 1.0, ..., levels
+    1% -> 4% as in the caplet term structure) with n_strikes caplets each at K = F e^m,
+    m in linspace(-0.8, 0.8) (the moneyness span of the paper's smiles).  Generating point:
+    phi_i ~ U(-0.8, 0.2), sigma ~ U(0.3, 0.8), alpha_i ~ U(0.05, 0.1) (the ranges of the paper's
+    calibrated Table tab:paramsMercurioVolas); search box phi in [-0.99, 0.99], sigma in
+    [0.01, 1.5], alpha in [0.001, 0.5].  Schedule: 4096 chains x 100 temperatures x 20 steps,
+    cooling 0.95.  2 n_fwd + 1 slots, all free."""
+    rng = np.random.default_rng(seed)
+    T, P, fwd = _semiannual_curve(n_fwd)
+    m = np.linspace(-0.8, 0.8, n_strikes)
+    cap_fwd = np.repeat(np.arange(n_fwd, dtype=np.int32), n_strikes)
+    cap_K = (fwd[:, None] * np.exp(m)[None, :]).reshape(-1)
+    theta = np.concatenate([rng.uniform(-0.8, 0.2, n_fwd), rng.uniform(0.3, 0.8, 1),
+                            rng.uniform(0.05, 0.1, n_fwd)])
+    lo = np.concatenate([np.full(n_fwd, -0.99), [0.01], np.full(n_fwd, 0.001)])
+    hi = np.concatenate([np.full(n_fwd, 0.99), [1.5], np.full(n_fwd, 0.5)])
+    n = len(cap_K)
+    noise = np.zeros(n) if noise_free else rng.normal(0.0, noise_volpt / 100.0, size=n)
+    return Skeleton(
+        name=f"mm_caplets_{n_fwd}x{n_strikes}", model=MODEL_MERCURIO_MORINI, formula=formula, beta=0.5,
+        T=T, P=P, cap_fwd=cap_fwd, cap_K=cap_K, swp_start=np.zeros(0, np.int32),
+        swp_end=np.zeros(0, np.int32), swp_K=np.zeros(0), lo=lo, hi=hi,
+        free=np.ones(2 * n_fwd + 1, np.uint8), theta_true=theta, noise=noise,
+        n_chains=4096, n_levels=100, steps=20, cooling=0.95)
+
+
 def uniform_in_box(skel: Skeleton, n: int, seed: int) -> np.ndarray:
     """n parameter sets drawn uniformly in the search box (fixed slots keep theta_true)."""
     rng = np.random.default_rng(seed)
@@ -292,12 +328,14 @@ def read_paper_market(path: str) -> dict:
     """The sections of a real-data market file (discount curve, moneyness, smiles, the paper's
     calibrated parameters and published figures), as plain lists; no arithmetic of the method."""
     sec, out = None, {"curve": [], "moneyness": [], "smiles": [], "params": [], "published": {}}
+    # (other sections, e.g. [sigma] and [model_vols] of a model's calibration, as lists of rows)
     for line in open(path):
         line = line.strip()
         if not line or line.startswith("#"):
             continue
         if line.startswith("["):
             sec = line.strip("[]")
+            out.setdefault(sec, [])
             continue
         parts = line.split()
         if sec == "published":
@@ -354,3 +392,65 @@ def paper_euribor_caplet_smiles(path: str):
         quotes.append(np.array([float(v) / 100.0 for v in row[1:]]))
     params = np.array([[float(r[3]), float(r[1]), float(r[2])] for r in d["params"]])
     return sks, quotes, params, d["published"]
+
+
+def paper_euribor_mm_market(path: str, mm_path: str):
+    """The 13 caplet smiles of the paper's real-data test (Section 4) as ONE market of the
+    Mercurio & Morini model (Section 2.2) with Eq. (sigmaHagan), beta = 0.5: 27 parameters
+    [phi_1..phi_13, sigma, alpha_1..alpha_13], coupled through sigma and the drift of
+    Eq. (haganForMercurio), so the smiles cannot be searched one by one.
+
+    Readings (the paper does not state them), beside those of paper_euribor_caplet_smiles: the 13
+    forwards are consecutive six-month periods, so they form the tenor structure whose fixing
+    dates the drift integral steps through; the tenor grid runs on the accrual clock, T_0 = the
+    first fixing (ACT/365 from 21/11/2011) and T_{i+1} = T_i + tau_i (ACT/360), so that
+    T_{i+1} - T_i is the accrual of forward i (with the fixings in ACT/365 instead, the descent
+    from the paper's parameters ends at the same MRE and parameters to 1e-6); discount factors
+    at the actual dates; box phi in [-0.99, 0.99], sigma in [0.01, 1.5], alpha in [0.001, 0.5].
+    Schedule: the paper's (16384 chains, N = 10, cooling 0.99 from T0 = 10 to T_min = 0.01:
+    688 levels).
+    Returns (skeleton, quotes [117], paper_params [27], paper model vols [12 x 5] (percent),
+    published figures)."""
+    import datetime as _dt
+    d = read_paper_market(path)
+    mm = read_paper_market(mm_path)
+    d0 = _dt.date(2011, 11, 21)
+
+    def days(s, sep, century):
+        a, b, c = (int(x) for x in s.split(sep))
+        return (_dt.date(c + century, b, a) - d0).days
+
+    ct = np.array([days(r[0], "/", 0) / 365.0 for r in d["curve"]])
+    lp = np.log(np.array([float(r[1]) for r in d["curve"]]))
+
+    def disc_days(n):
+        return float(np.exp(np.interp(n / 365.0, ct, lp)))
+
+    m = np.array([float(x) / 100.0 for x in d["moneyness"][0]])
+    fix = [days(r[0], "-", 2000) for r in d["smiles"]]
+    last = d0 + _dt.timedelta(days=fix[-1])
+    fix.append((_dt.date(last.year + (last.month + 6 - 1) // 12, (last.month + 6 - 1) % 12 + 1, last.day) - d0).days)
+    n_fwd = len(d["smiles"])
+    T = np.empty(n_fwd + 1)
+    T[0] = fix[0] / 365.0
+    for i in range(n_fwd):
+        T[i + 1] = T[i] + (fix[i + 1] - fix[i]) / 360.0
+    P = np.array([disc_days(n) for n in fix])
+    F = np.array([(P[i] / P[i + 1] - 1.0) / (T[i + 1] - T[i]) for i in range(n_fwd)])
+    cap_fwd = np.repeat(np.arange(n_fwd, dtype=np.int32), len(m))
+    cap_K = (F[:, None] * np.exp(m)[None, :]).reshape(-1)
+    quotes = np.array([[float(v) / 100.0 for v in row[1:]] for row in d["smiles"]]).reshape(-1)
+    phi = np.array([float(r[1]) for r in mm["params"]])
+    alpha = np.array([float(r[2]) for r in mm["params"]])
+    sigma = float(mm["sigma"][0][0])
+    params = np.concatenate([phi, [sigma], alpha])
+    vols = np.array([[float(v) for v in r[1:]] for r in mm["model_vols"]])
+    lo = np.concatenate([np.full(n_fwd, -0.99), [0.01], np.full(n_fwd, 0.001)])
+    hi = np.concatenate([np.full(n_fwd, 0.99), [1.5], np.full(n_fwd, 0.5)])
+    sk = Skeleton(
+        name="paper_mm", model=MODEL_MERCURIO_MORINI, formula=FORMULA_PAPER, beta=0.5, T=T, P=P,
+        cap_fwd=cap_fwd, cap_K=cap_K, swp_start=np.zeros(0, np.int32), swp_end=np.zeros(0, np.int32),
+        swp_K=np.zeros(0), lo=lo, hi=hi, free=np.ones(2 * n_fwd + 1, np.uint8),
+        theta_true=0.5 * (lo + hi), noise=np.zeros(len(cap_K)),
+        n_chains=16384, n_levels=688, steps=10, cooling=0.99)
+    return sk, quotes, params, vols, mm["published"]
