@@ -98,6 +98,13 @@ def _lib_handle():
             lib.orc_residuals_jac.restype = C.c_int
             lib.orc_residuals_jac.argtypes = [C.c_void_p, _D, _D, _D]
             lib.orc_philox4x64_10.argtypes = [C.POINTER(C.c_uint64)] * 3
+            lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+            lib.orc_mc_normals4.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int, _D]
+            _I = C.POINTER(C.c_int32)
+            lib.orc_mc_price.restype = C.c_int
+            lib.orc_mc_price.argtypes = [C.c_void_p, C.c_int, _D, _D, _D, _D, C.c_int, _I, _D, C.c_int, _I, _I,
+                                         _D, C.c_int64, C.c_double, C.c_uint64, C.c_int, _D, _D,
+                                         C.POINTER(C.c_int64)]
             lib.orc_step_uniforms.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int, _D]
             lib.orc_anneal.restype = C.c_int
             lib.orc_anneal.argtypes = [C.c_void_p, C.POINTER(_SAOpts), _D, _D, _D, _D, _D, _D,
@@ -167,6 +174,21 @@ def philox4x64_10(ctr, key):
     P = C.POINTER(C.c_uint64)
     _lib_handle().orc_philox4x64_10(c.ctypes.data_as(P), k.ctypes.data_as(P), o.ctypes.data_as(P))
     return o
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, np.uint32)
+    P = C.POINTER(C.c_uint32)
+    _lib_handle().orc_philox4x32_10(c.ctypes.data_as(P), k.ctypes.data_as(P), o.ctypes.data_as(P))
+    return o
+
+
+def mc_normals4(seed, path, step, block):
+    z = np.zeros(4)
+    _lib_handle().orc_mc_normals4(seed, path, step, block, _dp(z))
+    return z
 
 
 def step_uniforms(seed, chain_word, level, step, count):
@@ -273,8 +295,10 @@ class Market:
         return f, g
 
     def residuals_jac(self, theta):
+        """(r, J): the weighted residuals and their Jacobian (dual numbers, at most 12 slots; J is
+        None beyond that), or (None, None) at an infeasible point."""
         r = np.zeros(self.n_instr)
-        J = np.zeros((self.n_instr, self.n_param))
+        J = np.zeros((self.n_instr, self.n_param)) if self.n_param <= 12 else None
         rc = self._lib.orc_residuals_jac(self.h, _dp(_f64(theta)), _dp(r), _dp(J))
         return (r, J) if rc == 0 else (None, None)
 
@@ -317,6 +341,36 @@ class Market:
         self._lib.orc_lm(self.h, _dp(_f64(theta0)), int(max_iter), float(target_rmse), float(mu0),
                          _dp(th), _dp(f), _dp(r), C.byref(it))
         return dict(theta=th, f=f[0], rmse=r[0], iters=it.value)
+
+
+def mc_price(market, model, cap_fwd=(), cap_K=(), swp_a=(), swp_b=(), swp_K=(), n_paths=1000, dt=0.01,
+             seed=1, n_threads=1):
+    """Monte Carlo prices of caplets and swaptions under the Hagan SABR/LIBOR model (see
+    sabr_oracle.cpp mc_price) on `market`'s tenor structure.  model: dict with M, beta, eta1,
+    lambda1, eta2, lambda2, lambda3 and per-forward alpha, sigma, phi.  Returns (price, stderr,
+    n_bad), n_bad the paths left out (non-finite state), or None on a bad input."""
+    M = int(model["M"])
+    par = _f64([model["beta"], model["eta1"], model["lambda1"], model["eta2"], model["lambda2"], model["lambda3"]])
+    al, sg, ph = (_f64(model[k])[:M] for k in ("alpha", "sigma", "phi"))
+    cf = np.ascontiguousarray(cap_fwd, np.int32)
+    ck = _f64(cap_K)
+    sa = np.ascontiguousarray(swp_a, np.int32)
+    sb = np.ascontiguousarray(swp_b, np.int32)
+    sk = _f64(swp_K)
+    ni = len(cf) + len(sa)
+    price, sq = np.zeros(max(ni, 1)), np.zeros(max(ni, 1))
+    nb = C.c_int64(0)
+    _I = C.POINTER(C.c_int32)
+    rc = market._lib.orc_mc_price(market.h, M, _dp(par), _dp(al), _dp(sg), _dp(ph), len(cf), cf.ctypes.data_as(_I),
+                                  _dp(ck), len(sa), sa.ctypes.data_as(_I), sb.ctypes.data_as(_I), _dp(sk),
+                                  int(n_paths), float(dt), int(seed), int(n_threads), _dp(price), _dp(sq),
+                                  C.byref(nb))
+    if rc != 0:
+        return None
+    price, sq = price[:ni], sq[:ni]
+    ng = int(n_paths) - nb.value
+    se = np.sqrt(np.maximum(sq - price * price, 0.0) / max(ng - 1, 1))
+    return price, se, nb.value
 
 
 def quoted_market(skel, noise=True):

@@ -46,6 +46,15 @@
 //                                    3), standard coefficients.  Pins: a separable quadratic bowl
 //                                    in closed form, monotone best value, recovery on noise-free
 //                                    quotes.
+//   philox4x32_10, mc_normals4 ..... the 32-bit Philox and the Box-Muller normals of the Monte
+//                                    Carlo pricer.  Pins: Random123's known-answer vectors; the
+//                                    moments of the normals.
+//   mc_price ....................... the Monte Carlo pricer of Section 3 (Table tab:haganMCpricer):
+//                                    the Hagan SABR/LIBOR dynamics under the spot measure, log-Euler.
+//                                    Pins: a zero-strike caplet is worth P(0,T_i) - P(0,T_{i+1})
+//                                    and a zero-strike swaption P(0,T_a) - P(0,T_b) under any
+//                                    arbitrage-free dynamics; with sigma = 0, beta = 1 every caplet
+//                                    is Black's at vol alpha_i (the lognormal LIBOR market model).
 //   anneal ......................... the SA loop of Section 3 and its one-GPU parallel form
 //                                    (chains per level, min-reduction, broadcast).  Pins: the
 //                                    evaluation-count identity C(LN+1); recovery on tiny sets.
@@ -594,6 +603,259 @@ static void step_uniforms(uint64_t seed, uint64_t chain_word, int level, int ste
   }
 }
 
+// ------------------------------------------------------------------ Philox4x32-10
+// The 32-bit member of the same family (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications with the Weyl key schedule.  It feeds the Monte Carlo pricer.
+static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ k0; c1 = lo1; c2 = hi0 ^ c3 ^ k1; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Normals r = 4b .. 4b + 3 of time step `step` of path `path`: Philox4x32-10 at counter
+// (b, step, path, 0) under key (seed low word, seed high word); uniforms u = (x + 1/2) 2^-32 in
+// (0, 1); Box-Muller on the pairs (u0, u1) and (u2, u3): sqrt(-2 ln u_even) (cos, sin)(2 pi u_odd).
+static void mc_normals4(uint64_t seed, uint64_t path, int step, int b, double* z) {
+  const uint32_t ctr[4] = {(uint32_t)b, (uint32_t)step, (uint32_t)path, (uint32_t)(path >> 32)};
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  philox4x32_10(ctr, key, o);
+  for (int q = 0; q < 2; ++q) {
+    const double u0 = ((double)o[2 * q] + 0.5) * 0x1.0p-32, u1 = ((double)o[2 * q + 1] + 0.5) * 0x1.0p-32;
+    const double r = std::sqrt(-2.0 * std::log(u0));
+    z[2 * q] = r * std::cos(2.0 * M_PI * u1);
+    z[2 * q + 1] = r * std::sin(2.0 * M_PI * u1);
+  }
+}
+
+// ------------------------------------------------------------------ Monte Carlo pricer
+// The Hagan SABR/LIBOR model (Section 2.1, Eqs. dinamicasHagan1-2) under the spot measure:
+//   dF_i = mu^F_i dt + V_i F_i^b dW_i,   dV_i = mu^V_i dt + sigma_i V_i dZ_i,
+//   mu^F_i = V_i F_i^b sum_{j = h(t)}^{i} tau_j rho_ij V_j F_j^b / (1 + tau_j F_j),
+//   mu^V_i = sigma_i V_i sum_{j = h(t)}^{i} tau_j phi_ij V_j F_j^b / (1 + tau_j F_j),
+// V_i(0) = alpha_i, correlations rho_ij, theta_ij, phi_ij of Eqs. (rhoij), (thetaij), (phiij)
+// (phi_ij from the phi_ii), h(t) the first forward not yet fixed (Eq. h_t, forward j fixing at T_j).
+// phi_ij is the correlation of W_i with Z_j (the block of Section 2.1); the vol drift takes it with
+// the indices as printed.
+// Readings (the paper prints no scheme): Euler steps in F, absorbed at zero (for b < 1 the CEV
+// forward reaches zero; its drift and diffusion both carry F^b, so it stays there), log-Euler steps
+// in ln V, the drifts frozen over a step; a path whose state leaves the finite numbers is left out
+// and counted (n_bad); every interval [T_{k-1}, T_k] (T_{-1} = 0) is cut into ceil(len / dt) equal steps,
+// so the fixings fall on the grid; the Brownian increments of a step are L xi with xi standard
+// normals (mc_normals4, numbered r = 0, 1, ... within the step) and L the Cholesky factor of the
+// correlation matrix of (W, Z) ordered by forward, last forward first, W before Z (row 2(M-1-i)
+// is W_i, row 2(M-1-i) + 1 is Z_i): the forwards still alive are then the leading rows.  The spot
+// numeraire rolls over at the fixings, B(T_{i+1}) = prod_{k <= i} (1 + tau_k F_k(T_k)) / P(0, T_0).
+//   caplet on forward i, strike K: tau_i (F_i(T_i) - K)^+ paid at T_{i+1};
+//   swaption on the swap over [a, b), strike K: A(T_a) (S(T_a) - K)^+ at T_a, the annuity
+//   A = sum_k tau_k P(T_a, T_{k+1}) and S = (1 - P(T_a, T_b)) / A from the forwards at T_a.
+// price[k] = mean over the finite paths of the deflated payoff; sq[k] = mean of its square.
+struct McModel {
+  int M;                       // forwards simulated
+  double beta, eta1, lambda1, eta2, lambda2, lambda3;
+  std::vector<double> alpha, sigma, phi;   // per forward: V_i(0), vol of vol, phi_ii
+};
+
+static bool mc_cholesky(const Market& m, const McModel& md, std::vector<double>& L, std::vector<double>& C) {
+  const int n = 2 * md.M;
+  C.assign((size_t)n * n, 0.0);
+  auto fwd = [&](int r) { return md.M - 1 - r / 2; };
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      const int i = fwd(r), j = fwd(c);
+      const bool wi = (r % 2) == 0, wj = (c % 2) == 0;
+      const double dT = std::fabs(m.T[i] - m.T[j]);
+      double v;
+      if (wi && wj) v = md.eta1 + (1.0 - md.eta1) * std::exp(-md.lambda1 * dT);          // rho_ij
+      else if (!wi && !wj) v = md.eta2 + (1.0 - md.eta2) * std::exp(-md.lambda2 * dT);   // theta_ij
+      else {                                                                             // phi_ij (W_i with Z_j)
+        const int a = wi ? i : j, b = wi ? j : i;
+        const double pa = md.phi[a], pb = md.phi[b];
+        v = (pa < 0 ? -1.0 : 1.0) * std::sqrt(std::fabs(pa * pb)) * std::exp(-md.lambda3 * std::fabs(m.T[a] - m.T[b]));
+      }
+      C[(size_t)r * n + c] = v;
+    }
+  // Reading: with phi_ii of both signs Eq. (phiij) can make the matrix indefinite (the paper's own
+  // calibrated Hagan parameters do); it is then replaced by the nearest correlation matrix in the
+  // spectral sense (Rebonato and Jaeckel): eigenvalues below zero set to zero, B = S Lambda^(1/2)
+  // with every row scaled to unit length, C = B B^T.  Eigen-decomposition by cyclic Jacobi rotations.
+  // The repaired matrix replaces the printed one everywhere (increments and drifts), so that the
+  // discretised model stays free of arbitrage.
+  {
+    std::vector<double> A = C, S((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) S[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+      double off = 0.0;
+      for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+      if (off < 1e-30) break;
+      for (int p = 0; p < n; ++p)
+        for (int q = p + 1; q < n; ++q) {
+          const double apq = A[(size_t)p * n + q];
+          if (std::fabs(apq) < 1e-300) continue;
+          const double th = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+          const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+          const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+          for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+            const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+            A[(size_t)k * n + p] = c * akp - sn * akq;
+            A[(size_t)k * n + q] = sn * akp + c * akq;
+          }
+          for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+            const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+            A[(size_t)p * n + k] = c * apk - sn * aqk;
+            A[(size_t)q * n + k] = sn * apk + c * aqk;
+          }
+          for (int k = 0; k < n; ++k) {   // S <- S J
+            const double skp = S[(size_t)k * n + p], skq = S[(size_t)k * n + q];
+            S[(size_t)k * n + p] = c * skp - sn * skq;
+            S[(size_t)k * n + q] = sn * skp + c * skq;
+          }
+        }
+    }
+    bool neg = false;
+    for (int i = 0; i < n; ++i) neg = neg || A[(size_t)i * n + i] < 0.0;
+    if (neg) {
+      std::vector<double> B((size_t)n * n);
+      for (int i = 0; i < n; ++i) {
+        double nrm = 0.0;
+        for (int k = 0; k < n; ++k) {
+          const double v = S[(size_t)i * n + k] * std::sqrt(std::max(A[(size_t)k * n + k], 0.0));
+          B[(size_t)i * n + k] = v;
+          nrm += v * v;
+        }
+        for (int k = 0; k < n; ++k) B[(size_t)i * n + k] /= std::sqrt(nrm);
+      }
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          double v = 0.0;
+          for (int k = 0; k < n; ++k) v += B[(size_t)i * n + k] * B[(size_t)j * n + k];
+          C[(size_t)i * n + j] = v;
+        }
+    }
+  }
+  // Cholesky factor, semi-definite: a pivot at or below 1e-12 ends its column (no new noise there)
+  L.assign((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = C[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(d > 1e-12)) continue;
+    d = std::sqrt(d);
+    L[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = C[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / d;
+    }
+  }
+  return true;
+}
+
+static int mc_price(const Market& m, const McModel& md, int n_cap, const int* cap_fwd, const double* cap_K,
+                    int n_swp, const int* swp_a, const int* swp_b, const double* swp_K, int64_t n_paths, double dt,
+                    uint64_t seed, int n_threads, double* price, double* sq, int64_t* n_bad) {
+  const int M = md.M, n = 2 * M, ni = n_cap + n_swp;
+  std::vector<double> L, Cr;
+  if (!mc_cholesky(m, md, L, Cr)) return 1;
+  // the correlations the drifts use: those of the (repaired) matrix the increments are drawn from
+  auto rho = [&](int i, int j) { return Cr[(size_t)(2 * (M - 1 - i)) * n + 2 * (M - 1 - j)]; };
+  auto phi = [&](int i, int j) { return Cr[(size_t)(2 * (M - 1 - i)) * n + 2 * (M - 1 - j) + 1]; };
+  // the time grid: interval k ends at T_k
+  std::vector<int> nsteps(M);
+  for (int k = 0; k < M; ++k) {
+    const double len = m.T[k] - (k == 0 ? 0.0 : m.T[k - 1]);
+    nsteps[k] = std::max(1, (int)std::ceil(len / dt - 1e-9));
+  }
+  std::vector<double> sum(ni, 0.0), sum2(ni, 0.0);
+  int64_t bad = 0;
+#pragma omp parallel num_threads(n_threads > 0 ? n_threads : 1)
+  {
+    std::vector<double> ls(ni, 0.0), ls2(ni, 0.0);
+    int64_t lbad = 0;
+    std::vector<double> lnV(M), F(M), V(M), x(M), DF(M), DV(M), xi(n + 4), Z(n), fix(M), numer(M + 1);
+    std::vector<std::vector<double>> snap(M, std::vector<double>(M, 0.0));   // forwards at each fixing date
+#pragma omp for schedule(static)
+    for (int64_t p = 0; p < n_paths; ++p) {
+      for (int i = 0; i < M; ++i) { F[i] = m.F[i]; lnV[i] = std::log(md.alpha[i]); }
+      int step = 0;
+      for (int k = 0; k < M; ++k) {          // interval k: forwards k .. M-1 alive (h(t) = k)
+        const double h = (m.T[k] - (k == 0 ? 0.0 : m.T[k - 1])) / nsteps[k];
+        const int na = 2 * (M - k);          // alive rows of L
+        for (int s = 0; s < nsteps[k]; ++s, ++step) {
+          for (int b = 0; 4 * b < na; ++b) mc_normals4(seed, (uint64_t)p, step, b, &xi[4 * b]);
+          for (int r = 0; r < na; ++r) {
+            double z = 0.0;
+            for (int c = 0; c <= r; ++c) z += L[(size_t)r * n + c] * xi[c];
+            Z[r] = z;
+          }
+          for (int i = k; i < M; ++i) V[i] = std::exp(lnV[i]);
+          for (int i = k; i < M; ++i)
+            x[i] = m.tau[i] * V[i] * std::pow(F[i], md.beta) / (1.0 + m.tau[i] * F[i]);
+          for (int i = k; i < M; ++i) {
+            double dF = 0.0, dV = 0.0;
+            for (int j = k; j <= i; ++j) {
+              dF += rho(i, j) * x[j];
+              dV += phi(i, j) * x[j];
+            }
+            DF[i] = dF;
+            DV[i] = dV;
+          }
+          for (int i = k; i < M; ++i) {
+            const double vf = V[i] * std::pow(F[i], md.beta);          // V_i F_i^b
+            const int rw = 2 * (M - 1 - i);
+            F[i] = std::max(F[i] + vf * DF[i] * h + vf * std::sqrt(h) * Z[rw], 0.0);
+            lnV[i] += (md.sigma[i] * DV[i] - 0.5 * md.sigma[i] * md.sigma[i]) * h + md.sigma[i] * std::sqrt(h) * Z[rw + 1];
+          }
+        }
+        for (int i = k; i < M; ++i) snap[k][i] = F[i];   // the forwards at T_k
+        fix[k] = snap[k][k];
+      }
+      // a path whose state left the finite numbers (the vol process can explode: its spot-measure
+      // drift grows with the vols) is left out of every average and counted
+      bool finite = true;
+      for (int k = 0; k < M; ++k)
+        for (int i = k; i < M; ++i) finite = finite && std::isfinite(snap[k][i]);
+      if (!finite) { ++lbad; continue; }
+      // deflators: 1 / B(T_{i+1}) = P(0, T_0) / prod_{k <= i} (1 + tau_k F_k(T_k)); numer[i] = 1 / B(T_i)
+      numer[0] = m.P[0];
+      for (int k = 0; k < M; ++k) numer[k + 1] = numer[k] / (1.0 + m.tau[k] * fix[k]);
+      for (int c = 0; c < n_cap; ++c) {
+        const int i = cap_fwd[c];
+        const double pay = m.tau[i] * std::max(fix[i] - cap_K[c], 0.0) * numer[i + 1];
+        ls[c] += pay;
+        ls2[c] += pay * pay;
+      }
+      for (int c = 0; c < n_swp; ++c) {
+        const int a = swp_a[c], b = swp_b[c];
+        double disc = 1.0, A = 0.0;
+        for (int j = a; j < b; ++j) {
+          disc /= 1.0 + m.tau[j] * snap[a][j];
+          A += m.tau[j] * disc;
+        }
+        const double S = (1.0 - disc) / A;
+        const double pay = A * std::max(S - swp_K[c], 0.0) * numer[a];
+        ls[n_cap + c] += pay;
+        ls2[n_cap + c] += pay * pay;
+      }
+    }
+#pragma omp critical
+    {
+      for (int c = 0; c < ni; ++c) { sum[c] += ls[c]; sum2[c] += ls2[c]; }
+      bad += lbad;
+    }
+  }
+  const double ng = (double)(n_paths - bad);
+  for (int c = 0; c < ni; ++c) { price[c] = sum[c] / ng; sq[c] = sum2[c] / ng; }
+  if (n_bad) *n_bad = bad;
+  return 0;
+}
+
 // ------------------------------------------------------------------ simulated annealing
 struct SAOpts {  // mirrors oracle/__init__.py
   int32_t n_chains, n_levels, steps;
@@ -938,6 +1200,12 @@ double orc_objective_grad(const void* mp, const double* th, double* grad) {
 // Residuals r_k and their Jacobian J[k, p] (row-major, n_instr x n_param); returns 0 if feasible.
 int orc_residuals_jac(const void* mp, const double* th, double* r, double* J) {
   const orc::Market& m = *(const orc::Market*)mp;
+  if (!J) {   // residuals alone, in plain FP64
+    std::vector<double> rr;
+    if (!orc::residuals(m, th, rr)) return 1;
+    std::copy(rr.begin(), rr.end(), r);
+    return 0;
+  }
   if (m.n_param > orc::ND) return 2;   // more slots than dual components
   std::vector<orc::Dual> x, rr;
   orc::seed_duals(m, th, x);
@@ -950,6 +1218,23 @@ int orc_residuals_jac(const void* mp, const double* th, double* r, double* J) {
 }
 
 void orc_philox4x64_10(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { orc::philox4x64_10(ctr, key, out); }
+void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { orc::philox4x32_10(ctr, key, out); }
+void orc_mc_normals4(uint64_t seed, uint64_t path, int step, int b, double* z) { orc::mc_normals4(seed, path, step, b, z); }
+
+// Monte Carlo prices of caplets and swaptions on market mp's tenor structure (its first M forwards)
+// under the Hagan SABR/LIBOR model; params = [beta, eta1, lambda1, eta2, lambda2, lambda3] and the
+// per-forward alpha, sigma, phi_ii.  Returns 1 if the correlation matrix is not positive definite.
+int orc_mc_price(const void* mp, int M, const double* params, const double* alpha, const double* sigma,
+                 const double* phi, int n_cap, const int* cap_fwd, const double* cap_K, int n_swp, const int* swp_a,
+                 const int* swp_b, const double* swp_K, int64_t n_paths, double dt, uint64_t seed, int n_threads,
+                 double* price, double* sq, int64_t* n_bad) {
+  orc::McModel md;
+  md.M = M; md.beta = params[0]; md.eta1 = params[1]; md.lambda1 = params[2]; md.eta2 = params[3];
+  md.lambda2 = params[4]; md.lambda3 = params[5];
+  md.alpha.assign(alpha, alpha + M); md.sigma.assign(sigma, sigma + M); md.phi.assign(phi, phi + M);
+  return orc::mc_price(*(const orc::Market*)mp, md, n_cap, cap_fwd, cap_K, n_swp, swp_a, swp_b, swp_K, n_paths, dt,
+                       seed, n_threads, price, sq, n_bad);
+}
 
 void orc_step_uniforms(uint64_t seed, uint64_t chain_word, int level, int step, int count, double* u) {
   orc::step_uniforms(seed, chain_word, level, step, count, u);

@@ -454,3 +454,21 @@ def paper_euribor_mm_market(path: str, mm_path: str):
         theta_true=0.5 * (lo + hi), noise=np.zeros(len(cap_K)),
         n_chains=16384, n_levels=688, steps=10, cooling=0.99)
     return sk, quotes, params, vols, mm["published"]
+
+
+def paper_hagan_mc_model(path: str, mm_path: str, mc_path: str):
+    """The paper's calibrated Hagan SABR/LIBOR model (Section 4.1) as the input of the Monte Carlo
+    pricer: the 13-forward EURIBOR tenor structure of paper_euribor_mm_market (its skeleton carries
+    T and P), the per-forward (phi_ii, sigma_i, alpha_i) of Table tab:paramsHaganVolas, beta = 0.5,
+    the correlation parameters of Section 4.1.2, and the 117 caplets of Table tab:smilesFws (9
+    strikes on each forward).  Returns (skeleton, model dict, caplet forwards, caplet strikes,
+    Table tab:haganMCpricer rows [paths, dt, CPU s, GPU s, speedup])."""
+    sk, _, _, _, _ = paper_euribor_mm_market(path, mm_path)
+    _, _, hp, _ = paper_euribor_caplet_smiles(path)
+    mc = read_paper_market(mc_path)
+    corr = {r[0]: float(r[1]) for r in mc["correlation"]}
+    model = dict(M=sk.n_fwd, beta=0.5, eta1=corr["eta1"], lambda1=corr["lambda1"], eta2=corr["eta2"],
+                 lambda2=corr["lambda2"], lambda3=corr["lambda3"], alpha=hp[:, 0].copy(), sigma=hp[:, 2].copy(),
+                 phi=hp[:, 1].copy())
+    rows = np.array([[float(x) for x in r] for r in mc["mc_timings"]])
+    return sk, model, sk.cap_fwd.copy(), sk.cap_K.copy(), rows
