@@ -348,7 +348,7 @@ def mc_price(market, model, cap_fwd=(), cap_K=(), swp_a=(), swp_b=(), swp_K=(), 
     """Monte Carlo prices of caplets and swaptions under the Hagan SABR/LIBOR model (see
     sabr_oracle.cpp mc_price) on `market`'s tenor structure.  model: dict with M, beta, eta1,
     lambda1, eta2, lambda2, lambda3 and per-forward alpha, sigma, phi.  Returns (price, stderr,
-    n_bad), n_bad the paths left out (non-finite state), or None on a bad input."""
+    n_bad), n_bad the paths stopped at a non-finite state, or None on a bad input."""
     M = int(model["M"])
     par = _f64([model["beta"], model["eta1"], model["lambda1"], model["eta2"], model["lambda2"], model["lambda3"]])
     al, sg, ph = (_f64(model[k])[:M] for k in ("alpha", "sigma", "phi"))
@@ -368,8 +368,7 @@ def mc_price(market, model, cap_fwd=(), cap_K=(), swp_a=(), swp_b=(), swp_K=(), 
     if rc != 0:
         return None
     price, sq = price[:ni], sq[:ni]
-    ng = int(n_paths) - nb.value
-    se = np.sqrt(np.maximum(sq - price * price, 0.0) / max(ng - 1, 1))
+    se = np.sqrt(np.maximum(sq - price * price, 0.0) / max(int(n_paths) - 1, 1))
     return price, se, nb.value
 
 

@@ -645,8 +645,8 @@ static void mc_normals4(uint64_t seed, uint64_t path, int step, int b, double* z
 // the indices as printed.
 // Readings (the paper prints no scheme): Euler steps in F, absorbed at zero (for b < 1 the CEV
 // forward reaches zero; its drift and diffusion both carry F^b, so it stays there), log-Euler steps
-// in ln V, the drifts frozen over a step; a path whose state leaves the finite numbers is left out
-// and counted (n_bad); every interval [T_{k-1}, T_k] (T_{-1} = 0) is cut into ceil(len / dt) equal steps,
+// in ln V, the drifts frozen over a step; a path whose state (F or ln V) is not finite at a fixing
+// date pays nothing from there on and is counted (n_bad); every interval [T_{k-1}, T_k] (T_{-1} = 0) is cut into ceil(len / dt) equal steps,
 // so the fixings fall on the grid; the Brownian increments of a step are L xi with xi standard
 // normals (mc_normals4, numbered r = 0, 1, ... within the step) and L the Cholesky factor of the
 // correlation matrix of (W, Z) ordered by forward, last forward first, W before Z (row 2(M-1-i)
@@ -655,7 +655,7 @@ static void mc_normals4(uint64_t seed, uint64_t path, int step, int b, double* z
 //   caplet on forward i, strike K: tau_i (F_i(T_i) - K)^+ paid at T_{i+1};
 //   swaption on the swap over [a, b), strike K: A(T_a) (S(T_a) - K)^+ at T_a, the annuity
 //   A = sum_k tau_k P(T_a, T_{k+1}) and S = (1 - P(T_a, T_b)) / A from the forwards at T_a.
-// price[k] = mean over the finite paths of the deflated payoff; sq[k] = mean of its square.
+// price[k] = mean over all paths of the deflated payoff; sq[k] = mean of its square.
 struct McModel {
   int M;                       // forwards simulated
   double beta, eta1, lambda1, eta2, lambda2, lambda3;
@@ -780,6 +780,7 @@ static int mc_price(const Market& m, const McModel& md, int n_cap, const int* ca
     int64_t lbad = 0;
     std::vector<double> lnV(M), F(M), V(M), x(M), DF(M), DV(M), xi(n + 4), Z(n), fix(M), numer(M + 1);
     std::vector<std::vector<double>> snap(M, std::vector<double>(M, 0.0));   // forwards at each fixing date
+    std::vector<char> good(M);
 #pragma omp for schedule(static)
     for (int64_t p = 0; p < n_paths; ++p) {
       for (int i = 0; i < M; ++i) { F[i] = m.F[i]; lnV[i] = std::log(md.alpha[i]); }
@@ -809,30 +810,36 @@ static int mc_price(const Market& m, const McModel& md, int n_cap, const int* ca
           for (int i = k; i < M; ++i) {
             const double vf = V[i] * std::pow(F[i], md.beta);          // V_i F_i^b
             const int rw = 2 * (M - 1 - i);
-            F[i] = std::max(F[i] + vf * DF[i] * h + vf * std::sqrt(h) * Z[rw], 0.0);
+            const double fn = F[i] + vf * DF[i] * h + vf * std::sqrt(h) * Z[rw];
+            F[i] = fn > 0.0 ? fn : 0.0;
             lnV[i] += (md.sigma[i] * DV[i] - 0.5 * md.sigma[i] * md.sigma[i]) * h + md.sigma[i] * std::sqrt(h) * Z[rw + 1];
           }
         }
-        for (int i = k; i < M; ++i) snap[k][i] = F[i];   // the forwards at T_k
+        bool fin = true;
+        for (int i = k; i < M; ++i) {
+          snap[k][i] = F[i];   // the forwards at T_k
+          fin = fin && std::isfinite(F[i]) && std::isfinite(lnV[i]);
+        }
+        good[k] = fin && (k == 0 || good[k - 1]);
         fix[k] = snap[k][k];
       }
-      // a path whose state left the finite numbers (the vol process can explode: its spot-measure
-      // drift grows with the vols) is left out of every average and counted
-      bool finite = true;
-      for (int k = 0; k < M; ++k)
-        for (int i = k; i < M; ++i) finite = finite && std::isfinite(snap[k][i]);
-      if (!finite) { ++lbad; continue; }
+      // a path whose state leaves the finite numbers at a fixing date (the vol process can explode:
+      // its spot-measure drift grows with the vols) is stopped there: it pays nothing from that date
+      // on, and it is counted
+      if (!good[M - 1]) ++lbad;
       // deflators: 1 / B(T_{i+1}) = P(0, T_0) / prod_{k <= i} (1 + tau_k F_k(T_k)); numer[i] = 1 / B(T_i)
       numer[0] = m.P[0];
       for (int k = 0; k < M; ++k) numer[k + 1] = numer[k] / (1.0 + m.tau[k] * fix[k]);
       for (int c = 0; c < n_cap; ++c) {
         const int i = cap_fwd[c];
+        if (!good[i]) continue;
         const double pay = m.tau[i] * std::max(fix[i] - cap_K[c], 0.0) * numer[i + 1];
         ls[c] += pay;
         ls2[c] += pay * pay;
       }
       for (int c = 0; c < n_swp; ++c) {
         const int a = swp_a[c], b = swp_b[c];
+        if (!good[a]) continue;
         double disc = 1.0, A = 0.0;
         for (int j = a; j < b; ++j) {
           disc /= 1.0 + m.tau[j] * snap[a][j];
@@ -850,8 +857,7 @@ static int mc_price(const Market& m, const McModel& md, int n_cap, const int* ca
       bad += lbad;
     }
   }
-  const double ng = (double)(n_paths - bad);
-  for (int c = 0; c < ni; ++c) { price[c] = sum[c] / ng; sq[c] = sum2[c] / ng; }
+  for (int c = 0; c < ni; ++c) { price[c] = sum[c] / (double)n_paths; sq[c] = sum2[c] / (double)n_paths; }
   if (n_bad) *n_bad = bad;
   return 0;
 }
