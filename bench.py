@@ -406,6 +406,8 @@ def search_record(lib, name, prec, seed, stream, peaks, levels=None, cpu=None, e
 
 
 PAPER_DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "paper_euribor_20111121.txt")
+PAPER_MM = os.path.join(os.path.dirname(PAPER_DATA), "paper_mm_20111121.txt")
+PAPER_MC = os.path.join(os.path.dirname(PAPER_DATA), "paper_hagan_mc_20111121.txt")
 
 
 def paper_data_record(lib, seed, stream):
@@ -446,6 +448,106 @@ def paper_data_record(lib, seed, stream):
             "paper": {"mre": float(pub["mre"]), "sa_seconds": float(pub["sa_seconds"]),
                       "nm_seconds": float(pub["nm_seconds"]), "total_seconds": float(pub["total_seconds"]),
                       "evaluations": int(pub["evaluations"]), "hardware": pub["hardware"]}}
+
+
+def mm_paper_record(lib, seed, stream):
+    """The paper's Mercurio & Morini caplet calibration (Section 4.2.1): one search over the 27
+    parameters [phi_i, sigma, alpha_i] of the 13 EURIBOR smiles (coupled through sigma and the drift of
+    Eq. haganForMercurio), the paper's schedule and hybrid; device time and the mean relative vol
+    error beside the paper's figures (another GPU: context)."""
+    import torch
+    from paper_2408_01470_b300 import synth
+    sk, q, pr, pv, pub = synth.paper_euribor_mm_market(PAPER_DATA, PAPER_MM)
+    gm = lib.Market(sk, q)
+    kw = dict(prec="fp32", T0=10.0, lm_top_k=8, lm_max_iter=20000, polish_nm=True, use_graph=True, stream=stream)
+    warm = gm.anneal_prepare(sk.n_chains, 2, sk.steps, sk.cooling, seed, **kw)
+    warm.launch(stream=stream)
+    warm.fetch()
+    del warm
+    plan = gm.anneal_prepare(sk.n_chains, sk.n_levels, sk.steps, sk.cooling, seed, **kw)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plan.launch(stream=stream)
+    b.record(stream)
+    stream.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    r = plan.fetch()
+    del plan
+    v = gm.model_vols(r["x_best"][0][None, :], "fp64").cpu().numpy()[0]
+    return {"workload": f"paper_euribor_mercurio_morini_27params_{sk.n_chains}ch_x_{sk.n_levels}T_x_{sk.steps}steps",
+            "how": "one search over all 27 slots (warp kernels, one slot per lane), then Nelder-Mead (FP64) from "
+                   "the 8 best chains; device time of the whole call (CUDA events), of which the polish",
+            "seconds": t, "sa_seconds": t - float(r["lm_seconds"]), "nm_seconds": float(r["lm_seconds"]),
+            "mre": float(np.mean(np.abs(v - q) / q)), "evaluations": int(r["n_evals"]),
+            "prices_per_s": r["n_evals"] * sk.n_cap / t, "f_best": float(r["f_best"][0]),
+            "paper": {"mre": float(pub["mre"]), "sa_seconds": float(pub["sa_seconds"]),
+                      "nm_seconds": float(pub["nm_seconds"]), "total_seconds": float(pub["total_seconds"]),
+                      "evaluations": int(pub["evaluations"]), "hardware": pub["hardware"]}}
+
+
+def mc_flops_per_path(M, nsteps):
+    """Algorithmic floating-point operations of one Monte Carlo path (add, mul = 1; fma = 2; log,
+    sqrt, sin, cos, exp, reciprocal = 1), summed over the steps of every interval k with a = M - k
+    forwards alive: normals 2a (Box-Muller per pair: log, sqrt, sin, cos and 4 products = 8);
+    correlated increments, rows r < 2a of L: r + 1 fma each; per alive forward: V = exp(ln V),
+    F^b (log, exp), x (4 + reciprocal), two drift sums over its a - u partners (2 fma each), the F
+    step (5) and the ln V step (6)."""
+    total = 0.0
+    for k in range(M):
+        a = M - k
+        per = 8 * a + sum(2 * (r + 1) for r in range(2 * a))
+        per += sum(1 + 2 + 5 + 4 * (a - u) + 5 + 6 for u in range(a))
+        total += nsteps[k] * per
+    return total
+
+
+def mc_record(lib, stream, peaks, cpu=True):
+    """The Monte Carlo pricer on the paper's calibrated Hagan SABR/LIBOR model (13 EURIBOR forwards,
+    its 117 caplets), at the (paths, dt) of Table tab:haganMCpricer, FP32 as in the paper: device time
+    per pricing (CUDA events around the launch on its stream, after one untimed launch), path-steps/s
+    and the paper's GPU seconds (one GTX 470: context).  The roofline of the largest configuration
+    against the measured FP32 FMA rate, and the oracle's Monte Carlo on the host cores on a sample."""
+    import torch
+    from paper_2408_01470_b300 import synth
+    sk, model, cf, ck, rows = synth.paper_hagan_mc_model(PAPER_DATA, PAPER_MM, PAPER_MC)
+    out = {"workload": "paper_hagan_lmm_mc_13fwd_117caplets", "precision": "fp32", "configs": []}
+    big = None
+    for paths, dt, cpu_s, gpu_s, _ in rows:
+        plan = lib.McPlan(sk.T, sk.P, model, cf, ck, n_paths=int(paths), dt=float(dt), seed=20111121, prec="fp32",
+                          stream=stream)
+        plan.launch(stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5 if paths * (1 / dt) < 1e8 else 2
+        a.record(stream)
+        for _ in range(reps):
+            plan.launch(stream)
+        b.record(stream)
+        stream.synchronize()
+        t = a.elapsed_time(b) / 1e3 / reps
+        nsteps = [max(1, int(np.ceil((sk.T[k] - (sk.T[k - 1] if k else 0.0)) / dt - 1e-9))) for k in range(sk.n_fwd)]
+        steps = sum(nsteps)
+        rec = {"paths": int(paths), "dt": float(dt), "seconds": t, "path_steps_per_s": paths * steps / t,
+               "n_bad": int(plan.n_bad.item()), "paper_gpu_seconds": float(gpu_s), "paper_cpu_seconds": float(cpu_s),
+               "time_steps": steps}
+        out["configs"].append(rec)
+        big = (rec, nsteps)
+        del plan
+    rec, nsteps = big
+    flops = mc_flops_per_path(sk.n_fwd, nsteps) * rec["paths"]
+    out["roofline"] = roofline_alu(flops, rec["seconds"], peaks["fp32_tflops"], None, "mc_path_kernel<float>",
+                                   "measured FP32 FMA rate (libsabr_peaks.so)")
+    out["flops_per_path"] = mc_flops_per_path(sk.n_fwd, nsteps)
+    if cpu:
+        import oracle
+        om = oracle.Market(sk, np.full(sk.n_cap, 0.5))
+        threads = os.cpu_count() or 1
+        n, dt = 20000, float(rec["dt"])
+        t0 = time.perf_counter()
+        oracle.mc_price(om, model, cap_fwd=cf, cap_K=ck, n_paths=n, dt=dt, seed=1, n_threads=threads)
+        tc = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n * rec["time_steps"] / tc, "unit": "path-steps/s", "cores": threads,
+                               "kind": "oracle", "sample": f"{n} paths at dt = {dt} (FP64)"}
+    return out
 
 
 def lm_schedule_to_target(gm, C, N, cool, seed, target, schedule=(1, 2, 3, 5, 10, 20, 40, 80, 200)):
@@ -550,6 +652,7 @@ def main():
     ap.add_argument("--no-joint-variant", action="store_true")
     ap.add_argument("--no-batch-variant", action="store_true")
     ap.add_argument("--no-paper-data", action="store_true")
+    ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--clocks-dir", default="", help="folder for the raw nvidia-smi clock samples (default: temp dir)")
     ap.add_argument("--warps-per-block", type=int, default=0)
@@ -690,6 +793,12 @@ def main():
     # the paper's real-data caplet calibration, full schedule
     if args.prec == "fp32" and not args.no_paper_data:
         workloads["paper_euribor_caplets"] = paper_data_record(lib, seed, s)
+    # the paper's Mercurio & Morini calibration (27 coupled parameters), full schedule
+    if args.prec == "fp32" and not args.no_paper_data:
+        workloads["paper_euribor_mercurio_morini"] = mm_paper_record(lib, seed, s)
+    # the Monte Carlo pricer at the configurations of Table tab:haganMCpricer
+    if args.prec == "fp32" and not args.no_mc:
+        workloads["mc_hagan_caplets"] = mc_record(lib, s, peaks, cpu=not args.no_cpu_baseline)
     # the 256-market batch: one level (its full 100-level schedule: bench.py --workload batch)
     if args.prec == "fp32" and not args.no_batch_variant:
         rec, _, _, _, _ = search_record(lib, "batch", "fp32", seed, s, peaks, levels=1, e2e=False)

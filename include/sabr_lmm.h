@@ -68,8 +68,16 @@ typedef enum {
  *              [a, b, c, d, alpha_h, beta_h, gamma_h, delta_h, phi, lambda1, lambda2, lambda3]:
  *              g(u) = (a + b u) e^{-c u} + d and h(u) = (alpha_h + beta_h u) e^{-gamma_h u} + delta_h
  *              at time-to-fixing u, kappa = 1, phi_ii = phi, and the correlations of
- *              Eqs. (rhoij), (thetaij), (phiij) with eta1 = eta2 = 0.                       */
-typedef enum { SABR_LMM_MODEL_SMILE = 0, SABR_LMM_MODEL_REBONATO = 1 } sabr_lmm_model;
+ *              Eqs. (rhoij), (thetaij), (phiij) with eta1 = eta2 = 0.
+ *   MERCURIO_MORINI : the Mercurio & Morini SABR/LIBOR model (Section 2.2), caplets only, at
+ *              most 15 forwards, 2 n_fwd + 1 slots [phi_0..phi_{M-1}, sigma, alpha_0..alpha_{M-1}]:
+ *              forward i's smile has rho = phi_i, nu = sigma and the alpha of
+ *              Eq. (haganForMercurio), alpha_i exp(-sigma sum_{j <= i} tau_j phi_j alpha_j
+ *              F_j^b T_j / (1 + tau_j F_j)) (the drift integral between fixing dates, forward j
+ *              fixing at T_j).  The reverse sweep, the Levenberg-Marquardt polish and
+ *              sabr_lmm_anneal_noalloc cover at most 12 slots (ENOTSUP); the Nelder-Mead polish
+ *              covers every model.                                                          */
+typedef enum { SABR_LMM_MODEL_SMILE = 0, SABR_LMM_MODEL_REBONATO = 1, SABR_LMM_MODEL_MERCURIO_MORINI = 2 } sabr_lmm_model;
 
 /* SABR implied-vol formula.
  *   HAGAN2002 : Hagan, Kumar, Lesniewski, Woodward (2002) lognormal expansion with z/x(z) and
@@ -89,7 +97,8 @@ typedef enum { SABR_LMM_HAGAN2002 = 0, SABR_LMM_PAPER = 1 } sabr_lmm_formula;
  *                  over forwards [swp_start, swp_end) (annuity sum tau_k P[k+1], frozen weights).
  *   swp_w        : as cap_w.
  *   lo/hi[n_param], free_mask[n_param] : search box and the slots the annealer moves (1) or
- *                  keeps (0).  n_param must be 3 (SMILE) or 12 (REBONATO).
+ *                  keeps (0).  n_param must be 3 (SMILE), 12 (REBONATO) or 2 n_fwd + 1
+ *                  (MERCURIO_MORINI).
  *   panel        : quadrature panel width (years); for REBONATO every T[k] must be a whole
  *                  multiple of it.  quad_nodes: Gauss-Legendre nodes per panel (8 only).
  * Quotes are vols: the library prices them with Black's formula (the out-of-the-money option:
@@ -163,7 +172,8 @@ sabr_lmm_status sabr_lmm_model_vols(const sabr_lmm_market* m, int32_t market_idx
  * on caplet markets (FP64, or FP32 accumulating the parameter adjoints in FP64); markets with
  * swaptions are differentiated in FP64 whatever `prec`.  Paper: derivative of the cost functions
  * of Section 3.  Same errors, and ENOTSUP if a market's reverse sweep does not fit one CTA's
- * shared memory.                                                                              */
+ * shared memory, or for a Mercurio & Morini market (the sweep covers the smile and Rebonato
+ * models, at most 12 slots).                                                                  */
 sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int32_t market_idx,
                                         const double* X, int64_t n, int32_t prec, double* f,
                                         double* G, void* stream);
@@ -303,7 +313,9 @@ sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* m, int32_t market
  * beside the difference stencil; from J where the reverse sweep does not fit a CTA), projection
  * on the box, mu /10 on success, x10 on failure; a
  * point stops at target_rmse_volpt (if > 0) or once mu exceeds 1e16.  f, rmse: device [n] or
- * NULL, those of the final points.  Paper: the local polish of the hybrid scheme, Section 3.  */
+ * NULL, those of the final points.  ENOTSUP for a Mercurio & Morini market (it needs the
+ * reverse sweep; sabr_lmm_nm_polish covers every model).  Paper: the local polish of the hybrid
+ * scheme, Section 3.                                                                          */
 sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t market_idx, double* X,
                                    int64_t n, int32_t max_iter, double target_rmse_volpt,
                                    double* f, double* rmse, void* stream);
@@ -348,6 +360,80 @@ sabr_lmm_status sabr_lmm_quadrature_rule(int32_t q, double* x, double* w);
 
 const char* sabr_lmm_last_error(void);
 const char* sabr_lmm_version(void);
+
+/* ---------------------------------------------------------------- Monte Carlo pricer
+ * The Hagan SABR/LIBOR model (Section 2.1, Eqs. dinamicasHagan1-2) simulated under the spot
+ * measure with the drifts of Section 2.1 (h(t) the first forward not yet fixed), for the Monte
+ * Carlo pricing of caplets and swaptions of Section 3 (Table tab:haganMCpricer).
+ *   T[n_fwd+1], P[n_fwd+1] : tenor grid and discounts as in a market description: forward k fixes
+ *                  at T[k] and is paid at T[k+1], accrual tau_k = T[k+1] - T[k].
+ *   beta in [0, 1]; per forward alpha[k] = V_k(0) > 0, sigma[k] >= 0 (vol of vol), phi[k] = phi_kk
+ *                  in [-1, 1]; eta1, lambda1, eta2, lambda2, lambda3 of Eqs. (rhoij), (thetaij),
+ *                  (phiij): corr(W_i, W_j) = rho_ij, corr(Z_i, Z_j) = theta_ij, corr(W_i, Z_j) =
+ *                  sign(phi_ii) sqrt(|phi_ii phi_jj|) e^{-lambda3 |T_i - T_j|}.  An indefinite
+ *                  correlation matrix (the printed form makes one when the phi_kk differ in sign)
+ *                  is replaced by the nearest correlation matrix in the spectral sense (negative
+ *                  eigenvalues set to zero, rows rescaled to unit length), everywhere (increments
+ *                  and drifts).
+ *   caplets  : cap_fwd[n_cap], cap_K[n_cap] >= 0: tau_k (F_k(T_k) - K)^+ paid at T[k+1].
+ *   swaptions: swp_start/swp_end/swp_K[n_swp]: the payer swaption expiring at T[start] on the
+ *                  swap over forwards [start, end): A (S - K)^+ at expiry, A and S from the
+ *                  forwards at expiry.
+ * The instruments may reach at most 16 forwards (cap_fwd < 16, swp_end <= 16; ENOTSUP beyond);
+ * at most 4096 instruments.  All arrays are host memory, read during sabr_lmm_mc_prepare.     */
+typedef struct {
+  int32_t n_fwd;
+  const double* T;
+  const double* P;
+  double beta;
+  const double* alpha;
+  const double* sigma;
+  const double* phi;
+  double eta1, lambda1, eta2, lambda2, lambda3;
+  int32_t n_cap;
+  const int32_t* cap_fwd;
+  const double* cap_K;
+  int32_t n_swp;
+  const int32_t* swp_start;
+  const int32_t* swp_end;
+  const double* swp_K;
+} sabr_lmm_mc_desc;
+
+/* n_paths in [1, 2^40]; dt > 0: every interval between fixings (and [0, T[0]]) is cut into
+ * ceil(len / dt) equal steps; seed: the key of the paths' Philox4x32-10 streams (path p, step s,
+ * block b at counter (b, s, p low, p high)); prec: FP64 or FP32 (the path arithmetic; sums in
+ * FP64); grid: CTAs of 128 paths (0: one per 128 paths, at most 8 per SM, the rest looped).      */
+typedef struct {
+  int64_t n_paths;
+  double dt;
+  uint64_t seed;
+  int32_t prec;
+  int32_t grid;
+} sabr_lmm_mc_opts;
+
+typedef struct sabr_lmm_mc_plan sabr_lmm_mc_plan; /* opaque: the model constants and device buffers */
+
+/* Validate, build the time grid and the model constants (host, FP64: the correlation matrix, its
+ * spectral repair and Cholesky factor), allocate the plan's device buffers.  Synchronises
+ * `stream` once.  Errors: EINVAL (message names the field), ENOTSUP, ENOMEM, ECUDA.            */
+sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o, void* stream,
+                                    sabr_lmm_mc_plan** out);
+/* Enqueue one pricing on `stream` (the device of the plan): every path (one thread each) steps
+ * F by Euler (absorbed at zero: the CEV forward with beta < 1 reaches it) and ln V by log-Euler,
+ * the drifts frozen over a step, the increments L xi from Box-Muller normals; at each fixing the
+ * instruments fixing there are paid and deflated by the spot numeraire B(T_{k+1}) =
+ * prod_{j <= k} (1 + tau_j F_j(T_j)) / P(0, T_0).  A path whose F or ln V is not finite at a
+ * fixing pays nothing from there on and is counted in n_bad.  Outputs (device, caller-owned, or
+ * all NULL to keep them in the plan): price[n_cap + n_swp] (caplets, then swaptions, in the
+ * order given) = mean deflated payoff over n_paths, stderr_out[same] = its standard error,
+ * n_bad[1].  Asynchronous; calls on one plan must not overlap on the GPU.                      */
+sabr_lmm_status sabr_lmm_mc_launch(sabr_lmm_mc_plan* p, double* price, double* stderr_out,
+                                   long long* n_bad, void* stream);
+void sabr_lmm_mc_plan_free(sabr_lmm_mc_plan* p);
+/* prepare + launch + copy back: price, stderr_out (or NULL), n_bad (or NULL) are host memory.
+ * Synchronous.                                                                                 */
+sabr_lmm_status sabr_lmm_mc_price(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o, double* price,
+                                  double* stderr_out, int64_t* n_bad, void* stream);
 
 #ifdef __cplusplus
 }

@@ -90,6 +90,20 @@ class MarketInfo(C.Structure):
     ]
 
 
+class McDesc(C.Structure):
+    _fields_ = [
+        ("n_fwd", C.c_int32), ("T", _D), ("P", _D), ("beta", C.c_double), ("alpha", _D), ("sigma", _D),
+        ("phi", _D), ("eta1", C.c_double), ("lambda1", C.c_double), ("eta2", C.c_double),
+        ("lambda2", C.c_double), ("lambda3", C.c_double), ("n_cap", C.c_int32), ("cap_fwd", _I32),
+        ("cap_K", _D), ("n_swp", C.c_int32), ("swp_start", _I32), ("swp_end", _I32), ("swp_K", _D),
+    ]
+
+
+class McOpts(C.Structure):
+    _fields_ = [("n_paths", C.c_int64), ("dt", C.c_double), ("seed", C.c_uint64), ("prec", C.c_int32),
+                ("grid", C.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -98,7 +112,8 @@ EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective",
            "sabr_lmm_anneal_fetch", "sabr_lmm_anneal_plan_free", "sabr_lmm_anneal_noalloc", "sabr_lmm_lm_polish",
            "sabr_lmm_market_info", "sabr_lmm_selftest_wait", "sabr_lmm_quadrature_rule", "sabr_lmm_last_error",
            "sabr_lmm_version", "sabr_lmm_residuals", "sabr_lmm_sync", "sabr_lmm_test_raise_error",
-           "sabr_lmm_nm_polish", "sabr_lmm_anneal_plan_config")
+           "sabr_lmm_nm_polish", "sabr_lmm_anneal_plan_config", "sabr_lmm_mc_prepare", "sabr_lmm_mc_launch",
+           "sabr_lmm_mc_plan_free", "sabr_lmm_mc_price")
 
 
 def open_library(path: str = LIB_PATH):
@@ -132,6 +147,11 @@ def open_library(path: str = LIB_PATH):
     lib.sabr_lmm_market_info.argtypes = [C.c_void_p, C.c_int32, C.POINTER(MarketInfo)]
     lib.sabr_lmm_selftest_wait.argtypes = [C.c_int64, C.c_void_p]
     lib.sabr_lmm_quadrature_rule.argtypes = [C.c_int32, _D, _D]
+    lib.sabr_lmm_mc_prepare.argtypes = [C.POINTER(McDesc), C.POINTER(McOpts), C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.sabr_lmm_mc_launch.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.sabr_lmm_mc_plan_free.argtypes = [C.c_void_p]
+    lib.sabr_lmm_mc_plan_free.restype = None
+    lib.sabr_lmm_mc_price.argtypes = [C.POINTER(McDesc), C.POINTER(McOpts), _D, _D, C.POINTER(C.c_int64), C.c_void_p]
     lib.sabr_lmm_last_error.restype = C.c_char_p
     lib.sabr_lmm_version.restype = C.c_char_p
     return lib
@@ -465,3 +485,80 @@ class _LazyFunction:
 
 
 CalibrationObjective = _LazyFunction()
+
+
+# ---------------------------------------------------------------- Monte Carlo pricer
+def mc_describe(T, P, model, cap_fwd=(), cap_K=(), swp_start=(), swp_end=(), swp_K=()):
+    """An McDesc for a tenor structure (T, P) and a Hagan SABR/LIBOR model dict (beta, eta1, lambda1,
+    eta2, lambda2, lambda3 and per-forward alpha, sigma, phi); returns (desc, keep-alive arrays)."""
+    n_fwd = len(T) - 1
+    keep = dict(T=_f64(T), P=_f64(P), alpha=_f64(np.resize(model["alpha"], n_fwd)),
+                sigma=_f64(np.resize(model["sigma"], n_fwd)), phi=_f64(np.resize(model["phi"], n_fwd)),
+                cap_fwd=np.ascontiguousarray(cap_fwd, np.int32), cap_K=_f64(cap_K),
+                swp_start=np.ascontiguousarray(swp_start, np.int32), swp_end=np.ascontiguousarray(swp_end, np.int32),
+                swp_K=_f64(swp_K))
+    d = McDesc()
+    d.n_fwd = n_fwd
+    d.T, d.P = keep["T"].ctypes.data_as(_D), keep["P"].ctypes.data_as(_D)
+    d.beta = float(model["beta"])
+    d.alpha, d.sigma, d.phi = (keep[k].ctypes.data_as(_D) for k in ("alpha", "sigma", "phi"))
+    d.eta1, d.lambda1, d.eta2 = float(model["eta1"]), float(model["lambda1"]), float(model["eta2"])
+    d.lambda2, d.lambda3 = float(model["lambda2"]), float(model["lambda3"])
+    d.n_cap = len(keep["cap_fwd"])
+    d.cap_fwd, d.cap_K = keep["cap_fwd"].ctypes.data_as(_I32), keep["cap_K"].ctypes.data_as(_D)
+    d.n_swp = len(keep["swp_start"])
+    d.swp_start, d.swp_end = keep["swp_start"].ctypes.data_as(_I32), keep["swp_end"].ctypes.data_as(_I32)
+    d.swp_K = keep["swp_K"].ctypes.data_as(_D)
+    return d, keep
+
+
+def _mc_opts(n_paths, dt, seed, prec, grid):
+    o = McOpts()
+    o.n_paths, o.dt, o.seed, o.prec, o.grid = int(n_paths), float(dt), int(seed), _prec(prec), int(grid)
+    return o
+
+
+def mc_price(T, P, model, cap_fwd=(), cap_K=(), swp_start=(), swp_end=(), swp_K=(), n_paths=100000, dt=0.01,
+             seed=1, prec="fp32", grid=0, stream=None):
+    """sabr_lmm_mc_price: Monte Carlo prices (caplets, then swaptions), their standard errors and
+    the count of stopped paths, as numpy arrays (synchronous)."""
+    lib = load()
+    d, keep = mc_describe(T, P, model, cap_fwd, cap_K, swp_start, swp_end, swp_K)
+    o = _mc_opts(n_paths, dt, seed, prec, grid)
+    ni = d.n_cap + d.n_swp
+    price, se, nb = np.zeros(max(ni, 1)), np.zeros(max(ni, 1)), C.c_int64(0)
+    _check(lib.sabr_lmm_mc_price(C.byref(d), C.byref(o), price.ctypes.data_as(_D), se.ctypes.data_as(_D),
+                                 C.byref(nb), _stream_ptr(stream)))
+    del keep
+    return price[:ni], se[:ni], nb.value
+
+
+class McPlan:
+    """sabr_lmm_mc_prepare / launch / plan_free: the model's constants and device buffers, priced
+    again and again (launch is stream-ordered; outputs are device tensors)."""
+
+    def __init__(self, T, P, model, cap_fwd=(), cap_K=(), swp_start=(), swp_end=(), swp_K=(), n_paths=100000,
+                 dt=0.01, seed=1, prec="fp32", grid=0, stream=None):
+        import torch
+        self._lib = load()
+        d, keep = mc_describe(T, P, model, cap_fwd, cap_K, swp_start, swp_end, swp_K)
+        o = _mc_opts(n_paths, dt, seed, prec, grid)
+        h = C.c_void_p()
+        _check(self._lib.sabr_lmm_mc_prepare(C.byref(d), C.byref(o), _stream_ptr(stream), C.byref(h)))
+        del keep
+        self.h = h
+        self.n_instr = d.n_cap + d.n_swp
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.price = torch.zeros(self.n_instr, dtype=torch.float64, device=dev)
+        self.stderr = torch.zeros(self.n_instr, dtype=torch.float64, device=dev)
+        self.n_bad = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def launch(self, stream=None):
+        _check(self._lib.sabr_lmm_mc_launch(self.h, C.c_void_p(self.price.data_ptr()),
+                                            C.c_void_p(self.stderr.data_ptr()), C.c_void_p(self.n_bad.data_ptr()),
+                                            _stream_ptr(stream)))
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._lib.sabr_lmm_mc_plan_free(self.h)
+            self.h = None

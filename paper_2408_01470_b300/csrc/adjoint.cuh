@@ -293,9 +293,9 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
   const double f = warp_sum_d((double)facc);
   rho_bar = warp_sum_d(rho_bar);
   __syncwarp();
-  double gacc[kMaxParam];
+  double gacc[kMaxGradParam];
 #pragma unroll
-  for (int k = 0; k < kMaxParam; ++k) gacc[k] = 0.0;
+  for (int k = 0; k < kMaxGradParam; ++k) gacc[k] = 0.0;
   if (MODEL == 0) {
     double sa = 0.0, sn = 0.0;
     for (int j = lane; j < m.n_capfwd; j += 32) {
@@ -309,7 +309,7 @@ __device__ void warp_objective_grad(const DevMarket& m, const InstrView<R>& capB
     caplet_mapping_reverse<R>(m, qt, ws, as, lane, gacc);
   }
 #pragma unroll
-  for (int k = 0; k < kMaxParam; ++k) gacc[k] = warp_sum_d(gacc[k]);
+  for (int k = 0; k < kMaxGradParam; ++k) gacc[k] = warp_sum_d(gacc[k]);
   if (MODEL == 0) gacc[1] = rho_bar;
   else gacc[8] = rho_bar;
   if (lane == 0) {

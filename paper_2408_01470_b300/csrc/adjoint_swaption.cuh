@@ -102,9 +102,9 @@ __device__ void cta_objective_grad(const DevMarket& m, const InstrView<double>& 
     gs.cap.nbar[i] = 0.0;
   }
   __syncthreads();
-  double gacc[kMaxParam];
+  double gacc[kMaxGradParam];
 #pragma unroll
-  for (int k = 0; k < kMaxParam; ++k) gacc[k] = 0.0;
+  for (int k = 0; k < kMaxGradParam; ++k) gacc[k] = 0.0;
   // ---------------- R1: pricing with the local reverse sweep (caplets, then swaptions)
   bool ok = true;
   R facc = 0.0;
@@ -423,19 +423,19 @@ __device__ void cta_objective_grad(const DevMarket& m, const InstrView<double>& 
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, off);
 #pragma unroll
-  for (int k = 0; k < kMaxParam; ++k) gacc[k] = warp_sum_d(gacc[k]);
+  for (int k = 0; k < kMaxGradParam; ++k) gacc[k] = warp_sum_d(gacc[k]);
   if (lane == 0) {
     gs.red[warp * 16 + 12] = fsum;
 #pragma unroll
-    for (int k = 0; k < kMaxParam; ++k) gs.red[warp * 16 + k] = gacc[k];
+    for (int k = 0; k < kMaxGradParam; ++k) gs.red[warp * 16 + k] = gacc[k];
   }
   __syncthreads();
   if (tid == 0) {
-    double f = 0.0, g[kMaxParam];
-    for (int k = 0; k < kMaxParam; ++k) g[k] = 0.0;
+    double f = 0.0, g[kMaxGradParam];
+    for (int k = 0; k < kMaxGradParam; ++k) g[k] = 0.0;
     for (int w = 0; w < nw; ++w) {
       f += gs.red[w * 16 + 12];
-      for (int k = 0; k < kMaxParam; ++k) g[k] += gs.red[w * 16 + k];
+      for (int k = 0; k < kMaxGradParam; ++k) g[k] += gs.red[w * 16 + k];
     }
     const bool fin = !bad && isfinite(f);
     *f_out = fin ? f : __longlong_as_double(0x7ff0000000000000LL);

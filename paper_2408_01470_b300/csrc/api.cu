@@ -111,7 +111,8 @@ std::string validate(const sabr_lmm_market_desc& d, int idx) {
     snprintf(buf, sizeof buf, "market %d: %s", idx, what);
     return std::string(buf);
   };
-  if (d.model != SABR_LMM_MODEL_SMILE && d.model != SABR_LMM_MODEL_REBONATO) return bad("model must be 0 or 1");
+  if (d.model != SABR_LMM_MODEL_SMILE && d.model != SABR_LMM_MODEL_REBONATO && d.model != SABR_LMM_MODEL_MERCURIO_MORINI)
+    return bad("model must be 0, 1 or 2");
   if (d.formula != SABR_LMM_HAGAN2002 && d.formula != SABR_LMM_PAPER) return bad("formula must be 0 or 1");
   if (!(d.beta >= 0.0 && d.beta <= 1.0)) return bad("beta must be in [0, 1]");
   if (d.n_fwd < 1 || d.n_fwd > 120) return bad("n_fwd must be in [1, 120]");
@@ -141,6 +142,10 @@ std::string validate(const sabr_lmm_market_desc& d, int idx) {
   if (d.model == SABR_LMM_MODEL_SMILE) {
     if (d.n_param != 3) return bad("the smile model has 3 parameters [alpha, rho, nu]");
     if (d.n_swp != 0) return bad("the smile model prices caplets only");
+  } else if (d.model == SABR_LMM_MODEL_MERCURIO_MORINI) {
+    if (d.n_fwd > 15) return bad("the Mercurio & Morini model takes at most 15 forwards (2 n_fwd + 1 <= 31 slots)");
+    if (d.n_param != 2 * d.n_fwd + 1) return bad("the Mercurio & Morini model has 2 n_fwd + 1 slots [phi_i, sigma, alpha_i]");
+    if (d.n_swp != 0) return bad("the Mercurio & Morini model prices caplets only");
   } else {
     if (d.n_param != 12) return bad("the Rebonato model has 12 parameter slots");
     if (!(d.panel > 0.0)) return bad("panel must be > 0");
@@ -180,7 +185,7 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
         capfwd_list, fwd_np, lo, hi, freem, F, tau, swap_A, swap_S, swap_TE, swap_W, swap_np, cap_pm, cap_w, swp_pm,
         swp_w, cblk64, cblk32, cpair32, sblk64, sblk32, q64, q32, err, grp_a, grp_nE, grp_L, grp_delta, grp_swap0,
         swap_grp, swap_L, seg, col_seg0, col_u, grp_col0, grp_u64, grp_u32, swap_scale64, swap_scale32, seg_dsc,
-        seg_uix, seg_w64, seg_w32, swap_segs;
+        seg_uix, seg_w64, seg_w32, swap_segs, mm_k64, mm_k32;
   };
   std::vector<Off> off(n_markets);
   std::vector<DevMarket> dm(n_markets);
@@ -358,6 +363,9 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     o.grp_u32 = A.take((size_t)ng * m.max_gwin * 4);
     o.swap_scale64 = A.take((size_t)m.n_swap * 8);
     o.swap_scale32 = A.take((size_t)m.n_swap * 4);
+    const bool mm = d.model == SABR_LMM_MODEL_MERCURIO_MORINI;
+    o.mm_k64 = A.take(mm ? d.n_fwd * 8 : 0);
+    o.mm_k32 = A.take(mm ? d.n_fwd * 4 : 0);
   }
   std::vector<unsigned char> host(A.size, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { if (src && bytes) std::memcpy(host.data() + o, src, bytes); };
@@ -446,6 +454,9 @@ extern "C" sabr_lmm_status sabr_lmm_load_market(const sabr_lmm_market_desc* desc
     m.col_u = (const int*)(base + o.col_u); m.grp_col0 = (const int*)(base + o.grp_col0);
     m.grp_u64 = (const double*)(base + o.grp_u64); m.grp_u32 = (const float*)(base + o.grp_u32);
     m.swap_scale64 = (const double*)(base + o.swap_scale64); m.swap_scale32 = (const float*)(base + o.swap_scale32);
+    const bool mm = m.model == SABR_LMM_MODEL_MERCURIO_MORINI;
+    m.mm_k64 = mm ? (const double*)(base + o.mm_k64) : nullptr;
+    m.mm_k32 = mm ? (const float*)(base + o.mm_k32) : nullptr;
     setup_forwards_kernel<<<(m.n_fwd + 127) / 128, 128, 0, s>>>(m);
     if (m.n_swap > 0) {
       setup_swaps_kernel<<<(m.n_swap + 127) / 128, 128, 0, s>>>(m);
@@ -512,6 +523,7 @@ template <class R>
 cudaError_t launch_objective_r(const DevMarket& m, const double* X, long long n, double* f, double* vols, double* res,
                                cudaStream_t s) {
   if (m.model == 0) return m.formula == 0 ? launch_objective<R, 0, 0>(m, X, n, f, vols, res, s) : launch_objective<R, 0, 1>(m, X, n, f, vols, res, s);
+  if (m.model == 2) return m.formula == 0 ? launch_objective<R, 2, 0>(m, X, n, f, vols, res, s) : launch_objective<R, 2, 1>(m, X, n, f, vols, res, s);
   return m.formula == 0 ? launch_objective<R, 1, 0>(m, X, n, f, vols, res, s) : launch_objective<R, 1, 1>(m, X, n, f, vols, res, s);
 }
 
@@ -653,6 +665,8 @@ extern "C" sabr_lmm_status sabr_lmm_objective_grad(const sabr_lmm_market* m, int
                                                    int32_t prec, double* f, double* G, void* stream) {
   sabr_lmm_status st = check_call(m, idx, n, prec);
   if (st != SABR_LMM_OK) return st;
+  if (m->dm[idx].n_param > kMaxGradParam || m->dm[idx].model == SABR_LMM_MODEL_MERCURIO_MORINI)
+    return fail(SABR_LMM_ENOTSUP, "the reverse sweep covers the smile and Rebonato models (at most 12 parameter slots)");
   if (!grad_fits(m->dm[idx]))
     return fail(SABR_LMM_ENOTSUP, "the reverse sweep of this market does not fit one CTA's shared memory");
   if (n == 0) return SABR_LMM_OK;
@@ -697,6 +711,9 @@ cudaError_t launch_nm(const DevMarket& m, double* X, long long n, int max_iter, 
   if (m.model == 0)
     return m.formula == 0 ? launch_nm_t<0, 0>(m, X, n, max_iter, step, ftol, f, evals, s)
                           : launch_nm_t<0, 1>(m, X, n, max_iter, step, ftol, f, evals, s);
+  if (m.model == 2)
+    return m.formula == 0 ? launch_nm_t<2, 0>(m, X, n, max_iter, step, ftol, f, evals, s)
+                          : launch_nm_t<2, 1>(m, X, n, max_iter, step, ftol, f, evals, s);
   return m.formula == 0 ? launch_nm_t<1, 0>(m, X, n, max_iter, step, ftol, f, evals, s)
                         : launch_nm_t<1, 1>(m, X, n, max_iter, step, ftol, f, evals, s);
 }
@@ -858,6 +875,9 @@ extern "C" sabr_lmm_status sabr_lmm_lm_polish(const sabr_lmm_market* m, int32_t 
   if (n == 0) return SABR_LMM_OK;
   if (!X) return fail(SABR_LMM_EINVAL, "X is required");
   if (max_iter < 0 || n > (1 << 20)) return fail(SABR_LMM_EINVAL, "max_iter >= 0 and n <= 2^20 required");
+  if (m->dm[idx].n_param > kMaxGradParam || m->dm[idx].model == SABR_LMM_MODEL_MERCURIO_MORINI)
+    return fail(SABR_LMM_ENOTSUP, "the Levenberg-Marquardt polish covers the smile and Rebonato models (at most 12 "
+                                  "parameter slots)");
   const DevMarket& dm = m->dm[idx];
   cudaStream_t s = (cudaStream_t)stream;
   void* buf = nullptr;
@@ -937,6 +957,8 @@ cudaError_t enqueue_anneal(const DevMarket& m, int prec, const SAState& st, cons
 #define DISPATCH(R)                                                                                           \
   if (m.model == 0) return m.formula == 0 ? enqueue_anneal_t<R, 0, 0>(m, st, sp, W, grid, s, configure_only)  \
                                           : enqueue_anneal_t<R, 0, 1>(m, st, sp, W, grid, s, configure_only); \
+  if (m.model == 2) return m.formula == 0 ? enqueue_anneal_t<R, 2, 0>(m, st, sp, W, grid, s, configure_only)  \
+                                          : enqueue_anneal_t<R, 2, 1>(m, st, sp, W, grid, s, configure_only); \
   return m.formula == 0 ? enqueue_anneal_t<R, 1, 0>(m, st, sp, W, grid, s, configure_only)                   \
                         : enqueue_anneal_t<R, 1, 1>(m, st, sp, W, grid, s, configure_only);
   if (f64) { DISPATCH(double) } else { DISPATCH(float) }
@@ -1182,9 +1204,13 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_prepare(const sabr_lmm_market* mk, co
   if (o->lm_top_k < 0 || o->lm_top_k > o->n_chains || o->lm_top_k > 1024) return fail(SABR_LMM_EINVAL, "lm_top_k must be in [0, min(n_chains, 1024)]");
   if (o->lm_top_k > 0 && o->lm_max_iter < 0) return fail(SABR_LMM_EINVAL, "lm_max_iter must be >= 0");
   if (o->polish_nm != 0 && o->polish_nm != 1) return fail(SABR_LMM_EINVAL, "polish_nm must be 0 or 1");
-  for (const DevMarket& m : mk->dm)
+  for (const DevMarket& m : mk->dm) {
     if (o->lm_top_k > 0 && o->polish_nm && nm_smem(m) > 227u * 1024u)
       return fail(SABR_LMM_ENOTSUP, "a market and the Nelder-Mead simplex do not fit one CTA");
+    if (o->lm_top_k > 0 && !o->polish_nm && (m.n_param > kMaxGradParam || m.model == SABR_LMM_MODEL_MERCURIO_MORINI))
+      return fail(SABR_LMM_ENOTSUP, "the Levenberg-Marquardt polish covers the smile and Rebonato models, at most 12 "
+                                    "parameter slots (polish_nm = 1 runs Nelder-Mead instead)");
+  }
   for (size_t j = 0; o->x0 && j < mk->dm.size(); ++j)
     if (sabr_lmm_status st = check_x0(mk->hm[j], o->x0 + j * (size_t)mk->hm[j].n_param); st != SABR_LMM_OK) return st;
   for (const DevMarket& m : mk->dm) {
@@ -1618,7 +1644,7 @@ namespace {
 
 constexpr int kNoAllocMaxChains = 16384;
 constexpr int kNoAllocMaxLevels = 4096;
-constexpr int kNoAllocMaxParam = kMaxParam;
+constexpr int kNoAllocMaxParam = kMaxGradParam;
 constexpr int kNoAllocW = 4;  // warps (chains) per CTA: the 4-chain form of the caplet level kernel
 // level-minimum slots: one per CTA of the caplet kernel, one per chain for markets with swaptions
 constexpr int kNoAllocMaxParts = kNoAllocMaxChains;
@@ -1686,6 +1712,8 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, in
   if (sabr_lmm_status st = check_call(mk, market_idx, 0, o->prec); st != SABR_LMM_OK) return st;
   const DevMarket& m = mk->dm[market_idx];
   const HostMarket& h = mk->hm[market_idx];
+  if (m.n_param > kNoAllocMaxParam)
+    return fail(SABR_LMM_ENOTSUP, "anneal_noalloc takes markets of at most 12 parameter slots");
   if (o->x0)
     if (sabr_lmm_status st = check_x0(h, o->x0); st != SABR_LMM_OK) return st;
   const int P = m.n_param;
@@ -1730,3 +1758,5 @@ extern "C" sabr_lmm_status sabr_lmm_anneal_noalloc(const sabr_lmm_market* mk, in
   if (trace_f) CUDA_TRY(cudaMemcpyAsync(trace_f, st.trace_f, o->n_levels * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return SABR_LMM_OK;
 }
+
+#include "mc_api.cuh"

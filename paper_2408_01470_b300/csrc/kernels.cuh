@@ -37,8 +37,14 @@ __global__ void setup_forwards_kernel(DevMarket m) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m.n_fwd) {
     const double tau = m.T[i + 1] - m.T[i];
+    const double F = (m.P[i] / m.P[i + 1] - 1.0) / tau;
     m.tau[i] = tau;
-    m.F[i] = (m.P[i] / m.P[i + 1] - 1.0) / tau;
+    m.F[i] = F;
+    if (m.mm_k64) {   // Mercurio & Morini: the drift integral's constant of forward i
+      const double k = tau * pow(F, m.beta) * m.T[i] / (1.0 + tau * F);
+      ((double*)m.mm_k64)[i] = k;
+      ((float*)m.mm_k32)[i] = (float)k;
+    }
   }
 }
 
@@ -324,9 +330,10 @@ __device__ __forceinline__ bool stage_market(const CtaSmem<R>& cs, const DevMark
 }
 
 // Whether warp_objective prices the caplets with the packed FP32 pricer (and so reads the
-// pair-major block): FP32, the Hagan (2002) form, no model vols requested.
-template <class R, int FORMULA>
-__host__ __device__ constexpr bool packed_pricer() { return sizeof(R) == 4 && FORMULA == 0; }
+// pair-major block): FP32, the Hagan (2002) form, no model vols requested; not the Mercurio &
+// Morini model (a rho per forward: the scalar pricer).
+template <class R, int MODEL, int FORMULA>
+__host__ __device__ constexpr bool packed_pricer() { return sizeof(R) == 4 && FORMULA == 0 && MODEL != 2; }
 
 // ------------------------------------------------------------------ objective and vols
 // When a CTA's staging gave up (the error word is raised), its points' outputs are set to NaN
@@ -351,7 +358,7 @@ __global__ void objective_kernel(DevMarket m, const double* __restrict__ X, long
   const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   CtaSmem<R> cs = carve<R>(smem, m, W);
   const int n_instr = m.n_cap + m.n_swp;
-  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>() && vols == nullptr)) {
+  if (!stage_market<R>(cs, m, packed_pricer<R, MODEL, FORMULA>() && vols == nullptr)) {
     nan_outputs((long long)blockIdx.x * W + warp, (long long)gridDim.x * W, n, lane, 32, f, vols, n_instr, res, n_instr);
     return;
   }
@@ -439,7 +446,7 @@ __global__ void sa_start_kernel(DevMarket m, SAState st, SAParams sp) {
   CtaSmem<R> cs = carve<R>(smem, m, 1);
   // the start point in the chain-state precision (FP32 chains start from the rounded point)
   const double x0 = lane < sp.P ? (double)(R)sp.x0[lane] : 0.0;
-  if (!stage_market<R>(cs, m, packed_pricer<R, FORMULA>())) {
+  if (!stage_market<R>(cs, m, packed_pricer<R, MODEL, FORMULA>())) {
     sa_start_write(st, sp, lane, x0, __longlong_as_double(0x7ff0000000000000LL));
     return;
   }
@@ -511,7 +518,7 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
   // a CTA whose staging gave up (error word raised) runs no step: its chains end the level at the
   // start point with f = +inf, and it still takes its level ticket, so the level-end minimum over
   // the other CTAs completes
-  const bool staged = stage_market<R>(cs, m, packed_pricer<R, FORMULA>());
+  const bool staged = stage_market<R>(cs, m, packed_pricer<R, MODEL, FORMULA>());
   const InstrView<R> capB = instr_view<R>(cs.cap, m.n_cap_pad);
   WarpScratch<R> ws = warp_scratch<R>((R*)cs.scratch + (size_t)warp * warp_scratch_elems(m.NP, m.n_fwd), m.NP, m.n_fwd);
 
@@ -551,20 +558,25 @@ sa_level_kernel(DevMarket m, SAState st, SAParams sp, int level) {
     }
   }
   const unsigned long long cw = (unsigned long long)c | (sp.market_index << 32);
-  // Philox block (lane & 3) of step s0 + (lane >> 2), 8 steps at a time, parked in shared memory
+  // Philox block (lane & 3) of step s0 + (lane >> 2), 8 steps at a time, parked in shared memory;
+  // with 16 or more slots (Mercurio & Morini) block (lane & 7) of step s0 + (lane >> 3), 4 steps at
+  // a time (up to 32 words a step)
+  constexpr bool WIDE = MODEL == 2;
+  constexpr int BPS = WIDE ? 8 : 4, SPR = 32 / BPS;   // blocks per step, steps per refill
   uint64_t* rng = cs.rng + (size_t)warp * 128;
   for (int s = 0; s < sp.N; ++s) {
     if (active) {
       // S1: the step's uniforms; lane k needs word (k & 3) of block (k >> 2) of this step
-      if ((s & 7) == 0) {
-        const U4 o = philox4x64_10((uint64_t)(lane & 3), (uint64_t)(s + (lane >> 2)), (uint64_t)level, cw, sp.seed, 0ull);
+      if ((s & (SPR - 1)) == 0) {
+        const U4 o = philox4x64_10((uint64_t)(lane & (BPS - 1)), (uint64_t)(s + lane / BPS), (uint64_t)level, cw,
+                                   sp.seed, 0ull);
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < 4; ++j) rng[lane * 4 + j] = o.v[j];
         __syncwarp();
       }
-      const int row = (s & 7) << 2;
-      const uint64_t word = rng[(row | ((lane >> 2) & 3)) * 4 + (lane & 3)];
+      const int row = (s & (SPR - 1)) * BPS;
+      const uint64_t word = rng[(row | ((lane >> 2) & (BPS - 1))) * 4 + (lane & 3)];
       const uint64_t wacc = rng[(row | (P >> 2)) * 4 + (P & 3)];
       R y = x;
       if (lane < P && freek) y = neighbour(x, lo, hi, (R)sf, word);

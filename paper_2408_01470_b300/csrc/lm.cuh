@@ -15,7 +15,7 @@
 
 namespace sabr {
 
-constexpr int kLmStencil = 1 + kMaxParam;   // most points per stencil: theta and theta + h e_p
+constexpr int kLmStencil = 1 + kMaxGradParam;   // most points per stencil: theta and theta + h e_p
 
 __device__ __forceinline__ double lm_h(double x) { return 1e-7 * fmax(fabs(x), 1.0); }
 
@@ -65,10 +65,10 @@ __global__ void __launch_bounds__(256) lm_step_kernel(DevMarket m, int n, int S,
   const int i = blockIdx.x;
   if (i >= n) return;
   const int P = m.n_param, ni = m.n_cap + m.n_swp;
-  __shared__ int fi[kMaxParam];
+  __shared__ int fi[kMaxGradParam];
   __shared__ int nf_s;
-  __shared__ double A[kMaxParam * kMaxParam], g[kMaxParam], ih[kMaxParam], y[kMaxParam], id[kMaxParam];
-  __shared__ double D[kMaxParam + 1][kLmTile];   // row 0: r(theta); row 1 + a: (r(theta + h_a e_fa) - r(theta)) / h_a
+  __shared__ double A[kMaxGradParam * kMaxGradParam], g[kMaxGradParam], ih[kMaxGradParam], y[kMaxGradParam], id[kMaxGradParam];
+  __shared__ double D[kMaxGradParam + 1][kLmTile];   // row 0: r(theta); row 1 + a: (r(theta + h_a e_fa) - r(theta)) / h_a
   const double* x = X + (size_t)i * P;
   double* xt = Xt + (size_t)i * P;
   if ((int)threadIdx.x < P) xt[threadIdx.x] = x[threadIdx.x];   // no move unless a step is taken

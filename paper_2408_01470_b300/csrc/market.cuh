@@ -14,7 +14,8 @@
 namespace sabr {
 
 constexpr int kQ = 8;               // Gauss-Legendre nodes per panel
-constexpr int kMaxParam = 12;       // parameter slots
+constexpr int kMaxParam = 32;       // parameter slots (Mercurio & Morini: 2 n_fwd + 1 <= 31)
+constexpr int kMaxGradParam = 12;   // slots of the adjoint, Levenberg-Marquardt and no-alloc paths
 constexpr int kBlkArrays = 12;      // R values per instrument in a block (+ one int)
 constexpr int kSeg = 4;             // pairs per segment of a group's pair triangle (quadratic forms)
 
@@ -153,6 +154,9 @@ struct DevMarket {
   const QuadTab<double>* q64;
   const QuadTab<float>* q32;
   int* err;                        // device error word (nonzero: a bounded wait gave up)
+  // Mercurio & Morini markets: per forward k_i = tau_i F_i^b T_i / (1 + tau_i F_i) (null otherwise)
+  const double* mm_k64;
+  const float* mm_k32;
 };
 
 }  // namespace sabr

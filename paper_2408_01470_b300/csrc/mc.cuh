@@ -1,0 +1,268 @@
+// Monte Carlo pricer of the Hagan SABR/LIBOR model (Section 2.1, Eqs. dinamicasHagan1-2) under
+// the spot measure: the Monte Carlo pricing of caplets and swaptions of Section 3 (Table
+// tab:haganMCpricer).  One thread per path; the paths of a warp run in lockstep (every path has
+// the same time grid), so the per-instrument sums are warp reductions at the fixing dates.
+//
+// Per step of the interval [T_{k-1}, T_k] (h(t) = k, forwards k .. M-1 alive):
+//   xi    : 2a standard normals (a = M - k alive forwards), Philox4x32-10 at counter
+//           (b, step, path low word, path high word), key (seed low, seed high), uniforms
+//           (x + 1/2) 2^-32 (FP64) or (x >> 8 + 1/2) 2^-24 (FP32), Box-Muller on pairs;
+//   Z     : L xi with L the Cholesky factor of the (W, Z) correlation matrix ordered last forward
+//           first (u = M - 1 - i: row 2u is W_i, row 2u + 1 is Z_i), so the alive forwards are the
+//           leading 2a rows and need only the first 2a normals;
+//   x_i   = tau_i V_i F_i^b / (1 + tau_i F_i),
+//   F_i  <- max(F_i + V_i F_i^b (h sum_{j=k}^{i} rho_ij x_j + sqrt(h) Z_{W_i}), 0)   (Euler, absorbed at 0),
+//   ln V_i <- ln V_i + h (sigma_i sum_{j=k}^{i} phi_ij x_j - sigma_i^2 / 2) + sigma_i sqrt(h) Z_{Z_i};
+// at T_k forward k fixes: its caplets pay tau_k (F_k - K)^+ at T_{k+1}, deflated by
+// 1 / B(T_{k+1}) = P(0, T_0) / prod_{j <= k} (1 + tau_j F_j(T_j)); the swaptions expiring at T_k
+// pay A (S - K)^+ deflated by 1 / B(T_k), with the annuity and swap rate from the forwards at T_k.
+// A path whose F or ln V is not finite at a fixing date pays nothing from there on (counted).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sabr {
+
+constexpr int kMcMaxFwd = 16;            // forwards a pricer simulates
+constexpr int kMcRows = 2 * kMcMaxFwd;   // rows of the correlation factor
+constexpr int kMcThreads = 128;          // paths per CTA (4 warps)
+constexpr int kMcWarps = kMcThreads / 32;
+
+// Model constants, in u-order (u = M - 1 - i), one copy per precision.
+template <class R> struct McConsts {
+  R L[kMcRows * kMcRows];          // Cholesky factor, row-major
+  R rho[kMcMaxFwd * kMcMaxFwd];    // rho(u, v): correlation of W_(M-1-u) with W_(M-1-v)
+  R phi[kMcMaxFwd * kMcMaxFwd];    // phi(u, v): correlation of W_(M-1-u) with Z_(M-1-v)
+  R tau[kMcMaxFwd], sig[kMcMaxFwd], hs2[kMcMaxFwd], F0[kMcMaxFwd], lnV0[kMcMaxFwd];
+};
+
+struct McArgs {
+  int M;                         // forwards simulated (the largest forward any instrument needs + 1)
+  int n_cap, n_swp;
+  double beta, P0;               // P0 = P(0, T_0)
+  const int* nsteps;             // [M] steps of interval k
+  const double* h;               // [M] step length of interval k
+  // caplets sorted by forward, swaptions by expiry; per interval k the ranges [lo[k], lo[k+1])
+  const int* cap_lo;             // [M + 1]
+  const int* swp_lo;             // [M + 1]
+  const int* cap_out;            // [n_cap] output slot of sorted caplet c
+  const int* swp_out;            // [n_swp]
+  const double* cap_K;           // [n_cap] sorted
+  const double* swp_K;           // [n_swp] sorted
+  const int* swp_b;              // [n_swp] one past the swap's last forward (sorted)
+  const double* tau64;           // [M] accruals (FP64, for the payoffs)
+  unsigned long long seed;
+  long long n_paths;
+  double* part;                  // [grid x (n_cap + n_swp) x 2] per-CTA sums of payoff, payoff^2
+  unsigned long long* bad;       // [grid] stopped paths per CTA
+};
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t o[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0, hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
+}
+
+// Box-Muller on two 32-bit words.
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, double& z1) {
+  const double u0 = ((double)a + 0.5) * 0x1.0p-32, u1 = ((double)b + 0.5) * 0x1.0p-32;
+  const double r = sqrt(-2.0 * log(u0));
+  double s, c;
+  sincospi(2.0 * u1, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
+  const float u0 = ((float)(a >> 8) + 0.5f) * 0x1.0p-24f, u1 = ((float)(b >> 8) + 0.5f) * 0x1.0p-24f;
+  const float r = sqrtf(-2.0f * logf(u0));
+  float s, c;
+  sincospif(2.0f * u1, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+template <class R> __device__ __forceinline__ R mc_exp(R x);
+template <> __device__ __forceinline__ double mc_exp<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float mc_exp<float>(float x) { return __expf(x); }
+template <class R> __device__ __forceinline__ R mc_log(R x);
+template <> __device__ __forceinline__ double mc_log<double>(double x) { return log(x); }
+template <> __device__ __forceinline__ float mc_log<float>(float x) { return __logf(x); }
+template <class R> __device__ __forceinline__ R mc_rcp(R x);
+template <> __device__ __forceinline__ double mc_rcp<double>(double x) { return 1.0 / x; }
+template <> __device__ __forceinline__ float mc_rcp<float>(float x) { return __frcp_rn(x); }
+
+__device__ __forceinline__ double warp_sum_mc(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Dynamic shared memory of the path kernel: the per-warp sums.
+__host__ __device__ inline size_t mc_smem_bytes(int n_instr) { return (size_t)kMcWarps * n_instr * 2 * sizeof(double); }
+
+// The model constants travel as a kernel parameter (constant bank): after unrolling, every index
+// into them is a compile-time constant, so the FMAs of the correlation product and the drifts read
+// their coefficient straight from the constant bank, with no shared-memory load.
+template <class R>
+__global__ void __launch_bounds__(kMcThreads) mc_path_kernel(const __grid_constant__ McArgs a,
+                                                             const __grid_constant__ McConsts<R> C) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  double* acc = (double*)smem;   // [warps][n_instr][2]
+  const int n_instr = a.n_cap + a.n_swp;
+  for (int t = threadIdx.x; t < kMcWarps * n_instr * 2; t += blockDim.x) acc[t] = 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* wacc = acc + (size_t)warp * n_instr * 2;
+  const int M = a.M;
+  const R beta = (R)a.beta;
+  const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+  unsigned long long nbad = 0;
+  const long long stride = (long long)gridDim.x * kMcThreads;
+  for (long long base = (long long)blockIdx.x * kMcThreads + warp * 32; base < a.n_paths; base += stride) {
+    const long long p = base + lane;
+    const bool live = p < a.n_paths;
+    R F[kMcMaxFwd], lnV[kMcMaxFwd];
+#pragma unroll
+    for (int u = 0; u < kMcMaxFwd; ++u) { F[u] = C.F0[u]; lnV[u] = C.lnV0[u]; }
+    bool good = live;
+    double numer = a.P0;   // 1 / B(T_k) at the start of interval k
+    int step = 0;
+    for (int k = 0; k < M; ++k) {
+      const int na = M - k;   // alive forwards: u = 0 .. na - 1
+      const int ns = a.nsteps[k];
+      const R h = (R)a.h[k], sh = (R)sqrt(a.h[k]);
+      for (int s = 0; s < ns; ++s, ++step) {
+        R xi[kMcRows];
+#pragma unroll
+        for (int b = 0; b < kMcRows / 4; ++b) {
+          if (4 * b < 2 * na) {
+            uint32_t o[4];
+            philox4x32_10((uint32_t)b, (uint32_t)step, (uint32_t)p, (uint32_t)((unsigned long long)p >> 32), k0, k1, o);
+            box_muller(o[0], o[1], xi[4 * b], xi[4 * b + 1]);
+            box_muller(o[2], o[3], xi[4 * b + 2], xi[4 * b + 3]);
+          } else {
+            xi[4 * b] = xi[4 * b + 1] = xi[4 * b + 2] = xi[4 * b + 3] = R(0);
+          }
+        }
+        R x[kMcMaxFwd], vf[kMcMaxFwd], V[kMcMaxFwd];
+#pragma unroll
+        for (int u = 0; u < kMcMaxFwd; ++u) {
+          if (u < na) {
+            V[u] = mc_exp<R>(lnV[u]);
+            const R fb = F[u] > R(0) ? mc_exp<R>(beta * mc_log<R>(F[u])) : R(0);
+            vf[u] = V[u] * fb;
+            x[u] = C.tau[u] * vf[u] * mc_rcp<R>(R(1) + C.tau[u] * F[u]);
+          } else {
+            V[u] = vf[u] = x[u] = R(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kMcMaxFwd; ++u) {
+          if (u < na) {
+            // drifts: forwards j = k .. i, i.e. v = u .. na - 1
+            R dF = 0, dV = 0;
+#pragma unroll
+            for (int v = u; v < kMcMaxFwd; ++v)
+              if (v < na) {
+                dF += C.rho[u * kMcMaxFwd + v] * x[v];
+                dV += C.phi[u * kMcMaxFwd + v] * x[v];
+              }
+            R zw = 0, zz = 0;
+#pragma unroll
+            for (int c = 0; c <= 2 * u; ++c) zw += C.L[(2 * u) * kMcRows + c] * xi[c];
+#pragma unroll
+            for (int c = 0; c <= 2 * u + 1; ++c) zz += C.L[(2 * u + 1) * kMcRows + c] * xi[c];
+            const R fn = F[u] + vf[u] * (h * dF + sh * zw);
+            F[u] = fn > R(0) ? fn : R(0);
+            lnV[u] += h * (C.sig[u] * dV - C.hs2[u]) + C.sig[u] * sh * zz;
+          }
+        }
+      }
+      // T_k: forward k (u = na - 1) fixes
+      bool fin = true;
+      R Fs[kMcMaxFwd];
+#pragma unroll
+      for (int u = 0; u < kMcMaxFwd; ++u) {
+        Fs[u] = F[u];
+        if (u < na) fin = fin && isfinite(F[u]) && isfinite(lnV[u]);
+      }
+      if (good && !fin) ++nbad;
+      good = good && fin;
+      const double fix = (double)Fs[na - 1];
+      // swaptions expiring at T_k, deflated by 1 / B(T_k)
+      for (int c = a.swp_lo[k]; c < a.swp_lo[k + 1]; ++c) {
+        double pay = 0.0;
+        if (good) {
+          const int b = a.swp_b[c];
+          double disc = 1.0, A = 0.0;
+          for (int j = k; j < b; ++j) {
+            disc /= 1.0 + a.tau64[j] * (double)Fs[M - 1 - j];
+            A += a.tau64[j] * disc;
+          }
+          const double S = (1.0 - disc) / A;
+          pay = A * fmax(S - a.swp_K[c], 0.0) * numer;
+        }
+        const double s1 = warp_sum_mc(pay), s2 = warp_sum_mc(pay * pay);
+        if (lane == 0) { wacc[2 * (a.n_cap + c)] += s1; wacc[2 * (a.n_cap + c) + 1] += s2; }
+      }
+      numer = good ? numer / (1.0 + a.tau64[k] * fix) : 0.0;
+      // caplets on forward k, paid at T_{k+1}
+      for (int c = a.cap_lo[k]; c < a.cap_lo[k + 1]; ++c) {
+        const double pay = good ? a.tau64[k] * fmax(fix - a.cap_K[c], 0.0) * numer : 0.0;
+        const double s1 = warp_sum_mc(pay), s2 = warp_sum_mc(pay * pay);
+        if (lane == 0) { wacc[2 * c] += s1; wacc[2 * c + 1] += s2; }
+      }
+    }
+  }
+  __syncthreads();
+  // the CTA's sums, warp by warp in order
+  double* out = a.part + (size_t)blockIdx.x * n_instr * 2;
+  for (int t = threadIdx.x; t < n_instr * 2; t += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < kMcWarps; ++w) v += acc[(size_t)w * n_instr * 2 + t];
+    out[t] = v;
+  }
+  __shared__ unsigned long long sbad[kMcWarps];
+  nbad = (unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)nbad);
+  if (lane == 0) sbad[warp] = nbad;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kMcWarps; ++w) t += sbad[w];
+    a.bad[blockIdx.x] = t;
+  }
+}
+
+// Prices and standard errors from the per-CTA sums, CTA by CTA in order; out slot by the
+// instruments' original order.  One thread per instrument.
+__global__ void mc_reduce_kernel(McArgs a, int grid, double* price, double* stderr_out, long long* n_bad) {
+  const int n_instr = a.n_cap + a.n_swp;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_instr) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int g = 0; g < grid; ++g) {
+      s1 += a.part[((size_t)g * n_instr + t) * 2];
+      s2 += a.part[((size_t)g * n_instr + t) * 2 + 1];
+    }
+    const double n = (double)a.n_paths;
+    const double m = s1 / n;
+    const double var = fmax(s2 / n - m * m, 0.0);
+    const int o = t < a.n_cap ? a.cap_out[t] : a.n_cap + a.swp_out[t - a.n_cap];
+    price[o] = m;
+    if (stderr_out) stderr_out[o] = n > 1.0 ? sqrt(var / (n - 1.0)) : 0.0;
+  }
+  if (t == 0 && n_bad) {
+    long long b = 0;
+    for (int g = 0; g < grid; ++g) b += (long long)a.bad[g];
+    *n_bad = b;
+  }
+}
+
+}  // namespace sabr

@@ -46,7 +46,7 @@ template <class R> struct Q2 { R a, b; };
 // Per-forward SABR factors consumed by the pricer:
 //   F4 = {alpha, nu / alpha, alpha^2, rho nu alpha},  fA3 = (2 - 3 rho^2) nu^2.
 template <class R> struct WarpScratch {
-  R* xs;        // [16] parameter point in the pricing precision
+  R* xs;        // [kMaxParam] parameter point in the pricing precision
   R* Gp;        // [NPc] per-panel integrals
   R* Hp;
   R* Ap;
@@ -63,7 +63,7 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 // 4 elements (the alignment of Q4<R>).
 __host__ __device__ inline int warp_scratch_elems(int NP, int n_fwd) {
   const int NPc = round_up(NP > 0 ? NP : 1, 4), NFc = round_up(n_fwd, 4);
-  return 16 + 3 * NPc + 4 * NFc + NFc + 2 * NPc + 4 * 8 + 4 * 16;
+  return kMaxParam + 3 * NPc + 4 * NFc + NFc + 2 * NPc + 4 * 8 + 4 * 16;
 }
 
 template <class R>
@@ -71,7 +71,7 @@ __device__ __forceinline__ WarpScratch<R> warp_scratch(R* base, int NP, int n_fw
   WarpScratch<R> s;
   const int NPc = round_up(NP > 0 ? NP : 1, 4), NFc = round_up(n_fwd, 4);
   s.xs = base;
-  s.Gp = base + 16;
+  s.Gp = base + kMaxParam;
   s.Hp = s.Gp + NPc;
   s.Ap = s.Hp + NPc;
   s.F4 = (Q4<R>*)(s.Ap + NPc);
@@ -92,6 +92,45 @@ __device__ __forceinline__ void put_forward(const WarpScratch<R>& ws, int i, R a
   v.d = rho * nu * al;
   ws.F4[i] = v;
   ws.fA3[i] = (R(2) - R(3) * rho * rho) * nu * nu;
+}
+
+template <class R> __device__ __forceinline__ const R* mm_k(const DevMarket& m);
+template <> __device__ __forceinline__ const double* mm_k<double>(const DevMarket& m) { return m.mm_k64; }
+template <> __device__ __forceinline__ const float* mm_k<float>(const DevMarket& m) { return m.mm_k32; }
+template <class R> __device__ __forceinline__ R exp_mm(R x);
+template <> __device__ __forceinline__ double exp_mm<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float exp_mm<float>(float x) { return exp_approx(x); }
+
+// S2 for the Mercurio & Morini model (Eq. haganForMercurio): forward i's SABR alpha is
+// alpha_i exp(-sigma S_i) with S_i = sum_{j <= i} k_j phi_j alpha_j, where the market constant
+// k_j = tau_j F_j^b T_j / (1 + tau_j F_j) carries the drift integral's interval lengths (the
+// piecewise-constant M_i integrates to -sigma sum_{j <= i} c_j T_j).  Lane i holds forward i
+// (n_fwd <= 15): one warp scan.  Slots [phi_0..phi_{M-1}, sigma, alpha_0..alpha_{M-1}].  The
+// forward's rho phi_i sits in fA3 (the pricer forms (2 - 3 rho^2) nu^2 itself for this model).
+template <class R>
+__device__ __forceinline__ void mm_forward_params(const DevMarket& m, const WarpScratch<R>& ws, int lane) {
+  const int M = m.n_fwd;
+  const bool in = lane < M;
+  const R phi = in ? ws.xs[lane] : R(0), al = in ? ws.xs[M + 1 + lane] : R(0);
+  const R kj = in ? mm_k<R>(m)[lane] : R(0);
+  R c = kj * phi * al;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const R o = __shfl_up_sync(0xffffffffu, c, off);
+    if (lane >= off) c += o;
+  }
+  const R sig = ws.xs[M];
+  if (in) {
+    const R aS = al * exp_mm<R>(-sig * c);
+    Q4<R> v;
+    v.a = aS;
+    v.b = fdiv<R>(sig, aS);
+    v.c = aS * aS;
+    v.d = phi * sig * aS;
+    ws.F4[lane] = v;
+    ws.fA3[lane] = phi;
+  }
+  __syncwarp();
 }
 
 // Inclusive prefix scans over the panel integrals, in place (Gp -> SG, Ap -> SA, Hp -> SH, and
@@ -387,7 +426,8 @@ __device__ __forceinline__ R z_over_x_fast(R z, const RhoConsts<R>& rc) {
 // residuals in the pricing precision and clears `ok` on an infeasible vol.  With vols != null
 // the model vols are written instead (NaN where infeasible); with res != null the weighted
 // residuals sqrt(w_k) (P_k - P_k^mkt) are written as well (NaN where infeasible).
-template <class R, int FORMULA>
+// PFR: rho per forward (Mercurio & Morini: phi_i in fA3) instead of the chain's rho.
+template <class R, int FORMULA, bool PFR = false>
 __device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const WarpScratch<R>& ws, const RhoConsts<R>& rc,
                                            R omb, int lane, bool& ok, double* vols, double* res = nullptr) {
   typedef Num<R> M;
@@ -400,11 +440,21 @@ __device__ __forceinline__ R price_caplets(const InstrView<R>& B, int n, const W
     R sig;
     if (FORMULA == 0) {
       const R z = fw.b * g0.b;
-      const R zx = z_over_x_fast<R>(z, rc);
-      const R corr = R(1) + g0.d * fw.c + g1.a * fw.d + g1.b * ws.fA3[i];
+      R zx, a3;
+      if (PFR) {
+        RhoConsts<R> ri;
+        const R rho = ws.fA3[i], nu = fw.b * fw.a;
+        ri.init(rho);
+        zx = z_over_x_fast<R>(z, ri);
+        a3 = (R(2) - R(3) * rho * rho) * nu * nu;
+      } else {
+        zx = z_over_x_fast<R>(z, rc);
+        a3 = ws.fA3[i];
+      }
+      const R corr = R(1) + g0.d * fw.c + g1.a * fw.d + g1.b * a3;
       sig = fw.a * g0.c * zx * corr;
     } else {
-      sig = sabr_paper<R>(fw.a, rc.rho, fw.b * fw.a, g0.a, g0.b, omb);
+      sig = sabr_paper<R>(fw.a, PFR ? ws.fA3[i] : rc.rho, fw.b * fw.a, g0.a, g0.b, omb);
     }
     const bool good = (sig > R(0)) && M::finite_(sig);
     if (vols) { vols[k] = good ? (double)sig : __longlong_as_double(0x7ff8000000000000LL); continue; }
@@ -605,7 +655,8 @@ __device__ __forceinline__ void obj_from_double(double v, FF& o) {
 }
 
 // Objective of the point held in ws.xs (all 32 lanes call; all return the same value).
-// MODEL 0: SABR smile [alpha, rho, nu];  MODEL 1: Rebonato caplets.
+// MODEL 0: SABR smile [alpha, rho, nu];  MODEL 1: Rebonato caplets;  MODEL 2: Mercurio & Morini
+// caplets (scalar pricer with a rho per forward).
 // vols != null: the model vols are written instead.  res != null: the weighted residuals are
 // written as well, by the pricer the search uses (the packed one in FP32 with the Hagan form).
 template <class R, int MODEL, int FORMULA>
@@ -619,13 +670,18 @@ __device__ typename ObjOf<R>::T warp_objective(const DevMarket& m, const InstrVi
     for (int j = lane; j < m.n_capfwd; j += 32) put_forward<R>(ws, m.capfwd_list[j], al, nu, rho);
     __syncwarp();
     rc.init(rho);
+  } else if (MODEL == 2) {
+    mm_forward_params<R>(m, ws, lane);
+    rc.init(R(0));
   } else {
     forward_params<R>(m, qt, ws, lane);
     rc.init(ws.xs[8]);
   }
   bool ok = true;
   R part;
-  if constexpr (std::is_same<R, float>::value && FORMULA == 0) {
+  if constexpr (MODEL == 2) {
+    part = price_caplets<R, FORMULA, true>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols, res);
+  } else if constexpr (std::is_same<R, float>::value && FORMULA == 0) {
     // (with no vols requested the caller staged the pair-major block; its base is capB.g0)
     if (vols != nullptr)
       part = price_caplets<R, FORMULA>(capB, m.n_cap, ws, rc, (R)(1.0 - m.beta), lane, ok, vols);

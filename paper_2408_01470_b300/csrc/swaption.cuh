@@ -28,7 +28,7 @@
 namespace sabr {
 
 template <class R> struct CtaScratch {
-  R* xs;            // [16]
+  R* xs;            // [kMaxParam]
   WarpScratch<R> cap;  // caplet mapping (warp 0); its xs is a private copy
   Q2<R>* Ep;        // [NAc] {e^{-c A D}, e^{-gamma_h A D}}
   Q4<R>* Tq;        // [8]
@@ -81,7 +81,7 @@ template <class R> struct PairTables {
 template <class R>
 __host__ __device__ inline int cta_scratch_elems(const DevMarket& m) {
   const int NAc = round_up(m.NA, 4);
-  return round_up(16 + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + 4 * 16 + round_up(m.NA * cta_y_stride(), 4) +
+  return round_up(kMaxParam + warp_scratch_elems(m.NP, m.n_fwd) + 2 * NAc + 32 + 4 * 72 + 4 * 16 + round_up(m.NA * cta_y_stride(), 4) +
                       round_up(cta_pq_tables<R>() * m.ND * cta_pq_len(m.NA), 4) + 4 * m.ND + 4 * m.n_swap +
                       round_up(m.n_swap, 4) + 4 * m.n_swap + (m.qf_own ? round_up(3 * m.n_seg, 4) : 0),
                   4);
@@ -92,7 +92,7 @@ __device__ __forceinline__ CtaScratch<R> cta_scratch(R* base, const DevMarket& m
   CtaScratch<R> s;
   const int NAc = round_up(m.NA, 4);
   R* p = base;
-  s.xs = p; p += 16;
+  s.xs = p; p += kMaxParam;
   s.cap = warp_scratch<R>(p, m.NP, m.n_fwd); p += warp_scratch_elems(m.NP, m.n_fwd);
   s.Ep = (Q2<R>*)p; p += 2 * NAc;
   s.Tq = (Q4<R>*)p; p += 32;
