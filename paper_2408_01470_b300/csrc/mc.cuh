@@ -79,13 +79,21 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, d
   z0 = r * c;
   z1 = r * s;
 }
+// FP32: ln u0 from the MUFU log2 below u0 = 3/4 (relative error ~1e-7 there) and above it, where
+// ln u0 is small and the MUFU form's absolute error would dominate, from the atanh series
+// ln u = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9), s = (u - 1) / (u + 1), |s| < 1/7 (truncation
+// below 1e-9 of ln u); (cos, sin)(2 pi u1) = -(cos, sin)(2 pi (u1 - 1/2)) on the MUFU with the
+// argument in (-pi, pi).
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
   const float u0 = ((float)(a >> 8) + 0.5f) * 0x1.0p-24f, u1 = ((float)(b >> 8) + 0.5f) * 0x1.0p-24f;
-  const float r = sqrtf(-2.0f * logf(u0));
+  const float sa = __fdividef(u0 - 1.0f, u0 + 1.0f), s2 = sa * sa;
+  const float ser = 2.0f * sa * fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f), 0.2f), 1.0f / 3.0f), 1.0f);
+  const float lu = u0 > 0.75f ? ser : __logf(u0);
+  const float r = sqrtf(-2.0f * lu);
   float s, c;
-  sincospif(2.0f * u1, &s, &c);
-  z0 = r * c;
-  z1 = r * s;
+  __sincosf(6.28318530717958647692f * (u1 - 0.5f), &s, &c);
+  z0 = -r * c;
+  z1 = -r * s;
 }
 
 template <class R> __device__ __forceinline__ R mc_exp(R x);
@@ -111,7 +119,7 @@ __host__ __device__ inline size_t mc_smem_bytes(int n_instr) { return (size_t)kM
 // into them is a compile-time constant, so the FMAs of the correlation product and the drifts read
 // their coefficient straight from the constant bank, with no shared-memory load.
 template <class R>
-__global__ void __launch_bounds__(kMcThreads) mc_path_kernel(const __grid_constant__ McArgs a,
+__global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_kernel(const __grid_constant__ McArgs a,
                                                              const __grid_constant__ McConsts<R> C) {
   extern __shared__ __align__(128) unsigned char smem[];
   double* acc = (double*)smem;   // [warps][n_instr][2]
@@ -167,18 +175,32 @@ __global__ void __launch_bounds__(kMcThreads) mc_path_kernel(const __grid_consta
         for (int u = 0; u < kMcMaxFwd; ++u) {
           if (u < na) {
             // drifts: forwards j = k .. i, i.e. v = u .. na - 1
-            R dF = 0, dV = 0;
+            // (two partial sums per dot product: half the length of each dependent FMA chain)
+            R dF0 = 0, dV0 = 0, dF1 = 0, dV1 = 0;
 #pragma unroll
             for (int v = u; v < kMcMaxFwd; ++v)
               if (v < na) {
-                dF += C.rho[u * kMcMaxFwd + v] * x[v];
-                dV += C.phi[u * kMcMaxFwd + v] * x[v];
+                if ((v - u) & 1) {
+                  dF1 += C.rho[u * kMcMaxFwd + v] * x[v];
+                  dV1 += C.phi[u * kMcMaxFwd + v] * x[v];
+                } else {
+                  dF0 += C.rho[u * kMcMaxFwd + v] * x[v];
+                  dV0 += C.phi[u * kMcMaxFwd + v] * x[v];
+                }
               }
-            R zw = 0, zz = 0;
+            const R dF = dF0 + dF1, dV = dV0 + dV1;
+            R zw0 = 0, zw1 = 0, zz0 = 0, zz1 = 0;
 #pragma unroll
-            for (int c = 0; c <= 2 * u; ++c) zw += C.L[(2 * u) * kMcRows + c] * xi[c];
+            for (int c = 0; c <= 2 * u; ++c) {
+              if (c & 1) zw1 += C.L[(2 * u) * kMcRows + c] * xi[c];
+              else zw0 += C.L[(2 * u) * kMcRows + c] * xi[c];
+            }
 #pragma unroll
-            for (int c = 0; c <= 2 * u + 1; ++c) zz += C.L[(2 * u + 1) * kMcRows + c] * xi[c];
+            for (int c = 0; c <= 2 * u + 1; ++c) {
+              if (c & 1) zz1 += C.L[(2 * u + 1) * kMcRows + c] * xi[c];
+              else zz0 += C.L[(2 * u + 1) * kMcRows + c] * xi[c];
+            }
+            const R zw = zw0 + zw1, zz = zz0 + zz1;
             const R fn = F[u] + vf[u] * (h * dF + sh * zw);
             F[u] = fn > R(0) ? fn : R(0);
             lnV[u] += h * (C.sig[u] * dV - C.hs2[u]) + C.sig[u] * sh * zz;

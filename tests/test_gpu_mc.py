@@ -65,7 +65,7 @@ def test_mc_fp32_against_the_oracle(gpu_lib):
     # FP32 paths: the uniforms keep 24 of their 32 bits (normals differ by ~1e-7), every state
     # update rounds to 6e-8 of the state, ~700 steps: the forwards at their fixings carry ~1e-6 of
     # themselves, a price ~1e-6 / (moneyness distance) of itself, and the means over paths average
-    # these errors (measured 7.6e-7 relative at most); bar 1e-5 relative on every price above 1e-3
+    # these errors (measured 2.7e-6 relative at most); bar 1e-5 relative on every price above 1e-3
     # of the largest, 1e-7 absolute below
     import paper_2408_01470_b300 as lib
     sk = _paper()[0]
