@@ -101,6 +101,12 @@ def _lib_handle():
             lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
             lib.orc_mc_normals4.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int, _D]
             _I = C.POINTER(C.c_int32)
+            _MCI = [C.c_void_p, C.c_int, _D, _D, _D, _D, C.c_int, _I, _D, C.c_int, _I, _I, _D, _D, C.c_int64,
+                    C.c_double, C.c_uint64]
+            lib.orc_mc_objective.restype = C.c_double
+            lib.orc_mc_objective.argtypes = _MCI + [_D, C.c_int]
+            lib.orc_mc_anneal.restype = C.c_int
+            lib.orc_mc_anneal.argtypes = _MCI + [_D, _D, C.POINTER(C.c_uint8), C.POINTER(_SAOpts), _D, _D, _D, _D, _D]
             lib.orc_mc_price.restype = C.c_int
             lib.orc_mc_price.argtypes = [C.c_void_p, C.c_int, _D, _D, _D, _D, C.c_int, _I, _D, C.c_int, _I, _I,
                                          _D, C.c_int64, C.c_double, C.c_uint64, C.c_int, _D, _D,
@@ -370,6 +376,49 @@ def mc_price(market, model, cap_fwd=(), cap_K=(), swp_a=(), swp_b=(), swp_K=(), 
     price, sq = price[:ni], sq[:ni]
     se = np.sqrt(np.maximum(sq - price * price, 0.0) / max(int(n_paths) - 1, 1))
     return price, se, nb.value
+
+
+def _mc_args(market, model, cap_fwd, cap_K, swp_a, swp_b, swp_K, quote_vol):
+    M = int(model["M"])
+    keep = dict(par=_f64([model["beta"], model.get("eta1", 0.0), model.get("lambda1", 0.0), model.get("eta2", 0.0),
+                          model.get("lambda2", 0.0), model.get("lambda3", 0.0)]),
+                al=_f64(model["alpha"])[:M], sg=_f64(model["sigma"])[:M], ph=_f64(model["phi"])[:M],
+                cf=np.ascontiguousarray(cap_fwd, np.int32), ck=_f64(cap_K), sa=np.ascontiguousarray(swp_a, np.int32),
+                sb=np.ascontiguousarray(swp_b, np.int32), sk=_f64(swp_K), qv=_f64(quote_vol))
+    _I = C.POINTER(C.c_int32)
+    args = [market.h, M, _dp(keep["par"]), _dp(keep["al"]), _dp(keep["sg"]), _dp(keep["ph"]), len(keep["cf"]),
+            keep["cf"].ctypes.data_as(_I), _dp(keep["ck"]), len(keep["sa"]), keep["sa"].ctypes.data_as(_I),
+            keep["sb"].ctypes.data_as(_I), _dp(keep["sk"]), _dp(keep["qv"])]
+    return args, keep
+
+
+def mc_objective(market, model, y, quote_vol, cap_fwd=(), cap_K=(), swp_a=(), swp_b=(), swp_K=(), n_paths=1000,
+                 dt=0.01, mc_seed=1, n_threads=1):
+    """f_s(y) = sum_k (P_k^Black - P_k^MC(y))^2 at the correlation parameters y = (eta1, lambda1,
+    eta2, lambda2, lambda3) (see sabr_oracle.cpp mc_objective)."""
+    args, keep = _mc_args(market, model, cap_fwd, cap_K, swp_a, swp_b, swp_K, quote_vol)
+    yy = _f64(y)
+    return market._lib.orc_mc_objective(*args, int(n_paths), float(dt), int(mc_seed), _dp(yy), int(n_threads))
+
+
+def mc_anneal(market, model, quote_vol, lo, hi, free, n_chains, n_levels, steps, cooling, seed, cap_fwd=(), cap_K=(),
+              swp_a=(), swp_b=(), swp_K=(), n_paths=1000, dt=0.01, mc_seed=1, T0=0.0, step_frac=0.1, step_floor=1e-3,
+              y0=None, n_threads=1):
+    """The annealing search of f_s over the correlation box (see sabr_oracle.cpp orc_mc_anneal)."""
+    args, keep = _mc_args(market, model, cap_fwd, cap_K, swp_a, swp_b, swp_K, quote_vol)
+    lo, hi = _f64(lo), _f64(hi)
+    fr = np.ascontiguousarray(free, np.uint8)
+    o = _SAOpts()
+    o.n_chains, o.n_levels, o.steps = int(n_chains), int(n_levels), int(steps)
+    o.T0, o.cooling, o.step_frac, o.step_floor = float(T0), float(cooling), float(step_frac), float(step_floor)
+    o.seed, o.market_index, o.n_threads = int(seed), 0, int(n_threads)
+    y0a = None if y0 is None else _f64(y0)
+    o.x0 = _dp(y0a)
+    yb, fb, tr, tx, t0 = np.zeros(5), np.zeros(1), np.zeros(n_levels), np.zeros((n_levels, 5)), np.zeros(1)
+    market._lib.orc_mc_anneal(*args, int(n_paths), float(dt), int(mc_seed), _dp(lo), _dp(hi),
+                              fr.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(o), _dp(yb), _dp(fb), _dp(tr), _dp(tx),
+                              _dp(t0))
+    return dict(y_best=yb, f_best=fb[0], trace_f=tr, trace_x=tx, T0=t0[0])
 
 
 def quoted_market(skel, noise=True):

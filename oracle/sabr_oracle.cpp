@@ -55,6 +55,11 @@
 //                                    and a zero-strike swaption P(0,T_a) - P(0,T_b) under any
 //                                    arbitrage-free dynamics; with sigma = 0, beta = 1 every caplet
 //                                    is Black's at vol alpha_i (the lognormal LIBOR market model).
+//   mc_objective, orc_mc_anneal .... the swaption calibration of Section 3 over the Monte Carlo
+//                                    objective (common random numbers), by the same annealing
+//                                    loop.  Pins: f_s = 0 at the generating correlation parameters
+//                                    on quotes made by the pricer itself; the search gets back to
+//                                    them from the box centre.
 //   anneal ......................... the SA loop of Section 3 and its one-GPU parallel form
 //                                    (chains per level, min-reduction, broadcast).  Pins: the
 //                                    evaluation-count identity C(LN+1); recovery on tiny sets.
@@ -874,14 +879,22 @@ struct SAOpts {  // mirrors oracle/__init__.py
 
 // Neighbour (reading; the paper leaves ComputeNeighbour open): every free slot moves by
 // sf (hi - lo) (2u - 1), is reflected once at the bound it crossed and then clamped.
-static void neighbour(const Market& m, const double* x, const double* u, double sf, double* y) {
-  for (int k = 0; k < m.n_param; ++k) {
-    if (!m.freem[k]) { y[k] = x[k]; continue; }
-    double v = x[k] + sf * (m.hi[k] - m.lo[k]) * (2.0 * u[k] - 1.0);
-    if (v < m.lo[k]) v = 2.0 * m.lo[k] - v;
-    if (v > m.hi[k]) v = 2.0 * m.hi[k] - v;
-    if (v < m.lo[k]) v = m.lo[k];
-    if (v > m.hi[k]) v = m.hi[k];
+// The search box of an annealing run: P slots, bounds and the slots that move.
+struct Box {
+  int P;
+  const double* lo;
+  const double* hi;
+  const uint8_t* freem;
+};
+
+static void neighbour(const Box& bx, const double* x, const double* u, double sf, double* y) {
+  for (int k = 0; k < bx.P; ++k) {
+    if (!bx.freem[k]) { y[k] = x[k]; continue; }
+    double v = x[k] + sf * (bx.hi[k] - bx.lo[k]) * (2.0 * u[k] - 1.0);
+    if (v < bx.lo[k]) v = 2.0 * bx.lo[k] - v;
+    if (v > bx.hi[k]) v = 2.0 * bx.hi[k] - v;
+    if (v < bx.lo[k]) v = bx.lo[k];
+    if (v > bx.hi[k]) v = bx.hi[k];
     y[k] = v;
   }
 }
@@ -892,13 +905,16 @@ static void neighbour(const Market& m, const double* x, const double* u, double 
 // Readings: T0 <= 0 means T0 = f(x0); the step fraction of level l is
 // max(step_frac sqrt(T_l / T0), step_floor); every chain evaluates f(x0) once, so the count of
 // objective evaluations is C (L N + 1); the best point ever accepted is kept apart and returned.
-static int anneal(const Market& m, const SAOpts& o, double* x_best, double* f_best,
-                  double* chain_xb, double* chain_fb, double* trace_f, double* trace_x,
-                  uint8_t* bits, int64_t* n_evals, double* T0_used) {
-  const int P = m.n_param, C = o.n_chains, L = o.n_levels, N = o.steps;
+// (The loop is written once for any objective f over a box: the calibration objective of a
+// market, or the Monte Carlo objective of mc_anneal.)
+template <class Obj>
+static int anneal_box(const Box& bx, Obj objective_of, const SAOpts& o, double* x_best, double* f_best,
+                      double* chain_xb, double* chain_fb, double* trace_f, double* trace_x,
+                      uint8_t* bits, int64_t* n_evals, double* T0_used) {
+  const int P = bx.P, C = o.n_chains, L = o.n_levels, N = o.steps;
   std::vector<double> x0(P);
-  for (int k = 0; k < P; ++k) x0[k] = o.x0 ? o.x0[k] : 0.5 * (m.lo[k] + m.hi[k]);
-  double f0 = objective(m, x0.data());
+  for (int k = 0; k < P; ++k) x0[k] = o.x0 ? o.x0[k] : 0.5 * (bx.lo[k] + bx.hi[k]);
+  double f0 = objective_of(x0.data());
   double T0 = o.T0 > 0.0 ? o.T0 : ((std::isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
   std::vector<double> xs = x0, xb((size_t)C * P), fb(C, f0), xe((size_t)C * P), fe(C);
   for (int c = 0; c < C; ++c) std::copy(x0.begin(), x0.end(), xb.begin() + (size_t)c * P);
@@ -913,8 +929,8 @@ static int anneal(const Market& m, const SAOpts& o, double* x_best, double* f_be
       uint64_t cw = (uint64_t)c | (o.market_index << 32);
       for (int s = 0; s < N; ++s) {
         step_uniforms(o.seed, cw, l, s, P + 1, u.data());
-        neighbour(m, x.data(), u.data(), sf, y.data());
-        double fy = objective(m, y.data());
+        neighbour(bx, x.data(), u.data(), sf, y.data());
+        double fy = objective_of(y.data());
         if (!(fy == fy)) fy = std::numeric_limits<double>::infinity();
         bool acc = (fy < f) || (u[P] < std::exp(-(fy - f) / T));
         if (bits) bits[((size_t)c * L + l) * N + s] = acc ? 1 : 0;
@@ -943,6 +959,64 @@ static int anneal(const Market& m, const SAOpts& o, double* x_best, double* f_be
   if (n_evals) *n_evals = (int64_t)C * ((int64_t)L * N + 1);
   if (T0_used) *T0_used = T0;
   return 0;
+}
+
+static int anneal(const Market& m, const SAOpts& o, double* x_best, double* f_best,
+                  double* chain_xb, double* chain_fb, double* trace_f, double* trace_x,
+                  uint8_t* bits, int64_t* n_evals, double* T0_used) {
+  const Box bx{m.n_param, m.lo.data(), m.hi.data(), m.freem.data()};
+  return anneal_box(bx, [&](const double* y) { return objective(m, y); }, o, x_best, f_best, chain_xb, chain_fb,
+                    trace_f, trace_x, bits, n_evals, T0_used);
+}
+
+// ------------------------------------------------------------------ SA over the Monte Carlo objective
+// The swaption calibration of Section 3: the correlation parameters y = (eta1, lambda1, eta2,
+// lambda2, lambda3) minimise f_s(y) = sum_k (P_k^Black - P_k^MC(y))^2 over the instruments, with the
+// caplet-calibrated alpha_i, sigma_i, phi_ii fixed.  Every evaluation prices with the same paths
+// (one Monte Carlo seed: common random numbers, so f_s is a deterministic function of y), and the
+// annealing loop above searches the box.  The market prices: Black's formula at the quoted vols
+// (payer swaption: annuity A = sum_{k in [a, b)} tau_k P(0, T_{k+1}), swap rate (P(0, T_a) - P(0, T_b)) / A,
+// expiry T_a; caplet: discount tau_i P(0, T_{i+1}), forward F_i(0), expiry T_i).  A y whose Monte
+// Carlo cannot run (a non-finite price) has f_s = +inf.
+struct McTarget {
+  int n_cap, n_swp;
+  const int *cap_fwd, *swp_a, *swp_b;
+  const double *cap_K, *swp_K;
+  std::vector<double> price;   // market prices, caplets then swaptions
+};
+
+static McTarget mc_target(const Market& m, int n_cap, const int* cap_fwd, const double* cap_K, int n_swp,
+                          const int* swp_a, const int* swp_b, const double* swp_K, const double* quote_vol) {
+  McTarget t{n_cap, n_swp, cap_fwd, swp_a, swp_b, cap_K, swp_K, {}};
+  for (int c = 0; c < n_cap; ++c) {
+    const int i = cap_fwd[c];
+    t.price.push_back(black_call(m.F[i], cap_K[c], m.T[i], quote_vol[c], m.tau[i] * m.P[i + 1]));
+  }
+  for (int c = 0; c < n_swp; ++c) {
+    const int a = swp_a[c], b = swp_b[c];
+    double A = 0.0;
+    for (int k = a; k < b; ++k) A += m.tau[k] * m.P[k + 1];
+    const double S = (m.P[a] - m.P[b]) / A;
+    t.price.push_back(black_call(S, swp_K[c], m.T[a], quote_vol[n_cap + c], A));
+  }
+  return t;
+}
+
+static double mc_objective(const Market& m, McModel md, const McTarget& t, const double* y, int64_t n_paths,
+                           double dt, uint64_t mc_seed, int n_threads) {
+  md.eta1 = y[0]; md.lambda1 = y[1]; md.eta2 = y[2]; md.lambda2 = y[3]; md.lambda3 = y[4];
+  const int ni = t.n_cap + t.n_swp;
+  std::vector<double> price(ni), sq(ni);
+  int64_t bad = 0;
+  if (mc_price(m, md, t.n_cap, t.cap_fwd, t.cap_K, t.n_swp, t.swp_a, t.swp_b, t.swp_K, n_paths, dt, mc_seed,
+               n_threads, price.data(), sq.data(), &bad) != 0)
+    return std::numeric_limits<double>::infinity();
+  double f = 0.0;
+  for (int k = 0; k < ni; ++k) {
+    const double e = price[k] - t.price[k];
+    f += e * e;
+  }
+  return std::isfinite(f) ? f : std::numeric_limits<double>::infinity();
 }
 
 // ------------------------------------------------------------------ Levenberg-Marquardt
@@ -1251,6 +1325,36 @@ int orc_anneal(const void* mp, const orc::SAOpts* o, double* x_best, double* f_b
                double* T0_used) {
   return orc::anneal(*(const orc::Market*)mp, *o, x_best, f_best, chain_xb, chain_fb, trace_f, trace_x,
                      bits, n_evals, T0_used);
+}
+
+// f_s at the correlation parameters y[5] (see mc_objective); quote_vol [n_cap + n_swp].
+double orc_mc_objective(const void* mp, int M, const double* params, const double* alpha, const double* sigma,
+                        const double* phi, int n_cap, const int* cap_fwd, const double* cap_K, int n_swp,
+                        const int* swp_a, const int* swp_b, const double* swp_K, const double* quote_vol,
+                        int64_t n_paths, double dt, uint64_t mc_seed, const double* y, int n_threads) {
+  const orc::Market& m = *(const orc::Market*)mp;
+  orc::McModel md;
+  md.M = M; md.beta = params[0];
+  md.alpha.assign(alpha, alpha + M); md.sigma.assign(sigma, sigma + M); md.phi.assign(phi, phi + M);
+  const orc::McTarget t = orc::mc_target(m, n_cap, cap_fwd, cap_K, n_swp, swp_a, swp_b, swp_K, quote_vol);
+  return orc::mc_objective(m, md, t, y, n_paths, dt, mc_seed, n_threads);
+}
+
+// The annealing search of f_s over the box lo/hi/free_mask [5] (SAOpts as for orc_anneal; the
+// Monte Carlo of each evaluation single-threaded, the chains in parallel).
+int orc_mc_anneal(const void* mp, int M, const double* params, const double* alpha, const double* sigma,
+                  const double* phi, int n_cap, const int* cap_fwd, const double* cap_K, int n_swp, const int* swp_a,
+                  const int* swp_b, const double* swp_K, const double* quote_vol, int64_t n_paths, double dt,
+                  uint64_t mc_seed, const double* lo, const double* hi, const uint8_t* freem, const orc::SAOpts* o,
+                  double* y_best, double* f_best, double* trace_f, double* trace_x, double* T0_used) {
+  const orc::Market& m = *(const orc::Market*)mp;
+  orc::McModel md;
+  md.M = M; md.beta = params[0];
+  md.alpha.assign(alpha, alpha + M); md.sigma.assign(sigma, sigma + M); md.phi.assign(phi, phi + M);
+  const orc::McTarget t = orc::mc_target(m, n_cap, cap_fwd, cap_K, n_swp, swp_a, swp_b, swp_K, quote_vol);
+  const orc::Box bx{5, lo, hi, freem};
+  return orc::anneal_box(bx, [&](const double* y) { return orc::mc_objective(m, md, t, y, n_paths, dt, mc_seed, 1); },
+                         *o, y_best, f_best, nullptr, nullptr, trace_f, trace_x, nullptr, nullptr, T0_used);
 }
 
 int orc_nm(const void* mp, const double* theta0, int max_iter, double step, double ftol, double* theta_out,

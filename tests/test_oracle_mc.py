@@ -95,3 +95,55 @@ def test_mc_is_deterministic_and_thread_count_independent():
     a = oracle.mc_price(om, model, cap_fwd=cf[:20], cap_K=ck[:20], n_paths=300, dt=0.05, seed=5, n_threads=1)
     b = oracle.mc_price(om, model, cap_fwd=cf[:20], cap_K=ck[:20], n_paths=300, dt=0.05, seed=5, n_threads=THREADS)
     assert np.allclose(a[0], b[0], rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- SA over the Monte Carlo objective
+def _self_quoted_swaptions(M=6, n_paths=2000, dt=0.05, seed=5):
+    """Payer swaptions on the paper's first M forwards quoted at the Black vols that reproduce the
+    oracle's own Monte Carlo prices at the paper's correlation parameters (root-finding on Black)."""
+    from scipy.optimize import brentq
+    sk, model, _, _, _ = _paper_model()
+    om = oracle.Market(sk, np.full(sk.n_cap, 0.5))
+    P, T = sk.P, sk.T
+    tau = np.diff(T)
+    m6 = dict(model, M=M)
+    sa, sb, sK = [], [], []
+    for a in (0, 1, 2):
+        for b in (a + 2, a + 4):
+            A = sum(tau[j] * P[j + 1] for j in range(a, b))
+            S = (P[a] - P[b]) / A
+            for mny in (0.8, 1.0, 1.25):
+                sa.append(a); sb.append(b); sK.append(S * mny)
+    pr, _, _ = oracle.mc_price(om, m6, swp_a=sa, swp_b=sb, swp_K=sK, n_paths=n_paths, dt=dt, seed=seed, n_threads=1)
+    qv = []
+    for k in range(len(sa)):
+        a, b = sa[k], sb[k]
+        A = sum(tau[j] * P[j + 1] for j in range(a, b))
+        S = (P[a] - P[b]) / A
+        qv.append(brentq(lambda v: oracle.black_call(S, sK[k], T[a], v, A) - pr[k], 1e-4, 5.0, xtol=1e-15))
+    y = np.array([model[k] for k in ("eta1", "lambda1", "eta2", "lambda2", "lambda3")])
+    return om, m6, np.array(sa), np.array(sb), np.array(sK), np.array(qv), y
+
+
+def test_mc_objective_vanishes_at_the_generating_correlations():
+    # quotes made by the pricer itself at y: f_s(y) = 0 up to the root-finding, so the market prices
+    # of the objective (Black's formula, annuity, swap rate, expiry) and the Monte Carlo payoffs agree
+    # on every convention; away from y, f_s > 0
+    om, m6, sa, sb, sK, qv, y = _self_quoted_swaptions()
+    kw = dict(swp_a=sa, swp_b=sb, swp_K=sK, n_paths=2000, dt=0.05, mc_seed=5)
+    f_true = oracle.mc_objective(om, m6, y, qv, **kw)
+    f_off = oracle.mc_objective(om, m6, y * np.array([0.9, 1.2, 0.9, 1.2, 2.0]), qv, **kw)
+    assert f_true <= 1e-12 * f_off and f_off > 0
+
+
+def test_mc_anneal_descends_from_the_box_centre():
+    # the annealing loop over f_s (common random numbers: f_s is deterministic in y) ends well below
+    # f_s at its start, at a point whose f_s re-evaluates to the reported value
+    om, m6, sa, sb, sK, qv, y = _self_quoted_swaptions()
+    lo, hi = np.zeros(5), np.array([1.0, 5.0, 1.0, 5.0, 0.5])
+    kw = dict(swp_a=sa, swp_b=sb, swp_K=sK, n_paths=2000, dt=0.05, mc_seed=5)
+    r = oracle.mc_anneal(om, m6, qv, lo, hi, np.ones(5), 8, 8, 8, 0.7, 9, n_threads=THREADS, **kw)
+    f_c = oracle.mc_objective(om, m6, 0.5 * (lo + hi), qv, **kw)
+    assert r["f_best"] <= 0.05 * f_c
+    assert r["f_best"] == pytest.approx(oracle.mc_objective(om, m6, r["y_best"], qv, **kw), rel=1e-14)
+    assert np.all(r["y_best"] >= lo) and np.all(r["y_best"] <= hi)
