@@ -651,7 +651,8 @@ static void mc_normals4(uint64_t seed, uint64_t path, int step, int b, double* z
 // Readings (the paper prints no scheme): Euler steps in F, absorbed at zero (for b < 1 the CEV
 // forward reaches zero; its drift and diffusion both carry F^b, so it stays there), log-Euler steps
 // in ln V, the drifts frozen over a step; a path whose state (F or ln V) is not finite at a fixing
-// date pays nothing from there on and is counted (n_bad); every interval [T_{k-1}, T_k] (T_{-1} = 0) is cut into ceil(len / dt) equal steps,
+// date pays nothing from there on and is counted (n_bad); the simulation ends at the last fixing
+// an instrument needs; every interval [T_{k-1}, T_k] (T_{-1} = 0) is cut into ceil(len / dt) equal steps,
 // so the fixings fall on the grid; the Brownian increments of a step are L xi with xi standard
 // normals (mc_normals4, numbered r = 0, 1, ... within the step) and L the Cholesky factor of the
 // correlation matrix of (W, Z) ordered by forward, last forward first, W before Z (row 2(M-1-i)
@@ -777,6 +778,10 @@ static int mc_price(const Market& m, const McModel& md, int n_cap, const int* ca
     const double len = m.T[k] - (k == 0 ? 0.0 : m.T[k - 1]);
     nsteps[k] = std::max(1, (int)std::ceil(len / dt - 1e-9));
   }
+  // the simulation ends at the last fixing an instrument needs
+  int K_end = 1;
+  for (int c = 0; c < n_cap; ++c) K_end = std::max(K_end, cap_fwd[c] + 1);
+  for (int c = 0; c < n_swp; ++c) K_end = std::max(K_end, swp_a[c] + 1);
   std::vector<double> sum(ni, 0.0), sum2(ni, 0.0);
   int64_t bad = 0;
 #pragma omp parallel num_threads(n_threads > 0 ? n_threads : 1)
@@ -790,7 +795,7 @@ static int mc_price(const Market& m, const McModel& md, int n_cap, const int* ca
     for (int64_t p = 0; p < n_paths; ++p) {
       for (int i = 0; i < M; ++i) { F[i] = m.F[i]; lnV[i] = std::log(md.alpha[i]); }
       int step = 0;
-      for (int k = 0; k < M; ++k) {          // interval k: forwards k .. M-1 alive (h(t) = k)
+      for (int k = 0; k < K_end; ++k) {      // interval k: forwards k .. M-1 alive (h(t) = k)
         const double h = (m.T[k] - (k == 0 ? 0.0 : m.T[k - 1])) / nsteps[k];
         const int na = 2 * (M - k);          // alive rows of L
         for (int s = 0; s < nsteps[k]; ++s, ++step) {
@@ -831,10 +836,10 @@ static int mc_price(const Market& m, const McModel& md, int n_cap, const int* ca
       // a path whose state leaves the finite numbers at a fixing date (the vol process can explode:
       // its spot-measure drift grows with the vols) is stopped there: it pays nothing from that date
       // on, and it is counted
-      if (!good[M - 1]) ++lbad;
+      if (!good[K_end - 1]) ++lbad;
       // deflators: 1 / B(T_{i+1}) = P(0, T_0) / prod_{k <= i} (1 + tau_k F_k(T_k)); numer[i] = 1 / B(T_i)
       numer[0] = m.P[0];
-      for (int k = 0; k < M; ++k) numer[k + 1] = numer[k] / (1.0 + m.tau[k] * fix[k]);
+      for (int k = 0; k < K_end; ++k) numer[k + 1] = numer[k] / (1.0 + m.tau[k] * fix[k]);
       for (int c = 0; c < n_cap; ++c) {
         const int i = cap_fwd[c];
         if (!good[i]) continue;
