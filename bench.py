@@ -323,6 +323,24 @@ def run_profile(args):
                       "rmse_volpt": float(r["rmse_volpt"][0])}))
 
 
+def run_mc_profile(args):
+    """Three launches of the Monte Carlo pricer on the paper's Hagan model (its 117 caplets, FP32),
+    --mc-paths paths at --mc-dt, for ncu captures."""
+    import paper_2408_01470_b300 as lib
+    import torch
+    from paper_2408_01470_b300 import synth
+    lib.load()
+    sk, model, cf, ck, _ = synth.paper_hagan_mc_model(PAPER_DATA, PAPER_MM, PAPER_MC)
+    s = torch.cuda.Stream()
+    plan = lib.McPlan(sk.T, sk.P, model, cf, ck, n_paths=args.mc_paths, dt=args.mc_dt, seed=1, prec=args.prec,
+                      stream=s)
+    for _ in range(3):
+        plan.launch(s)
+    s.synchronize()
+    print(json.dumps({"mc_profile": True, "paths": args.mc_paths, "dt": args.mc_dt, "prec": args.prec,
+                      "price_first": float(plan.price[0].item()), "n_bad": int(plan.n_bad.item())}))
+
+
 def rmse_per_level(gm, trace_x, quotes, market=0):
     """The true vol RMSE (vol points) of each level's start point: FP64 model vols against the quotes."""
     v = gm.model_vols(trace_x, "fp64", market=market).cpu().numpy()
@@ -408,6 +426,7 @@ def search_record(lib, name, prec, seed, stream, peaks, levels=None, cpu=None, e
 PAPER_DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "paper_euribor_20111121.txt")
 PAPER_MM = os.path.join(os.path.dirname(PAPER_DATA), "paper_mm_20111121.txt")
 PAPER_MC = os.path.join(os.path.dirname(PAPER_DATA), "paper_hagan_mc_20111121.txt")
+PAPER_SWP = os.path.join(os.path.dirname(PAPER_DATA), "paper_swaptions_20111121.txt")
 
 
 def paper_data_record(lib, seed, stream):
@@ -550,6 +569,45 @@ def mc_record(lib, stream, peaks, cpu=True):
     return out
 
 
+def mc_calibration_record(lib, stream, chains=64, levels=20, steps=5, n_paths=10000, dt=0.02):
+    """The paper's swaption calibration of the Hagan model over a Monte Carlo objective (Section 4.1.2):
+    the correlation parameters (eta1, lambda1, eta2, lambda2, lambda3) against the 180 swaptions of
+    Table tab:smilesTS, the caplet-calibrated alpha_i, sigma_i, phi_ii of Table tab:paramsHaganVolas
+    fixed; FP32 paths with common random numbers, every step's proposals of all chains in one launch.
+    Reports the search's wall time (against the paper's ~2 hours on two GTX 470s: context), f_s, and
+    the mean absolute error of the swaption prices in percent of the notional (the paper's MAE
+    6.19e-2; Black prices here with the annuity of the real accruals)."""
+    from paper_2408_01470_b300 import synth
+    from scipy.special import ndtr
+    sk, sa, sb, sK, vol, pub = synth.paper_swaption_smiles(PAPER_DATA, PAPER_MM, PAPER_SWP)
+    _, model, _, _, _ = synth.paper_hagan_mc_model(PAPER_DATA, PAPER_MM, PAPER_MC)
+    lo, hi = np.array([0.0, 0.0, 0.0, 0.0, 0.0]), np.array([1.0, 5.0, 1.0, 5.0, 0.5])
+    kw = dict(swp_start=sa, swp_end=sb, swp_K=sK, n_paths=n_paths, dt=dt, mc_seed=20111121, prec="fp32")
+    r = lib.mc_anneal(sk.T, sk.P, model, vol, lo, hi, np.ones(5), chains, levels, steps, 0.8, 20111121, stream=stream,
+                      **kw)
+    m_best = dict(model, eta1=r["y_best"][0], lambda1=r["y_best"][1], eta2=r["y_best"][2], lambda2=r["y_best"][3],
+                  lambda3=r["y_best"][4])
+    mc, _, _ = lib.mc_price(sk.T, sk.P, m_best, (), (), sa, sb, sK, n_paths=n_paths, dt=dt, seed=20111121, prec="fp32",
+                            stream=stream)
+    tau = np.diff(sk.T)
+    A = np.array([sum(tau[k] * sk.P[k + 1] for k in range(a, b)) for a, b in zip(sa, sb)])
+    S = (sk.P[sa] - sk.P[sb]) / A
+    sd = vol * np.sqrt(sk.T[sa])
+    d1 = np.log(S / sK) / sd + 0.5 * sd
+    black = A * (S * ndtr(d1) - sK * ndtr(d1 - sd))
+    return {"workload": f"paper_hagan_swaption_calibration_mc_180swaptions_{chains}ch_x_{levels}T_x_{steps}steps_"
+                        f"{n_paths}paths_dt{dt}",
+            "how": "sabr_lmm_mc_anneal: host-driven annealing (the paper's own split), every step's proposals priced "
+                   "in one batched Monte Carlo launch; wall time of the whole search",
+            "seconds": r["seconds"], "evaluations": int(r["n_evals"]), "f_best": r["f_best"],
+            "y_best": [float(x) for x in r["y_best"]],
+            "mae_percent": float(100.0 * np.mean(np.abs(mc - black))),
+            "path_steps_per_s": r["n_evals"] * n_paths * int(np.ceil(sk.T[3] / dt)) / r["seconds"],
+            "paper": {"mae_percent": float(pub["mae_percent"]), "calibration_hours": float(pub["calibration_hours"]),
+                      "y": [model[k] for k in ("eta1", "lambda1", "eta2", "lambda2", "lambda3")],
+                      "hardware": "2x NVIDIA GeForce GTX 470 (Fermi)"}}
+
+
 def lm_schedule_to_target(gm, C, N, cool, seed, target, schedule=(1, 2, 3, 5, 10, 20, 40, 80, 200)):
     """The mixed-precision, adjoint-polished form: the shortest FP32 search of the schedule (the same
     cooling, fewer levels) whose Levenberg-Marquardt polish of its 64 best chains reaches the target
@@ -667,9 +725,28 @@ def main():
                     help="with --profile: Levenberg-Marquardt polish of the k best chains after the search")
     ap.add_argument("--workload", default="", choices=[""] + list(WORKLOADS),
                     help="with --profile / --quality: the search to run; alone: that workload's full line")
+    ap.add_argument("--mc-profile", action="store_true",
+                    help="three launches of the Monte Carlo pricer (--mc-paths, --mc-dt), for ncu captures")
+    ap.add_argument("--mc-calibration", action="store_true",
+                    help="the paper's swaption calibration over the Monte Carlo objective alone (--mc-chains, "
+                         "--mc-levels, --mc-steps, --mc-paths, --mc-dt)")
+    ap.add_argument("--mc-chains", type=int, default=64)
+    ap.add_argument("--mc-levels", type=int, default=20)
+    ap.add_argument("--mc-steps", type=int, default=5)
+    ap.add_argument("--mc-paths", type=int, default=100000)
+    ap.add_argument("--mc-dt", type=float, default=0.01)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mc_profile:
+        return run_mc_profile(args)
+    if args.mc_calibration:
+        import paper_2408_01470_b300 as lib
+        import torch
+        lib.load()
+        print(json.dumps(mc_calibration_record(lib, torch.cuda.Stream(), args.mc_chains, args.mc_levels,
+                                               args.mc_steps, args.mc_paths, args.mc_dt)))
+        return None
     if args.profile:
         args.workload = args.workload or "caplets"
         return run_profile(args)
@@ -799,6 +876,7 @@ def main():
     # the Monte Carlo pricer at the configurations of Table tab:haganMCpricer
     if args.prec == "fp32" and not args.no_mc:
         workloads["mc_hagan_caplets"] = mc_record(lib, s, peaks, cpu=not args.no_cpu_baseline)
+        workloads["mc_swaption_calibration"] = mc_calibration_record(lib, s)
     # the 256-market batch: one level (its full 100-level schedule: bench.py --workload batch)
     if args.prec == "fp32" and not args.no_batch_variant:
         rec, _, _, _, _ = search_record(lib, "batch", "fp32", seed, s, peaks, levels=1, e2e=False)

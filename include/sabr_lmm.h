@@ -435,6 +435,46 @@ void sabr_lmm_mc_plan_free(sabr_lmm_mc_plan* p);
 sabr_lmm_status sabr_lmm_mc_price(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o, double* price,
                                   double* stderr_out, int64_t* n_bad, void* stream);
 
+/* The swaption calibration of Section 3 by simulated annealing over a Monte Carlo objective: the
+ * correlation parameters y = (eta1, lambda1, eta2, lambda2, lambda3) minimise
+ *   f_s(y) = sum_k (P_k^Black - P_k^MC(y))^2
+ * over the description's instruments (caplets, then swaptions), with its alpha, sigma, phi fixed
+ * (the caplet calibration's result) and its own correlation fields ignored.  P_k^Black: Black's
+ * formula at quote_vol[k] (host, [n_cap + n_swp], > 0): caplet on forward i with discount
+ * tau_i P(0, T[i+1]) and forward F_i(0); payer swaption over [a, b) with annuity sum tau_k
+ * P(0, T[k+1]) and swap rate (P(0, T[a]) - P(0, T[b])) / annuity; expiry T[i] or T[a].
+ * P_k^MC(y): sabr_lmm_mc_launch's price with `mc` (n_paths, dt, seed, prec) at y; the same seed at
+ * every y (common random numbers), so f_s is a deterministic function of y.
+ * The search: the annealing loop of sabr_lmm_anneal on the 5-slot box lo/hi/free_mask (0 <= lo <=
+ * hi, eta's <= 1), from y0 (or the box centre), T0 (<= 0: f_s(y0)), the same neighbour rule and
+ * Philox4x64-10 uniforms (word k moves slot k, word 5 decides, chain c at counter (block, step,
+ * level, c) under key (seed, 0)).  Every step evaluates the n_chains proposals in one launch (a
+ * CTA grid per proposal, its constants staged in shared memory); the proposals' correlation
+ * factors are built on the host threads, the Metropolis decisions taken on the host in FP64.
+ * Synchronous; allocates device and pinned host memory for the search.                       */
+typedef struct {
+  int32_t n_chains, n_levels, steps_per_level;
+  double T0, cooling, step_frac, step_floor;
+  uint64_t seed;
+  const double* y0;             /* [5] or NULL */
+  const double* lo;             /* [5] */
+  const double* hi;             /* [5] */
+  const uint8_t* free_mask;     /* [5] */
+} sabr_lmm_mc_anneal_opts;
+
+typedef struct {
+  double y_best[5];             /* the best point ever accepted */
+  double f_best;
+  double T0_used;
+  int64_t n_evals;              /* Monte Carlo objective evaluations: n_chains n_levels steps + 1 */
+  double seconds;               /* host wall time of the search */
+  double* trace_f;              /* caller [n_levels] or NULL: each level's best end value */
+  double* trace_y;              /* caller [n_levels x 5] or NULL: each next level's start point */
+} sabr_lmm_mc_anneal_result;
+
+sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const double* quote_vol, const sabr_lmm_mc_opts* mc,
+                                   const sabr_lmm_mc_anneal_opts* o, sabr_lmm_mc_anneal_result* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,17 @@ class McOpts(C.Structure):
                 ("grid", C.c_int32)]
 
 
+class McAnnealOpts(C.Structure):
+    _fields_ = [("n_chains", C.c_int32), ("n_levels", C.c_int32), ("steps_per_level", C.c_int32),
+                ("T0", C.c_double), ("cooling", C.c_double), ("step_frac", C.c_double), ("step_floor", C.c_double),
+                ("seed", C.c_uint64), ("y0", _D), ("lo", _D), ("hi", _D), ("free_mask", _U8)]
+
+
+class McAnnealResult(C.Structure):
+    _fields_ = [("y_best", C.c_double * 5), ("f_best", C.c_double), ("T0_used", C.c_double), ("n_evals", C.c_int64),
+                ("seconds", C.c_double), ("trace_f", _D), ("trace_y", _D)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -113,7 +124,7 @@ EXPORTS = ("sabr_lmm_load_market", "sabr_lmm_free_market", "sabr_lmm_objective",
            "sabr_lmm_market_info", "sabr_lmm_selftest_wait", "sabr_lmm_quadrature_rule", "sabr_lmm_last_error",
            "sabr_lmm_version", "sabr_lmm_residuals", "sabr_lmm_sync", "sabr_lmm_test_raise_error",
            "sabr_lmm_nm_polish", "sabr_lmm_anneal_plan_config", "sabr_lmm_mc_prepare", "sabr_lmm_mc_launch",
-           "sabr_lmm_mc_plan_free", "sabr_lmm_mc_price")
+           "sabr_lmm_mc_plan_free", "sabr_lmm_mc_price", "sabr_lmm_mc_anneal")
 
 
 def open_library(path: str = LIB_PATH):
@@ -152,6 +163,8 @@ def open_library(path: str = LIB_PATH):
     lib.sabr_lmm_mc_plan_free.argtypes = [C.c_void_p]
     lib.sabr_lmm_mc_plan_free.restype = None
     lib.sabr_lmm_mc_price.argtypes = [C.POINTER(McDesc), C.POINTER(McOpts), _D, _D, C.POINTER(C.c_int64), C.c_void_p]
+    lib.sabr_lmm_mc_anneal.argtypes = [C.POINTER(McDesc), _D, C.POINTER(McOpts), C.POINTER(McAnnealOpts),
+                                       C.POINTER(McAnnealResult), C.c_void_p]
     lib.sabr_lmm_last_error.restype = C.c_char_p
     lib.sabr_lmm_version.restype = C.c_char_p
     return lib
@@ -562,3 +575,31 @@ class McPlan:
         if getattr(self, "h", None) is not None and self.h.value:
             self._lib.sabr_lmm_mc_plan_free(self.h)
             self.h = None
+
+
+def mc_anneal(T, P, model, quote_vol, lo, hi, free, n_chains, n_levels, steps, cooling, seed, cap_fwd=(), cap_K=(),
+              swp_start=(), swp_end=(), swp_K=(), n_paths=10000, dt=0.02, mc_seed=1, prec="fp32", T0=0.0,
+              step_frac=0.1, step_floor=1e-3, y0=None, stream=None):
+    """sabr_lmm_mc_anneal: the correlation parameters (eta1, lambda1, eta2, lambda2, lambda3) by
+    simulated annealing over the Monte Carlo objective; returns a dict (synchronous)."""
+    lib = load()
+    d, keep = mc_describe(T, P, model, cap_fwd, cap_K, swp_start, swp_end, swp_K)
+    mo = _mc_opts(n_paths, dt, mc_seed, prec, 0)
+    qv = _f64(quote_vol)
+    lo, hi = _f64(lo), _f64(hi)
+    fr = np.ascontiguousarray(free, np.uint8)
+    o = McAnnealOpts()
+    o.n_chains, o.n_levels, o.steps_per_level = int(n_chains), int(n_levels), int(steps)
+    o.T0, o.cooling, o.step_frac, o.step_floor, o.seed = float(T0), float(cooling), float(step_frac), \
+        float(step_floor), int(seed)
+    y0a = None if y0 is None else _f64(y0)
+    o.y0 = None if y0a is None else y0a.ctypes.data_as(_D)
+    o.lo, o.hi, o.free_mask = lo.ctypes.data_as(_D), hi.ctypes.data_as(_D), fr.ctypes.data_as(_U8)
+    tf, ty = np.zeros(n_levels), np.zeros((n_levels, 5))
+    r = McAnnealResult()
+    r.trace_f, r.trace_y = tf.ctypes.data_as(_D), ty.ctypes.data_as(_D)
+    _check(lib.sabr_lmm_mc_anneal(C.byref(d), qv.ctypes.data_as(_D), C.byref(mo), C.byref(o), C.byref(r),
+                                  _stream_ptr(stream)))
+    del keep
+    return dict(y_best=np.array(r.y_best[:]), f_best=r.f_best, T0=r.T0_used, n_evals=r.n_evals, seconds=r.seconds,
+                trace_f=tf, trace_y=ty)

@@ -13,6 +13,8 @@
 #include <tuple>
 #include <string>
 #include <vector>
+#include <thread>
+#include <chrono>
 
 #include "../../include/sabr_lmm.h"
 #include "kernels.cuh"

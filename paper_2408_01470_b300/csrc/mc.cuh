@@ -38,6 +38,7 @@ template <class R> struct McConsts {
 
 struct McArgs {
   int M;                         // forwards simulated (the largest forward any instrument needs + 1)
+  int n_int;                     // intervals simulated: the last fixing any instrument needs + 1
   int n_cap, n_swp;
   double beta, P0;               // P0 = P(0, T_0)
   const int* nsteps;             // [M] steps of interval k
@@ -115,14 +116,12 @@ __device__ __forceinline__ double warp_sum_mc(double v) {
 // Dynamic shared memory of the path kernel: the per-warp sums.
 __host__ __device__ inline size_t mc_smem_bytes(int n_instr) { return (size_t)kMcWarps * n_instr * 2 * sizeof(double); }
 
-// The model constants travel as a kernel parameter (constant bank): after unrolling, every index
-// into them is a compile-time constant, so the FMAs of the correlation product and the drifts read
-// their coefficient straight from the constant bank, with no shared-memory load.
+// The paths of CTA blockIdx.x (grid-stride over gridDim.x CTAs): their per-warp sums in acc
+// (shared, [warps][n_instr][2]), the CTA's sums to part_out [n_instr x 2] and its stopped paths to
+// bad_out.  C is read with compile-time indices after unrolling.
 template <class R>
-__global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_kernel(const __grid_constant__ McArgs a,
-                                                             const __grid_constant__ McConsts<R> C) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  double* acc = (double*)smem;   // [warps][n_instr][2]
+__device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, double* acc, double* part_out,
+                                         unsigned long long* bad_out) {
   const int n_instr = a.n_cap + a.n_swp;
   for (int t = threadIdx.x; t < kMcWarps * n_instr * 2; t += blockDim.x) acc[t] = 0.0;
   __syncthreads();
@@ -142,7 +141,7 @@ __global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_ke
     bool good = live;
     double numer = a.P0;   // 1 / B(T_k) at the start of interval k
     int step = 0;
-    for (int k = 0; k < M; ++k) {
+    for (int k = 0; k < a.n_int; ++k) {
       const int na = M - k;   // alive forwards: u = 0 .. na - 1
       const int ns = a.nsteps[k];
       const R h = (R)a.h[k], sh = (R)sqrt(a.h[k]);
@@ -245,7 +244,7 @@ __global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_ke
   }
   __syncthreads();
   // the CTA's sums, warp by warp in order
-  double* out = a.part + (size_t)blockIdx.x * n_instr * 2;
+  double* out = part_out;
   for (int t = threadIdx.x; t < n_instr * 2; t += blockDim.x) {
     double v = 0.0;
     for (int w = 0; w < kMcWarps; ++w) v += acc[(size_t)w * n_instr * 2 + t];
@@ -258,7 +257,85 @@ __global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_ke
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
     for (int w = 0; w < kMcWarps; ++w) t += sbad[w];
-    a.bad[blockIdx.x] = t;
+    *bad_out = t;
+  }
+}
+
+// The model constants travel as a kernel parameter (constant bank): after unrolling, every index
+// into them is a compile-time constant, so the FMAs of the correlation product and the drifts read
+// their coefficient straight from the constant bank, with no shared-memory load.
+template <class R>
+__global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_kernel(const __grid_constant__ McArgs a,
+                                                             const __grid_constant__ McConsts<R> C) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int n_instr = a.n_cap + a.n_swp;
+  mc_paths<R>(a, C, (double*)smem, a.part + (size_t)blockIdx.x * n_instr * 2, a.bad + blockIdx.x);
+}
+
+// Many parameter sets in one launch (the annealer's proposals): set blockIdx.y has its constants
+// Cs[set] (staged into shared memory ahead of the per-warp sums) and its own CTA sums,
+// part[(set x gridDim.x + CTA) x n_instr x 2], bad[set x gridDim.x + CTA].
+template <class R>
+__host__ __device__ inline size_t mc_batch_smem_bytes(int n_instr) {
+  return ((sizeof(McConsts<R>) + 127) & ~(size_t)127) + mc_smem_bytes(n_instr);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_batch_kernel(const __grid_constant__ McArgs a,
+                                                                   const McConsts<R>* __restrict__ Cs) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  McConsts<R>& C = *(McConsts<R>*)smem;
+  const int set = blockIdx.y, n_instr = a.n_cap + a.n_swp;
+  {
+    const uint4* src = (const uint4*)(Cs + set);
+    uint4* dst = (uint4*)smem;
+    for (int t = threadIdx.x; t < (int)(sizeof(McConsts<R>) / 16); t += blockDim.x) dst[t] = src[t];
+  }
+  // (mc_paths synchronises the CTA before it reads C)
+  double* acc = (double*)(smem + ((sizeof(McConsts<R>) + 127) & ~(size_t)127));
+  const size_t cta = (size_t)set * gridDim.x + blockIdx.x;
+  mc_paths<R>(a, C, acc, a.part + cta * n_instr * 2, a.bad + cta);
+}
+
+// f_s of every set: the Monte Carlo prices from its CTA sums (CTA by CTA in order) against the
+// market prices mkt [n_instr] (sorted order), f[set] = sum_k (price_k - mkt_k)^2 (+inf if any
+// price is not finite); one warp per set.
+__global__ void mc_objective_kernel(McArgs a, int grid, int n_sets, const double* mkt, double* f) {
+  const int set = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (set >= n_sets) return;
+  const int n_instr = a.n_cap + a.n_swp;
+  double acc = 0.0;
+  for (int t = lane; t < n_instr; t += 32) {
+    double s1 = 0.0;
+    for (int g = 0; g < grid; ++g) s1 += a.part[(((size_t)set * grid + g) * n_instr + t) * 2];
+    const double e = s1 / (double)a.n_paths - mkt[t];
+    acc += e * e;
+  }
+  acc = warp_sum_mc(acc);
+  if (lane == 0) f[set] = isfinite(acc) ? acc : __longlong_as_double(0x7ff0000000000000LL);
+}
+
+// Market prices of the sorted instruments from their quoted Black vols: caplet on forward i,
+// discount tau_i P(0, T_{i+1}), forward F_i(0), expiry T_i; payer swaption over [a, b), annuity
+// A = sum tau_k P(0, T_{k+1}), swap rate (P(0, T_a) - P(0, T_b)) / A, expiry T_a.  One thread each.
+__device__ __forceinline__ double mc_black_call(double F, double K, double T, double v, double D) {
+  const double s = v * sqrt(T);
+  const double d1 = log(F / K) / s + 0.5 * s;
+  return D * (F * normcdf(d1) - K * normcdf(d1 - s));
+}
+__global__ void mc_market_kernel(McArgs a, const double* T, const double* P, const int* cap_fwd_sorted,
+                                 const int* swp_a_sorted, const double* vol_sorted, double* mkt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < a.n_cap) {
+    const int i = cap_fwd_sorted[t];
+    const double tau = T[i + 1] - T[i];
+    const double F = (P[i] / P[i + 1] - 1.0) / tau;
+    mkt[t] = mc_black_call(F, a.cap_K[t], T[i], vol_sorted[t], tau * P[i + 1]);
+  } else if (t < a.n_cap + a.n_swp) {
+    const int c = t - a.n_cap, s0 = swp_a_sorted[c], b = a.swp_b[c];
+    double A = 0.0;
+    for (int k = s0; k < b; ++k) A += (T[k + 1] - T[k]) * P[k + 1];
+    mkt[t] = mc_black_call((P[s0] - P[b]) / A, a.swp_K[c], T[s0], vol_sorted[t], A);
   }
 }
 

@@ -20,6 +20,10 @@ struct sabr_lmm_mc_plan {
   void* buf = nullptr;          // device: time grid, instruments, partial sums
   double* out = nullptr;        // device: price [ni], stderr [ni]
   long long* nbad = nullptr;    // device
+  // host copies for re-deriving constants at other correlation parameters (the annealer)
+  int M = 0;
+  std::vector<double> tau;
+  std::vector<int> cap_order, swp_order;   // sorted position -> the caller's index
 };
 
 namespace {
@@ -80,6 +84,64 @@ bool mc_repair(std::vector<double>& C, int n) {
       C[(size_t)i * n + j] = v;
     }
   return true;
+}
+
+// The model constants of one parameter point: the correlation matrix in u-order (u = M - 1 - i;
+// row 2u is W_i, row 2u + 1 is Z_i) from eta1, lambda1, eta2, lambda2, lambda3 (y[0..4] when y is
+// given, else the description's), repaired when indefinite, its Cholesky factor, and the
+// per-forward constants; in FP64 and FP32.
+void mc_build_consts(const sabr_lmm_mc_desc* d, int M, const double* tau, const double* y, McConsts<double>& c64,
+                     McConsts<float>& c32) {
+  const double eta1 = y ? y[0] : d->eta1, lambda1 = y ? y[1] : d->lambda1, eta2 = y ? y[2] : d->eta2;
+  const double lambda2 = y ? y[3] : d->lambda2, lambda3 = y ? y[4] : d->lambda3;
+  const int n = 2 * M;
+  std::vector<double> Cm((size_t)n * n);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      const int i = M - 1 - r / 2, j = M - 1 - c / 2;
+      const bool wr = (r & 1) == 0, wc = (c & 1) == 0;
+      const double dT = std::fabs(d->T[i] - d->T[j]);
+      double v;
+      if (wr && wc) v = eta1 + (1.0 - eta1) * std::exp(-lambda1 * dT);
+      else if (!wr && !wc) v = eta2 + (1.0 - eta2) * std::exp(-lambda2 * dT);
+      else {   // corr(W_a, Z_b) = sign(phi_aa) sqrt(|phi_aa phi_bb|) e^{-lambda3 |T_a - T_b|}
+        const int fa = wr ? i : j, fb = wr ? j : i;
+        v = (d->phi[fa] < 0.0 ? -1.0 : 1.0) * std::sqrt(std::fabs(d->phi[fa] * d->phi[fb])) * std::exp(-lambda3 * dT);
+      }
+      Cm[(size_t)r * n + c] = v;
+    }
+  mc_repair(Cm, n);
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double dd = Cm[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) dd -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(dd > 1e-12)) continue;
+    dd = std::sqrt(dd);
+    L[(size_t)j * n + j] = dd;
+    for (int i = j + 1; i < n; ++i) {
+      double t = Cm[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / dd;
+    }
+  }
+  c64 = McConsts<double>{};
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) c64.L[r * kMcRows + c] = L[(size_t)r * n + c];
+  for (int u = 0; u < M; ++u) {
+    const int i = M - 1 - u;
+    for (int v = 0; v < M; ++v) {
+      c64.rho[u * kMcMaxFwd + v] = Cm[(size_t)(2 * u) * n + 2 * v];
+      c64.phi[u * kMcMaxFwd + v] = Cm[(size_t)(2 * u) * n + 2 * v + 1];
+    }
+    c64.tau[u] = tau[i];
+    c64.sig[u] = d->sigma[i];
+    c64.hs2[u] = 0.5 * d->sigma[i] * d->sigma[i];
+    c64.F0[u] = (d->P[i] / d->P[i + 1] - 1.0) / tau[i];
+    c64.lnV0[u] = std::log(d->alpha[i]);
+  }
+  const double* src = (const double*)&c64;
+  float* dst = (float*)&c32;
+  for (size_t k = 0; k < sizeof(McConsts<double>) / sizeof(double); ++k) dst[k] = (float)src[k];
 }
 
 std::string mc_validate(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o) {
@@ -144,61 +206,14 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
     total += nsteps[k];
   }
   if (total > (1 << 30)) return fail(SABR_LMM_EINVAL, "mc: too many time steps");
-  // the correlation matrix in u-order (u = M - 1 - i; row 2u is W_i, row 2u + 1 is Z_i)
-  const int n = 2 * M;
-  std::vector<double> Cm((size_t)n * n);
-  for (int r = 0; r < n; ++r)
-    for (int c = 0; c < n; ++c) {
-      const int i = M - 1 - r / 2, j = M - 1 - c / 2;
-      const bool wr = (r & 1) == 0, wc = (c & 1) == 0;
-      const double dT = std::fabs(d->T[i] - d->T[j]);
-      double v;
-      if (wr && wc) v = d->eta1 + (1.0 - d->eta1) * std::exp(-d->lambda1 * dT);
-      else if (!wr && !wc) v = d->eta2 + (1.0 - d->eta2) * std::exp(-d->lambda2 * dT);
-      else {   // corr(W_a, Z_b) = sign(phi_aa) sqrt(|phi_aa phi_bb|) e^{-lambda3 |T_a - T_b|}
-        const int fa = wr ? i : j, fb = wr ? j : i;
-        v = (d->phi[fa] < 0.0 ? -1.0 : 1.0) * std::sqrt(std::fabs(d->phi[fa] * d->phi[fb])) * std::exp(-d->lambda3 * dT);
-      }
-      Cm[(size_t)r * n + c] = v;
-    }
-  mc_repair(Cm, n);
-  std::vector<double> L((size_t)n * n, 0.0);
-  for (int j = 0; j < n; ++j) {
-    double dd = Cm[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) dd -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
-    if (!(dd > 1e-12)) continue;
-    dd = std::sqrt(dd);
-    L[(size_t)j * n + j] = dd;
-    for (int i = j + 1; i < n; ++i) {
-      double t = Cm[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-      L[(size_t)i * n + j] = t / dd;
-    }
-  }
   sabr_lmm_mc_plan* p = new sabr_lmm_mc_plan();
   cudaGetDevice(&p->device);
   p->prec = o->prec;
   p->n_cap = d->n_cap;
   p->n_swp = d->n_swp;
-  for (int r = 0; r < n; ++r)
-    for (int c = 0; c < n; ++c) p->c64.L[r * kMcRows + c] = L[(size_t)r * n + c];
-  for (int u = 0; u < M; ++u) {
-    const int i = M - 1 - u;
-    for (int v = 0; v < M; ++v) {
-      p->c64.rho[u * kMcMaxFwd + v] = Cm[(size_t)(2 * u) * n + 2 * v];
-      p->c64.phi[u * kMcMaxFwd + v] = Cm[(size_t)(2 * u) * n + 2 * v + 1];
-    }
-    p->c64.tau[u] = tau[i];
-    p->c64.sig[u] = d->sigma[i];
-    p->c64.hs2[u] = 0.5 * d->sigma[i] * d->sigma[i];
-    p->c64.F0[u] = (d->P[i] / d->P[i + 1] - 1.0) / tau[i];
-    p->c64.lnV0[u] = std::log(d->alpha[i]);
-  }
-  {
-    const double* s = (const double*)&p->c64;
-    float* t = (float*)&p->c32;
-    for (size_t k = 0; k < sizeof(McConsts<double>) / sizeof(double); ++k) t[k] = (float)s[k];
-  }
+  p->M = M;
+  p->tau = tau;
+  mc_build_consts(d, M, tau.data(), nullptr, p->c64, p->c32);
   // instruments sorted by fixing (stable), with their output slots
   std::vector<int> ci(d->n_cap), si(d->n_swp);
   for (int c = 0; c < d->n_cap; ++c) ci[c] = c;
@@ -219,6 +234,8 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
     swp_lo[d->swp_start[si[c]] + 1]++;
   }
   for (int k = 0; k < M; ++k) { cap_lo[k + 1] += cap_lo[k]; swp_lo[k + 1] += swp_lo[k]; }
+  p->cap_order = ci;
+  p->swp_order = si;
   // grid: enough CTAs for every path, at most 8 per SM (persistent beyond that)
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
@@ -253,6 +270,9 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   char* b = (char*)p->buf;
   McArgs& a = p->args;
   a.M = M; a.n_cap = d->n_cap; a.n_swp = d->n_swp; a.beta = d->beta; a.P0 = d->P[0];
+  a.n_int = 1;   // the simulation ends at the last fixing an instrument needs
+  for (int c = 0; c < d->n_cap; ++c) a.n_int = std::max(a.n_int, d->cap_fwd[c] + 1);
+  for (int c = 0; c < d->n_swp; ++c) a.n_int = std::max(a.n_int, d->swp_start[c] + 1);
   a.nsteps = (const int*)(b + o_ns); a.h = (const double*)(b + o_h); a.tau64 = (const double*)(b + o_tau);
   a.cap_lo = (const int*)(b + o_clo); a.swp_lo = (const int*)(b + o_slo);
   a.cap_out = (const int*)(b + o_cout); a.swp_out = (const int*)(b + o_sout); a.swp_b = (const int*)(b + o_sb);
@@ -319,5 +339,222 @@ extern "C" sabr_lmm_status sabr_lmm_mc_price(const sabr_lmm_mc_desc* d, const sa
   std::memcpy(price, hout.data(), ni * sizeof(double));
   if (stderr_out) std::memcpy(stderr_out, hout.data() + ni, ni * sizeof(double));
   if (n_bad) *n_bad = hb;
+  return SABR_LMM_OK;
+}
+
+// ====================================================================== SA over the Monte Carlo objective
+namespace {
+
+// Philox4x64-10 on the host (the counter-based generator of the annealer's uniforms, Salmon et al.
+// SC'11), and the uniforms of one annealing step: word w of block b at counter (b, step, level,
+// chain) under key (seed, 0), u = (x >> 11) 2^-53.
+void philox4x64_10_host(const uint64_t ctr[4], uint64_t k0, uint64_t k1, uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+  uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  for (int r = 0; r < 10; ++r) {
+    const unsigned __int128 p0 = (unsigned __int128)M0 * c0, p1 = (unsigned __int128)M1 * c2;
+    const uint64_t n0 = (uint64_t)(p1 >> 64) ^ c1 ^ k0, n2 = (uint64_t)(p0 >> 64) ^ c3 ^ k1;
+    c0 = n0; c1 = (uint64_t)p1; c2 = n2; c3 = (uint64_t)p0;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void sa_step_uniforms(uint64_t seed, uint64_t chain, int level, int step, int count, double* u) {
+  for (int b = 0; 4 * b < count; ++b) {
+    const uint64_t ctr[4] = {(uint64_t)b, (uint64_t)step, (uint64_t)level, chain};
+    uint64_t o[4];
+    philox4x64_10_host(ctr, seed, 0, o);
+    for (int w = 0; w < 4 && 4 * b + w < count; ++w) u[4 * b + w] = (double)(o[w] >> 11) * 0x1.0p-53;
+  }
+}
+
+}  // namespace
+
+extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const double* quote_vol,
+                                              const sabr_lmm_mc_opts* mo, const sabr_lmm_mc_anneal_opts* o,
+                                              sabr_lmm_mc_anneal_result* out, void* stream) {
+  if (!quote_vol || !o || !out) return fail(SABR_LMM_EINVAL, "mc_anneal: quote_vol, opts and out are required");
+  if (o->n_chains < 1 || o->n_chains > 4096 || o->n_levels < 1 || o->steps_per_level < 1)
+    return fail(SABR_LMM_EINVAL, "mc_anneal: n_chains in [1, 4096], n_levels and steps_per_level >= 1 required");
+  if (!(o->cooling > 0.0 && o->cooling <= 1.0) || !(o->step_frac > 0.0) || !(o->step_floor >= 0.0))
+    return fail(SABR_LMM_EINVAL, "mc_anneal: cooling in (0, 1], step_frac > 0, step_floor >= 0 required");
+  if (!o->lo || !o->hi || !o->free_mask) return fail(SABR_LMM_EINVAL, "mc_anneal: lo, hi and free_mask are required");
+  for (int k = 0; k < 5; ++k) {
+    const double ub = (k == 0 || k == 2) ? 1.0 : 1e6;
+    if (!(o->lo[k] >= 0.0 && o->lo[k] <= o->hi[k] && o->hi[k] <= ub))
+      return fail(SABR_LMM_EINVAL, "mc_anneal: the box must satisfy 0 <= lo <= hi (eta1, eta2 <= 1)");
+    if (o->y0 && !(o->y0[k] >= o->lo[k] && o->y0[k] <= o->hi[k])) return fail(SABR_LMM_EINVAL, "mc_anneal: y0 outside the box");
+  }
+  const int ni = d ? d->n_cap + d->n_swp : 0;
+  for (int k = 0; k < ni; ++k)
+    if (!(quote_vol[k] > 0.0) || !std::isfinite(quote_vol[k])) return fail(SABR_LMM_EINVAL, "mc_anneal: quote_vol must be finite and > 0");
+  sabr_lmm_mc_plan* p = nullptr;
+  sabr_lmm_status st = sabr_lmm_mc_prepare(d, mo, stream, &p);
+  if (st != SABR_LMM_OK) return st;
+  const int C = o->n_chains, L = o->n_levels, N = o->steps_per_level, P = 5, M = p->M, G = p->grid;
+  const bool f64 = p->prec == SABR_LMM_FP64;
+  const size_t csz = f64 ? sizeof(McConsts<double>) : sizeof(McConsts<float>);
+  cudaStream_t s = (cudaStream_t)stream;
+  // device: the constants of C sets, their CTA sums and stopped paths, f, the market prices, and the
+  // sorted instruments' quotes with the tenor grid; host (pinned): the constants and f
+  Arena A;
+  const size_t o_cs = A.take((size_t)C * csz), o_part = A.take((size_t)C * G * ni * 16), o_bad = A.take((size_t)C * G * 8),
+               o_f = A.take((size_t)C * 8), o_mkt = A.take((size_t)ni * 8), o_vol = A.take((size_t)ni * 8),
+               o_cf = A.take((size_t)p->n_cap * 4), o_sa = A.take((size_t)p->n_swp * 4),
+               o_T = A.take((size_t)(d->n_fwd + 1) * 8), o_P = A.take((size_t)(d->n_fwd + 1) * 8);
+  void* dbuf = nullptr;
+  unsigned char* hcs = nullptr;
+  double* hf = nullptr;
+  if (cudaMalloc(&dbuf, A.size) != cudaSuccess || cudaMallocHost((void**)&hcs, (size_t)C * csz) != cudaSuccess ||
+      cudaMallocHost((void**)&hf, (size_t)C * 8) != cudaSuccess) {
+    if (dbuf) cudaFree(dbuf);
+    if (hcs) cudaFreeHost(hcs);
+    sabr_lmm_mc_plan_free(p);
+    return fail(SABR_LMM_ENOMEM, "mc_anneal: allocation of the search buffers failed");
+  }
+  char* b = (char*)dbuf;
+  auto cleanup = [&]() {
+    cudaFree(dbuf);
+    cudaFreeHost(hcs);
+    cudaFreeHost(hf);
+    sabr_lmm_mc_plan_free(p);
+  };
+  std::vector<double> vol_sorted(ni);
+  std::vector<int> cf_sorted(p->n_cap), sa_sorted(p->n_swp);
+  for (int c = 0; c < p->n_cap; ++c) {
+    vol_sorted[c] = quote_vol[p->cap_order[c]];
+    cf_sorted[c] = d->cap_fwd[p->cap_order[c]];
+  }
+  for (int c = 0; c < p->n_swp; ++c) {
+    vol_sorted[p->n_cap + c] = quote_vol[p->n_cap + p->swp_order[c]];
+    sa_sorted[c] = d->swp_start[p->swp_order[c]];
+  }
+  cudaError_t e = cudaSuccess;
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b + off, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  put(o_vol, vol_sorted.data(), ni * 8);
+  put(o_cf, cf_sorted.data(), p->n_cap * 4);
+  put(o_sa, sa_sorted.data(), p->n_swp * 4);
+  put(o_T, d->T, (d->n_fwd + 1) * 8);
+  put(o_P, d->P, (d->n_fwd + 1) * 8);
+  McArgs ab = p->args;
+  ab.part = (double*)(b + o_part);
+  ab.bad = (unsigned long long*)(b + o_bad);
+  if (e == cudaSuccess) {
+    mc_market_kernel<<<(ni + 127) / 128, 128, 0, s>>>(ab, (const double*)(b + o_T), (const double*)(b + o_P),
+                                                      (const int*)(b + o_cf), (const int*)(b + o_sa),
+                                                      (const double*)(b + o_vol), (double*)(b + o_mkt));
+    e = cudaGetLastError();
+  }
+  const size_t smb = f64 ? mc_batch_smem_bytes<double>(ni) : mc_batch_smem_bytes<float>(ni);
+  if (e == cudaSuccess)
+    e = f64 ? raise_smem_limit(mc_path_batch_kernel<double>, (uint32_t)smb)
+            : raise_smem_limit(mc_path_batch_kernel<float>, (uint32_t)smb);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(SABR_LMM_ECUDA, std::string("mc_anneal: ") + cudaGetErrorString(e));
+  }
+  // f_s of n points Y [n x 5]: constants on the host (threads), one batched launch, f back
+  const unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  auto evaluate = [&](const std::vector<double>& Y, int n, double* f) -> cudaError_t {
+    auto work = [&](int lo, int hi) {
+      for (int i = lo; i < hi; ++i) {
+        McConsts<double> c64;
+        McConsts<float> c32;
+        mc_build_consts(d, M, p->tau.data(), &Y[(size_t)i * P], c64, c32);
+        if (f64) std::memcpy(hcs + (size_t)i * csz, &c64, csz);
+        else std::memcpy(hcs + (size_t)i * csz, &c32, csz);
+      }
+    };
+    std::vector<std::thread> th;
+    const int per = (n + (int)nthr - 1) / (int)nthr;
+    for (int t = 0; t * per < n; ++t) th.emplace_back(work, t * per, std::min(n, (t + 1) * per));
+    for (auto& t : th) t.join();
+    cudaError_t ee = cudaMemcpyAsync(b + o_cs, hcs, (size_t)n * csz, cudaMemcpyHostToDevice, s);
+    if (ee != cudaSuccess) return ee;
+    const dim3 grid(G, n);
+    if (f64) mc_path_batch_kernel<double><<<grid, kMcThreads, smb, s>>>(ab, (const McConsts<double>*)(b + o_cs));
+    else mc_path_batch_kernel<float><<<grid, kMcThreads, smb, s>>>(ab, (const McConsts<float>*)(b + o_cs));
+    mc_objective_kernel<<<(n + 3) / 4, 128, 0, s>>>(ab, G, n, (const double*)(b + o_mkt), (double*)(b + o_f));
+    if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
+    if ((ee = cudaMemcpyAsync(hf, b + o_f, (size_t)n * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return ee;
+    if ((ee = cudaStreamSynchronize(s)) != cudaSuccess) return ee;
+    for (int i = 0; i < n; ++i) f[i] = (hf[i] == hf[i]) ? hf[i] : HUGE_VAL;
+    return cudaSuccess;
+  };
+  const auto t_start = std::chrono::steady_clock::now();
+  // the annealing loop of Section 3 (as in the closed-form search): chains from a shared start
+  // point, the best end point starts the next level, the best point ever accepted is returned
+  std::vector<double> x0(P);
+  for (int k = 0; k < P; ++k) x0[k] = o->y0 ? o->y0[k] : 0.5 * (o->lo[k] + o->hi[k]);
+  double f0 = 0.0;
+  if ((e = evaluate(x0, 1, &f0)) != cudaSuccess) {
+    cleanup();
+    return fail(SABR_LMM_ECUDA, std::string("mc_anneal: ") + cudaGetErrorString(e));
+  }
+  const double T0 = o->T0 > 0.0 ? o->T0 : ((std::isfinite(f0) && f0 > 0.0) ? f0 : 1.0);
+  std::vector<double> xs = x0, X((size_t)C * P), Y((size_t)C * P), xb((size_t)C * P), fx(C), fy(C), fb(C, f0);
+  for (int c = 0; c < C; ++c) std::copy(x0.begin(), x0.end(), xb.begin() + (size_t)c * P);
+  double fs = f0, T = T0;
+  std::vector<double> u(P + 1);
+  for (int l = 0; l < L; ++l) {
+    const double sf = std::max(o->step_frac * std::sqrt(T / T0), o->step_floor);
+    for (int c = 0; c < C; ++c) {
+      std::copy(xs.begin(), xs.end(), X.begin() + (size_t)c * P);
+      fx[c] = fs;
+    }
+    for (int st2 = 0; st2 < N; ++st2) {
+      std::vector<double> uacc(C);
+      for (int c = 0; c < C; ++c) {
+        sa_step_uniforms(o->seed, (uint64_t)c, l, st2, P + 1, u.data());
+        for (int k = 0; k < P; ++k) {
+          const double xk = X[(size_t)c * P + k];
+          double v = xk;
+          if (o->free_mask[k]) {
+            v = xk + sf * (o->hi[k] - o->lo[k]) * (2.0 * u[k] - 1.0);
+            if (v < o->lo[k]) v = 2.0 * o->lo[k] - v;
+            if (v > o->hi[k]) v = 2.0 * o->hi[k] - v;
+            v = std::min(std::max(v, o->lo[k]), o->hi[k]);
+          }
+          Y[(size_t)c * P + k] = v;
+        }
+        uacc[c] = u[P];
+      }
+      if ((e = evaluate(Y, C, fy.data())) != cudaSuccess) {
+        cleanup();
+        return fail(SABR_LMM_ECUDA, std::string("mc_anneal: ") + cudaGetErrorString(e));
+      }
+      for (int c = 0; c < C; ++c) {
+        const bool acc = (fy[c] < fx[c]) || (uacc[c] < std::exp(-(fy[c] - fx[c]) / T));
+        if (!acc) continue;
+        std::copy(Y.begin() + (size_t)c * P, Y.begin() + (size_t)(c + 1) * P, X.begin() + (size_t)c * P);
+        fx[c] = fy[c];
+        if (fx[c] < fb[c]) {
+          fb[c] = fx[c];
+          std::copy(X.begin() + (size_t)c * P, X.begin() + (size_t)(c + 1) * P, xb.begin() + (size_t)c * P);
+        }
+      }
+    }
+    int best = 0;
+    for (int c = 1; c < C; ++c)
+      if (fx[c] < fx[best]) best = c;
+    std::copy(X.begin() + (size_t)best * P, X.begin() + (size_t)(best + 1) * P, xs.begin());
+    fs = fx[best];
+    if (out->trace_f) out->trace_f[l] = fs;
+    if (out->trace_y) std::copy(xs.begin(), xs.end(), out->trace_y + (size_t)l * P);
+    T *= o->cooling;
+  }
+  int best = 0;
+  for (int c = 1; c < C; ++c)
+    if (fb[c] < fb[best]) best = c;
+  for (int k = 0; k < P; ++k) out->y_best[k] = xb[(size_t)best * P + k];
+  out->f_best = fb[best];
+  out->T0_used = T0;
+  out->n_evals = (int64_t)C * ((int64_t)L * N) + 1;
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  cleanup();
   return SABR_LMM_OK;
 }

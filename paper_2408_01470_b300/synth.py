@@ -472,3 +472,30 @@ def paper_hagan_mc_model(path: str, mm_path: str, mc_path: str):
                  phi=hp[:, 1].copy())
     rows = np.array([[float(x) for x in r] for r in mc["mc_timings"]])
     return sk, model, sk.cap_fwd.copy(), sk.cap_K.copy(), rows
+
+
+def paper_swaption_smiles(path: str, mm_path: str, swp_path: str):
+    """The 180 swaptions of the paper's real-data test (Table tab:smilesTS: maturities 21/05/2012 ..
+    21/11/2013, the fixings of the first four forwards, swaps of 1 .. 5 years, nine moneyness
+    levels) on the 13-forward tenor structure of paper_euribor_mm_market: payer swaption on the
+    forwards [a, a + 2 x years) with strike K = S e^m, S = (P(0, T_a) - P(0, T_b)) / sum tau_k
+    P(0, T_{k+1}) the forward swap rate (input preparation: the swap rate's definition).
+    Returns (skeleton, swp_start, swp_end, swp_K, quote vols [180], published figures)."""
+    import datetime as _dt
+    sk, _, _, _, _ = paper_euribor_mm_market(path, mm_path)
+    d = read_paper_market(swp_path)
+    fix_dates = [r[0] for r in read_paper_market(path)["smiles"]]
+    m = np.array([float(x) / 100.0 for x in d["moneyness"][0]])
+    T, P = sk.T, sk.P
+    sa, sb, sK, vol = [], [], [], []
+    for row in d["smiles"]:
+        years = int(row[0])
+        dd, mo, yy = (int(x) for x in row[1].split("/"))
+        key = _dt.date(yy, mo, dd).strftime("%d-%m-%y")
+        a = fix_dates.index(key)
+        b = a + 2 * years
+        A = sum((T[k + 1] - T[k]) * P[k + 1] for k in range(a, b))
+        S = (P[a] - P[b]) / A
+        for mk, v in zip(m, row[2:]):
+            sa.append(a); sb.append(b); sK.append(S * np.exp(mk)); vol.append(float(v) / 100.0)
+    return (sk, np.array(sa, np.int32), np.array(sb, np.int32), np.array(sK), np.array(vol), d["published"])

@@ -155,3 +155,67 @@ def test_mc_rejects_bad_input(gpu_lib):
     with pytest.raises(lib.SabrLmmError) as e:
         lib.mc_price(sk20.T, sk20.P, m20, [17], [0.03], n_paths=10)
     assert e.value.status == 5 and "16 forwards" in str(e.value)
+
+
+# ---------------------------------------------------------------- SA over the Monte Carlo objective
+def _self_quoted(M=6, n_paths=2000, dt=0.05, seed=5):
+    """Payer swaptions on the paper's first M forwards, quoted at the Black vols that reproduce the
+    oracle's Monte Carlo prices at the paper's correlation parameters (root-finding on Black)."""
+    from scipy.optimize import brentq
+    sk, model, _, _, _ = _paper()
+    om = oracle.Market(sk, np.full(sk.n_cap, 0.5))
+    P, T = sk.P, sk.T
+    tau = np.diff(T)
+    m6 = dict(model, M=M)
+    sa, sb, sK = [], [], []
+    for a in (0, 1, 2):
+        for b in (a + 2, a + 4):
+            A = sum(tau[j] * P[j + 1] for j in range(a, b))
+            S = (P[a] - P[b]) / A
+            for mny in (0.8, 1.0, 1.25):
+                sa.append(a); sb.append(b); sK.append(S * mny)
+    pr, _, _ = oracle.mc_price(om, m6, swp_a=sa, swp_b=sb, swp_K=sK, n_paths=n_paths, dt=dt, seed=seed, n_threads=16)
+    qv = []
+    for k in range(len(sa)):
+        a, b = sa[k], sb[k]
+        A = sum(tau[j] * P[j + 1] for j in range(a, b))
+        S = (P[a] - P[b]) / A
+        qv.append(brentq(lambda v: oracle.black_call(S, sK[k], T[a], v, A) - pr[k], 1e-4, 5.0, xtol=1e-15))
+    return sk, om, m6, np.array(sa), np.array(sb), np.array(sK), np.array(qv)
+
+
+def test_mc_anneal_fp64_matches_the_oracle(gpu_lib):
+    # the same search on both sides: FP64 paths equal to the oracle's (f_s to rounding order), the
+    # same proposals and Metropolis decisions, so the same trace and result
+    import paper_2408_01470_b300 as lib
+    sk, om, m6, sa, sb, sK, qv = _self_quoted()
+    lo, hi = np.zeros(5), np.array([1.0, 5.0, 1.0, 5.0, 0.5])
+    kw = dict(n_paths=2000, dt=0.05, mc_seed=5)
+    ro = oracle.mc_anneal(om, m6, qv, lo, hi, np.ones(5), 8, 3, 4, 0.7, 9, swp_a=sa, swp_b=sb, swp_K=sK,
+                          n_threads=16, **kw)
+    T6, P6 = sk.T[:7], sk.P[:7]
+    rg = lib.mc_anneal(T6, P6, m6, qv, lo, hi, np.ones(5), 8, 3, 4, 0.7, 9, swp_start=sa, swp_end=sb, swp_K=sK,
+                       prec="fp64", **kw)
+    assert rg["T0"] == pytest.approx(ro["T0"], rel=1e-10)
+    assert np.allclose(rg["trace_f"], ro["trace_f"], rtol=1e-9, atol=0)
+    assert np.allclose(rg["trace_y"], ro["trace_x"], rtol=1e-12, atol=1e-15)
+    assert np.allclose(rg["y_best"], ro["y_best"], rtol=1e-12, atol=1e-15)
+    assert rg["f_best"] == pytest.approx(ro["f_best"], rel=1e-9)
+    assert rg["n_evals"] == 8 * 3 * 4 + 1
+
+
+def test_mc_anneal_fp32_descends(gpu_lib):
+    # FP32 paths, more chains and levels: the search ends far below its start and at a point the
+    # oracle's f_s (FP64, the same paths up to FP32 rounding) confirms
+    import paper_2408_01470_b300 as lib
+    sk, om, m6, sa, sb, sK, qv = _self_quoted()
+    lo, hi = np.zeros(5), np.array([1.0, 5.0, 1.0, 5.0, 0.5])
+    rg = lib.mc_anneal(sk.T[:7], sk.P[:7], m6, qv, lo, hi, np.ones(5), 64, 12, 8, 0.7, 3, swp_start=sa, swp_end=sb,
+                       swp_K=sK, n_paths=2000, dt=0.05, mc_seed=5, prec="fp32")
+    kw = dict(swp_a=sa, swp_b=sb, swp_K=sK, n_paths=2000, dt=0.05, mc_seed=5)
+    f_c = oracle.mc_objective(om, m6, 0.5 * (lo + hi), qv, **kw)
+    f_o = oracle.mc_objective(om, m6, rg["y_best"], qv, **kw)
+    print(f"MC anneal FP32: f_s {rg['f_best']:.3e} (oracle at the point {f_o:.3e}, box centre {f_c:.3e}), "
+          f"{rg['n_evals']} evaluations in {rg['seconds']:.2f} s")
+    assert rg["f_best"] <= 0.02 * f_c
+    assert f_o <= 0.02 * f_c
