@@ -182,3 +182,23 @@ def test_mm_paper_calibration_hybrid_search(gpu_lib):
     print(f"MM paper calibration: f {r['f_best'][0]:.6e} (printed parameters {om.objective(pr):.6e}), "
           f"MRE {mre:.4e}, search {r['seconds']:.3f} s")
     assert mre <= 3.11e-2 * 1.03
+
+
+def test_mm_noalloc_refuses_wide_markets(gpu_lib):
+    # the fixed state array of sabr_lmm_anneal_noalloc holds 12 slots a chain: a 27-slot market is ENOTSUP
+    import ctypes as C
+    import paper_2408_01470_b300 as lib
+    sk = CASES["mm_13x9_paper"]()
+    om, gm, _ = _markets(sk)
+    L = lib.load()
+    fn = L.sabr_lmm_anneal_noalloc
+    fn.argtypes = [C.c_void_p, C.c_int32, C.POINTER(lib.AnnealOpts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    o, keep = gm._opts(64, 2, 2, 0.9, 1, "fp32", 0.0, 0.1, 1e-3, None, 0, 50, 0.0, 0, False, False)
+    st = fn(gm.h, 0, C.byref(o), None, None, None, None)
+    assert st == 1   # x_best / f_best missing: EINVAL before anything else
+    import torch
+    x = torch.zeros(sk.n_param, dtype=torch.float64, device="cuda")
+    f = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = fn(gm.h, 0, C.byref(o), C.c_void_p(x.data_ptr()), C.c_void_p(f.data_ptr()), None, None)
+    assert st == 5 and "12 parameter slots" in L.sabr_lmm_last_error().decode()
+    del keep
