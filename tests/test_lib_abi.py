@@ -101,3 +101,64 @@ def test_quad_nodes_other_than_8_not_supported(lib):
     d, keep = _desc(sk, quad_nodes=6)
     h = C.c_void_p()
     assert lib.sabr_lmm_load_market(C.byref(d), 1, None, C.byref(h)) == 5
+
+
+def test_mercurio_morini_shapes_validated_before_any_cuda_call(lib):
+    # 2 n_fwd + 1 slots, at most 15 forwards, caplets only
+    from paper_2408_01470_b300 import synth
+    sk = synth.mercurio_morini_caplets()
+    h = C.c_void_p()
+    d, keep = _desc(sk, n_param=sk.n_param - 1)
+    assert lib.sabr_lmm_load_market(C.byref(d), 1, None, C.byref(h)) == 1
+    assert "2 n_fwd + 1" in lib.sabr_lmm_last_error().decode()
+    wide = synth.mercurio_morini_caplets(n_fwd=16, n_strikes=2)
+    d, keep = _desc(wide)
+    assert lib.sabr_lmm_load_market(C.byref(d), 1, None, C.byref(h)) == 1
+    assert "15 forwards" in lib.sabr_lmm_last_error().decode()
+
+
+def _mc_desc(**over):
+    import paper_2408_01470_b300 as pkg
+    from paper_2408_01470_b300 import synth
+    sk = synth.caplet_term_structure(n_fwd=6)
+    model = dict(beta=0.5, eta1=0.8, lambda1=1.0, eta2=0.9, lambda2=1.0, lambda3=0.01, alpha=np.full(6, 0.2),
+                 sigma=np.full(6, 0.3), phi=np.full(6, -0.3))
+    model.update(over)
+    return pkg.mc_describe(sk.T, sk.P, model, cap_fwd=[0, 3], cap_K=[0.01, 0.02], swp_start=[1], swp_end=[4],
+                           swp_K=[0.02])
+
+
+@pytest.mark.parametrize("over,opts,msg", [
+    (dict(eta1=1.5), {}, "eta1"), (dict(beta=2.0), {}, "beta"), (dict(alpha=np.zeros(6)), {}, "alpha"),
+    ({}, dict(n_paths=0), "n_paths"), ({}, dict(dt=0.0), "dt"), ({}, dict(prec=3), "prec")])
+def test_mc_prepare_validates_before_any_cuda_call(lib, over, opts, msg):
+    import paper_2408_01470_b300 as pkg
+    d, keep = _mc_desc(**over)
+    kw = dict(n_paths=100, dt=0.01, seed=1, prec=1, grid=0)
+    kw.update(opts)
+    o = pkg.McOpts()
+    o.n_paths, o.dt, o.seed, o.prec, o.grid = kw["n_paths"], kw["dt"], kw["seed"], kw["prec"], kw["grid"]
+    h = C.c_void_p()
+    assert lib.sabr_lmm_mc_prepare(C.byref(d), C.byref(o), None, C.byref(h)) == 1
+    assert msg in lib.sabr_lmm_last_error().decode()
+    assert h.value is None
+
+
+def test_mc_anneal_validates_its_box_before_any_cuda_call(lib):
+    import paper_2408_01470_b300 as pkg
+    d, keep = _mc_desc()
+    o = pkg.McOpts()
+    o.n_paths, o.dt, o.seed, o.prec, o.grid = 100, 0.01, 1, 1, 0
+    lo, hi = np.zeros(5), np.array([1.0, 5.0, 1.0, 5.0, 0.5])
+    bad_hi = hi.copy()
+    bad_hi[0] = 1.5   # eta1 above 1
+    fr = np.ones(5, np.uint8)
+    qv = np.full(3, 0.3)
+    for h_arr in (bad_hi,):
+        a = pkg.McAnnealOpts()
+        a.n_chains, a.n_levels, a.steps_per_level, a.cooling, a.step_frac, a.step_floor = 4, 2, 2, 0.9, 0.1, 1e-3
+        a.lo, a.hi = lo.ctypes.data_as(pkg._D), h_arr.ctypes.data_as(pkg._D)
+        a.free_mask = fr.ctypes.data_as(pkg._U8)
+        r = pkg.McAnnealResult()
+        st = lib.sabr_lmm_mc_anneal(C.byref(d), qv.ctypes.data_as(pkg._D), C.byref(o), C.byref(a), C.byref(r), None)
+        assert st == 1 and "box" in lib.sabr_lmm_last_error().decode()
