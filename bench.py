@@ -221,16 +221,17 @@ WORKLOADS = {
 PREC_DTYPE = {"fp32": "f32", "fp64": "f64", "bf16x3": "f32+bf16x3"}
 
 
-def workload_markets(lib, name):
-    """(Market, skeletons, quotes list, chains, levels, steps, cooling) of a named workload.  The
-    quotes are the library's own FP64 model vols at the generating point plus the noise draws."""
+def workload_markets(lib, name, markets=0):
+    """(Market, skeletons, quotes list, chains, levels, steps, cooling) of a named workload (the
+    batch: its first `markets` markets when markets > 0).  The quotes are the library's own FP64
+    model vols at the generating point plus the noise draws."""
     from paper_2408_01470_b300 import synth
     if name == "caplets":
         sks = [synth.caplet_term_structure()]
     elif name == "joint":
         sks = [synth.joint_caplet_swaption()]
     else:
-        sks = [synth.batch_market(j) for j in range(256)]
+        sks = [synth.batch_market(j) for j in range(markets if markets > 0 else 256)]
     vols = []
     for sk in sks:
         placeholder = lib.Market(sk, np.full(sk.n_instr, 0.2))
@@ -628,25 +629,33 @@ def run_quality(args):
     import paper_2408_01470_b300 as lib
     import torch
     lib.load()
-    gm, sks, vols, C, L, N, cool = workload_markets(lib, args.workload)
+    gm, sks, vols, C, L, N, cool = workload_markets(lib, args.workload, args.markets)
     C = args.chains or C
+    nm = len(sks)
     rows = []
     for k in range(args.seeds):
         seed = 240801470 + 7919 * k
         row = {"seed": seed}
         for prec in ("fp64", "fp32"):
             r = gm.anneal(C, L, N, cool, seed, prec=prec)
-            # the adjoint-driven Levenberg-Marquardt polish of the search's best point (FP64)
+            # the adjoint-driven Levenberg-Marquardt polish of each market's best point (FP64)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Xp, fp, rp = gm.lm_polish(r["x_best"], max_iter=50)
-            rp = float(rp.cpu().numpy()[0])
+            rps = []
+            for j in range(nm):
+                Xp, fp, rp = gm.lm_polish(r["x_best"][j:j + 1], max_iter=50, market=j)
+                rps.append(float(rp.cpu().numpy()[0]))
             tp = time.perf_counter() - t0
-            row[prec] = {"rmse_volpt": float(r["rmse_volpt"][0]), "seconds": float(r["seconds"]),
-                         "polished_rmse_volpt": rp, "polish_s": tp}
+            # batches: the mean over the markets of each market's final vol RMSE
+            row[prec] = {"rmse_volpt": float(np.mean(r["rmse_volpt"][:nm])), "seconds": float(r["seconds"]),
+                         "polished_rmse_volpt": float(np.mean(rps)), "polish_s": tp}
+            if nm > 1:
+                row[prec]["per_market_rmse_volpt"] = [float(x) for x in r["rmse_volpt"][:nm]]
+                row[prec]["per_market_polished_rmse_volpt"] = rps
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
-    out = {"quality": True, "workload": args.workload, "chains": C, "levels": L, "steps": N, "seeds": args.seeds}
+    out = {"quality": True, "workload": args.workload, "chains": C, "levels": L, "steps": N, "seeds": args.seeds,
+           "markets": nm}
     for key in ("rmse_volpt", "polished_rmse_volpt"):
         a64 = np.array([r["fp64"][key] for r in rows])
         a32 = np.array([r["fp32"][key] for r in rows])
@@ -719,6 +728,7 @@ def main():
     ap.add_argument("--quality", action="store_true",
                     help="FP32 against FP64 final RMSE over --seeds seeds of --workload (one JSON line)")
     ap.add_argument("--seeds", type=int, default=8)
+    ap.add_argument("--markets", type=int, default=0, help="with --quality --workload batch: the first K markets")
     ap.add_argument("--levels", type=int, default=0, help="with --profile: temperature levels (0 = workload's)")
     ap.add_argument("--chains", type=int, default=0, help="with --profile / --quality: chains per market")
     ap.add_argument("--lm-top-k", type=int, default=0,
