@@ -101,14 +101,14 @@ def _lib_handle():
             lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
             lib.orc_mc_normals4.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int, _D]
             _I = C.POINTER(C.c_int32)
-            _MCI = [C.c_void_p, C.c_int, _D, _D, _D, _D, C.c_int, _I, _D, C.c_int, _I, _I, _D, _D, C.c_int64,
+            _MCI = [C.c_void_p, C.c_int, C.c_int, _D, _D, _D, _D, C.c_int, _I, _D, C.c_int, _I, _I, _D, _D, C.c_int64,
                     C.c_double, C.c_uint64]
             lib.orc_mc_objective.restype = C.c_double
             lib.orc_mc_objective.argtypes = _MCI + [_D, C.c_int]
             lib.orc_mc_anneal.restype = C.c_int
             lib.orc_mc_anneal.argtypes = _MCI + [_D, _D, C.POINTER(C.c_uint8), C.POINTER(_SAOpts), _D, _D, _D, _D, _D]
             lib.orc_mc_price.restype = C.c_int
-            lib.orc_mc_price.argtypes = [C.c_void_p, C.c_int, _D, _D, _D, _D, C.c_int, _I, _D, C.c_int, _I, _I,
+            lib.orc_mc_price.argtypes = [C.c_void_p, C.c_int, C.c_int, _D, _D, _D, _D, C.c_int, _I, _D, C.c_int, _I, _I,
                                          _D, C.c_int64, C.c_double, C.c_uint64, C.c_int, _D, _D,
                                          C.POINTER(C.c_int64)]
             lib.orc_step_uniforms.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int, _D]
@@ -351,9 +351,10 @@ class Market:
 
 def mc_price(market, model, cap_fwd=(), cap_K=(), swp_a=(), swp_b=(), swp_K=(), n_paths=1000, dt=0.01,
              seed=1, n_threads=1):
-    """Monte Carlo prices of caplets and swaptions under the Hagan SABR/LIBOR model (see
-    sabr_oracle.cpp mc_price) on `market`'s tenor structure.  model: dict with M, beta, eta1,
-    lambda1, eta2, lambda2, lambda3 and per-forward alpha, sigma, phi.  Returns (price, stderr,
+    """Monte Carlo prices of caplets and swaptions under the Hagan SABR/LIBOR model, or with
+    model["model"] = 2 the Mercurio & Morini one (see sabr_oracle.cpp mc_price), on `market`'s
+    tenor structure.  model: dict with M, beta, eta1, lambda1, eta2, lambda2, lambda3 and per-forward
+    alpha, sigma, phi (Mercurio & Morini: sigma[0] is the common vol of vol, phi_i = corr(W_i, Z)).  Returns (price, stderr,
     n_bad), n_bad the paths stopped at a non-finite state, or None on a bad input."""
     M = int(model["M"])
     par = _f64([model["beta"], model["eta1"], model["lambda1"], model["eta2"], model["lambda2"], model["lambda3"]])
@@ -367,7 +368,7 @@ def mc_price(market, model, cap_fwd=(), cap_K=(), swp_a=(), swp_b=(), swp_K=(), 
     price, sq = np.zeros(max(ni, 1)), np.zeros(max(ni, 1))
     nb = C.c_int64(0)
     _I = C.POINTER(C.c_int32)
-    rc = market._lib.orc_mc_price(market.h, M, _dp(par), _dp(al), _dp(sg), _dp(ph), len(cf), cf.ctypes.data_as(_I),
+    rc = market._lib.orc_mc_price(market.h, M, int(model.get("model", 0)), _dp(par), _dp(al), _dp(sg), _dp(ph), len(cf), cf.ctypes.data_as(_I),
                                   _dp(ck), len(sa), sa.ctypes.data_as(_I), sb.ctypes.data_as(_I), _dp(sk),
                                   int(n_paths), float(dt), int(seed), int(n_threads), _dp(price), _dp(sq),
                                   C.byref(nb))
@@ -386,7 +387,7 @@ def _mc_args(market, model, cap_fwd, cap_K, swp_a, swp_b, swp_K, quote_vol):
                 cf=np.ascontiguousarray(cap_fwd, np.int32), ck=_f64(cap_K), sa=np.ascontiguousarray(swp_a, np.int32),
                 sb=np.ascontiguousarray(swp_b, np.int32), sk=_f64(swp_K), qv=_f64(quote_vol))
     _I = C.POINTER(C.c_int32)
-    args = [market.h, M, _dp(keep["par"]), _dp(keep["al"]), _dp(keep["sg"]), _dp(keep["ph"]), len(keep["cf"]),
+    args = [market.h, M, int(model.get("model", 0)), _dp(keep["par"]), _dp(keep["al"]), _dp(keep["sg"]), _dp(keep["ph"]), len(keep["cf"]),
             keep["cf"].ctypes.data_as(_I), _dp(keep["ck"]), len(keep["sa"]), keep["sa"].ctypes.data_as(_I),
             keep["sb"].ctypes.data_as(_I), _dp(keep["sk"]), _dp(keep["qv"])]
     return args, keep

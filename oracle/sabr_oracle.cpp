@@ -55,6 +55,10 @@
 //                                    and a zero-strike swaption P(0,T_a) - P(0,T_b) under any
 //                                    arbitrage-free dynamics; with sigma = 0, beta = 1 every caplet
 //                                    is Black's at vol alpha_i (the lognormal LIBOR market model).
+//   mc_price, model 2 .............. the Mercurio & Morini dynamics (Section 2.2) under the spot
+//                                    measure, one vol process.  Pins: the zero-strike floating legs;
+//                                    sigma = 0, beta = 1 gives Black at alpha_i; the vol of vol
+//                                    lifts far out-of-the-money caplets above Black.
 //   mc_objective, orc_mc_anneal .... the swaption calibration of Section 3 over the Monte Carlo
 //                                    objective (common random numbers), by the same annealing
 //                                    loop.  Pins: f_s = 0 at the generating correlation parameters
@@ -664,15 +668,38 @@ static void mc_normals4(uint64_t seed, uint64_t path, int step, int b, double* z
 // price[k] = mean over all paths of the deflated payoff; sq[k] = mean of its square.
 struct McModel {
   int M;                       // forwards simulated
+  int model = 0;               // 0: Hagan (Section 2.1); 2: Mercurio & Morini (Section 2.2)
   double beta, eta1, lambda1, eta2, lambda2, lambda3;
-  std::vector<double> alpha, sigma, phi;   // per forward: V_i(0), vol of vol, phi_ii
+  std::vector<double> alpha, sigma, phi;   // per forward: V_i(0), vol of vol, phi_ii (Hagan);
+                                           // alpha_i, the common sigma (sigma[0]), phi_i (MM)
 };
 
+// The Mercurio & Morini dynamics (Section 2.2, Eqs. dinamicasMercurio1-2) under the spot measure:
+//   dF_i = mu^F_i dt + alpha_i V F_i^b dW_i,  dV = sigma V dZ,  V(0) = 1,
+//   mu^F_i = alpha_i V F_i^b sum_{j = h(t)}^{i} tau_j rho_ij alpha_j V F_j^b / (1 + tau_j F_j),
+// corr(W_i, W_j) = rho_ij of Eq. (rhoij), corr(W_i, Z) = phi_i; V has no drift (as printed).  The
+// increments are L xi with L the Cholesky factor of the correlation matrix ordered Z first, then
+// the forwards last first (row 0 is Z, row 1 + (M - 1 - i) is W_i): the alive forwards again lead.
+
 static bool mc_cholesky(const Market& m, const McModel& md, std::vector<double>& L, std::vector<double>& C) {
-  const int n = 2 * md.M;
+  const bool mm = md.model == 2;
+  const int n = mm ? md.M + 1 : 2 * md.M;
   C.assign((size_t)n * n, 0.0);
   auto fwd = [&](int r) { return md.M - 1 - r / 2; };
-  for (int r = 0; r < n; ++r)
+  if (mm) {
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) {
+        double v;
+        if (r == 0 && c == 0) v = 1.0;
+        else if (r == 0 || c == 0) v = md.phi[md.M - 1 - (r + c - 1)];      // corr(W_i, Z) = phi_i
+        else {
+          const int i = md.M - r, j = md.M - c;                               // row 1 + (M - 1 - i)
+          v = md.eta1 + (1.0 - md.eta1) * std::exp(-md.lambda1 * std::fabs(m.T[i] - m.T[j]));
+        }
+        C[(size_t)r * n + c] = v;
+      }
+  }
+  for (int r = 0; r < n && !mm; ++r)
     for (int c = 0; c < n; ++c) {
       const int i = fwd(r), j = fwd(c);
       const bool wi = (r % 2) == 0, wj = (c % 2) == 0;
@@ -766,11 +793,14 @@ static bool mc_cholesky(const Market& m, const McModel& md, std::vector<double>&
 static int mc_price(const Market& m, const McModel& md, int n_cap, const int* cap_fwd, const double* cap_K,
                     int n_swp, const int* swp_a, const int* swp_b, const double* swp_K, int64_t n_paths, double dt,
                     uint64_t seed, int n_threads, double* price, double* sq, int64_t* n_bad) {
-  const int M = md.M, n = 2 * M, ni = n_cap + n_swp;
+  const bool mm = md.model == 2;
+  const int M = md.M, n = mm ? M + 1 : 2 * M, ni = n_cap + n_swp;
   std::vector<double> L, Cr;
   if (!mc_cholesky(m, md, L, Cr)) return 1;
   // the correlations the drifts use: those of the (repaired) matrix the increments are drawn from
-  auto rho = [&](int i, int j) { return Cr[(size_t)(2 * (M - 1 - i)) * n + 2 * (M - 1 - j)]; };
+  auto rho = [&](int i, int j) {
+    return mm ? Cr[(size_t)(M - i) * n + (M - j)] : Cr[(size_t)(2 * (M - 1 - i)) * n + 2 * (M - 1 - j)];
+  };
   auto phi = [&](int i, int j) { return Cr[(size_t)(2 * (M - 1 - i)) * n + 2 * (M - 1 - j) + 1]; };
   // the time grid: interval k ends at T_k
   std::vector<int> nsteps(M);
@@ -793,17 +823,34 @@ static int mc_price(const Market& m, const McModel& md, int n_cap, const int* ca
     std::vector<char> good(M);
 #pragma omp for schedule(static)
     for (int64_t p = 0; p < n_paths; ++p) {
-      for (int i = 0; i < M; ++i) { F[i] = m.F[i]; lnV[i] = std::log(md.alpha[i]); }
+      for (int i = 0; i < M; ++i) { F[i] = m.F[i]; lnV[i] = mm ? 0.0 : std::log(md.alpha[i]); }
       int step = 0;
       for (int k = 0; k < K_end; ++k) {      // interval k: forwards k .. M-1 alive (h(t) = k)
         const double h = (m.T[k] - (k == 0 ? 0.0 : m.T[k - 1])) / nsteps[k];
-        const int na = 2 * (M - k);          // alive rows of L
+        const int na = mm ? 1 + (M - k) : 2 * (M - k);   // alive rows of L
         for (int s = 0; s < nsteps[k]; ++s, ++step) {
           for (int b = 0; 4 * b < na; ++b) mc_normals4(seed, (uint64_t)p, step, b, &xi[4 * b]);
           for (int r = 0; r < na; ++r) {
             double z = 0.0;
             for (int c = 0; c <= r; ++c) z += L[(size_t)r * n + c] * xi[c];
             Z[r] = z;
+          }
+          if (mm) {   // the Mercurio & Morini step: one vol process for every forward
+            const double Vc = std::exp(lnV[0]);
+            for (int i = k; i < M; ++i)
+              x[i] = m.tau[i] * md.alpha[i] * std::pow(F[i], md.beta) / (1.0 + m.tau[i] * F[i]);
+            for (int i = k; i < M; ++i) {
+              double dF = 0.0;
+              for (int j = k; j <= i; ++j) dF += rho(i, j) * x[j];
+              DF[i] = dF;
+            }
+            for (int i = k; i < M; ++i) {
+              const double vf = md.alpha[i] * Vc * std::pow(F[i], md.beta);   // alpha_i V F_i^b
+              const double fn = F[i] + vf * Vc * DF[i] * h + vf * std::sqrt(h) * Z[M - i];
+              F[i] = fn > 0.0 ? fn : 0.0;
+            }
+            lnV[0] += -0.5 * md.sigma[0] * md.sigma[0] * h + md.sigma[0] * std::sqrt(h) * Z[0];
+            continue;
           }
           for (int i = k; i < M; ++i) V[i] = std::exp(lnV[i]);
           for (int i = k; i < M; ++i)
@@ -828,7 +875,7 @@ static int mc_price(const Market& m, const McModel& md, int n_cap, const int* ca
         bool fin = true;
         for (int i = k; i < M; ++i) {
           snap[k][i] = F[i];   // the forwards at T_k
-          fin = fin && std::isfinite(F[i]) && std::isfinite(lnV[i]);
+          fin = fin && std::isfinite(F[i]) && std::isfinite(lnV[mm ? 0 : i]);
         }
         good[k] = fin && (k == 0 || good[k - 1]);
         fix[k] = snap[k][k];
@@ -1309,12 +1356,12 @@ void orc_mc_normals4(uint64_t seed, uint64_t path, int step, int b, double* z) {
 // Monte Carlo prices of caplets and swaptions on market mp's tenor structure (its first M forwards)
 // under the Hagan SABR/LIBOR model; params = [beta, eta1, lambda1, eta2, lambda2, lambda3] and the
 // per-forward alpha, sigma, phi_ii.  Returns 1 if the correlation matrix is not positive definite.
-int orc_mc_price(const void* mp, int M, const double* params, const double* alpha, const double* sigma,
+int orc_mc_price(const void* mp, int M, int model, const double* params, const double* alpha, const double* sigma,
                  const double* phi, int n_cap, const int* cap_fwd, const double* cap_K, int n_swp, const int* swp_a,
                  const int* swp_b, const double* swp_K, int64_t n_paths, double dt, uint64_t seed, int n_threads,
                  double* price, double* sq, int64_t* n_bad) {
   orc::McModel md;
-  md.M = M; md.beta = params[0]; md.eta1 = params[1]; md.lambda1 = params[2]; md.eta2 = params[3];
+  md.M = M; md.model = model; md.beta = params[0]; md.eta1 = params[1]; md.lambda1 = params[2]; md.eta2 = params[3];
   md.lambda2 = params[4]; md.lambda3 = params[5];
   md.alpha.assign(alpha, alpha + M); md.sigma.assign(sigma, sigma + M); md.phi.assign(phi, phi + M);
   return orc::mc_price(*(const orc::Market*)mp, md, n_cap, cap_fwd, cap_K, n_swp, swp_a, swp_b, swp_K, n_paths, dt,
@@ -1333,13 +1380,13 @@ int orc_anneal(const void* mp, const orc::SAOpts* o, double* x_best, double* f_b
 }
 
 // f_s at the correlation parameters y[5] (see mc_objective); quote_vol [n_cap + n_swp].
-double orc_mc_objective(const void* mp, int M, const double* params, const double* alpha, const double* sigma,
+double orc_mc_objective(const void* mp, int M, int model, const double* params, const double* alpha, const double* sigma,
                         const double* phi, int n_cap, const int* cap_fwd, const double* cap_K, int n_swp,
                         const int* swp_a, const int* swp_b, const double* swp_K, const double* quote_vol,
                         int64_t n_paths, double dt, uint64_t mc_seed, const double* y, int n_threads) {
   const orc::Market& m = *(const orc::Market*)mp;
   orc::McModel md;
-  md.M = M; md.beta = params[0];
+  md.M = M; md.model = model; md.beta = params[0];
   md.alpha.assign(alpha, alpha + M); md.sigma.assign(sigma, sigma + M); md.phi.assign(phi, phi + M);
   const orc::McTarget t = orc::mc_target(m, n_cap, cap_fwd, cap_K, n_swp, swp_a, swp_b, swp_K, quote_vol);
   return orc::mc_objective(m, md, t, y, n_paths, dt, mc_seed, n_threads);
@@ -1347,14 +1394,14 @@ double orc_mc_objective(const void* mp, int M, const double* params, const doubl
 
 // The annealing search of f_s over the box lo/hi/free_mask [5] (SAOpts as for orc_anneal; the
 // Monte Carlo of each evaluation single-threaded, the chains in parallel).
-int orc_mc_anneal(const void* mp, int M, const double* params, const double* alpha, const double* sigma,
+int orc_mc_anneal(const void* mp, int M, int model, const double* params, const double* alpha, const double* sigma,
                   const double* phi, int n_cap, const int* cap_fwd, const double* cap_K, int n_swp, const int* swp_a,
                   const int* swp_b, const double* swp_K, const double* quote_vol, int64_t n_paths, double dt,
                   uint64_t mc_seed, const double* lo, const double* hi, const uint8_t* freem, const orc::SAOpts* o,
                   double* y_best, double* f_best, double* trace_f, double* trace_x, double* T0_used) {
   const orc::Market& m = *(const orc::Market*)mp;
   orc::McModel md;
-  md.M = M; md.beta = params[0];
+  md.M = M; md.model = model; md.beta = params[0];
   md.alpha.assign(alpha, alpha + M); md.sigma.assign(sigma, sigma + M); md.phi.assign(phi, phi + M);
   const orc::McTarget t = orc::mc_target(m, n_cap, cap_fwd, cap_K, n_swp, swp_a, swp_b, swp_K, quote_vol);
   const orc::Box bx{5, lo, hi, freem};

@@ -499,3 +499,19 @@ def paper_swaption_smiles(path: str, mm_path: str, swp_path: str):
         for mk, v in zip(m, row[2:]):
             sa.append(a); sb.append(b); sK.append(S * np.exp(mk)); vol.append(float(v) / 100.0)
     return (sk, np.array(sa, np.int32), np.array(sb, np.int32), np.array(sK), np.array(vol), d["published"])
+
+
+def paper_mm_mc_model(path: str, mm_path: str):
+    """The paper's calibrated Mercurio & Morini model (Section 4.2) as the input of the Monte Carlo
+    pricer: the 13-forward tenor structure of paper_euribor_mm_market, alpha_i and phi_i of Table
+    tab:paramsMercurioVolas, the common sigma (sigma[i] = sigma for every forward), beta = 0.5, and
+    eta1, lambda1 of Section 4.2.2 (the other correlation fields are unused by the model).  Returns
+    (skeleton, model dict with model = 2)."""
+    sk, _, params, _, _ = paper_euribor_mm_market(path, mm_path)
+    mm = read_paper_market(mm_path)
+    corr = {r[0]: float(r[1]) for r in mm["correlation"]}
+    M = sk.n_fwd
+    model = dict(M=M, model=MODEL_MERCURIO_MORINI, beta=0.5, eta1=corr["eta1"], lambda1=corr["lambda1"], eta2=0.0,
+                 lambda2=0.0, lambda3=0.0, alpha=params[M + 1:].copy(), sigma=np.full(M, params[M]),
+                 phi=params[:M].copy())
+    return sk, model

@@ -147,3 +147,60 @@ def test_mc_anneal_descends_from_the_box_centre():
     assert r["f_best"] <= 0.05 * f_c
     assert r["f_best"] == pytest.approx(oracle.mc_objective(om, m6, r["y_best"], qv, **kw), rel=1e-14)
     assert np.all(r["y_best"] >= lo) and np.all(r["y_best"] <= hi)
+
+
+# ---------------------------------------------------------------- Mercurio & Morini dynamics
+def _mm_model():
+    return synth.paper_mm_mc_model(os.path.join(GOLDEN, "paper_euribor_20111121.txt"),
+                                   os.path.join(GOLDEN, "paper_mm_20111121.txt"))
+
+
+def test_mc_mm_zero_strike_instruments_are_the_floating_legs():
+    # the paper's calibrated Mercurio & Morini model (Section 4.2), one vol process for all forwards
+    sk, model = _mm_model()
+    om = oracle.Market(sk, np.full(sk.n_cap, 0.5))
+    P = sk.P
+    M = sk.n_fwd
+    swp_a, swp_b = [0, 2, 4, 0], [13, 10, 13, 1]
+    price, se, n_bad = oracle.mc_price(om, model, cap_fwd=np.arange(M), cap_K=np.zeros(M), swp_a=swp_a, swp_b=swp_b,
+                                       swp_K=np.zeros(4), n_paths=20000, dt=0.01, seed=6, n_threads=THREADS)
+    assert n_bad == 0
+    exact = np.concatenate([P[:M] - P[1:M + 1], [P[a] - P[b] for a, b in zip(swp_a, swp_b)]])
+    z = (price - exact) / se
+    assert np.max(np.abs(z)) < 4.5, z
+    assert price[-1] == pytest.approx(price[0], rel=1e-13)
+
+
+def test_mc_mm_lognormal_limit_is_black():
+    # sigma = 0 (V stays 1), beta = 1, phi_i = 0: dF_i = F_i (drift dt + alpha_i dW_i), Black at alpha_i
+    sk, model = _mm_model()
+    om = oracle.Market(sk, np.full(sk.n_cap, 0.5))
+    F = om.info()["F"]
+    M = sk.n_fwd
+    tau = np.diff(sk.T)
+    al = np.linspace(0.2, 0.4, M)
+    m2 = dict(model, beta=1.0, sigma=np.zeros(M), alpha=al, phi=np.zeros(M))
+    K = F * 1.1
+    price, se, n_bad = oracle.mc_price(om, m2, cap_fwd=np.arange(M), cap_K=K, n_paths=20000, dt=0.01, seed=7,
+                                       n_threads=THREADS)
+    bl = np.array([oracle.black_call(F[i], K[i], sk.T[i], al[i], tau[i] * sk.P[i + 1]) for i in range(M)])
+    z = (price - bl) / se
+    assert n_bad == 0 and np.max(np.abs(z)) < 4.5, z
+
+
+def test_mc_mm_vol_of_vol_fattens_the_tails():
+    # with beta = 1 and every phi_i = 0 the common vol process only mixes the lognormal variance:
+    # sigma > 0 raises the price of far out-of-the-money caplets above Black's at alpha_i (the
+    # same paths give Black within sampling error at sigma = 0, test above)
+    sk, model = _mm_model()
+    om = oracle.Market(sk, np.full(sk.n_cap, 0.5))
+    F = om.info()["F"]
+    M = sk.n_fwd
+    tau = np.diff(sk.T)
+    m2 = dict(model, beta=1.0, sigma=np.full(M, 0.8), alpha=np.full(M, 0.3), phi=np.zeros(M))
+    K = F * 2.5
+    price, se, _ = oracle.mc_price(om, m2, cap_fwd=np.arange(M), cap_K=K, n_paths=20000, dt=0.01, seed=8,
+                                   n_threads=THREADS)
+    bl = np.array([oracle.black_call(F[i], K[i], sk.T[i], 0.3, tau[i] * sk.P[i + 1]) for i in range(M)])
+    z = (price[1:] - bl[1:]) / se[1:]
+    assert np.all(z > 2.0) and np.mean(z) > 4.5, z
