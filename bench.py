@@ -553,6 +553,22 @@ def mc_record(lib, stream, peaks, cpu=True):
         big = (rec, nsteps)
         del plan
     rec, nsteps = big
+    # the Mercurio & Morini dynamics (one vol process, 1 + a normals a step) at the largest configuration
+    skm, mmod = synth.paper_mm_mc_model(PAPER_DATA, PAPER_MM)
+    plan = lib.McPlan(skm.T, skm.P, mmod, cf, ck, n_paths=rec["paths"], dt=rec["dt"], seed=20111121, prec="fp32",
+                      stream=stream)
+    plan.launch(stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(2):
+        plan.launch(stream)
+    b.record(stream)
+    stream.synchronize()
+    t = a.elapsed_time(b) / 1e3 / 2
+    out["mercurio_morini"] = {"paths": rec["paths"], "dt": rec["dt"], "seconds": t,
+                              "path_steps_per_s": rec["paths"] * rec["time_steps"] / t,
+                              "n_bad": int(plan.n_bad.item())}
+    del plan
     flops = mc_flops_per_path(sk.n_fwd, nsteps) * rec["paths"]
     out["roofline"] = roofline_alu(flops, rec["seconds"], peaks["fp32_tflops"], None, "mc_path_kernel<float>",
                                    "measured FP32 FMA rate (libsabr_peaks.so)")
@@ -570,21 +586,30 @@ def mc_record(lib, stream, peaks, cpu=True):
     return out
 
 
-def mc_calibration_record(lib, stream, chains=64, levels=20, steps=5, n_paths=10000, dt=0.02):
+def mc_calibration_record(lib, stream, chains=64, levels=20, steps=5, n_paths=10000, dt=0.02, model="hagan"):
     """The paper's swaption calibration of the Hagan model over a Monte Carlo objective (Section 4.1.2):
     the correlation parameters (eta1, lambda1, eta2, lambda2, lambda3) against the 180 swaptions of
     Table tab:smilesTS, the caplet-calibrated alpha_i, sigma_i, phi_ii of Table tab:paramsHaganVolas
     fixed; FP32 paths with common random numbers, every step's proposals of all chains in one launch.
     Reports the search's wall time (against the paper's ~2 hours on two GTX 470s: context), f_s, and
     the mean absolute error of the swaption prices in percent of the notional (the paper's MAE
-    6.19e-2; Black prices here with the annuity of the real accruals)."""
+    6.19e-2; Black prices here with the annuity of the real accruals).  model="mm": the same for the
+    Mercurio & Morini model of Section 4.2 (alpha_i, phi_i, sigma of Table tab:paramsMercurioVolas
+    fixed; eta1, lambda1 searched; the paper's MAE 5.50e-2)."""
     from paper_2408_01470_b300 import synth
     from scipy.special import ndtr
     sk, sa, sb, sK, vol, pub = synth.paper_swaption_smiles(PAPER_DATA, PAPER_MM, PAPER_SWP)
-    _, model, _, _, _ = synth.paper_hagan_mc_model(PAPER_DATA, PAPER_MM, PAPER_MC)
+    mm = model == "mm"
+    if mm:
+        _, model = synth.paper_mm_mc_model(PAPER_DATA, PAPER_MM)
+        mmpub = {r[0]: float(r[1]) for r in synth.read_paper_market(PAPER_MM)["published_swaptions"]}
+        pub = {"mae_percent": mmpub["mae_percent"], "calibration_hours": pub["calibration_hours"]}
+    else:
+        _, model, _, _, _ = synth.paper_hagan_mc_model(PAPER_DATA, PAPER_MM, PAPER_MC)
     lo, hi = np.array([0.0, 0.0, 0.0, 0.0, 0.0]), np.array([1.0, 5.0, 1.0, 5.0, 0.5])
+    free = np.array([1, 1, 0, 0, 0]) if mm else np.ones(5)
     kw = dict(swp_start=sa, swp_end=sb, swp_K=sK, n_paths=n_paths, dt=dt, mc_seed=20111121, prec="fp32")
-    r = lib.mc_anneal(sk.T, sk.P, model, vol, lo, hi, np.ones(5), chains, levels, steps, 0.8, 20111121, stream=stream,
+    r = lib.mc_anneal(sk.T, sk.P, model, vol, lo, hi, free, chains, levels, steps, 0.8, 20111121, stream=stream,
                       **kw)
     m_best = dict(model, eta1=r["y_best"][0], lambda1=r["y_best"][1], eta2=r["y_best"][2], lambda2=r["y_best"][3],
                   lambda3=r["y_best"][4])
@@ -596,7 +621,8 @@ def mc_calibration_record(lib, stream, chains=64, levels=20, steps=5, n_paths=10
     sd = vol * np.sqrt(sk.T[sa])
     d1 = np.log(S / sK) / sd + 0.5 * sd
     black = A * (S * ndtr(d1) - sK * ndtr(d1 - sd))
-    return {"workload": f"paper_hagan_swaption_calibration_mc_180swaptions_{chains}ch_x_{levels}T_x_{steps}steps_"
+    name = "mercurio_morini" if mm else "hagan"
+    return {"workload": f"paper_{name}_swaption_calibration_mc_180swaptions_{chains}ch_x_{levels}T_x_{steps}steps_"
                         f"{n_paths}paths_dt{dt}",
             "how": "sabr_lmm_mc_anneal: host-driven annealing (the paper's own split), every step's proposals priced "
                    "in one batched Monte Carlo launch; wall time of the whole search",
@@ -605,7 +631,8 @@ def mc_calibration_record(lib, stream, chains=64, levels=20, steps=5, n_paths=10
             "mae_percent": float(100.0 * np.mean(np.abs(mc - black))),
             "path_steps_per_s": r["n_evals"] * n_paths * int(np.ceil(sk.T[3] / dt)) / r["seconds"],
             "paper": {"mae_percent": float(pub["mae_percent"]), "calibration_hours": float(pub["calibration_hours"]),
-                      "y": [model[k] for k in ("eta1", "lambda1", "eta2", "lambda2", "lambda3")],
+                      "y": [model[k] for k in (("eta1", "lambda1") if mm else
+                                                ("eta1", "lambda1", "eta2", "lambda2", "lambda3"))],
                       "hardware": "2x NVIDIA GeForce GTX 470 (Fermi)"}}
 
 
@@ -740,6 +767,8 @@ def main():
     ap.add_argument("--mc-calibration", action="store_true",
                     help="the paper's swaption calibration over the Monte Carlo objective alone (--mc-chains, "
                          "--mc-levels, --mc-steps, --mc-paths, --mc-dt)")
+    ap.add_argument("--mc-model", default="hagan", choices=["hagan", "mm"],
+                    help="with --mc-calibration: the Hagan or the Mercurio & Morini dynamics")
     ap.add_argument("--mc-chains", type=int, default=64)
     ap.add_argument("--mc-levels", type=int, default=20)
     ap.add_argument("--mc-steps", type=int, default=5)
@@ -755,7 +784,7 @@ def main():
         import torch
         lib.load()
         print(json.dumps(mc_calibration_record(lib, torch.cuda.Stream(), args.mc_chains, args.mc_levels,
-                                               args.mc_steps, args.mc_paths, args.mc_dt)))
+                                               args.mc_steps, args.mc_paths, args.mc_dt, args.mc_model)))
         return None
     if args.profile:
         args.workload = args.workload or "caplets"
@@ -887,6 +916,7 @@ def main():
     if args.prec == "fp32" and not args.no_mc:
         workloads["mc_hagan_caplets"] = mc_record(lib, s, peaks, cpu=not args.no_cpu_baseline)
         workloads["mc_swaption_calibration"] = mc_calibration_record(lib, s)
+        workloads["mc_swaption_calibration_mm"] = mc_calibration_record(lib, s, model="mm")
     # the 256-market batch: one level (its full 100-level schedule: bench.py --workload batch)
     if args.prec == "fp32" and not args.no_batch_variant:
         rec, _, _, _, _ = search_record(lib, "batch", "fp32", seed, s, peaks, levels=1, e2e=False)

@@ -397,6 +397,12 @@ typedef struct {
   const int32_t* swp_start;
   const int32_t* swp_end;
   const double* swp_K;
+  int32_t model;   /* SABR_LMM_MODEL_SMILE (0): the Hagan dynamics above; SABR_LMM_MODEL_MERCURIO_MORINI
+                    * (2): the one-factor volatility of Section 2.2, dF_i = mu_i dt + alpha_i V F_i^beta
+                    * dW_i, dV = sigma V dZ, V(0) = 1, with sigma[0] the common vol of vol, phi[i] =
+                    * corr(W_i, Z), corr(W_i, W_j) = rho_ij (eta1, lambda1) and mu_i the spot-measure
+                    * drift alpha_i V F_i^beta sum_{j<=i} rho_ij tau_j alpha_j V F_j^beta / (1 + tau_j
+                    * F_j); eta2, lambda2, lambda3 and sigma[1..] unused.  Others: EINVAL.         */
 } sabr_lmm_mc_desc;
 
 /* n_paths in [1, 2^40]; dt > 0: every interval between fixings (and [0, T[0]]) is cut into

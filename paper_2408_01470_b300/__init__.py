@@ -96,6 +96,7 @@ class McDesc(C.Structure):
         ("phi", _D), ("eta1", C.c_double), ("lambda1", C.c_double), ("eta2", C.c_double),
         ("lambda2", C.c_double), ("lambda3", C.c_double), ("n_cap", C.c_int32), ("cap_fwd", _I32),
         ("cap_K", _D), ("n_swp", C.c_int32), ("swp_start", _I32), ("swp_end", _I32), ("swp_K", _D),
+        ("model", C.c_int32),
     ]
 
 
@@ -502,8 +503,9 @@ CalibrationObjective = _LazyFunction()
 
 # ---------------------------------------------------------------- Monte Carlo pricer
 def mc_describe(T, P, model, cap_fwd=(), cap_K=(), swp_start=(), swp_end=(), swp_K=()):
-    """An McDesc for a tenor structure (T, P) and a Hagan SABR/LIBOR model dict (beta, eta1, lambda1,
-    eta2, lambda2, lambda3 and per-forward alpha, sigma, phi); returns (desc, keep-alive arrays)."""
+    """An McDesc for a tenor structure (T, P) and a model dict: beta, eta1, lambda1, per-forward
+    alpha, sigma, phi; for the Hagan dynamics also eta2, lambda2, lambda3; "model": 2 selects the
+    Mercurio & Morini dynamics (sigma[0] the common vol of vol).  Returns (desc, keep-alive arrays)."""
     n_fwd = len(T) - 1
     keep = dict(T=_f64(T), P=_f64(P), alpha=_f64(np.resize(model["alpha"], n_fwd)),
                 sigma=_f64(np.resize(model["sigma"], n_fwd)), phi=_f64(np.resize(model["phi"], n_fwd)),
@@ -515,8 +517,9 @@ def mc_describe(T, P, model, cap_fwd=(), cap_K=(), swp_start=(), swp_end=(), swp
     d.T, d.P = keep["T"].ctypes.data_as(_D), keep["P"].ctypes.data_as(_D)
     d.beta = float(model["beta"])
     d.alpha, d.sigma, d.phi = (keep[k].ctypes.data_as(_D) for k in ("alpha", "sigma", "phi"))
-    d.eta1, d.lambda1, d.eta2 = float(model["eta1"]), float(model["lambda1"]), float(model["eta2"])
-    d.lambda2, d.lambda3 = float(model["lambda2"]), float(model["lambda3"])
+    d.eta1, d.lambda1, d.eta2 = float(model["eta1"]), float(model["lambda1"]), float(model.get("eta2", 0.0))
+    d.lambda2, d.lambda3 = float(model.get("lambda2", 0.0)), float(model.get("lambda3", 0.0))
+    d.model = int(model.get("model", 0))
     d.n_cap = len(keep["cap_fwd"])
     d.cap_fwd, d.cap_K = keep["cap_fwd"].ctypes.data_as(_I32), keep["cap_K"].ctypes.data_as(_D)
     d.n_swp = len(keep["swp_start"])

@@ -34,10 +34,12 @@ template <class R> struct McConsts {
   R rho[kMcMaxFwd * kMcMaxFwd];    // rho(u, v): correlation of W_(M-1-u) with W_(M-1-v)
   R phi[kMcMaxFwd * kMcMaxFwd];    // phi(u, v): correlation of W_(M-1-u) with Z_(M-1-v)
   R tau[kMcMaxFwd], sig[kMcMaxFwd], hs2[kMcMaxFwd], F0[kMcMaxFwd], lnV0[kMcMaxFwd];
+  R alpha[kMcMaxFwd];              // Mercurio & Morini: alpha_i (the Hagan model's alpha is V_i(0))
 };
 
 struct McArgs {
   int M;                         // forwards simulated (the largest forward any instrument needs + 1)
+  int model;                     // 0: Hagan; 2: Mercurio & Morini (one vol process, row 0 of L is Z)
   int n_int;                     // intervals simulated: the last fixing any instrument needs + 1
   int n_cap, n_swp;
   double beta, P0;               // P0 = P(0, T_0)
@@ -121,7 +123,11 @@ __host__ __device__ inline size_t mc_smem_bytes(int n_instr) { return (size_t)kM
 // The paths of CTA blockIdx.x (grid-stride over gridDim.x CTAs): their per-warp sums in acc
 // (shared, [warps][n_instr][2]), the CTA's sums to part_out [n_instr x 2] and its stopped paths to
 // bad_out.  C is read with compile-time indices after unrolling.
-template <class R>
+// MM: the Mercurio & Morini dynamics (Section 2.2): dF_i = mu_i dt + alpha_i V F_i^b dW_i with
+// mu_i = alpha_i V F_i^b V sum_{j=k}^{i} rho_ij tau_j alpha_j F_j^b / (1 + tau_j F_j), dV = sigma V dZ,
+// V(0) = 1; the factor's row 0 is Z and row 1 + u is W of forward M - 1 - u, so a step draws 1 + a
+// normals; ln V is lnV[0].
+template <class R, bool MM>
 __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, double* acc, double* part_out,
                                          unsigned long long* bad_out) {
   const int n_instr = a.n_cap + a.n_swp;
@@ -151,7 +157,7 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
         R xi[kMcRows];
 #pragma unroll
         for (int b = 0; b < kMcRows / 4; ++b) {
-          if (4 * b < 2 * na) {
+          if (4 * b < (MM ? na + 1 : 2 * na)) {
             uint32_t o[4];
             philox4x32_10((uint32_t)b, (uint32_t)step, (uint32_t)p, (uint32_t)((unsigned long long)p >> 32), k0, k1, o);
             box_muller(o[0], o[1], xi[4 * b], xi[4 * b + 1]);
@@ -160,6 +166,42 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
             xi[4 * b] = xi[4 * b + 1] = xi[4 * b + 2] = xi[4 * b + 3] = R(0);
           }
         }
+        if constexpr (MM) {
+          const R Vc = mc_exp<R>(lnV[0]);
+          R x[kMcMaxFwd], vf[kMcMaxFwd];
+#pragma unroll
+          for (int u = 0; u < kMcMaxFwd; ++u) {
+            if (u < na) {
+              const R fb = F[u] > R(0) ? mc_exp<R>(beta * mc_log<R>(F[u])) : R(0);
+              vf[u] = C.alpha[u] * Vc * fb;
+              x[u] = C.tau[u] * C.alpha[u] * fb * mc_rcp<R>(R(1) + C.tau[u] * F[u]);
+            } else {
+              vf[u] = x[u] = R(0);
+            }
+          }
+          const R zz = C.L[0] * xi[0];
+#pragma unroll
+          for (int u = 0; u < kMcMaxFwd; ++u) {
+            if (u < na) {
+              R dF0 = 0, dF1 = 0;
+#pragma unroll
+              for (int v = u; v < kMcMaxFwd; ++v)
+                if (v < na) {
+                  if ((v - u) & 1) dF1 += C.rho[u * kMcMaxFwd + v] * x[v];
+                  else dF0 += C.rho[u * kMcMaxFwd + v] * x[v];
+                }
+              R zw0 = 0, zw1 = 0;
+#pragma unroll
+              for (int c = 0; c <= u + 1; ++c) {
+                if (c & 1) zw1 += C.L[(u + 1) * kMcRows + c] * xi[c];
+                else zw0 += C.L[(u + 1) * kMcRows + c] * xi[c];
+              }
+              const R fn = F[u] + vf[u] * (h * Vc * (dF0 + dF1) + sh * (zw0 + zw1));
+              F[u] = fn > R(0) ? fn : R(0);
+            }
+          }
+          lnV[0] += h * (-C.hs2[0]) + C.sig[0] * sh * zz;
+        } else {
         R x[kMcMaxFwd], vf[kMcMaxFwd], V[kMcMaxFwd];
 #pragma unroll
         for (int u = 0; u < kMcMaxFwd; ++u) {
@@ -207,6 +249,7 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
             lnV[u] += h * (C.sig[u] * dV - C.hs2[u]) + C.sig[u] * sh * zz;
           }
         }
+        }
       }
       // T_k: forward k (u = na - 1) fixes
       bool fin = true;
@@ -214,7 +257,7 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
 #pragma unroll
       for (int u = 0; u < kMcMaxFwd; ++u) {
         Fs[u] = F[u];
-        if (u < na) fin = fin && isfinite(F[u]) && isfinite(lnV[u]);
+        if (u < na) fin = fin && isfinite(F[u]) && isfinite(lnV[MM ? 0 : u]);
       }
       if (good && !fin) ++nbad;
       good = good && fin;
@@ -266,12 +309,12 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
 // The model constants travel as a kernel parameter (constant bank): after unrolling, every index
 // into them is a compile-time constant, so the FMAs of the correlation product and the drifts read
 // their coefficient straight from the constant bank, with no shared-memory load.
-template <class R>
+template <class R, bool MM>
 __global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_kernel(const __grid_constant__ McArgs a,
                                                              const __grid_constant__ McConsts<R> C) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n_instr = a.n_cap + a.n_swp;
-  mc_paths<R>(a, C, (double*)smem, a.part + (size_t)blockIdx.x * n_instr * 2, a.bad + blockIdx.x);
+  mc_paths<R, MM>(a, C, (double*)smem, a.part + (size_t)blockIdx.x * n_instr * 2, a.bad + blockIdx.x);
 }
 
 // Many parameter sets in one launch (the annealer's proposals): set blockIdx.y has its constants
@@ -282,7 +325,7 @@ __host__ __device__ inline size_t mc_batch_smem_bytes(int n_instr) {
   return ((sizeof(McConsts<R>) + 127) & ~(size_t)127) + mc_smem_bytes(n_instr);
 }
 
-template <class R>
+template <class R, bool MM>
 __global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_batch_kernel(const __grid_constant__ McArgs a,
                                                                    const McConsts<R>* __restrict__ Cs) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -296,7 +339,7 @@ __global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_ba
   // (mc_paths synchronises the CTA before it reads C)
   double* acc = (double*)(smem + ((sizeof(McConsts<R>) + 127) & ~(size_t)127));
   const size_t cta = (size_t)set * gridDim.x + blockIdx.x;
-  mc_paths<R>(a, C, acc, a.part + cta * n_instr * 2, a.bad + cta);
+  mc_paths<R, MM>(a, C, acc, a.part + cta * n_instr * 2, a.bad + cta);
 }
 
 // f_s of every set: the Monte Carlo prices from its CTA sums (CTA by CTA in order) against the

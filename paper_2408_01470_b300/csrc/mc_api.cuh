@@ -94,9 +94,19 @@ void mc_build_consts(const sabr_lmm_mc_desc* d, int M, const double* tau, const 
                      McConsts<float>& c32) {
   const double eta1 = y ? y[0] : d->eta1, lambda1 = y ? y[1] : d->lambda1, eta2 = y ? y[2] : d->eta2;
   const double lambda2 = y ? y[3] : d->lambda2, lambda3 = y ? y[4] : d->lambda3;
-  const int n = 2 * M;
+  const bool mm = d->model == SABR_LMM_MODEL_MERCURIO_MORINI;
+  // Mercurio & Morini: row 0 is Z, row 1 + u is W of forward M - 1 - u; corr(W_i, Z) = phi_i
+  const int n = mm ? M + 1 : 2 * M;
   std::vector<double> Cm((size_t)n * n);
-  for (int r = 0; r < n; ++r)
+  for (int r = 0; r < n && mm; ++r)
+    for (int c = 0; c < n; ++c) {
+      double v;
+      if (r == 0 && c == 0) v = 1.0;
+      else if (r == 0 || c == 0) v = d->phi[M - (r + c)];
+      else v = eta1 + (1.0 - eta1) * std::exp(-lambda1 * std::fabs(d->T[M - r] - d->T[M - c]));
+      Cm[(size_t)r * n + c] = v;
+    }
+  for (int r = 0; r < n && !mm; ++r)
     for (int c = 0; c < n; ++c) {
       const int i = M - 1 - r / 2, j = M - 1 - c / 2;
       const bool wr = (r & 1) == 0, wc = (c & 1) == 0;
@@ -130,14 +140,15 @@ void mc_build_consts(const sabr_lmm_mc_desc* d, int M, const double* tau, const 
   for (int u = 0; u < M; ++u) {
     const int i = M - 1 - u;
     for (int v = 0; v < M; ++v) {
-      c64.rho[u * kMcMaxFwd + v] = Cm[(size_t)(2 * u) * n + 2 * v];
-      c64.phi[u * kMcMaxFwd + v] = Cm[(size_t)(2 * u) * n + 2 * v + 1];
+      c64.rho[u * kMcMaxFwd + v] = mm ? Cm[(size_t)(1 + u) * n + 1 + v] : Cm[(size_t)(2 * u) * n + 2 * v];
+      c64.phi[u * kMcMaxFwd + v] = mm ? 0.0 : Cm[(size_t)(2 * u) * n + 2 * v + 1];
     }
     c64.tau[u] = tau[i];
-    c64.sig[u] = d->sigma[i];
-    c64.hs2[u] = 0.5 * d->sigma[i] * d->sigma[i];
+    c64.sig[u] = mm ? d->sigma[0] : d->sigma[i];
+    c64.hs2[u] = 0.5 * c64.sig[u] * c64.sig[u];
     c64.F0[u] = (d->P[i] / d->P[i + 1] - 1.0) / tau[i];
-    c64.lnV0[u] = std::log(d->alpha[i]);
+    c64.lnV0[u] = mm ? 0.0 : std::log(d->alpha[i]);
+    c64.alpha[u] = d->alpha[i];
   }
   const double* src = (const double*)&c64;
   float* dst = (float*)&c32;
@@ -154,6 +165,8 @@ std::string mc_validate(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o) {
     if (!(d->P[k] > 0.0) || !std::isfinite(d->P[k])) return "P must be finite and > 0";
   }
   if (!(d->beta >= 0.0 && d->beta <= 1.0)) return "beta must be in [0, 1]";
+  if (d->model != SABR_LMM_MODEL_SMILE && d->model != SABR_LMM_MODEL_MERCURIO_MORINI)
+    return "model must be 0 (Hagan) or 2 (Mercurio & Morini)";
   for (int i = 0; i < d->n_fwd; ++i) {
     if (!(d->alpha[i] > 0.0) || !std::isfinite(d->alpha[i])) return "alpha must be finite and > 0";
     if (!(d->sigma[i] >= 0.0) || !std::isfinite(d->sigma[i])) return "sigma must be finite and >= 0";
@@ -270,6 +283,7 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   char* b = (char*)p->buf;
   McArgs& a = p->args;
   a.M = M; a.n_cap = d->n_cap; a.n_swp = d->n_swp; a.beta = d->beta; a.P0 = d->P[0];
+  a.model = d->model;
   a.n_int = 1;   // the simulation ends at the last fixing an instrument needs
   for (int c = 0; c < d->n_cap; ++c) a.n_int = std::max(a.n_int, d->cap_fwd[c] + 1);
   for (int c = 0; c < d->n_swp; ++c) a.n_int = std::max(a.n_int, d->swp_start[c] + 1);
@@ -282,8 +296,11 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   p->out = (double*)(b + o_out);
   p->nbad = (long long*)(b + o_nbad);
   const size_t sm = mc_smem_bytes(ni);
-  e = o->prec == SABR_LMM_FP64 ? raise_smem_limit(mc_path_kernel<double>, (uint32_t)sm)
-                               : raise_smem_limit(mc_path_kernel<float>, (uint32_t)sm);
+  const bool mm = d->model == SABR_LMM_MODEL_MERCURIO_MORINI;
+  e = o->prec == SABR_LMM_FP64 ? (mm ? raise_smem_limit(mc_path_kernel<double, true>, (uint32_t)sm)
+                                     : raise_smem_limit(mc_path_kernel<double, false>, (uint32_t)sm))
+                               : (mm ? raise_smem_limit(mc_path_kernel<float, true>, (uint32_t)sm)
+                                     : raise_smem_limit(mc_path_kernel<float, false>, (uint32_t)sm));
   if (e != cudaSuccess) {
     cudaFree(p->buf);
     delete p;
@@ -302,8 +319,14 @@ extern "C" sabr_lmm_status sabr_lmm_mc_launch(sabr_lmm_mc_plan* p, double* price
   cudaStream_t s = (cudaStream_t)stream;
   const int ni = p->n_cap + p->n_swp;
   const size_t sm = mc_smem_bytes(ni);
-  if (p->prec == SABR_LMM_FP64) mc_path_kernel<double><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c64);
-  else mc_path_kernel<float><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c32);
+  const bool mm = p->args.model == SABR_LMM_MODEL_MERCURIO_MORINI;
+  if (p->prec == SABR_LMM_FP64) {
+    if (mm) mc_path_kernel<double, true><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c64);
+    else mc_path_kernel<double, false><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c64);
+  } else {
+    if (mm) mc_path_kernel<float, true><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c32);
+    else mc_path_kernel<float, false><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c32);
+  }
   mc_reduce_kernel<<<(ni + 127) / 128, 128, 0, s>>>(p->args, p->grid, price ? price : p->out,
                                                       price ? stderr_out : p->out + ni, n_bad ? n_bad : p->nbad);
   CUDA_TRY(cudaGetLastError());
@@ -450,9 +473,12 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
     e = cudaGetLastError();
   }
   const size_t smb = f64 ? mc_batch_smem_bytes<double>(ni) : mc_batch_smem_bytes<float>(ni);
+  const bool mmb = p->args.model == SABR_LMM_MODEL_MERCURIO_MORINI;
   if (e == cudaSuccess)
-    e = f64 ? raise_smem_limit(mc_path_batch_kernel<double>, (uint32_t)smb)
-            : raise_smem_limit(mc_path_batch_kernel<float>, (uint32_t)smb);
+    e = f64 ? (mmb ? raise_smem_limit(mc_path_batch_kernel<double, true>, (uint32_t)smb)
+                   : raise_smem_limit(mc_path_batch_kernel<double, false>, (uint32_t)smb))
+            : (mmb ? raise_smem_limit(mc_path_batch_kernel<float, true>, (uint32_t)smb)
+                   : raise_smem_limit(mc_path_batch_kernel<float, false>, (uint32_t)smb));
   if (e != cudaSuccess) {
     cleanup();
     return fail(SABR_LMM_ECUDA, std::string("mc_anneal: ") + cudaGetErrorString(e));
@@ -476,8 +502,15 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
     cudaError_t ee = cudaMemcpyAsync(b + o_cs, hcs, (size_t)n * csz, cudaMemcpyHostToDevice, s);
     if (ee != cudaSuccess) return ee;
     const dim3 grid(G, n);
-    if (f64) mc_path_batch_kernel<double><<<grid, kMcThreads, smb, s>>>(ab, (const McConsts<double>*)(b + o_cs));
-    else mc_path_batch_kernel<float><<<grid, kMcThreads, smb, s>>>(ab, (const McConsts<float>*)(b + o_cs));
+    const McConsts<double>* c64 = (const McConsts<double>*)(b + o_cs);
+    const McConsts<float>* c32 = (const McConsts<float>*)(b + o_cs);
+    if (f64) {
+      if (mmb) mc_path_batch_kernel<double, true><<<grid, kMcThreads, smb, s>>>(ab, c64);
+      else mc_path_batch_kernel<double, false><<<grid, kMcThreads, smb, s>>>(ab, c64);
+    } else {
+      if (mmb) mc_path_batch_kernel<float, true><<<grid, kMcThreads, smb, s>>>(ab, c32);
+      else mc_path_batch_kernel<float, false><<<grid, kMcThreads, smb, s>>>(ab, c32);
+    }
     mc_objective_kernel<<<(n + 3) / 4, 128, 0, s>>>(ab, G, n, (const double*)(b + o_mkt), (double*)(b + o_f));
     if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
     if ((ee = cudaMemcpyAsync(hf, b + o_f, (size_t)n * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return ee;
