@@ -408,7 +408,9 @@ typedef struct {
 /* n_paths in [1, 2^40]; dt > 0: every interval between fixings (and [0, T[0]]) is cut into
  * ceil(len / dt) equal steps; seed: the key of the paths' Philox4x32-10 streams (path p, step s,
  * block b at counter (b, s, p low, p high)); prec: FP64 or FP32 (the path arithmetic; sums in
- * FP64); grid: CTAs of 128 paths (0: one per 128 paths, at most 8 per SM, the rest looped).      */
+ * FP64); grid: CTAs (0: enough for every path, at most one wave per SM, the rest looped); a CTA
+ * takes 512 paths in FP32 and 128 in FP64, halved while its per-warp sums (16 bytes per
+ * instrument and warp) would not fit in 227 KB of shared memory.                                */
 typedef struct {
   int64_t n_paths;
   double dt;

@@ -25,8 +25,12 @@ namespace sabr {
 
 constexpr int kMcMaxFwd = 16;            // forwards a pricer simulates
 constexpr int kMcRows = 2 * kMcMaxFwd;   // rows of the correlation factor
-constexpr int kMcThreads = 128;          // paths per CTA (4 warps)
-constexpr int kMcWarps = kMcThreads / 32;
+// Paths per CTA (one thread each): at most 512 in FP32 (one CTA of 16 warps per SM at 128
+// registers, so that every warp of an SM runs the same interval's code), 128 in FP64; fewer when
+// the per-warp sums of many instruments would not fit in shared memory.
+template <class R> __host__ __device__ constexpr int mc_max_threads() { return sizeof(R) == 4 ? 512 : 128; }
+constexpr int kMcMaxWarps = 16;
+constexpr size_t kMcSmemMax = 227 * 1024;   // dynamic shared memory a CTA may take
 
 // Model constants, in u-order (u = M - 1 - i), one copy per precision.
 template <class R> struct McConsts {
@@ -118,7 +122,120 @@ __device__ __forceinline__ double warp_sum_mc(double v) {
 }
 
 // Dynamic shared memory of the path kernel: the per-warp sums.
-__host__ __device__ inline size_t mc_smem_bytes(int n_instr) { return (size_t)kMcWarps * n_instr * 2 * sizeof(double); }
+__host__ __device__ inline size_t mc_smem_bytes(int n_instr, int threads) {
+  return (size_t)(threads / 32) * n_instr * 2 * sizeof(double);
+}
+
+// The steps of one interval with NA alive forwards (u = 0 .. NA - 1), NA a compile-time constant:
+// every guard on the alive count folds away, and only the normals, rows and drift terms the
+// interval needs are generated.  The arithmetic and its order are those of every NA.
+template <class R, bool MM, int NA>
+__device__ __forceinline__ void mc_interval(const McConsts<R>& C, R (&F)[kMcMaxFwd], R (&lnV)[kMcMaxFwd], const int ns,
+                                            const R h, const R sh, int& step, const long long p, const uint32_t k0,
+                                            const uint32_t k1, const R beta) {
+  constexpr int na = NA;
+  for (int s = 0; s < ns; ++s, ++step) {
+    // The constants are read where they are used, every step: held across the steps (shared
+    // memory in the batch kernel) they would take more registers than a thread has.
+    asm volatile("" ::: "memory");
+    R xi[kMcRows];
+#pragma unroll
+    for (int b = 0; b < kMcRows / 4; ++b) {
+      if (4 * b < (MM ? na + 1 : 2 * na)) {
+        uint32_t o[4];
+        philox4x32_10((uint32_t)b, (uint32_t)step, (uint32_t)p, (uint32_t)((unsigned long long)p >> 32), k0, k1, o);
+        box_muller(o[0], o[1], xi[4 * b], xi[4 * b + 1]);
+        box_muller(o[2], o[3], xi[4 * b + 2], xi[4 * b + 3]);
+      } else {
+        xi[4 * b] = xi[4 * b + 1] = xi[4 * b + 2] = xi[4 * b + 3] = R(0);
+      }
+    }
+    if constexpr (MM) {
+      const R Vc = mc_exp<R>(lnV[0]);
+      R x[kMcMaxFwd], vf[kMcMaxFwd];
+#pragma unroll
+      for (int u = 0; u < kMcMaxFwd; ++u) {
+        if (u < na) {
+          const R fb = F[u] > R(0) ? mc_exp<R>(beta * mc_log<R>(F[u])) : R(0);
+          vf[u] = C.alpha[u] * Vc * fb;
+          x[u] = C.tau[u] * C.alpha[u] * fb * mc_rcp<R>(R(1) + C.tau[u] * F[u]);
+        } else {
+          vf[u] = x[u] = R(0);
+        }
+      }
+      const R zz = C.L[0] * xi[0];
+#pragma unroll
+      for (int u = 0; u < kMcMaxFwd; ++u) {
+        if (u < na) {
+          R dF0 = 0, dF1 = 0;
+#pragma unroll
+          for (int v = u; v < kMcMaxFwd; ++v)
+            if (v < na) {
+              if ((v - u) & 1) dF1 += C.rho[u * kMcMaxFwd + v] * x[v];
+              else dF0 += C.rho[u * kMcMaxFwd + v] * x[v];
+            }
+          R zw0 = 0, zw1 = 0;
+#pragma unroll
+          for (int c = 0; c <= u + 1; ++c) {
+            if (c & 1) zw1 += C.L[(u + 1) * kMcRows + c] * xi[c];
+            else zw0 += C.L[(u + 1) * kMcRows + c] * xi[c];
+          }
+          const R fn = F[u] + vf[u] * (h * Vc * (dF0 + dF1) + sh * (zw0 + zw1));
+          F[u] = fn > R(0) ? fn : R(0);
+        }
+      }
+      lnV[0] += h * (-C.hs2[0]) + C.sig[0] * sh * zz;
+    } else {
+    R x[kMcMaxFwd], vf[kMcMaxFwd], V[kMcMaxFwd];
+#pragma unroll
+    for (int u = 0; u < kMcMaxFwd; ++u) {
+      if (u < na) {
+        V[u] = mc_exp<R>(lnV[u]);
+        const R fb = F[u] > R(0) ? mc_exp<R>(beta * mc_log<R>(F[u])) : R(0);
+        vf[u] = V[u] * fb;
+        x[u] = C.tau[u] * vf[u] * mc_rcp<R>(R(1) + C.tau[u] * F[u]);
+      } else {
+        V[u] = vf[u] = x[u] = R(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kMcMaxFwd; ++u) {
+      if (u < na) {
+        // drifts: forwards j = k .. i, i.e. v = u .. na - 1
+        // (two partial sums per dot product: half the length of each dependent FMA chain)
+        R dF0 = 0, dV0 = 0, dF1 = 0, dV1 = 0;
+#pragma unroll
+        for (int v = u; v < kMcMaxFwd; ++v)
+          if (v < na) {
+            if ((v - u) & 1) {
+              dF1 += C.rho[u * kMcMaxFwd + v] * x[v];
+              dV1 += C.phi[u * kMcMaxFwd + v] * x[v];
+            } else {
+              dF0 += C.rho[u * kMcMaxFwd + v] * x[v];
+              dV0 += C.phi[u * kMcMaxFwd + v] * x[v];
+            }
+          }
+        const R dF = dF0 + dF1, dV = dV0 + dV1;
+        R zw0 = 0, zw1 = 0, zz0 = 0, zz1 = 0;
+#pragma unroll
+        for (int c = 0; c <= 2 * u; ++c) {
+          if (c & 1) zw1 += C.L[(2 * u) * kMcRows + c] * xi[c];
+          else zw0 += C.L[(2 * u) * kMcRows + c] * xi[c];
+        }
+#pragma unroll
+        for (int c = 0; c <= 2 * u + 1; ++c) {
+          if (c & 1) zz1 += C.L[(2 * u + 1) * kMcRows + c] * xi[c];
+          else zz0 += C.L[(2 * u + 1) * kMcRows + c] * xi[c];
+        }
+        const R zw = zw0 + zw1, zz = zz0 + zz1;
+        const R fn = F[u] + vf[u] * (h * dF + sh * zw);
+        F[u] = fn > R(0) ? fn : R(0);
+        lnV[u] += h * (C.sig[u] * dV - C.hs2[u]) + C.sig[u] * sh * zz;
+      }
+    }
+    }
+  }
+}
 
 // The paths of CTA blockIdx.x (grid-stride over gridDim.x CTAs): their per-warp sums in acc
 // (shared, [warps][n_instr][2]), the CTA's sums to part_out [n_instr x 2] and its stopped paths to
@@ -130,8 +247,8 @@ __host__ __device__ inline size_t mc_smem_bytes(int n_instr) { return (size_t)kM
 template <class R, bool MM>
 __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, double* acc, double* part_out,
                                          unsigned long long* bad_out) {
-  const int n_instr = a.n_cap + a.n_swp;
-  for (int t = threadIdx.x; t < kMcWarps * n_instr * 2; t += blockDim.x) acc[t] = 0.0;
+  const int n_instr = a.n_cap + a.n_swp, n_warps = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < n_warps * n_instr * 2; t += blockDim.x) acc[t] = 0.0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* wacc = acc + (size_t)warp * n_instr * 2;
@@ -139,8 +256,13 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
   const R beta = (R)a.beta;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
   unsigned long long nbad = 0;
-  const long long stride = (long long)gridDim.x * kMcThreads;
-  for (long long base = (long long)blockIdx.x * kMcThreads + warp * 32; base < a.n_paths; base += stride) {
+  // The CTA's batches of blockDim.x paths: every warp takes the same number of batches and meets the
+  // barrier at the end of every interval (a warp past the last path only meets the barriers), so
+  // the warps of the CTA run the same interval's code at the same time.
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long cbase = (long long)blockIdx.x * blockDim.x; cbase < a.n_paths; cbase += stride) {
+    const long long base = cbase + warp * 32;
+    const bool warp_live = base < a.n_paths;
     const long long p = base + lane;
     const bool live = p < a.n_paths;
     R F[kMcMaxFwd], lnV[kMcMaxFwd];
@@ -150,141 +272,55 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
     double numer = a.P0;   // 1 / B(T_k) at the start of interval k
     int step = 0;
     for (int k = 0; k < a.n_int; ++k) {
-      const int na = M - k;   // alive forwards: u = 0 .. na - 1
-      const int ns = a.nsteps[k];
-      const R h = (R)a.h[k], sh = (R)sqrt(a.h[k]);
-      for (int s = 0; s < ns; ++s, ++step) {
-        R xi[kMcRows];
-#pragma unroll
-        for (int b = 0; b < kMcRows / 4; ++b) {
-          if (4 * b < (MM ? na + 1 : 2 * na)) {
-            uint32_t o[4];
-            philox4x32_10((uint32_t)b, (uint32_t)step, (uint32_t)p, (uint32_t)((unsigned long long)p >> 32), k0, k1, o);
-            box_muller(o[0], o[1], xi[4 * b], xi[4 * b + 1]);
-            box_muller(o[2], o[3], xi[4 * b + 2], xi[4 * b + 3]);
-          } else {
-            xi[4 * b] = xi[4 * b + 1] = xi[4 * b + 2] = xi[4 * b + 3] = R(0);
-          }
+      if (warp_live) {
+        const int na = M - k;   // alive forwards: u = 0 .. na - 1
+        const int ns = a.nsteps[k];
+        const R h = (R)a.h[k], sh = (R)sqrt(a.h[k]);
+        switch (na) {
+#define SABR_MC_CASE(n) \
+    case n: mc_interval<R, MM, n>(C, F, lnV, ns, h, sh, step, p, k0, k1, beta); break;
+          SABR_MC_CASE(1) SABR_MC_CASE(2) SABR_MC_CASE(3) SABR_MC_CASE(4) SABR_MC_CASE(5) SABR_MC_CASE(6)
+          SABR_MC_CASE(7) SABR_MC_CASE(8) SABR_MC_CASE(9) SABR_MC_CASE(10) SABR_MC_CASE(11) SABR_MC_CASE(12)
+          SABR_MC_CASE(13) SABR_MC_CASE(14) SABR_MC_CASE(15) SABR_MC_CASE(16)
+#undef SABR_MC_CASE
+          default: break;
         }
-        if constexpr (MM) {
-          const R Vc = mc_exp<R>(lnV[0]);
-          R x[kMcMaxFwd], vf[kMcMaxFwd];
-#pragma unroll
-          for (int u = 0; u < kMcMaxFwd; ++u) {
-            if (u < na) {
-              const R fb = F[u] > R(0) ? mc_exp<R>(beta * mc_log<R>(F[u])) : R(0);
-              vf[u] = C.alpha[u] * Vc * fb;
-              x[u] = C.tau[u] * C.alpha[u] * fb * mc_rcp<R>(R(1) + C.tau[u] * F[u]);
-            } else {
-              vf[u] = x[u] = R(0);
-            }
-          }
-          const R zz = C.L[0] * xi[0];
-#pragma unroll
-          for (int u = 0; u < kMcMaxFwd; ++u) {
-            if (u < na) {
-              R dF0 = 0, dF1 = 0;
-#pragma unroll
-              for (int v = u; v < kMcMaxFwd; ++v)
-                if (v < na) {
-                  if ((v - u) & 1) dF1 += C.rho[u * kMcMaxFwd + v] * x[v];
-                  else dF0 += C.rho[u * kMcMaxFwd + v] * x[v];
-                }
-              R zw0 = 0, zw1 = 0;
-#pragma unroll
-              for (int c = 0; c <= u + 1; ++c) {
-                if (c & 1) zw1 += C.L[(u + 1) * kMcRows + c] * xi[c];
-                else zw0 += C.L[(u + 1) * kMcRows + c] * xi[c];
-              }
-              const R fn = F[u] + vf[u] * (h * Vc * (dF0 + dF1) + sh * (zw0 + zw1));
-              F[u] = fn > R(0) ? fn : R(0);
-            }
-          }
-          lnV[0] += h * (-C.hs2[0]) + C.sig[0] * sh * zz;
-        } else {
-        R x[kMcMaxFwd], vf[kMcMaxFwd], V[kMcMaxFwd];
+        // T_k: forward k (u = na - 1) fixes
+        bool fin = true;
+        R Fs[kMcMaxFwd];
 #pragma unroll
         for (int u = 0; u < kMcMaxFwd; ++u) {
-          if (u < na) {
-            V[u] = mc_exp<R>(lnV[u]);
-            const R fb = F[u] > R(0) ? mc_exp<R>(beta * mc_log<R>(F[u])) : R(0);
-            vf[u] = V[u] * fb;
-            x[u] = C.tau[u] * vf[u] * mc_rcp<R>(R(1) + C.tau[u] * F[u]);
-          } else {
-            V[u] = vf[u] = x[u] = R(0);
-          }
+          Fs[u] = F[u];
+          if (u < na) fin = fin && isfinite(F[u]) && isfinite(lnV[MM ? 0 : u]);
         }
-#pragma unroll
-        for (int u = 0; u < kMcMaxFwd; ++u) {
-          if (u < na) {
-            // drifts: forwards j = k .. i, i.e. v = u .. na - 1
-            // (two partial sums per dot product: half the length of each dependent FMA chain)
-            R dF0 = 0, dV0 = 0, dF1 = 0, dV1 = 0;
-#pragma unroll
-            for (int v = u; v < kMcMaxFwd; ++v)
-              if (v < na) {
-                if ((v - u) & 1) {
-                  dF1 += C.rho[u * kMcMaxFwd + v] * x[v];
-                  dV1 += C.phi[u * kMcMaxFwd + v] * x[v];
-                } else {
-                  dF0 += C.rho[u * kMcMaxFwd + v] * x[v];
-                  dV0 += C.phi[u * kMcMaxFwd + v] * x[v];
-                }
-              }
-            const R dF = dF0 + dF1, dV = dV0 + dV1;
-            R zw0 = 0, zw1 = 0, zz0 = 0, zz1 = 0;
-#pragma unroll
-            for (int c = 0; c <= 2 * u; ++c) {
-              if (c & 1) zw1 += C.L[(2 * u) * kMcRows + c] * xi[c];
-              else zw0 += C.L[(2 * u) * kMcRows + c] * xi[c];
+        if (good && !fin) ++nbad;
+        good = good && fin;
+        const double fix = (double)Fs[na - 1];
+        // swaptions expiring at T_k, deflated by 1 / B(T_k)
+        for (int c = a.swp_lo[k]; c < a.swp_lo[k + 1]; ++c) {
+          double pay = 0.0;
+          if (good) {
+            const int b = a.swp_b[c];
+            double disc = 1.0, A = 0.0;
+            for (int j = k; j < b; ++j) {
+              disc /= 1.0 + a.tau64[j] * (double)Fs[M - 1 - j];
+              A += a.tau64[j] * disc;
             }
-#pragma unroll
-            for (int c = 0; c <= 2 * u + 1; ++c) {
-              if (c & 1) zz1 += C.L[(2 * u + 1) * kMcRows + c] * xi[c];
-              else zz0 += C.L[(2 * u + 1) * kMcRows + c] * xi[c];
-            }
-            const R zw = zw0 + zw1, zz = zz0 + zz1;
-            const R fn = F[u] + vf[u] * (h * dF + sh * zw);
-            F[u] = fn > R(0) ? fn : R(0);
-            lnV[u] += h * (C.sig[u] * dV - C.hs2[u]) + C.sig[u] * sh * zz;
+            const double S = (1.0 - disc) / A;
+            pay = A * fmax(S - a.swp_K[c], 0.0) * numer;
           }
+          const double s1 = warp_sum_mc(pay), s2 = warp_sum_mc(pay * pay);
+          if (lane == 0) { wacc[2 * (a.n_cap + c)] += s1; wacc[2 * (a.n_cap + c) + 1] += s2; }
         }
+        numer = good ? numer / (1.0 + a.tau64[k] * fix) : 0.0;
+        // caplets on forward k, paid at T_{k+1}
+        for (int c = a.cap_lo[k]; c < a.cap_lo[k + 1]; ++c) {
+          const double pay = good ? a.tau64[k] * fmax(fix - a.cap_K[c], 0.0) * numer : 0.0;
+          const double s1 = warp_sum_mc(pay), s2 = warp_sum_mc(pay * pay);
+          if (lane == 0) { wacc[2 * c] += s1; wacc[2 * c + 1] += s2; }
         }
       }
-      // T_k: forward k (u = na - 1) fixes
-      bool fin = true;
-      R Fs[kMcMaxFwd];
-#pragma unroll
-      for (int u = 0; u < kMcMaxFwd; ++u) {
-        Fs[u] = F[u];
-        if (u < na) fin = fin && isfinite(F[u]) && isfinite(lnV[MM ? 0 : u]);
-      }
-      if (good && !fin) ++nbad;
-      good = good && fin;
-      const double fix = (double)Fs[na - 1];
-      // swaptions expiring at T_k, deflated by 1 / B(T_k)
-      for (int c = a.swp_lo[k]; c < a.swp_lo[k + 1]; ++c) {
-        double pay = 0.0;
-        if (good) {
-          const int b = a.swp_b[c];
-          double disc = 1.0, A = 0.0;
-          for (int j = k; j < b; ++j) {
-            disc /= 1.0 + a.tau64[j] * (double)Fs[M - 1 - j];
-            A += a.tau64[j] * disc;
-          }
-          const double S = (1.0 - disc) / A;
-          pay = A * fmax(S - a.swp_K[c], 0.0) * numer;
-        }
-        const double s1 = warp_sum_mc(pay), s2 = warp_sum_mc(pay * pay);
-        if (lane == 0) { wacc[2 * (a.n_cap + c)] += s1; wacc[2 * (a.n_cap + c) + 1] += s2; }
-      }
-      numer = good ? numer / (1.0 + a.tau64[k] * fix) : 0.0;
-      // caplets on forward k, paid at T_{k+1}
-      for (int c = a.cap_lo[k]; c < a.cap_lo[k + 1]; ++c) {
-        const double pay = good ? a.tau64[k] * fmax(fix - a.cap_K[c], 0.0) * numer : 0.0;
-        const double s1 = warp_sum_mc(pay), s2 = warp_sum_mc(pay * pay);
-        if (lane == 0) { wacc[2 * c] += s1; wacc[2 * c + 1] += s2; }
-      }
+      __syncthreads();
     }
   }
   __syncthreads();
@@ -292,16 +328,16 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
   double* out = part_out;
   for (int t = threadIdx.x; t < n_instr * 2; t += blockDim.x) {
     double v = 0.0;
-    for (int w = 0; w < kMcWarps; ++w) v += acc[(size_t)w * n_instr * 2 + t];
+    for (int w = 0; w < n_warps; ++w) v += acc[(size_t)w * n_instr * 2 + t];
     out[t] = v;
   }
-  __shared__ unsigned long long sbad[kMcWarps];
+  __shared__ unsigned long long sbad[kMcMaxWarps];
   nbad = (unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)nbad);
   if (lane == 0) sbad[warp] = nbad;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int w = 0; w < kMcWarps; ++w) t += sbad[w];
+    for (int w = 0; w < n_warps; ++w) t += sbad[w];
     *bad_out = t;
   }
 }
@@ -310,8 +346,8 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
 // into them is a compile-time constant, so the FMAs of the correlation product and the drifts read
 // their coefficient straight from the constant bank, with no shared-memory load.
 template <class R, bool MM>
-__global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_kernel(const __grid_constant__ McArgs a,
-                                                             const __grid_constant__ McConsts<R> C) {
+__global__ void __launch_bounds__(mc_max_threads<R>(), 1) mc_path_kernel(const __grid_constant__ McArgs a,
+                                                                    const __grid_constant__ McConsts<R> C) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n_instr = a.n_cap + a.n_swp;
   mc_paths<R, MM>(a, C, (double*)smem, a.part + (size_t)blockIdx.x * n_instr * 2, a.bad + blockIdx.x);
@@ -321,13 +357,13 @@ __global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_ke
 // Cs[set] (staged into shared memory ahead of the per-warp sums) and its own CTA sums,
 // part[(set x gridDim.x + CTA) x n_instr x 2], bad[set x gridDim.x + CTA].
 template <class R>
-__host__ __device__ inline size_t mc_batch_smem_bytes(int n_instr) {
-  return ((sizeof(McConsts<R>) + 127) & ~(size_t)127) + mc_smem_bytes(n_instr);
+__host__ __device__ inline size_t mc_batch_smem_bytes(int n_instr, int threads) {
+  return ((sizeof(McConsts<R>) + 127) & ~(size_t)127) + mc_smem_bytes(n_instr, threads);
 }
 
 template <class R, bool MM>
-__global__ void __launch_bounds__(kMcThreads, sizeof(R) == 4 ? 4 : 1) mc_path_batch_kernel(const __grid_constant__ McArgs a,
-                                                                   const McConsts<R>* __restrict__ Cs) {
+__global__ void __launch_bounds__(mc_max_threads<R>(), 1) mc_path_batch_kernel(const __grid_constant__ McArgs a,
+                                                                          const McConsts<R>* __restrict__ Cs) {
   extern __shared__ __align__(128) unsigned char smem[];
   McConsts<R>& C = *(McConsts<R>*)smem;
   const int set = blockIdx.y, n_instr = a.n_cap + a.n_swp;

@@ -13,6 +13,7 @@ struct sabr_lmm_mc_plan {
   int device = 0;
   int prec = SABR_LMM_FP32;
   int grid = 0;
+  int threads = 128;            // paths per CTA
   int n_cap = 0, n_swp = 0;
   McArgs args{};
   McConsts<double> c64{};
@@ -249,12 +250,21 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   for (int k = 0; k < M; ++k) { cap_lo[k + 1] += cap_lo[k]; swp_lo[k + 1] += swp_lo[k]; }
   p->cap_order = ci;
   p->swp_order = si;
-  // grid: enough CTAs for every path, at most 8 per SM (persistent beyond that)
+  const int ni = d->n_cap + d->n_swp;
+  // CTA size: the largest (up to 512 paths in FP32, 128 in FP64) whose per-warp sums, with the
+  // batch kernel's staged constants, fit in a CTA's shared memory.  Grid: enough CTAs for every
+  // path, at most one wave of 512 paths per SM in FP32 (8 CTAs per SM in FP64), persistent beyond.
+  const bool f64 = o->prec == SABR_LMM_FP64;
+  const int tmax = f64 ? mc_max_threads<double>() : mc_max_threads<float>();
+  p->threads = tmax;
+  while (p->threads > 32 && (f64 ? mc_batch_smem_bytes<double>(ni, p->threads)
+                                 : mc_batch_smem_bytes<float>(ni, p->threads)) > kMcSmemMax)
+    p->threads /= 2;
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
-  const long long need = (o->n_paths + kMcThreads - 1) / kMcThreads;
-  p->grid = (int)std::min<long long>(need, o->grid > 0 ? o->grid : (long long)nsm * 8);
-  const int ni = d->n_cap + d->n_swp;
+  const long long need = (o->n_paths + p->threads - 1) / p->threads;
+  const long long cap = (long long)nsm * (f64 ? 8 : tmax / p->threads);
+  p->grid = (int)std::min<long long>(need, o->grid > 0 ? o->grid : cap);
   // device buffer: nsteps, h, tau, cap_lo, swp_lo, cap_out, swp_out, swp_b, cap_K, swp_K, part, bad, out, nbad
   Arena A;
   const size_t o_ns = A.take(M * 4), o_h = A.take(M * 8), o_tau = A.take(M * 8), o_clo = A.take((M + 1) * 4),
@@ -295,7 +305,7 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   a.part = (double*)(b + o_part); a.bad = (unsigned long long*)(b + o_bad);
   p->out = (double*)(b + o_out);
   p->nbad = (long long*)(b + o_nbad);
-  const size_t sm = mc_smem_bytes(ni);
+  const size_t sm = mc_smem_bytes(ni, p->threads);
   const bool mm = d->model == SABR_LMM_MODEL_MERCURIO_MORINI;
   e = o->prec == SABR_LMM_FP64 ? (mm ? raise_smem_limit(mc_path_kernel<double, true>, (uint32_t)sm)
                                      : raise_smem_limit(mc_path_kernel<double, false>, (uint32_t)sm))
@@ -318,14 +328,14 @@ extern "C" sabr_lmm_status sabr_lmm_mc_launch(sabr_lmm_mc_plan* p, double* price
   if (dev != p->device) return fail(SABR_LMM_EINVAL, "mc: the plan belongs to another device");
   cudaStream_t s = (cudaStream_t)stream;
   const int ni = p->n_cap + p->n_swp;
-  const size_t sm = mc_smem_bytes(ni);
+  const size_t sm = mc_smem_bytes(ni, p->threads);
   const bool mm = p->args.model == SABR_LMM_MODEL_MERCURIO_MORINI;
   if (p->prec == SABR_LMM_FP64) {
-    if (mm) mc_path_kernel<double, true><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c64);
-    else mc_path_kernel<double, false><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c64);
+    if (mm) mc_path_kernel<double, true><<<p->grid, p->threads, sm, s>>>(p->args, p->c64);
+    else mc_path_kernel<double, false><<<p->grid, p->threads, sm, s>>>(p->args, p->c64);
   } else {
-    if (mm) mc_path_kernel<float, true><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c32);
-    else mc_path_kernel<float, false><<<p->grid, kMcThreads, sm, s>>>(p->args, p->c32);
+    if (mm) mc_path_kernel<float, true><<<p->grid, p->threads, sm, s>>>(p->args, p->c32);
+    else mc_path_kernel<float, false><<<p->grid, p->threads, sm, s>>>(p->args, p->c32);
   }
   mc_reduce_kernel<<<(ni + 127) / 128, 128, 0, s>>>(p->args, p->grid, price ? price : p->out,
                                                       price ? stderr_out : p->out + ni, n_bad ? n_bad : p->nbad);
@@ -472,7 +482,7 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
                                                       (const double*)(b + o_vol), (double*)(b + o_mkt));
     e = cudaGetLastError();
   }
-  const size_t smb = f64 ? mc_batch_smem_bytes<double>(ni) : mc_batch_smem_bytes<float>(ni);
+  const size_t smb = f64 ? mc_batch_smem_bytes<double>(ni, p->threads) : mc_batch_smem_bytes<float>(ni, p->threads);
   const bool mmb = p->args.model == SABR_LMM_MODEL_MERCURIO_MORINI;
   if (e == cudaSuccess)
     e = f64 ? (mmb ? raise_smem_limit(mc_path_batch_kernel<double, true>, (uint32_t)smb)
@@ -505,11 +515,11 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
     const McConsts<double>* c64 = (const McConsts<double>*)(b + o_cs);
     const McConsts<float>* c32 = (const McConsts<float>*)(b + o_cs);
     if (f64) {
-      if (mmb) mc_path_batch_kernel<double, true><<<grid, kMcThreads, smb, s>>>(ab, c64);
-      else mc_path_batch_kernel<double, false><<<grid, kMcThreads, smb, s>>>(ab, c64);
+      if (mmb) mc_path_batch_kernel<double, true><<<grid, p->threads, smb, s>>>(ab, c64);
+      else mc_path_batch_kernel<double, false><<<grid, p->threads, smb, s>>>(ab, c64);
     } else {
-      if (mmb) mc_path_batch_kernel<float, true><<<grid, kMcThreads, smb, s>>>(ab, c32);
-      else mc_path_batch_kernel<float, false><<<grid, kMcThreads, smb, s>>>(ab, c32);
+      if (mmb) mc_path_batch_kernel<float, true><<<grid, p->threads, smb, s>>>(ab, c32);
+      else mc_path_batch_kernel<float, false><<<grid, p->threads, smb, s>>>(ab, c32);
     }
     mc_objective_kernel<<<(n + 3) / 4, 128, 0, s>>>(ab, G, n, (const double*)(b + o_mkt), (double*)(b + o_f));
     if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
