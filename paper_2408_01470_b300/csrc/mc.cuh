@@ -57,7 +57,10 @@ struct McArgs {
   const double* cap_K;           // [n_cap] sorted
   const double* swp_K;           // [n_swp] sorted
   const int* swp_b;              // [n_swp] one past the swap's last forward (sorted)
-  const double* tau64;           // [M] accruals (FP64, for the payoffs)
+  const double* tau64;           // [M] accruals (for the FP64 payoffs)
+  const float* cap_K32;          // [n_cap] cap_K in FP32 (the FP32 payoffs)
+  const float* swp_K32;          // [n_swp]
+  const float* tau32;            // [M]
   unsigned long long seed;
   long long n_paths;
   double* part;                  // [grid x (n_cap + n_swp) x 2] per-CTA sums of payoff, payoff^2
@@ -114,6 +117,27 @@ template <> __device__ __forceinline__ float mc_log<float>(float x) { return __l
 template <class R> __device__ __forceinline__ R mc_rcp(R x);
 template <> __device__ __forceinline__ double mc_rcp<double>(double x) { return 1.0 / x; }
 template <> __device__ __forceinline__ float mc_rcp<float>(float x) { return __frcp_rn(x); }
+
+// Payoff inputs in the path precision: FP32 copies of the strikes and accruals for the FP32 paths.
+template <class R> __device__ __forceinline__ R mc_tau(const McArgs& a, int j) {
+  if constexpr (sizeof(R) == 4) return a.tau32[j];
+  else return a.tau64[j];
+}
+template <class R> __device__ __forceinline__ R mc_cap_K(const McArgs& a, int c) {
+  if constexpr (sizeof(R) == 4) return a.cap_K32[c];
+  else return a.cap_K[c];
+}
+template <class R> __device__ __forceinline__ R mc_swp_K(const McArgs& a, int c) {
+  if constexpr (sizeof(R) == 4) return a.swp_K32[c];
+  else return a.swp_K[c];
+}
+// Sum over the warp (butterfly), in the path precision: the 32 payoffs of a warp in FP32 for FP32
+// paths (relative rounding ~1e-7 of the sum), every warp's sum then accumulated in FP64.
+template <class R> __device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
 
 __device__ __forceinline__ double warp_sum_mc(double v) {
 #pragma unroll
@@ -269,7 +293,7 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
 #pragma unroll
     for (int u = 0; u < kMcMaxFwd; ++u) { F[u] = C.F0[u]; lnV[u] = C.lnV0[u]; }
     bool good = live;
-    double numer = a.P0;   // 1 / B(T_k) at the start of interval k
+    R numer = (R)a.P0;     // 1 / B(T_k) at the start of interval k
     int step = 0;
     for (int k = 0; k < a.n_int; ++k) {
       if (warp_live) {
@@ -295,29 +319,41 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
         }
         if (good && !fin) ++nbad;
         good = good && fin;
-        const double fix = (double)Fs[na - 1];
-        // swaptions expiring at T_k, deflated by 1 / B(T_k)
-        for (int c = a.swp_lo[k]; c < a.swp_lo[k + 1]; ++c) {
-          double pay = 0.0;
-          if (good) {
-            const int b = a.swp_b[c];
-            double disc = 1.0, A = 0.0;
-            for (int j = k; j < b; ++j) {
-              disc /= 1.0 + a.tau64[j] * (double)Fs[M - 1 - j];
-              A += a.tau64[j] * disc;
+        const R fix = Fs[na - 1];
+        // swaptions expiring at T_k (sorted by swap end), deflated by 1 / B(T_k): one running product
+        // disc_j = prod_{l=k..j} 1 / (1 + tau_l F_l) serves them all, with the annuity A = sum tau_j
+        // disc_j; the swap rate is (1 - disc) / A, in FP32 (sum tau_j F_j disc_j) / A, the same
+        // number as a sum of positive terms (1 - disc_j telescopes into it), free of cancellation
+        {
+          R disc = 1, A = 0, fl = 0;
+          int j = k;
+          for (int c = a.swp_lo[k]; c < a.swp_lo[k + 1]; ++c) {
+            R pay = 0;
+            if (good) {
+              for (const int b = a.swp_b[c]; j < b; ++j) {
+                const R tj = mc_tau<R>(a, j), Fj = Fs[M - 1 - j];
+                disc = disc / (R(1) + tj * Fj);
+                A += tj * disc;
+                if constexpr (sizeof(R) == 4) fl += tj * Fj * disc;
+              }
+              R S;
+              if constexpr (sizeof(R) == 4) S = fl / A;
+              else S = (R(1) - disc) / A;
+              const R dS = S - mc_swp_K<R>(a, c);
+              pay = dS > R(0) ? A * dS * numer : R(0);
             }
-            const double S = (1.0 - disc) / A;
-            pay = A * fmax(S - a.swp_K[c], 0.0) * numer;
+            const R s1 = warp_sum_r(pay), s2 = warp_sum_r(pay * pay);
+            if (lane == 0) { wacc[2 * (a.n_cap + c)] += (double)s1; wacc[2 * (a.n_cap + c) + 1] += (double)s2; }
           }
-          const double s1 = warp_sum_mc(pay), s2 = warp_sum_mc(pay * pay);
-          if (lane == 0) { wacc[2 * (a.n_cap + c)] += s1; wacc[2 * (a.n_cap + c) + 1] += s2; }
         }
-        numer = good ? numer / (1.0 + a.tau64[k] * fix) : 0.0;
+        const R tk = mc_tau<R>(a, k);
+        numer = good ? numer / (R(1) + tk * fix) : R(0);
         // caplets on forward k, paid at T_{k+1}
         for (int c = a.cap_lo[k]; c < a.cap_lo[k + 1]; ++c) {
-          const double pay = good ? a.tau64[k] * fmax(fix - a.cap_K[c], 0.0) * numer : 0.0;
-          const double s1 = warp_sum_mc(pay), s2 = warp_sum_mc(pay * pay);
-          if (lane == 0) { wacc[2 * c] += s1; wacc[2 * c + 1] += s2; }
+          const R dK = fix - mc_cap_K<R>(a, c);
+          const R pay = good && dK > R(0) ? tk * dK * numer : R(0);
+          const R s1 = warp_sum_r(pay), s2 = warp_sum_r(pay * pay);
+          if (lane == 0) { wacc[2 * c] += (double)s1; wacc[2 * c + 1] += (double)s2; }
         }
       }
       __syncthreads();

@@ -233,17 +233,23 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   for (int c = 0; c < d->n_cap; ++c) ci[c] = c;
   for (int c = 0; c < d->n_swp; ++c) si[c] = c;
   std::stable_sort(ci.begin(), ci.end(), [&](int x, int y) { return d->cap_fwd[x] < d->cap_fwd[y]; });
-  std::stable_sort(si.begin(), si.end(), [&](int x, int y) { return d->swp_start[x] < d->swp_start[y]; });
+  // swaptions by expiry, then by swap end: at a fixing one running discount product serves them all
+  std::stable_sort(si.begin(), si.end(), [&](int x, int y) {
+    return d->swp_start[x] != d->swp_start[y] ? d->swp_start[x] < d->swp_start[y] : d->swp_end[x] < d->swp_end[y];
+  });
   std::vector<int> cap_lo(M + 1, 0), swp_lo(M + 1, 0), cap_out(d->n_cap), swp_out(d->n_swp), swp_b(d->n_swp);
   std::vector<double> cap_K(d->n_cap), swp_K(d->n_swp);
+  std::vector<float> cap_K32(d->n_cap), swp_K32(d->n_swp), tau32(M);
   for (int c = 0; c < d->n_cap; ++c) {
     cap_out[c] = ci[c];
     cap_K[c] = d->cap_K[ci[c]];
+    cap_K32[c] = (float)cap_K[c];
     cap_lo[d->cap_fwd[ci[c]] + 1]++;
   }
   for (int c = 0; c < d->n_swp; ++c) {
     swp_out[c] = si[c];
     swp_K[c] = d->swp_K[si[c]];
+    swp_K32[c] = (float)swp_K[c];
     swp_b[c] = d->swp_end[si[c]];
     swp_lo[d->swp_start[si[c]] + 1]++;
   }
@@ -265,11 +271,14 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   const long long need = (o->n_paths + p->threads - 1) / p->threads;
   const long long cap = (long long)nsm * (f64 ? 8 : tmax / p->threads);
   p->grid = (int)std::min<long long>(need, o->grid > 0 ? o->grid : cap);
-  // device buffer: nsteps, h, tau, cap_lo, swp_lo, cap_out, swp_out, swp_b, cap_K, swp_K, part, bad, out, nbad
+  for (int k = 0; k < M; ++k) tau32[k] = (float)tau[k];
+  // device buffer: nsteps, h, tau, cap_lo, swp_lo, cap_out, swp_out, swp_b, cap_K, swp_K, their FP32
+  // copies, part, bad, out, nbad
   Arena A;
   const size_t o_ns = A.take(M * 4), o_h = A.take(M * 8), o_tau = A.take(M * 8), o_clo = A.take((M + 1) * 4),
                o_slo = A.take((M + 1) * 4), o_cout = A.take(d->n_cap * 4), o_sout = A.take(d->n_swp * 4),
                o_sb = A.take(d->n_swp * 4), o_cK = A.take(d->n_cap * 8), o_sK = A.take(d->n_swp * 8),
+               o_cK32 = A.take(d->n_cap * 4), o_sK32 = A.take(d->n_swp * 4), o_tau32 = A.take(M * 4),
                o_part = A.take((size_t)p->grid * ni * 16), o_bad = A.take((size_t)p->grid * 8),
                o_out = A.take((size_t)ni * 16), o_nbad = A.take(8);
   std::vector<unsigned char> host(A.size, 0);
@@ -278,6 +287,7 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   put(o_clo, cap_lo.data(), (M + 1) * 4); put(o_slo, swp_lo.data(), (M + 1) * 4);
   put(o_cout, cap_out.data(), d->n_cap * 4); put(o_sout, swp_out.data(), d->n_swp * 4);
   put(o_sb, swp_b.data(), d->n_swp * 4); put(o_cK, cap_K.data(), d->n_cap * 8); put(o_sK, swp_K.data(), d->n_swp * 8);
+  put(o_cK32, cap_K32.data(), d->n_cap * 4); put(o_sK32, swp_K32.data(), d->n_swp * 4); put(o_tau32, tau32.data(), M * 4);
   if (cudaMalloc(&p->buf, A.size) != cudaSuccess) {
     delete p;
     return fail(SABR_LMM_ENOMEM, "mc: cudaMalloc of the plan's buffers failed");
@@ -301,6 +311,7 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   a.cap_lo = (const int*)(b + o_clo); a.swp_lo = (const int*)(b + o_slo);
   a.cap_out = (const int*)(b + o_cout); a.swp_out = (const int*)(b + o_sout); a.swp_b = (const int*)(b + o_sb);
   a.cap_K = (const double*)(b + o_cK); a.swp_K = (const double*)(b + o_sK);
+  a.cap_K32 = (const float*)(b + o_cK32); a.swp_K32 = (const float*)(b + o_sK32); a.tau32 = (const float*)(b + o_tau32);
   a.seed = o->seed; a.n_paths = o->n_paths;
   a.part = (double*)(b + o_part); a.bad = (unsigned long long*)(b + o_bad);
   p->out = (double*)(b + o_out);
