@@ -159,9 +159,6 @@ __device__ __forceinline__ void mc_interval(const McConsts<R>& C, R (&F)[kMcMaxF
                                             const uint32_t k1, const R beta) {
   constexpr int na = NA;
   for (int s = 0; s < ns; ++s, ++step) {
-    // The constants are read where they are used, every step: held across the steps (shared
-    // memory in the batch kernel) they would take more registers than a thread has.
-    asm volatile("" ::: "memory");
     R xi[kMcRows];
 #pragma unroll
     for (int b = 0; b < kMcRows / 4; ++b) {
@@ -387,31 +384,6 @@ __global__ void __launch_bounds__(mc_max_threads<R>(), 1) mc_path_kernel(const _
   extern __shared__ __align__(128) unsigned char smem[];
   const int n_instr = a.n_cap + a.n_swp;
   mc_paths<R, MM>(a, C, (double*)smem, a.part + (size_t)blockIdx.x * n_instr * 2, a.bad + blockIdx.x);
-}
-
-// Many parameter sets in one launch (the annealer's proposals): set blockIdx.y has its constants
-// Cs[set] (staged into shared memory ahead of the per-warp sums) and its own CTA sums,
-// part[(set x gridDim.x + CTA) x n_instr x 2], bad[set x gridDim.x + CTA].
-template <class R>
-__host__ __device__ inline size_t mc_batch_smem_bytes(int n_instr, int threads) {
-  return ((sizeof(McConsts<R>) + 127) & ~(size_t)127) + mc_smem_bytes(n_instr, threads);
-}
-
-template <class R, bool MM>
-__global__ void __launch_bounds__(mc_max_threads<R>(), 1) mc_path_batch_kernel(const __grid_constant__ McArgs a,
-                                                                          const McConsts<R>* __restrict__ Cs) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  McConsts<R>& C = *(McConsts<R>*)smem;
-  const int set = blockIdx.y, n_instr = a.n_cap + a.n_swp;
-  {
-    const uint4* src = (const uint4*)(Cs + set);
-    uint4* dst = (uint4*)smem;
-    for (int t = threadIdx.x; t < (int)(sizeof(McConsts<R>) / 16); t += blockDim.x) dst[t] = src[t];
-  }
-  // (mc_paths synchronises the CTA before it reads C)
-  double* acc = (double*)(smem + ((sizeof(McConsts<R>) + 127) & ~(size_t)127));
-  const size_t cta = (size_t)set * gridDim.x + blockIdx.x;
-  mc_paths<R, MM>(a, C, acc, a.part + cta * n_instr * 2, a.bad + cta);
 }
 
 // f_s of every set: the Monte Carlo prices from its CTA sums (CTA by CTA in order) against the

@@ -257,14 +257,13 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   p->cap_order = ci;
   p->swp_order = si;
   const int ni = d->n_cap + d->n_swp;
-  // CTA size: the largest (up to 512 paths in FP32, 128 in FP64) whose per-warp sums, with the
-  // batch kernel's staged constants, fit in a CTA's shared memory.  Grid: enough CTAs for every
-  // path, at most one wave of 512 paths per SM in FP32 (8 CTAs per SM in FP64), persistent beyond.
+  // CTA size: the largest (up to 512 paths in FP32, 128 in FP64) whose per-warp sums fit in a
+  // CTA's shared memory.  Grid: enough CTAs for every path, at most one wave of 512 paths per SM in
+  // FP32 (8 CTAs per SM in FP64), persistent beyond.
   const bool f64 = o->prec == SABR_LMM_FP64;
   const int tmax = f64 ? mc_max_threads<double>() : mc_max_threads<float>();
   p->threads = tmax;
-  while (p->threads > 32 && (f64 ? mc_batch_smem_bytes<double>(ni, p->threads)
-                                 : mc_batch_smem_bytes<float>(ni, p->threads)) > kMcSmemMax)
+  while (p->threads > 32 && mc_smem_bytes(ni, p->threads) > kMcSmemMax)
     p->threads /= 2;
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
@@ -439,32 +438,40 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
   if (st != SABR_LMM_OK) return st;
   const int C = o->n_chains, L = o->n_levels, N = o->steps_per_level, P = 5, M = p->M, G = p->grid;
   const bool f64 = p->prec == SABR_LMM_FP64;
-  const size_t csz = f64 ? sizeof(McConsts<double>) : sizeof(McConsts<float>);
   cudaStream_t s = (cudaStream_t)stream;
-  // device: the constants of C sets, their CTA sums and stopped paths, f, the market prices, and the
-  // sorted instruments' quotes with the tenor grid; host (pinned): the constants and f
+  // device: the CTA sums and stopped paths of C sets, f, the market prices, and the sorted
+  // instruments' quotes with the tenor grid; host (pinned): f
   Arena A;
-  const size_t o_cs = A.take((size_t)C * csz), o_part = A.take((size_t)C * G * ni * 16), o_bad = A.take((size_t)C * G * 8),
+  const size_t o_part = A.take((size_t)C * G * ni * 16), o_bad = A.take((size_t)C * G * 8),
                o_f = A.take((size_t)C * 8), o_mkt = A.take((size_t)ni * 8), o_vol = A.take((size_t)ni * 8),
                o_cf = A.take((size_t)p->n_cap * 4), o_sa = A.take((size_t)p->n_swp * 4),
                o_T = A.take((size_t)(d->n_fwd + 1) * 8), o_P = A.take((size_t)(d->n_fwd + 1) * 8);
   void* dbuf = nullptr;
-  unsigned char* hcs = nullptr;
   double* hf = nullptr;
-  if (cudaMalloc(&dbuf, A.size) != cudaSuccess || cudaMallocHost((void**)&hcs, (size_t)C * csz) != cudaSuccess ||
-      cudaMallocHost((void**)&hf, (size_t)C * 8) != cudaSuccess) {
-    if (dbuf) cudaFree(dbuf);
-    if (hcs) cudaFreeHost(hcs);
-    sabr_lmm_mc_plan_free(p);
-    return fail(SABR_LMM_ENOMEM, "mc_anneal: allocation of the search buffers failed");
-  }
+  // the proposals' launches spread over side streams (each launch fills G CTAs of the GPU)
+  constexpr int kSide = 8;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
+  bool ok = cudaMalloc(&dbuf, A.size) == cudaSuccess && cudaMallocHost((void**)&hf, (size_t)C * 8) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < kSide && ok; ++k)
+    ok = cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev_join[k], cudaEventDisableTiming) == cudaSuccess;
   char* b = (char*)dbuf;
   auto cleanup = [&]() {
-    cudaFree(dbuf);
-    cudaFreeHost(hcs);
-    cudaFreeHost(hf);
+    if (dbuf) cudaFree(dbuf);
+    if (hf) cudaFreeHost(hf);
+    for (int k = 0; k < kSide; ++k) {
+      if (side[k]) cudaStreamDestroy(side[k]);
+      if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
     sabr_lmm_mc_plan_free(p);
   };
+  if (!ok) {
+    cleanup();
+    return fail(SABR_LMM_ENOMEM, "mc_anneal: allocation of the search buffers or streams failed");
+  }
   std::vector<double> vol_sorted(ni);
   std::vector<int> cf_sorted(p->n_cap), sa_sorted(p->n_swp);
   for (int c = 0; c < p->n_cap; ++c) {
@@ -493,45 +500,53 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
                                                       (const double*)(b + o_vol), (double*)(b + o_mkt));
     e = cudaGetLastError();
   }
-  const size_t smb = f64 ? mc_batch_smem_bytes<double>(ni, p->threads) : mc_batch_smem_bytes<float>(ni, p->threads);
+  const size_t sm = mc_smem_bytes(ni, p->threads);   // the plan's kernel: its limit is raised already
   const bool mmb = p->args.model == SABR_LMM_MODEL_MERCURIO_MORINI;
-  if (e == cudaSuccess)
-    e = f64 ? (mmb ? raise_smem_limit(mc_path_batch_kernel<double, true>, (uint32_t)smb)
-                   : raise_smem_limit(mc_path_batch_kernel<double, false>, (uint32_t)smb))
-            : (mmb ? raise_smem_limit(mc_path_batch_kernel<float, true>, (uint32_t)smb)
-                   : raise_smem_limit(mc_path_batch_kernel<float, false>, (uint32_t)smb));
   if (e != cudaSuccess) {
     cleanup();
     return fail(SABR_LMM_ECUDA, std::string("mc_anneal: ") + cudaGetErrorString(e));
   }
-  // f_s of n points Y [n x 5]: constants on the host (threads), one batched launch, f back
+  // f_s of n points Y [n x 5]: constants on the host (threads); one pricing launch per point, its
+  // constants in the kernel parameters (the constant bank, as in the pricer: every coefficient an
+  // FMA operand), the launches spread over the side streams; f back on `stream`
   const unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<McConsts<double>> h64(f64 ? C : 0);
+  std::vector<McConsts<float>> h32(f64 ? 0 : C);
   auto evaluate = [&](const std::vector<double>& Y, int n, double* f) -> cudaError_t {
     auto work = [&](int lo, int hi) {
       for (int i = lo; i < hi; ++i) {
         McConsts<double> c64;
         McConsts<float> c32;
         mc_build_consts(d, M, p->tau.data(), &Y[(size_t)i * P], c64, c32);
-        if (f64) std::memcpy(hcs + (size_t)i * csz, &c64, csz);
-        else std::memcpy(hcs + (size_t)i * csz, &c32, csz);
+        if (f64) h64[i] = c64;
+        else h32[i] = c32;
       }
     };
     std::vector<std::thread> th;
     const int per = (n + (int)nthr - 1) / (int)nthr;
     for (int t = 0; t * per < n; ++t) th.emplace_back(work, t * per, std::min(n, (t + 1) * per));
     for (auto& t : th) t.join();
-    cudaError_t ee = cudaMemcpyAsync(b + o_cs, hcs, (size_t)n * csz, cudaMemcpyHostToDevice, s);
-    if (ee != cudaSuccess) return ee;
-    const dim3 grid(G, n);
-    const McConsts<double>* c64 = (const McConsts<double>*)(b + o_cs);
-    const McConsts<float>* c32 = (const McConsts<float>*)(b + o_cs);
-    if (f64) {
-      if (mmb) mc_path_batch_kernel<double, true><<<grid, p->threads, smb, s>>>(ab, c64);
-      else mc_path_batch_kernel<double, false><<<grid, p->threads, smb, s>>>(ab, c64);
-    } else {
-      if (mmb) mc_path_batch_kernel<float, true><<<grid, p->threads, smb, s>>>(ab, c32);
-      else mc_path_batch_kernel<float, false><<<grid, p->threads, smb, s>>>(ab, c32);
+    cudaError_t ee = cudaEventRecord(ev_fork, s);
+    for (int k = 0; k < kSide && ee == cudaSuccess; ++k) ee = cudaStreamWaitEvent(side[k], ev_fork, 0);
+    for (int i = 0; i < n && ee == cudaSuccess; ++i) {
+      McArgs ai = ab;
+      ai.part = ab.part + (size_t)i * G * ni * 2;
+      ai.bad = ab.bad + (size_t)i * G;
+      cudaStream_t si = side[i % kSide];
+      if (f64) {
+        if (mmb) mc_path_kernel<double, true><<<G, p->threads, sm, si>>>(ai, h64[i]);
+        else mc_path_kernel<double, false><<<G, p->threads, sm, si>>>(ai, h64[i]);
+      } else {
+        if (mmb) mc_path_kernel<float, true><<<G, p->threads, sm, si>>>(ai, h32[i]);
+        else mc_path_kernel<float, false><<<G, p->threads, sm, si>>>(ai, h32[i]);
+      }
+      ee = cudaGetLastError();
     }
+    for (int k = 0; k < kSide && ee == cudaSuccess; ++k) {
+      ee = cudaEventRecord(ev_join[k], side[k]);
+      if (ee == cudaSuccess) ee = cudaStreamWaitEvent(s, ev_join[k], 0);
+    }
+    if (ee != cudaSuccess) return ee;
     mc_objective_kernel<<<(n + 3) / 4, 128, 0, s>>>(ab, G, n, (const double*)(b + o_mkt), (double*)(b + o_f));
     if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
     if ((ee = cudaMemcpyAsync(hf, b + o_f, (size_t)n * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return ee;
