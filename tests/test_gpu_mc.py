@@ -157,6 +157,55 @@ def test_mc_rejects_bad_input(gpu_lib):
     assert e.value.status == 5 and "16 forwards" in str(e.value)
 
 
+def test_mc_sixteen_forwards_match_the_oracle(gpu_lib):
+    # the largest tenor structure the pricer takes: every interval's step code, down to 16 alive
+    # forwards, against the oracle's paths (FP64) and within the FP32 bar
+    import paper_2408_01470_b300 as lib
+    sk = synth.caplet_term_structure(n_fwd=16)
+    M = 16
+    m16 = dict(M=M, beta=0.5, eta1=0.8, lambda1=0.5, eta2=0.9, lambda2=0.3, lambda3=0.1,
+               alpha=np.linspace(0.05, 0.08, M), sigma=np.linspace(0.4, 0.25, M), phi=np.linspace(-0.4, 0.2, M))
+    om = oracle.Market(sk, np.full(sk.n_cap, 0.5))
+    F = om.info()["F"]
+    cf = np.repeat(np.arange(M), 2)
+    ck = np.concatenate([F[i] * np.array([0.9, 1.2]) for i in range(M)])
+    sa, sb = np.array([0, 3, 7, 12]), np.array([16, 10, 16, 16])
+    P, T = sk.P, sk.T
+    sK = np.array([(P[a] - P[b]) / sum((T[j + 1] - T[j]) * P[j + 1] for j in range(a, b)) for a, b in zip(sa, sb)])
+    po, so, bo = oracle.mc_price(om, m16, cap_fwd=cf, cap_K=ck, swp_a=sa, swp_b=sb, swp_K=sK, n_paths=1000, dt=0.1,
+                                 seed=41, n_threads=16)
+    pg, sg, bg = lib.mc_price(T, P, m16, cf, ck, sa, sb, sK, n_paths=1000, dt=0.1, seed=41, prec="fp64")
+    assert bg == bo
+    nz = po > 0
+    assert np.array_equal(nz, pg > 0)
+    assert np.max(np.abs(pg[nz] - po[nz]) / po[nz]) <= 1e-11
+    p32, _, b32 = lib.mc_price(T, P, m16, cf, ck, sa, sb, sK, n_paths=1000, dt=0.1, seed=41, prec="fp32")
+    big = po > 1e-3 * po.max()
+    rel = np.abs(p32[big] - po[big]) / po[big]
+    print(f"MC 16 forwards: FP64 max relative {np.max(np.abs(pg[nz] - po[nz]) / po[nz]):.2e}, FP32 {rel.max():.2e}")
+    assert b32 == bo and rel.max() <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mc_many_instruments_shrink_the_cta(gpu_lib, prec):
+    # 4096 caplets (the limit): the per-warp sums of a 512- or 128-path CTA would not fit in shared
+    # memory, so the plan takes 64-path CTAs; the prices are still the oracle's
+    import paper_2408_01470_b300 as lib
+    sk, model, _, _, _ = _paper()
+    om = oracle.Market(sk, np.full(sk.n_cap, 0.5))
+    F = om.info()["F"]
+    rng = np.random.default_rng(7)
+    cf = rng.integers(0, sk.n_fwd, 4096)
+    ck = F[cf] * rng.uniform(0.6, 1.6, 4096)
+    po, _, bo = oracle.mc_price(om, model, cap_fwd=cf, cap_K=ck, n_paths=1024, dt=0.1, seed=43, n_threads=16)
+    pg, _, bg = lib.mc_price(sk.T, sk.P, model, cf, ck, n_paths=1024, dt=0.1, seed=43, prec=prec)
+    assert bg == bo == 0
+    big = po > 1e-3 * po.max()
+    rel = np.abs(pg[big] - po[big]) / po[big]
+    assert rel.max() <= (1e-11 if prec == "fp64" else 1e-5), rel.max()
+    assert np.max(np.abs(pg[~big] - po[~big]), initial=0.0) <= (1e-15 if prec == "fp64" else 1e-7)
+
+
 # ---------------------------------------------------------------- SA over the Monte Carlo objective
 def _self_quoted(M=6, n_paths=2000, dt=0.05, seed=5):
     """Payer swaptions on the paper's first M forwards, quoted at the Black vols that reproduce the
