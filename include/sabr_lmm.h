@@ -409,8 +409,9 @@ typedef struct {
  * ceil(len / dt) equal steps; seed: the key of the paths' Philox4x32-10 streams (path p, step s,
  * block b at counter (b, s, p low, p high)); prec: FP64 or FP32 (the path arithmetic; sums in
  * FP64); grid: CTAs (0: enough for every path, at most one wave per SM, the rest looped); a CTA
- * takes 512 paths in FP32 and 128 in FP64, halved while its per-warp sums (16 bytes per
- * instrument and warp) would not fit in 227 KB of shared memory.                                */
+ * takes 512 paths in FP32 and 128 in FP64 (fewer, in whole warps, when the paths do not fill one
+ * such CTA per SM), halved while its per-warp sums (16 bytes per instrument and warp) would not
+ * fit in 227 KB of shared memory.                                                              */
 typedef struct {
   int64_t n_paths;
   double dt;

@@ -198,8 +198,11 @@ std::string mc_validate(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o) {
 
 }  // namespace
 
-extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o, void* stream,
-                                               sabr_lmm_mc_plan** out) {
+namespace {
+// shrink: CTAs smaller than the largest when the paths do not fill one per SM (a pricing alone on the
+// GPU); the annealer's many concurrent launches keep the largest, so that an SM runs one CTA.
+sabr_lmm_status mc_prepare(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o, void* stream, sabr_lmm_mc_plan** out,
+                           bool shrink) {
   if (!out) return fail(SABR_LMM_EINVAL, "out is required");
   *out = nullptr;
   const std::string e0 = mc_validate(d, o);
@@ -262,13 +265,25 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   // FP32 (8 CTAs per SM in FP64), persistent beyond.
   const bool f64 = o->prec == SABR_LMM_FP64;
   const int tmax = f64 ? mc_max_threads<double>() : mc_max_threads<float>();
-  p->threads = tmax;
-  while (p->threads > 32 && mc_smem_bytes(ni, p->threads) > kMcSmemMax)
-    p->threads /= 2;
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+  // a pricing alone on the GPU: the paths split evenly over the rounds of one CTA per SM, in whole
+  // warps (the rounds a largest CTA would need, each of fewer paths: the last round is not mostly
+  // empty, and fewer paths than one largest CTA per SM spread over all SMs)
+  p->threads = tmax;
+  if (shrink) {
+    const long long per_round = (long long)nsm * tmax;
+    const long long rounds = (o->n_paths + per_round - 1) / per_round;
+    const long long per_cta = (o->n_paths + nsm * rounds - 1) / (nsm * rounds);
+    p->threads = (int)std::min<long long>(tmax, std::max<long long>(32, (per_cta + 31) / 32 * 32));
+  }
+  const int t_req = p->threads;
+  while (p->threads > 32 && mc_smem_bytes(ni, p->threads) > kMcSmemMax)
+    p->threads = std::max(32, p->threads / 64 * 32);
   const long long need = (o->n_paths + p->threads - 1) / p->threads;
-  const long long cap = (long long)nsm * (f64 ? 8 : tmax / p->threads);
+  // FP32: one CTA per SM, looping over its rounds (as many CTAs per SM as the shared-memory limit
+  // took from the CTA size); FP64: up to 8 CTAs per SM
+  const long long cap = (long long)nsm * (f64 ? 8 : std::max(1, t_req / p->threads));
   p->grid = (int)std::min<long long>(need, o->grid > 0 ? o->grid : cap);
   for (int k = 0; k < M; ++k) tau32[k] = (float)tau[k];
   // device buffer: nsteps, h, tau, cap_lo, swp_lo, cap_out, swp_out, swp_b, cap_K, swp_K, their FP32
@@ -328,6 +343,12 @@ extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const 
   }
   *out = p;
   return SABR_LMM_OK;
+}
+}  // namespace
+
+extern "C" sabr_lmm_status sabr_lmm_mc_prepare(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o, void* stream,
+                                               sabr_lmm_mc_plan** out) {
+  return mc_prepare(d, o, stream, out, true);
 }
 
 extern "C" sabr_lmm_status sabr_lmm_mc_launch(sabr_lmm_mc_plan* p, double* price, double* stderr_out,
@@ -434,7 +455,7 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
   for (int k = 0; k < ni; ++k)
     if (!(quote_vol[k] > 0.0) || !std::isfinite(quote_vol[k])) return fail(SABR_LMM_EINVAL, "mc_anneal: quote_vol must be finite and > 0");
   sabr_lmm_mc_plan* p = nullptr;
-  sabr_lmm_status st = sabr_lmm_mc_prepare(d, mo, stream, &p);
+  sabr_lmm_status st = mc_prepare(d, mo, stream, &p, false);
   if (st != SABR_LMM_OK) return st;
   const int C = o->n_chains, L = o->n_levels, N = o->steps_per_level, P = 5, M = p->M, G = p->grid;
   const bool f64 = p->prec == SABR_LMM_FP64;
