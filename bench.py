@@ -625,8 +625,8 @@ def mc_calibration_record(lib, stream, chains=64, levels=20, steps=5, n_paths=10
     return {"workload": f"paper_{name}_swaption_calibration_mc_180swaptions_{chains}ch_x_{levels}T_x_{steps}steps_"
                         f"{n_paths}paths_dt{dt}",
             "how": "sabr_lmm_mc_anneal: host-driven annealing (the paper's own split), every step's proposals priced "
-                   "as one pricing launch each (constants in the kernel parameters) over eight side streams; wall time of "
-                   "the whole search",
+                   "in one batched Monte Carlo launch, their constants built by a pool of host threads; wall time of the "
+                   "whole search",
             "seconds": r["seconds"], "evaluations": int(r["n_evals"]), "f_best": r["f_best"],
             "y_best": [float(x) for x in r["y_best"]],
             "mae_percent": float(100.0 * np.mean(np.abs(mc - black))),

@@ -457,10 +457,10 @@ sabr_lmm_status sabr_lmm_mc_price(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_o
  * The search: the annealing loop of sabr_lmm_anneal on the 5-slot box lo/hi/free_mask (0 <= lo <=
  * hi, eta's <= 1), from y0 (or the box centre), T0 (<= 0: f_s(y0)), the same neighbour rule and
  * Philox4x64-10 uniforms (word k moves slot k, word 5 decides, chain c at counter (block, step,
- * level, c) under key (seed, 0)).  Every step evaluates the n_chains proposals with one pricing
- * launch each (its constants in the kernel parameters) spread over eight side streams that join
- * `stream` before f is read; the proposals' correlation
- * factors are built on the host threads, the Metropolis decisions taken on the host in FP64.
+ * level, c) under key (seed, 0)).  Every step evaluates the n_chains proposals in one launch (a
+ * CTA grid per proposal, its constants staged in shared memory); the proposals' correlation
+ * factors are built by a pool of host threads that lives for the call, the Metropolis decisions
+ * taken on the host in FP64.
  * Synchronous; allocates device and pinned host memory for the search.                       */
 typedef struct {
   int32_t n_chains, n_levels, steps_per_level;

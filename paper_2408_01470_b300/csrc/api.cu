@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 #include <thread>
+#include <condition_variable>
+#include <atomic>
 #include <chrono>
 
 #include "../../include/sabr_lmm.h"

@@ -33,12 +33,18 @@ constexpr int kMcMaxWarps = 16;
 constexpr size_t kMcSmemMax = 227 * 1024;   // dynamic shared memory a CTA may take
 
 // Model constants, in u-order (u = M - 1 - i), one copy per precision.
+// (16-byte aligned rows, so that reads of consecutive coefficients from shared memory combine into
+// 16-byte loads)
 template <class R> struct McConsts {
-  R L[kMcRows * kMcRows];          // Cholesky factor, row-major
-  R rho[kMcMaxFwd * kMcMaxFwd];    // rho(u, v): correlation of W_(M-1-u) with W_(M-1-v)
-  R phi[kMcMaxFwd * kMcMaxFwd];    // phi(u, v): correlation of W_(M-1-u) with Z_(M-1-v)
-  R tau[kMcMaxFwd], sig[kMcMaxFwd], hs2[kMcMaxFwd], F0[kMcMaxFwd], lnV0[kMcMaxFwd];
-  R alpha[kMcMaxFwd];              // Mercurio & Morini: alpha_i (the Hagan model's alpha is V_i(0))
+  alignas(16) R L[kMcRows * kMcRows];          // Cholesky factor, row-major
+  alignas(16) R rho[kMcMaxFwd * kMcMaxFwd];    // rho(u, v): correlation of W_(M-1-u) with W_(M-1-v)
+  alignas(16) R phi[kMcMaxFwd * kMcMaxFwd];    // phi(u, v): correlation of W_(M-1-u) with Z_(M-1-v)
+  alignas(16) R tau[kMcMaxFwd];
+  alignas(16) R sig[kMcMaxFwd];
+  alignas(16) R hs2[kMcMaxFwd];
+  alignas(16) R F0[kMcMaxFwd];
+  alignas(16) R lnV0[kMcMaxFwd];
+  alignas(16) R alpha[kMcMaxFwd];              // Mercurio & Morini: alpha_i (the Hagan model's alpha is V_i(0))
 };
 
 struct McArgs {
@@ -153,12 +159,15 @@ __host__ __device__ inline size_t mc_smem_bytes(int n_instr, int threads) {
 // The steps of one interval with NA alive forwards (u = 0 .. NA - 1), NA a compile-time constant:
 // every guard on the alive count folds away, and only the normals, rows and drift terms the
 // interval needs are generated.  The arithmetic and its order are those of every NA.
-template <class R, bool MM, int NA>
+template <class R, bool MM, bool SMEM, int NA>
 __device__ __forceinline__ void mc_interval(const McConsts<R>& C, R (&F)[kMcMaxFwd], R (&lnV)[kMcMaxFwd], const int ns,
                                             const R h, const R sh, int& step, const long long p, const uint32_t k0,
                                             const uint32_t k1, const R beta) {
   constexpr int na = NA;
   for (int s = 0; s < ns; ++s, ++step) {
+    // SMEM (constants in shared memory): read where they are used, every step; held in registers
+    // across the steps they would take more than a thread has
+    if constexpr (SMEM) asm volatile("" ::: "memory");
     R xi[kMcRows];
 #pragma unroll
     for (int b = 0; b < kMcRows / 4; ++b) {
@@ -265,7 +274,7 @@ __device__ __forceinline__ void mc_interval(const McConsts<R>& C, R (&F)[kMcMaxF
 // mu_i = alpha_i V F_i^b V sum_{j=k}^{i} rho_ij tau_j alpha_j F_j^b / (1 + tau_j F_j), dV = sigma V dZ,
 // V(0) = 1; the factor's row 0 is Z and row 1 + u is W of forward M - 1 - u, so a step draws 1 + a
 // normals; ln V is lnV[0].
-template <class R, bool MM>
+template <class R, bool MM, bool SMEM>
 __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, double* acc, double* part_out,
                                          unsigned long long* bad_out) {
   const int n_instr = a.n_cap + a.n_swp, n_warps = blockDim.x >> 5;
@@ -299,7 +308,7 @@ __device__ __forceinline__ void mc_paths(const McArgs& a, const McConsts<R>& C, 
         const R h = (R)a.h[k], sh = (R)sqrt(a.h[k]);
         switch (na) {
 #define SABR_MC_CASE(n) \
-    case n: mc_interval<R, MM, n>(C, F, lnV, ns, h, sh, step, p, k0, k1, beta); break;
+    case n: mc_interval<R, MM, SMEM, n>(C, F, lnV, ns, h, sh, step, p, k0, k1, beta); break;
           SABR_MC_CASE(1) SABR_MC_CASE(2) SABR_MC_CASE(3) SABR_MC_CASE(4) SABR_MC_CASE(5) SABR_MC_CASE(6)
           SABR_MC_CASE(7) SABR_MC_CASE(8) SABR_MC_CASE(9) SABR_MC_CASE(10) SABR_MC_CASE(11) SABR_MC_CASE(12)
           SABR_MC_CASE(13) SABR_MC_CASE(14) SABR_MC_CASE(15) SABR_MC_CASE(16)
@@ -383,7 +392,32 @@ __global__ void __launch_bounds__(mc_max_threads<R>(), 1) mc_path_kernel(const _
                                                                     const __grid_constant__ McConsts<R> C) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n_instr = a.n_cap + a.n_swp;
-  mc_paths<R, MM>(a, C, (double*)smem, a.part + (size_t)blockIdx.x * n_instr * 2, a.bad + blockIdx.x);
+  mc_paths<R, MM, false>(a, C, (double*)smem, a.part + (size_t)blockIdx.x * n_instr * 2, a.bad + blockIdx.x);
+}
+
+// Many parameter sets in one launch (the annealer's proposals): set blockIdx.y has its constants
+// Cs[set], staged into shared memory ahead of the per-warp sums, and its own CTA sums,
+// part[(set x gridDim.x + CTA) x n_instr x 2], bad[set x gridDim.x + CTA].
+template <class R>
+__host__ __device__ inline size_t mc_batch_smem_bytes(int n_instr, int threads) {
+  return ((sizeof(McConsts<R>) + 127) & ~(size_t)127) + mc_smem_bytes(n_instr, threads);
+}
+
+template <class R, bool MM>
+__global__ void __launch_bounds__(mc_max_threads<R>(), 1) mc_path_batch_kernel(const __grid_constant__ McArgs a,
+                                                                          const McConsts<R>* __restrict__ Cs) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  McConsts<R>& C = *(McConsts<R>*)smem;
+  const int set = blockIdx.y, n_instr = a.n_cap + a.n_swp;
+  {
+    const uint4* src = (const uint4*)(Cs + set);
+    uint4* dst = (uint4*)smem;
+    for (int t = threadIdx.x; t < (int)(sizeof(McConsts<R>) / 16); t += blockDim.x) dst[t] = src[t];
+  }
+  // (mc_paths synchronises the CTA before it reads C)
+  double* acc = (double*)(smem + ((sizeof(McConsts<R>) + 127) & ~(size_t)127));
+  const size_t cta = (size_t)set * gridDim.x + blockIdx.x;
+  mc_paths<R, MM, true>(a, C, acc, a.part + cta * n_instr * 2, a.bad + cta);
 }
 
 // f_s of every set: the Monte Carlo prices from its CTA sums (CTA by CTA in order) against the

@@ -153,6 +153,7 @@ void mc_build_consts(const sabr_lmm_mc_desc* d, int M, const double* tau, const 
   }
   const double* src = (const double*)&c64;
   float* dst = (float*)&c32;
+  static_assert(sizeof(McConsts<double>) == 2 * sizeof(McConsts<float>), "the two layouts must match element by element");
   for (size_t k = 0; k < sizeof(McConsts<double>) / sizeof(double); ++k) dst[k] = (float)src[k];
 }
 
@@ -278,7 +279,9 @@ sabr_lmm_status mc_prepare(const sabr_lmm_mc_desc* d, const sabr_lmm_mc_opts* o,
     p->threads = (int)std::min<long long>(tmax, std::max<long long>(32, (per_cta + 31) / 32 * 32));
   }
   const int t_req = p->threads;
-  while (p->threads > 32 && mc_smem_bytes(ni, p->threads) > kMcSmemMax)
+  // (the annealer's batch kernel also stages one set's constants in shared memory)
+  const size_t extra = shrink ? 0 : ((f64 ? sizeof(McConsts<double>) : sizeof(McConsts<float>)) + 127) & ~(size_t)127;
+  while (p->threads > 32 && mc_smem_bytes(ni, p->threads) + extra > kMcSmemMax)
     p->threads = std::max(32, p->threads / 64 * 32);
   const long long need = (o->n_paths + p->threads - 1) / p->threads;
   // FP32: one CTA per SM, looping over its rounds (as many CTAs per SM as the shared-memory limit
@@ -436,6 +439,74 @@ void sa_step_uniforms(uint64_t seed, uint64_t chain, int level, int step, int co
 
 }  // namespace
 
+namespace {
+// Worker threads that live for one search: run(n, fn) calls fn(i) for i in [0, n) spread over the
+// workers and the caller, and returns when all are done.  Between calls a worker spins for a while
+// (about a millisecond) before it sleeps, so that the next annealing step finds it awake: on a
+// loaded host, waking sleeping threads took longer than the constants they were to build.
+class McPool {
+ public:
+  explicit McPool(unsigned n_workers) {
+    for (unsigned t = 0; t < n_workers; ++t) th_.emplace_back([this] { loop(); });
+  }
+  ~McPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_.store(true);
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  void run(int n, const std::function<void(int)>& fn) {
+    fn_ = &fn;
+    n_ = n;
+    next_.store(0);
+    busy_.store((int)th_.size());
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      gen_.fetch_add(1, std::memory_order_release);
+    }
+    cv_.notify_all();
+    drain();
+    for (int k = 0; k < kSpin && busy_.load(std::memory_order_acquire) != 0; ++k) std::this_thread::yield();
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [this] { return busy_.load() == 0; });
+  }
+
+ private:
+  static constexpr int kSpin = 20000;
+  void drain() {
+    for (int i = next_.fetch_add(1); i < n_; i = next_.fetch_add(1)) (*fn_)(i);
+  }
+  void loop() {
+    unsigned long long seen = 0;
+    for (;;) {
+      for (int k = 0; k < kSpin && !stop_.load() && gen_.load(std::memory_order_acquire) == seen; ++k)
+        std::this_thread::yield();
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_.load() || gen_.load() != seen; });
+        if (stop_.load()) return;
+        seen = gen_.load();
+      }
+      drain();
+      if (busy_.fetch_sub(1) == 1) {
+        std::lock_guard<std::mutex> lk(mu_);
+        done_.notify_one();
+      }
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int n_ = 0;
+  std::atomic<int> next_{0}, busy_{0};
+  std::atomic<unsigned long long> gen_{0};
+  std::atomic<bool> stop_{false};
+};
+}  // namespace
+
 extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const double* quote_vol,
                                               const sabr_lmm_mc_opts* mo, const sabr_lmm_mc_anneal_opts* o,
                                               sabr_lmm_mc_anneal_result* out, void* stream) {
@@ -459,39 +530,31 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
   if (st != SABR_LMM_OK) return st;
   const int C = o->n_chains, L = o->n_levels, N = o->steps_per_level, P = 5, M = p->M, G = p->grid;
   const bool f64 = p->prec == SABR_LMM_FP64;
+  const size_t csz = f64 ? sizeof(McConsts<double>) : sizeof(McConsts<float>);
   cudaStream_t s = (cudaStream_t)stream;
-  // device: the CTA sums and stopped paths of C sets, f, the market prices, and the sorted
-  // instruments' quotes with the tenor grid; host (pinned): f
+  // device: the constants of C sets, their CTA sums and stopped paths, f, the market prices, and the
+  // sorted instruments' quotes with the tenor grid; host (pinned): the constants and f
   Arena A;
-  const size_t o_part = A.take((size_t)C * G * ni * 16), o_bad = A.take((size_t)C * G * 8),
+  const size_t o_cs = A.take((size_t)C * csz), o_part = A.take((size_t)C * G * ni * 16), o_bad = A.take((size_t)C * G * 8),
                o_f = A.take((size_t)C * 8), o_mkt = A.take((size_t)ni * 8), o_vol = A.take((size_t)ni * 8),
                o_cf = A.take((size_t)p->n_cap * 4), o_sa = A.take((size_t)p->n_swp * 4),
                o_T = A.take((size_t)(d->n_fwd + 1) * 8), o_P = A.take((size_t)(d->n_fwd + 1) * 8);
   void* dbuf = nullptr;
+  unsigned char* hcs = nullptr;
   double* hf = nullptr;
-  // the proposals' launches spread over side streams (each launch fills G CTAs of the GPU)
-  constexpr int kSide = 8;
-  cudaStream_t side[kSide] = {};
-  cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
-  bool ok = cudaMalloc(&dbuf, A.size) == cudaSuccess && cudaMallocHost((void**)&hf, (size_t)C * 8) == cudaSuccess &&
-            cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess;
-  for (int k = 0; k < kSide && ok; ++k)
-    ok = cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  const bool ok = cudaMalloc(&dbuf, A.size) == cudaSuccess &&
+                  cudaMallocHost((void**)&hcs, (size_t)C * csz) == cudaSuccess &&
+                  cudaMallocHost((void**)&hf, (size_t)C * 8) == cudaSuccess;
   char* b = (char*)dbuf;
   auto cleanup = [&]() {
     if (dbuf) cudaFree(dbuf);
+    if (hcs) cudaFreeHost(hcs);
     if (hf) cudaFreeHost(hf);
-    for (int k = 0; k < kSide; ++k) {
-      if (side[k]) cudaStreamDestroy(side[k]);
-      if (ev_join[k]) cudaEventDestroy(ev_join[k]);
-    }
-    if (ev_fork) cudaEventDestroy(ev_fork);
     sabr_lmm_mc_plan_free(p);
   };
   if (!ok) {
     cleanup();
-    return fail(SABR_LMM_ENOMEM, "mc_anneal: allocation of the search buffers or streams failed");
+    return fail(SABR_LMM_ENOMEM, "mc_anneal: allocation of the search buffers failed");
   }
   std::vector<double> vol_sorted(ni);
   std::vector<int> cf_sorted(p->n_cap), sa_sorted(p->n_swp);
@@ -521,53 +584,43 @@ extern "C" sabr_lmm_status sabr_lmm_mc_anneal(const sabr_lmm_mc_desc* d, const d
                                                       (const double*)(b + o_vol), (double*)(b + o_mkt));
     e = cudaGetLastError();
   }
-  const size_t sm = mc_smem_bytes(ni, p->threads);   // the plan's kernel: its limit is raised already
+  const size_t smb = f64 ? mc_batch_smem_bytes<double>(ni, p->threads) : mc_batch_smem_bytes<float>(ni, p->threads);
   const bool mmb = p->args.model == SABR_LMM_MODEL_MERCURIO_MORINI;
+  if (e == cudaSuccess && smb > kMcSmemMax) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess)
+    e = f64 ? (mmb ? raise_smem_limit(mc_path_batch_kernel<double, true>, (uint32_t)smb)
+                   : raise_smem_limit(mc_path_batch_kernel<double, false>, (uint32_t)smb))
+            : (mmb ? raise_smem_limit(mc_path_batch_kernel<float, true>, (uint32_t)smb)
+                   : raise_smem_limit(mc_path_batch_kernel<float, false>, (uint32_t)smb));
   if (e != cudaSuccess) {
     cleanup();
     return fail(SABR_LMM_ECUDA, std::string("mc_anneal: ") + cudaGetErrorString(e));
   }
-  // f_s of n points Y [n x 5]: constants on the host (threads); one pricing launch per point, its
-  // constants in the kernel parameters (the constant bank, as in the pricer: every coefficient an
-  // FMA operand), the launches spread over the side streams; f back on `stream`
+  // f_s of n points Y [n x 5]: constants on the host (threads), one batched launch (a CTA grid per
+  // point, its constants staged in shared memory), f back
   const unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  std::vector<McConsts<double>> h64(f64 ? C : 0);
-  std::vector<McConsts<float>> h32(f64 ? 0 : C);
+  McPool pool(std::min<unsigned>(nthr - 1, (unsigned)std::max(0, C - 1)));
   auto evaluate = [&](const std::vector<double>& Y, int n, double* f) -> cudaError_t {
-    auto work = [&](int lo, int hi) {
-      for (int i = lo; i < hi; ++i) {
-        McConsts<double> c64;
-        McConsts<float> c32;
-        mc_build_consts(d, M, p->tau.data(), &Y[(size_t)i * P], c64, c32);
-        if (f64) h64[i] = c64;
-        else h32[i] = c32;
-      }
+    const std::function<void(int)> work = [&](int i) {
+      McConsts<double> c64;
+      McConsts<float> c32;
+      mc_build_consts(d, M, p->tau.data(), &Y[(size_t)i * P], c64, c32);
+      if (f64) std::memcpy(hcs + (size_t)i * csz, &c64, csz);
+      else std::memcpy(hcs + (size_t)i * csz, &c32, csz);
     };
-    std::vector<std::thread> th;
-    const int per = (n + (int)nthr - 1) / (int)nthr;
-    for (int t = 0; t * per < n; ++t) th.emplace_back(work, t * per, std::min(n, (t + 1) * per));
-    for (auto& t : th) t.join();
-    cudaError_t ee = cudaEventRecord(ev_fork, s);
-    for (int k = 0; k < kSide && ee == cudaSuccess; ++k) ee = cudaStreamWaitEvent(side[k], ev_fork, 0);
-    for (int i = 0; i < n && ee == cudaSuccess; ++i) {
-      McArgs ai = ab;
-      ai.part = ab.part + (size_t)i * G * ni * 2;
-      ai.bad = ab.bad + (size_t)i * G;
-      cudaStream_t si = side[i % kSide];
-      if (f64) {
-        if (mmb) mc_path_kernel<double, true><<<G, p->threads, sm, si>>>(ai, h64[i]);
-        else mc_path_kernel<double, false><<<G, p->threads, sm, si>>>(ai, h64[i]);
-      } else {
-        if (mmb) mc_path_kernel<float, true><<<G, p->threads, sm, si>>>(ai, h32[i]);
-        else mc_path_kernel<float, false><<<G, p->threads, sm, si>>>(ai, h32[i]);
-      }
-      ee = cudaGetLastError();
-    }
-    for (int k = 0; k < kSide && ee == cudaSuccess; ++k) {
-      ee = cudaEventRecord(ev_join[k], side[k]);
-      if (ee == cudaSuccess) ee = cudaStreamWaitEvent(s, ev_join[k], 0);
-    }
+    pool.run(n, work);
+    cudaError_t ee = cudaMemcpyAsync(b + o_cs, hcs, (size_t)n * csz, cudaMemcpyHostToDevice, s);
     if (ee != cudaSuccess) return ee;
+    const dim3 grid(G, n);
+    const McConsts<double>* c64 = (const McConsts<double>*)(b + o_cs);
+    const McConsts<float>* c32 = (const McConsts<float>*)(b + o_cs);
+    if (f64) {
+      if (mmb) mc_path_batch_kernel<double, true><<<grid, p->threads, smb, s>>>(ab, c64);
+      else mc_path_batch_kernel<double, false><<<grid, p->threads, smb, s>>>(ab, c64);
+    } else {
+      if (mmb) mc_path_batch_kernel<float, true><<<grid, p->threads, smb, s>>>(ab, c32);
+      else mc_path_batch_kernel<float, false><<<grid, p->threads, smb, s>>>(ab, c32);
+    }
     mc_objective_kernel<<<(n + 3) / 4, 128, 0, s>>>(ab, G, n, (const double*)(b + o_mkt), (double*)(b + o_f));
     if ((ee = cudaGetLastError()) != cudaSuccess) return ee;
     if ((ee = cudaMemcpyAsync(hf, b + o_f, (size_t)n * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return ee;
