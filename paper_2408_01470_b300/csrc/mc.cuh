@@ -1,7 +1,9 @@
-// Monte Carlo pricer of the Hagan SABR/LIBOR model (Section 2.1, Eqs. dinamicasHagan1-2) under
-// the spot measure: the Monte Carlo pricing of caplets and swaptions of Section 3 (Table
+// Monte Carlo pricer of the Hagan SABR/LIBOR model (Section 2.1, Eqs. dinamicasHagan1-2) and of
+// the Mercurio & Morini one (Section 2.2, one volatility process; the MM branch below) under the
+// spot measure: the Monte Carlo pricing of caplets and swaptions of Section 3 (Table
 // tab:haganMCpricer).  One thread per path; the paths of a warp run in lockstep (every path has
-// the same time grid), so the per-instrument sums are warp reductions at the fixing dates.
+// the same time grid), so the per-instrument sums are warp reductions at the fixing dates, and the
+// warps of a CTA meet at every fixing date.
 //
 // Per step of the interval [T_{k-1}, T_k] (h(t) = k, forwards k .. M-1 alive):
 //   xi    : 2a standard normals (a = M - k alive forwards), Philox4x32-10 at counter

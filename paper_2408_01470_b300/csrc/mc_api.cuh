@@ -5,7 +5,8 @@
 // correlation matrix in the spectral sense when it is indefinite (negative eigenvalues set to
 // zero, rows of S Lambda^(1/2) scaled to unit length; eigenvectors by cyclic Jacobi rotations), and
 // its semi-definite Cholesky factor (a pivot at or below 1e-12 ends its column).  Launch: the path
-// kernel (every step of every path) and the reduction kernel, stream-ordered.
+// kernel (every step of every path) and the reduction kernel, stream-ordered.  Mercurio & Morini:
+// the (M + 1) x (M + 1) matrix of (Z, W) with corr(W_i, Z) = phi_i, treated the same way.
 #pragma once
 #include "mc.cuh"
 
