@@ -407,8 +407,8 @@ typedef struct {
 
 /* n_paths in [1, 2^40]; dt > 0: every interval between fixings (and [0, T[0]]) is cut into
  * ceil(len / dt) equal steps; seed: the key of the paths' Philox4x32-10 streams (path p, step s,
- * block b at counter (b, s, p low, p high)); prec: FP64 or FP32 (the path arithmetic; sums in
- * FP64); grid: CTAs (0: enough for every path, at most one wave per SM, the rest looped); a CTA
+ * block b at counter (b, s, p low, p high)); prec: FP64 or FP32 (the path arithmetic and the
+ * payoffs with their sums over a warp's 32 paths; the warp sums accumulated in FP64); grid: CTAs (0: enough for every path, at most one wave per SM, the rest looped); a CTA
  * takes 512 paths in FP32 and 128 in FP64 (fewer, in whole warps, when the paths do not fill one
  * such CTA per SM), halved while its per-warp sums (16 bytes per instrument and warp) would not
  * fit in 227 KB of shared memory.                                                              */

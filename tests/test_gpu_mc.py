@@ -3,8 +3,8 @@ tab:haganMCpricer) on the GPU, through the C-ABI.
 
 FP64: the same paths as the oracle (the same Philox4x32-10 counters, Box-Muller normals, time grid
 and correlation factor), so every price and standard error agrees to rounding order (1e-12
-relative).  FP32: the same normals up to the 24-bit uniforms, the path arithmetic in FP32 and the
-sums in FP64; bar derived below.  At production path counts the no-arbitrage pins of the oracle
+relative).  FP32: the same normals up to the 24-bit uniforms, the path arithmetic, the payoffs and
+their sums over a warp's 32 paths in FP32, the warp sums accumulated in FP64; bar derived below.  At production path counts the no-arbitrage pins of the oracle
 (zero-strike floating legs, the lognormal LMM's Black prices) hold for the device's own paths.
 """
 import os
@@ -65,8 +65,8 @@ def test_mc_fp32_against_the_oracle(gpu_lib):
     # FP32 paths: the uniforms keep 24 of their 32 bits (normals differ by ~1e-7), every state
     # update rounds to 6e-8 of the state, ~700 steps: the forwards at their fixings carry ~1e-6 of
     # themselves, a price ~1e-6 / (moneyness distance) of itself, and the means over paths average
-    # these errors (measured 2.7e-6 relative at most); bar 1e-5 relative on every price above 1e-3
-    # of the largest, 1e-7 absolute below
+    # these errors; a warp's FP32 payoff sum adds ~1e-7 of itself (measured 2.7e-6 relative at most
+    # in all); bar 1e-5 relative on every price above 1e-3 of the largest, 1e-7 absolute below
     import paper_2408_01470_b300 as lib
     sk = _paper()[0]
     model, cf, ck, sa, sb, sK = _instruments(sk)
