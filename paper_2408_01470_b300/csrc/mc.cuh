@@ -109,7 +109,8 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
   const float sa = __fdividef(u0 - 1.0f, u0 + 1.0f), s2 = sa * sa;
   const float ser = 2.0f * sa * fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f), 0.2f), 1.0f / 3.0f), 1.0f);
   const float lu = u0 > 0.75f ? ser : __logf(u0);
-  const float r = sqrtf(-2.0f * lu);
+  float r;   // the MUFU square root (the argument is > 0: u0 < 1)
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-2.0f * lu));
   float s, c;
   __sincosf(6.28318530717958647692f * (u1 - 0.5f), &s, &c);
   z0 = -r * c;
@@ -124,7 +125,11 @@ template <> __device__ __forceinline__ double mc_log<double>(double x) { return 
 template <> __device__ __forceinline__ float mc_log<float>(float x) { return __logf(x); }
 template <class R> __device__ __forceinline__ R mc_rcp(R x);
 template <> __device__ __forceinline__ double mc_rcp<double>(double x) { return 1.0 / x; }
-template <> __device__ __forceinline__ float mc_rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ float mc_rcp<float>(float x) {   // the MUFU reciprocal (x >= 1 here)
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // Payoff inputs in the path precision: FP32 copies of the strikes and accruals for the FP32 paths.
 template <class R> __device__ __forceinline__ R mc_tau(const McArgs& a, int j) {
