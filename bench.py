@@ -326,19 +326,22 @@ def run_profile(args):
 
 def run_mc_profile(args):
     """Three launches of the Monte Carlo pricer on the paper's Hagan model (its 117 caplets, FP32),
-    --mc-paths paths at --mc-dt, for ncu captures."""
+    or with --mc-model mm its Mercurio & Morini model on the same caplets, --mc-paths paths at
+    --mc-dt, for ncu captures."""
     import paper_2408_01470_b300 as lib
     import torch
     from paper_2408_01470_b300 import synth
     lib.load()
     sk, model, cf, ck, _ = synth.paper_hagan_mc_model(PAPER_DATA, PAPER_MM, PAPER_MC)
+    if args.mc_model == "mm":
+        sk, model = synth.paper_mm_mc_model(PAPER_DATA, PAPER_MM)
     s = torch.cuda.Stream()
     plan = lib.McPlan(sk.T, sk.P, model, cf, ck, n_paths=args.mc_paths, dt=args.mc_dt, seed=1, prec=args.prec,
                       stream=s)
     for _ in range(3):
         plan.launch(s)
     s.synchronize()
-    print(json.dumps({"mc_profile": True, "paths": args.mc_paths, "dt": args.mc_dt, "prec": args.prec,
+    print(json.dumps({"mc_profile": True, "model": args.mc_model, "paths": args.mc_paths, "dt": args.mc_dt, "prec": args.prec,
                       "price_first": float(plan.price[0].item()), "n_bad": int(plan.n_bad.item())}))
 
 
@@ -769,7 +772,7 @@ def main():
                     help="the paper's swaption calibration over the Monte Carlo objective alone (--mc-chains, "
                          "--mc-levels, --mc-steps, --mc-paths, --mc-dt)")
     ap.add_argument("--mc-model", default="hagan", choices=["hagan", "mm"],
-                    help="with --mc-calibration: the Hagan or the Mercurio & Morini dynamics")
+                    help="with --mc-calibration or --mc-profile: the Hagan or the Mercurio & Morini dynamics")
     ap.add_argument("--mc-chains", type=int, default=64)
     ap.add_argument("--mc-levels", type=int, default=20)
     ap.add_argument("--mc-steps", type=int, default=5)
